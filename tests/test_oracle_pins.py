@@ -1,0 +1,596 @@
+"""Pins of the CPU oracle against results fixed by the paper or by mathematics.
+
+Nothing here compares the oracle with itself: every check uses an independent
+route -- a library routine (PyTorch's CPU Philox engine, numpy interpolation,
+scipy quadrature and NNLS), a closed form, brute force, or an invariant the
+paper states (weight conservation, rotational symmetry, Eq. 3 totals).
+"""
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize, stats
+
+from oracle import nnls as N
+from oracle import oracle as O
+from paper_1503_01725_b300 import workloads as W
+
+ME = 0.51099895
+RE = 2.8179403262e-13
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 against PyTorch's header-only CPU engine (a library routine)
+# ---------------------------------------------------------------------------
+
+_PHILOX_PROG = r"""
+#include <ATen/core/PhiloxRNGEngine.h>
+#include <cstdio>
+#include <cstdlib>
+int main(int argc, char** argv) {
+  unsigned long long k = strtoull(argv[1], 0, 10), off = strtoull(argv[2], 0, 10),
+                     sub = strtoull(argv[3], 0, 10);
+  at::philox_engine e(k, sub, off);
+  unsigned a = e(), b = e(), c = e(), d = e();
+  printf("%u %u %u %u\n", a, b, c, d);
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def torch_philox():
+    import torch
+    inc = os.path.join(os.path.dirname(torch.__file__), "include")
+    d = tempfile.mkdtemp()
+    src = os.path.join(d, "p.cpp")
+    exe = os.path.join(d, "p")
+    open(src, "w").write(_PHILOX_PROG)
+    try:
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-I", inc, src, "-o", exe],
+                              stderr=subprocess.DEVNULL)
+    except Exception:
+        pytest.skip("cannot compile against PyTorch's Philox header")
+
+    def f(key64, ctr):
+        off = int(ctr[0]) | (int(ctr[1]) << 32)
+        sub = int(ctr[2]) | (int(ctr[3]) << 32)
+        out = subprocess.check_output([exe, str(key64), str(off), str(sub)]).split()
+        return np.array([int(v) for v in out], dtype=np.uint32)
+    return f
+
+
+def test_philox_matches_pytorch_engine(torch_philox):
+    rng = np.random.default_rng(0)
+    cases = [(0, (0, 0, 0, 0)), (2 ** 64 - 1, (2 ** 32 - 1,) * 4), (1, (5, 0, 0, 0)),
+             (123456789, (7, 3, 1, 2 ** 31 + 5))]
+    for _ in range(6):
+        cases.append((int(rng.integers(0, 2 ** 63)), tuple(int(v) for v in rng.integers(0, 2 ** 32, 4))))
+    for key64, ctr in cases:
+        key = (key64 & 0xFFFFFFFF, key64 >> 32)
+        got = O.philox4x32_10(key, ctr)
+        want = torch_philox(key64, ctr)
+        assert np.array_equal(got, want), (key64, ctr, got, want)
+
+
+# ---------------------------------------------------------------------------
+# interaction data
+# ---------------------------------------------------------------------------
+
+def _kn_diff(E, cost):
+    """Klein-Nishina differential cross section per electron, dsigma/dOmega."""
+    k = E / ME
+    ratio = 1.0 / (1.0 + k * (1.0 - cost))
+    return 0.5 * RE * RE * ratio * ratio * (ratio + 1.0 / ratio - (1.0 - cost * cost))
+
+
+@pytest.mark.parametrize("E", [0.01, 0.05, 0.3, 1.0, 2.5, 6.0])
+def test_kn_total_equals_integral_of_differential(E):
+    tot, _ = integrate.quad(lambda c: 2 * np.pi * _kn_diff(E, c), -1.0, 1.0, epsabs=0,
+                            epsrel=1e-12)
+    assert O.kn_sigma(E) == pytest.approx(tot, rel=1e-9)
+
+
+def test_kn_thomson_limit():
+    assert O.kn_sigma(1e-3) == pytest.approx(8 * np.pi / 3 * RE * RE, rel=5e-3)
+
+
+@pytest.mark.parametrize("E", [0.1, 1.0, 6.0])
+def test_kahn_sampler_moments(E):
+    """Sampled <E'/E> and <cos theta> match the KN-weighted quadrature."""
+    s = O.kn_samples(E, 11, 200_000)
+    k = E / ME
+    norm, _ = integrate.quad(lambda c: _kn_diff(E, c), -1, 1, epsrel=1e-12)
+    m_ratio, _ = integrate.quad(lambda c: _kn_diff(E, c) / (1 + k * (1 - c)), -1, 1, epsrel=1e-12)
+    m_cos, _ = integrate.quad(lambda c: _kn_diff(E, c) * c, -1, 1, epsrel=1e-12)
+    for col, want in ((0, m_ratio / norm), (1, m_cos / norm)):
+        x = s[:, col]
+        se = x.std() / np.sqrt(len(x))
+        assert abs(x.mean() - want) < 4 * se, (col, x.mean(), want, se)
+    # full distribution of cos theta against the KN density (KS)
+    cdf = np.vectorize(lambda c: integrate.quad(lambda t: _kn_diff(E, t), -1, c)[0] / norm)
+    grid = np.linspace(-1, 1, 401)
+    cg = cdf(grid)
+    ks = stats.kstest(s[:20000, 1], lambda c: np.interp(c, grid, cg))
+    assert ks.pvalue > 1e-3
+
+
+def test_cross_section_calibration_points():
+    # photoelectric equals Compton at 30 keV in water; pair is 5% at 6 MeV in water
+    assert O.mu_mass(0.03, 0, 1) == pytest.approx(O.mu_mass(0.03, 0, 0), rel=1e-12)
+    assert O.mu_mass(6.0, 0, 2) / O.mu_mass(6.0, 0, 3) == pytest.approx(0.05, rel=1e-12)
+    assert O.mu_mass(1.0, 0, 2) == 0.0
+    assert O.mu_mass(1.0219, 0, 2) == 0.0
+    # photoelectric scales as Z^3 / E^3 per electron
+    r = O.mu_mass(0.1, 1, 1) / O.mu_mass(0.1, 0, 1)
+    assert r == pytest.approx(0.96 * (13.8 / 7.4) ** 3, rel=1e-12)
+    assert O.mu_mass(0.05, 0, 1) / O.mu_mass(0.1, 0, 1) == pytest.approx(8.0, rel=1e-12)
+    # Compton per gram proportional to the electron density
+    assert O.mu_mass(1.0, 1, 0) / O.mu_mass(1.0, 0, 0) == pytest.approx(0.96, rel=1e-12)
+    # total = sum of parts
+    for E in (0.06, 0.5, 2.0, 5.5):
+        assert O.mu_mass(E, 0, 3) == pytest.approx(sum(O.mu_mass(E, 0, c) for c in range(3)),
+                                                   rel=1e-14)
+
+
+def test_bethe_stopping_power_textbook_range():
+    # water collision stopping power ~1.85 MeV cm2/g near 1 MeV (no density effect)
+    assert 1.80 < O.scol_mass(1.0, 0) < 1.90
+    # minimum-ionising behaviour: S falls from 0.2 MeV to a minimum near 1-2 MeV
+    es = np.linspace(0.2, 6.0, 200)
+    s = np.array([O.scol_mass(e, 0) for e in es])
+    assert 0.8 < es[np.argmin(s)] < 2.5
+    assert s[0] > 2.5
+    # CSDA range of a 1 MeV electron in water ~0.44 g/cm2 (integral of 1/S)
+    rng_, _ = integrate.quad(lambda e: 1.0 / O.scol_mass(e, 0), 0.01, 1.0)
+    assert 0.41 < rng_ < 0.46
+    # low-energy 1/beta^2 growth: S * beta^2 varies slowly compared to S
+    def b2(e):
+        g = 1 + e / ME
+        return 1 - 1 / (g * g)
+    assert O.scol_mass(0.2, 0) / O.scol_mass(0.4, 0) == pytest.approx(
+        b2(0.4) / b2(0.2), rel=0.15)
+
+
+def test_highland_special_cases():
+    for E in (0.3, 1.0, 5.0):
+        bcp = E * (E + 2 * ME) / (E + ME)
+        assert O.highland(E, 1.0) == pytest.approx(13.6 / bcp, rel=1e-14)
+    # sqrt(t) scaling with the log correction below t = 1
+    assert O.highland(1.0, 0.01) < O.highland(1.0, 1.0) * 0.1
+
+
+# ---------------------------------------------------------------------------
+# PSR -> PSL conversion (Sec. 2.1.1, Eq. 1-2)
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def model3():
+    return W.psr_model(6, 8, 0.25, seed=5)
+
+
+def test_psl_weights_match_library_interpolation(model3):
+    m = model3
+    p = O.Plan(m, W.beams(W.square_field(10.0)), 1000)
+    nxy = 2 * m.n_r
+    c = (np.arange(nxy) - m.n_r + 0.5) * m.dr
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    r = np.sqrt(X ** 2 + Y ** 2)
+    rc = (np.arange(m.n_r) + 0.5) * m.dr
+    for s in range(3):
+        for e in range(m.n_e):
+            dens = m.w[s, e] / m.dr
+            val = np.interp(r, rc, dens, left=dens[0], right=dens[-1])
+            val[r >= m.n_r * m.dr] = 0.0
+            raw = val / (2 * np.pi * r)
+            want = raw * m.w[s, e].sum() / raw.sum()
+            np.testing.assert_allclose(p.wpsl[s, e], want, rtol=1e-12, atol=1e-18)
+
+
+def test_psl_block_conservation_and_symmetry(model3):
+    p = O.Plan(model3, W.beams(W.square_field(10.0)), 1000)
+    np.testing.assert_allclose(p.wpsl.sum(axis=(2, 3)), model3.w.sum(axis=2), rtol=1e-12)
+    assert p.wpsl.sum() == pytest.approx(1.0, rel=1e-12)
+    w = p.wpsl
+    # rotational symmetry of the ring model survives exactly on the symmetric grid
+    assert np.array_equal(w, np.rot90(w, 1, axes=(2, 3)))
+    assert np.array_equal(w, w[:, :, ::-1, :])
+    assert np.array_equal(w, np.swapaxes(w, 2, 3))
+
+
+def test_psl_ring_mass_converges_to_ring_weight():
+    """Eq. 1: as the rings get wider relative to the curvature of the profile,
+    the PSL mass falling in each ring approaches W_R (error shrinks with dr)."""
+    errs = []
+    for n_r, dr in ((8, 0.5), (16, 0.25), (32, 0.125)):
+        m = W.psr_model(1, n_r, dr, seed=7)
+        rc = (np.arange(n_r) + 0.5) * dr
+        prof = np.exp(-rc ** 2 / 2.0) * rc          # smooth ring profile, same physical shape
+        w = m.w.copy()
+        w[0, 0] = prof / prof.sum() * 0.9
+        m = m.with_weights(w)
+        p = O.Plan(m, W.beams(W.square_field(40.0)), 1000)
+        c = (np.arange(2 * n_r) - n_r + 0.5) * dr
+        X, Y = np.meshgrid(c, c)
+        ring = np.minimum((np.sqrt(X ** 2 + Y ** 2) / dr).astype(int), n_r - 1)
+        mass = np.bincount(ring.ravel(), weights=p.wpsl[0, 0].ravel(), minlength=n_r)
+        # compare cumulative mass inside radius R (less sensitive to edge binning)
+        errs.append(np.max(np.abs(np.cumsum(mass) - np.cumsum(w[0, 0]))) / w[0, 0].sum())
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 0.02
+
+
+# ---------------------------------------------------------------------------
+# sampling areas (Sec. 2.1.2, Fig. 3) and Eq. 3
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("jaw", [(-5, 5, -5, 5), (-2, 6, -4, 1.5), (-1.3, 0.7, -2.9, 3.3)])
+def test_sampling_area_geometry_and_inclusion(jaw):
+    m = W.psr_model(2, 12, 0.25, seed=1)
+    bm = W.beams(np.array(jaw, dtype=float))
+    p = O.Plan(m, bm, 1000)
+    x1, x2, y1, y2 = jaw
+    # primary area: jaw opening scaled by z_phsp / SAD
+    np.testing.assert_allclose(p.area[0, 0], np.array(jaw) * W.Z_PHSP / W.SAD, rtol=1e-14)
+    # scatter area: each edge lies on the line from the field centre at the
+    # isocentre plane through the corresponding jaw edge (collinearity)
+    cx, cy = 0.5 * (x1 + x2), 0.5 * (y1 + y2)
+    for val, edge, zj, c in ((p.area[0, 1, 0], x1, W.Z_JAW_X, cx), (p.area[0, 1, 1], x2, W.Z_JAW_X, cx),
+                             (p.area[0, 1, 2], y1, W.Z_JAW_Y, cy), (p.area[0, 1, 3], y2, W.Z_JAW_Y, cy)):
+        a = np.array([c, W.SAD])
+        b = np.array([edge * zj / W.SAD, zj])
+        q = np.array([val, W.Z_PHSP])
+        cross = (b - a)[0] * (q - a)[1] - (b - a)[1] * (q - a)[0]
+        assert abs(cross) < 1e-9
+    # inclusion: brute force over interior points of every PSL square
+    n = p.n_xy
+    res = 4000
+    t = (np.arange(1, res) / res)
+    for cls in range(2):
+        xa, xb, ya, yb = p.area[0, cls]
+        for iy in range(n):
+            for ix in range(n):
+                xs = (ix - m.n_r + t) * m.dr
+                ys = (iy - m.n_r + t) * m.dr
+                hit = np.any((xs > xa) & (xs < xb)) and np.any((ys > ya) & (ys < yb))
+                if bool(p.incl[0, cls, iy, ix]) != hit:
+                    # only an overlap thinner than the point grid may be missed
+                    lo = np.array([ix - m.n_r, iy - m.n_r]) * m.dr
+                    gaps = np.abs(np.concatenate([lo + m.dr - [xa, ya], [xb, yb] - lo]))
+                    assert gaps.min() < m.dr / res, (cls, ix, iy)
+
+
+def test_eq3_counts_total_and_rounding():
+    m = W.psr_model(5, 10, 0.25, seed=9)
+    bm = W.beams(W.square_field(10.0), W.square_field(4.0, cx=1.0))
+    N_ = 123_457
+    p = O.Plan(m, bm, N_)
+    assert p.count.sum() == N_
+    # q = N W / D over included PSLs; every count is floor(q) or floor(q)+1
+    q = np.zeros_like(p.count, dtype=float)
+    D = 0.0
+    for b in range(2):
+        for s in range(3):
+            inc = p.incl[b, 1 if s else 0].astype(bool)
+            D += p.wpsl[s][:, inc].sum()
+    assert D == pytest.approx(p.denom, rel=1e-12)
+    for b in range(2):
+        for s in range(3):
+            inc = p.incl[b, 1 if s else 0].astype(bool)
+            q[b, s][:, inc] = N_ * p.wpsl[s][:, inc] / D
+            assert np.all(p.count[b, s][:, ~inc] == 0)
+    fl = np.floor(q)
+    assert np.all((p.count == fl) | (p.count == fl + 1))
+    # the +1s go to the largest remainders
+    rem = (q - fl).ravel()
+    up = (p.count - fl).ravel() == 1
+    if up.any() and (~up).any():
+        assert rem[up].min() >= rem[~up & (q.ravel() > 0)].max() - 1e-12
+    # prefix over entries in loop order (beam, stype, energy, y, x)
+    assert p.ent_start[-1] == N_
+    e = p.entries
+    key = ((e[:, 0] * 3 + e[:, 1]) * m.n_e + e[:, 2]) * p.n_xy ** 2 + e[:, 4] * p.n_xy + e[:, 3]
+    assert np.all(np.diff(key) > 0)
+    cnt = p.count[e[:, 0], e[:, 1], e[:, 2], e[:, 4], e[:, 3]]
+    assert np.array_equal(np.diff(p.ent_start), cnt)
+
+
+def test_per_psr_plan_is_linear_share_of_whole_plan():
+    m = W.psr_model(4, 6, 0.3, seed=3)
+    bm = W.beams(W.square_field(10.0), W.square_field(4.0))
+    n_k = np.full(m.n_psr, 500, dtype=np.int64)
+    pk = O.Plan(m, bm, per_psr_n=n_k)
+    assert pk.count.sum(axis=(2, 3)).tolist() == [[500, 500]] * m.n_psr or \
+        np.all((pk.count.sum(axis=(2, 3)) == 500) | (pk.count.sum(axis=(2, 3)) == 0))
+    # sum over PSRs of their in-area weight equals each beam's whole-plan share
+    for b in range(2):
+        bb = W.beams(bm.jaws[b])
+        whole = O.Plan(m, bb, 1000)
+        sel = pk.entries[:, 0] == b
+        k = pk.entries[sel, 5]
+        dk = {}
+        for kk, sc in zip(k, pk.ent_scale[sel]):
+            dk[kk] = sc * 500
+        assert sum(dk.values()) == pytest.approx(whole.denom, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# sampling, steps S3-S5
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def sampled():
+    m = W.psr_model(4, 10, 0.25, seed=21)
+    bm = W.beams(W.square_field(10.0, cx=0.5, cy=-0.3))
+    p = O.Plan(m, bm, 60_000)
+    s = O.sample(p, 77, 0, 60_000)
+    return m, bm, p, s
+
+
+def test_samples_lie_in_their_psl_and_energy_bin(sampled):
+    m, bm, p, s = sampled
+    e = p.entries[s["entry"]]
+    xl = (e[:, 3] - m.n_r) * m.dr
+    yl = (e[:, 4] - m.n_r) * m.dr
+    assert np.all((s["xp"] > xl) & (s["xp"] <= xl + m.dr + 1e-12))
+    assert np.all((s["yp"] > yl) & (s["yp"] <= yl + m.dr + 1e-12))
+    lo = m.e_lo[s["stype"]] + s["ebin"] * m.de[s["stype"]]
+    assert np.all((s["E"] > lo) & (s["E"] <= lo + m.de[s["stype"]] + 1e-12))
+    # every history maps to the entry whose prefix range holds it
+    g = np.arange(len(s["x"]))
+    assert np.all(p.ent_start[s["entry"]] <= g) and np.all(g < p.ent_start[s["entry"] + 1])
+    # included PSLs only
+    cls = (s["stype"] > 0).astype(int)
+    assert np.all(p.incl[0, cls, e[:, 4], e[:, 3]] == 1)
+
+
+def test_jaw_rejection_is_exact_straight_line_test(sampled):
+    m, bm, p, s = sampled
+    x1, x2, y1, y2 = bm.jaws[0]
+    yJ = s["yp"] + (W.Z_JAW_Y - W.Z_PHSP) * s["vp"] / s["wp"]
+    xJ = s["xp"] + (W.Z_JAW_X - W.Z_PHSP) * s["up"] / s["wp"]
+    inside = (yJ >= y1 * W.Z_JAW_Y / W.SAD) & (yJ <= y2 * W.Z_JAW_Y / W.SAD) & \
+             (xJ >= x1 * W.Z_JAW_X / W.SAD) & (xJ <= x2 * W.Z_JAW_X / W.SAD)
+    assert np.array_equal(inside, s["status"] == 0)
+    assert 0.3 < inside.mean() < 1.0
+    # transport start: straight line from the plane to the phantom surface
+    np.testing.assert_allclose(s["x"], s["xp"] + (W.SSD - W.Z_PHSP) * s["up"] / s["wp"], rtol=1e-12)
+    np.testing.assert_allclose(s["u"] ** 2 + s["v"] ** 2 + s["w"] ** 2, 1.0, rtol=1e-12)
+
+
+def test_primary_direction_pencil_limit():
+    """sigma_s -> 0 in Eq. 4: the direction is the unit vector from the target to (x, y, z_phsp)."""
+    m = W.psr_model(3, 6, 0.3, sigma_s=0.0, seed=2, weights=(1.0, 0.0, 0.0))
+    p = O.Plan(m, W.beams(W.square_field(20.0)), 5000)
+    s = O.sample(p, 3, 0, 5000)
+    n = np.sqrt(s["xp"] ** 2 + s["yp"] ** 2 + W.Z_PHSP ** 2)
+    np.testing.assert_allclose(s["up"], s["xp"] / n, atol=1e-13)
+    np.testing.assert_allclose(s["vp"], s["yp"] / n, atol=1e-13)
+    np.testing.assert_allclose(s["wp"], W.Z_PHSP / n, atol=1e-13)
+
+
+def _local_angles(s):
+    th = np.arctan2(s["yp"], s["xp"])
+    ul = s["up"] * np.cos(th) + s["vp"] * np.sin(th)
+    vl = -s["up"] * np.sin(th) + s["vp"] * np.cos(th)
+    return np.arctan(ul / s["wp"]), np.arctan(vl / s["wp"])
+
+
+def test_primary_spot_direction_moments():
+    """Eq. 4-5: in the local frame, (r - x_s, -y_s) / z_phsp with Gaussian spot."""
+    m = W.psr_model(2, 8, 0.25, sigma_s=0.15, seed=4, weights=(1.0, 0.0, 0.0))
+    p = O.Plan(m, W.beams(W.square_field(20.0)), 40_000)
+    s = O.sample(p, 5, 0, 40_000)
+    th = np.arctan2(s["yp"], s["xp"])
+    ul = s["up"] * np.cos(th) + s["vp"] * np.sin(th)
+    vl = -s["up"] * np.sin(th) + s["vp"] * np.cos(th)
+    r = np.hypot(s["xp"], s["yp"])
+    xs = r - ul / s["wp"] * W.Z_PHSP
+    ys = -vl / s["wp"] * W.Z_PHSP
+    for v in (xs, ys):
+        assert abs(v.mean()) < 4 * 0.15 / np.sqrt(len(v))
+        assert v.std() == pytest.approx(0.15, rel=0.02)
+    assert abs(np.corrcoef(xs, ys)[0, 1]) < 0.03
+
+
+def test_electron_direction_moments():
+    m = W.psr_model(3, 8, 0.25, seed=8, weights=(0.0, 0.0, 1.0))
+    m.e_sa[:] = 0.04
+    m.e_sb[:] = 0.07
+    p = O.Plan(m, W.beams(W.square_field(40.0)), 40_000)
+    s = O.sample(p, 9, 0, 40_000)
+    a, b = _local_angles(s)
+    assert np.all(s["type"] == 1)
+    assert a.std() == pytest.approx(0.04, rel=0.02) and b.std() == pytest.approx(0.07, rel=0.02)
+    assert abs(a.mean()) < 4 * 0.04 / np.sqrt(len(a))
+
+
+def test_scatter_mixture_moments_and_component_frequencies():
+    m = W.psr_model(2, 6, 0.3, seed=12, weights=(0.0, 1.0, 0.0))
+    p = O.Plan(m, W.beams(W.square_field(40.0)), 80_000)
+    s = O.sample(p, 13, 0, 80_000)
+    a, b = _local_angles(s)
+    # ring from the sampled radius (S4)
+    r = np.hypot(s["xp"], s["yp"])
+    ring = np.minimum((r / m.dr).astype(int), m.n_r - 1)
+    near = np.abs(r / m.dr - np.round(r / m.dr)) < 1e-5
+    assert np.array_equal(ring[~near], s["ring"][~near])
+    for e in range(m.n_e):
+        for i in range(m.n_r):
+            sel = (s["ebin"] == e) & (s["ring"] == i)
+            if sel.sum() < 2000:
+                continue
+            c, mu, sa = m.mix_c[e, i], m.mix_mu[e, i], m.mix_sa[e, i]
+            freq = np.bincount(s["comp"][sel], minlength=3)
+            chi = stats.chisquare(freq, c / c.sum() * sel.sum())
+            assert chi.pvalue > 1e-4
+            mean = (c * mu).sum()
+            var = (c * (sa ** 2 + mu ** 2)).sum() - mean ** 2
+            n = sel.sum()
+            assert abs(a[sel].mean() - mean) < 4 * np.sqrt(var / n)
+            assert a[sel].var() == pytest.approx(var, rel=0.1)
+            for k in range(3):
+                sk = sel & (s["comp"] == k)
+                if sk.sum() > 300:
+                    assert abs(a[sk].mean() - mu[k]) < 4 * sa[k] / np.sqrt(sk.sum())
+
+
+def test_psr_tag_follows_interpolation_shares(sampled):
+    m, bm, p, s = sampled
+    e = p.entries[s["entry"]]
+    r0 = p.tag_r0[e[:, 4], e[:, 3]]
+    l0 = p.tag_l0[e[:, 4], e[:, 3]]
+    R = s["psr"] % m.n_r
+    assert np.all((R == r0) | (R == r0 + 1))
+    mid = l0 < 1.0
+    w = m.w[s["stype"], s["ebin"]]
+    a0 = l0 * w[np.arange(len(R)), r0]
+    a1 = (1 - l0) * w[np.arange(len(R)), np.minimum(r0 + 1, m.n_r - 1)]
+    p0 = np.where(mid, a0 / (a0 + a1), 1.0)
+    got = (R == r0).astype(float)
+    # aggregated over all histories: sum of Bernoulli(p0)
+    assert abs(got[mid].sum() - p0[mid].sum()) < 4 * np.sqrt((p0[mid] * (1 - p0[mid])).sum())
+
+
+def test_open_field_positions_are_isotropic():
+    m = W.psr_model(2, 10, 0.25, seed=14)
+    p = O.Plan(m, W.beams(W.square_field(40.0)), 60_000)
+    s = O.sample(p, 15, 0, 60_000)
+    r = np.hypot(s["xp"], s["yp"])
+    sel = r < m.n_r * m.dr * 0.95
+    ang = np.arctan2(s["yp"][sel], s["xp"][sel])
+    hist = np.histogram(ang, bins=16, range=(-np.pi, np.pi))[0]
+    assert stats.chisquare(hist).pvalue > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# transport (stated simplification)
+# ---------------------------------------------------------------------------
+
+def test_first_collision_depth_is_beer_lambert():
+    ph = W.water_phantom(8, 8, 100, 1.0, dz=10.0)   # 1000 cm deep
+    for E, co in ((0.5, 1), (2.0, 0), (6.0, 0)):
+        mu = O.mu_mass(E, 0, 0 if co else 3)
+        for fmaj in (1.0, 2.0):
+            d = O.first_collision(ph, E, 3, 40_000, compton_only=co, majorant_factor=fmaj)
+            assert np.all(d >= 0)   # exp(-mu 1000 cm) ~ 1e-12: none leave uncollided
+            ks = stats.kstest(d, "expon", args=(0, 1.0 / mu))
+            assert ks.pvalue > 1e-4, (E, fmaj, ks)
+
+
+def test_csda_path_length_matches_range_integral():
+    ph = W.water_phantom(4, 4, 400, 0.25)
+    for E in (0.5, 2.0, 5.0):
+        rng_, _ = integrate.quad(lambda e: 1.0 / O.scol_mass(e, 0), 0.2, E)
+        path, dep = O.electron_path(ph, E, ms_off=1, f_e=0.05)
+        # midpoint stepping: the residual below the 200 keV cutoff is deposited locally
+        assert path == pytest.approx(rng_, rel=0.01)
+        assert dep == pytest.approx(E, rel=1e-12)
+
+
+@pytest.fixture(scope="module")
+def small_dose():
+    wl = W.workload_full_10x10(4000)
+    ph = W.water_phantom(24, 24, 40, 0.5)
+    p = O.Plan(wl.model, wl.beams, wl.n_hist)
+    r = O.run(p, ph, 5, n_batches=8, electron_mode=1)
+    return wl, ph, p, r
+
+
+def test_energy_conservation_per_history(small_dose):
+    wl, ph, p, r = small_dose
+    L = r["ledger"]
+    assert r["max_balance"] < 1e-12
+    assert L["source"] == pytest.approx(L["rejected"] + L["escaped"] + L["deposited"], rel=1e-13)
+    assert r["s1"].sum() == pytest.approx(L["deposited"], rel=1e-12)
+    assert r["cap_hits"] == 0
+
+
+def test_dose_mirror_symmetry_of_centred_field(small_dose):
+    wl, ph, p, r = small_dose
+    d, sd = O.dose_and_sigma(r["s1"], r["s2"], r["n_batches"])
+    dm = d[:, :, ::-1]
+    sm = sd[:, :, ::-1]
+    sel = d > 0.2 * d.max()
+    z = (d - dm)[sel] / np.sqrt(sd[sel] ** 2 + sm[sel] ** 2 + 1e-30)
+    assert np.mean(np.abs(z) < 4) > 0.98
+
+
+def test_woodcock_majorant_inflation_is_unbiased():
+    wl = W.workload_primary_5x5(30_000)
+    ph = W.heterogeneous_phantom(16, 16, 24, 0.5, seed=6, n_slabs=3, n_spheres=4)
+    p = O.Plan(wl.model, wl.beams, wl.n_hist)
+    a = O.run(p, ph, 7, n_batches=8, electron_mode=0)
+    b = O.run(p, ph, 7, n_batches=8, electron_mode=0, majorant_factor=2.0)
+    assert b["stats"]["flights"] > 1.5 * a["stats"]["flights"]
+    assert a["ledger"]["deposited"] == pytest.approx(b["ledger"]["deposited"], rel=0.02)
+    da, sa = O.dose_and_sigma(a["s1"], a["s2"], 8)
+    db, sb = O.dose_and_sigma(b["s1"], b["s2"], 8)
+    sel = da > 0.2 * da.max()
+    z = (da - db)[sel] / np.sqrt(sa[sel] ** 2 + sb[sel] ** 2 + 1e-30)
+    assert np.mean(np.abs(z) < 4) > 0.98
+
+
+def test_basis_tally_sums_to_dose_tally(small_dose):
+    """Sec. 2.2.2: summing the PSR columns of the 2D dose array gives back the
+    dose of the same histories at the indexed voxels."""
+    wl, ph, p, r = small_dose
+    idx, n_rows = W.commissioning_index(ph, depths_cm=(1.5, 10.0))
+    rb = O.run(p, ph, 5, n_batches=8, electron_mode=1, tally_mode=1, idx3d=idx, n_rows=n_rows)
+    A = rb["s1"]
+    vox = np.flatnonzero(idx.ravel())
+    rows = idx.ravel()[vox] - 1
+    np.testing.assert_allclose(A.sum(axis=1)[rows], r["s1"].ravel()[vox], rtol=1e-10, atol=1e-9)
+    # only PSRs of the model appear; electrons-only columns only get electron energy
+    assert A.shape[1] == wl.model.n_psr
+
+
+# ---------------------------------------------------------------------------
+# commissioning NNLS (Eq. 8, Sec. 2.2.4)
+# ---------------------------------------------------------------------------
+
+def _rand_problem(m, n, seed, cond=1e3):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = np.logspace(0, -np.log10(cond), n)
+    A = U @ np.diag(s) @ V.T
+    b = rng.standard_normal(m)
+    return A, b
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_lawson_hanson_matches_scipy(seed):
+    A, b = _rand_problem(60, 25, seed)
+    x, _ = N.lawson_hanson(A, b)
+    xs, _ = optimize.nnls(A, b)
+    np.testing.assert_allclose(x, xs, atol=1e-9)
+    assert N.kkt_residual(A, b, x) < 1e-10 * np.linalg.norm(A.T @ b)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_brute_force_agrees_on_tiny(seed):
+    A, b = _rand_problem(20, 8, 100 + seed, cond=30)
+    xb = N.brute_force(A, b)
+    x, _ = N.lawson_hanson(A, b)
+    np.testing.assert_allclose(x, xb, atol=1e-10)
+
+
+def test_gradient_projection_reaches_kkt_point():
+    A, b = _rand_problem(80, 20, 7, cond=20)
+    x, it, ok = N.gradient_projection(A, b, delta=1e-15)
+    xs, _ = optimize.nnls(A, b)
+    assert ok
+    assert N.objective(A, b, x) == pytest.approx(N.objective(A, b, xs), rel=1e-8)
+    np.testing.assert_allclose(x, xs, atol=1e-5)
+
+
+def test_noiseless_recovery():
+    rng = np.random.default_rng(3)
+    A = np.abs(rng.standard_normal((200, 30)))
+    xt = rng.uniform(0.8, 1.2, 30)
+    xt[[3, 17]] = 0.0
+    x, _ = N.lawson_hanson(A, A @ xt)
+    np.testing.assert_allclose(x, xt, atol=1e-8)
