@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the analytic-source-model dose calculation on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step is one pass of the whole hot path over one workload: PSR -> PSL
+conversion with sampling areas and Eq. 3 counts (lsm_build_psl), then n_batches
+passes of [sample M histories -> transport photons -> annihilation photons ->
+electrons -> tally flush] (lsm_run), then dose and batch uncertainty
+(lsm_dose). The workload is all three sub-sources, a 10x10 cm2 field, water
+64^3 at 0.25 cm, 1e7 histories, CSDA electrons (synthetic inputs from
+paper_1503_01725_b300.workloads). Prints one JSON line.
+
+Metric: histories/s (source histories including jaw-rejected ones, per second
+of device time) and seconds to 1% dose uncertainty, t_1% = T (u / 0.01)^2 with
+u the mean batch relative standard deviation over voxels above 50% of Dmax.
+
+--impl reference times the CPU oracle (plain single-threaded FP64 C) on a
+bounded sample of the same workload on this host's cores.
+Under torchrun (N > 1) every rank runs the same workload with its own Philox
+key (independent histories, no data-path collective: weak scaling); rank 0
+prints the line with the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+
+# Algorithmic bytes per unit of work (measurement section):
+#   sampling: per history, plan lookup (16 B entry + 8 B prefix) + particle write (44 B);
+#   photon transport: per Woodcock flight one density load (4 B), per photon the
+#     queue read (44 B), per real interaction one tally update (8 B) or queue write (44 B);
+#   electron transport: per CSDA step one density load (4 B) + one tally update
+#     (4 B read + 4 B write), per electron the queue read (44 B).
+B_SAMPLE_PER_HIST = 68.0
+B_FLIGHT = 4.0
+B_QUEUE = 44.0
+B_DEPOSIT = 8.0
+B_ESTEP = 12.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n-hist", type=int, default=10_000_000)
+    p.add_argument("--n-batches", type=int, default=16)
+    p.add_argument("--chunk", type=int, default=131072)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            P = json.load(f)
+        return float(P["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self) -> dict:
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for k, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(k)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def u_mean_rel(dose: np.ndarray, sigma: np.ndarray) -> float:
+    sel = dose > 0.5 * dose.max()
+    return float(np.mean(sigma[sel] / dose[sel]))
+
+
+def cpu_oracle_rate(wl, seconds: float, per_step_hist: int = 100_000):
+    """Oracle histories/s on a bounded sample: repeated 1e5-history plans of the
+    same workload (same model, field, phantom) with fresh seeds."""
+    from oracle import oracle as O
+    plan = O.Plan(wl.model, wl.beams, per_step_hist)
+    done, t0, seed = 0, time.perf_counter(), 1000
+    while True:
+        O.run(plan, wl.phantom, seed, n_batches=1, electron_mode=wl.electron_mode)
+        done += per_step_hist
+        seed += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return done / el, done, el
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle, as it stands, timed on this host (reference arm)."""
+    from paper_1503_01725_b300 import workloads as W
+    if rank != 0:
+        return
+    wl = W.workload_full_10x10(args.n_hist)
+    from oracle import oracle as O
+    per = 50_000
+    plan = O.Plan(wl.model, wl.beams, per)
+    for i in range(args.warmup):
+        O.run(plan, wl.phantom, 10 + i, n_batches=1, electron_mode=1)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        O.run(plan, wl.phantom, 100 + i, n_batches=1, electron_mode=1)
+    el = time.perf_counter() - t0
+    rate = per * args.steps / el
+    line = {
+        "impl": "reference", "metric": "histories/s", "value": rate, "unit": "histories/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n_hist_workload": args.n_hist,
+                   "sample": f"{per} histories per step (one pass of a {per}-history plan of the same workload)"},
+        "cpu_baseline": {"value": rate, "unit": "histories/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} x {per} histories"},
+        "e2e": {"value": rate, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_1503_01725_b300 import lsm
+    from paper_1503_01725_b300 import workloads as W
+
+    lsm.load_library()
+    wl = W.workload_full_10x10(args.n_hist)
+    n_plan = args.n_hist // args.n_batches
+    opts = lsm.RunOpts(electron_mode=1, n_batches=args.n_batches, chunk=args.chunk)
+    seed0 = 1 + 7919 * rank
+    stream = torch.cuda.current_stream()
+
+    # device-resident inputs: phantom and tally created once
+    ph = lsm.lsm_phantom_create(W.Phantom(**{**wl.phantom.__dict__,
+                                            "rho": torch.tensor(wl.phantom.rho, device="cuda"),
+                                            "mat": torch.tensor(wl.phantom.mat, device="cuda")}))
+    ph.desc = wl.phantom
+    tally = lsm.lsm_tally_create(ph)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(i):
+        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)
+        lsm.lsm_tally_reset(tally)
+        lsm.lsm_run(psl, ph, tally, seed0 + i, opts)
+        d, s = lsm.lsm_dose(tally, ph, psl.denom / n_plan, device=True)
+        return psl, d, s
+
+    for i in range(args.warmup):
+        step(1000 + i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    lsm.lsm_timing_read(reset=True)
+    lsm.lsm_timing_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = lsm.lsm_launch_count()
+    ms_steps = []
+    u_vals = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)                      # L2 flush outside the timed events
+            ev[i][0].record(stream)
+            _, d, s = step(i)
+            ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            ms_steps.append(ev[i][0].elapsed_time(ev[i][1]))
+            u_vals.append(u_mean_rel(d.cpu().numpy(), s.cpu().numpy()))
+    launches = lsm.lsm_launch_count() - launches0
+    timers = lsm.lsm_timing_read(reset=True)
+    lsm.lsm_timing_enable(False)
+    led, st = lsm.lsm_tally_ledger(tally)      # counters of the last step (reset each step)
+    total_ms = float(sum(ms_steps))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # end-to-end through the public API with host buffers
+    e2e_s, h2d, d2h = [], 0, 0
+    for i in range(max(2, min(3, args.steps))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        phh = lsm.lsm_phantom_create(wl.phantom)              # host rho/mat -> device
+        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)   # host model arrays -> device
+        tt = lsm.lsm_tally_create(phh)
+        lsm.lsm_run(psl, phh, tt, 5000 + i, opts)
+        dose, sig = lsm.lsm_dose(tt, phh, psl.denom / n_plan)  # device -> host
+        e2e_s.append(time.perf_counter() - t0)
+        h2d = wl.phantom.rho.nbytes + wl.phantom.mat.nbytes + sum(
+            np.asarray(getattr(wl.model, k)).nbytes for k in ("w", "mix_c", "mix_mu", "mix_sa", "mix_sb", "e_sa", "e_sb")) \
+            + wl.beams.jaws.nbytes
+        d2h = dose.nbytes + sig.nbytes
+        del tt, phh, psl
+    e2e_rate = world * args.n_hist / statistics.median(e2e_s)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hist_total = world * args.n_hist * args.steps
+    value = hist_total / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+    u = float(np.mean(u_vals))
+    t1 = ms_per_step / 1e3 * (u / 0.01) ** 2
+
+    # roofline of the dominant kernel group, algorithmic bytes / event-timed duration
+    hbm, hbm_kind = peaks()
+    n_st = args.steps
+    per_step = {k: v[0] / n_st for k, v in timers.items()}
+    units = {
+        "sample": args.n_hist * B_SAMPLE_PER_HIST,
+        "photon": st["flights"] * B_FLIGHT + st["photons"] * B_QUEUE + st["real"] * B_DEPOSIT,
+        "electron": st["esteps"] * B_ESTEP + st["electrons"] * B_QUEUE,
+    }
+    dom = max(("sample", "photon", "electron"), key=lambda k: per_step[k])
+    achieved = units[dom] / (per_step[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "peak_source": f"{hbm_kind} hbm_gbs",
+                "algorithmic_bytes_per_step": units[dom]}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, n_done, el = cpu_oracle_rate(wl, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "histories/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_done} histories as 1e5-history plans of the same workload, {el:.1f} s"}
+    line = {
+        "metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "n_hist": args.n_hist, "n_batches": args.n_batches,
+                   "chunk": args.chunk, "phantom": "water 64^3 x 0.25 cm", "field_cm": 10,
+                   "sub_sources": 3, "electrons": "CSDA", "parallelism": f"replicas x{world}",
+                   "l2": "flushed by a 512 MiB write before each step, outside the timed events"},
+        "s_to_1pct": t1, "u_mean_rel_D50": u,
+        "kernels_ms_per_step": {k: round(v, 4) for k, v in per_step.items() if v > 0},
+        "work_per_step": {"photons": st["photons"], "electrons": st["electrons"], "flights": st["flights"],
+                          "real": st["real"], "esteps": st["esteps"], "rejected": st["rejected"]},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_rate, "unit": "histories/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

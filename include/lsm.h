@@ -1,0 +1,346 @@
+/*
+ * lsm.h -- C ABI of liblsm.so: the analytic linac source model of Tian et al.,
+ * "An analytic linear accelerator source model for Monte Carlo dose
+ * calculations. II. Model utilization in a GPU-based Monte Carlo package and
+ * automatic source commissioning" (arXiv:1503.01725), on one B300 GPU.
+ *
+ * Conventions
+ *   - Every call returns lsm_status. LSM_ERR_ARG: an argument failed
+ *     validation before any GPU work was queued (nothing was changed).
+ *     LSM_ERR_CUDA: a CUDA runtime call failed; the message is available from
+ *     lsm_last_error(). LSM_ERR_OVERFLOW / LSM_ERR_TIMEOUT: the GPU work ran to
+ *     completion but a bounded resource (a particle queue, a step cap, a
+ *     bounded wait) was exhausted; results are complete except for the counted
+ *     events, which were handled as documented at the call.
+ *   - Handles (lsm_psl, lsm_phantom, lsm_tally) are opaque, created and owned
+ *     by the library, and must be released with the matching *_destroy. A
+ *     handle lives on the device that was current when it was created.
+ *   - Input arrays are owned by the caller and are only read during the call
+ *     (host pointers are copied before the call returns).
+ *   - lsm_mem says whether a pointer is host or device memory; device pointers
+ *     may come from any allocator (e.g. PyTorch tensors).
+ *   - lsm_stream is a cudaStream_t (NULL = legacy default stream). Calls that
+ *     take a stream return once the work is queued, unless stated otherwise;
+ *     results written to device memory are stream-ordered. Calls that write
+ *     host memory synchronise the stream before returning.
+ *   - Positions are in cm along a beam axis from the target (z = 0) towards
+ *     the phantom; energies in MeV; angles in radians.
+ */
+#ifndef LSM_H
+#define LSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSM_OK = 0,
+    LSM_ERR_ARG = 1,
+    LSM_ERR_CUDA = 2,
+    LSM_ERR_OVERFLOW = 3,
+    LSM_ERR_TIMEOUT = 4,
+    LSM_ERR_NOT_CONVERGED = 5
+} lsm_status;
+
+typedef enum { LSM_MEM_HOST = 0, LSM_MEM_DEVICE = 1 } lsm_mem;
+
+typedef void *lsm_stream;              /* cudaStream_t */
+typedef struct lsm_psl lsm_psl;
+typedef struct lsm_phantom lsm_phantom;
+typedef struct lsm_tally lsm_tally;
+
+/* Sub-source types (Sec. 2.1.3): 0 primary photon, 1 scatter photon, 2 electron. */
+#define LSM_N_STYPE 3
+/* Gaussian components of the scatter-photon direction model (Eq. 6, K = 3). */
+#define LSM_K_MIX 3
+
+/*
+ * PSR model (Sec. 2.1.1; the model and its parameters come from part I of the
+ * paper). A PSR is (sub-source s, energy bin e, ring R). Ring R covers radii
+ * [R dr, (R+1) dr) on the phase-space plane at z = z_phsp; energy bin e of
+ * sub-source s covers [e_lo[s] + e de[s], e_lo[s] + (e+1) de[s]).
+ * All arrays are host memory, C order.
+ *   w       [3][n_e][n_r]   PSR weights (>= 0, finite)
+ *   sigma_s                 primary focal-spot Gaussian width (Eq. 4), cm
+ *   mix_c   [n_e][n_r][3]   scatter mixture weights c_{i,k} (Eq. 6), >= 0, sum > 0
+ *   mix_mu  [n_e][n_r][3]   mixture means mu_{i,k} of alpha
+ *   mix_sa, mix_sb          mixture widths sigma_alpha, sigma_beta
+ *   e_sa, e_sb [n_e][n_r]   electron direction widths (Eq. 7)
+ * Validation: 1 <= n_e <= 64, 1 <= n_r <= 32, dr > 0, z_phsp > 0, de > 0,
+ * sigma_s >= 0, |mu| + 5.8 sigma_alpha < pi/2 and 5.8 sigma_beta < pi/2 for
+ * every component (the largest Gaussian deviate the sampler can draw is 5.77).
+ */
+typedef struct {
+    int32_t n_e, n_r;
+    double dr, z_phsp, sigma_s;
+    double e_lo[3], de[3];
+    const double *w, *mix_c, *mix_mu, *mix_sa, *mix_sb, *e_sa, *e_sb;
+} lsm_psr_model;
+
+/*
+ * Beams of a plan (step S1). Jaw edges x1 < x2, y1 < y2 are given at the
+ * isocentre plane z = sad; the Y and X jaws have their upper surfaces at
+ * z_jaw_y and z_jaw_x (z_phsp < z_jaw < sad). jaws: host [n_beams][4]
+ * (x1, x2, y1, y2). 1 <= n_beams <= 16.
+ */
+typedef struct {
+    double sad, z_jaw_y, z_jaw_x;
+    int32_t n_beams;
+    const double *jaws;
+} lsm_beams;
+
+/*
+ * lsm_build_psl -- Sec. 2.1.1-2.1.3 (Eq. 1-3, Fig. 3), on the GPU in FP64.
+ * Converts the PSR model to its PSL representation on a 2 n_r x 2 n_r grid of
+ * pitch dr centred on the axis (steps 1-4 of Sec. 2.1.1, normalised per
+ * (sub-source, energy bin) block), determines the sampling areas of every
+ * beam (primary: jaw opening scaled to the plane; scatter and electrons: upper
+ * jaw surfaces back-projected from the field centre on the isocentre plane,
+ * X and Y separately, intersected), keeps the PSLs that overlap an area with
+ * positive area, and integerises Eq. 3 (largest remainders, ties to the lower
+ * loop index) so that the counts sum exactly to the requested histories.
+ * Plan loop order: beam, sub-source, energy bin, PSL row (y), PSL column (x).
+ *
+ *   per_psr_hist == NULL: one plan of n_hist histories over the whole source.
+ *   per_psr_hist != NULL (host, [3 n_e n_r]): batched basis runs for
+ *     commissioning (Sec. 2.2.2) -- for every PSR k and beam b a run of
+ *     per_psr_hist[k] histories drawn from PSR k's share of the PSL weights
+ *     (the k-th term of the linear PSR -> PSL map); n_hist is ignored. Every
+ *     particle of such a run carries PSR index k.
+ * The plan is periodic: history g uses plan position g mod (plan size), so a
+ * run of B passes is B statistically independent batches.
+ * Errors: LSM_ERR_ARG on invalid model/beams, n_hist < 1 (whole-source), an
+ * empty sampling area, or a plan larger than 2^31 entries.
+ */
+lsm_status lsm_build_psl(const lsm_psr_model *model, const lsm_beams *beams, int64_t n_hist,
+                         const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream);
+void lsm_psl_destroy(lsm_psl *psl);
+
+/* info: [n_xy, n_entries, plan size (histories per pass), per_psr flag];
+ * denom: the Eq. 3 denominator (whole-source plans). Synchronises. */
+lsm_status lsm_psl_info(const lsm_psl *psl, int64_t info[4], double *denom);
+/*
+ * Copy a plan table to host memory (synchronises). which:
+ *   0 PSL weights   double [3][n_e][n_xy][n_xy]
+ *   1 inclusion     uint8  [n_beams][2][n_xy][n_xy] (class 0 primary, 1 scatter+electron)
+ *   2 areas         double [n_beams][2][4] (xa, xb, ya, yb on the phase-space plane)
+ *   3 counts        int64  whole-source [n_beams][3][n_e][n_xy][n_xy];
+ *                          per-PSR [3 n_e n_r][n_beams][n_xy][n_xy]
+ *   4 entry starts  int64  [n_entries + 1] (exclusive prefix of the counts)
+ *   5 entries       int32  [n_entries][6] (beam, stype, ebin, ix, iy, forced PSR or -1)
+ *   6 entry scale   double [n_entries] per-PSR plans: (in-area weight of the
+ *                          PSR for that beam) / per_psr_hist[k]; 0 otherwise
+ */
+lsm_status lsm_psl_copy(const lsm_psl *psl, int which, void *host_dst);
+
+/*
+ * Particles in structure-of-arrays form, all DEVICE pointers with capacity n.
+ * Position (x, y, z) and direction (u, v, w) are where the particle crosses
+ * the phantom surface plane (z = phantom z0); E kinetic energy.
+ * hist: history id g. psr: PSR index (s n_e + e) n_r + R carried for the
+ * basis tally; beam: beam index; type: 0 photon, 1 electron; status:
+ * 0 accepted, 1 rejected by the jaws, 2 missed the phantom top face.
+ * info (optional, may be NULL): int32 [n][4] = (stype | ebin << 8,
+ * ring used for the direction model, mixture component or -1, plan entry).
+ */
+typedef struct {
+    float *x, *y, *z, *u, *v, *w, *E;
+    uint64_t *hist;
+    uint16_t *psr;
+    uint8_t *beam, *type, *status;
+    int32_t *info;
+} lsm_particles;
+
+/*
+ * lsm_sample -- steps S3-S5 on the GPU (Eq. 4-7): particles for histories
+ * [hist_begin, hist_begin + n) of the plan, drawn from Philox4x32-10 with key
+ * `seed` and counter (history, stream 0, draw index). Position uniform in the
+ * PSL, energy uniform in the bin; primary direction from a Gaussian focal spot
+ * (Eq. 4-5); scatter direction from the K=3 mixture of the ring that holds the
+ * sampled radius (Eq. 6); electron direction from Eq. 7; rotation by the polar
+ * angle of (x, y); straight flight to the jaw planes (rejection) and to the
+ * phantom surface at z = z_surface. Every history produces one record.
+ * Errors: LSM_ERR_ARG if n < 0 or a required pointer is NULL.
+ */
+lsm_status lsm_sample(const lsm_psl *psl, uint64_t seed, uint64_t hist_begin, int64_t n,
+                      double z_surface, const lsm_particles *out, lsm_stream stream);
+
+/*
+ * Voxel phantom: nx * ny * nz voxels of dx * dy * dz cm, first voxel corner
+ * at (x0, y0, z0); z0 is the phantom surface. rho: float32 density (g/cm^3,
+ * 1e-4 <= rho <= 25), mat: uint8 material class (0 water-like, 1 bone), both
+ * [nz][ny][nx] in `mem`. Creation also generates the interaction tables of the
+ * stated transport model (Klein-Nishina Compton, photoelectric and pair cross
+ * sections, Bethe collision stopping power; 1024 log-spaced energies from
+ * 1 keV to 7 MeV) and the Woodcock majorant of this phantom.
+ */
+typedef struct {
+    int32_t nx, ny, nz;
+    double dx, dy, dz, x0, y0, z0;
+    const float *rho;
+    const uint8_t *mat;
+    lsm_mem mem;
+} lsm_phantom_desc;
+
+lsm_status lsm_phantom_create(const lsm_phantom_desc *desc, lsm_phantom **out, lsm_stream stream);
+void lsm_phantom_destroy(lsm_phantom *ph);
+/* Copy the interaction tables to host (synchronises): out float
+ * [2 materials][1024][4] = (mu_compton, mu_photo, mu_pair in cm^2/g, S_col in
+ * MeV cm^2/g), then [1024] majorant (1/cm); grid[2] = (ln E_min, d ln E). */
+lsm_status lsm_phantom_tables(const lsm_phantom *ph, float *out, double grid[2]);
+
+/*
+ * Tally. mode 0: energy per voxel. mode 1: basis tally of Sec. 2.2.2 -- a 2D
+ * array [n_beams * n_rows][n_psr]; a deposit in voxel v goes to row
+ * idx3d[v] - 1 of the particle's beam block, column = the particle's PSR,
+ * and is dropped when idx3d[v] == 0. idx3d: uint16 [nz][ny][nx] in idx3d_mem.
+ * Deposits accumulate in FP32 partials that are flushed into FP64 after every
+ * sample/transport iteration; lsm_tally_end_batch folds the open FP64 batch
+ * into the running sums S1 (sum of batch totals) and S2 (sum of squares).
+ */
+typedef struct {
+    int32_t mode;
+    const uint16_t *idx3d;
+    lsm_mem idx3d_mem;
+    int32_t n_rows, n_psr, n_beams;
+} lsm_tally_desc;
+
+lsm_status lsm_tally_create(const lsm_phantom *ph, const lsm_tally_desc *desc, lsm_tally **out,
+                            lsm_stream stream);
+void lsm_tally_destroy(lsm_tally *t);
+/* Zero every sum, counter and the energy ledger. */
+lsm_status lsm_tally_reset(lsm_tally *t, lsm_stream stream);
+/* Flush pending FP32 partials and fold the open batch into S1/S2. */
+lsm_status lsm_tally_end_batch(lsm_tally *t, lsm_stream stream);
+/* s1, s2: double [cells] in `mem` (either may be NULL); *n_batches = folded
+ * batches. Synchronises when mem is HOST. */
+lsm_status lsm_tally_read(lsm_tally *t, double *s1, double *s2, lsm_mem mem, int32_t *n_batches,
+                          lsm_stream stream);
+/* ledger (MeV): source, rejected, escaped (incl. missed), deposited.
+ * stats: histories, accepted photons, accepted electrons, rejected, missed,
+ * Woodcock flights, real photon interactions, electron steps, step-cap hits,
+ * queue overflows. Synchronises. */
+lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], lsm_stream stream);
+
+/*
+ * Transport options (the stated simplification of the paper's engine; the
+ * paper fixes only the cutoffs, electrons 200 keV and photons 50 keV,
+ * Sec. 2.3). electron_mode 0 deposits electron energy where the electron is
+ * created; 1 transports electrons by CSDA steps: step = min(s_geo, f_e E/S),
+ * energy loss by the midpoint rule, deposit at the step midpoint, Highland
+ * Gaussian deflection. s_geo <= 0 means half the smallest voxel side.
+ * majorant_factor >= 1 inflates the Woodcock majorant (results unchanged in
+ * expectation). chunk: histories per sample/transport iteration (the paper's
+ * M; 0 = 131072). max_steps: per-particle step cap (>= 1), after which the
+ * remaining energy is deposited locally and counted.
+ */
+typedef struct {
+    int32_t electron_mode;
+    int32_t n_batches;
+    double majorant_factor, f_e, s_geo;
+    int32_t max_steps;
+    int32_t chunk;
+} lsm_run_opts;
+
+/*
+ * lsm_transport -- transport the accepted particles (status 0) of `in`
+ * (device SoA of n records, as written by lsm_sample with the same seed) and
+ * every secondary they create, depositing into `tally`'s open batch. Each
+ * particle draws from its own Philox stream: primaries use stream 1 of their
+ * history; a particle created at an interaction uses the stream id given by
+ * its parent's block at counter (draw index | 2^31).
+ * Errors: LSM_ERR_ARG on mismatched handles; LSM_ERR_OVERFLOW when the
+ * secondary-electron queue filled up (the excess electrons were deposited at
+ * their creation point and counted in stats[9]).
+ */
+lsm_status lsm_transport(const lsm_phantom *ph, const lsm_particles *in, int64_t n, uint64_t seed,
+                         lsm_tally *tally, const lsm_run_opts *opts, lsm_stream stream);
+
+/*
+ * lsm_run -- the whole dose calculation of Sec. 2.1.3: n_batches passes over
+ * the plan, each iterating [sample M histories -> transport photons ->
+ * transport annihilation photons -> transport electrons -> flush] until the
+ * plan is exhausted, then folding the batch (lsm_tally_end_batch). Histories
+ * of pass b are g = b * plan size + h.
+ * Errors: as lsm_transport.
+ */
+lsm_status lsm_run(const lsm_psl *psl, const lsm_phantom *ph, lsm_tally *tally, uint64_t seed,
+                   const lsm_run_opts *opts, lsm_stream stream);
+
+/*
+ * Dose per source particle (MeV/g) and its batch standard deviation from a
+ * mode-0 tally: dose = S1 / B * scale / (rho V), sigma from the batch spread,
+ * where scale = (Eq. 3 denominator) / (plan size) converts per-history to
+ * per-source-particle. dose, sigma: double [nvox] in mem (sigma may be NULL).
+ */
+lsm_status lsm_dose(const lsm_tally *t, const lsm_phantom *ph, double scale, double *dose,
+                    double *sigma, lsm_mem mem, lsm_stream stream);
+
+/*
+ * Basis matrix A of Sec. 2.2.2 from a mode-1 tally over a per-PSR plan:
+ * A[(b, row), k] = S1 / B * (entry scale of PSR k, beam b) / (rho V of the row's
+ * voxel), i.e. the dose per source particle of the full model contributed by
+ * PSR k. A: double [n_beams * n_rows][n_psr] in mem.
+ */
+lsm_status lsm_basis_matrix(const lsm_tally *t, const lsm_psl *psl, const lsm_phantom *ph,
+                            const uint16_t *idx3d, lsm_mem idx3d_mem, double *A, lsm_mem mem,
+                            lsm_stream stream);
+
+/*
+ * lsm_commission -- Eq. 8: x = argmin_{x >= 0} ||A x - b||^2 in FP64 on the
+ * GPU. A: double [m][n] row-major, b: double [m], both in `mem`; x: host
+ * double [n] (also the starting point of the projected-gradient method when
+ * opts->use_x0 != 0). method 0: active set (Lawson & Hanson) with the
+ * passive-set least squares solved by Cholesky of the normal equations;
+ * method 1: gradient projection with Armijo's rule (Sec. 2.2.4), stopped when
+ * the relative change of F falls below delta. Synchronises.
+ * Errors: LSM_ERR_ARG for m < 1, 1 > n > 1024 or NULL pointers;
+ * LSM_ERR_NOT_CONVERGED when max_iter was reached (x holds the last iterate).
+ */
+typedef struct {
+    int32_t method;
+    int32_t max_iter;
+    double delta;
+    double armijo_sigma, armijo_beta;
+    int32_t use_x0;
+} lsm_nnls_opts;
+
+typedef struct {
+    int32_t iterations;
+    int32_t converged;
+    double objective;
+    double kkt;            /* max violation of x >= 0, grad >= 0, x * grad = 0 */
+} lsm_nnls_report;
+
+lsm_status lsm_commission(const double *A, int32_t m, int32_t n, const double *b, lsm_mem mem,
+                          const lsm_nnls_opts *opts, double *x, lsm_nnls_report *report,
+                          lsm_stream stream);
+
+/*
+ * Timers (the breakdown of Sec. 3.1 / Table 1: source initialisation, particle
+ * generation, transport simulation). When enabled, the library records CUDA
+ * events on the launching stream around each kernel group and accumulates
+ * their elapsed device time:
+ *   0 PSL build (T_src_init)       1 sampling (T_par_gen_tr)
+ *   2 photon transport             3 annihilation-photon transport
+ *   4 electron transport           5 tally flush and fold
+ *   6 NNLS solve                   7 phantom set-up and tables
+ * lsm_timing_read synchronises the device, returns milliseconds and launch
+ * counts per timer, and clears them when reset != 0. Disabled by default.
+ */
+#define LSM_N_TIMERS 8
+lsm_status lsm_timing_enable(int on);
+lsm_status lsm_timing_read(double ms[LSM_N_TIMERS], int64_t launches[LSM_N_TIMERS], int reset);
+
+/* Library diagnostics. */
+const char *lsm_last_error(void);
+/* Kernels launched by this library in this process so far. */
+int64_t lsm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSM_H */

@@ -1,0 +1,144 @@
+// common.cuh -- device-side building blocks shared by the kernels of liblsm.so.
+//
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) counter RNG; the u32 ->
+// (0,1] map; particle-queue and interaction-table layouts; launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lsm.h"
+
+namespace lsm {
+
+constexpr float kMe = 0.51099895f;       // electron rest energy, MeV
+constexpr double kMeD = 0.51099895;
+constexpr float kCutE = 0.2f;            // electron cutoff, MeV (Sec. 2.3)
+constexpr float kCutG = 0.05f;           // photon cutoff, MeV (Sec. 2.3)
+constexpr float kPi = 3.14159265358979f;
+constexpr double kPiD = 3.14159265358979323846;
+constexpr int kGrid = 1024;              // log-energy table points
+constexpr double kLnEmin = -6.907755278982137;  // ln(1 keV in MeV)
+constexpr double kLnEmax = 1.9459101090932196;  // ln(7 MeV)
+
+// ---------------------------------------------------------------- Philox ---
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                                               uint32_t c2, uint32_t c3)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = c0 * 0xD2511F53u, hi0 = __umulhi(c0, 0xD2511F53u);
+        const uint32_t lo1 = c2 * 0xCD9E8D57u, hi1 = __umulhi(c2, 0xCD9E8D57u);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// ((x >> 8) + 1) * 2^-24: exact in FP32, never 0.
+__device__ __forceinline__ float u01(uint32_t x)
+{
+    return __fmul_rn((float)(x >> 8) + 1.0f, 5.9604644775390625e-8f);
+}
+
+// A particle's random stream: counter (history lo, history hi, stream id, draw).
+struct Stream {
+    uint32_t k0, k1, glo, ghi, sid, ctr;
+    __device__ __forceinline__ uint4 next()
+    {
+        return philox4x32_10(k0, k1, glo, ghi, sid, ctr++);
+    }
+    // stream ids of particles created at the current draw position
+    __device__ __forceinline__ uint4 child_ids() const
+    {
+        uint4 r = philox4x32_10(k0, k1, glo, ghi, sid, ctr | 0x80000000u);
+        r.x += (r.x < 2u) ? 2u : 0u;
+        r.y += (r.y < 2u) ? 2u : 0u;
+        r.z += (r.z < 2u) ? 2u : 0u;
+        r.w += (r.w < 2u) ? 2u : 0u;
+        return r;
+    }
+};
+
+// --------------------------------------------------------- particle queue ---
+// SoA queue of particles waiting for transport, phantom-local coordinates
+// (x - x0, y - y0, z - z0). pb = psr | beam << 16.
+struct Queue {
+    float *x, *y, *z, *u, *v, *w, *E;
+    uint32_t *glo, *ghi, *sid, *pb;
+    uint32_t cap;
+};
+
+// Counters of one sample/transport iteration (device memory, zeroed per iteration).
+struct IterCounters {
+    uint32_t n[3];      // queue fill: 0 primary photons, 1 annihilation photons, 2 electrons
+    uint32_t head[3];   // refill cursors of the persistent transport kernels
+    uint32_t overflow;  // electrons deposited in place because the queue was full
+    uint32_t pad;
+};
+
+// Run-long statistics and the FP64 energy ledger.
+struct RunStats {
+    double ledger[4];     // source, rejected, escaped, deposited (MeV)
+    unsigned long long c[10];
+};
+
+// ---------------------------------------------------- interaction tables ---
+// Per material class: float4 (mu_compton, mu_photo, mu_pair [cm^2/g], S_col [MeV cm^2/g])
+// at ln E_i = kLnEmin + i * dlnE; majorant [1/cm] per phantom.
+struct Tables {
+    const float4 *xs;    // [2][kGrid]
+    const float *mumax;  // [kGrid]
+    float inv_dlnE;
+};
+
+// ------------------------------------------------------------- warp utils ---
+__device__ __forceinline__ unsigned lane_id()
+{
+    unsigned l;
+    asm volatile("mov.u32 %0, %%laneid;" : "=r"(l));
+    return l;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace lsm
+
+// ---------------------------------------------------------------- host side --
+namespace lsm {
+// Event timers around kernel groups (see lsm_timing_enable). timer_begin
+// returns a token that timer_end closes; both are no-ops while disabled.
+int timer_begin(int which, cudaStream_t st);
+void timer_end(int token, cudaStream_t st);
+void count_launch();
+lsm_status set_cuda_error(cudaError_t e, const char *where);
+lsm_status set_arg_error(const char *msg);
+int sm_count();
+}  // namespace lsm
+
+#define LSM_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return lsm::set_cuda_error(_e, #call);    \
+    } while (0)
+
+#define LSM_LAUNCHED(where)                                              \
+    do {                                                                 \
+        lsm::count_launch();                                             \
+        cudaError_t _e = cudaGetLastError();                             \
+        if (_e != cudaSuccess) return lsm::set_cuda_error(_e, where);    \
+    } while (0)

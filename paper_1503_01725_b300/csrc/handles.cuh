@@ -1,0 +1,79 @@
+// handles.cuh -- layouts of the opaque handles of liblsm.so.
+#pragma once
+
+#include "common.cuh"
+
+namespace lsm {
+
+// One plan entry: a PSL with a non-zero particle count (16 bytes).
+struct EntryRec {
+    uint16_t ix, iy;
+    uint8_t beam, stype;
+    uint16_t ebin;
+    int16_t fixed_ring;   // ring carried as PSR index; -1: drawn from (r0, r0 + 1)
+    uint8_t r0, pad;
+    uint32_t thr;         // drawn tag: ring r0 when the draw < thr, else r0 + 1
+};
+
+// Everything the sampling kernels read, passed by value.
+struct SampleParams {
+    const int64_t *start;      // [n_ent + 1]
+    const EntryRec *ent;       // [n_ent]
+    const unsigned long long *mixthr;  // [n_e][n_r][2]
+    const float4 *mix;         // [n_e][n_r][3] (mu, sigma_alpha, sigma_beta, 0)
+    const float2 *esig;        // [n_e][n_r]
+    const float *jaws_f;       // [n_beams][4] jaw limits in the jaw planes: ylo yhi xlo xhi
+    int64_t n_ent;
+    int n_e, n_r;
+    float pitch, z_phsp, sigma_s;
+    float e_lo[3], de[3];
+    float zy_rel, zx_rel;      // jaw plane minus phase-space plane
+};
+
+}  // namespace lsm
+
+struct lsm_psl {
+    int device;
+    int n_e, n_r, n_xy, n_beams, per_psr;
+    double dr, z_phsp, sigma_s, e_lo[3], de[3];
+    double sad, z_jaw_y, z_jaw_x;
+    double denom;
+    int64_t plan_size, n_ent, ncell;
+    double *d_w, *d_wpsl, *d_scale, *d_jaws, *d_area, *d_escale;
+    uint8_t *d_incl;
+    int64_t *d_count, *d_start;
+    lsm::EntryRec *d_ent;
+    unsigned long long *d_mixthr;
+    float4 *d_mix;
+    float2 *d_esig;
+    float *d_jaws_f;
+    int32_t *d_tag_r0;
+    double *d_tag_l0;
+    lsm::SampleParams sp;
+};
+
+struct lsm_phantom {
+    int device;
+    int nx, ny, nz;
+    double dx, dy, dz, x0, y0, z0;
+    float *d_rho;         // density
+    uint8_t *d_mat;
+    float *d_rhomat;      // density, negated for material class 1 (one load per voxel)
+    float4 *d_xs;         // [2][kGrid]
+    float *d_mumax;       // [kGrid] majorant at factor 1
+    double rho_max[2];
+};
+
+struct lsm_tally {
+    int device;
+    int mode, n_rows, n_psr, n_beams;
+    int64_t ncell, nvox;
+    float *d_part;        // FP32 partials of the current iteration
+    double *d_batch;      // FP64 open batch
+    double *d_s1, *d_s2;
+    uint16_t *d_idx;      // basis mode
+    lsm::RunStats *d_stats;
+    int n_batches;
+    void *ws;             // cached particle queues of lsm_run / lsm_transport
+    uint32_t ws_chunk, ws_ecap;
+};

@@ -1,0 +1,477 @@
+// nnls.cu -- the commissioning problem of Eq. 8 in FP64 on the GPU.
+//
+//   min_{x >= 0} F(x) = ||A x - b||^2
+//
+// k_gram forms G = A^T A and c = A^T b (FP64 CUDA cores). Two solvers then run
+// in one CTA of 1024 threads with G resident in L2:
+//   * active set (Lawson & Hanson 1974): the passive-set least squares is
+//     solved by a Cholesky factorisation of G restricted to the passive set;
+//   * gradient projection with Armijo's rule (Sec. 2.2.4):
+//     x <- max(0, x - s grad F), s = s_bar beta^j for the first j with
+//     F(x_new) <= F(x) + sigma grad F . (x_new - x); stop when the relative
+//     change of F is below delta. The decrease F(x_new) - F(x) is evaluated as
+//     g.d + d^T G d (d = x_new - x) so that no large terms cancel.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "handles.cuh"
+
+namespace lsm {
+namespace {
+
+constexpr int kT = 1024;
+
+__global__ void k_gram(const double *__restrict__ A, const double *__restrict__ b, int m, int n,
+                       double *__restrict__ G, double *__restrict__ c)
+{
+    __shared__ double ta[32][33], tb[32][33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    double acc[4] = {0, 0, 0, 0};
+    double accb = 0.0;
+    for (int r0 = 0; r0 < m; r0 += 32) {
+        for (int q = ty; q < 32; q += 8) {
+            const int r = r0 + q;
+            ta[q][tx] = (r < m && i0 + tx < n) ? A[(size_t)r * n + i0 + tx] : 0.0;
+            tb[q][tx] = (r < m && j0 + tx < n) ? A[(size_t)r * n + j0 + tx] : 0.0;
+        }
+        __syncthreads();
+        for (int q = 0; q < 32; ++q) {
+            const double bj = tb[q][tx];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] += ta[q][ty + 8 * k] * bj;
+        }
+        if (blockIdx.x == 0 && ty == 0) {
+            for (int q = 0; q < 32 && r0 + q < m; ++q) accb += ta[q][tx] * b[r0 + q];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = i0 + ty + 8 * k, j = j0 + tx;
+        if (i < n && j < n) G[(size_t)i * n + j] = acc[k];
+    }
+    if (blockIdx.x == 0 && ty == 0 && i0 + tx < n) c[i0 + tx] = accb;
+}
+
+// ---- block helpers (1024 threads) ----
+__device__ double block_sum(double v, double *red)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double t = red[l];
+        t = warp_sum(t);
+        if (l == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// argmax of v over j with mask(j) true; returns index (-1 if none) and value
+__device__ int block_argmax(double v, int j, double *redv, int *redi, double *best)
+{
+    // warp stage
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+        if (ov > v || (ov == v && oj >= 0 && (j < 0 || oj < j))) { v = ov; j = oj; }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) { redv[w] = v; redi[w] = j; }
+    __syncthreads();
+    if (w == 0) {
+        v = redv[l]; j = redi[l];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+            if (ov > v || (ov == v && oj >= 0 && (j < 0 || oj < j))) { v = ov; j = oj; }
+        }
+        if (l == 0) { redv[32] = v; redi[32] = j; }
+    }
+    __syncthreads();
+    *best = redv[32];
+    return redi[32];
+}
+
+struct NnlsOut {
+    int iterations, converged, status;   // status 0 ok, 1 not converged, 2 numerical failure
+    double objective;
+};
+
+// Cholesky solve of G[P,P] z_P = c_P into z (z = 0 outside P); k = |P|, idx = P in order.
+// L: scratch k x k. Returns false if the restricted Gram matrix is not positive definite.
+__device__ bool chol_solve(const double *__restrict__ G, int n, const int *idx, int k, const double *c,
+                           double *L, double *z, double *y, double *red)
+{
+    for (int t = threadIdx.x; t < k * k; t += kT) {
+        const int i = t / k, l = t % k;
+        L[t] = G[(size_t)idx[i] * n + idx[l]];
+    }
+    __syncthreads();
+    __shared__ int fail;
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = L[j * k + j];
+            if (!(d > 0.0)) fail = 1;
+            L[j * k + j] = sqrt(d > 0.0 ? d : 1.0);
+        }
+        __syncthreads();
+        if (fail) return false;
+        const double djj = L[j * k + j];
+        for (int i = j + 1 + threadIdx.x; i < k; i += kT) L[i * k + j] /= djj;
+        __syncthreads();
+        const int rem = k - j - 1;
+        for (int t = threadIdx.x; t < rem * rem; t += kT) {
+            const int i = j + 1 + t / rem, l = j + 1 + t % rem;
+            if (l <= i) L[i * k + l] -= L[i * k + j] * L[l * k + j];
+        }
+        __syncthreads();
+    }
+    // forward: L y = c_P
+    for (int i = 0; i < k; ++i) {
+        double s = 0.0;
+        for (int l = threadIdx.x; l < i; l += kT) s += L[i * k + l] * y[l];
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) y[i] = (c[idx[i]] - s) / L[i * k + i];
+        __syncthreads();
+    }
+    // backward: L^T zP = y
+    for (int i = k - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int l = i + 1 + threadIdx.x; l < k; l += kT) s += L[l * k + i] * z[idx[l]];
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) z[idx[i]] = (y[i] - s) / L[i * k + i];
+        __syncthreads();
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kT) k_lawson_hanson(const double *__restrict__ G, const double *__restrict__ cg,
+                                                      int n, double tol_scale, int max_iter, double *__restrict__ L,
+                                                      double *__restrict__ xout, NnlsOut *out)
+{
+    extern __shared__ double sm[];
+    double *x = sm, *w = sm + n, *z = sm + 2 * n, *y = sm + 3 * n, *c = sm + 4 * n;
+    int *P = (int *)(sm + 5 * n), *idx = P + n;
+    __shared__ double red[33];
+    __shared__ int redi[33];
+    __shared__ int s_k, s_status;
+    for (int j = threadIdx.x; j < n; j += kT) { x[j] = 0.0; P[j] = 0; c[j] = cg[j]; w[j] = cg[j]; }
+    if (threadIdx.x == 0) s_status = 0;
+    // tolerance 10 eps ||G||_1 max(m, n) (Lawson & Hanson's test on the dual)
+    double cmax = 0.0;
+    for (int j = threadIdx.x; j < n; j += kT) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += fabs(G[(size_t)i * n + j]);
+        cmax = fmax(cmax, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int q = 0; q < 32; ++q) v = fmax(v, red[q]);
+        red[32] = v;
+    }
+    __syncthreads();
+    const double tol = tol_scale * red[32];
+    __syncthreads();
+    int it = 0;
+    for (;;) {
+        // most positive gradient component outside the passive set
+        double bv = -INFINITY;
+        int bj = -1;
+        for (int j = threadIdx.x; j < n; j += kT)
+            if (!P[j] && (w[j] > bv || (w[j] == bv && bj >= 0 && j < bj) || bj < 0)) { bv = w[j]; bj = j; }
+        double best;
+        const int t = block_argmax(bj >= 0 ? bv : -INFINITY, bj, red, redi, &best);
+        if (t < 0 || !(best > tol) || it >= max_iter) break;
+        if (threadIdx.x == 0) P[t] = 1;
+        __syncthreads();
+        for (;;) {
+            ++it;
+            if (threadIdx.x == 0) {
+                int k = 0;
+                for (int j = 0; j < n; ++j)
+                    if (P[j]) idx[k++] = j;
+                s_k = k;
+            }
+            for (int j = threadIdx.x; j < n; j += kT) z[j] = 0.0;
+            __syncthreads();
+            const int k = s_k;
+            if (!chol_solve(G, n, idx, k, c, L, z, y, red)) {
+                if (threadIdx.x == 0) s_status = 2;
+                __syncthreads();
+                break;
+            }
+            // all passive z positive?
+            int bad = 0;
+            for (int q = threadIdx.x; q < k; q += kT) bad |= !(z[idx[q]] > 0.0);
+            bad = __syncthreads_or(bad);
+            if (!bad) {
+                for (int j = threadIdx.x; j < n; j += kT) x[j] = z[j];
+                __syncthreads();
+                break;
+            }
+            double a = INFINITY;
+            for (int q = threadIdx.x; q < k; q += kT) {
+                const int j = idx[q];
+                if (!(z[j] > 0.0)) a = fmin(a, x[j] / (x[j] - z[j]));
+            }
+            for (int o = 16; o > 0; o >>= 1) a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                double v = red[threadIdx.x];
+                for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+                if (threadIdx.x == 0) red[32] = v;
+            }
+            __syncthreads();
+            const double alpha = red[32];
+            for (int j = threadIdx.x; j < n; j += kT) {
+                x[j] = x[j] + alpha * (z[j] - x[j]);
+                if (P[j] && !(x[j] > tol)) P[j] = 0;
+                if (!P[j]) x[j] = 0.0;
+            }
+            __syncthreads();
+            if (it >= max_iter) break;
+        }
+        if (s_status) break;
+        // w = c - G x
+        for (int j = threadIdx.x; j < n; j += kT) {
+            double s = 0.0;
+            const double *g = G + (size_t)j * n;
+            for (int l = 0; l < n; ++l) s += g[l] * x[l];
+            w[j] = c[j] - s;
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < n; j += kT) xout[j] = x[j];
+    if (threadIdx.x == 0) {
+        out->iterations = it;
+        out->converged = (s_status == 0 && it < max_iter) ? 1 : 0;
+        out->status = s_status ? 2 : (it >= max_iter ? 1 : 0);
+    }
+}
+
+// Gradient projection with Armijo's rule along the projection arc.
+__global__ void __launch_bounds__(kT) k_projected_gradient(const double *__restrict__ G,
+                                                           const double *__restrict__ cg, int n, double F0,
+                                                           double delta, int max_iter, double sigma,
+                                                           double beta, double *__restrict__ xio, NnlsOut *out)
+{
+    extern __shared__ double sm[];
+    double *x = sm, *gx = sm + n, *g = sm + 2 * n, *d = sm + 3 * n, *gd = sm + 4 * n, *v = sm + 5 * n;
+    __shared__ double red[33];
+    for (int j = threadIdx.x; j < n; j += kT) { x[j] = fmax(xio[j], 0.0); v[j] = rsqrt((double)n); }
+    __syncthreads();
+    // s_bar = 1 / lambda_max(G) by power iteration
+    double lam = 0.0;
+    for (int p = 0; p < 100; ++p) {
+        for (int j = threadIdx.x; j < n; j += kT) {
+            double s = 0.0;
+            const double *gr = G + (size_t)j * n;
+            for (int l = 0; l < n; ++l) s += gr[l] * v[l];
+            gd[j] = s;
+        }
+        __syncthreads();
+        double q = 0.0;
+        for (int j = threadIdx.x; j < n; j += kT) q += gd[j] * gd[j];
+        q = block_sum(q, red);
+        const double nrm = sqrt(q);
+        double rq = 0.0;
+        for (int j = threadIdx.x; j < n; j += kT) rq += v[j] * gd[j];
+        rq = block_sum(rq, red);
+        lam = rq;
+        for (int j = threadIdx.x; j < n; j += kT) v[j] = gd[j] / nrm;
+        __syncthreads();
+    }
+    const double s_bar = 1.0 / lam;
+    // G x
+    for (int j = threadIdx.x; j < n; j += kT) {
+        double s = 0.0;
+        const double *gr = G + (size_t)j * n;
+        for (int l = 0; l < n; ++l) s += gr[l] * x[l];
+        gx[j] = s;
+    }
+    __syncthreads();
+    double F = F0;
+    int it = 0, conv = 0;
+    while (it < max_iter) {
+        ++it;
+        for (int j = threadIdx.x; j < n; j += kT) g[j] = 2.0 * (gx[j] - cg[j]);
+        __syncthreads();
+        double s = s_bar, dF = 0.0;
+        for (int trial = 0; trial < 200; ++trial) {
+            for (int j = threadIdx.x; j < n; j += kT) d[j] = fmax(x[j] - s * g[j], 0.0) - x[j];
+            __syncthreads();
+            for (int j = threadIdx.x; j < n; j += kT) {
+                double q = 0.0;
+                const double *gr = G + (size_t)j * n;
+                for (int l = 0; l < n; ++l) q += gr[l] * d[l];
+                gd[j] = q;
+            }
+            __syncthreads();
+            double gdot = 0.0, dgd = 0.0;
+            for (int j = threadIdx.x; j < n; j += kT) { gdot += g[j] * d[j]; dgd += d[j] * gd[j]; }
+            gdot = block_sum(gdot, red);
+            dgd = block_sum(dgd, red);
+            dF = gdot + dgd;                      // F(x + d) - F(x)
+            if (dF <= sigma * gdot || s < 1e-30) break;
+            s *= beta;
+        }
+        for (int j = threadIdx.x; j < n; j += kT) { x[j] += d[j]; gx[j] += gd[j]; }
+        __syncthreads();
+        const double Fprev = F;
+        F = F + dF;
+        if (fabs(dF) <= delta * fmax(Fprev, 1e-300)) { conv = 1; break; }
+    }
+    for (int j = threadIdx.x; j < n; j += kT) xio[j] = x[j];
+    if (threadIdx.x == 0) {
+        out->iterations = it;
+        out->converged = conv;
+        out->status = conv ? 0 : 1;
+        out->objective = F;
+    }
+}
+
+// F(x) = ||A x - b||^2 and the KKT violation of x, after a solve
+__global__ void __launch_bounds__(kT) k_nnls_report(const double *__restrict__ A, const double *__restrict__ b,
+                                                    const double *__restrict__ G, const double *__restrict__ c,
+                                                    const double *__restrict__ x, int m, int n, NnlsOut *out,
+                                                    double *__restrict__ kkt)
+{
+    __shared__ double red[33];
+    double f = 0.0;
+    for (int r = threadIdx.x; r < m; r += kT) {
+        double s = -b[r];
+        const double *ar = A + (size_t)r * n;
+        for (int l = 0; l < n; ++l) s += ar[l] * x[l];
+        f += s * s;
+    }
+    f = block_sum(f, red);
+    double viol = 0.0;
+    for (int j = threadIdx.x; j < n; j += kT) {
+        double s = 0.0;
+        const double *gr = G + (size_t)j * n;
+        for (int l = 0; l < n; ++l) s += gr[l] * x[l];
+        const double gj = 2.0 * (s - c[j]);
+        viol = fmax(viol, fmax(fmax(-x[j], -gj), fabs(x[j] * gj)));
+    }
+    for (int o = 16; o > 0; o >>= 1) viol = fmax(viol, __shfl_xor_sync(0xffffffffu, viol, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = viol;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < 32; ++w) v = fmax(v, red[w]);
+        *kkt = v;
+        out->objective = f;
+    }
+}
+
+}  // namespace
+
+lsm_status commission(const double *A, int32_t m, int32_t n, const double *b, lsm_mem mem,
+                      const lsm_nnls_opts *opts, double *x, lsm_nnls_report *rep, cudaStream_t st)
+{
+    if (!A || !b || !x || m < 1 || n < 1 || n > 1024) return set_arg_error("lsm_commission: need m >= 1, 1 <= n <= 1024");
+    lsm_nnls_opts o = {0, 0, 1e-12, 1e-4, 0.5, 0};
+    if (opts) o = *opts;
+    if (o.method != 0 && o.method != 1) return set_arg_error("lsm_commission: method must be 0 or 1");
+    if (o.max_iter <= 0) o.max_iter = o.method == 0 ? 3 * n : 200000;
+    if (!(o.delta > 0)) o.delta = 1e-12;
+    if (!(o.armijo_sigma > 0 && o.armijo_sigma < 1)) o.armijo_sigma = 1e-4;
+    if (!(o.armijo_beta > 0 && o.armijo_beta < 1)) o.armijo_beta = 0.5;
+    const size_t szA = (size_t)m * n * 8;
+    char *buf = nullptr;
+    const size_t need = (mem == LSM_MEM_HOST ? szA + (size_t)m * 8 : 0) + (size_t)n * n * 8 * 2 + (size_t)n * 8 * 2 +
+                        64 + sizeof(NnlsOut) + 64;
+    LSM_CUDA(cudaMalloc(&buf, need));
+    const double *dA = A, *db = b;
+    char *p = buf;
+    if (mem == LSM_MEM_HOST) {
+        double *tA = (double *)p; p += szA;
+        double *tb = (double *)p; p += (size_t)m * 8;
+        cudaError_t e1 = cudaMemcpyAsync(tA, A, szA, cudaMemcpyHostToDevice, st);
+        cudaError_t e2 = cudaMemcpyAsync(tb, b, (size_t)m * 8, cudaMemcpyHostToDevice, st);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) { cudaFree(buf); return set_cuda_error(e1 ? e1 : e2, "copy A,b"); }
+        dA = tA; db = tb;
+    }
+    double *G = (double *)p; p += (size_t)n * n * 8;
+    double *L = (double *)p; p += (size_t)n * n * 8;
+    double *c = (double *)p; p += (size_t)n * 8;
+    double *dx = (double *)p; p += (size_t)n * 8;
+    double *kkt = (double *)p; p += 64;
+    NnlsOut *dout = (NnlsOut *)p;
+    lsm_status rc = LSM_OK;
+    cudaError_t e = cudaSuccess;
+    NnlsOut hout = {0, 0, 0, 0.0};
+    double hkkt = 0.0;
+    do {
+        dim3 gb((n + 31) / 32, (n + 31) / 32);
+        k_gram<<<gb, dim3(32, 8), 0, st>>>(dA, db, m, n, G, c);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if (o.method == 0) {
+            const size_t smem = (size_t)n * 8 * 5 + (size_t)n * 4 * 2;
+            cudaFuncSetAttribute(k_lawson_hanson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const double tol_scale = 10.0 * 2.220446049250313e-16 * (m > n ? m : n);
+            k_lawson_hanson<<<1, kT, smem, st>>>(G, c, n, tol_scale, o.max_iter, L, dx, dout);
+            count_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+        } else {
+            // starting point: x (use_x0) or all ones (the uncommissioned weights)
+            std::vector<double> x0((size_t)n, 1.0);
+            if (o.use_x0) for (int j = 0; j < n; ++j) x0[j] = x[j];
+            if ((e = cudaMemcpyAsync(dx, x0.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+            k_nnls_report<<<1, kT, 0, st>>>(dA, db, G, c, dx, m, n, dout, kkt);
+            count_launch();
+            NnlsOut f0;
+            if ((e = cudaMemcpyAsync(&f0, dout, sizeof(NnlsOut), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+            const size_t smem = (size_t)n * 8 * 6;
+            cudaFuncSetAttribute(k_projected_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_projected_gradient<<<1, kT, smem, st>>>(G, c, n, f0.objective, o.delta, o.max_iter, o.armijo_sigma,
+                                                      o.armijo_beta, dx, dout);
+            count_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+        }
+        NnlsOut keep;
+        if ((e = cudaMemcpyAsync(&keep, dout, sizeof(NnlsOut), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+        k_nnls_report<<<1, kT, 0, st>>>(dA, db, G, c, dx, m, n, dout, kkt);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(&hout, dout, sizeof(NnlsOut), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(&hkkt, kkt, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(x, dx, (size_t)n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+        hout.iterations = keep.iterations;
+        hout.converged = keep.converged;
+        hout.status = keep.status;
+    } while (0);
+    cudaFree(buf);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsm_commission");
+    if (rep) {
+        rep->iterations = hout.iterations;
+        rep->converged = hout.converged;
+        rep->objective = hout.objective;
+        rep->kkt = hkkt;
+    }
+    if (hout.status == 2) return set_arg_error("lsm_commission: passive-set Gram matrix not positive definite");
+    if (hout.status == 1) rc = LSM_ERR_NOT_CONVERGED;
+    return rc;
+}
+
+}  // namespace lsm

@@ -1,0 +1,628 @@
+// psl_build.cu -- PSR -> PSL conversion, sampling areas and Eq. 3 counts on the GPU.
+//
+// Sec. 2.1.1 (Eq. 1-2 and the four conversion steps), Sec. 2.1.2 (sampling
+// areas, Fig. 3), step S2 (Eq. 3) and the loop order of Sec. 2.1.3.
+//
+// Everything here is FP64 and this translation unit is compiled with
+// -fmad=false: each per-PSL value is the correctly rounded result of one fixed
+// sequence of IEEE operations, and every sum runs sequentially in loop order,
+// so the integer counts that Eq. 3 produces do not depend on thread
+// scheduling. The integerisation is largest-remainder (Hamilton) with ties to
+// the lower loop index; integer sums use 64-bit atomics (exact, any order).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "handles.cuh"
+
+namespace lsm {
+namespace {
+
+__device__ void ring_interp(double r, int n_r, double dr, int *r0, double *l0, int *inside)
+{
+    *inside = 1;
+    if (r >= (double)n_r * dr) { *r0 = n_r - 1; *l0 = 1.0; *inside = 0; return; }
+    double t = r / dr - 0.5;
+    if (t <= 0.0) { *r0 = 0; *l0 = 1.0; return; }
+    if (t >= (double)(n_r - 1)) { *r0 = n_r - 1; *l0 = 1.0; return; }
+    int i = (int)floor(t);
+    *r0 = i;
+    *l0 = 1.0 - (t - (double)i);
+}
+
+__device__ __forceinline__ double psl_radius(int ix, int iy, int n_r, double p)
+{
+    double xc = ((double)(ix - n_r) + 0.5) * p;
+    double yc = ((double)(iy - n_r) + 0.5) * p;
+    return sqrt(xc * xc + yc * yc);
+}
+
+// Steps 1-4 per (sub-source, energy bin) block: one CTA per block.
+__global__ void k_psl_weights(const double *__restrict__ w, int n_e, int n_r, double dr,
+                              double *__restrict__ wpsl, double *__restrict__ block_scale,
+                              int32_t *__restrict__ tag_r0, double *__restrict__ tag_l0)
+{
+    const int blk = blockIdx.x;               // s * n_e + e
+    const int nxy = 2 * n_r, npsl = nxy * nxy;
+    const double *W = w + (size_t)blk * n_r;
+    double *out = wpsl + (size_t)blk * npsl;
+    for (int j = threadIdx.x; j < npsl; j += blockDim.x) {
+        const int iy = j / nxy, ix = j % nxy;
+        const double r = psl_radius(ix, iy, n_r, dr);                    // step 1
+        int r0, in;
+        double l0;
+        ring_interp(r, n_r, dr, &r0, &l0, &in);
+        double dens = 0.0;                                               // step 2
+        if (in) {
+            dens = l0 * (W[r0] / dr);
+            if (l0 < 1.0) dens += (1.0 - l0) * (W[r0 + 1] / dr);
+        }
+        out[j] = dens / (2.0 * kPiD * r);                               // step 3
+        if (blk == 0) {
+            tag_r0[j] = r0;
+            tag_l0[j] = in ? l0 : 0.0;
+        }
+    }
+    __syncthreads();
+    __shared__ double s_scale;
+    if (threadIdx.x == 0) {                                              // step 4
+        double sraw = 0.0, sR = 0.0;
+        for (int j = 0; j < npsl; ++j) sraw += out[j];
+        for (int R = 0; R < n_r; ++R) sR += W[R];
+        s_scale = sraw > 0.0 ? sR / sraw : 0.0;
+        block_scale[blk] = s_scale;
+    }
+    __syncthreads();
+    const double sc = s_scale;
+    for (int j = threadIdx.x; j < npsl; j += blockDim.x) out[j] = out[j] * sc;
+}
+
+// Sampling areas on the phase-space plane, one thread per beam.
+__global__ void k_areas(const double *__restrict__ jaws, int n_beams, double z_phsp, double sad,
+                        double z_jaw_x, double z_jaw_y, double *__restrict__ area,
+                        float *__restrict__ jaws_f)
+{
+    const int b = threadIdx.x;
+    if (b >= n_beams) return;
+    const double x1 = jaws[4 * b], x2 = jaws[4 * b + 1], y1 = jaws[4 * b + 2], y2 = jaws[4 * b + 3];
+    double *a = area + 8 * b;
+    const double k = z_phsp / sad;                    // primary: opening scaled to the plane
+    a[0] = x1 * k; a[1] = x2 * k; a[2] = y1 * k; a[3] = y2 * k;
+    const double cx = 0.5 * (x1 + x2), cy = 0.5 * (y1 + y2);
+    const double fx = (sad - z_phsp) / (sad - z_jaw_x), fy = (sad - z_phsp) / (sad - z_jaw_y);
+    const double kx = z_jaw_x / sad, ky = z_jaw_y / sad;
+    a[4] = cx + (x1 * kx - cx) * fx;                  // scatter/electrons: back projection
+    a[5] = cx + (x2 * kx - cx) * fx;
+    a[6] = cy + (y1 * ky - cy) * fy;
+    a[7] = cy + (y2 * ky - cy) * fy;
+    // jaw limits in the jaw planes for the rejection test (single precision)
+    jaws_f[4 * b + 0] = (float)(y1 * z_jaw_y / sad);
+    jaws_f[4 * b + 1] = (float)(y2 * z_jaw_y / sad);
+    jaws_f[4 * b + 2] = (float)(x1 * z_jaw_x / sad);
+    jaws_f[4 * b + 3] = (float)(x2 * z_jaw_x / sad);
+}
+
+// PSL inclusion: positive-area overlap with the sampling area.
+__global__ void k_incl(const double *__restrict__ area, int n_beams, int n_r, double p,
+                       uint8_t *__restrict__ incl)
+{
+    const int nxy = 2 * n_r, npsl = nxy * nxy;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_beams * 2 * npsl) return;
+    const int j = (int)(i % npsl), bc = (int)(i / npsl);
+    const int iy = j / nxy, ix = j % nxy;
+    const double *a = area + 4 * bc;
+    const double xl = (double)(ix - n_r) * p, xh = (double)(ix - n_r + 1) * p;
+    const double yl = (double)(iy - n_r) * p, yh = (double)(iy - n_r + 1) * p;
+    incl[i] = (uint8_t)(xh > a[0] && xl < a[1] && yh > a[2] && yl < a[3]);
+}
+
+// ------------------------------------------------ whole-source plan (Eq. 3) --
+
+// partial sum of included weights per (beam, sub-source, energy), sequential in PSL order
+__global__ void k_eq3_parts(const double *__restrict__ wpsl, const uint8_t *__restrict__ incl,
+                            int n_beams, int n_e, int npsl, double *__restrict__ parts)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_beams * 3 * n_e) return;
+    const int b = i / (3 * n_e), s = (i / n_e) % 3, e = i % n_e;
+    const uint8_t *inc = incl + (size_t)(b * 2 + (s ? 1 : 0)) * npsl;
+    const double *W = wpsl + ((size_t)s * n_e + e) * npsl;
+    double part = 0.0;
+    for (int j = 0; j < npsl; ++j)
+        if (inc[j]) part += W[j];
+    parts[i] = part;
+}
+
+__global__ void k_eq3_denom(const double *__restrict__ parts, int n, double *__restrict__ denom)
+{
+    double D = 0.0;
+    for (int i = 0; i < n; ++i) D += parts[i];
+    *denom = D;
+}
+
+__global__ void k_eq3_floor(const double *__restrict__ wpsl, const uint8_t *__restrict__ incl,
+                            int n_e, int npsl, int64_t ncell, int64_t n_hist,
+                            const double *__restrict__ denom, int64_t *__restrict__ count,
+                            double *__restrict__ rem, unsigned long long *__restrict__ floor_sum)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    long long f = 0;
+    if (i < ncell) {
+        const int j = (int)(i % npsl);
+        const int64_t bse = i / npsl;
+        const int e = (int)(bse % n_e), s = (int)((bse / n_e) % 3), b = (int)(bse / (3 * n_e));
+        const double D = *denom;
+        const bool inc = incl[(size_t)(b * 2 + (s ? 1 : 0)) * npsl + j] != 0;
+        const double q = (inc && D > 0.0) ? ((double)n_hist * wpsl[((size_t)s * n_e + e) * npsl + j]) / D
+                                          : 0.0;
+        const double fl = floor(q);
+        f = (long long)fl;
+        count[i] = f;
+        rem[i] = q - fl;
+    }
+    // block-level reduction of the floors, then one atomic per block
+    __shared__ unsigned long long red[32];
+    unsigned long long v = warp_sum_u64((unsigned long long)f);
+    if (lane_id() == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+        t = warp_sum_u64(t);
+        if (threadIdx.x == 0) atomicAdd(floor_sum, t);
+    }
+}
+
+// rank of each remainder (descending, ties to the lower index); the `left`
+// largest get one more particle
+__global__ void k_eq3_rank(const double *__restrict__ rem, int64_t ncell, int64_t n_hist,
+                           const unsigned long long *__restrict__ floor_sum, const double *__restrict__ denom,
+                           int64_t *__restrict__ count)
+{
+    __shared__ double tile[1024];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double ri = i < ncell ? rem[i] : -1.0;
+    int64_t rank = 0;
+    for (int64_t base = 0; base < ncell; base += 1024) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < 1024; t += blockDim.x)
+            tile[t] = (base + t < ncell) ? rem[base + t] : -2.0;
+        __syncthreads();
+        const int lim = (int)((ncell - base) < 1024 ? (ncell - base) : 1024);
+        for (int t = 0; t < lim; ++t) {
+            const double rt = tile[t];
+            rank += (rt > ri) || (rt == ri && base + t < i);
+        }
+    }
+    if (i < ncell) {
+        // an empty sampling area (denominator 0) distributes nothing
+        const int64_t left = (*denom > 0.0 ? n_hist : 0) - (int64_t)(*floor_sum);
+        if (rank < left) count[i] += 1;
+    }
+}
+
+// ------------------------------------------------- per-PSR basis-run plans --
+
+// One CTA per (PSR k, beam b): weights of PSR k's share, Eq. 3 within the run.
+__global__ void k_psr_counts(const double *__restrict__ w, const double *__restrict__ block_scale,
+                             const uint8_t *__restrict__ incl, const int64_t *__restrict__ n_k,
+                             int n_e, int n_r, double dr, int n_beams,
+                             int64_t *__restrict__ count, double *__restrict__ dkb)
+{
+    extern __shared__ double sm[];
+    const int nxy = 2 * n_r, npsl = nxy * nxy;
+    double *q = sm;                 // [npsl]
+    double *rm = sm + npsl;         // [npsl]
+    long long *fl = (long long *)(sm + 2 * npsl);
+    __shared__ double s_D;
+    __shared__ long long s_left;
+    const int kb = blockIdx.x;
+    const int k = kb / n_beams, b = kb % n_beams;
+    const int s = k / (n_e * n_r), e = (k / n_r) % n_e, R = k % n_r;
+    const double *W = w + ((size_t)s * n_e + e) * n_r;
+    const double scale = block_scale[s * n_e + e];
+    const uint8_t *inc = incl + (size_t)(b * 2 + (s ? 1 : 0)) * npsl;
+    for (int j = threadIdx.x; j < npsl; j += blockDim.x) {
+        const int iy = j / nxy, ix = j % nxy;
+        const double r = psl_radius(ix, iy, n_r, dr);
+        int r0, in;
+        double l0;
+        ring_interp(r, n_r, dr, &r0, &l0, &in);
+        double dk = 0.0;
+        if (in) {
+            if (r0 == R) dk = l0 * (W[R] / dr);
+            else if (r0 + 1 == R && l0 < 1.0) dk = (1.0 - l0) * (W[R] / dr);
+        }
+        q[j] = (dk / (2.0 * kPiD * r)) * scale;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double D = 0.0;
+        for (int j = 0; j < npsl; ++j)
+            if (inc[j]) D += q[j];
+        s_D = D;
+        dkb[kb] = D;
+    }
+    __syncthreads();
+    const double D = s_D;
+    const int64_t nk = n_k[k];
+    for (int j = threadIdx.x; j < npsl; j += blockDim.x) {
+        const double qq = (inc[j] && D > 0.0) ? ((double)nk * q[j]) / D : 0.0;
+        const double f = floor(qq);
+        fl[j] = (long long)f;
+        rm[j] = qq - f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long sfl = 0;
+        for (int j = 0; j < npsl; ++j) sfl += fl[j];
+        s_left = (D > 0.0 ? nk : 0) - sfl;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < npsl; j += blockDim.x) {
+        const double rj = rm[j];
+        int rank = 0;
+        for (int t = 0; t < npsl; ++t) rank += (rm[t] > rj) || (rm[t] == rj && t < j);
+        count[(size_t)kb * npsl + j] = fl[j] + (rank < s_left ? 1 : 0);
+    }
+}
+
+// ------------------------------------------------------ scans and entries --
+
+// Single-CTA exclusive scan of v(i) over [0, n); out[n] = total.
+template <class F>
+__global__ void k_scan(F f, int64_t n, int64_t *__restrict__ out)
+{
+    __shared__ long long part[1024];
+    const int T = blockDim.x;
+    const int64_t seg = (n + T - 1) / T;
+    const int64_t a = (int64_t)threadIdx.x * seg, bnd = a + seg < n ? a + seg : n;
+    long long s = 0;
+    for (int64_t i = a; i < bnd; ++i) s += f(i);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int t = 0; t < T; ++t) { long long v = part[t]; part[t] = run; run += v; }
+        out[n] = run;
+    }
+    __syncthreads();
+    long long run = part[threadIdx.x];
+    for (int64_t i = a; i < bnd; ++i) { out[i] = run; run += f(i); }
+}
+
+struct CountOf {
+    const int64_t *c;
+    __device__ long long operator()(int64_t i) const { return c[i]; }
+};
+struct NonZero {
+    const int64_t *c;
+    __device__ long long operator()(int64_t i) const { return c[i] > 0 ? 1 : 0; }
+};
+
+__device__ unsigned long long thresh32(double p)
+{
+    double t = floor(p * 4294967296.0);
+    if (t < 0.0) t = 0.0;
+    if (t > 4294967296.0) t = 4294967296.0;
+    return (unsigned long long)t;
+}
+
+// write the entry table; cells in loop order (whole-source: [b][s][e][y][x],
+// per-PSR: [k][b][y][x])
+__global__ void k_entries(const int64_t *__restrict__ count, const int64_t *__restrict__ cstart,
+                          const int64_t *__restrict__ eidx, int64_t ncell, int per_psr, int n_beams,
+                          int n_e, int n_r, const double *__restrict__ w,
+                          const int32_t *__restrict__ tag_r0, const double *__restrict__ tag_l0,
+                          const double *__restrict__ dkb, const int64_t *__restrict__ n_k,
+                          int64_t *__restrict__ start, EntryRec *__restrict__ ent,
+                          double *__restrict__ escale)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncell || count[i] <= 0) return;
+    const int nxy = 2 * n_r, npsl = nxy * nxy;
+    const int j = (int)(i % npsl);
+    const int64_t o = i / npsl;
+    int b, s, e, fixed = -1;
+    double sc = 0.0;
+    if (per_psr) {
+        const int k = (int)(o / n_beams);
+        b = (int)(o % n_beams);
+        s = k / (n_e * n_r); e = (k / n_r) % n_e;
+        fixed = k % n_r;
+        sc = dkb[k * n_beams + b] / (double)n_k[k];
+    } else {
+        e = (int)(o % n_e); s = (int)((o / n_e) % 3); b = (int)(o / (3 * n_e));
+    }
+    EntryRec r;
+    r.ix = (uint16_t)(j % nxy);
+    r.iy = (uint16_t)(j / nxy);
+    r.beam = (uint8_t)b;
+    r.stype = (uint8_t)s;
+    r.ebin = (uint16_t)e;
+    r.pad = 0;
+    const int r0 = tag_r0[j];
+    const double l0 = tag_l0[j];
+    r.r0 = (uint8_t)r0;
+    r.thr = 0;
+    if (fixed < 0) {
+        fixed = r0;
+        if (l0 < 1.0 && r0 + 1 < n_r) {
+            const double *W = w + ((size_t)s * n_e + e) * n_r;
+            const double a0 = l0 * W[r0], a1 = (1.0 - l0) * W[r0 + 1];
+            const double p0 = (a0 + a1) > 0.0 ? a0 / (a0 + a1) : 1.0;
+            const unsigned long long T = thresh32(p0);
+            if (T == 0ull) fixed = r0 + 1;
+            else if (T >= 4294967296ull) fixed = r0;
+            else { fixed = -1; r.thr = (uint32_t)T; }
+        }
+    }
+    r.fixed_ring = (int16_t)fixed;
+    const int64_t q = eidx[i];
+    ent[q] = r;
+    start[q] = cstart[i];
+    escale[q] = sc;
+}
+
+__global__ void k_entries_end(const int64_t *__restrict__ cstart, int64_t ncell,
+                              const int64_t *__restrict__ eidx, int64_t *__restrict__ start)
+{
+    start[eidx[ncell]] = cstart[ncell];
+}
+
+// scatter-mixture component thresholds and single-precision direction tables
+__global__ void k_dir_tables(const double *__restrict__ mc, const double *__restrict__ mmu,
+                             const double *__restrict__ msa, const double *__restrict__ msb,
+                             const double *__restrict__ esa, const double *__restrict__ esb, int n,
+                             unsigned long long *__restrict__ thr, float4 *__restrict__ mix,
+                             float2 *__restrict__ esig)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *c = mc + 3 * i;
+    const double tot = c[0] + c[1] + c[2];
+    thr[2 * i] = thresh32(c[0] / tot);
+    thr[2 * i + 1] = thresh32((c[0] + c[1]) / tot);
+    for (int k = 0; k < 3; ++k)
+        mix[3 * i + k] = make_float4((float)mmu[3 * i + k], (float)msa[3 * i + k],
+                                     (float)msb[3 * i + k], 0.0f);
+    esig[i] = make_float2((float)esa[i], (float)esb[i]);
+}
+
+bool finite_nonneg(const double *a, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!(a[i] >= 0.0) || !isfinite(a[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+lsm_status free_psl(lsm_psl *p);
+
+lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
+                     const int64_t *per_psr_hist, lsm_psl **out, cudaStream_t st)
+{
+    if (!M || !B || !out) return set_arg_error("lsm_build_psl: NULL argument");
+    *out = nullptr;
+    if (M->n_e < 1 || M->n_e > 64 || M->n_r < 1 || M->n_r > 32)
+        return set_arg_error("lsm_build_psl: need 1 <= n_e <= 64 and 1 <= n_r <= 32");
+    if (!(M->dr > 0) || !(M->z_phsp > 0) || !(M->sigma_s >= 0) || !isfinite(M->sigma_s))
+        return set_arg_error("lsm_build_psl: dr, z_phsp must be > 0 and sigma_s >= 0");
+    for (int s = 0; s < 3; ++s)
+        if (!(M->de[s] > 0) || !isfinite(M->e_lo[s]) || M->e_lo[s] < 0)
+            return set_arg_error("lsm_build_psl: energy bins must have de > 0, e_lo >= 0");
+    if (!M->w || !M->mix_c || !M->mix_mu || !M->mix_sa || !M->mix_sb || !M->e_sa || !M->e_sb)
+        return set_arg_error("lsm_build_psl: NULL model array");
+    const int ne = M->n_e, nr = M->n_r, nxy = 2 * nr, npsl = nxy * nxy;
+    const size_t nw = 3 * (size_t)ne * nr, nm = (size_t)ne * nr * 3, nes = (size_t)ne * nr;
+    if (!finite_nonneg(M->w, nw)) return set_arg_error("lsm_build_psl: PSR weights must be finite, >= 0");
+    if (!finite_nonneg(M->mix_c, nm)) return set_arg_error("lsm_build_psl: mixture weights must be >= 0");
+    for (size_t i = 0; i < nes; ++i) {
+        const double *c = M->mix_c + 3 * i;
+        if (!(c[0] + c[1] + c[2] > 0)) return set_arg_error("lsm_build_psl: mixture weights sum to 0");
+        for (int k = 0; k < 3; ++k) {
+            const double mu = M->mix_mu[3 * i + k], sa = M->mix_sa[3 * i + k], sb = M->mix_sb[3 * i + k];
+            if (!(sa >= 0) || !(sb >= 0) || !(fabs(mu) + 5.8 * sa < 0.5 * kPiD) || !(5.8 * sb < 0.5 * kPiD))
+                return set_arg_error("lsm_build_psl: scatter direction mixture out of range");
+        }
+        if (!(M->e_sa[i] >= 0) || !(M->e_sb[i] >= 0) || !(5.8 * M->e_sa[i] < 0.5 * kPiD) ||
+            !(5.8 * M->e_sb[i] < 0.5 * kPiD))
+            return set_arg_error("lsm_build_psl: electron direction widths out of range");
+    }
+    if (B->n_beams < 1 || B->n_beams > 16 || !B->jaws) return set_arg_error("lsm_build_psl: 1..16 beams");
+    if (!(B->sad > B->z_jaw_x && B->z_jaw_x > M->z_phsp && B->sad > B->z_jaw_y && B->z_jaw_y > M->z_phsp))
+        return set_arg_error("lsm_build_psl: need z_phsp < jaw planes < sad");
+    for (int b = 0; b < B->n_beams; ++b) {
+        const double *j = B->jaws + 4 * b;
+        if (!(j[0] < j[1]) || !(j[2] < j[3]) || !isfinite(j[0]) || !isfinite(j[1]) || !isfinite(j[2]) ||
+            !isfinite(j[3]))
+            return set_arg_error("lsm_build_psl: jaws need x1 < x2 and y1 < y2");
+    }
+    const int nb = B->n_beams;
+    const int npsr = 3 * ne * nr;
+    if (!per_psr_hist && n_hist < 1) return set_arg_error("lsm_build_psl: n_hist must be >= 1");
+    if (per_psr_hist)
+        for (int k = 0; k < npsr; ++k)
+            if (per_psr_hist[k] < 0) return set_arg_error("lsm_build_psl: negative per-PSR history count");
+
+    lsm_psl *P = (lsm_psl *)calloc(1, sizeof(lsm_psl));
+    cudaGetDevice(&P->device);
+    P->n_e = ne; P->n_r = nr; P->n_xy = nxy; P->n_beams = nb; P->per_psr = per_psr_hist != nullptr;
+    P->dr = M->dr; P->z_phsp = M->z_phsp; P->sigma_s = M->sigma_s;
+    for (int s = 0; s < 3; ++s) { P->e_lo[s] = M->e_lo[s]; P->de[s] = M->de[s]; }
+    P->sad = B->sad; P->z_jaw_y = B->z_jaw_y; P->z_jaw_x = B->z_jaw_x;
+    const int64_t ncell = P->per_psr ? (int64_t)npsr * nb * npsl : (int64_t)nb * 3 * ne * npsl;
+    P->ncell = ncell;
+
+#define ALLOC(ptr, bytes)                                        \
+    do {                                                         \
+        cudaError_t e_ = cudaMalloc((void **)&(ptr), (bytes));   \
+        if (e_ != cudaSuccess) { free_psl(P); return set_cuda_error(e_, "cudaMalloc"); } \
+    } while (0)
+#define CK(call)                                                 \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) { free_psl(P); return set_cuda_error(e_, #call); } \
+    } while (0)
+#define CKL(where)                                               \
+    do {                                                         \
+        count_launch();                                          \
+        cudaError_t e_ = cudaGetLastError();                     \
+        if (e_ != cudaSuccess) { free_psl(P); return set_cuda_error(e_, where); } \
+    } while (0)
+
+    // model arrays: one staging buffer
+    double *d_mc, *d_mmu, *d_msa, *d_msb, *d_esa, *d_esb, *d_tmp;
+    int64_t *d_nk = nullptr, *d_cstart, *d_eidx;
+    double *d_rem, *d_parts, *d_denom, *d_dkb = nullptr;
+    unsigned long long *d_fsum;
+    ALLOC(P->d_w, nw * 8);
+    ALLOC(P->d_wpsl, 3 * (size_t)ne * npsl * 8);
+    ALLOC(P->d_scale, 3 * (size_t)ne * 8);
+    ALLOC(P->d_jaws, (size_t)nb * 4 * 8);
+    ALLOC(P->d_jaws_f, (size_t)nb * 4 * 4);
+    ALLOC(P->d_area, (size_t)nb * 8 * 8);
+    ALLOC(P->d_incl, (size_t)nb * 2 * npsl);
+    ALLOC(P->d_count, (size_t)ncell * 8);
+    ALLOC(P->d_tag_r0, (size_t)npsl * 4);
+    ALLOC(P->d_tag_l0, (size_t)npsl * 8);
+    ALLOC(P->d_mixthr, nes * 2 * 8);
+    ALLOC(P->d_mix, nes * 3 * sizeof(float4));
+    ALLOC(P->d_esig, nes * sizeof(float2));
+    ALLOC(d_tmp, (4 * nm + 2 * nes) * 8 + 64);
+    d_mc = d_tmp; d_mmu = d_mc + nm; d_msa = d_mmu + nm; d_msb = d_msa + nm; d_esa = d_msb + nm; d_esb = d_esa + nes;
+    // scratch of the integerisation
+    const size_t scratch = (size_t)ncell * 8 * 3 + 16 * 8 + (size_t)nb * 3 * ne * 8 + 64 + (size_t)npsr * nb * 8 +
+                           (size_t)npsr * 8;
+    char *d_scr;
+    cudaError_t ea = cudaMalloc((void **)&d_scr, scratch);
+    if (ea != cudaSuccess) { cudaFree(d_tmp); free_psl(P); return set_cuda_error(ea, "cudaMalloc"); }
+    d_rem = (double *)d_scr;
+    d_cstart = (int64_t *)(d_scr + (size_t)ncell * 8);
+    d_eidx = (int64_t *)(d_scr + (size_t)ncell * 16 + 8);
+    char *tail = d_scr + (size_t)ncell * 24 + 16 * 8;
+    d_parts = (double *)tail; tail += (size_t)nb * 3 * ne * 8;
+    d_denom = (double *)tail; tail += 8;
+    d_fsum = (unsigned long long *)tail; tail += 8;
+    tail += 48;
+    d_dkb = (double *)tail; tail += (size_t)npsr * nb * 8;
+    d_nk = (int64_t *)tail;
+
+    auto cleanup = [&]() { cudaFree(d_tmp); cudaFree(d_scr); };
+#undef CK
+#define CK(call)                                                 \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) { cleanup(); free_psl(P); return set_cuda_error(e_, #call); } \
+    } while (0)
+#undef CKL
+#define CKL(where)                                               \
+    do {                                                         \
+        count_launch();                                          \
+        cudaError_t e_ = cudaGetLastError();                     \
+        if (e_ != cudaSuccess) { cleanup(); free_psl(P); return set_cuda_error(e_, where); } \
+    } while (0)
+
+    CK(cudaMemcpyAsync(P->d_w, M->w, nw * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P->d_jaws, B->jaws, (size_t)nb * 32, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_mc, M->mix_c, nm * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_mmu, M->mix_mu, nm * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_msa, M->mix_sa, nm * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_msb, M->mix_sb, nm * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_esa, M->e_sa, nes * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_esb, M->e_sb, nes * 8, cudaMemcpyHostToDevice, st));
+    if (per_psr_hist) CK(cudaMemcpyAsync(d_nk, per_psr_hist, (size_t)npsr * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d_fsum, 0, 8, st));
+
+    k_psl_weights<<<3 * ne, 256, 0, st>>>(P->d_w, ne, nr, M->dr, P->d_wpsl, P->d_scale, P->d_tag_r0,
+                                          P->d_tag_l0);
+    CKL("k_psl_weights");
+    k_areas<<<1, 32, 0, st>>>(P->d_jaws, nb, M->z_phsp, B->sad, B->z_jaw_x, B->z_jaw_y, P->d_area, P->d_jaws_f);
+    CKL("k_areas");
+    {
+        const int64_t n = (int64_t)nb * 2 * npsl;
+        k_incl<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P->d_area, nb, nr, M->dr, P->d_incl);
+        CKL("k_incl");
+    }
+    k_dir_tables<<<(unsigned)((nes + 127) / 128), 128, 0, st>>>(d_mc, d_mmu, d_msa, d_msb, d_esa, d_esb,
+                                                                (int)nes, P->d_mixthr, P->d_mix, P->d_esig);
+    CKL("k_dir_tables");
+
+    if (!per_psr_hist) {
+        const int nbse = nb * 3 * ne;
+        k_eq3_parts<<<(nbse + 63) / 64, 64, 0, st>>>(P->d_wpsl, P->d_incl, nb, ne, npsl, d_parts);
+        CKL("k_eq3_parts");
+        k_eq3_denom<<<1, 1, 0, st>>>(d_parts, nbse, d_denom);
+        CKL("k_eq3_denom");
+        const unsigned g = (unsigned)((ncell + 255) / 256);
+        k_eq3_floor<<<g, 256, 0, st>>>(P->d_wpsl, P->d_incl, ne, npsl, ncell, n_hist, d_denom, P->d_count,
+                                       d_rem, d_fsum);
+        CKL("k_eq3_floor");
+        k_eq3_rank<<<g, 256, 0, st>>>(d_rem, ncell, n_hist, d_fsum, d_denom, P->d_count);
+        CKL("k_eq3_rank");
+        CK(cudaMemcpyAsync(&P->denom, d_denom, 8, cudaMemcpyDeviceToHost, st));
+    } else {
+        const size_t smem = (size_t)npsl * 24;
+        if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_psr_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_psr_counts<<<npsr * nb, 256, smem, st>>>(P->d_w, P->d_scale, P->d_incl, d_nk, ne, nr, M->dr, nb,
+                                                   P->d_count, d_dkb);
+        CKL("k_psr_counts");
+        P->denom = 0.0;
+    }
+    k_scan<<<1, 1024, 0, st>>>(CountOf{P->d_count}, ncell, d_cstart);
+    CKL("k_scan");
+    k_scan<<<1, 1024, 0, st>>>(NonZero{P->d_count}, ncell, d_eidx);
+    CKL("k_scan");
+    int64_t n_ent = 0, total = 0;
+    CK(cudaMemcpyAsync(&n_ent, d_eidx + ncell, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&total, d_cstart + ncell, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_ent < 1 || total < 1) {
+        cleanup(); free_psl(P);
+        return set_arg_error("lsm_build_psl: the sampling areas hold no PSL with non-zero weight");
+    }
+    if (n_ent >= (int64_t)1 << 31) { cleanup(); free_psl(P); return set_arg_error("lsm_build_psl: plan too large"); }
+    P->n_ent = n_ent;
+    P->plan_size = total;
+    ALLOC(P->d_start, (size_t)(n_ent + 1) * 8);
+    ALLOC(P->d_ent, (size_t)n_ent * sizeof(EntryRec));
+    ALLOC(P->d_escale, (size_t)n_ent * 8);
+    k_entries<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(P->d_count, d_cstart, d_eidx, ncell, P->per_psr, nb, ne,
+                                                              nr, P->d_w, P->d_tag_r0, P->d_tag_l0, d_dkb, d_nk,
+                                                              P->d_start, P->d_ent, P->d_escale);
+    CKL("k_entries");
+    k_entries_end<<<1, 1, 0, st>>>(d_cstart, ncell, d_eidx, P->d_start);
+    CKL("k_entries_end");
+    CK(cudaStreamSynchronize(st));
+    cleanup();
+
+    SampleParams &sp = P->sp;
+    sp.start = P->d_start; sp.ent = P->d_ent; sp.mixthr = P->d_mixthr; sp.mix = P->d_mix; sp.esig = P->d_esig;
+    sp.jaws_f = P->d_jaws_f; sp.n_ent = n_ent; sp.n_e = ne; sp.n_r = nr;
+    sp.pitch = (float)M->dr; sp.z_phsp = (float)M->z_phsp; sp.sigma_s = (float)M->sigma_s;
+    for (int s = 0; s < 3; ++s) { sp.e_lo[s] = (float)M->e_lo[s]; sp.de[s] = (float)M->de[s]; }
+    sp.zy_rel = (float)(B->z_jaw_y - M->z_phsp);
+    sp.zx_rel = (float)(B->z_jaw_x - M->z_phsp);
+    *out = P;
+    return LSM_OK;
+#undef ALLOC
+#undef CK
+#undef CKL
+}
+
+lsm_status free_psl(lsm_psl *P)
+{
+    if (!P) return LSM_OK;
+    void *ptrs[] = {P->d_w, P->d_wpsl, P->d_scale, P->d_jaws, P->d_area, P->d_escale, P->d_incl,
+                    P->d_count, P->d_start, P->d_ent, P->d_mixthr, P->d_mix, P->d_esig, P->d_jaws_f,
+                    P->d_tag_r0, P->d_tag_l0};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    free(P);
+    return LSM_OK;
+}
+
+}  // namespace lsm

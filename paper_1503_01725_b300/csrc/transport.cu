@@ -1,0 +1,1001 @@
+// transport.cu -- the sample/transport iteration of Sec. 2.1.3 on the GPU.
+//
+// Per iteration of M histories:
+//   k_sample_queue   steps S3-S5 for M histories; accepted particles that hit
+//                    the phantom are compacted by warp ballots into a photon
+//                    queue and an electron queue (sub-sources handled apart so
+//                    that warps never mix photon and electron code);
+//   k_photon (x2)    Woodcock tracking of the primary/scatter photons, then of
+//                    the annihilation photons they created;
+//   k_electron       CSDA condensed-history electrons;
+//   k_flush          FP32 partial tally -> FP64 batch accumulator.
+// The transport kernels are persistent: each warp keeps 32 live particles and
+// refills a lane from its queue as soon as that lane's particle ends, so warps
+// stay full while the queue lasts (the thread-divergence concern of Sec. 2.1.3).
+//
+// The transport physics is the stated simplification of the paper's engine
+// (the paper gives only the 200 keV / 50 keV cutoffs, Sec. 2.3): Compton by
+// Klein-Nishina (Kahn's rejection method), photoelectric and pair from closed
+// forms; electrons by CSDA steps with Bethe stopping power and Highland
+// Gaussian deflection. All transport arithmetic is FP32; tallies are flushed
+// to FP64.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "sample.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace lsm {
+
+struct TP {
+    // phantom, local coordinates
+    const float *rhomat;
+    int nx, ny, nz;
+    float inv_dx, inv_dy, inv_dz;
+    float lx, ly;              // lateral extent (top face)
+    // tables
+    const float4 *xs;
+    const float *mumax;
+    float inv_dlnE, maj;
+    // tally
+    float *part;
+    const uint16_t *idx;
+    int n_rows, n_psr, n_beams;
+    // run
+    int electron_mode, max_steps;
+    float f_e, s_geo;
+    uint32_t k0, k1;
+    RunStats *stats;
+    IterCounters *cnt;
+};
+
+constexpr int kTableBytes = 2 * kGrid * 16 + kGrid * 4;   // 36 KB
+// radiation lengths (g/cm^2): water-like 36.08, bone 21.68
+
+// ---------------------------------------------------------------- tables ---
+// Stage the interaction tables into shared memory with one bulk asynchronous
+// copy (cp.async.bulk, completion on an mbarrier). The wait is bounded; on
+// timeout the block reports through *err and runs from global memory.
+__device__ __forceinline__ bool stage_tables(float4 *s_xs, const float4 *g_xs, const float *g_mumax,
+                                             uint64_t *mbar, unsigned *err)
+{
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTableBytes)
+                     : "memory");
+        const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(s_xs);
+        const uint32_t d1 = (uint32_t)__cvta_generic_to_shared(s_xs + 2 * kGrid);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d0),
+            "l"(g_xs), "r"(2 * kGrid * 16), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d1),
+            "l"(g_mumax), "r"(kGrid * 4), "r"(bar)
+            : "memory");
+    }
+    __syncthreads();
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+    }
+    const int all = __syncthreads_and(done);
+    if (!all && threadIdx.x == 0) atomicOr(err, 1u);
+    return all != 0;
+}
+
+__device__ __forceinline__ void tab_pos(float inv_dlnE, float E, int &i, float &f)
+{
+    float t = (__logf(E) - (float)kLnEmin) * inv_dlnE;
+    t = fminf(fmaxf(t, 0.0f), (float)(kGrid - 1) - 1e-3f);
+    i = (int)t;
+    f = t - (float)i;
+}
+
+__device__ __forceinline__ float4 lerp4(const float4 *a, int i, float f)
+{
+    const float4 p = a[i], q = a[i + 1];
+    return make_float4(p.x + f * (q.x - p.x), p.y + f * (q.y - p.y), p.z + f * (q.z - p.z),
+                       p.w + f * (q.w - p.w));
+}
+
+__device__ __forceinline__ int voxel(const TP &T, float x, float y, float z)
+{
+    const int ix = __float2int_rd(x * T.inv_dx), iy = __float2int_rd(y * T.inv_dy),
+              iz = __float2int_rd(z * T.inv_dz);
+    if ((unsigned)ix >= (unsigned)T.nx || (unsigned)iy >= (unsigned)T.ny || (unsigned)iz >= (unsigned)T.nz)
+        return -1;
+    return (iz * T.ny + iy) * T.nx + ix;
+}
+
+struct Acc {
+    double esc, dep;
+    unsigned long long flights, real, esteps, cap;
+};
+
+template <int MODE>
+__device__ __forceinline__ void deposit(const TP &T, Acc &A, int vox, float e, uint32_t pb)
+{
+    A.dep += e;
+    if (MODE == 0) {
+        atomicAdd(T.part + vox, e);
+    } else {
+        // rows, PSRs and beams are checked so that caller-supplied particles
+        // or index arrays can never write outside the basis tally
+        const int row = T.idx[vox];
+        const uint32_t beam = pb >> 16, k = pb & 0xFFFFu;
+        if (row && row <= T.n_rows && k < (uint32_t)T.n_psr && beam < (uint32_t)T.n_beams)
+            atomicAdd(T.part + ((size_t)beam * T.n_rows + (row - 1)) * T.n_psr + k, e);
+    }
+}
+
+// rotate (u, v, w) by polar cos(theta) and azimuth 2 pi uphi
+__device__ __forceinline__ void rotate(float &u, float &v, float &w, float cost, float uphi)
+{
+    const float sint = sqrtf(fmaxf(0.0f, 1.0f - cost * cost));
+    float sp, cp;
+    sincospif(2.0f * uphi, &sp, &cp);
+    float un, vn, wn;
+    if (fabsf(w) < 0.99999f) {
+        const float s = sqrtf(1.0f - w * w), is = 1.0f / s;
+        un = u * cost + sint * (u * w * cp - v * sp) * is;
+        vn = v * cost + sint * (v * w * cp + u * sp) * is;
+        wn = w * cost - sint * s * cp;
+    } else {
+        un = sint * cp;
+        vn = sint * sp;
+        wn = (w > 0.0f ? 1.0f : -1.0f) * cost;
+    }
+    const float in = rsqrtf(un * un + vn * vn + wn * wn);
+    u = un * in; v = vn * in; w = wn * in;
+}
+
+struct Part {
+    float x, y, z, u, v, w, E;
+    Stream rng;
+    uint32_t pb;
+    int steps;
+};
+
+__device__ __forceinline__ void load_part(const Queue &q, uint32_t i, uint32_t k0, uint32_t k1, Part &p)
+{
+    p.x = q.x[i]; p.y = q.y[i]; p.z = q.z[i];
+    p.u = q.u[i]; p.v = q.v[i]; p.w = q.w[i]; p.E = q.E[i];
+    p.rng.k0 = k0; p.rng.k1 = k1;
+    p.rng.glo = q.glo[i]; p.rng.ghi = q.ghi[i]; p.rng.sid = q.sid[i]; p.rng.ctr = 0;
+    p.pb = q.pb[i];
+    p.steps = 0;
+}
+
+__device__ __forceinline__ void store_part(const Queue &q, uint32_t i, float x, float y, float z, float u,
+                                           float v, float w, float E, uint32_t glo, uint32_t ghi, uint32_t sid,
+                                           uint32_t pb)
+{
+    q.x[i] = x; q.y[i] = y; q.z[i] = z; q.u[i] = u; q.v[i] = v; q.w[i] = w; q.E[i] = E;
+    q.glo[i] = glo; q.ghi[i] = ghi; q.sid[i] = sid; q.pb[i] = pb;
+}
+
+// Append one particle from divergent code: one atomic per coalesced group.
+__device__ __forceinline__ uint32_t push_slot(uint32_t *counter)
+{
+    cg::coalesced_group g = cg::coalesced_threads();
+    uint32_t base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, (uint32_t)g.size());
+    base = g.shfl(base, 0);
+    return base + g.thread_rank();
+}
+
+template <int MODE>
+__device__ __forceinline__ void spawn_electron(const TP &T, Acc &A, const Queue &eq, const Part &p, float Te,
+                                               float u, float v, float w, uint32_t sid, int vox)
+{
+    if (T.electron_mode == 0 || Te < kCutE) {
+        deposit<MODE>(T, A, vox, Te, p.pb);
+        return;
+    }
+    const uint32_t slot = push_slot(&T.cnt->n[2]);
+    if (slot >= eq.cap) {
+        atomicAdd(&T.stats->c[9], 1ull);
+        deposit<MODE>(T, A, vox, Te, p.pb);
+        return;
+    }
+    store_part(eq, slot, p.x, p.y, p.z, u, v, w, Te, p.rng.glo, p.rng.ghi, sid, p.pb);
+}
+
+// One Woodcock flight (and the interaction if the collision is real).
+// Returns false when the photon's history ends.
+template <int MODE>
+__device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t, Acc &A, Part &p,
+                            const Queue &eq, const Queue *pq)
+{
+    int vox = voxel(T, p.x, p.y, p.z);
+    if (vox < 0) { A.esc += p.E; return false; }
+    if (p.E < kCutG) { deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
+    if (++p.steps > T.max_steps) { A.cap++; deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
+    const uint4 r = p.rng.next();
+    int ti;
+    float tf;
+    tab_pos(T.inv_dlnE, p.E, ti, tf);
+    const float mm = (mumax_t[ti] + tf * (mumax_t[ti + 1] - mumax_t[ti])) * T.maj;
+    const float s = -__logf(u01(r.x)) / mm;
+    p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
+    A.flights++;
+    vox = voxel(T, p.x, p.y, p.z);
+    if (vox < 0) { A.esc += p.E; return false; }
+    const float rm = __ldg(T.rhomat + vox);
+    const int m = rm < 0.0f;
+    const float rho = fabsf(rm);
+    const float4 c = lerp4(xs + m * kGrid, ti, tf);
+    const float muC = c.x * rho, muP = c.y * rho, muQ = c.z * rho;
+    const float mut = muC + muP + muQ;
+    if (u01(r.y) * mm > mut) return true;                       // virtual collision
+    A.real++;
+    const float t = u01(r.z) * mut;
+    if (t <= muC) {
+        // Compton: Kahn's method; one block per trial, fourth word = azimuth
+        const float k = p.E / kMe;
+        float eta = 1.0f, uphi = 0.0f;
+        for (int trial = 0; trial < 1000; ++trial) {
+            const uint4 q = p.rng.next();
+            const float r1 = u01(q.x), r2 = u01(q.y), r3 = u01(q.z);
+            bool acc;
+            if (r1 <= (1.0f + 2.0f * k) / (9.0f + 2.0f * k)) {
+                eta = 1.0f + 2.0f * k * r2;
+                acc = r3 <= 4.0f * (1.0f / eta - 1.0f / (eta * eta));
+            } else {
+                eta = (1.0f + 2.0f * k) / (1.0f + 2.0f * k * r2);
+                const float cc = 1.0f - (eta - 1.0f) / k;
+                acc = r3 <= 0.5f * (cc * cc + 1.0f / eta);
+            }
+            if (acc) { uphi = u01(q.w); break; }
+        }
+        const float cost = 1.0f - (eta - 1.0f) / k;
+        const float E1 = p.E / eta;
+        float u = p.u, v = p.v, w = p.w;
+        rotate(u, v, w, cost, uphi);
+        float ex = p.E * p.u - E1 * u, ey = p.E * p.v - E1 * v, ez = p.E * p.w - E1 * w;
+        const float en2 = ex * ex + ey * ey + ez * ez;
+        if (en2 > 0.0f) { const float in = rsqrtf(en2); ex *= in; ey *= in; ez *= in; }
+        else { ex = p.u; ey = p.v; ez = p.w; }
+        const uint4 ids = p.rng.child_ids();
+        spawn_electron<MODE>(T, A, eq, p, p.E - E1, ex, ey, ez, ids.x, vox);
+        p.E = E1; p.u = u; p.v = v; p.w = w;
+        return true;
+    }
+    if (t <= muC + muP) {
+        // photoelectric: the electron takes the photon's energy and direction
+        const uint4 ids = p.rng.child_ids();
+        spawn_electron<MODE>(T, A, eq, p, p.E, p.u, p.v, p.w, ids.x, vox);
+        return false;
+    }
+    // pair: uniform kinetic split, leptons along the photon; annihilation
+    // photons leave the interaction point back to back, isotropic
+    const uint4 q = p.rng.next();
+    const float Tk = p.E - 2.0f * kMe;
+    const float Tm = u01(q.x) * Tk, Tp = Tk - Tm;
+    const float ca = 2.0f * u01(q.y) - 1.0f;
+    const float sa = sqrtf(fmaxf(0.0f, 1.0f - ca * ca));
+    float sp, cp;
+    sincospif(2.0f * u01(q.z), &sp, &cp);
+    const float ax = sa * cp, ay = sa * sp, az = ca;
+    const uint4 ids = p.rng.child_ids();
+    spawn_electron<MODE>(T, A, eq, p, Tm, p.u, p.v, p.w, ids.x, vox);
+    spawn_electron<MODE>(T, A, eq, p, Tp, p.u, p.v, p.w, ids.y, vox);
+    // the annihilation-photon queue holds two per photon of the input queue
+    for (int h = 0; h < 2; ++h) {
+        const float sg = h ? -1.0f : 1.0f;
+        const uint32_t slot = pq ? push_slot(&T.cnt->n[1]) : 0xffffffffu;
+        if (pq && slot < pq->cap)
+            store_part(*pq, slot, p.x, p.y, p.z, sg * ax, sg * ay, sg * az, kMe, p.rng.glo, p.rng.ghi,
+                       h ? ids.w : ids.z, p.pb);
+        else
+            deposit<MODE>(T, A, vox, kMe, p.pb);
+    }
+    return false;
+}
+
+// One CSDA step. Returns false when the electron's history ends.
+template <int MODE>
+__device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
+{
+    const int vox = voxel(T, p.x, p.y, p.z);
+    if (vox < 0) { A.esc += p.E; return false; }
+    if (p.E < kCutE) { deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
+    if (++p.steps > T.max_steps) { A.cap++; deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
+    const float rm = __ldg(T.rhomat + vox);
+    const int m = rm < 0.0f;
+    const float rho = fabsf(rm);
+    int ti;
+    float tf;
+    tab_pos(T.inv_dlnE, p.E, ti, tf);
+    const float4 c0 = lerp4(xs + m * kGrid, ti, tf);
+    const float S = c0.w * rho;
+    const float ds = fminf(T.f_e * p.E / S, T.s_geo);
+    const float Emid = p.E - 0.5f * S * ds;               // midpoint rule
+    tab_pos(T.inv_dlnE, Emid, ti, tf);
+    const float4 c1 = lerp4(xs + m * kGrid, ti, tf);
+    const float dE = fminf(c1.w * rho * ds, p.E);
+    const float hs = 0.5f * ds;
+    const int vm = voxel(T, p.x + hs * p.u, p.y + hs * p.v, p.z + hs * p.w);
+    if (vm >= 0) deposit<MODE>(T, A, vm, dE, p.pb);
+    else A.esc += dE;
+    A.esteps++;
+    const float E0 = p.E;
+    p.x += ds * p.u; p.y += ds * p.v; p.z += ds * p.w;
+    p.E -= dE;
+    if (p.E >= kCutE) {
+        const uint4 r = p.rng.next();
+        const float t = rho * ds * (m ? (1.0f / 21.68f) : (1.0f / 36.08f));
+        const float bcp = E0 * (E0 + 2.0f * kMe) / (E0 + kMe);
+        const float f = fmaxf(1.0f + 0.038f * __logf(t), 0.0f);
+        const float th0 = 13.6f / bcp * sqrtf(t) * f;
+        const float th = fminf(th0 * sqrtf(-2.0f * __logf(u01(r.x))), kPi);
+        rotate(p.u, p.v, p.w, cosf(th), u01(r.y));
+    }
+    return true;
+}
+
+__device__ void flush_acc(const TP &T, const Acc &A)
+{
+    const double esc = warp_sum(A.esc), dep = warp_sum(A.dep);
+    const unsigned long long fl = warp_sum_u64(A.flights), re = warp_sum_u64(A.real),
+                             es = warp_sum_u64(A.esteps), cp = warp_sum_u64(A.cap);
+    if (lane_id() == 0) {
+        if (esc != 0.0) atomicAdd(&T.stats->ledger[2], esc);
+        if (dep != 0.0) atomicAdd(&T.stats->ledger[3], dep);
+        if (fl) atomicAdd(&T.stats->c[5], fl);
+        if (re) atomicAdd(&T.stats->c[6], re);
+        if (es) atomicAdd(&T.stats->c[7], es);
+        if (cp) atomicAdd(&T.stats->c[8], cp);
+    }
+}
+
+// Persistent transport kernel with per-lane refill from queue `qi`.
+// KIND 0: photons (Woodcock), KIND 1: electrons (CSDA).
+template <int MODE, int KIND>
+__global__ void __launch_bounds__(256) k_transport(TP T, Queue in, int qi, Queue eq, Queue pq, int has_pq)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    float4 *s_xs = reinterpret_cast<float4 *>(smem);
+    float *s_mm = reinterpret_cast<float *>(smem + 2 * kGrid * 16);
+    const bool staged = stage_tables(s_xs, T.xs, T.mumax, &mbar, &T.cnt->pad);
+    const float4 *xs = staged ? s_xs : T.xs;
+    const float *mm = staged ? s_mm : T.mumax;
+
+    const uint32_t n_q = *(volatile uint32_t *)&T.cnt->n[qi];
+    const uint32_t n_in = n_q < in.cap ? n_q : in.cap;     // pushes beyond capacity were not stored
+    uint32_t *head = &T.cnt->head[qi];
+    const unsigned lane = lane_id();
+    unsigned lt;
+    lanemask_lt(lt);
+    Acc A = {0.0, 0.0, 0ull, 0ull, 0ull, 0ull};
+    Part p;
+    bool alive = false, drained = false;
+    for (;;) {
+        const unsigned need = __ballot_sync(0xffffffffu, !alive);
+        if (need && !drained) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(head, (uint32_t)__popc(need));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + (uint32_t)__popc(need) >= n_in) drained = true;
+            if (!alive) {
+                const uint32_t i = base + (uint32_t)__popc(need & lt);
+                if (i < n_in) { load_part(in, i, T.k0, T.k1, p); alive = true; }
+            }
+        }
+        if (!__any_sync(0xffffffffu, alive)) break;
+        if (alive) {
+            if (KIND == 0) alive = photon_step<MODE>(T, xs, mm, A, p, eq, has_pq ? &pq : nullptr);
+            else alive = electron_step<MODE>(T, xs, A, p);
+        }
+    }
+    flush_acc(T, A);
+}
+
+// ------------------------------------------------------------ sampling ---
+
+struct SQ {
+    SampleParams sp;
+    uint32_t k0, k1;
+    uint64_t g0;
+    int64_t h0, n;
+    float z_rel;            // phantom surface - z_phsp
+    float x0, y0;           // phantom corner on the surface plane
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queue eq)
+{
+    const unsigned lane = lane_id();
+    unsigned lt;
+    lanemask_lt(lt);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double src = 0.0, rej = 0.0, esc = 0.0;
+    Acc A = {0.0, 0.0, 0ull, 0ull, 0ull, 0ull};
+    unsigned long long nph = 0, nel = 0, nrej = 0, nmiss = 0;
+    for (int64_t base = warp * 32; base < S.n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < S.n;
+        SrcParticle o;
+        o.stype = 0;
+        bool in = false;
+        float lx = 0.0f, ly = 0.0f;
+        if (valid) {
+            sample_history(S.sp, S.k0, S.k1, S.g0 + (uint64_t)i, S.h0 + i, S.z_rel, o);
+            src += o.E;
+            if (!o.accepted) { rej += o.E; nrej++; }
+            else {
+                lx = o.x - S.x0; ly = o.y - S.y0;
+                in = voxel(T, lx, ly, 0.0f) >= 0;       // crosses the phantom's top face
+                if (!in) { esc += o.E; nmiss++; }
+            }
+        }
+        const bool is_e = o.stype == 2;
+        const bool local_e = in && is_e && T.electron_mode == 0;
+        const unsigned mp = __ballot_sync(0xffffffffu, in && !is_e);
+        const unsigned me = __ballot_sync(0xffffffffu, in && is_e && !local_e);
+        uint32_t bp = 0, be = 0;
+        if (lane == 0) {
+            if (mp) bp = atomicAdd(&T.cnt->n[0], (uint32_t)__popc(mp));
+            if (me) be = atomicAdd(&T.cnt->n[2], (uint32_t)__popc(me));
+        }
+        bp = __shfl_sync(0xffffffffu, bp, 0);
+        be = __shfl_sync(0xffffffffu, be, 0);
+        if (in) {
+            const uint64_t g = S.g0 + (uint64_t)i;
+            const uint32_t pb = (uint32_t)o.psr | ((uint32_t)o.beam << 16);
+            if (!is_e) {
+                nph++;
+                store_part(pq, bp + __popc(mp & lt), lx, ly, 0.0f, o.u, o.v, o.w, o.E, (uint32_t)g,
+                           (uint32_t)(g >> 32), 1u, pb);
+            } else {
+                nel++;
+                if (local_e) {
+                    deposit<MODE>(T, A, voxel(T, lx, ly, 0.0f), o.E, pb);
+                } else {
+                    store_part(eq, be + __popc(me & lt), lx, ly, 0.0f, o.u, o.v, o.w, o.E, (uint32_t)g,
+                               (uint32_t)(g >> 32), 1u, pb);
+                }
+            }
+        }
+    }
+    src = warp_sum(src); rej = warp_sum(rej); esc = warp_sum(esc);
+    const double dep = warp_sum(A.dep);
+    nph = warp_sum_u64(nph); nel = warp_sum_u64(nel); nrej = warp_sum_u64(nrej); nmiss = warp_sum_u64(nmiss);
+    if (lane == 0) {
+        atomicAdd(&T.stats->ledger[0], src);
+        if (rej != 0.0) atomicAdd(&T.stats->ledger[1], rej);
+        if (esc != 0.0) atomicAdd(&T.stats->ledger[2], esc);
+        if (dep != 0.0) atomicAdd(&T.stats->ledger[3], dep);
+        if (nph) atomicAdd(&T.stats->c[1], nph);
+        if (nel) atomicAdd(&T.stats->c[2], nel);
+        if (nrej) atomicAdd(&T.stats->c[3], nrej);
+        if (nmiss) atomicAdd(&T.stats->c[4], nmiss);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&T.stats->c[0], (unsigned long long)S.n);
+}
+
+// Public sampler: one record per history (global coordinates).
+__global__ void k_sample_public(SampleParams sp, uint32_t k0, uint32_t k1, uint64_t g0, int64_t h0,
+                                int64_t plan_size, int64_t n, float z_rel, float z_surf, lsm_particles out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int64_t h = h0 + i;
+        if (h >= plan_size) h %= plan_size;
+        SrcParticle o;
+        sample_history(sp, k0, k1, g0 + (uint64_t)i, h, z_rel, o);
+        out.x[i] = o.x; out.y[i] = o.y; out.z[i] = z_surf;
+        out.u[i] = o.u; out.v[i] = o.v; out.w[i] = o.w; out.E[i] = o.E;
+        out.hist[i] = g0 + (uint64_t)i;
+        out.psr[i] = (uint16_t)o.psr;
+        out.beam[i] = (uint8_t)o.beam;
+        out.type[i] = o.stype == 2 ? 1 : 0;
+        out.status[i] = o.accepted ? 0 : 1;
+        if (out.info) {
+            int32_t *q = out.info + 4 * i;
+            q[0] = o.stype | (o.ebin << 8);
+            q[1] = o.ring;
+            q[2] = o.comp;
+            q[3] = (int32_t)o.entry;
+        }
+    }
+}
+
+// Load caller-provided particles (global coordinates) into the queues.
+template <int MODE>
+__global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float z0, TP T, Queue pq, Queue eq)
+{
+    const unsigned lane = lane_id();
+    unsigned lt;
+    lanemask_lt(lt);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double esc = 0.0;
+    Acc A = {0.0, 0.0, 0ull, 0ull, 0ull, 0ull};
+    unsigned long long nph = 0, nel = 0, nmiss = 0;
+    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        bool is_e = false, inside = false;
+        float lx = 0, ly = 0, lz = 0;
+        if (i < n && P.status[i] == 0) {
+            is_e = P.type[i] == 1;
+            lx = P.x[i] - x0; ly = P.y[i] - y0; lz = P.z[i] - z0;
+            inside = lx >= 0.0f && lx < T.lx && ly >= 0.0f && ly < T.ly && lz >= 0.0f &&
+                     voxel(T, lx, ly, lz) >= 0;
+            if (!inside) { esc += P.E[i]; nmiss++; }
+        }
+        const bool local_e = inside && is_e && T.electron_mode == 0;
+        const unsigned mp = __ballot_sync(0xffffffffu, inside && !is_e);
+        const unsigned me = __ballot_sync(0xffffffffu, inside && is_e && !local_e);
+        uint32_t bp = 0, be = 0;
+        if (lane == 0) {
+            if (mp) bp = atomicAdd(&T.cnt->n[0], (uint32_t)__popc(mp));
+            if (me) be = atomicAdd(&T.cnt->n[2], (uint32_t)__popc(me));
+        }
+        bp = __shfl_sync(0xffffffffu, bp, 0);
+        be = __shfl_sync(0xffffffffu, be, 0);
+        if (inside) {
+            const uint64_t g = P.hist[i];
+            const uint32_t pb = (uint32_t)P.psr[i] | ((uint32_t)P.beam[i] << 16);
+            if (!is_e) {
+                nph++;
+                store_part(pq, bp + __popc(mp & lt), lx, ly, lz, P.u[i], P.v[i], P.w[i], P.E[i], (uint32_t)g,
+                           (uint32_t)(g >> 32), 1u, pb);
+            } else {
+                nel++;
+                if (local_e)
+                    deposit<MODE>(T, A, voxel(T, lx, ly, lz), P.E[i], pb);
+                else
+                    store_part(eq, be + __popc(me & lt), lx, ly, lz, P.u[i], P.v[i], P.w[i], P.E[i],
+                               (uint32_t)g, (uint32_t)(g >> 32), 1u, pb);
+            }
+        }
+    }
+    esc = warp_sum(esc);
+    const double dep = warp_sum(A.dep);
+    nph = warp_sum_u64(nph); nel = warp_sum_u64(nel); nmiss = warp_sum_u64(nmiss);
+    if (lane == 0) {
+        if (esc != 0.0) atomicAdd(&T.stats->ledger[2], esc);
+        if (dep != 0.0) atomicAdd(&T.stats->ledger[3], dep);
+        if (nph) atomicAdd(&T.stats->c[1], nph);
+        if (nel) atomicAdd(&T.stats->c[2], nel);
+        if (nmiss) atomicAdd(&T.stats->c[4], nmiss);
+    }
+}
+
+// ------------------------------------------------------------- tallies ---
+
+__global__ void k_flush(float *__restrict__ part, double *__restrict__ batch, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n >> 2;
+    float4 *p4 = reinterpret_cast<float4 *>(part);
+    double2 *b2 = reinterpret_cast<double2 *>(batch);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 v = p4[i];
+        if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f) {
+            double2 a = b2[2 * i], b = b2[2 * i + 1];
+            a.x += v.x; a.y += v.y; b.x += v.z; b.y += v.w;
+            b2[2 * i] = a; b2[2 * i + 1] = b;
+            p4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float v = part[i];
+        if (v != 0.0f) { batch[i] += v; part[i] = 0.0f; }
+    }
+}
+
+__global__ void k_fold(double *__restrict__ batch, double *__restrict__ s1, double *__restrict__ s2, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double v = batch[i];
+        if (v != 0.0) {
+            s1[i] += v;
+            s2[i] += v * v;
+            batch[i] = 0.0;
+        }
+    }
+}
+
+
+// ---------------------------------------------------------- normalisation ---
+
+// dose per source particle (MeV/g) and its batch standard deviation
+__global__ void k_dose(const double *__restrict__ s1, const double *__restrict__ s2, const float *__restrict__ rho,
+                       int64_t n, int B, double scale, double vol, double *__restrict__ dose,
+                       double *__restrict__ sigma)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double m = (double)rho[i] * vol;
+        const double a = s1[i];
+        dose[i] = a / B * scale / m;
+        if (sigma) {
+            const double var = B > 1 ? fmax(s2[i] - a * a / B, 0.0) / (B - 1) : 0.0;
+            sigma[i] = sqrt(B * var) / B * scale / m;
+        }
+    }
+}
+
+// A[(b,row),k] = S1 / B * scale(k,b) / (rho V of the row's voxel)
+__global__ void k_basis(const double *__restrict__ s1, const double *__restrict__ cell_scale,
+                        const double *__restrict__ row_mass, int n_rows, int n_psr, int n_beams, int B,
+                        double *__restrict__ A)
+{
+    const int64_t n = (int64_t)n_beams * n_rows * n_psr;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int k = (int)(i % n_psr);
+        const int64_t br = i / n_psr;
+        const int row = (int)(br % n_rows), b = (int)(br / n_rows);
+        const double m = row_mass[row];
+        A[i] = m > 0.0 ? s1[i] / B * cell_scale[(size_t)k * n_beams + b] / m : 0.0;
+    }
+}
+
+// per (PSR, beam) scale of a per-PSR plan, gathered from the entry table
+__global__ void k_cell_scale(const EntryRec *__restrict__ ent, const double *__restrict__ escale, int64_t n_ent,
+                             int n_e, int n_r, int n_beams, double *__restrict__ cell_scale)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_ent) return;
+    const EntryRec e = ent[i];
+    const int k = ((int)e.stype * n_e + e.ebin) * n_r + e.fixed_ring;
+    cell_scale[(size_t)k * n_beams + e.beam] = escale[i];   // identical for every entry of (k, b)
+}
+
+// mass of the voxel each basis row refers to
+__global__ void k_row_mass(const uint16_t *__restrict__ idx, const float *__restrict__ rho, int64_t nvox,
+                           int n_rows, double vol, double *__restrict__ row_mass)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+        const int r = idx[i];
+        if (r && r <= n_rows) row_mass[r - 1] = (double)rho[i] * vol;
+    }
+}
+
+// ------------------------------------------------------------ host side ---
+
+namespace {
+
+int grid_for(const void *fn, int threads, size_t smem)
+{
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
+    if (per < 1) per = 1;
+    return per * sm_count();
+}
+
+struct Workspace {
+    Queue q[3];          // 0 primary photons, 1 annihilation photons, 2 electrons
+    IterCounters *cnt;
+    void *mem;
+};
+
+// Queues live in one allocation cached on the tally and reused by later runs.
+cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t)
+{
+    if (t->ws && t->ws_chunk >= chunk && t->ws_ecap >= ecap) {
+        chunk = t->ws_chunk;
+        ecap = t->ws_ecap;
+    } else {
+        if (t->ws) cudaFree(t->ws);
+        t->ws = nullptr;
+        size_t total = 256;
+        const uint32_t c2[3] = {chunk, 2 * chunk, ecap};
+        for (int k = 0; k < 3; ++k) total += (size_t)c2[k] * 44 + 11 * 256;
+        cudaError_t e = cudaMalloc(&t->ws, total);
+        if (e != cudaSuccess) return e;
+        t->ws_chunk = chunk;
+        t->ws_ecap = ecap;
+    }
+    const uint32_t caps[3] = {chunk, 2 * chunk, ecap};
+    char *p = (char *)t->ws;
+    W.mem = nullptr;
+    W.cnt = (IterCounters *)p;
+    p += 256;
+    for (int k = 0; k < 3; ++k) {
+        Queue &q = W.q[k];
+        q.cap = caps[k];
+        float **f[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
+        for (int j = 0; j < 7; ++j) { *f[j] = (float *)p; p += ((size_t)caps[k] * 4 + 255) / 256 * 256; }
+        uint32_t **u[4] = {&q.glo, &q.ghi, &q.sid, &q.pb};
+        for (int j = 0; j < 4; ++j) { *u[j] = (uint32_t *)p; p += ((size_t)caps[k] * 4 + 255) / 256 * 256; }
+    }
+    return cudaSuccess;
+}
+
+TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, uint64_t seed, IterCounters *cnt)
+{
+    TP T;
+    T.rhomat = ph->d_rhomat;
+    T.nx = ph->nx; T.ny = ph->ny; T.nz = ph->nz;
+    T.inv_dx = (float)(1.0 / ph->dx); T.inv_dy = (float)(1.0 / ph->dy); T.inv_dz = (float)(1.0 / ph->dz);
+    T.lx = (float)(ph->nx * ph->dx); T.ly = (float)(ph->ny * ph->dy);
+    T.xs = ph->d_xs; T.mumax = ph->d_mumax;
+    T.inv_dlnE = (float)((kGrid - 1) / (kLnEmax - kLnEmin));
+    T.maj = (float)o.majorant_factor;
+    T.part = t->d_part;
+    T.idx = t->mode == 1 ? t->d_idx : nullptr;
+    T.n_rows = t->n_rows; T.n_psr = t->n_psr; T.n_beams = t->n_beams;
+    T.electron_mode = o.electron_mode;
+    T.max_steps = o.max_steps;
+    T.f_e = (float)o.f_e;
+    const double sg = o.s_geo > 0 ? o.s_geo : 0.5 * fmin(ph->dx, fmin(ph->dy, ph->dz));
+    T.s_geo = (float)sg;
+    T.k0 = (uint32_t)seed; T.k1 = (uint32_t)(seed >> 32);
+    T.stats = t->d_stats;
+    T.cnt = cnt;
+    return T;
+}
+
+lsm_status check_opts(lsm_run_opts &o)
+{
+    if (o.electron_mode != 0 && o.electron_mode != 1) return set_arg_error("electron_mode must be 0 or 1");
+    if (!(o.majorant_factor >= 1.0) || !isfinite(o.majorant_factor)) return set_arg_error("majorant_factor must be >= 1");
+    if (!(o.f_e > 0.0 && o.f_e <= 1.0)) return set_arg_error("f_e must be in (0, 1]");
+    if (o.max_steps < 1) return set_arg_error("max_steps must be >= 1");
+    if (o.chunk <= 0) o.chunk = 131072;
+    if (o.chunk > (1 << 24)) return set_arg_error("chunk must be <= 2^24");
+    if (o.n_batches < 1) o.n_batches = 1;
+    return LSM_OK;
+}
+
+// transport everything queued in W (photons of queue 0, then annihilation
+// photons, then electrons) and flush the tally partials
+template <int MODE>
+lsm_status drain(const TP &T, Workspace &W, lsm_tally *t, cudaStream_t st)
+{
+    const size_t smem = (size_t)kTableBytes;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_transport<MODE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_transport<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    static int gp = 0, ge = 0;
+    if (!gp) gp = grid_for((const void *)k_transport<MODE, 0>, 256, smem);
+    if (!ge) ge = grid_for((const void *)k_transport<MODE, 1>, 256, smem);
+    int tk = timer_begin(2, st);
+    k_transport<MODE, 0><<<gp, 256, smem, st>>>(T, W.q[0], 0, W.q[2], W.q[1], 1);
+    LSM_LAUNCHED("k_transport<photon>");
+    timer_end(tk, st);
+    tk = timer_begin(3, st);
+    k_transport<MODE, 0><<<gp, 256, smem, st>>>(T, W.q[1], 1, W.q[2], W.q[1], 0);
+    LSM_LAUNCHED("k_transport<annihilation photon>");
+    timer_end(tk, st);
+    if (T.electron_mode) {
+        tk = timer_begin(4, st);
+        k_transport<MODE, 1><<<ge, 256, smem, st>>>(T, W.q[2], 2, W.q[2], W.q[1], 0);
+        LSM_LAUNCHED("k_transport<electron>");
+        timer_end(tk, st);
+    }
+    const int64_t n = t->ncell;
+    const int gf = (int)std::min<int64_t>((n / 4 + 255) / 256 + 1, 8 * sm_count());
+    tk = timer_begin(5, st);
+    k_flush<<<gf, 256, 0, st>>>(t->d_part, t->d_batch, n);
+    LSM_LAUNCHED("k_flush");
+    timer_end(tk, st);
+    return LSM_OK;
+}
+
+// queue overflows so far (run statistics counter 9); synchronises
+lsm_status read_overflow(lsm_tally *t, cudaStream_t st, unsigned long long *out)
+{
+    LSM_CUDA(cudaMemcpyAsync(out, &t->d_stats->c[9], 8, cudaMemcpyDeviceToHost, st));
+    LSM_CUDA(cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+}  // namespace
+
+lsm_status fold_batch(lsm_tally *t, cudaStream_t st)
+{
+    const int64_t n = t->ncell;
+    const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
+    const int tk = timer_begin(5, st);
+    k_fold<<<g, 256, 0, st>>>(t->d_batch, t->d_s1, t->d_s2, n);
+    count_launch();
+    timer_end(tk, st);
+    LSM_CUDA(cudaGetLastError());
+    t->n_batches++;
+    return LSM_OK;
+}
+
+lsm_status flush_partials(lsm_tally *t, cudaStream_t st)
+{
+    const int64_t n = t->ncell;
+    const int gf = (int)std::min<int64_t>((n / 4 + 255) / 256 + 1, 8 * sm_count());
+    k_flush<<<gf, 256, 0, st>>>(t->d_part, t->d_batch, n);
+    LSM_LAUNCHED("k_flush");
+    return LSM_OK;
+}
+
+lsm_status sample_public(const lsm_psl *P, uint64_t seed, uint64_t g0, int64_t n, double z_surf,
+                         const lsm_particles *out, cudaStream_t st)
+{
+    if (!P || !out) return set_arg_error("lsm_sample: NULL argument");
+    if (n < 0) return set_arg_error("lsm_sample: n < 0");
+    if (n == 0) return LSM_OK;
+    if (!out->x || !out->y || !out->z || !out->u || !out->v || !out->w || !out->E || !out->hist || !out->psr ||
+        !out->beam || !out->type || !out->status)
+        return set_arg_error("lsm_sample: NULL output array");
+    const int64_t h0 = (int64_t)(g0 % (uint64_t)P->plan_size);
+    const int g = (int)std::min<int64_t>((n + 255) / 256, 16 * sm_count());
+    k_sample_public<<<g, 256, 0, st>>>(P->sp, (uint32_t)seed, (uint32_t)(seed >> 32), g0, h0, P->plan_size, n,
+                                       (float)(z_surf - P->z_phsp), (float)z_surf, *out);
+    LSM_LAUNCHED("k_sample_public");
+    return LSM_OK;
+}
+
+lsm_status transport_particles(const lsm_phantom *ph, const lsm_particles *in, int64_t n, uint64_t seed,
+                               lsm_tally *t, const lsm_run_opts *opts, cudaStream_t st)
+{
+    if (!ph || !in || !t || !opts) return set_arg_error("lsm_transport: NULL argument");
+    if (n < 0 || n > (1 << 24)) return set_arg_error("lsm_transport: 0 <= n <= 2^24");
+    lsm_run_opts o = *opts;
+    lsm_status rc = check_opts(o);
+    if (rc) return rc;
+    if (t->nvox != (int64_t)ph->nx * ph->ny * ph->nz) return set_arg_error("lsm_transport: tally of another phantom");
+    if (n == 0) return LSM_OK;
+    Workspace W = {};
+    const uint32_t cap = (uint32_t)std::max<int64_t>(n, 1024);
+    unsigned long long ovf0 = 0, ovf = 0;
+    rc = read_overflow(t, st, &ovf0);
+    if (rc) return rc;
+    cudaError_t e = ws_alloc(W, cap, (uint32_t)std::min<int64_t>(8 * (int64_t)cap + 65536, 1u << 28), t);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsm_transport workspace");
+    TP T = make_tp(ph, t, o, seed, W.cnt);
+    do {
+        if ((e = cudaMemsetAsync(W.cnt, 0, sizeof(IterCounters), st)) != cudaSuccess) { rc = set_cuda_error(e, "memset"); break; }
+        const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
+        if (t->mode == 0)
+            k_enqueue<0><<<g, 256, 0, st>>>(*in, n, (float)ph->x0, (float)ph->y0, (float)ph->z0, T, W.q[0], W.q[2]);
+        else
+            k_enqueue<1><<<g, 256, 0, st>>>(*in, n, (float)ph->x0, (float)ph->y0, (float)ph->z0, T, W.q[0], W.q[2]);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) { rc = set_cuda_error(e, "k_enqueue"); break; }
+        rc = t->mode == 0 ? drain<0>(T, W, t, st) : drain<1>(T, W, t, st);
+        if (rc) break;
+        rc = read_overflow(t, st, &ovf);
+    } while (0);
+    if (rc) return rc;
+    if (ovf > ovf0) return LSM_ERR_OVERFLOW;
+    return LSM_OK;
+}
+
+lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint64_t seed,
+                    const lsm_run_opts *opts, cudaStream_t st)
+{
+    if (!P || !ph || !t || !opts) return set_arg_error("lsm_run: NULL argument");
+    lsm_run_opts o = *opts;
+    lsm_status rc = check_opts(o);
+    if (rc) return rc;
+    if (t->nvox != (int64_t)ph->nx * ph->ny * ph->nz) return set_arg_error("lsm_run: tally of another phantom");
+    if (t->mode == 1 && (t->n_beams != P->n_beams || t->n_psr != 3 * P->n_e * P->n_r))
+        return set_arg_error("lsm_run: basis tally shape does not match the plan");
+    const uint32_t chunk = (uint32_t)std::min<int64_t>(o.chunk, P->plan_size);
+    Workspace W = {};
+    unsigned long long ovf0 = 0, ovf = 0;
+    rc = read_overflow(t, st, &ovf0);
+    if (rc) return rc;
+    cudaError_t e = ws_alloc(W, chunk, 8 * chunk + 65536, t);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsm_run workspace");
+    TP T = make_tp(ph, t, o, seed, W.cnt);
+    SQ S;
+    S.sp = P->sp;
+    S.k0 = T.k0; S.k1 = T.k1;
+    S.z_rel = (float)(ph->z0 - P->z_phsp);
+    S.x0 = (float)ph->x0; S.y0 = (float)ph->y0;
+    static int gs0 = 0, gs1 = 0;
+    if (!gs0) gs0 = grid_for((const void *)k_sample_queue<0>, 256, 0);
+    if (!gs1) gs1 = grid_for((const void *)k_sample_queue<1>, 256, 0);
+    for (int b = 0; b < o.n_batches && rc == LSM_OK; ++b) {
+        for (int64_t h0 = 0; h0 < P->plan_size && rc == LSM_OK; h0 += chunk) {
+            S.h0 = h0;
+            S.n = std::min<int64_t>(chunk, P->plan_size - h0);
+            S.g0 = (uint64_t)b * (uint64_t)P->plan_size + (uint64_t)h0;
+            if ((e = cudaMemsetAsync(W.cnt, 0, sizeof(IterCounters), st)) != cudaSuccess) {
+                rc = set_cuda_error(e, "memset");
+                break;
+            }
+            const int gs = (int)std::min<int64_t>((S.n + 255) / 256, t->mode == 0 ? gs0 : gs1);
+            const int tk = timer_begin(1, st);
+            if (t->mode == 0) k_sample_queue<0><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
+            else k_sample_queue<1><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
+            count_launch();
+            timer_end(tk, st);
+            if ((e = cudaGetLastError()) != cudaSuccess) { rc = set_cuda_error(e, "k_sample_queue"); break; }
+            rc = t->mode == 0 ? drain<0>(T, W, t, st) : drain<1>(T, W, t, st);
+            if (rc) break;
+        }
+        if (rc == LSM_OK) rc = fold_batch(t, st);
+    }
+    if (rc == LSM_OK) rc = read_overflow(t, st, &ovf);
+    if (rc) return rc;
+    if (ovf > ovf0) return LSM_ERR_OVERFLOW;
+    return LSM_OK;
+}
+
+lsm_status dose_impl(const lsm_tally *t, const lsm_phantom *ph, double scale, double *dose, double *sigma,
+                     lsm_mem mem, cudaStream_t st)
+{
+    if (!t || !ph || !dose) return set_arg_error("lsm_dose: NULL argument");
+    if (t->mode != 0) return set_arg_error("lsm_dose: needs an energy (mode 0) tally");
+    if (t->n_batches < 1) return set_arg_error("lsm_dose: no batch folded yet");
+    const int64_t n = t->nvox;
+    double *dd = dose, *ds = sigma;
+    void *tmp = nullptr;
+    if (mem == LSM_MEM_HOST) {
+        LSM_CUDA(cudaMalloc(&tmp, (size_t)n * 16));
+        dd = (double *)tmp;
+        ds = sigma ? dd + n : nullptr;
+    }
+    const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
+    k_dose<<<g, 256, 0, st>>>(t->d_s1, t->d_s2, ph->d_rho, n, t->n_batches, scale, ph->dx * ph->dy * ph->dz, dd, ds);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && mem == LSM_MEM_HOST) {
+        e = cudaMemcpyAsync(dose, dd, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && sigma) e = cudaMemcpyAsync(sigma, ds, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsm_dose");
+    return LSM_OK;
+}
+
+lsm_status basis_impl(const lsm_tally *t, const lsm_psl *P, const lsm_phantom *ph, const uint16_t *idx3d,
+                      lsm_mem idx_mem, double *A, lsm_mem mem, cudaStream_t st)
+{
+    if (!t || !P || !ph || !A) return set_arg_error("lsm_basis_matrix: NULL argument");
+    if (t->mode != 1 || !P->per_psr) return set_arg_error("lsm_basis_matrix: needs a basis tally and a per-PSR plan");
+    if (t->n_batches < 1) return set_arg_error("lsm_basis_matrix: no batch folded yet");
+    const int npsr = t->n_psr, nb = t->n_beams, nr = t->n_rows;
+    const int64_t ncell = (int64_t)nb * nr * npsr;
+    char *tmp = nullptr;
+    const size_t bytes = (size_t)npsr * nb * 8 + (size_t)nr * 8 + (mem == LSM_MEM_HOST ? (size_t)ncell * 8 : 0) + 64;
+    LSM_CUDA(cudaMalloc(&tmp, bytes));
+    double *cs = (double *)tmp, *rm = cs + (size_t)npsr * nb;
+    double *dA = mem == LSM_MEM_HOST ? rm + nr : A;
+    cudaError_t e = cudaMemsetAsync(tmp, 0, (size_t)npsr * nb * 8 + (size_t)nr * 8, st);
+    const uint16_t *didx = t->d_idx;
+    (void)idx3d; (void)idx_mem;
+    if (e == cudaSuccess) {
+        k_cell_scale<<<(unsigned)((P->n_ent + 255) / 256), 256, 0, st>>>(P->d_ent, P->d_escale, P->n_ent, P->n_e,
+                                                                          P->n_r, nb, cs);
+        count_launch();
+        const int g = (int)std::min<int64_t>((t->nvox + 255) / 256, 8 * sm_count());
+        k_row_mass<<<g, 256, 0, st>>>(didx, ph->d_rho, t->nvox, nr, ph->dx * ph->dy * ph->dz, rm);
+        count_launch();
+        const int g2 = (int)std::min<int64_t>((ncell + 255) / 256, 8 * sm_count());
+        k_basis<<<g2, 256, 0, st>>>(t->d_s1, cs, rm, nr, npsr, nb, t->n_batches, dA);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && mem == LSM_MEM_HOST) {
+        e = cudaMemcpyAsync(A, dA, (size_t)ncell * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFree(tmp);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsm_basis_matrix");
+    return LSM_OK;
+}
+
+}  // namespace lsm

@@ -1,0 +1,433 @@
+"""Python binding of liblsm.so (include/lsm.h): argument marshalling only.
+
+Every function keeps the name of the C entry point it wraps. Device memory
+comes from PyTorch tensors; streams are PyTorch CUDA streams. Every step of
+the method runs in the library's CUDA kernels: there is no CPU path here, and
+loading fails loudly when the compiled library or a CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblsm.so")
+
+LSM_OK, LSM_ERR_ARG, LSM_ERR_CUDA, LSM_ERR_OVERFLOW, LSM_ERR_TIMEOUT, LSM_ERR_NOT_CONVERGED = range(6)
+LSM_MEM_HOST, LSM_MEM_DEVICE = 0, 1
+_STATUS = {1: "LSM_ERR_ARG", 2: "LSM_ERR_CUDA", 3: "LSM_ERR_OVERFLOW", 4: "LSM_ERR_TIMEOUT",
+           5: "LSM_ERR_NOT_CONVERGED"}
+
+_dp = C.POINTER(C.c_double)
+
+
+class LSMError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lsm_psr_model(C.Structure):
+    _fields_ = [("n_e", C.c_int32), ("n_r", C.c_int32), ("dr", C.c_double), ("z_phsp", C.c_double),
+                ("sigma_s", C.c_double), ("e_lo", C.c_double * 3), ("de", C.c_double * 3),
+                ("w", _dp), ("mix_c", _dp), ("mix_mu", _dp), ("mix_sa", _dp), ("mix_sb", _dp),
+                ("e_sa", _dp), ("e_sb", _dp)]
+
+
+class lsm_beams(C.Structure):
+    _fields_ = [("sad", C.c_double), ("z_jaw_y", C.c_double), ("z_jaw_x", C.c_double),
+                ("n_beams", C.c_int32), ("jaws", _dp)]
+
+
+class lsm_particles(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("x", "y", "z", "u", "v", "w", "E", "hist", "psr", "beam",
+                                          "type", "status", "info")]
+
+
+class lsm_phantom_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dx", C.c_double),
+                ("dy", C.c_double), ("dz", C.c_double), ("x0", C.c_double), ("y0", C.c_double),
+                ("z0", C.c_double), ("rho", C.c_void_p), ("mat", C.c_void_p), ("mem", C.c_int)]
+
+
+class lsm_tally_desc(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("idx3d", C.c_void_p), ("idx3d_mem", C.c_int),
+                ("n_rows", C.c_int32), ("n_psr", C.c_int32), ("n_beams", C.c_int32)]
+
+
+class lsm_run_opts(C.Structure):
+    _fields_ = [("electron_mode", C.c_int32), ("n_batches", C.c_int32),
+                ("majorant_factor", C.c_double), ("f_e", C.c_double), ("s_geo", C.c_double),
+                ("max_steps", C.c_int32), ("chunk", C.c_int32)]
+
+
+class lsm_nnls_opts(C.Structure):
+    _fields_ = [("method", C.c_int32), ("max_iter", C.c_int32), ("delta", C.c_double),
+                ("armijo_sigma", C.c_double), ("armijo_beta", C.c_double), ("use_x0", C.c_int32)]
+
+
+class lsm_nnls_report(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("objective", C.c_double),
+                ("kkt", C.c_double)]
+
+
+_EXPORTS = {
+    "lsm_build_psl": (C.c_int, [C.POINTER(lsm_psr_model), C.POINTER(lsm_beams), C.c_int64,
+                                C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.c_void_p]),
+    "lsm_psl_destroy": (None, [C.c_void_p]),
+    "lsm_psl_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), _dp]),
+    "lsm_psl_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "lsm_sample": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64, C.c_double,
+                             C.POINTER(lsm_particles), C.c_void_p]),
+    "lsm_phantom_create": (C.c_int, [C.POINTER(lsm_phantom_desc), C.POINTER(C.c_void_p), C.c_void_p]),
+    "lsm_phantom_destroy": (None, [C.c_void_p]),
+    "lsm_phantom_tables": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), _dp]),
+    "lsm_tally_create": (C.c_int, [C.c_void_p, C.POINTER(lsm_tally_desc), C.POINTER(C.c_void_p),
+                                   C.c_void_p]),
+    "lsm_tally_destroy": (None, [C.c_void_p]),
+    "lsm_tally_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lsm_tally_end_batch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lsm_tally_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                 C.POINTER(C.c_int32), C.c_void_p]),
+    "lsm_tally_ledger": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.c_void_p]),
+    "lsm_transport": (C.c_int, [C.c_void_p, C.POINTER(lsm_particles), C.c_int64, C.c_uint64,
+                                C.c_void_p, C.POINTER(lsm_run_opts), C.c_void_p]),
+    "lsm_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(lsm_run_opts),
+                          C.c_void_p]),
+    "lsm_dose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
+                           C.c_void_p]),
+    "lsm_basis_matrix": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                   C.c_void_p, C.c_int, C.c_void_p]),
+    "lsm_commission": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int,
+                                 C.POINTER(lsm_nnls_opts), _dp, C.POINTER(lsm_nnls_report),
+                                 C.c_void_p]),
+    "lsm_timing_enable": (C.c_int, [C.c_int]),
+    "lsm_timing_read": (C.c_int, [_dp, C.POINTER(C.c_int64), C.c_int]),
+    "lsm_last_error": (C.c_char_p, []),
+    "lsm_launch_count": (C.c_int64, []),
+}
+
+_lib = None
+
+
+def load_library(require_gpu: bool = True):
+    """Load liblsm.so. Raises if it is missing (build it with
+    ``python -m paper_1503_01725_b300.build``) or, by default, if no CUDA
+    device is present."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_1503_01725_b300.build")
+    if require_gpu:
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblsm needs a CUDA device; there is no CPU path")
+    L = C.CDLL(LIB_PATH)
+    for name, (res, args) in _EXPORTS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str, ok=(LSM_OK,)):
+    if rc not in ok:
+        raise LSMError(rc, where, _lib.lsm_last_error().decode())
+    return rc
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+class Handle:
+    _destroy = None
+
+    def __init__(self, ptr: C.c_void_p, keep=None):
+        self.ptr = ptr
+        self._keep = keep
+
+    def close(self):
+        if self.ptr and self.ptr.value and _lib is not None:
+            getattr(_lib, self._destroy)(self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PSL(Handle):
+    _destroy = "lsm_psl_destroy"
+
+
+class PhantomHandle(Handle):
+    _destroy = "lsm_phantom_destroy"
+
+
+class Tally(Handle):
+    _destroy = "lsm_tally_destroy"
+
+
+def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None) -> PSL:
+    L = load_library()
+    keep = [_f64(getattr(model, k)) for k in ("w", "mix_c", "mix_mu", "mix_sa", "mix_sb", "e_sa", "e_sb")]
+    ms = lsm_psr_model(n_e=model.n_e, n_r=model.n_r, dr=model.dr, z_phsp=model.z_phsp,
+                       sigma_s=model.sigma_s, e_lo=(C.c_double * 3)(*model.e_lo),
+                       de=(C.c_double * 3)(*model.de),
+                       **{k: a.ctypes.data_as(_dp) for k, a in
+                          zip(("w", "mix_c", "mix_mu", "mix_sa", "mix_sb", "e_sa", "e_sb"), keep)})
+    jaws = _f64(beams.jaws)
+    bs = lsm_beams(sad=beams.sad, z_jaw_y=beams.z_jaw_y, z_jaw_x=beams.z_jaw_x,
+                   n_beams=beams.n_beams, jaws=jaws.ctypes.data_as(_dp))
+    pp = None
+    if per_psr_hist is not None:
+        ppa = np.ascontiguousarray(per_psr_hist, dtype=np.int64)
+        keep.append(ppa)
+        pp = ppa.ctypes.data_as(C.POINTER(C.c_int64))
+    out = C.c_void_p()
+    _check(L.lsm_build_psl(C.byref(ms), C.byref(bs), int(n_hist), pp, C.byref(out), _stream(stream)),
+           "lsm_build_psl")
+    h = PSL(out)
+    h.model, h.beams = model, beams
+    h.info, h.denom = lsm_psl_info(h)
+    return h
+
+
+def lsm_psl_info(psl: PSL):
+    info = np.zeros(4, dtype=np.int64)
+    den = C.c_double()
+    _check(_lib.lsm_psl_info(psl.ptr, info.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(den)),
+           "lsm_psl_info")
+    return {"n_xy": int(info[0]), "n_ent": int(info[1]), "plan_size": int(info[2]),
+            "per_psr": int(info[3])}, den.value
+
+
+def lsm_psl_copy(psl: PSL, which: int) -> np.ndarray:
+    m, b = psl.model, psl.beams
+    n_xy, n_ent = psl.info["n_xy"], psl.info["n_ent"]
+    nb = b.n_beams
+    shapes = {0: ((3, m.n_e, n_xy, n_xy), np.float64), 1: ((nb, 2, n_xy, n_xy), np.uint8),
+              2: ((nb, 2, 4), np.float64),
+              3: (((m.n_psr, nb, n_xy, n_xy) if psl.info["per_psr"] else (nb, 3, m.n_e, n_xy, n_xy)),
+                  np.int64),
+              4: ((n_ent + 1,), np.int64), 5: ((n_ent, 6), np.int32), 6: ((n_ent,), np.float64)}
+    shp, dt = shapes[which]
+    a = np.zeros(shp, dtype=dt)
+    _check(_lib.lsm_psl_copy(psl.ptr, which, a.ctypes.data_as(C.c_void_p)), "lsm_psl_copy")
+    return a
+
+
+def _particles_struct(t: dict) -> lsm_particles:
+    return lsm_particles(**{k: (t[k].data_ptr() if t.get(k) is not None else None)
+                            for k in ("x", "y", "z", "u", "v", "w", "E", "hist", "psr", "beam",
+                                      "type", "status", "info")})
+
+
+def alloc_particles(n: int, with_info: bool = True, device="cuda") -> dict:
+    import torch
+    f = lambda: torch.empty(n, dtype=torch.float32, device=device)  # noqa: E731
+    d = {k: f() for k in ("x", "y", "z", "u", "v", "w", "E")}
+    d["hist"] = torch.empty(n, dtype=torch.int64, device=device)
+    d["psr"] = torch.empty(n, dtype=torch.int16, device=device)
+    for k in ("beam", "type", "status"):
+        d[k] = torch.empty(n, dtype=torch.uint8, device=device)
+    d["info"] = torch.empty((n, 4), dtype=torch.int32, device=device) if with_info else None
+    return d
+
+
+def lsm_sample(psl: PSL, seed: int, hist_begin: int, n: int, z_surface: float = 100.0, out=None,
+               stream=None) -> dict:
+    if out is None:
+        out = alloc_particles(n)
+    ps = _particles_struct(out)
+    _check(_lib.lsm_sample(psl.ptr, seed, hist_begin, n, z_surface, C.byref(ps), _stream(stream)),
+           "lsm_sample")
+    return out
+
+
+def lsm_phantom_create(ph, stream=None) -> PhantomHandle:
+    L = load_library()
+    import torch
+    rho = ph.rho if isinstance(ph.rho, torch.Tensor) else np.ascontiguousarray(ph.rho, dtype=np.float32)
+    mat = ph.mat if isinstance(ph.mat, torch.Tensor) else np.ascontiguousarray(ph.mat, dtype=np.uint8)
+    dev = isinstance(rho, torch.Tensor)
+    ptr = (lambda a: a.data_ptr()) if dev else (lambda a: a.ctypes.data)
+    d = lsm_phantom_desc(nx=ph.nx, ny=ph.ny, nz=ph.nz, dx=ph.dx, dy=ph.dy, dz=ph.dz, x0=ph.x0, y0=ph.y0,
+                         z0=ph.z0, rho=ptr(rho), mat=ptr(mat),
+                         mem=LSM_MEM_DEVICE if dev else LSM_MEM_HOST)
+    out = C.c_void_p()
+    _check(L.lsm_phantom_create(C.byref(d), C.byref(out), _stream(stream)), "lsm_phantom_create")
+    h = PhantomHandle(out)
+    h.desc = ph
+    return h
+
+
+def lsm_phantom_tables(ph: PhantomHandle):
+    out = np.zeros(2 * 1024 * 4 + 1024, dtype=np.float32)
+    grid = np.zeros(2)
+    _check(_lib.lsm_phantom_tables(ph.ptr, out.ctypes.data_as(C.POINTER(C.c_float)),
+                                   grid.ctypes.data_as(_dp)), "lsm_phantom_tables")
+    return out[: 8192].reshape(2, 1024, 4), out[8192:], grid
+
+
+def lsm_tally_create(ph: PhantomHandle, mode: int = 0, idx3d=None, n_rows: int = 0, n_psr: int = 0,
+                     n_beams: int = 1, stream=None) -> Tally:
+    idx = None
+    mem = LSM_MEM_HOST
+    if idx3d is not None:
+        idx = np.ascontiguousarray(idx3d, dtype=np.uint16)
+    d = lsm_tally_desc(mode=mode, idx3d=idx.ctypes.data if idx is not None else None, idx3d_mem=mem,
+                       n_rows=n_rows, n_psr=n_psr, n_beams=n_beams)
+    out = C.c_void_p()
+    _check(_lib.lsm_tally_create(ph.ptr, C.byref(d), C.byref(out), _stream(stream)), "lsm_tally_create")
+    t = Tally(out, keep=idx)
+    t.mode, t.n_rows, t.n_psr, t.n_beams = mode, n_rows, n_psr, n_beams
+    t.ncell = ph.desc.nvox if mode == 0 else n_beams * n_rows * n_psr
+    return t
+
+
+def lsm_tally_reset(t: Tally, stream=None):
+    _check(_lib.lsm_tally_reset(t.ptr, _stream(stream)), "lsm_tally_reset")
+
+
+def lsm_tally_end_batch(t: Tally, stream=None):
+    _check(_lib.lsm_tally_end_batch(t.ptr, _stream(stream)), "lsm_tally_end_batch")
+
+
+def lsm_tally_read(t: Tally, stream=None):
+    s1 = np.zeros(t.ncell)
+    s2 = np.zeros(t.ncell)
+    nb = C.c_int32()
+    _check(_lib.lsm_tally_read(t.ptr, s1.ctypes.data, s2.ctypes.data, LSM_MEM_HOST, C.byref(nb),
+                               _stream(stream)), "lsm_tally_read")
+    return s1, s2, nb.value
+
+
+def lsm_tally_ledger(t: Tally, stream=None):
+    led = np.zeros(4)
+    st = np.zeros(10, dtype=np.int64)
+    _check(_lib.lsm_tally_ledger(t.ptr, led.ctypes.data_as(_dp), st.ctypes.data_as(C.POINTER(C.c_int64)),
+                                 _stream(stream)), "lsm_tally_ledger")
+    keys = ["histories", "photons", "electrons", "rejected", "missed", "flights", "real", "esteps",
+            "cap_hits", "overflows"]
+    return dict(zip(["source", "rejected", "escaped", "deposited"], led)), dict(zip(keys, (int(v) for v in st)))
+
+
+@dataclass
+class RunOpts:
+    electron_mode: int = 1
+    n_batches: int = 16
+    majorant_factor: float = 1.0
+    f_e: float = 0.25
+    s_geo: float = 0.0
+    max_steps: int = 100000
+    chunk: int = 131072
+
+    def struct(self) -> lsm_run_opts:
+        return lsm_run_opts(electron_mode=self.electron_mode, n_batches=self.n_batches,
+                            majorant_factor=self.majorant_factor, f_e=self.f_e, s_geo=self.s_geo,
+                            max_steps=self.max_steps, chunk=self.chunk)
+
+
+def lsm_transport(ph: PhantomHandle, particles: dict, n: int, seed: int, tally: Tally,
+                  opts: RunOpts | None = None, stream=None) -> int:
+    o = (opts or RunOpts()).struct()
+    ps = _particles_struct(particles)
+    return _check(_lib.lsm_transport(ph.ptr, C.byref(ps), n, seed, tally.ptr, C.byref(o), _stream(stream)),
+                  "lsm_transport", ok=(LSM_OK, LSM_ERR_OVERFLOW))
+
+
+def lsm_run(psl: PSL, ph: PhantomHandle, tally: Tally, seed: int, opts: RunOpts | None = None,
+            stream=None) -> int:
+    o = (opts or RunOpts()).struct()
+    return _check(_lib.lsm_run(psl.ptr, ph.ptr, tally.ptr, seed, C.byref(o), _stream(stream)), "lsm_run",
+                  ok=(LSM_OK, LSM_ERR_OVERFLOW))
+
+
+def lsm_dose(t: Tally, ph: PhantomHandle, scale: float, device: bool = False, stream=None):
+    """Dose per source particle (MeV/g) and its batch sigma."""
+    n = ph.desc.nvox
+    if device:
+        import torch
+        d = torch.empty(n, dtype=torch.float64, device="cuda")
+        s = torch.empty(n, dtype=torch.float64, device="cuda")
+        _check(_lib.lsm_dose(t.ptr, ph.ptr, scale, d.data_ptr(), s.data_ptr(), LSM_MEM_DEVICE,
+                             _stream(stream)), "lsm_dose")
+        return d, s
+    d = np.zeros(n)
+    s = np.zeros(n)
+    _check(_lib.lsm_dose(t.ptr, ph.ptr, scale, d.ctypes.data, s.ctypes.data, LSM_MEM_HOST, _stream(stream)),
+           "lsm_dose")
+    shp = (ph.desc.nz, ph.desc.ny, ph.desc.nx)
+    return d.reshape(shp), s.reshape(shp)
+
+
+def lsm_basis_matrix(t: Tally, psl: PSL, ph: PhantomHandle, stream=None) -> np.ndarray:
+    A = np.zeros((t.n_beams * t.n_rows, t.n_psr))
+    _check(_lib.lsm_basis_matrix(t.ptr, psl.ptr, ph.ptr, None, LSM_MEM_DEVICE, A.ctypes.data, LSM_MEM_HOST,
+                                 _stream(stream)), "lsm_basis_matrix")
+    return A
+
+
+def lsm_commission(A, b, method: int = 0, max_iter: int = 0, delta: float = 1e-12, sigma: float = 1e-4,
+                   beta: float = 0.5, x0=None, stream=None):
+    """Eq. 8 on the GPU in FP64. A, b: numpy (host) or CUDA float64 tensors."""
+    import torch
+    L = load_library()
+    dev = isinstance(A, torch.Tensor)
+    if dev:
+        A_ = A.contiguous().to(torch.float64)
+        b_ = b.contiguous().to(torch.float64)
+        pa, pb, mem = A_.data_ptr(), b_.data_ptr(), LSM_MEM_DEVICE
+    else:
+        A_ = _f64(A)
+        b_ = _f64(b)
+        pa, pb, mem = A_.ctypes.data, b_.ctypes.data, LSM_MEM_HOST
+    m, n = A_.shape
+    x = np.ones(n) if x0 is None else _f64(x0).copy()
+    o = lsm_nnls_opts(method=method, max_iter=max_iter, delta=delta, armijo_sigma=sigma,
+                      armijo_beta=beta, use_x0=int(x0 is not None))
+    rep = lsm_nnls_report()
+    rc = _check(L.lsm_commission(pa, m, n, pb, mem, C.byref(o), x.ctypes.data_as(_dp), C.byref(rep),
+                                 _stream(stream)), "lsm_commission", ok=(LSM_OK, LSM_ERR_NOT_CONVERGED))
+    return x, {"iterations": rep.iterations, "converged": bool(rep.converged), "objective": rep.objective,
+               "kkt": rep.kkt, "status": rc}
+
+
+TIMER_NAMES = ("psl_build", "sample", "photon", "annihilation_photon", "electron", "tally", "nnls",
+               "phantom")
+
+
+def lsm_timing_enable(on: bool = True):
+    _check(load_library().lsm_timing_enable(int(on)), "lsm_timing_enable")
+
+
+def lsm_timing_read(reset: bool = True) -> dict:
+    ms = np.zeros(8)
+    n = np.zeros(8, dtype=np.int64)
+    _check(_lib.lsm_timing_read(ms.ctypes.data_as(_dp), n.ctypes.data_as(C.POINTER(C.c_int64)), int(reset)),
+           "lsm_timing_read")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(TIMER_NAMES)}
+
+
+def lsm_launch_count() -> int:
+    return int(load_library(require_gpu=False).lsm_launch_count())
+
+
+def exported_symbols() -> list[str]:
+    return list(_EXPORTS)

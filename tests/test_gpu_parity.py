@@ -1,0 +1,319 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars:
+* integer work is bit-exact: PSL inclusion, Eq. 3 counts, plan entries and
+  prefixes, and per history the plan entry, sub-source, energy bin, ring,
+  mixture component, PSR index, beam and particle type;
+* the FP64 PSL weights, sampling areas and per-PSR scales are bit-identical
+  (same IEEE operations in the same order, no FMA on either side);
+* jaw rejection agrees except within 1e-4 cm of a jaw edge (the decision
+  follows a chain of transcendentals evaluated in FP32 on the GPU and FP64 in
+  the oracle); such histories must be fewer than 1e-3 of the total;
+* sampled attributes within 1e-5 relative (positions also 1e-5 cm absolute,
+  direction components 2e-6 absolute);
+* dose: |z| < 3 on >= 99% of voxels above 10% of the maximum and mean dose
+  within 0.5%, z = (D_gpu - D_oracle) / sqrt(s_gpu^2 + s_oracle^2).
+"""
+import numpy as np
+import pytest
+
+from oracle import nnls as N
+from oracle import oracle as O
+from paper_1503_01725_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1503_01725_b300 import lsm
+    lsm.load_library()
+    return lsm
+
+
+def _models():
+    m1 = W.primary_only_model()
+    m2 = W.psr_model(6, 10, 0.25, seed=2)
+    m3 = W.psr_model(5, 12, 0.3, seed=31)
+    return [
+        (m1, W.beams(W.square_field(5.0)), 100_000),
+        (m2, W.beams(W.square_field(10.0)), 1_000_003),
+        (m3, W.beams(W.square_field(4.0, cx=1.5, cy=-2.0), W.square_field(20.0),
+                     np.array([-7.0, 2.0, -1.0, 9.0])), 777_777),
+    ]
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_psl_build_bit_exact(L, case):
+    m, b, n = _models()[case]
+    g = L.lsm_build_psl(m, b, n)
+    o = O.Plan(m, b, n)
+    assert g.info["n_xy"] == o.n_xy and g.info["n_ent"] == o.n_ent and g.info["plan_size"] == n
+    assert g.denom == o.denom
+    assert np.array_equal(L.lsm_psl_copy(g, 0), o.wpsl)          # FP64 bit-identical
+    assert np.array_equal(L.lsm_psl_copy(g, 1), o.incl)
+    assert np.array_equal(L.lsm_psl_copy(g, 2), o.area)
+    assert np.array_equal(L.lsm_psl_copy(g, 3), o.count)
+    assert np.array_equal(L.lsm_psl_copy(g, 4), o.ent_start)
+    assert np.array_equal(L.lsm_psl_copy(g, 5), o.entries)
+
+
+def test_per_psr_plan_bit_exact(L):
+    wl = W.workload_commissioning(hist_lo=200, hist_hi=5000)
+    n_k = wl.extra["n_k"]
+    g = L.lsm_build_psl(wl.model, wl.beams, per_psr_hist=n_k)
+    o = O.Plan(wl.model, wl.beams, per_psr_n=n_k)
+    assert g.info["plan_size"] == o.n_hist and g.info["n_ent"] == o.n_ent
+    assert np.array_equal(L.lsm_psl_copy(g, 3), o.count)
+    assert np.array_equal(L.lsm_psl_copy(g, 4), o.ent_start)
+    assert np.array_equal(L.lsm_psl_copy(g, 5), o.entries)
+    assert np.array_equal(L.lsm_psl_copy(g, 6), o.ent_scale)
+
+
+def test_empty_sampling_area_is_an_argument_error(L):
+    m = W.psr_model(3, 4, 0.25, seed=1)
+    with pytest.raises(L.LSMError) as e:
+        L.lsm_build_psl(m, W.beams(np.array([60.0, 70.0, 60.0, 70.0])), 1000)
+    assert e.value.status == L.LSM_ERR_ARG
+
+
+def _sample_both(L, m, b, n_plan, seed, g0, n):
+    import torch
+    g = L.lsm_build_psl(m, b, n_plan)
+    o = O.Plan(m, b, n_plan)
+    out = L.lsm_sample(g, seed, g0, n, W.SSD)
+    torch.cuda.synchronize()
+    gs = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+    os_ = O.sample(o, seed, g0, n, W.SSD)
+    return gs, os_
+
+
+@pytest.mark.parametrize("case,seed,g0", [(0, 1, 0), (1, 7, 3_000_000), (2, 99, 2 ** 33 + 5)])
+def test_sampling_parity(L, case, seed, g0):
+    m, b, n_plan = _models()[case]
+    n = 200_000
+    gs, os_ = _sample_both(L, m, b, n_plan, seed, g0, n)
+    info = gs["info"]
+    assert np.array_equal(info[:, 3], os_["entry"])
+    assert np.array_equal(info[:, 0] & 0xFF, os_["stype"])
+    assert np.array_equal(info[:, 0] >> 8, os_["ebin"])
+    assert np.array_equal(info[:, 1], os_["ring"])
+    assert np.array_equal(info[:, 2], os_["comp"])
+    assert np.array_equal(gs["psr"].astype(np.int64) & 0xFFFF, os_["psr"])
+    assert np.array_equal(gs["beam"], os_["beam"])
+    assert np.array_equal(gs["type"], os_["type"])
+    assert np.array_equal(gs["hist"], g0 + np.arange(n))
+    # jaw rejection: equal away from the jaw edges
+    far = os_["edge"] > 1e-4
+    assert np.mean(~far) < 1e-3
+    assert np.array_equal(gs["status"][far], os_["status"][far])
+    ok = far & (os_["status"] == 0)
+    for k, atol in (("x", 1e-5), ("y", 1e-5), ("u", 2e-6), ("v", 2e-6), ("w", 2e-6), ("E", 0.0)):
+        np.testing.assert_allclose(gs[k][ok], os_[k][ok], rtol=1e-5, atol=atol, err_msg=k)
+    assert np.all(gs["z"] == np.float32(W.SSD))
+
+
+def test_sampling_edge_cases(L):
+    import torch
+    m, b, n_plan = _models()[0]
+    g = L.lsm_build_psl(m, b, n_plan)
+    L.lsm_sample(g, 1, 0, 0, W.SSD, out=L.alloc_particles(1))   # n = 0 is a no-op
+    # the plan is periodic: history g and g + plan size share the PSL
+    a = L.lsm_sample(g, 5, 10, 1000, W.SSD)
+    c = L.lsm_sample(g, 5, 10 + n_plan, 1000, W.SSD)
+    torch.cuda.synchronize()
+    assert torch.equal(a["info"][:, 3], c["info"][:, 3])
+    assert not torch.equal(a["x"], c["x"])
+    with pytest.raises(L.LSMError):
+        L.lsm_sample(g, 1, 0, -1, W.SSD, out=L.alloc_particles(1))
+
+
+def test_interaction_tables_match_closed_forms(L):
+    ph = L.lsm_phantom_create(W.heterogeneous_phantom(16, 16, 16, 0.5, seed=3))
+    xs, mm, grid = L.lsm_phantom_tables(ph)
+    E = np.exp(grid[0] + grid[1] * np.arange(1024))
+    sel = (E > 0.01) & (E < 7.0)
+    for m in (0, 1):
+        for comp in range(3):
+            want = np.array([O.mu_mass(e, m, comp) for e in E[sel]])
+            np.testing.assert_allclose(xs[m, sel, comp], want, rtol=2e-6, atol=1e-30)
+        want = np.array([O.scol_mass(e, m) for e in E[sel]])
+        np.testing.assert_allclose(xs[m, sel, 3], want, rtol=2e-6)
+    rho = ph.desc.rho
+    rmax = [rho[ph.desc.mat == k].max() if (ph.desc.mat == k).any() else 0.0 for k in (0, 1)]
+    want = np.maximum(rmax[0] * np.array([O.mu_mass(e, 0, 3) for e in E[sel]]),
+                      rmax[1] * np.array([O.mu_mass(e, 1, 3) for e in E[sel]]))
+    assert np.all(mm[sel] >= want * (1 - 1e-6))
+    np.testing.assert_allclose(mm[sel], want, rtol=5e-5)
+
+
+def _dose_zcheck(dg, sg, do, so, frac=0.99, thr=0.1, mean_tol=0.005):
+    sel = do > thr * do.max()
+    z = (dg - do)[sel] / np.sqrt(sg[sel] ** 2 + so[sel] ** 2 + 1e-300)
+    assert np.mean(np.abs(z) < 3) >= frac, np.mean(np.abs(z) < 3)
+    assert abs(dg[sel].mean() / do[sel].mean() - 1) < mean_tol
+
+
+def _run_both(L, wl, n_batches, **kw):
+    g = L.lsm_build_psl(wl.model, wl.beams, wl.n_hist)
+    ph = L.lsm_phantom_create(wl.phantom)
+    t = L.lsm_tally_create(ph)
+    opts = L.RunOpts(electron_mode=wl.electron_mode, n_batches=n_batches, **kw)
+    rc = L.lsm_run(g, ph, t, wl.seed, opts)
+    assert rc == L.LSM_OK
+    s1, s2, nb = L.lsm_tally_read(t)
+    led, st = L.lsm_tally_ledger(t)
+    o = O.Plan(wl.model, wl.beams, wl.n_hist)
+    r = O.run(o, wl.phantom, wl.seed, n_batches=n_batches, electron_mode=wl.electron_mode)
+    return (s1, s2, nb, led, st), r, (g, ph, t)
+
+
+def test_dose_parity_primary_local_deposition(L):
+    wl = W.workload_primary_5x5(100_000)
+    (s1, s2, nb, led, st), r, _ = _run_both(L, wl, 8)
+    assert nb == 8
+    dg, sg = O.dose_and_sigma(s1, s2, nb)
+    do, so = O.dose_and_sigma(r["s1"].ravel(), r["s2"].ravel(), 8)
+    _dose_zcheck(dg, sg, do, so)
+    # histories and the integer outcome of sampling agree exactly
+    assert st["histories"] == r["stats"]["histories"]
+    assert abs(st["rejected"] - r["stats"]["rejected"]) <= 1e-3 * st["histories"]
+    assert led["source"] == pytest.approx(r["ledger"]["source"], rel=1e-6)
+    assert led["source"] == pytest.approx(led["rejected"] + led["escaped"] + led["deposited"], rel=1e-6)
+    assert s1.sum() == pytest.approx(led["deposited"], rel=1e-5)
+
+
+def test_dose_parity_three_sources_csda(L):
+    wl = W.workload_full_10x10(400_000)
+    (s1, s2, nb, led, st), r, _ = _run_both(L, wl, 8)
+    dg, sg = O.dose_and_sigma(s1, s2, nb)
+    do, so = O.dose_and_sigma(r["s1"].ravel(), r["s2"].ravel(), 8)
+    _dose_zcheck(dg, sg, do, so)
+    assert st["overflows"] == 0 and st["cap_hits"] == 0
+    assert led["source"] == pytest.approx(led["rejected"] + led["escaped"] + led["deposited"], rel=1e-6)
+    # algorithmic work within statistics of the oracle's counts
+    for k in ("flights", "real", "esteps"):
+        assert st[k] == pytest.approx(r["stats"][k], rel=0.01), k
+    assert st["electrons"] == r["stats"]["electrons"]
+
+
+def test_dose_parity_heterogeneous(L):
+    wl = W.workload_full_10x10(200_000)
+    wl.phantom = W.heterogeneous_phantom(48, 48, 40, 0.4, seed=4, n_slabs=3, n_spheres=6)
+    (s1, s2, nb, led, st), r, _ = _run_both(L, wl, 8)
+    dg, sg = O.dose_and_sigma(s1, s2, nb)
+    do, so = O.dose_and_sigma(r["s1"].ravel(), r["s2"].ravel(), 8)
+    _dose_zcheck(dg, sg, do, so)
+
+
+def test_ragged_chunks_and_reuse(L):
+    """Plan size not a multiple of the iteration size; a second run on the same
+    tally continues the batch count."""
+    wl = W.workload_full_10x10(50_021)
+    g = L.lsm_build_psl(wl.model, wl.beams, wl.n_hist)
+    ph = L.lsm_phantom_create(wl.phantom)
+    t = L.lsm_tally_create(ph)
+    L.lsm_run(g, ph, t, 3, L.RunOpts(n_batches=2, chunk=4096))
+    a1, _, nb = L.lsm_tally_read(t)
+    assert nb == 2
+    t2 = L.lsm_tally_create(ph)
+    L.lsm_run(g, ph, t2, 3, L.RunOpts(n_batches=2, chunk=50_021))
+    b1, _, _ = L.lsm_tally_read(t2)
+    # same histories, different iteration split: identical up to FP32 atomics order
+    np.testing.assert_allclose(a1, b1, rtol=1e-4, atol=1e-6 * a1.max())
+    L.lsm_run(g, ph, t2, 4, L.RunOpts(n_batches=1))
+    _, _, nb2 = L.lsm_tally_read(t2)
+    assert nb2 == 3
+
+
+def test_sample_then_transport_equals_run(L):
+    import torch
+    wl = W.workload_full_10x10(30_000)
+    g = L.lsm_build_psl(wl.model, wl.beams, wl.n_hist)
+    ph = L.lsm_phantom_create(wl.phantom)
+    t1 = L.lsm_tally_create(ph)
+    L.lsm_run(g, ph, t1, 9, L.RunOpts(n_batches=1))
+    a, _, _ = L.lsm_tally_read(t1)
+    t2 = L.lsm_tally_create(ph)
+    parts = L.lsm_sample(g, 9, 0, wl.n_hist, ph.desc.z0)
+    L.lsm_transport(ph, parts, wl.n_hist, 9, t2, L.RunOpts(n_batches=1))
+    L.lsm_tally_end_batch(t2)
+    torch.cuda.synchronize()
+    b, _, _ = L.lsm_tally_read(t2)
+    np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6 * a.max())
+
+
+def test_basis_tally_parity(L):
+    wl = W.workload_commissioning(hist_lo=100, hist_hi=2000)
+    ph = W.water_phantom(32, 32, 48, 0.5)
+    idx, n_rows = W.commissioning_index(ph, depths_cm=(1.5, 10.0))
+    n_k = wl.extra["n_k"]
+    g = L.lsm_build_psl(wl.model, wl.beams, per_psr_hist=n_k)
+    phh = L.lsm_phantom_create(ph)
+    t = L.lsm_tally_create(phh, mode=1, idx3d=idx, n_rows=n_rows, n_psr=wl.model.n_psr,
+                           n_beams=wl.beams.n_beams)
+    L.lsm_run(g, phh, t, 3, L.RunOpts(n_batches=4))
+    s1, s2, nb = L.lsm_tally_read(t)
+    o = O.Plan(wl.model, wl.beams, per_psr_n=n_k)
+    r = O.run(o, ph, 3, n_batches=4, tally_mode=1, idx3d=idx, n_rows=n_rows)
+    dg, sg = O.dose_and_sigma(s1, s2, 4)
+    do, so = O.dose_and_sigma(r["s1"].ravel(), r["s2"].ravel(), 4)
+    _dose_zcheck(dg, sg, do, so, thr=0.1)
+    # basis matrix normalisation: S1 / B * (in-area PSR weight / n_k) / voxel mass
+    A = L.lsm_basis_matrix(t, g, phh)
+    scale = np.zeros((wl.model.n_psr, wl.beams.n_beams))
+    for (b_, s, e, ix, iy, k), sc in zip(o.entries, o.ent_scale):
+        scale[k, b_] = sc
+    mass = np.zeros(n_rows)
+    flat = idx.ravel()
+    mass[flat[flat > 0] - 1] = ph.rho.ravel()[flat > 0] * ph.dx * ph.dy * ph.dz
+    S = s1.reshape(wl.beams.n_beams, n_rows, -1)
+    want = S / 4 * scale.T[:, None, :] / mass[None, :, None]
+    np.testing.assert_allclose(A.reshape(S.shape), want, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_commission_active_set_parity(L, seed):
+    rng = np.random.default_rng(seed)
+    m, n = 400, 60
+    A = np.abs(rng.standard_normal((m, n))) + 0.1 * rng.standard_normal((m, n))
+    xt = rng.uniform(0.8, 1.2, n)
+    xt[rng.random(n) < 0.1] = 0
+    b = A @ xt * (1 + 0.005 * rng.standard_normal(m))
+    x, rep = L.lsm_commission(A, b, method=0)
+    xo, _ = N.lawson_hanson(A, b)
+    np.testing.assert_allclose(x, xo, atol=1e-9 * max(1.0, np.abs(xo).max()))
+    assert rep["kkt"] < 1e-10 * np.linalg.norm(2 * A.T @ b)
+    assert rep["objective"] == pytest.approx(N.objective(A, b, xo), rel=1e-9)
+
+
+def test_commission_projected_gradient(L):
+    """Sec. 2.2.4 on an inconsistent problem (F* > 0, so the relative change of
+    F goes to zero and the stopping rule fires); the limit is the NNLS minimiser."""
+    rng = np.random.default_rng(5)
+    A = np.abs(rng.standard_normal((300, 40)))
+    xt = rng.uniform(0.8, 1.2, 40)
+    xt[[4, 9]] = 0.0
+    b = A @ xt * (1 + 0.005 * rng.standard_normal(300))
+    x, rep = L.lsm_commission(A, b, method=1, delta=1e-13, max_iter=200000)
+    assert rep["converged"]
+    xo, _ = N.lawson_hanson(A, b)
+    xp, _, ok = N.gradient_projection(A, b, delta=1e-13)
+    assert ok
+    fo = N.objective(A, b, xo)
+    assert N.objective(A, b, x) == pytest.approx(fo, rel=1e-7)
+    np.testing.assert_allclose(x, xo, atol=2e-3)
+    np.testing.assert_allclose(x, xp, atol=2e-3)
+
+
+def test_commission_device_inputs_and_errors(L):
+    import torch
+    rng = np.random.default_rng(1)
+    A = np.abs(rng.standard_normal((50, 8)))
+    b = A @ np.linspace(0.5, 1.5, 8)
+    x_h, _ = L.lsm_commission(A, b)
+    x_d, _ = L.lsm_commission(torch.tensor(A, device="cuda"), torch.tensor(b, device="cuda"))
+    np.testing.assert_array_equal(x_h, x_d)
+    np.testing.assert_allclose(x_h, np.linspace(0.5, 1.5, 8), atol=1e-9)
+    with pytest.raises(L.LSMError):
+        L.lsm_commission(np.zeros((5, 2000)), np.zeros(5))
