@@ -71,6 +71,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def rank_seed(rank: int) -> int:
+    """Philox key of a rank: every rank draws independent histories (no
+    data-path exchange; the ranks are replicas of the same workload)."""
+    return 1 + 7919 * rank
+
+
+def slowest_ms(total_ms: float, world: int) -> float:
+    """Timing reduction over ranks: the job takes as long as its slowest rank."""
+    if world <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -198,7 +215,7 @@ def main():
     wl = W.workload_full_10x10(args.n_hist)
     n_plan = args.n_hist // args.n_batches
     opts = lsm.RunOpts(electron_mode=1, n_batches=args.n_batches, chunk=args.chunk)
-    seed0 = 1 + 7919 * rank
+    seed0 = rank_seed(rank)
     stream = torch.cuda.current_stream()
 
     # device-resident inputs: phantom and tally created once
@@ -243,10 +260,8 @@ def main():
     lsm.lsm_timing_enable(False)
     led, st = lsm.lsm_tally_ledger(tally)      # counters of the last step (reset each step)
     total_ms = float(sum(ms_steps))
+    total_ms = slowest_ms(total_ms, world)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
 
     # end-to-end through the public API with host buffers
