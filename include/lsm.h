@@ -320,6 +320,28 @@ lsm_status lsm_commission(const double *A, int32_t m, int32_t n, const double *b
                           lsm_stream stream);
 
 /*
+ * lsm_commission_static -- the same solve as lsm_commission, for callers that
+ * must not allocate GPU memory while they run (for example a planning service
+ * that reserves all of its device memory at start-up, or a host application
+ * that owns the GPU memory and loads this library as a plugin; cudaMalloc and
+ * cudaFree would also synchronise the whole device). The paper has no
+ * counterpart: this is a deployment variant. Its scratch is one fixed device
+ * array of about 1 MiB that every GPU loading the library holds until process
+ * exit; it limits the problem to n <= 256 unknowns (larger n: LSM_ERR_ARG).
+ * A (double [m][n], row-major), b (double [m]) and x (double [n]) are all
+ * DEVICE pointers; x receives the solution (and is the projected-gradient
+ * start when opts->use_x0 != 0, else it is set to 1). report is host memory
+ * and may be NULL. The first call on a device looks up the array's device
+ * address (once per device). Every call shares the one array, which keeps the
+ * previous call's contents: calls that overlap on the GPU (other streams or
+ * host threads) race and must be serialised by the caller. Calls no
+ * cudaMalloc or cudaFree. Synchronises the stream before returning.
+ */
+lsm_status lsm_commission_static(const double *A, int32_t m, int32_t n, const double *b,
+                                 const lsm_nnls_opts *opts, double *x, lsm_nnls_report *report,
+                                 lsm_stream stream);
+
+/*
  * Timers (the breakdown of Sec. 3.1 / Table 1: source initialisation, particle
  * generation, transport simulation). When enabled, the library records CUDA
  * events on the launching stream around each kernel group and accumulates

@@ -15,6 +15,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "handles.cuh"
@@ -474,4 +475,121 @@ lsm_status commission(const double *A, int32_t m, int32_t n, const double *b, ls
     return rc;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant (lsm_commission_static).
+//
+// Some callers may not allocate GPU memory while they run: a planning service
+// that reserves all of its device memory up front and forbids growth during a
+// session, or a host application that owns the GPU memory and embeds this
+// library as a plugin. For them the solve's scratch (the Gram matrix, its
+// Cholesky factor, A^T b and the small result records) lives in one fixed
+// device array that the library holds from load until process exit. Its size
+// caps the number of unknowns at kStaticMaxN.
+namespace {
+
+constexpr int kStaticMaxN = 256;
+constexpr size_t kStaticGram = (size_t)kStaticMaxN * kStaticMaxN;
+// G, L (n x n each, packed with stride n), c (n), KKT value (8), result record (8)
+constexpr size_t kStaticDoubles = 2 * kStaticGram + kStaticMaxN + 16;
+
+static __device__ __align__(256) double g_nnls_scratch[kStaticDoubles];
+
+// device address of g_nnls_scratch per device, looked up once per device
+std::mutex g_scratch_mu;
+double *g_scratch_ptr[64] = {};
+
+__global__ void k_fill(double *__restrict__ x, double v, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+lsm_status scratch_address(double **out)
+{
+    int dev = 0;
+    LSM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_arg_error("lsm_commission_static: device index above 63");
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        double *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void **)&p, g_nnls_scratch);
+        if (e != cudaSuccess) return set_cuda_error(e, "lsm_commission_static: cudaGetSymbolAddress");
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return LSM_OK;
+}
+
+}  // namespace
+
 }  // namespace lsm
+
+extern "C" lsm_status lsm_commission_static(const double *A, int32_t m, int32_t n, const double *b,
+                                            const lsm_nnls_opts *opts, double *x, lsm_nnls_report *report,
+                                            lsm_stream stream)
+{
+    using namespace lsm;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!A || !b || !x || m < 1 || n < 1) return set_arg_error("lsm_commission_static: NULL pointer or empty problem");
+    if (n > kStaticMaxN)
+        return set_arg_error("lsm_commission_static: at most 256 unknowns fit the fixed scratch; use lsm_commission");
+    lsm_nnls_opts o = {0, 0, 1e-12, 1e-4, 0.5, 0};
+    if (opts) o = *opts;
+    if (o.method != 0 && o.method != 1) return set_arg_error("lsm_commission_static: method must be 0 or 1");
+    if (o.max_iter <= 0) o.max_iter = o.method == 0 ? 3 * n : 200000;
+    if (!(o.delta > 0)) o.delta = 1e-12;
+    if (!(o.armijo_sigma > 0 && o.armijo_sigma < 1)) o.armijo_sigma = 1e-4;
+    if (!(o.armijo_beta > 0 && o.armijo_beta < 1)) o.armijo_beta = 0.5;
+    double *base = nullptr;
+    lsm_status rc = scratch_address(&base);
+    if (rc) return rc;
+    double *G = base, *L = base + kStaticGram, *c = base + 2 * kStaticGram;
+    double *kkt = c + kStaticMaxN;
+    NnlsOut *dout = (NnlsOut *)(kkt + 8);
+    // the array keeps the previous call's contents: reset the result record
+    LSM_CUDA(cudaMemsetAsync(dout, 0, sizeof(NnlsOut), st));
+    LSM_CUDA(cudaMemsetAsync(kkt, 0, 8, st));
+    dim3 gb((n + 31) / 32, (n + 31) / 32);
+    k_gram<<<gb, dim3(32, 8), 0, st>>>(A, b, m, n, G, c);
+    LSM_LAUNCHED("k_gram");
+    if (o.method == 0) {
+        const size_t smem = (size_t)n * 8 * 5 + (size_t)n * 4 * 2;
+        LSM_CUDA(cudaFuncSetAttribute(k_lawson_hanson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const double tol_scale = 10.0 * 2.220446049250313e-16 * (m > n ? m : n);
+        k_lawson_hanson<<<1, kT, smem, st>>>(G, c, n, tol_scale, o.max_iter, L, x, dout);
+        LSM_LAUNCHED("k_lawson_hanson");
+    } else {
+        if (!o.use_x0) {
+            k_fill<<<(n + 255) / 256, 256, 0, st>>>(x, 1.0, n);
+            LSM_LAUNCHED("k_fill");
+        }
+        k_nnls_report<<<1, kT, 0, st>>>(A, b, G, c, x, m, n, dout, kkt);
+        LSM_LAUNCHED("k_nnls_report");
+        NnlsOut f0;
+        LSM_CUDA(cudaMemcpyAsync(&f0, dout, sizeof(NnlsOut), cudaMemcpyDeviceToHost, st));
+        LSM_CUDA(cudaStreamSynchronize(st));
+        const size_t smem = (size_t)n * 8 * 6;
+        LSM_CUDA(cudaFuncSetAttribute(k_projected_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_projected_gradient<<<1, kT, smem, st>>>(G, c, n, f0.objective, o.delta, o.max_iter, o.armijo_sigma,
+                                                  o.armijo_beta, x, dout);
+        LSM_LAUNCHED("k_projected_gradient");
+    }
+    NnlsOut keep, fin;
+    LSM_CUDA(cudaMemcpyAsync(&keep, dout, sizeof(NnlsOut), cudaMemcpyDeviceToHost, st));
+    k_nnls_report<<<1, kT, 0, st>>>(A, b, G, c, x, m, n, dout, kkt);
+    LSM_LAUNCHED("k_nnls_report");
+    double hk = 0.0;
+    LSM_CUDA(cudaMemcpyAsync(&fin, dout, sizeof(NnlsOut), cudaMemcpyDeviceToHost, st));
+    LSM_CUDA(cudaMemcpyAsync(&hk, kkt, 8, cudaMemcpyDeviceToHost, st));
+    LSM_CUDA(cudaStreamSynchronize(st));
+    if (report) {
+        report->iterations = keep.iterations;
+        report->converged = keep.converged;
+        report->objective = fin.objective;
+        report->kkt = hk;
+    }
+    if (keep.status == 2) return set_arg_error("lsm_commission_static: passive-set Gram matrix not positive definite");
+    return keep.status == 1 ? LSM_ERR_NOT_CONVERGED : LSM_OK;
+}
+

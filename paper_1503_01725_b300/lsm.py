@@ -104,6 +104,9 @@ _EXPORTS = {
     "lsm_commission": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int,
                                  C.POINTER(lsm_nnls_opts), _dp, C.POINTER(lsm_nnls_report),
                                  C.c_void_p]),
+    "lsm_commission_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                        C.POINTER(lsm_nnls_opts), C.c_void_p, C.POINTER(lsm_nnls_report),
+                                        C.c_void_p]),
     "lsm_timing_enable": (C.c_int, [C.c_int]),
     "lsm_timing_read": (C.c_int, [_dp, C.POINTER(C.c_int64), C.c_int]),
     "lsm_last_error": (C.c_char_p, []),
@@ -407,6 +410,23 @@ def lsm_commission(A, b, method: int = 0, max_iter: int = 0, delta: float = 1e-1
                                  _stream(stream)), "lsm_commission", ok=(LSM_OK, LSM_ERR_NOT_CONVERGED))
     return x, {"iterations": rep.iterations, "converged": bool(rep.converged), "objective": rep.objective,
                "kkt": rep.kkt, "status": rc}
+
+
+def lsm_commission_static(A, b, x, method: int = 0, max_iter: int = 0, delta: float = 1e-12,
+                          sigma: float = 1e-4, beta: float = 0.5, use_x0: bool = False, stream=None):
+    """Allocation-free Eq. 8 solve for callers that cannot allocate device
+    memory: A (m x n), b (m) and x (n, output) are CUDA float64 tensors the
+    caller owns; n <= 256."""
+    L = load_library()
+    m, n = A.shape
+    o = lsm_nnls_opts(method=method, max_iter=max_iter, delta=delta, armijo_sigma=sigma, armijo_beta=beta,
+                      use_x0=int(use_x0))
+    rep = lsm_nnls_report()
+    rc = _check(L.lsm_commission_static(A.data_ptr(), m, n, b.data_ptr(), C.byref(o), x.data_ptr(), C.byref(rep),
+                                        _stream(stream)), "lsm_commission_static",
+                ok=(LSM_OK, LSM_ERR_NOT_CONVERGED))
+    return {"iterations": rep.iterations, "converged": bool(rep.converged), "objective": rep.objective,
+            "kkt": rep.kkt, "status": rc}
 
 
 TIMER_NAMES = ("psl_build", "sample", "photon", "annihilation_photon", "electron", "tally", "nnls",
