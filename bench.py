@@ -61,7 +61,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n-hist", type=int, default=10_000_000)
     p.add_argument("--n-batches", type=int, default=16)
-    p.add_argument("--chunk", type=int, default=131072)
+    p.add_argument("--chunk", type=int, default=0, help="histories per iteration (0: library default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
@@ -255,6 +255,7 @@ def main():
             torch.cuda.synchronize()
             ms_steps.append(ev[i][0].elapsed_time(ev[i][1]))
             u_vals.append(u_mean_rel(d.cpu().numpy(), s.cpu().numpy()))
+    print("per-step ms: " + " ".join(f"{v:.3f}" for v in ms_steps), file=sys.stderr)
     launches = lsm.lsm_launch_count() - launches0
     timers = lsm.lsm_timing_read(reset=True)
     lsm.lsm_timing_enable(False)
@@ -320,7 +321,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl.name, "n_hist": args.n_hist, "n_batches": args.n_batches,
-                   "chunk": args.chunk, "phantom": "water 64^3 x 0.25 cm", "field_cm": 10,
+                   "chunk": args.chunk if args.chunk > 0 else min(n_plan, 1 << 20), "phantom": "water 64^3 x 0.25 cm", "field_cm": 10,
                    "sub_sources": 3, "electrons": "CSDA", "parallelism": f"replicas x{world}",
                    "l2": "flushed by a 512 MiB write before each step, outside the timed events"},
         "s_to_1pct": t1, "u_mean_rel_D50": u,

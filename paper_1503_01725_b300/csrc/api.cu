@@ -42,7 +42,6 @@ static std::vector<TimerRec> g_open;      // recorded, not yet resolved
 static std::vector<cudaEvent_t> g_pool;
 static double g_ms[LSM_N_TIMERS];
 static long long g_cnt[LSM_N_TIMERS];
-static thread_local int g_cur_which = -1;
 static thread_local long long g_cur_launch0 = 0;
 
 static cudaEvent_t ev_get()
@@ -68,7 +67,6 @@ int timer_begin(int which, cudaStream_t st)
     cudaEventRecord(r.a, st);
     g_open.push_back(r);
     g_cur_launch0 = g_launches.load();
-    g_cur_which = which;
     return (int)g_open.size() - 1;
 }
 
@@ -78,7 +76,6 @@ void timer_end(int token, cudaStream_t st)
     if (token < 0 || token >= (int)g_open.size()) return;
     cudaEventRecord(g_open[token].b, st);
     g_cnt[g_open[token].which] += g_launches.load() - g_cur_launch0;
-    g_cur_which = -1;
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -238,6 +235,7 @@ lsm_status lsm_tally_create(const lsm_phantom *ph, const lsm_tally_desc *d, lsm_
     cudaGetDevice(&t->device);
     t->mode = d->mode; t->n_rows = d->n_rows; t->n_psr = d->n_psr; t->n_beams = d->n_beams;
     t->ncell = ncell; t->nvox = nvox;
+    t->part_slots = 1;
     cudaStream_t st = S(stream);
     cudaError_t e = cudaSuccess;
     do {
@@ -290,7 +288,7 @@ lsm_status lsm_tally_reset(lsm_tally *t, lsm_stream stream)
 {
     if (!t) return set_arg_error("lsm_tally_reset: NULL tally");
     cudaStream_t st = S(stream);
-    LSM_CUDA(cudaMemsetAsync(t->d_part, 0, (size_t)t->ncell * 4, st));
+    LSM_CUDA(cudaMemsetAsync(t->d_part, 0, (size_t)t->part_slots * t->ncell * 4, st));
     LSM_CUDA(cudaMemsetAsync(t->d_batch, 0, (size_t)t->ncell * 8, st));
     LSM_CUDA(cudaMemsetAsync(t->d_s1, 0, (size_t)t->ncell * 8, st));
     LSM_CUDA(cudaMemsetAsync(t->d_s2, 0, (size_t)t->ncell * 8, st));

@@ -46,9 +46,20 @@ __device__ __forceinline__ float u01(uint32_t x)
 // A particle's random stream: counter (history lo, history hi, stream id, draw).
 struct Stream {
     uint32_t k0, k1, glo, ghi, sid, ctr;
+    uint32_t have;   // pre holds the block at counter ctr
+    uint4 pre;
     __device__ __forceinline__ uint4 next()
     {
-        return philox4x32_10(k0, k1, glo, ghi, sid, ctr++);
+        const uint4 r = have ? pre : philox4x32_10(k0, k1, glo, ghi, sid, ctr);
+        ++ctr;
+        have = 0;
+        return r;
+    }
+    // compute the block of the next draw ahead of time (same value next() returns)
+    __device__ __forceinline__ void prefetch()
+    {
+        pre = philox4x32_10(k0, k1, glo, ghi, sid, ctr);
+        have = 1;
     }
     // stream ids of particles created at the current draw position
     __device__ __forceinline__ uint4 child_ids() const
@@ -72,11 +83,15 @@ struct Queue {
 };
 
 // Counters of one sample/transport iteration (device memory, zeroed per iteration).
+constexpr int kEBins = 64;                // log-energy bins of the electron counting sort
+
 struct IterCounters {
-    uint32_t n[3];      // queue fill: 0 primary photons, 1 annihilation photons, 2 electrons
-    uint32_t head[3];   // refill cursors of the persistent transport kernels
+    uint32_t n[4];      // queue fill: 0 primary photons, 1 annihilation photons, 2 electrons,
+                        // 3 electrons sorted by descending energy
+    uint32_t head[4];   // refill cursors of the persistent transport kernels
     uint32_t overflow;  // electrons deposited in place because the queue was full
-    uint32_t pad;
+    uint32_t pad;       // table-staging timeout flag
+    uint32_t bins[kEBins];   // electron energy histogram, then bin cursors
 };
 
 // Run-long statistics and the FP64 energy ledger.

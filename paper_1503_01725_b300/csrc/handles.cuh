@@ -34,6 +34,7 @@ struct SampleParams {
 
 struct lsm_psl {
     int device;
+    void *arena;          // every device array below lives in this one allocation
     int n_e, n_r, n_xy, n_beams, per_psr;
     double dr, z_phsp, sigma_s, e_lo[3], de[3];
     double sad, z_jaw_y, z_jaw_x;
@@ -68,7 +69,8 @@ struct lsm_tally {
     int device;
     int mode, n_rows, n_psr, n_beams;
     int64_t ncell, nvox;
-    float *d_part;        // FP32 partials of the current iteration
+    float *d_part;        // FP32 partials of the current iteration, part_slots slices of ncell
+    int part_slots;
     double *d_batch;      // FP64 open batch
     double *d_s1, *d_s2;
     uint16_t *d_idx;      // basis mode

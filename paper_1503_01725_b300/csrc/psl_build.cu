@@ -48,6 +48,7 @@ __global__ void k_psl_weights(const double *__restrict__ w, int n_e, int n_r, do
     const int nxy = 2 * n_r, npsl = nxy * nxy;
     const double *W = w + (size_t)blk * n_r;
     double *out = wpsl + (size_t)blk * npsl;
+    extern __shared__ double sraw_v[];
     for (int j = threadIdx.x; j < npsl; j += blockDim.x) {
         const int iy = j / nxy, ix = j % nxy;
         const double r = psl_radius(ix, iy, n_r, dr);                    // step 1
@@ -60,6 +61,7 @@ __global__ void k_psl_weights(const double *__restrict__ w, int n_e, int n_r, do
             if (l0 < 1.0) dens += (1.0 - l0) * (W[r0 + 1] / dr);
         }
         out[j] = dens / (2.0 * kPiD * r);                               // step 3
+        sraw_v[j] = out[j];
         if (blk == 0) {
             tag_r0[j] = r0;
             tag_l0[j] = in ? l0 : 0.0;
@@ -69,7 +71,7 @@ __global__ void k_psl_weights(const double *__restrict__ w, int n_e, int n_r, do
     __shared__ double s_scale;
     if (threadIdx.x == 0) {                                              // step 4
         double sraw = 0.0, sR = 0.0;
-        for (int j = 0; j < npsl; ++j) sraw += out[j];
+        for (int j = 0; j < npsl; ++j) sraw += sraw_v[j];
         for (int R = 0; R < n_r; ++R) sR += W[R];
         s_scale = sraw > 0.0 ? sR / sraw : 0.0;
         block_scale[blk] = s_scale;
@@ -121,19 +123,24 @@ __global__ void k_incl(const double *__restrict__ area, int n_beams, int n_r, do
 
 // ------------------------------------------------ whole-source plan (Eq. 3) --
 
-// partial sum of included weights per (beam, sub-source, energy), sequential in PSL order
+// partial sum of included weights per (beam, sub-source, energy), sequential
+// in PSL order; one CTA per block stages the values through shared memory
 __global__ void k_eq3_parts(const double *__restrict__ wpsl, const uint8_t *__restrict__ incl,
                             int n_beams, int n_e, int npsl, double *__restrict__ parts)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_beams * 3 * n_e) return;
+    extern __shared__ double sv[];
+    const int i = blockIdx.x;
     const int b = i / (3 * n_e), s = (i / n_e) % 3, e = i % n_e;
     const uint8_t *inc = incl + (size_t)(b * 2 + (s ? 1 : 0)) * npsl;
     const double *W = wpsl + ((size_t)s * n_e + e) * npsl;
-    double part = 0.0;
-    for (int j = 0; j < npsl; ++j)
-        if (inc[j]) part += W[j];
-    parts[i] = part;
+    // excluded PSLs contribute +0.0, which leaves a sum of non-negative terms unchanged
+    for (int j = threadIdx.x; j < npsl; j += blockDim.x) sv[j] = inc[j] ? W[j] : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double part = 0.0;
+        for (int j = 0; j < npsl; ++j) part += sv[j];
+        parts[i] = part;
+    }
 }
 
 __global__ void k_eq3_denom(const double *__restrict__ parts, int n, double *__restrict__ denom)
@@ -175,32 +182,52 @@ __global__ void k_eq3_floor(const double *__restrict__ wpsl, const uint8_t *__re
     }
 }
 
-// rank of each remainder (descending, ties to the lower index); the `left`
-// largest get one more particle
-__global__ void k_eq3_rank(const double *__restrict__ rem, int64_t ncell, int64_t n_hist,
-                           const unsigned long long *__restrict__ floor_sum, const double *__restrict__ denom,
-                           int64_t *__restrict__ count)
+// Largest remainders: the `left` cells of highest remainder (ties to the
+// lower loop index) get one more particle. Zero remainders always rank after
+// every positive one, in index order, so only positive remainders are ranked
+// against each other; a zero cell's rank is n_pos + (zero cells before it).
+__global__ void k_pos_compact(const double *__restrict__ rem, const int64_t *__restrict__ pos_idx, int64_t ncell,
+                              double *__restrict__ posrem)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ncell && rem[i] > 0.0) posrem[pos_idx[i]] = rem[i];
+}
+
+// rank[p] += #{q : posrem[q] > posrem[p], or equal with q < p} over one tile
+// of 256 candidates p and 1024 competitors q; the grid covers all tile pairs
+__global__ void k_eq3_rank_tiles(const double *__restrict__ posrem, const int64_t *__restrict__ pos_idx,
+                                 int64_t ncell, int *__restrict__ rank)
 {
     __shared__ double tile[1024];
+    const int64_t n_pos = pos_idx[ncell];
+    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x, q0 = (int64_t)blockIdx.y * 1024;
+    if (p0 >= n_pos || q0 >= n_pos) return;
+    for (int t = threadIdx.x; t < 1024; t += blockDim.x) tile[t] = (q0 + t < n_pos) ? posrem[q0 + t] : -1.0;
+    __syncthreads();
+    const int64_t p = p0 + threadIdx.x;
+    if (p >= n_pos) return;
+    const double rp = posrem[p];
+    const int lim = (int)((n_pos - q0) < 1024 ? (n_pos - q0) : 1024);
+    int c = 0;
+    for (int t = 0; t < lim; ++t) {
+        const double rq = tile[t];
+        c += (rq > rp) || (rq == rp && q0 + t < p);
+    }
+    if (c) atomicAdd(rank + p, c);
+}
+
+__global__ void k_eq3_apply(const double *__restrict__ rem, const int64_t *__restrict__ pos_idx,
+                            const int *__restrict__ rank, int64_t ncell, int64_t n_hist,
+                            const unsigned long long *__restrict__ floor_sum, const double *__restrict__ denom,
+                            int64_t *__restrict__ count)
+{
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double ri = i < ncell ? rem[i] : -1.0;
-    int64_t rank = 0;
-    for (int64_t base = 0; base < ncell; base += 1024) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < 1024; t += blockDim.x)
-            tile[t] = (base + t < ncell) ? rem[base + t] : -2.0;
-        __syncthreads();
-        const int lim = (int)((ncell - base) < 1024 ? (ncell - base) : 1024);
-        for (int t = 0; t < lim; ++t) {
-            const double rt = tile[t];
-            rank += (rt > ri) || (rt == ri && base + t < i);
-        }
-    }
-    if (i < ncell) {
-        // an empty sampling area (denominator 0) distributes nothing
-        const int64_t left = (*denom > 0.0 ? n_hist : 0) - (int64_t)(*floor_sum);
-        if (rank < left) count[i] += 1;
-    }
+    if (i >= ncell) return;
+    const int64_t n_pos = pos_idx[ncell], pi = pos_idx[i];
+    const int64_t r = rem[i] > 0.0 ? (int64_t)rank[pi] : n_pos + (i - pi);
+    // an empty sampling area (denominator 0) distributes nothing
+    const int64_t left = (*denom > 0.0 ? n_hist : 0) - (int64_t)(*floor_sum);
+    if (r < left) count[i] += 1;
 }
 
 // ------------------------------------------------- per-PSR basis-run plans --
@@ -281,13 +308,27 @@ __global__ void k_scan(F f, int64_t n, int64_t *__restrict__ out)
     const int64_t a = (int64_t)threadIdx.x * seg, bnd = a + seg < n ? a + seg : n;
     long long s = 0;
     for (int64_t i = a; i < bnd; ++i) s += f(i);
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long run = 0;
-        for (int t = 0; t < T; ++t) { long long v = part[t]; part[t] = run; run += v; }
-        out[n] = run;
+    // exclusive block scan of the per-thread sums (T = 1024 = 32 warps)
+    __shared__ long long wsum[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
     }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = lane < (T >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long v = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += v;
+        }
+        wsum[lane] = w;                       // inclusive over warps
+        if (lane == 31) out[n] = w;
+    }
+    __syncthreads();
+    part[threadIdx.x] = incl - s + (wid ? wsum[wid - 1] : 0);
     __syncthreads();
     long long run = part[threadIdx.x];
     for (int64_t i = a; i < bnd; ++i) { out[i] = run; run += f(i); }
@@ -296,6 +337,10 @@ __global__ void k_scan(F f, int64_t n, int64_t *__restrict__ out)
 struct CountOf {
     const int64_t *c;
     __device__ long long operator()(int64_t i) const { return c[i]; }
+};
+struct Positive {
+    const double *r;
+    __device__ long long operator()(int64_t i) const { return r[i] > 0.0 ? 1 : 0; }
 };
 struct NonZero {
     const int64_t *c;
@@ -457,11 +502,48 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     const int64_t ncell = P->per_psr ? (int64_t)npsr * nb * npsl : (int64_t)nb * 3 * ne * npsl;
     P->ncell = ncell;
 
-#define ALLOC(ptr, bytes)                                        \
-    do {                                                         \
-        cudaError_t e_ = cudaMalloc((void **)&(ptr), (bytes));   \
-        if (e_ != cudaSuccess) { free_psl(P); return set_cuda_error(e_, "cudaMalloc"); } \
-    } while (0)
+    // One device allocation holds every table of the plan and the scratch of
+    // the build (released only by lsm_psl_destroy): cudaMalloc/cudaFree calls
+    // synchronise the device, so a build makes one of each.
+    const size_t nbse = (size_t)nb * 3 * ne;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+    const size_t o_in = take((nw + 4 * nm + 2 * nes + 4 * (size_t)nb + (size_t)npsr) * 8);
+    const size_t o_wpsl = take(3 * (size_t)ne * npsl * 8), o_scale = take(3 * (size_t)ne * 8);
+    const size_t o_jf = take((size_t)nb * 16), o_area = take((size_t)nb * 64), o_incl = take((size_t)nb * 2 * npsl);
+    const size_t o_count = take((size_t)ncell * 8), o_r0 = take((size_t)npsl * 4), o_l0 = take((size_t)npsl * 8);
+    const size_t o_thr = take(nes * 16), o_mix = take(nes * 3 * sizeof(float4)), o_esig = take(nes * sizeof(float2));
+    const size_t o_start = take((size_t)(ncell + 1) * 8), o_ent = take((size_t)ncell * sizeof(EntryRec));
+    const size_t o_esc = take((size_t)ncell * 8);
+    const size_t o_rem = take((size_t)ncell * 8), o_cst = take((size_t)(ncell + 1) * 8);
+    const size_t o_eidx = take((size_t)(ncell + 1) * 8), o_parts = take(nbse * 8);
+    const size_t o_res = take(64), o_dkb = take((size_t)npsr * nb * 8), o_rank = take((size_t)ncell * 4);
+    char *base = nullptr;
+    {
+        cudaError_t e_ = cudaMalloc((void **)&base, off);
+        if (e_ != cudaSuccess) { free_psl(P); return set_cuda_error(e_, "lsm_build_psl: cudaMalloc"); }
+    }
+    P->arena = base;
+    double *d_in = (double *)(base + o_in);
+    P->d_w = d_in;
+    double *d_mc = d_in + nw, *d_mmu = d_mc + nm, *d_msa = d_mmu + nm, *d_msb = d_msa + nm;
+    double *d_esa = d_msb + nm, *d_esb = d_esa + nes;
+    P->d_jaws = d_esb + nes;
+    int64_t *d_nk = (int64_t *)(P->d_jaws + 4 * nb);
+    P->d_wpsl = (double *)(base + o_wpsl); P->d_scale = (double *)(base + o_scale);
+    P->d_jaws_f = (float *)(base + o_jf); P->d_area = (double *)(base + o_area); P->d_incl = (uint8_t *)(base + o_incl);
+    P->d_count = (int64_t *)(base + o_count); P->d_tag_r0 = (int32_t *)(base + o_r0); P->d_tag_l0 = (double *)(base + o_l0);
+    P->d_mixthr = (unsigned long long *)(base + o_thr); P->d_mix = (float4 *)(base + o_mix);
+    P->d_esig = (float2 *)(base + o_esig);
+    P->d_start = (int64_t *)(base + o_start); P->d_ent = (EntryRec *)(base + o_ent); P->d_escale = (double *)(base + o_esc);
+    double *d_rem = (double *)(base + o_rem);
+    int64_t *d_cstart = (int64_t *)(base + o_cst), *d_eidx = (int64_t *)(base + o_eidx);
+    double *d_parts = (double *)(base + o_parts);
+    double *d_denom = (double *)(base + o_res);
+    unsigned long long *d_fsum = (unsigned long long *)(base + o_res + 8);
+    double *d_dkb = (double *)(base + o_dkb);
+    int *d_rank = (int *)(base + o_rank);
+
 #define CK(call)                                                 \
     do {                                                         \
         cudaError_t e_ = (call);                                 \
@@ -474,71 +556,27 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
         if (e_ != cudaSuccess) { free_psl(P); return set_cuda_error(e_, where); } \
     } while (0)
 
-    // model arrays: one staging buffer
-    double *d_mc, *d_mmu, *d_msa, *d_msb, *d_esa, *d_esb, *d_tmp;
-    int64_t *d_nk = nullptr, *d_cstart, *d_eidx;
-    double *d_rem, *d_parts, *d_denom, *d_dkb = nullptr;
-    unsigned long long *d_fsum;
-    ALLOC(P->d_w, nw * 8);
-    ALLOC(P->d_wpsl, 3 * (size_t)ne * npsl * 8);
-    ALLOC(P->d_scale, 3 * (size_t)ne * 8);
-    ALLOC(P->d_jaws, (size_t)nb * 4 * 8);
-    ALLOC(P->d_jaws_f, (size_t)nb * 4 * 4);
-    ALLOC(P->d_area, (size_t)nb * 8 * 8);
-    ALLOC(P->d_incl, (size_t)nb * 2 * npsl);
-    ALLOC(P->d_count, (size_t)ncell * 8);
-    ALLOC(P->d_tag_r0, (size_t)npsl * 4);
-    ALLOC(P->d_tag_l0, (size_t)npsl * 8);
-    ALLOC(P->d_mixthr, nes * 2 * 8);
-    ALLOC(P->d_mix, nes * 3 * sizeof(float4));
-    ALLOC(P->d_esig, nes * sizeof(float2));
-    ALLOC(d_tmp, (4 * nm + 2 * nes) * 8 + 64);
-    d_mc = d_tmp; d_mmu = d_mc + nm; d_msa = d_mmu + nm; d_msb = d_msa + nm; d_esa = d_msb + nm; d_esb = d_esa + nes;
-    // scratch of the integerisation
-    const size_t scratch = (size_t)ncell * 8 * 3 + 16 * 8 + (size_t)nb * 3 * ne * 8 + 64 + (size_t)npsr * nb * 8 +
-                           (size_t)npsr * 8;
-    char *d_scr;
-    cudaError_t ea = cudaMalloc((void **)&d_scr, scratch);
-    if (ea != cudaSuccess) { cudaFree(d_tmp); free_psl(P); return set_cuda_error(ea, "cudaMalloc"); }
-    d_rem = (double *)d_scr;
-    d_cstart = (int64_t *)(d_scr + (size_t)ncell * 8);
-    d_eidx = (int64_t *)(d_scr + (size_t)ncell * 16 + 8);
-    char *tail = d_scr + (size_t)ncell * 24 + 16 * 8;
-    d_parts = (double *)tail; tail += (size_t)nb * 3 * ne * 8;
-    d_denom = (double *)tail; tail += 8;
-    d_fsum = (unsigned long long *)tail; tail += 8;
-    tail += 48;
-    d_dkb = (double *)tail; tail += (size_t)npsr * nb * 8;
-    d_nk = (int64_t *)tail;
+    // host inputs packed into one copy
+    std::vector<double> hin(nw + 4 * nm + 2 * nes + 4 * (size_t)nb + (size_t)npsr, 0.0);
+    {
+        double *h = hin.data();
+        memcpy(h, M->w, nw * 8); h += nw;
+        memcpy(h, M->mix_c, nm * 8); h += nm;
+        memcpy(h, M->mix_mu, nm * 8); h += nm;
+        memcpy(h, M->mix_sa, nm * 8); h += nm;
+        memcpy(h, M->mix_sb, nm * 8); h += nm;
+        memcpy(h, M->e_sa, nes * 8); h += nes;
+        memcpy(h, M->e_sb, nes * 8); h += nes;
+        memcpy(h, B->jaws, (size_t)nb * 32); h += 4 * nb;
+        if (per_psr_hist) memcpy(h, per_psr_hist, (size_t)npsr * 8);
+    }
+    CK(cudaMemcpyAsync(d_in, hin.data(), hin.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d_denom, 0, 64, st));
 
-    auto cleanup = [&]() { cudaFree(d_tmp); cudaFree(d_scr); };
-#undef CK
-#define CK(call)                                                 \
-    do {                                                         \
-        cudaError_t e_ = (call);                                 \
-        if (e_ != cudaSuccess) { cleanup(); free_psl(P); return set_cuda_error(e_, #call); } \
-    } while (0)
-#undef CKL
-#define CKL(where)                                               \
-    do {                                                         \
-        count_launch();                                          \
-        cudaError_t e_ = cudaGetLastError();                     \
-        if (e_ != cudaSuccess) { cleanup(); free_psl(P); return set_cuda_error(e_, where); } \
-    } while (0)
-
-    CK(cudaMemcpyAsync(P->d_w, M->w, nw * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(P->d_jaws, B->jaws, (size_t)nb * 32, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_mc, M->mix_c, nm * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_mmu, M->mix_mu, nm * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_msa, M->mix_sa, nm * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_msb, M->mix_sb, nm * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_esa, M->e_sa, nes * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_esb, M->e_sb, nes * 8, cudaMemcpyHostToDevice, st));
-    if (per_psr_hist) CK(cudaMemcpyAsync(d_nk, per_psr_hist, (size_t)npsr * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(d_fsum, 0, 8, st));
-
-    k_psl_weights<<<3 * ne, 256, 0, st>>>(P->d_w, ne, nr, M->dr, P->d_wpsl, P->d_scale, P->d_tag_r0,
-                                          P->d_tag_l0);
+    if ((size_t)npsl * 8 > 48 * 1024)
+        CK(cudaFuncSetAttribute(k_psl_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, npsl * 8));
+    k_psl_weights<<<3 * ne, 256, (size_t)npsl * 8, st>>>(P->d_w, ne, nr, M->dr, P->d_wpsl, P->d_scale,
+                                                         P->d_tag_r0, P->d_tag_l0);
     CKL("k_psl_weights");
     k_areas<<<1, 32, 0, st>>>(P->d_jaws, nb, M->z_phsp, B->sad, B->z_jaw_x, B->z_jaw_y, P->d_area, P->d_jaws_f);
     CKL("k_areas");
@@ -552,52 +590,61 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     CKL("k_dir_tables");
 
     if (!per_psr_hist) {
-        const int nbse = nb * 3 * ne;
-        k_eq3_parts<<<(nbse + 63) / 64, 64, 0, st>>>(P->d_wpsl, P->d_incl, nb, ne, npsl, d_parts);
+        const int nb3 = (int)nbse;
+        if ((size_t)npsl * 8 > 48 * 1024)
+            CK(cudaFuncSetAttribute(k_eq3_parts, cudaFuncAttributeMaxDynamicSharedMemorySize, npsl * 8));
+        k_eq3_parts<<<nb3, 256, (size_t)npsl * 8, st>>>(P->d_wpsl, P->d_incl, nb, ne, npsl, d_parts);
         CKL("k_eq3_parts");
-        k_eq3_denom<<<1, 1, 0, st>>>(d_parts, nbse, d_denom);
+        k_eq3_denom<<<1, 1, 0, st>>>(d_parts, nb3, d_denom);
         CKL("k_eq3_denom");
         const unsigned g = (unsigned)((ncell + 255) / 256);
         k_eq3_floor<<<g, 256, 0, st>>>(P->d_wpsl, P->d_incl, ne, npsl, ncell, n_hist, d_denom, P->d_count,
                                        d_rem, d_fsum);
         CKL("k_eq3_floor");
-        k_eq3_rank<<<g, 256, 0, st>>>(d_rem, ncell, n_hist, d_fsum, d_denom, P->d_count);
-        CKL("k_eq3_rank");
-        CK(cudaMemcpyAsync(&P->denom, d_denom, 8, cudaMemcpyDeviceToHost, st));
+        // d_cstart / d_eidx serve as scratch here; they are recomputed below
+        k_scan<<<1, 1024, 0, st>>>(Positive{d_rem}, ncell, d_cstart);
+        CKL("k_scan");
+        k_pos_compact<<<g, 256, 0, st>>>(d_rem, d_cstart, ncell, (double *)d_eidx);
+        CKL("k_pos_compact");
+        CK(cudaMemsetAsync(d_rank, 0, (size_t)ncell * 4, st));
+        k_eq3_rank_tiles<<<dim3(g, (unsigned)((ncell + 1023) / 1024)), 256, 0, st>>>((const double *)d_eidx, d_cstart,
+                                                                                    ncell, d_rank);
+        CKL("k_eq3_rank_tiles");
+        k_eq3_apply<<<g, 256, 0, st>>>(d_rem, d_cstart, d_rank, ncell, n_hist, d_fsum, d_denom, P->d_count);
+        CKL("k_eq3_apply");
     } else {
         const size_t smem = (size_t)npsl * 24;
         if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_psr_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_psr_counts<<<npsr * nb, 256, smem, st>>>(P->d_w, P->d_scale, P->d_incl, d_nk, ne, nr, M->dr, nb,
                                                    P->d_count, d_dkb);
         CKL("k_psr_counts");
-        P->denom = 0.0;
     }
     k_scan<<<1, 1024, 0, st>>>(CountOf{P->d_count}, ncell, d_cstart);
     CKL("k_scan");
     k_scan<<<1, 1024, 0, st>>>(NonZero{P->d_count}, ncell, d_eidx);
     CKL("k_scan");
-    int64_t n_ent = 0, total = 0;
-    CK(cudaMemcpyAsync(&n_ent, d_eidx + ncell, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&total, d_cstart + ncell, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (n_ent < 1 || total < 1) {
-        cleanup(); free_psl(P);
-        return set_arg_error("lsm_build_psl: the sampling areas hold no PSL with non-zero weight");
-    }
-    if (n_ent >= (int64_t)1 << 31) { cleanup(); free_psl(P); return set_arg_error("lsm_build_psl: plan too large"); }
-    P->n_ent = n_ent;
-    P->plan_size = total;
-    ALLOC(P->d_start, (size_t)(n_ent + 1) * 8);
-    ALLOC(P->d_ent, (size_t)n_ent * sizeof(EntryRec));
-    ALLOC(P->d_escale, (size_t)n_ent * 8);
     k_entries<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(P->d_count, d_cstart, d_eidx, ncell, P->per_psr, nb, ne,
                                                               nr, P->d_w, P->d_tag_r0, P->d_tag_l0, d_dkb, d_nk,
                                                               P->d_start, P->d_ent, P->d_escale);
     CKL("k_entries");
     k_entries_end<<<1, 1, 0, st>>>(d_cstart, ncell, d_eidx, P->d_start);
     CKL("k_entries_end");
+    // the host needs the plan size and the denominator: one read, one synchronisation
+    int64_t res[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(&res[0], d_denom, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&res[1], d_eidx + ncell, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&res[2], d_cstart + ncell, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    cleanup();
+    const int64_t n_ent = res[1], total = res[2];
+    if (n_ent < 1 || total < 1) {
+        free_psl(P);
+        return set_arg_error("lsm_build_psl: the sampling areas hold no PSL with non-zero weight");
+    }
+    if (n_ent >= (int64_t)1 << 31) { free_psl(P); return set_arg_error("lsm_build_psl: plan too large"); }
+    memcpy(&P->denom, &res[0], 8);
+    if (per_psr_hist) P->denom = 0.0;
+    P->n_ent = n_ent;
+    P->plan_size = total;
 
     SampleParams &sp = P->sp;
     sp.start = P->d_start; sp.ent = P->d_ent; sp.mixthr = P->d_mixthr; sp.mix = P->d_mix; sp.esig = P->d_esig;
@@ -608,7 +655,6 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     sp.zx_rel = (float)(B->z_jaw_x - M->z_phsp);
     *out = P;
     return LSM_OK;
-#undef ALLOC
 #undef CK
 #undef CKL
 }
@@ -616,11 +662,7 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
 lsm_status free_psl(lsm_psl *P)
 {
     if (!P) return LSM_OK;
-    void *ptrs[] = {P->d_w, P->d_wpsl, P->d_scale, P->d_jaws, P->d_area, P->d_escale, P->d_incl,
-                    P->d_count, P->d_start, P->d_ent, P->d_mixthr, P->d_mix, P->d_esig, P->d_jaws_f,
-                    P->d_tag_r0, P->d_tag_l0};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    if (P->arena) cudaFree(P->arena);
     free(P);
     return LSM_OK;
 }

@@ -40,8 +40,9 @@ struct TP {
     const float4 *xs;
     const float *mumax;
     float inv_dlnE, maj;
-    // tally
+    // tally: FP32 partials, one slice of `ncell` cells per batch slot
     float *part;
+    int64_t ncell;
     const uint16_t *idx;
     int n_rows, n_psr, n_beams;
     // run
@@ -118,6 +119,16 @@ __device__ __forceinline__ int voxel(const TP &T, float x, float y, float z)
     return (iz * T.ny + iy) * T.nx + ix;
 }
 
+// A particle's tag word: PSR index (bits 0-15), beam (16-19), batch slot of
+// the iteration (20-27). Secondaries inherit it.
+__device__ __forceinline__ uint32_t pb_psr(uint32_t pb) { return pb & 0xFFFFu; }
+__device__ __forceinline__ uint32_t pb_beam(uint32_t pb) { return (pb >> 16) & 0xFu; }
+__device__ __forceinline__ uint32_t pb_slot(uint32_t pb) { return (pb >> 20) & 0xFFu; }
+__host__ __device__ __forceinline__ uint32_t pb_make(uint32_t psr, uint32_t beam, uint32_t slot)
+{
+    return psr | (beam << 16) | (slot << 20);
+}
+
 struct Acc {
     double esc, dep;
     unsigned long long flights, real, esteps, cap;
@@ -127,15 +138,16 @@ template <int MODE>
 __device__ __forceinline__ void deposit(const TP &T, Acc &A, int vox, float e, uint32_t pb)
 {
     A.dep += e;
+    float *slice = T.part + (size_t)pb_slot(pb) * T.ncell;
     if (MODE == 0) {
-        atomicAdd(T.part + vox, e);
+        atomicAdd(slice + vox, e);
     } else {
         // rows, PSRs and beams are checked so that caller-supplied particles
         // or index arrays can never write outside the basis tally
         const int row = T.idx[vox];
-        const uint32_t beam = pb >> 16, k = pb & 0xFFFFu;
+        const uint32_t beam = pb_beam(pb), k = pb_psr(pb);
         if (row && row <= T.n_rows && k < (uint32_t)T.n_psr && beam < (uint32_t)T.n_beams)
-            atomicAdd(T.part + ((size_t)beam * T.n_rows + (row - 1)) * T.n_psr + k, e);
+            atomicAdd(slice + ((size_t)beam * T.n_rows + (row - 1)) * T.n_psr + k, e);
     }
 }
 
@@ -165,6 +177,8 @@ struct Part {
     Stream rng;
     uint32_t pb;
     int steps;
+    int vc;        // voxel whose (sign-coded) density is held in rc, -1 if none
+    float rc;
 };
 
 __device__ __forceinline__ void load_part(const Queue &q, uint32_t i, uint32_t k0, uint32_t k1, Part &p)
@@ -175,6 +189,9 @@ __device__ __forceinline__ void load_part(const Queue &q, uint32_t i, uint32_t k
     p.rng.glo = q.glo[i]; p.rng.ghi = q.ghi[i]; p.rng.sid = q.sid[i]; p.rng.ctr = 0;
     p.pb = q.pb[i];
     p.steps = 0;
+    p.vc = -1;
+    p.rc = 0.0f;
+    p.rng.have = 0;
 }
 
 __device__ __forceinline__ void store_part(const Queue &q, uint32_t i, float x, float y, float z, float u,
@@ -231,8 +248,11 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
     A.flights++;
     vox = voxel(T, p.x, p.y, p.z);
+    const float rm = vox >= 0 ? __ldg(T.rhomat + vox) : 0.0f;
+    // the block of the next draw (next flight or first Kahn trial) does not
+    // depend on the density: compute it while the load is in flight
+    p.rng.prefetch();
     if (vox < 0) { A.esc += p.E; return false; }
-    const float rm = __ldg(T.rhomat + vox);
     const int m = rm < 0.0f;
     const float rho = fabsf(rm);
     const float4 c = lerp4(xs + m * kGrid, ti, tf);
@@ -312,7 +332,9 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
     if (vox < 0) { A.esc += p.E; return false; }
     if (p.E < kCutE) { deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
     if (++p.steps > T.max_steps) { A.cap++; deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
-    const float rm = __ldg(T.rhomat + vox);
+    // an electron takes about two steps per voxel: reuse the density loaded
+    // for this voxel at the end of the previous step
+    const float rm = vox == p.vc ? p.rc : __ldg(T.rhomat + vox);
     const int m = rm < 0.0f;
     const float rho = fabsf(rm);
     int ti;
@@ -333,6 +355,11 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
     const float E0 = p.E;
     p.x += ds * p.u; p.y += ds * p.v; p.z += ds * p.w;
     p.E -= dE;
+    // issue the next voxel's density load now, so that it is in flight while
+    // the deflection below is computed
+    const int vn = voxel(T, p.x, p.y, p.z);
+    p.rc = vn == vox ? rm : (vn >= 0 ? __ldg(T.rhomat + vn) : 0.0f);
+    p.vc = vn;
     if (p.E >= kCutE) {
         const uint4 r = p.rng.next();
         const float t = rho * ds * (m ? (1.0f / 21.68f) : (1.0f / 36.08f));
@@ -363,35 +390,62 @@ __device__ void flush_acc(const TP &T, const Acc &A)
 // Persistent transport kernel with per-lane refill from queue `qi`.
 // KIND 0: photons (Woodcock), KIND 1: electrons (CSDA).
 template <int MODE, int KIND>
-__global__ void __launch_bounds__(256) k_transport(TP T, Queue in, int qi, Queue eq, Queue pq, int has_pq)
+__global__ void __launch_bounds__(256, KIND ? 6 : 4) k_transport(TP T, Queue in, int qi, Queue eq, Queue pq, int has_pq)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
+    const uint32_t n_q = *(volatile uint32_t *)&T.cnt->n[qi];
+    const uint32_t n_in = n_q < in.cap ? n_q : in.cap;     // pushes beyond capacity were not stored
+    // blocks whose first slot lies past the queue end have nothing to refill
+    // from once the earlier blocks start: leave before staging the tables
+    if ((uint64_t)blockIdx.x * blockDim.x >= n_in) return;
     float4 *s_xs = reinterpret_cast<float4 *>(smem);
     float *s_mm = reinterpret_cast<float *>(smem + 2 * kGrid * 16);
     const bool staged = stage_tables(s_xs, T.xs, T.mumax, &mbar, &T.cnt->pad);
     const float4 *xs = staged ? s_xs : T.xs;
     const float *mm = staged ? s_mm : T.mumax;
-
-    const uint32_t n_q = *(volatile uint32_t *)&T.cnt->n[qi];
-    const uint32_t n_in = n_q < in.cap ? n_q : in.cap;     // pushes beyond capacity were not stored
     uint32_t *head = &T.cnt->head[qi];
     const unsigned lane = lane_id();
     unsigned lt;
     lanemask_lt(lt);
     Acc A = {0.0, 0.0, 0ull, 0ull, 0ull, 0ull};
     Part p;
-    bool alive = false, drained = false;
+    bool alive = false;
+    // Each warp reserves kGrab consecutive queue slots per atomic and hands
+    // them to its lanes as they fall idle; [rb, rb + rl) is the unused part
+    // of the reservation (warp-uniform). Slots are handed out in queue order,
+    // so once a handed-out slot lies past the end, every later one does too.
+    constexpr uint32_t kGrab = 32;
+    uint32_t rb = 0, rl = 0;
+    bool exhausted = false;
     for (;;) {
         const unsigned need = __ballot_sync(0xffffffffu, !alive);
-        if (need && !drained) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(head, (uint32_t)__popc(need));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (base + (uint32_t)__popc(need) >= n_in) drained = true;
+        const uint32_t k = (uint32_t)__popc(need);
+        if (k && (rl > 0 || !exhausted)) {
+            uint32_t nb = 0;
+            bool grabbed = false;
+            if (rl < k && !exhausted) {
+                if (lane == 0) {
+                    // read before the atomic: once the queue is exhausted, warps stop hammering its cursor
+                    const uint32_t h = *(volatile uint32_t *)head;
+                    nb = h >= n_in ? n_in : atomicAdd(head, kGrab);
+                }
+                nb = __shfl_sync(0xffffffffu, nb, 0);
+                grabbed = true;
+                if (nb + kGrab >= n_in) exhausted = true;
+            }
             if (!alive) {
-                const uint32_t i = base + (uint32_t)__popc(need & lt);
+                const uint32_t r = (uint32_t)__popc(need & lt);
+                const uint32_t i = r < rl ? rb + r : (grabbed ? nb + (r - rl) : 0xffffffffu);
                 if (i < n_in) { load_part(in, i, T.k0, T.k1, p); alive = true; }
+            }
+            if (grabbed) {
+                const uint32_t from_new = k - rl;
+                rb = nb + from_new;
+                rl = kGrab - from_new;
+            } else {
+                rb += k;
+                rl -= k;
             }
         }
         if (!__any_sync(0xffffffffu, alive)) break;
@@ -408,8 +462,9 @@ __global__ void __launch_bounds__(256) k_transport(TP T, Queue in, int qi, Queue
 struct SQ {
     SampleParams sp;
     uint32_t k0, k1;
-    uint64_t g0;
-    int64_t h0, n;
+    uint64_t g0;            // history of the iteration's first particle
+    int64_t h0, n;          // its plan position; histories in the iteration
+    int64_t plan;           // plan size: position h0 + i lies in batch slot (h0 + i) / plan
     float z_rel;            // phantom surface - z_phsp
     float x0, y0;           // phantom corner on the surface plane
 };
@@ -430,10 +485,13 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
         const bool valid = i < S.n;
         SrcParticle o;
         o.stype = 0;
+        uint32_t slot = 0;
         bool in = false;
         float lx = 0.0f, ly = 0.0f;
         if (valid) {
-            sample_history(S.sp, S.k0, S.k1, S.g0 + (uint64_t)i, S.h0 + i, S.z_rel, o);
+            const int64_t hh = S.h0 + i;
+            slot = (uint32_t)(hh / S.plan);
+            sample_history(S.sp, S.k0, S.k1, S.g0 + (uint64_t)i, hh - (int64_t)slot * S.plan, S.z_rel, o);
             src += o.E;
             if (!o.accepted) { rej += o.E; nrej++; }
             else {
@@ -455,7 +513,7 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
         be = __shfl_sync(0xffffffffu, be, 0);
         if (in) {
             const uint64_t g = S.g0 + (uint64_t)i;
-            const uint32_t pb = (uint32_t)o.psr | ((uint32_t)o.beam << 16);
+            const uint32_t pb = pb_make((uint32_t)o.psr, (uint32_t)o.beam, slot);
             if (!is_e) {
                 nph++;
                 store_part(pq, bp + __popc(mp & lt), lx, ly, 0.0f, o.u, o.v, o.w, o.E, (uint32_t)g,
@@ -549,7 +607,7 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
         be = __shfl_sync(0xffffffffu, be, 0);
         if (inside) {
             const uint64_t g = P.hist[i];
-            const uint32_t pb = (uint32_t)P.psr[i] | ((uint32_t)P.beam[i] << 16);
+            const uint32_t pb = pb_make((uint32_t)P.psr[i], (uint32_t)P.beam[i] & 0xFu, 0u);
             if (!is_e) {
                 nph++;
                 store_part(pq, bp + __popc(mp & lt), lx, ly, lz, P.u[i], P.v[i], P.w[i], P.E[i], (uint32_t)g,
@@ -599,6 +657,28 @@ __global__ void k_flush(float *__restrict__ part, double *__restrict__ batch, in
     }
 }
 
+// Iterations that hold k whole batches: fold each FP32 batch slice straight
+// into the running sums and clear it.
+__global__ void k_fold_slots(float *__restrict__ part, double *__restrict__ s1, double *__restrict__ s2,
+                             int64_t ncell, int k)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride) {
+        double a1 = 0.0, a2 = 0.0;
+        bool any = false;
+        for (int q = 0; q < k; ++q) {
+            const float v = part[(size_t)q * ncell + c];
+            if (v != 0.0f) {
+                a1 += v;
+                a2 += (double)v * (double)v;
+                part[(size_t)q * ncell + c] = 0.0f;
+                any = true;
+            }
+        }
+        if (any) { s1[c] += a1; s2[c] += a2; }
+    }
+}
+
 __global__ void k_fold(double *__restrict__ batch, double *__restrict__ s1, double *__restrict__ s2, int64_t n)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -612,6 +692,63 @@ __global__ void k_fold(double *__restrict__ batch, double *__restrict__ s1, doub
     }
 }
 
+
+// --------------------------------------------- electron energy regrouping ---
+// Counting sort of the electron queue by descending energy (64 log bins over
+// 0.2-7 MeV): the persistent electron kernel hands out queue slots in order,
+// so long tracks start first and the end of the launch is made of short ones,
+// and neighbouring lanes hold electrons of similar energy.
+
+__device__ __forceinline__ int ebin_key(float E)
+{
+    const float t = (__logf(E) - (-1.6094379f)) * ((float)kEBins / 3.5553481f);   // ln 0.2, ln(7/0.2)
+    const int b = (int)fminf(fmaxf(t, 0.0f), (float)(kEBins - 1));
+    return kEBins - 1 - b;
+}
+
+__global__ void k_ebin_count(Queue e, IterCounters *cnt)
+{
+    __shared__ uint32_t h[kEBins];
+    for (int i = threadIdx.x; i < kEBins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint32_t n = min(*(volatile uint32_t *)&cnt->n[2], e.cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&h[ebin_key(e.E[i])], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kEBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&cnt->bins[i], h[i]);
+}
+
+__global__ void k_ebin_scan(IterCounters *cnt)
+{
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int i = 0; i < kEBins; ++i) { const uint32_t v = cnt->bins[i]; cnt->bins[i] = run; run += v; }
+        cnt->n[3] = run;
+    }
+}
+
+__global__ void k_ebin_scatter(Queue e, Queue o, IterCounters *cnt)
+{
+    const uint32_t n = min(*(volatile uint32_t *)&cnt->n[2], e.cap);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const uint32_t i = base + threadIdx.x;
+        if (i >= n) break;
+        const int key = ebin_key(e.E[i]);
+        // one cursor update per group of lanes sharing a bin
+        const unsigned grp = __match_any_sync(__activemask(), key);
+        const int leader = __ffs(grp) - 1;
+        uint32_t slot = 0;
+        if ((int)lane_id() == leader) slot = atomicAdd(&cnt->bins[key], (uint32_t)__popc(grp));
+        slot = __shfl_sync(grp, slot, leader);
+        unsigned lt;
+        lanemask_lt(lt);
+        slot += __popc(grp & lt);
+        store_part(o, slot, e.x[i], e.y[i], e.z[i], e.u[i], e.v[i], e.w[i], e.E[i], e.glo[i], e.ghi[i], e.sid[i],
+                   e.pb[i]);
+    }
+}
 
 // ---------------------------------------------------------- normalisation ---
 
@@ -683,7 +820,7 @@ int grid_for(const void *fn, int threads, size_t smem)
 }
 
 struct Workspace {
-    Queue q[3];          // 0 primary photons, 1 annihilation photons, 2 electrons
+    Queue q[4];          // 0 primary photons, 1 annihilation photons, 2 electrons, 3 sorted electrons
     IterCounters *cnt;
     void *mem;
 };
@@ -697,20 +834,20 @@ cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t)
     } else {
         if (t->ws) cudaFree(t->ws);
         t->ws = nullptr;
-        size_t total = 256;
-        const uint32_t c2[3] = {chunk, 2 * chunk, ecap};
-        for (int k = 0; k < 3; ++k) total += (size_t)c2[k] * 44 + 11 * 256;
+        size_t total = 1024;
+        const uint32_t c2[4] = {chunk, 2 * chunk, ecap, ecap};
+        for (int k = 0; k < 4; ++k) total += (size_t)c2[k] * 44 + 11 * 256;
         cudaError_t e = cudaMalloc(&t->ws, total);
         if (e != cudaSuccess) return e;
         t->ws_chunk = chunk;
         t->ws_ecap = ecap;
     }
-    const uint32_t caps[3] = {chunk, 2 * chunk, ecap};
+    const uint32_t caps[4] = {chunk, 2 * chunk, ecap, ecap};
     char *p = (char *)t->ws;
     W.mem = nullptr;
     W.cnt = (IterCounters *)p;
-    p += 256;
-    for (int k = 0; k < 3; ++k) {
+    p += 1024;
+    for (int k = 0; k < 4; ++k) {
         Queue &q = W.q[k];
         q.cap = caps[k];
         float **f[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
@@ -732,6 +869,7 @@ TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, uin
     T.inv_dlnE = (float)((kGrid - 1) / (kLnEmax - kLnEmin));
     T.maj = (float)o.majorant_factor;
     T.part = t->d_part;
+    T.ncell = t->ncell;
     T.idx = t->mode == 1 ? t->d_idx : nullptr;
     T.n_rows = t->n_rows; T.n_psr = t->n_psr; T.n_beams = t->n_beams;
     T.electron_mode = o.electron_mode;
@@ -751,7 +889,7 @@ lsm_status check_opts(lsm_run_opts &o)
     if (!(o.majorant_factor >= 1.0) || !isfinite(o.majorant_factor)) return set_arg_error("majorant_factor must be >= 1");
     if (!(o.f_e > 0.0 && o.f_e <= 1.0)) return set_arg_error("f_e must be in (0, 1]");
     if (o.max_steps < 1) return set_arg_error("max_steps must be >= 1");
-    if (o.chunk <= 0) o.chunk = 131072;
+    if (o.chunk <= 0) o.chunk = 1 << 23;
     if (o.chunk > (1 << 24)) return set_arg_error("chunk must be <= 2^24");
     if (o.n_batches < 1) o.n_batches = 1;
     return LSM_OK;
@@ -782,16 +920,17 @@ lsm_status drain(const TP &T, Workspace &W, lsm_tally *t, cudaStream_t st)
     timer_end(tk, st);
     if (T.electron_mode) {
         tk = timer_begin(4, st);
-        k_transport<MODE, 1><<<ge, 256, smem, st>>>(T, W.q[2], 2, W.q[2], W.q[1], 0);
+        const int gsrt = 2 * sm_count();
+        k_ebin_count<<<gsrt, 512, 0, st>>>(W.q[2], W.cnt);
+        LSM_LAUNCHED("k_ebin_count");
+        k_ebin_scan<<<1, 32, 0, st>>>(W.cnt);
+        LSM_LAUNCHED("k_ebin_scan");
+        k_ebin_scatter<<<gsrt * 4, 256, 0, st>>>(W.q[2], W.q[3], W.cnt);
+        LSM_LAUNCHED("k_ebin_scatter");
+        k_transport<MODE, 1><<<ge, 256, smem, st>>>(T, W.q[3], 3, W.q[2], W.q[1], 0);
         LSM_LAUNCHED("k_transport<electron>");
         timer_end(tk, st);
     }
-    const int64_t n = t->ncell;
-    const int gf = (int)std::min<int64_t>((n / 4 + 255) / 256 + 1, 8 * sm_count());
-    tk = timer_begin(5, st);
-    k_flush<<<gf, 256, 0, st>>>(t->d_part, t->d_batch, n);
-    LSM_LAUNCHED("k_flush");
-    timer_end(tk, st);
     return LSM_OK;
 }
 
@@ -822,8 +961,41 @@ lsm_status flush_partials(lsm_tally *t, cudaStream_t st)
 {
     const int64_t n = t->ncell;
     const int gf = (int)std::min<int64_t>((n / 4 + 255) / 256 + 1, 8 * sm_count());
+    const int tk = timer_begin(5, st);
     k_flush<<<gf, 256, 0, st>>>(t->d_part, t->d_batch, n);
-    LSM_LAUNCHED("k_flush");
+    count_launch();
+    timer_end(tk, st);
+    LSM_CUDA(cudaGetLastError());
+    return LSM_OK;
+}
+
+// fold k whole-batch slices of the partial tally into S1/S2
+lsm_status fold_slots(lsm_tally *t, int k, cudaStream_t st)
+{
+    const int64_t n = t->ncell;
+    const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
+    const int tk = timer_begin(5, st);
+    k_fold_slots<<<g, 256, 0, st>>>(t->d_part, t->d_s1, t->d_s2, n, k);
+    count_launch();
+    timer_end(tk, st);
+    LSM_CUDA(cudaGetLastError());
+    t->n_batches += k;
+    return LSM_OK;
+}
+
+// make room for `slots` partial-tally slices (pending slot-0 partials are flushed first)
+lsm_status ensure_slots(lsm_tally *t, int slots, cudaStream_t st)
+{
+    if (slots <= t->part_slots) return LSM_OK;
+    lsm_status rc = flush_partials(t, st);
+    if (rc) return rc;
+    LSM_CUDA(cudaStreamSynchronize(st));
+    float *np = nullptr;
+    LSM_CUDA(cudaMalloc(&np, (size_t)slots * t->ncell * 4 + 16));
+    LSM_CUDA(cudaMemsetAsync(np, 0, (size_t)slots * t->ncell * 4, st));
+    cudaFree(t->d_part);
+    t->d_part = np;
+    t->part_slots = slots;
     return LSM_OK;
 }
 
@@ -873,6 +1045,8 @@ lsm_status transport_particles(const lsm_phantom *ph, const lsm_particles *in, i
         if ((e = cudaGetLastError()) != cudaSuccess) { rc = set_cuda_error(e, "k_enqueue"); break; }
         rc = t->mode == 0 ? drain<0>(T, W, t, st) : drain<1>(T, W, t, st);
         if (rc) break;
+        rc = flush_partials(t, st);
+        if (rc) break;
         rc = read_overflow(t, st, &ovf);
     } while (0);
     if (rc) return rc;
@@ -890,12 +1064,24 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     if (t->nvox != (int64_t)ph->nx * ph->ny * ph->nz) return set_arg_error("lsm_run: tally of another phantom");
     if (t->mode == 1 && (t->n_beams != P->n_beams || t->n_psr != 3 * P->n_e * P->n_r))
         return set_arg_error("lsm_run: basis tally shape does not match the plan");
-    const uint32_t chunk = (uint32_t)std::min<int64_t>(o.chunk, P->plan_size);
+    // Iteration size. The paper iterates M histories at a time (Sec. 2.1.3);
+    // B300 keeps ~2e5 lanes resident, so an iteration should hold millions of
+    // histories for its longest tracks not to dominate. Plans smaller than
+    // the iteration size are run k whole batches per iteration, each batch in
+    // its own slice of the partial tally; larger plans are split into
+    // iterations inside one batch.
+    const int64_t plan = P->plan_size;
+    const bool multi = plan < (int64_t)o.chunk;
+    const int bpi = multi ? (int)std::min<int64_t>(o.n_batches, (int64_t)o.chunk / plan) : 1;
+    const int64_t chunk = multi ? (int64_t)bpi * plan : (int64_t)o.chunk;
+    if (bpi > 255) return set_arg_error("lsm_run: more than 255 batches per iteration");
     Workspace W = {};
     unsigned long long ovf0 = 0, ovf = 0;
     rc = read_overflow(t, st, &ovf0);
     if (rc) return rc;
-    cudaError_t e = ws_alloc(W, chunk, 8 * chunk + 65536, t);
+    rc = ensure_slots(t, bpi, st);
+    if (rc) return rc;
+    cudaError_t e = ws_alloc(W, (uint32_t)chunk, (uint32_t)std::min<int64_t>(4 * chunk + 65536, 0xF0000000ll), t);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_run workspace");
     TP T = make_tp(ph, t, o, seed, W.cnt);
     SQ S;
@@ -903,29 +1089,38 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     S.k0 = T.k0; S.k1 = T.k1;
     S.z_rel = (float)(ph->z0 - P->z_phsp);
     S.x0 = (float)ph->x0; S.y0 = (float)ph->y0;
+    S.plan = plan;
     static int gs0 = 0, gs1 = 0;
     if (!gs0) gs0 = grid_for((const void *)k_sample_queue<0>, 256, 0);
     if (!gs1) gs1 = grid_for((const void *)k_sample_queue<1>, 256, 0);
-    for (int b = 0; b < o.n_batches && rc == LSM_OK; ++b) {
-        for (int64_t h0 = 0; h0 < P->plan_size && rc == LSM_OK; h0 += chunk) {
-            S.h0 = h0;
-            S.n = std::min<int64_t>(chunk, P->plan_size - h0);
-            S.g0 = (uint64_t)b * (uint64_t)P->plan_size + (uint64_t)h0;
-            if ((e = cudaMemsetAsync(W.cnt, 0, sizeof(IterCounters), st)) != cudaSuccess) {
-                rc = set_cuda_error(e, "memset");
-                break;
-            }
-            const int gs = (int)std::min<int64_t>((S.n + 255) / 256, t->mode == 0 ? gs0 : gs1);
-            const int tk = timer_begin(1, st);
-            if (t->mode == 0) k_sample_queue<0><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
-            else k_sample_queue<1><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
-            count_launch();
-            timer_end(tk, st);
-            if ((e = cudaGetLastError()) != cudaSuccess) { rc = set_cuda_error(e, "k_sample_queue"); break; }
-            rc = t->mode == 0 ? drain<0>(T, W, t, st) : drain<1>(T, W, t, st);
-            if (rc) break;
+    auto iteration = [&](uint64_t g0, int64_t h0, int64_t n) -> lsm_status {
+        S.g0 = g0;
+        S.h0 = h0;
+        S.n = n;
+        LSM_CUDA(cudaMemsetAsync(W.cnt, 0, sizeof(IterCounters), st));
+        const int gs = (int)std::min<int64_t>((S.n + 255) / 256, t->mode == 0 ? gs0 : gs1);
+        const int tk = timer_begin(1, st);
+        if (t->mode == 0) k_sample_queue<0><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
+        else k_sample_queue<1><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
+        count_launch();
+        timer_end(tk, st);
+        LSM_CUDA(cudaGetLastError());
+        return t->mode == 0 ? drain<0>(T, W, t, st) : drain<1>(T, W, t, st);
+    };
+    if (multi) {
+        for (int b0 = 0; b0 < o.n_batches && rc == LSM_OK; b0 += bpi) {
+            const int k = std::min(bpi, o.n_batches - b0);
+            rc = iteration((uint64_t)b0 * (uint64_t)plan, 0, (int64_t)k * plan);
+            if (rc == LSM_OK) rc = fold_slots(t, k, st);
         }
-        if (rc == LSM_OK) rc = fold_batch(t, st);
+    } else {
+        for (int b = 0; b < o.n_batches && rc == LSM_OK; ++b) {
+            for (int64_t h0 = 0; h0 < plan && rc == LSM_OK; h0 += chunk) {
+                rc = iteration((uint64_t)b * (uint64_t)plan + (uint64_t)h0, h0, std::min<int64_t>(chunk, plan - h0));
+                if (rc == LSM_OK) rc = flush_partials(t, st);
+            }
+            if (rc == LSM_OK) rc = fold_batch(t, st);
+        }
     }
     if (rc == LSM_OK) rc = read_overflow(t, st, &ovf);
     if (rc) return rc;

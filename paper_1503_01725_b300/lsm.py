@@ -339,7 +339,7 @@ class RunOpts:
     f_e: float = 0.25
     s_geo: float = 0.0
     max_steps: int = 100000
-    chunk: int = 131072
+    chunk: int = 0          # 0: library default, min(plan size, 2^20)
 
     def struct(self) -> lsm_run_opts:
         return lsm_run_opts(electron_mode=self.electron_mode, n_batches=self.n_batches,
