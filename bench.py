@@ -98,8 +98,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock and throttle-reason samples. Started before the
+    warm-up (its start-up must not overlap the timed steps); only samples
+    time-stamped inside the timed window are summarised."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -107,18 +109,28 @@ class ClockSampler:
         self.idx = gpu_index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.t0 = self.t1 = None
 
-    def __enter__(self):
+    def start(self):
+        if os.environ.get("LSM_BENCH_NO_CLOCKS") == "1":
+            return self
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 20
+            while time.time() < deadline and os.path.getsize(self.f.name) == 0:
+                time.sleep(0.05)
         except Exception:
             self.p = None
         return self
 
-    def __exit__(self, *a):
+    def window(self, t0: float, t1: float):
+        self.t0, self.t1 = t0, t1
+
+    def stop(self):
         if self.p:
+            time.sleep(0.25)
             self.p.terminate()
             try:
                 self.p.wait(timeout=5)
@@ -126,6 +138,7 @@ class ClockSampler:
                 self.p.kill()
 
     def summary(self) -> dict:
+        import datetime
         self.f.flush()
         self.f.seek(0)
         rows = [r.strip().split(",") for r in self.f.read().strip().splitlines() if r.strip()]
@@ -134,9 +147,12 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             try:
-                sm.append(float(r[1]))
-                smax = float(r[2])
-                for k, v in zip(names, r[5:9]):
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if self.t0 is not None and not (self.t0 - 0.15 <= ts <= self.t1 + 0.15):
+                    continue
+                sm.append(float(r[2]))
+                smax = float(r[3])
+                for k, v in zip(names, r[6:10]):
                     if v.strip().lower() == "active":
                         reasons.add(k)
             except Exception:
@@ -233,6 +249,7 @@ def main():
         d, s = lsm.lsm_dose(tally, ph, psl.denom / n_plan, device=True)
         return psl, d, s
 
+    clk = ClockSampler(local).start()
     for i in range(args.warmup):
         step(1000 + i)
     torch.cuda.synchronize()
@@ -245,8 +262,9 @@ def main():
     launches0 = lsm.lsm_launch_count()
     ms_steps = []
     u_vals = []
-    with ClockSampler(local) as clk:
+    if True:
         torch.cuda.synchronize()
+        tw0 = time.time()
         for i in range(args.steps):
             flush.fill_(i & 0xFF)                      # L2 flush outside the timed events
             ev[i][0].record(stream)
@@ -255,6 +273,8 @@ def main():
             torch.cuda.synchronize()
             ms_steps.append(ev[i][0].elapsed_time(ev[i][1]))
             u_vals.append(u_mean_rel(d.cpu().numpy(), s.cpu().numpy()))
+        clk.window(tw0, time.time())
+        clk.stop()
     print("per-step ms: " + " ".join(f"{v:.3f}" for v in ms_steps), file=sys.stderr)
     launches = lsm.lsm_launch_count() - launches0
     timers = lsm.lsm_timing_read(reset=True)

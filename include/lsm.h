@@ -189,7 +189,10 @@ lsm_status lsm_phantom_create(const lsm_phantom_desc *desc, lsm_phantom **out, l
 void lsm_phantom_destroy(lsm_phantom *ph);
 /* Copy the interaction tables to host (synchronises): out float
  * [2 materials][1024][4] = (mu_compton, mu_photo, mu_pair in cm^2/g, S_col in
- * MeV cm^2/g), then [1024] majorant (1/cm); grid[2] = (ln E_min, d ln E). */
+ * MeV cm^2/g), then [1024] majorant (1/cm), then [32][129] inverse
+ * Klein-Nishina CDF v = (eta - 1) / (2k) at ln E = ln 0.05 + i (ln 7 - ln 0.05)/31
+ * and u = j/128 (eta = E/E', k = E/mc^2); grid[2] = (ln E_min, d ln E) of the
+ * 1024-point grid. */
 lsm_status lsm_phantom_tables(const lsm_phantom *ph, float *out, double grid[2]);
 
 /*

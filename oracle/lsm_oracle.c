@@ -20,7 +20,7 @@
  * The paper does not describe its transport physics (Sec. 2.3 gives only the
  * 200 keV electron and 50 keV photon cutoffs). This file therefore implements
  * the stated simplification: photons by Woodcock tracking with Compton
- * (Klein-Nishina, sampled by Kahn's rejection method), photoelectric and pair
+ * (Klein-Nishina, sampled by inverting its closed-form CDF), photoelectric and pair
  * interactions whose cross sections come from closed forms with two synthetic
  * constants; electrons by condensed-history CSDA steps with Bethe collision
  * stopping power and a Gaussian (Highland) multiple-scattering deflection.
@@ -89,15 +89,24 @@ static void draw(stream_t *s, uint32_t out[4])
     s->ctr++;
 }
 
-/* Stream ids of the particles created at one interaction: the words of the
- * parent's block at counter (ctr | 2^31), a range ordinary draws never reach.
- * Ids 0 (source sampling) and 1 (primary transport) are reserved. */
-static void child_ids(const stream_t *s, uint32_t ids[4])
+/* MurmurHash3's 32-bit finaliser (Appleby). */
+static uint32_t fmix32(uint32_t h)
 {
-    uint32_t c[4] = {s->g_lo, s->g_hi, s->sid, s->ctr | 0x80000000u};
-    or_philox4x32_10(s->key, c, ids);
-    for (int i = 0; i < 4; ++i)
-        if (ids[i] < 2u) ids[i] += 2u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+/* Stream id of the slot-th particle created at one interaction: a hash of the
+ * parent's stream id and its current draw counter. Ids 0 (source sampling) and
+ * 1 (primary transport) are reserved. */
+static uint32_t child_id(const stream_t *s, uint32_t slot)
+{
+    uint32_t h = fmix32(s->sid ^ fmix32(s->ctr ^ (0x9E3779B9u * (slot + 1u))));
+    return h < 2u ? h + 2u : h;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -740,6 +749,8 @@ typedef struct {
     double x, y, z, u, v, w, E;
     int type, psr, beam;
     stream_t rng;
+    int have;            /* electrons: words 2-3 of the last block are still unused */
+    uint32_t hold[2];
 } part_t;
 
 typedef struct {
@@ -820,32 +831,34 @@ static void spawn_electron(tctx *T, const part_t *par, double Ee, double u, doub
     if (T->O->electron_mode == 0 || Ee < E_CUT_E) { deposit(T, vox, Ee, par); return; }
     part_t c = *par;
     c.type = 1; c.E = Ee; c.u = u; c.v = v; c.w = w;
-    c.rng.sid = sid; c.rng.ctr = 0;
+    c.rng.sid = sid; c.rng.ctr = 0; c.have = 0;
     push(T, &c);
 }
 
-/* Kahn's rejection method for the Klein-Nishina distribution of
- * eta = E / E' (k = E / mc^2). One Philox block per trial: three uniforms for
- * the test, the fourth gives the azimuth of the accepted trial. */
-static void kahn(stream_t *st, double k, double *eta_out, double *phi_out)
+/* Integral from 1 to eta of the Klein-Nishina density of eta = E/E' (up to a
+ * constant factor), k = E/mc^2: the density is t^-2 (1/t + t - sin^2 theta)
+ * with cos theta = 1 - (t - 1)/k, whose integral has this closed form. */
+OR_API double or_kn_cdf(double eta, double k)
 {
-    double eta = 1.0, phi = 0.0;
-    for (int trial = 0; trial < 1000; ++trial) {
-        uint32_t q[4];
-        draw(st, q);
-        double r1 = u01(q[0]), r2 = u01(q[1]), r3 = u01(q[2]);
-        int acc;
-        if (r1 <= (1.0 + 2.0 * k) / (9.0 + 2.0 * k)) {
-            eta = 1.0 + 2.0 * k * r2;
-            acc = r3 <= 4.0 * (1.0 / eta - 1.0 / (eta * eta));
-        } else {
-            eta = (1.0 + 2.0 * k) / (1.0 + 2.0 * k * r2);
-            double c = 1.0 - (eta - 1.0) / k;
-            acc = r3 <= 0.5 * (c * c + 1.0 / eta);
-        }
-        if (acc) { phi = 2.0 * PI_D * u01(q[3]); break; }
+    double ie = 1.0 / eta, le = log(eta), k1 = k + 1.0;
+    return 0.5 * (1.0 - ie * ie) + le + ie - 1.0 + (k1 * k1 * (1.0 - ie) - 2.0 * k1 * le + eta - 1.0) / (k * k);
+}
+
+/* Compton sampling by inverting the Klein-Nishina CDF (bisection in FP64).
+ * One Philox block: word 0 -> eta, word 1 -> azimuth. */
+static void kn_sample(stream_t *st, double k, double *eta_out, double *phi_out)
+{
+    uint32_t q[4];
+    draw(st, q);
+    double emax = 1.0 + 2.0 * k;
+    double target = u01(q[0]) * or_kn_cdf(emax, k);
+    double lo = 1.0, hi = emax;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (or_kn_cdf(mid, k) < target) lo = mid; else hi = mid;
     }
-    *eta_out = eta; *phi_out = phi;
+    *eta_out = 0.5 * (lo + hi);
+    *phi_out = 2.0 * PI_D * u01(q[1]);
 }
 
 static void photon_track(tctx *T, part_t *p)
@@ -875,9 +888,9 @@ static void photon_track(tctx *T, part_t *p)
         T->n_real++;
         double t = u01(r[2]) * mut;
         if (t <= muC) {
-            /* Compton: Kahn's rejection sampling of the Klein-Nishina distribution */
+            /* Compton: E'/E from the inverse Klein-Nishina CDF */
             double k = p->E / ME, eta, cost, phi;
-            kahn(&p->rng, k, &eta, &phi);
+            kn_sample(&p->rng, k, &eta, &phi);
             cost = 1.0 - (eta - 1.0) / k;
             double E1 = p->E / eta;
             double u = p->u, v = p->v, w = p->w;
@@ -886,15 +899,11 @@ static void photon_track(tctx *T, part_t *p)
             double ex = p->E * p->u - E1 * u, ey = p->E * p->v - E1 * v, ez = p->E * p->w - E1 * w;
             double en = sqrt(ex * ex + ey * ey + ez * ez);
             if (en > 0.0) { ex /= en; ey /= en; ez /= en; } else { ex = p->u; ey = p->v; ez = p->w; }
-            uint32_t ids[4];
-            child_ids(&p->rng, ids);
-            spawn_electron(T, p, p->E - E1, ex, ey, ez, ids[0], vox);
+            spawn_electron(T, p, p->E - E1, ex, ey, ez, child_id(&p->rng, 0), vox);
             p->E = E1; p->u = u; p->v = v; p->w = w;
         } else if (t <= muC + muP) {
             /* photoelectric: the electron takes the photon energy and direction */
-            uint32_t ids[4];
-            child_ids(&p->rng, ids);
-            spawn_electron(T, p, p->E, p->u, p->v, p->w, ids[0], vox);
+            spawn_electron(T, p, p->E, p->u, p->v, p->w, child_id(&p->rng, 0), vox);
             return;
         } else {
             /* pair: uniform kinetic split, both leptons along the photon; the
@@ -908,11 +917,11 @@ static void photon_track(tctx *T, part_t *p)
             double sa = sqrt(fmax(0.0, 1.0 - ca * ca));
             double ax = sa * cos(pa), ay = sa * sin(pa), az = ca;
             uint32_t ids[4];
-            child_ids(&p->rng, ids);
+            for (uint32_t c = 0; c < 4; ++c) ids[c] = child_id(&p->rng, c);
             spawn_electron(T, p, Tm, p->u, p->v, p->w, ids[0], vox);
             spawn_electron(T, p, Tp, p->u, p->v, p->w, ids[1], vox);
             part_t g = *p;
-            g.type = 0; g.E = ME; g.rng.ctr = 0;
+            g.type = 0; g.E = ME; g.rng.ctr = 0; g.have = 0;
             g.u = ax; g.v = ay; g.w = az; g.rng.sid = ids[2];
             push(T, &g);
             g.u = -ax; g.v = -ay; g.w = -az; g.rng.sid = ids[3];
@@ -950,12 +959,19 @@ static void electron_track(tctx *T, part_t *p)
         p->x += ds * p->u; p->y += ds * p->v; p->z += ds * p->w;
         p->E -= dE;
         if (p->E >= E_CUT_E && !O->ms_off) {
-            uint32_t r[4];
-            draw(&p->rng, r);
+            /* one block serves two deflections: words 0-1, then words 2-3 */
+            uint32_t ua, ub;
+            if (p->have) {
+                ua = p->hold[0]; ub = p->hold[1]; p->have = 0;
+            } else {
+                uint32_t r[4];
+                draw(&p->rng, r);
+                ua = r[0]; ub = r[1]; p->hold[0] = r[2]; p->hold[1] = r[3]; p->have = 1;
+            }
             double th0 = or_highland(E0, rho * ds / X0G[m]);
-            double th = th0 * sqrt(-2.0 * log(u01(r[0])));
+            double th = th0 * sqrt(-2.0 * log(u01(ua)));
             if (th > PI_D) th = PI_D;
-            rotate_dir(&p->u, &p->v, &p->w, cos(th), 2.0 * PI_D * u01(r[1]));
+            rotate_dir(&p->u, &p->v, &p->w, cos(th), 2.0 * PI_D * u01(ub));
         }
     }
 }
@@ -1007,6 +1023,7 @@ OR_API int or_run(const void *h, const or_phantom *Ph, const or_opts *O, uint64_
                 p.x = o.x; p.y = o.y; p.z = o.z; p.u = o.u; p.v = o.v; p.w = o.w; p.E = o.E;
                 p.type = o.type; p.psr = o.psr; p.beam = o.beam;
                 stream_init(&p.rng, seed, g, 1u);
+                p.have = 0;
                 int vox = voxel_of(Ph, p.x, p.y, p.z);
                 if (vox < 0) { T.esc += p.E; stats[4]++; }
                 else {
@@ -1057,6 +1074,7 @@ OR_API void or_first_collision(const or_phantom *Ph, const or_opts *O, double E,
         part_t p;
         p.x = xc; p.y = yc; p.z = Ph->z0; p.u = 0; p.v = 0; p.w = 1; p.E = E;
         stream_init(&p.rng, seed, (uint64_t)i, 1u);
+        p.have = 0;
         depth[i] = -1.0;
         for (;;) {
             uint32_t r[4];
@@ -1073,7 +1091,7 @@ OR_API void or_first_collision(const or_phantom *Ph, const or_opts *O, double E,
     }
 }
 
-/* Pin helper: n Compton events at energy E through the same Kahn sampler;
+/* Pin helper: n Compton events at energy E through the same inverse-CDF sampler;
  * out [n][2] = (E'/E, cos theta). */
 OR_API void or_kn_samples(double E, uint64_t seed, int64_t n, double *out)
 {
@@ -1081,7 +1099,7 @@ OR_API void or_kn_samples(double E, uint64_t seed, int64_t n, double *out)
         stream_t st;
         stream_init(&st, seed, (uint64_t)i, 1u);
         double k = E / ME, eta, phi;
-        kahn(&st, k, &eta, &phi);
+        kn_sample(&st, k, &eta, &phi);
         out[2 * i] = 1.0 / eta;
         out[2 * i + 1] = 1.0 - (eta - 1.0) / k;
     }
@@ -1100,6 +1118,7 @@ OR_API void or_electron_path(const or_phantom *Ph, const or_opts *O, double E, u
     p.x = Ph->x0 + 0.5 * Ph->nx * Ph->dx; p.y = Ph->y0 + 0.5 * Ph->ny * Ph->dy;
     p.z = Ph->z0 + 1e-9; p.u = 0; p.v = 0; p.w = 1; p.E = E; p.type = 1; p.psr = 0; p.beam = 0;
     stream_init(&p.rng, seed, 0, 1u);
+    p.have = 0;
     double z0 = p.z;
     /* tally_mode 0 with a scratch accumulator */
     size_t nvox = (size_t)Ph->nx * Ph->ny * Ph->nz;

@@ -73,6 +73,8 @@ def lib():
         for f in ("or_kn_sigma",):
             getattr(L, f).restype = C.c_double
             getattr(L, f).argtypes = [C.c_double]
+        L.or_kn_cdf.restype = C.c_double
+        L.or_kn_cdf.argtypes = [C.c_double, C.c_double]
         L.or_mu_mass.restype = C.c_double
         L.or_mu_mass.argtypes = [C.c_double, C.c_int, C.c_int]
         L.or_scol_mass.restype = C.c_double
@@ -112,6 +114,11 @@ def philox4x32_10(key, ctr) -> np.ndarray:
 
 def kn_sigma(E: float) -> float:
     return lib().or_kn_sigma(E)
+
+
+def kn_cdf(eta: float, k: float) -> float:
+    """Closed-form integral of the Klein-Nishina density of eta = E/E' from 1 to eta."""
+    return lib().or_kn_cdf(eta, k)
 
 
 def mu_mass(E: float, mat: int, comp: int) -> float:

@@ -212,7 +212,7 @@ lsm_status lsm_phantom_tables(const lsm_phantom *ph, float *out, double grid[2])
     if (!ph || !out) return set_arg_error("lsm_phantom_tables: NULL argument");
     LSM_CUDA(cudaDeviceSynchronize());
     LSM_CUDA(cudaMemcpy(out, ph->d_xs, 2 * kGrid * sizeof(float4), cudaMemcpyDeviceToHost));
-    LSM_CUDA(cudaMemcpy(out + 8 * kGrid, ph->d_mumax, kGrid * 4, cudaMemcpyDeviceToHost));
+    LSM_CUDA(cudaMemcpy(out + 8 * kGrid, ph->d_mumax, kGrid * 4 + kKnE * kKnU * 4, cudaMemcpyDeviceToHost));
     if (grid) { grid[0] = kLnEmin; grid[1] = (kLnEmax - kLnEmin) / (kGrid - 1); }
     return LSM_OK;
 }

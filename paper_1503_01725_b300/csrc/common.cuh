@@ -20,6 +20,12 @@ constexpr double kPiD = 3.14159265358979323846;
 constexpr int kGrid = 1024;              // log-energy table points
 constexpr double kLnEmin = -6.907755278982137;  // ln(1 keV in MeV)
 constexpr double kLnEmax = 1.9459101090932196;  // ln(7 MeV)
+// Inverse Klein-Nishina CDF table: v = (eta - 1) / (2k) as a function of
+// (ln E, u), eta = E/E', k = E/mc^2; kKnE log-spaced energies 50 keV - 7 MeV,
+// kKnU uniform u points on [0, 1].
+constexpr int kKnE = 32, kKnU = 129;
+constexpr double kKnLnE0 = -2.995732273553991;   // ln(0.05)
+constexpr double kKnLnE1 = 1.9459101090932196;   // ln(7)
 
 // ---------------------------------------------------------------- Philox ---
 __device__ __forceinline__ uint4 philox4x32_10(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
@@ -61,15 +67,24 @@ struct Stream {
         pre = philox4x32_10(k0, k1, glo, ghi, sid, ctr);
         have = 1;
     }
-    // stream ids of particles created at the current draw position
-    __device__ __forceinline__ uint4 child_ids() const
+    // stream ids of the (up to four) particles created at the current draw
+    // position: a hash of (stream id, draw counter, slot); ids 0 and 1 are
+    // reserved for source sampling and primary transport
+    __device__ __forceinline__ uint32_t child_id(uint32_t slot) const
     {
-        uint4 r = philox4x32_10(k0, k1, glo, ghi, sid, ctr | 0x80000000u);
-        r.x += (r.x < 2u) ? 2u : 0u;
-        r.y += (r.y < 2u) ? 2u : 0u;
-        r.z += (r.z < 2u) ? 2u : 0u;
-        r.w += (r.w < 2u) ? 2u : 0u;
-        return r;
+        uint32_t h = sid ^ fmix32(ctr ^ (0x9E3779B9u * (slot + 1u)));
+        h = fmix32(h);
+        return h < 2u ? h + 2u : h;
+    }
+    // MurmurHash3's 32-bit finaliser (Appleby)
+    __device__ __forceinline__ static uint32_t fmix32(uint32_t h)
+    {
+        h ^= h >> 16;
+        h *= 0x85EBCA6Bu;
+        h ^= h >> 13;
+        h *= 0xC2B2AE35u;
+        h ^= h >> 16;
+        return h;
     }
 };
 

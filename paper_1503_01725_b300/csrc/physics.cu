@@ -68,6 +68,35 @@ __global__ void k_tables(float4 *__restrict__ xs, double *__restrict__ mutot)
     mutot[i] = c + p + q;
 }
 
+// integral of the Klein-Nishina density of eta = E/E' from 1 to eta (up to a
+// constant factor), k = E/mc^2:  f(t) = t^-2 (1/t + t - sin^2 theta),
+// cos theta = 1 - (t - 1)/k
+__device__ double kn_cdf(double eta, double k)
+{
+    const double ie = 1.0 / eta, le = log(eta), k1 = k + 1.0;
+    return 0.5 * (1.0 - ie * ie) + le + ie - 1.0 + (k1 * k1 * (1.0 - ie) - 2.0 * k1 * le + eta - 1.0) / (k * k);
+}
+
+// inverse CDF table, v = (eta - 1) / (2k), by bisection in FP64
+__global__ void k_kn_table(float *__restrict__ tab)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kKnE * kKnU) return;
+    const int ie = i / kKnU, ju = i % kKnU;
+    const double E = exp(kKnLnE0 + ie * ((kKnLnE1 - kKnLnE0) / (kKnE - 1)));
+    const double k = E / kMeD, emax = 1.0 + 2.0 * k;
+    const double target = ((double)ju / (kKnU - 1)) * kn_cdf(emax, k);
+    double lo = 1.0, hi = emax;
+    for (int it = 0; it < 64; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (kn_cdf(mid, k) < target) lo = mid; else hi = mid;
+    }
+    double v = (0.5 * (lo + hi) - 1.0) / (2.0 * k);
+    if (ju == 0) v = 0.0;
+    if (ju == kKnU - 1) v = 1.0;
+    tab[i] = (float)v;
+}
+
 __global__ void k_rho_max(const float *__restrict__ rho, const uint8_t *__restrict__ mat, int64_t n,
                           unsigned *__restrict__ bits)
 {
@@ -162,7 +191,8 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     CK(cudaMalloc(&P->d_mat, n));
     CK(cudaMalloc(&P->d_rhomat, n * 4));
     CK(cudaMalloc(&P->d_xs, 2 * kGrid * sizeof(float4)));
-    CK(cudaMalloc(&P->d_mumax, kGrid * 4));
+    // majorant followed by the inverse-KN table: staged into shared memory by one copy
+    CK(cudaMalloc(&P->d_mumax, kGrid * 4 + kKnE * kKnU * 4));
     CK(cudaMalloc(&d_mutot, 2 * kGrid * 8));
     CK(cudaMalloc(&d_bits, 16));
     CK(cudaMemcpyAsync(P->d_rho, D->rho, n * 4, kind, st));
@@ -179,6 +209,8 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     CKL("k_tables");
     k_majorant<<<(kGrid + 127) / 128, 128, 0, st>>>(d_mutot, d_bits, P->d_mumax);
     CKL("k_majorant");
+    k_kn_table<<<(kKnE * kKnU + 127) / 128, 128, 0, st>>>(P->d_mumax + kGrid);
+    CKL("k_kn_table");
     CK(cudaMemcpyAsync(bits, d_bits, 12, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     cudaFree(d_mutot);

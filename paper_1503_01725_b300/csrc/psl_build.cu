@@ -194,25 +194,28 @@ __global__ void k_pos_compact(const double *__restrict__ rem, const int64_t *__r
 }
 
 // rank[p] += #{q : posrem[q] > posrem[p], or equal with q < p} over one tile
-// of 256 candidates p and 1024 competitors q; the grid covers all tile pairs
+// of 256 candidates p and 1024 competitors q; the grid covers all tile pairs.
+// Remainders are finite and >= 0, so they order exactly as their IEEE bit
+// patterns read as unsigned integers: the comparisons run on the integer
+// pipes instead of B300's narrow FP64 pipe.
 __global__ void k_eq3_rank_tiles(const double *__restrict__ posrem, const int64_t *__restrict__ pos_idx,
                                  int64_t ncell, int *__restrict__ rank)
 {
-    __shared__ double tile[1024];
+    __shared__ unsigned long long tile[1024];
     const int64_t n_pos = pos_idx[ncell];
     const int64_t p0 = (int64_t)blockIdx.x * blockDim.x, q0 = (int64_t)blockIdx.y * 1024;
     if (p0 >= n_pos || q0 >= n_pos) return;
-    for (int t = threadIdx.x; t < 1024; t += blockDim.x) tile[t] = (q0 + t < n_pos) ? posrem[q0 + t] : -1.0;
+    const unsigned long long *bits = reinterpret_cast<const unsigned long long *>(posrem);
+    for (int t = threadIdx.x; t < 1024; t += blockDim.x) tile[t] = (q0 + t < n_pos) ? bits[q0 + t] : 0ull;
     __syncthreads();
     const int64_t p = p0 + threadIdx.x;
     if (p >= n_pos) return;
-    const double rp = posrem[p];
+    const unsigned long long rp = bits[p];
     const int lim = (int)((n_pos - q0) < 1024 ? (n_pos - q0) : 1024);
+    const int tie_end = (p > q0) ? (int)((p - q0) < lim ? (p - q0) : lim) : 0;   // q < p inside this tile
     int c = 0;
-    for (int t = 0; t < lim; ++t) {
-        const double rq = tile[t];
-        c += (rq > rp) || (rq == rp && q0 + t < p);
-    }
+    for (int t = 0; t < lim; ++t) c += tile[t] > rp;
+    for (int t = 0; t < tie_end; ++t) c += tile[t] == rp;
     if (c) atomicAdd(rank + p, c);
 }
 

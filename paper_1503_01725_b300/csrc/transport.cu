@@ -15,7 +15,7 @@
 //
 // The transport physics is the stated simplification of the paper's engine
 // (the paper gives only the 200 keV / 50 keV cutoffs, Sec. 2.3): Compton by
-// Klein-Nishina (Kahn's rejection method), photoelectric and pair from closed
+// Klein-Nishina (inverse of its closed-form CDF), photoelectric and pair from closed
 // forms; electrons by CSDA steps with Bethe stopping power and Highland
 // Gaussian deflection. All transport arithmetic is FP32; tallies are flushed
 // to FP64.
@@ -53,7 +53,15 @@ struct TP {
     IterCounters *cnt;
 };
 
-constexpr int kTableBytes = 2 * kGrid * 16 + kGrid * 4;   // 36 KB
+constexpr int kTableBytes = 2 * kGrid * 16 + kGrid * 4 + kKnE * kKnU * 4;   // 52 KB
+
+// resident CTAs per SM the transport kernels are compiled for (register budget)
+#ifndef LSM_PHOTON_MINB
+#define LSM_PHOTON_MINB 4
+#endif
+#ifndef LSM_ELECTRON_MINB
+#define LSM_ELECTRON_MINB 5
+#endif
 // radiation lengths (g/cm^2): water-like 36.08, bone 21.68
 
 // ---------------------------------------------------------------- tables ---
@@ -78,7 +86,7 @@ __device__ __forceinline__ bool stage_tables(float4 *s_xs, const float4 *g_xs, c
             : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d1),
-            "l"(g_mumax), "r"(kGrid * 4), "r"(bar)
+            "l"(g_mumax), "r"(kGrid * 4 + kKnE * kKnU * 4), "r"(bar)
             : "memory");
     }
     __syncthreads();
@@ -129,15 +137,32 @@ __host__ __device__ __forceinline__ uint32_t pb_make(uint32_t psr, uint32_t beam
     return psr | (beam << 16) | (slot << 20);
 }
 
+// Compton scattering: v = (eta - 1) / (2k) from the inverse Klein-Nishina CDF
+// table, bilinear in (ln E, u); then eta = 1 + 2 k v and cos theta = 1 - 2 v.
+__device__ __forceinline__ float kn_inverse(const float *__restrict__ kn, float E, float u)
+{
+    float t = (__logf(E) - (float)kKnLnE0) * (float)((kKnE - 1) / (kKnLnE1 - kKnLnE0));
+    t = fminf(fmaxf(t, 0.0f), (float)(kKnE - 1) - 1e-3f);
+    const int i = (int)t;
+    const float f = t - (float)i;
+    const float sidx = fminf(u * (float)(kKnU - 1), (float)(kKnU - 1) - 1e-4f);
+    const int j = (int)sidx;
+    const float g = sidx - (float)j;
+    const float *a = kn + i * kKnU + j, *b = a + kKnU;
+    const float lo = a[0] + g * (a[1] - a[0]), hi = b[0] + g * (b[1] - b[0]);
+    return lo + f * (hi - lo);
+}
+
 struct Acc {
     double esc, dep;
+    float dep32;       // deposits of the current particle, folded into dep when it ends
     unsigned long long flights, real, esteps, cap;
 };
 
 template <int MODE>
 __device__ __forceinline__ void deposit(const TP &T, Acc &A, int vox, float e, uint32_t pb)
 {
-    A.dep += e;
+    A.dep32 += e;
     float *slice = T.part + (size_t)pb_slot(pb) * T.ncell;
     if (MODE == 0) {
         atomicAdd(slice + vox, e);
@@ -156,10 +181,10 @@ __device__ __forceinline__ void rotate(float &u, float &v, float &w, float cost,
 {
     const float sint = sqrtf(fmaxf(0.0f, 1.0f - cost * cost));
     float sp, cp;
-    sincospif(2.0f * uphi, &sp, &cp);
+    __sincosf(6.28318531f * uphi, &sp, &cp);
     float un, vn, wn;
     if (fabsf(w) < 0.99999f) {
-        const float s = sqrtf(1.0f - w * w), is = 1.0f / s;
+        const float q = 1.0f - w * w, is = rsqrtf(q), s = q * is;
         un = u * cost + sint * (u * w * cp - v * sp) * is;
         vn = v * cost + sint * (v * w * cp + u * sp) * is;
         wn = w * cost - sint * s * cp;
@@ -171,6 +196,14 @@ __device__ __forceinline__ void rotate(float &u, float &v, float &w, float cost,
     const float in = rsqrtf(un * un + vn * vn + wn * wn);
     u = un * in; v = vn * in; w = wn * in;
 }
+
+// An electron a photon created during its step, pushed by the whole warp
+// after the step (one queue reservation serves many pushes).
+struct Pend {
+    float x, y, z, u, v, w, E;
+    uint32_t sid;
+    int vox;
+};
 
 struct Part {
     float x, y, z, u, v, w, E;
@@ -233,7 +266,7 @@ __device__ __forceinline__ void spawn_electron(const TP &T, Acc &A, const Queue 
 // Returns false when the photon's history ends.
 template <int MODE>
 __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t, Acc &A, Part &p,
-                            const Queue &eq, const Queue *pq)
+                            const Queue &eq, const Queue *pq, Pend &pe, bool &pend)
 {
     int vox = voxel(T, p.x, p.y, p.z);
     if (vox < 0) { A.esc += p.E; return false; }
@@ -244,12 +277,12 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     float tf;
     tab_pos(T.inv_dlnE, p.E, ti, tf);
     const float mm = (mumax_t[ti] + tf * (mumax_t[ti + 1] - mumax_t[ti])) * T.maj;
-    const float s = -__logf(u01(r.x)) / mm;
+    const float s = -__logf(u01(r.x)) * __frcp_rn(mm);
     p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
     A.flights++;
     vox = voxel(T, p.x, p.y, p.z);
     const float rm = vox >= 0 ? __ldg(T.rhomat + vox) : 0.0f;
-    // the block of the next draw (next flight or first Kahn trial) does not
+    // the block of the next draw (next flight or the Compton block) does not
     // depend on the density: compute it while the load is in flight
     p.rng.prefetch();
     if (vox < 0) { A.esc += p.E; return false; }
@@ -262,40 +295,38 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     A.real++;
     const float t = u01(r.z) * mut;
     if (t <= muC) {
-        // Compton: Kahn's method; one block per trial, fourth word = azimuth
-        const float k = p.E / kMe;
-        float eta = 1.0f, uphi = 0.0f;
-        for (int trial = 0; trial < 1000; ++trial) {
-            const uint4 q = p.rng.next();
-            const float r1 = u01(q.x), r2 = u01(q.y), r3 = u01(q.z);
-            bool acc;
-            if (r1 <= (1.0f + 2.0f * k) / (9.0f + 2.0f * k)) {
-                eta = 1.0f + 2.0f * k * r2;
-                acc = r3 <= 4.0f * (1.0f / eta - 1.0f / (eta * eta));
-            } else {
-                eta = (1.0f + 2.0f * k) / (1.0f + 2.0f * k * r2);
-                const float cc = 1.0f - (eta - 1.0f) / k;
-                acc = r3 <= 0.5f * (cc * cc + 1.0f / eta);
-            }
-            if (acc) { uphi = u01(q.w); break; }
-        }
-        const float cost = 1.0f - (eta - 1.0f) / k;
-        const float E1 = p.E / eta;
+        // Compton: one block, word 0 -> E'/E by the inverse Klein-Nishina CDF, word 1 -> azimuth
+        const uint4 q = p.rng.next();
+        const float k = p.E * (1.0f / kMe);
+        const float vkn = kn_inverse(mumax_t + kGrid, p.E, u01(q.x));
+        const float eta = 1.0f + 2.0f * k * vkn;
+        const float cost = 1.0f - 2.0f * vkn;
+        const float E1 = __fdividef(p.E, eta);
+        const float uphi = u01(q.y);
         float u = p.u, v = p.v, w = p.w;
         rotate(u, v, w, cost, uphi);
         float ex = p.E * p.u - E1 * u, ey = p.E * p.v - E1 * v, ez = p.E * p.w - E1 * w;
         const float en2 = ex * ex + ey * ey + ez * ez;
         if (en2 > 0.0f) { const float in = rsqrtf(en2); ex *= in; ey *= in; ez *= in; }
         else { ex = p.u; ey = p.v; ez = p.w; }
-        const uint4 ids = p.rng.child_ids();
-        spawn_electron<MODE>(T, A, eq, p, p.E - E1, ex, ey, ez, ids.x, vox);
+        const float Te = p.E - E1;
+        if (T.electron_mode && Te >= kCutE) {
+            pe = Pend{p.x, p.y, p.z, ex, ey, ez, Te, p.rng.child_id(0), vox};
+            pend = true;
+        } else {
+            deposit<MODE>(T, A, vox, Te, p.pb);
+        }
         p.E = E1; p.u = u; p.v = v; p.w = w;
         return true;
     }
     if (t <= muC + muP) {
         // photoelectric: the electron takes the photon's energy and direction
-        const uint4 ids = p.rng.child_ids();
-        spawn_electron<MODE>(T, A, eq, p, p.E, p.u, p.v, p.w, ids.x, vox);
+        if (T.electron_mode && p.E >= kCutE) {
+            pe = Pend{p.x, p.y, p.z, p.u, p.v, p.w, p.E, p.rng.child_id(0), vox};
+            pend = true;
+        } else {
+            deposit<MODE>(T, A, vox, p.E, p.pb);
+        }
         return false;
     }
     // pair: uniform kinetic split, leptons along the photon; annihilation
@@ -308,16 +339,15 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     float sp, cp;
     sincospif(2.0f * u01(q.z), &sp, &cp);
     const float ax = sa * cp, ay = sa * sp, az = ca;
-    const uint4 ids = p.rng.child_ids();
-    spawn_electron<MODE>(T, A, eq, p, Tm, p.u, p.v, p.w, ids.x, vox);
-    spawn_electron<MODE>(T, A, eq, p, Tp, p.u, p.v, p.w, ids.y, vox);
+    spawn_electron<MODE>(T, A, eq, p, Tm, p.u, p.v, p.w, p.rng.child_id(0), vox);
+    spawn_electron<MODE>(T, A, eq, p, Tp, p.u, p.v, p.w, p.rng.child_id(1), vox);
     // the annihilation-photon queue holds two per photon of the input queue
     for (int h = 0; h < 2; ++h) {
         const float sg = h ? -1.0f : 1.0f;
         const uint32_t slot = pq ? push_slot(&T.cnt->n[1]) : 0xffffffffu;
         if (pq && slot < pq->cap)
             store_part(*pq, slot, p.x, p.y, p.z, sg * ax, sg * ay, sg * az, kMe, p.rng.glo, p.rng.ghi,
-                       h ? ids.w : ids.z, p.pb);
+                       p.rng.child_id(2 + h), p.pb);
         else
             deposit<MODE>(T, A, vox, kMe, p.pb);
     }
@@ -342,7 +372,7 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
     tab_pos(T.inv_dlnE, p.E, ti, tf);
     const float4 c0 = lerp4(xs + m * kGrid, ti, tf);
     const float S = c0.w * rho;
-    const float ds = fminf(T.f_e * p.E / S, T.s_geo);
+    const float ds = fminf(__fdividef(T.f_e * p.E, S), T.s_geo);
     const float Emid = p.E - 0.5f * S * ds;               // midpoint rule
     tab_pos(T.inv_dlnE, Emid, ti, tf);
     const float4 c1 = lerp4(xs + m * kGrid, ti, tf);
@@ -361,20 +391,33 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
     p.rc = vn == vox ? rm : (vn >= 0 ? __ldg(T.rhomat + vn) : 0.0f);
     p.vc = vn;
     if (p.E >= kCutE) {
-        const uint4 r = p.rng.next();
+        // one block serves two deflections: words 0-1, then words 2-3 (held in
+        // pre while `have` is set; electrons never prefetch blocks)
+        float ua, ub;
+        if (p.rng.have) {
+            ua = u01(p.rng.pre.z);
+            ub = u01(p.rng.pre.w);
+            p.rng.have = 0;
+        } else {
+            const uint4 r = p.rng.next();
+            ua = u01(r.x);
+            ub = u01(r.y);
+            p.rng.pre = r;
+            p.rng.have = 1;
+        }
         const float t = rho * ds * (m ? (1.0f / 21.68f) : (1.0f / 36.08f));
-        const float bcp = E0 * (E0 + 2.0f * kMe) / (E0 + kMe);
+        // Highland width: 13.6 MeV / (beta c p) sqrt(t) (1 + 0.038 ln t), beta c p = E(E + 2m)/(E + m)
         const float f = fmaxf(1.0f + 0.038f * __logf(t), 0.0f);
-        const float th0 = 13.6f / bcp * sqrtf(t) * f;
-        const float th = fminf(th0 * sqrtf(-2.0f * __logf(u01(r.x))), kPi);
-        rotate(p.u, p.v, p.w, cosf(th), u01(r.y));
+        const float th0 = __fdividef(13.6f * (E0 + kMe), E0 * (E0 + 2.0f * kMe)) * sqrtf(t) * f;
+        const float th = fminf(th0 * sqrtf(-2.0f * __logf(ua)), kPi);
+        rotate(p.u, p.v, p.w, __cosf(th), ub);
     }
     return true;
 }
 
 __device__ void flush_acc(const TP &T, const Acc &A)
 {
-    const double esc = warp_sum(A.esc), dep = warp_sum(A.dep);
+    const double esc = warp_sum(A.esc), dep = warp_sum(A.dep + (double)A.dep32);
     const unsigned long long fl = warp_sum_u64(A.flights), re = warp_sum_u64(A.real),
                              es = warp_sum_u64(A.esteps), cp = warp_sum_u64(A.cap);
     if (lane_id() == 0) {
@@ -390,7 +433,7 @@ __device__ void flush_acc(const TP &T, const Acc &A)
 // Persistent transport kernel with per-lane refill from queue `qi`.
 // KIND 0: photons (Woodcock), KIND 1: electrons (CSDA).
 template <int MODE, int KIND>
-__global__ void __launch_bounds__(256, KIND ? 6 : 4) k_transport(TP T, Queue in, int qi, Queue eq, Queue pq, int has_pq)
+__global__ void __launch_bounds__(256, KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MINB) k_transport(TP T, Queue in, int qi, Queue eq, Queue pq, int has_pq)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -408,7 +451,7 @@ __global__ void __launch_bounds__(256, KIND ? 6 : 4) k_transport(TP T, Queue in,
     const unsigned lane = lane_id();
     unsigned lt;
     lanemask_lt(lt);
-    Acc A = {0.0, 0.0, 0ull, 0ull, 0ull, 0ull};
+    Acc A = {0.0, 0.0, 0.0f, 0ull, 0ull, 0ull, 0ull};
     Part p;
     bool alive = false;
     // Each warp reserves kGrab consecutive queue slots per atomic and hands
@@ -418,6 +461,9 @@ __global__ void __launch_bounds__(256, KIND ? 6 : 4) k_transport(TP T, Queue in,
     constexpr uint32_t kGrab = 32;
     uint32_t rb = 0, rl = 0;
     bool exhausted = false;
+    // output reservation for the electrons photons create: [ob, ob + ol)
+    constexpr uint32_t kOut = 32;
+    uint32_t ob = 0, ol = 0;
     for (;;) {
         const unsigned need = __ballot_sync(0xffffffffu, !alive);
         const uint32_t k = (uint32_t)__popc(need);
@@ -445,14 +491,63 @@ __global__ void __launch_bounds__(256, KIND ? 6 : 4) k_transport(TP T, Queue in,
                 rl = kGrab - from_new;
             } else {
                 rb += k;
-                rl -= k;
+                rl = rl > k ? rl - k : 0;
             }
         }
         if (!__any_sync(0xffffffffu, alive)) break;
-        if (alive) {
-            if (KIND == 0) alive = photon_step<MODE>(T, xs, mm, A, p, eq, has_pq ? &pq : nullptr);
-            else alive = electron_step<MODE>(T, xs, A, p);
+        if constexpr (KIND == 1) {
+            if (alive) {
+                alive = electron_step<MODE>(T, xs, A, p);
+                if (!alive) { A.dep += A.dep32; A.dep32 = 0.0f; }
+            }
+        } else {
+            bool pend = false;
+            Pend pe;
+            const uint32_t pb_keep = p.pb;
+            if (alive) {
+                alive = photon_step<MODE>(T, xs, mm, A, p, eq, has_pq ? &pq : nullptr, pe, pend);
+                if (!alive) { A.dep += A.dep32; A.dep32 = 0.0f; }
+            }
+            // warp-wide push of the electrons created in this step
+            const unsigned pm = __ballot_sync(0xffffffffu, pend);
+            if (pm) {
+                const uint32_t n = (uint32_t)__popc(pm);
+                uint32_t nb = 0;
+                bool g2 = false;
+                if (ol < n) {
+                    if (lane == 0) nb = atomicAdd(&T.cnt->n[2], kOut);
+                    nb = __shfl_sync(0xffffffffu, nb, 0);
+                    g2 = true;
+                }
+                if (pend) {
+                    const uint32_t r = (uint32_t)__popc(pm & lt);
+                    const uint32_t slot = r < ol ? ob + r : nb + (r - ol);
+                    if (slot < eq.cap) {
+                        store_part(eq, slot, pe.x, pe.y, pe.z, pe.u, pe.v, pe.w, pe.E, p.rng.glo, p.rng.ghi, pe.sid,
+                                   pb_keep);
+                    } else {
+                        atomicAdd(&T.stats->c[9], 1ull);
+                        deposit<MODE>(T, A, pe.vox, pe.E, pb_keep);
+                        A.dep += A.dep32;
+                        A.dep32 = 0.0f;
+                    }
+                }
+                if (g2) {
+                    const uint32_t from_new = n - ol;
+                    ob = nb + from_new;
+                    ol = kOut - from_new;
+                } else {
+                    ob += n;
+                    ol -= n;
+                }
+            }
         }
+    }
+    if (KIND == 0 && ol) {
+        // reserved output slots this warp did not fill hold dead entries
+        // (outside the phantom, no energy) that the electron kernel discards
+        if (lane < ol && ob + lane < eq.cap)
+            store_part(eq, ob + lane, -1.0f, -1.0f, -1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0u, 0u, 2u, 0u);
     }
     flush_acc(T, A);
 }
@@ -478,7 +573,7 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double src = 0.0, rej = 0.0, esc = 0.0;
-    Acc A = {0.0, 0.0, 0ull, 0ull, 0ull, 0ull};
+    Acc A = {0.0, 0.0, 0.0f, 0ull, 0ull, 0ull, 0ull};
     unsigned long long nph = 0, nel = 0, nrej = 0, nmiss = 0;
     for (int64_t base = warp * 32; base < S.n; base += nwarps * 32) {
         const int64_t i = base + lane;
@@ -530,7 +625,7 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
         }
     }
     src = warp_sum(src); rej = warp_sum(rej); esc = warp_sum(esc);
-    const double dep = warp_sum(A.dep);
+    const double dep = warp_sum(A.dep + (double)A.dep32);
     nph = warp_sum_u64(nph); nel = warp_sum_u64(nel); nrej = warp_sum_u64(nrej); nmiss = warp_sum_u64(nmiss);
     if (lane == 0) {
         atomicAdd(&T.stats->ledger[0], src);
@@ -582,7 +677,7 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double esc = 0.0;
-    Acc A = {0.0, 0.0, 0ull, 0ull, 0ull, 0ull};
+    Acc A = {0.0, 0.0, 0.0f, 0ull, 0ull, 0ull, 0ull};
     unsigned long long nph = 0, nel = 0, nmiss = 0;
     for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
         const int64_t i = base + lane;
@@ -623,7 +718,7 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
         }
     }
     esc = warp_sum(esc);
-    const double dep = warp_sum(A.dep);
+    const double dep = warp_sum(A.dep + (double)A.dep32);
     nph = warp_sum_u64(nph); nel = warp_sum_u64(nel); nmiss = warp_sum_u64(nmiss);
     if (lane == 0) {
         if (esc != 0.0) atomicAdd(&T.stats->ledger[2], esc);
@@ -1031,7 +1126,7 @@ lsm_status transport_particles(const lsm_phantom *ph, const lsm_particles *in, i
     unsigned long long ovf0 = 0, ovf = 0;
     rc = read_overflow(t, st, &ovf0);
     if (rc) return rc;
-    cudaError_t e = ws_alloc(W, cap, (uint32_t)std::min<int64_t>(8 * (int64_t)cap + 65536, 1u << 28), t);
+    cudaError_t e = ws_alloc(W, cap, (uint32_t)std::min<int64_t>(8 * (int64_t)cap + (1 << 18), 1u << 28), t);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_transport workspace");
     TP T = make_tp(ph, t, o, seed, W.cnt);
     do {
@@ -1081,7 +1176,7 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     if (rc) return rc;
     rc = ensure_slots(t, bpi, st);
     if (rc) return rc;
-    cudaError_t e = ws_alloc(W, (uint32_t)chunk, (uint32_t)std::min<int64_t>(4 * chunk + 65536, 0xF0000000ll), t);
+    cudaError_t e = ws_alloc(W, (uint32_t)chunk, (uint32_t)std::min<int64_t>(4 * chunk + (1 << 18), 0xF0000000ll), t);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_run workspace");
     TP T = make_tp(ph, t, o, seed, W.cnt);
     SQ S;

@@ -281,11 +281,12 @@ def lsm_phantom_create(ph, stream=None) -> PhantomHandle:
 
 
 def lsm_phantom_tables(ph: PhantomHandle):
-    out = np.zeros(2 * 1024 * 4 + 1024, dtype=np.float32)
+    """(xs [2][1024][4], majorant [1024], inverse-KN table [32][129], grid)."""
+    out = np.zeros(2 * 1024 * 4 + 1024 + 32 * 129, dtype=np.float32)
     grid = np.zeros(2)
     _check(_lib.lsm_phantom_tables(ph.ptr, out.ctypes.data_as(C.POINTER(C.c_float)),
                                    grid.ctypes.data_as(_dp)), "lsm_phantom_tables")
-    return out[: 8192].reshape(2, 1024, 4), out[8192:], grid
+    return out[: 8192].reshape(2, 1024, 4), out[8192:9216], out[9216:].reshape(32, 129), grid
 
 
 def lsm_tally_create(ph: PhantomHandle, mode: int = 0, idx3d=None, n_rows: int = 0, n_psr: int = 0,

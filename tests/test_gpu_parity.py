@@ -130,7 +130,7 @@ def test_sampling_edge_cases(L):
 
 def test_interaction_tables_match_closed_forms(L):
     ph = L.lsm_phantom_create(W.heterogeneous_phantom(16, 16, 16, 0.5, seed=3))
-    xs, mm, grid = L.lsm_phantom_tables(ph)
+    xs, mm, kn, grid = L.lsm_phantom_tables(ph)
     E = np.exp(grid[0] + grid[1] * np.arange(1024))
     sel = (E > 0.01) & (E < 7.0)
     for m in (0, 1):
@@ -145,6 +145,24 @@ def test_interaction_tables_match_closed_forms(L):
                       rmax[1] * np.array([O.mu_mass(e, 1, 3) for e in E[sel]]))
     assert np.all(mm[sel] >= want * (1 - 1e-6))
     np.testing.assert_allclose(mm[sel], want, rtol=5e-5)
+
+
+def test_inverse_kn_table_matches_exact_inversion(L):
+    """GPU Compton table against the closed-form CDF inverted in FP64."""
+    from scipy import optimize
+    ph = L.lsm_phantom_create(W.water_phantom(8, 8, 8, 0.5))
+    _, _, kn, _ = L.lsm_phantom_tables(ph)
+    lnE = np.linspace(np.log(0.05), np.log(7.0), 32)
+    for i in range(0, 32, 3):
+        k = np.exp(lnE[i]) / 0.51099895
+        emax = 1 + 2 * k
+        tot = O.kn_cdf(emax, k)
+        for j in range(1, 128, 7):
+            u = j / 128
+            eta = optimize.brentq(lambda t: O.kn_cdf(t, k) - u * tot, 1.0, emax, xtol=1e-14)
+            assert kn[i, j] == pytest.approx((eta - 1) / (2 * k), rel=2e-6, abs=1e-7)
+    assert np.all(kn[:, 0] == 0) and np.all(kn[:, -1] == 1)
+    assert np.all(np.diff(kn, axis=1) >= 0)
 
 
 def _dose_zcheck(dg, sg, do, so, frac=0.99, thr=0.1, mean_tol=0.005):

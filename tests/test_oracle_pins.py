@@ -98,7 +98,7 @@ def test_kn_thomson_limit():
 
 
 @pytest.mark.parametrize("E", [0.1, 1.0, 6.0])
-def test_kahn_sampler_moments(E):
+def test_compton_sampler_moments(E):
     """Sampled <E'/E> and <cos theta> match the KN-weighted quadrature."""
     s = O.kn_samples(E, 11, 200_000)
     k = E / ME
@@ -115,6 +115,19 @@ def test_kahn_sampler_moments(E):
     cg = cdf(grid)
     ks = stats.kstest(s[:20000, 1], lambda c: np.interp(c, grid, cg))
     assert ks.pvalue > 1e-3
+
+
+@pytest.mark.parametrize("E", [0.06, 0.5, 2.0, 6.0])
+def test_kn_cdf_closed_form_is_integral_of_density(E):
+    """The closed-form CDF the Compton sampler inverts equals the quadrature of
+    the KN density in eta = E/E' (d sigma / d eta from d sigma / d Omega)."""
+    k = E / ME
+    emax = 1 + 2 * k
+    dens = lambda t: _kn_diff(E, 1 - (t - 1) / k) / k   # d cos(theta) / d eta = 1/k
+    tot, _ = integrate.quad(dens, 1, emax, epsabs=0, epsrel=1e-12)
+    for eta in (1.0 + 0.1 * (emax - 1), 1 + 0.5 * (emax - 1), emax):
+        part, _ = integrate.quad(dens, 1, eta, epsabs=0, epsrel=1e-12)
+        assert O.kn_cdf(eta, k) / O.kn_cdf(emax, k) == pytest.approx(part / tot, rel=1e-10)
 
 
 def test_cross_section_calibration_points():
