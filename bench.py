@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--n-batches", type=int, default=16)
     p.add_argument("--chunk", type=int, default=0, help="histories per iteration (0: library default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true", help="skip the commissioning (batched) block")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
@@ -180,6 +181,76 @@ def cpu_oracle_rate(wl, seconds: float, per_step_hist: int = 100_000):
         if el >= seconds:
             break
     return done / el, done, el
+
+
+def commissioning_block(lsm, W, reps: int = 3, n_batches: int = 16):
+    """Batched basis-dose runs of commissioning (Sec. 2.2.2: 300 PSRs x 3
+    fields, per-PSR history counts proportional to weight, clamped to
+    1e4-1e6, all runs in one plan and one launch sequence) and the FP64 NNLS
+    fit of Eq. 8 on the GPU. Electron PSRs are grouped per energy bin."""
+    import torch
+    wl = W.workload_commissioning()
+    n_k = wl.extra["n_k"]
+    ph = lsm.lsm_phantom_create(wl.phantom)
+    idx, n_rows = W.commissioning_index(wl.phantom)
+    m = wl.model
+    tally = lsm.lsm_tally_create(ph, mode=1, idx3d=idx, n_rows=n_rows, n_psr=m.n_psr, n_beams=wl.beams.n_beams)
+    opts = lsm.RunOpts(electron_mode=1, n_batches=n_batches)
+    stream = torch.cuda.current_stream()
+
+    def basis(seed):
+        psl = lsm.lsm_build_psl(m, wl.beams, per_psr_hist=n_k)
+        lsm.lsm_tally_reset(tally)
+        lsm.lsm_run(psl, ph, tally, seed, opts)
+        return psl
+
+    basis(1)                                   # warm-up
+    ms = []
+    for r in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        psl = basis(10 + r)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    s1, s2, nb = lsm.lsm_tally_read(tally)
+    A = lsm.lsm_basis_matrix(tally, psl, ph)
+    hist = int(psl.info["plan_size"]) * n_batches
+    # relative batch uncertainty of the A entries above half their column's maximum
+    var_b = np.clip(s2 - s1 * s1 / nb, 0, None) / max(nb - 1, 1)
+    sig = np.sqrt(nb * var_b)
+    S1 = s1.reshape(A.shape)
+    sel = S1 > 0.5 * S1.max(axis=0, keepdims=True)
+    sel &= S1 > 0
+    u_A = float(np.mean(sig.reshape(A.shape)[sel] / S1[sel]))
+    t_basis = float(np.median(ms)) / 1e3
+    # group electron PSRs (sub-source 2) per energy bin: 200 photon PSRs + 10 units
+    n_ph = 2 * m.n_e * m.n_r
+    Ae = A[:, n_ph:].reshape(A.shape[0], m.n_e, m.n_r).sum(axis=2)
+    Ag = np.concatenate([A[:, :n_ph], Ae], axis=1)
+    # synthetic measurement from an independent basis run, known weights, 0.5 % noise
+    basis(999)
+    A2 = lsm.lsm_basis_matrix(tally, psl, ph)
+    A2g = np.concatenate([A2[:, :n_ph], A2[:, n_ph:].reshape(A.shape[0], m.n_e, m.n_r).sum(axis=2)], axis=1)
+    x_true = W.commissioning_truth(Ag.shape[1])
+    rng = np.random.default_rng(3)
+    bvec = A2g @ x_true * (1 + 0.005 * rng.standard_normal(Ag.shape[0]))
+    scale = 1.0 / np.abs(bvec).max()
+    out = {}
+    for method, name, it in ((0, "active_set", 0), (1, "projected_gradient", 50000)):
+        lsm.lsm_commission(Ag * scale, bvec * scale, method=method, max_iter=it)      # warm-up
+        t0 = time.perf_counter()
+        x, rep = lsm.lsm_commission(Ag * scale, bvec * scale, method=method, max_iter=it)
+        out[name] = {"ms": (time.perf_counter() - t0) * 1e3, "iterations": rep["iterations"],
+                     "converged": rep["converged"],
+                     # fit residual and error of the dose the fitted weights predict
+                     "fit_residual": float(np.linalg.norm(Ag @ x - bvec) / np.linalg.norm(bvec)),
+                     "dose_rel_err": float(np.linalg.norm(A2g @ (x - x_true)) / np.linalg.norm(A2g @ x_true))}
+    return {"workload": wl.name, "histories": hist, "ms_basis": t_basis * 1e3,
+            "histories_per_s": hist / t_basis, "u_A_rel_D50": u_A,
+            "s_to_1pct_A": t_basis * (u_A / 0.01) ** 2, "A_shape": list(Ag.shape),
+            "nnls": out}
 
 
 def run_reference(args, rank, world):
@@ -330,6 +401,9 @@ def main():
                 "peak_source": f"{hbm_kind} hbm_gbs",
                 "algorithmic_bytes_per_step": units[dom]}
 
+    batched = None
+    if not args.no_batched:
+        batched = commissioning_block(lsm, W)
     cpu = None
     if not args.no_cpu_baseline:
         rate, n_done, el = cpu_oracle_rate(wl, args.cpu_seconds)
@@ -349,6 +423,7 @@ def main():
         "work_per_step": {"photons": st["photons"], "electrons": st["electrons"], "flights": st["flights"],
                           "real": st["real"], "esteps": st["esteps"], "rejected": st["rejected"]},
         "roofline": roofline,
+        "batched": batched,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "histories/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},

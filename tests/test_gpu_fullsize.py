@@ -1,0 +1,181 @@
+"""Parity at the benchmark's full sizes and launch configuration.
+
+The oracle cannot redo 1e7-1e8 histories in test time, so these tests use
+what it can compute one by one (sampled particles of scattered history ids),
+subsets it can run exactly (the first batches of the same plan), and
+properties that hold at any size (energy balance, bit-exact plans, two GPU
+estimators of the same basis matrix).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1503_01725_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+N_FULL = 10_000_000
+B_FULL = 16
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1503_01725_b300 import lsm
+    lsm.load_library()
+    return lsm
+
+
+@pytest.fixture(scope="module")
+def full_run(L):
+    """The benchmark's workload and launch configuration: 1e7 histories as 16
+    batches of a 625k-history plan, default iteration size."""
+    wl = W.workload_full_10x10(N_FULL)
+    n_plan = N_FULL // B_FULL
+    g = L.lsm_build_psl(wl.model, wl.beams, n_plan)
+    ph = L.lsm_phantom_create(wl.phantom)
+    t = L.lsm_tally_create(ph)
+    rc = L.lsm_run(g, ph, t, wl.seed, L.RunOpts(electron_mode=1, n_batches=B_FULL))
+    s1, s2, nb = L.lsm_tally_read(t)
+    led, st = L.lsm_tally_ledger(t)
+    return wl, n_plan, g, (s1, s2, nb, led, st, rc)
+
+
+def test_full_plan_bit_exact(L, full_run):
+    wl, n_plan, g, _ = full_run
+    o = O.Plan(wl.model, wl.beams, n_plan)
+    assert np.array_equal(L.lsm_psl_copy(g, 3), o.count)
+    assert np.array_equal(L.lsm_psl_copy(g, 4), o.ent_start)
+
+
+def test_full_sampling_on_scattered_histories(L, full_run):
+    import torch
+    wl, n_plan, g, _ = full_run
+    o = O.Plan(wl.model, wl.beams, n_plan)
+    for g0 in (0, 3_141_592, N_FULL - 20_000):
+        out = L.lsm_sample(g, wl.seed, g0, 20_000, W.SSD)
+        torch.cuda.synchronize()
+        gs = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+        os_ = O.sample(o, wl.seed, g0, 20_000, W.SSD)
+        assert np.array_equal(gs["info"][:, 3], os_["entry"])
+        assert np.array_equal(gs["info"][:, 1], os_["ring"])
+        assert np.array_equal(gs["info"][:, 2], os_["comp"])
+        assert np.array_equal(gs["psr"].astype(np.int64) & 0xFFFF, os_["psr"])
+        far = os_["edge"] > 1e-4
+        assert np.array_equal(gs["status"][far], os_["status"][far])
+        ok = far & (os_["status"] == 0)
+        for k in ("u", "v", "w"):
+            np.testing.assert_allclose(gs[k][ok], os_[k][ok], rtol=1e-5, atol=2e-6, err_msg=k)
+        np.testing.assert_allclose(gs["E"][ok], os_["E"][ok], rtol=1e-6, err_msg="E")
+        # surface positions follow an 80 cm straight flight: they inherit the
+        # direction tolerance times the flight length
+        for k in ("x", "y"):
+            np.testing.assert_allclose(gs[k][ok], os_[k][ok], rtol=1e-5, atol=2e-6 * (W.SSD - W.Z_PHSP),
+                                       err_msg=k)
+
+
+def test_full_energy_ledger(full_run):
+    _, _, _, (s1, s2, nb, led, st, rc) = full_run
+    assert rc == 0 and nb == B_FULL
+    assert st["histories"] == N_FULL
+    assert st["overflows"] == 0 and st["cap_hits"] == 0
+    assert led["source"] == pytest.approx(led["rejected"] + led["escaped"] + led["deposited"], rel=1e-6)
+    assert s1.sum() == pytest.approx(led["deposited"], rel=1e-5)
+
+
+def test_full_dose_against_oracle_batches(full_run):
+    """The oracle runs batches 0-1 of the same plan (histories 0 .. 1.25e6);
+    per-batch dose from the full GPU run must agree with them."""
+    wl, n_plan, _, (s1, s2, nb, led, st, rc) = full_run
+    o = O.Plan(wl.model, wl.beams, n_plan)
+    r = O.run(o, wl.phantom, wl.seed, n_batches=2, electron_mode=1)
+    dg, sg = O.dose_and_sigma(s1, s2, nb)
+    do, so = O.dose_and_sigma(r["s1"].ravel(), r["s2"].ravel(), 2)
+    dg, sg = dg / nb, sg / nb
+    do, so = do / 2, so / 2
+    # two oracle batches give a poor batch sigma: use the GPU's per-batch spread for both.
+    # Voxels are selected on a smoothed GPU dose, not on the 16x noisier oracle
+    # dose (selecting on noisy values biases the selected mean upwards).
+    from scipy import ndimage
+    sm = ndimage.uniform_filter(dg.reshape(wl.phantom.rho.shape), size=3).ravel()
+    sel = sm > 0.1 * sm.max()
+    sb = np.sqrt(np.clip(s2 / nb - (s1 / nb) ** 2, 0, None))          # per-batch sd of the GPU run
+    z = (dg - do)[sel] / np.sqrt(sg[sel] ** 2 + (sb[sel] / np.sqrt(2)) ** 2 + 1e-300)
+    assert np.mean(np.abs(z) < 3) >= 0.99
+    assert abs(dg[sel].mean() / do[sel].mean() - 1) < 0.005
+
+
+def test_full_heterogeneous_phantom(L):
+    """256x256x160 heterogeneous phantom at 0.25 cm, 1e8 histories (FP32
+    transport, FP32 partial tallies flushed to FP64): energy balance at full
+    size, and dose against an oracle run of the first 2e5 histories."""
+    wl = W.workload_hetero(100_000_000)
+    n_plan = wl.n_hist // 16
+    g = L.lsm_build_psl(wl.model, wl.beams, n_plan)
+    ph = L.lsm_phantom_create(wl.phantom)
+    t = L.lsm_tally_create(ph)
+    rc = L.lsm_run(g, ph, t, wl.seed, L.RunOpts(electron_mode=1, n_batches=16))
+    s1, s2, nb = L.lsm_tally_read(t)
+    led, st = L.lsm_tally_ledger(t)
+    assert rc == 0 and st["histories"] == wl.n_hist and st["overflows"] == 0
+    assert led["source"] == pytest.approx(led["rejected"] + led["escaped"] + led["deposited"], rel=1e-6)
+    # oracle: a 100k-history plan of the same workload, 2 batches; compare depth-dose
+    # of the central column region (summed over a 2x2 cm block to get oracle statistics)
+    o = O.Plan(wl.model, wl.beams, 100_000)
+    r = O.run(o, wl.phantom, 17, n_batches=2, electron_mode=1)
+    D = O.Plan(wl.model, wl.beams, 100_000).denom
+    dg = s1.reshape(ph.desc.nz, ph.desc.ny, ph.desc.nx) / (nb * n_plan) * D
+    do = r["s1"] / (2 * 100_000) * D
+    c = ph.desc.nx // 2
+    prof_g = dg[:, c - 4:c + 4, c - 4:c + 4].sum(axis=(1, 2))
+    prof_o = do[:, c - 4:c + 4, c - 4:c + 4].sum(axis=(1, 2))
+    sel = prof_o > 0.2 * prof_o.max()
+    # energy per history deposited along the central column agrees within the oracle's statistics
+    assert abs(prof_g[sel].sum() / prof_o[sel].sum() - 1) < 0.03
+
+
+def test_batched_basis_equals_single_run_decomposition(L):
+    """Two estimators of the commissioning basis matrix: per-PSR batched runs
+    (lsm_build_psl with per-PSR counts) and one whole-source run tallied by the
+    PSR index each particle carries (Sec. 2.2.2). Both estimate the dose per
+    source particle of every PSR at the measurement points."""
+    wl = W.workload_commissioning(hist_lo=2000, hist_hi=100_000)
+    m = wl.model
+    ph = W.water_phantom(64, 64, 128, 0.25)
+    idx, n_rows = W.commissioning_index(ph)
+    phh = L.lsm_phantom_create(ph)
+    # batched per-PSR runs
+    gk = L.lsm_build_psl(m, wl.beams, per_psr_hist=wl.extra["n_k"])
+    tk = L.lsm_tally_create(phh, mode=1, idx3d=idx, n_rows=n_rows, n_psr=m.n_psr, n_beams=wl.beams.n_beams)
+    L.lsm_run(gk, phh, tk, 5, L.RunOpts(n_batches=8))
+    Ak = L.lsm_basis_matrix(tk, gk, phh)
+    s1k, s2k, nbk = L.lsm_tally_read(tk)
+    # one whole-source run, PSR-indexed tally; dose per source particle = S1 / (B N) * D / mass
+    N = 4_000_000
+    gw = L.lsm_build_psl(m, wl.beams, N)
+    tw = L.lsm_tally_create(phh, mode=1, idx3d=idx, n_rows=n_rows, n_psr=m.n_psr, n_beams=wl.beams.n_beams)
+    L.lsm_run(gw, phh, tw, 6, L.RunOpts(n_batches=8))
+    s1w, s2w, nbw = L.lsm_tally_read(tw)
+    mass = np.zeros(n_rows)
+    flat = idx.ravel()
+    mass[flat[flat > 0] - 1] = ph.rho.ravel()[flat > 0] * ph.dx * ph.dy * ph.dz
+    mass_r = np.tile(mass, wl.beams.n_beams)[:, None]
+    Aw = s1w.reshape(Ak.shape) / (nbw * N) * gw.denom / mass_r
+    # per-cell z-scores with each estimator's batch standard deviation (8
+    # batches: chi-square tails, hence the 4-sigma band), over cells carrying signal
+    def sd(s1_, s2_, nb_, scale):
+        v = np.clip(s2_ - s1_ * s1_ / nb_, 0, None) / (nb_ - 1)
+        return np.sqrt(nb_ * v).reshape(Ak.shape) * scale
+    scale_k = np.divide(Ak, s1k.reshape(Ak.shape), out=np.zeros_like(Ak), where=s1k.reshape(Ak.shape) > 0)
+    sk = sd(s1k, s2k, nbk, scale_k)
+    sw = sd(s1w, s2w, nbw, 1.0 / (nbw * N) * gw.denom / mass_r)
+    # cells are selected on the mean of the two estimates, so that neither
+    # estimate's own fluctuations decide which cells are compared
+    Am = 0.5 * (Ak + Aw)
+    sel = (Am > 0.1 * Am.max(axis=0, keepdims=True)) & (sk > 0) & (sw > 0)
+    z = (Ak - Aw)[sel] / np.sqrt(sk[sel] ** 2 + sw[sel] ** 2)
+    assert sel.sum() > 1000
+    assert np.mean(np.abs(z) < 4) >= 0.99
+    # unselected totals per field
+    tk_ = Ak.reshape(wl.beams.n_beams, -1).sum(axis=1)
+    tw_ = Aw.reshape(wl.beams.n_beams, -1).sum(axis=1)
+    np.testing.assert_allclose(tk_, tw_, rtol=0.03)
