@@ -46,6 +46,10 @@ FALLBACK_HBM_GBS = 6400.0
 #     queue read (44 B), per real interaction one tally update (8 B) or queue write (44 B);
 #   electron transport: per CSDA step one density load (4 B) + one tally update
 #     (4 B read + 4 B write), per electron the queue read (44 B).
+# DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# on a reduced case of this workload; profiles/transport_3src-10x10-water64.md.
+# Valid for the kernels as profiled; set to None when they change.
+TRAFFIC_PER_UNIT = {"photon": ("photons", 57.6), "electron": ("esteps", 9.55)}
 B_SAMPLE_PER_HIST = 68.0
 B_FLIGHT = 4.0
 B_QUEUE = 44.0
@@ -396,8 +400,12 @@ def main():
     }
     dom = max(("sample", "photon", "electron"), key=lambda k: per_step[k])
     achieved = units[dom] / (per_step[dom] / 1e3) / 1e9
+    traffic = None
+    if dom in TRAFFIC_PER_UNIT and TRAFFIC_PER_UNIT[dom] is not None:
+        unit_key, per = TRAFFIC_PER_UNIT[dom]
+        traffic = per * st[unit_key]                       # bytes per step, like achieved
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm, "traffic": traffic, "traffic_unit": "bytes per step",
                 "peak_source": f"{hbm_kind} hbm_gbs",
                 "algorithmic_bytes_per_step": units[dom]}
 
