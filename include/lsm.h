@@ -237,8 +237,13 @@ lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], l
  * Gaussian deflection. s_geo <= 0 means half the smallest voxel side.
  * majorant_factor >= 1 inflates the Woodcock majorant (results unchanged in
  * expectation). chunk: histories per sample/transport iteration (the paper's
- * M; 0 = 131072). max_steps: per-particle step cap (>= 1), after which the
- * remaining energy is deposited locally and counted.
+ * M); 0 = 2^23. Plans smaller than chunk run several whole batches per
+ * iteration. max_steps: per-particle step cap (>= 1), after which the
+ * remaining energy is deposited locally and counted. ctas_per_sm: CTAs per SM
+ * of the persistent transport kernels (0 = as many as fit). use_graph != 0:
+ * lsm_run captures its launch sequence into a CUDA graph on first use and
+ * replays it for later runs with the same plan, phantom, tally and options
+ * (the seed may change); ignored while the timers are enabled.
  */
 typedef struct {
     int32_t electron_mode;
@@ -246,6 +251,8 @@ typedef struct {
     double majorant_factor, f_e, s_geo;
     int32_t max_steps;
     int32_t chunk;
+    int32_t ctas_per_sm;
+    int32_t use_graph;
 } lsm_run_opts;
 
 /*

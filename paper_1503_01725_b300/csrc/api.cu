@@ -20,7 +20,7 @@ lsm_status sample_public(const lsm_psl *, uint64_t, uint64_t, int64_t, double, c
 lsm_status transport_particles(const lsm_phantom *, const lsm_particles *, int64_t, uint64_t, lsm_tally *,
                                const lsm_run_opts *, cudaStream_t);
 lsm_status run_plan(const lsm_psl *, const lsm_phantom *, lsm_tally *, uint64_t, const lsm_run_opts *, cudaStream_t);
-lsm_status fold_batch(lsm_tally *, cudaStream_t);
+lsm_status fold_batch(lsm_tally *, cudaStream_t, bool);
 lsm_status flush_partials(lsm_tally *, cudaStream_t);
 lsm_status dose_impl(const lsm_tally *, const lsm_phantom *, double, double *, double *, lsm_mem, cudaStream_t);
 lsm_status basis_impl(const lsm_tally *, const lsm_psl *, const lsm_phantom *, const uint16_t *, lsm_mem, double *,
@@ -79,6 +79,12 @@ void timer_end(int token, cudaStream_t st)
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool timing_enabled()
+{
+    std::lock_guard<std::mutex> lk(g_tm);
+    return g_timing;
+}
 
 lsm_status set_cuda_error(cudaError_t e, const char *where)
 {
@@ -281,6 +287,13 @@ void lsm_tally_destroy(lsm_tally *t)
     cudaFree(t->d_part); cudaFree(t->d_batch); cudaFree(t->d_s1); cudaFree(t->d_s2); cudaFree(t->d_stats);
     if (t->d_idx) cudaFree(t->d_idx);
     if (t->ws) cudaFree(t->ws);
+    if (t->gexec) cudaGraphExecDestroy((cudaGraphExec_t)t->gexec);
+    if (t->gstream) {
+        cudaStreamSynchronize((cudaStream_t)t->gstream);
+        cudaStreamDestroy((cudaStream_t)t->gstream);
+        cudaEventDestroy((cudaEvent_t)t->gev[0]);
+        cudaEventDestroy((cudaEvent_t)t->gev[1]);
+    }
     free(t);
 }
 
@@ -302,7 +315,7 @@ lsm_status lsm_tally_end_batch(lsm_tally *t, lsm_stream stream)
     if (!t) return set_arg_error("lsm_tally_end_batch: NULL tally");
     lsm_status rc = flush_partials(t, S(stream));
     if (rc) return rc;
-    return fold_batch(t, S(stream));
+    return fold_batch(t, S(stream), true);
 }
 
 lsm_status lsm_tally_read(lsm_tally *t, double *s1, double *s2, lsm_mem mem, int32_t *n_batches, lsm_stream stream)

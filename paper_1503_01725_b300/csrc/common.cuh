@@ -155,6 +155,8 @@ namespace lsm {
 int timer_begin(int which, cudaStream_t st);
 void timer_end(int token, cudaStream_t st);
 void count_launch();
+void add_launches(int64_t n);     // kernels launched by a replayed graph
+bool timing_enabled();
 lsm_status set_cuda_error(cudaError_t e, const char *where);
 lsm_status set_arg_error(const char *msg);
 int sm_count();

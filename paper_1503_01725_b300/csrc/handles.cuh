@@ -30,6 +30,12 @@ struct SampleParams {
     float zy_rel, zx_rel;      // jaw plane minus phase-space plane
 };
 
+// What a captured run graph depends on besides the seed.
+struct GraphKey {
+    const void *psl, *ph, *part, *ws, *batch;
+    lsm_run_opts o;
+};
+
 }  // namespace lsm
 
 struct lsm_psl {
@@ -78,4 +84,9 @@ struct lsm_tally {
     int n_batches;
     void *ws;             // cached particle queues of lsm_run / lsm_transport
     uint32_t ws_chunk, ws_ecap;
+    void *gexec;          // captured run graph (cudaGraphExec_t) and what it was captured for
+    lsm::GraphKey gkey;
+    int64_t graph_kernels;
+    void *gstream;        // stream of graph capture and replay, and its two events
+    void *gev[2];
 };

@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <string.h>
 
 #include "sample.cuh"
 
@@ -48,9 +49,10 @@ struct TP {
     // run
     int electron_mode, max_steps;
     float f_e, s_geo;
-    uint32_t k0, k1;
+    const uint32_t *key;       // Philox key (seed) in device memory, so one captured graph serves every seed
     RunStats *stats;
     IterCounters *cnt;
+    int ctas_per_sm;           // transport grid: CTAs per SM (0: as many as fit)
 };
 
 constexpr int kTableBytes = 2 * kGrid * 16 + kGrid * 4 + kKnE * kKnU * 4;   // 52 KB
@@ -439,6 +441,7 @@ __global__ void __launch_bounds__(256, KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MIN
     __shared__ __align__(8) uint64_t mbar;
     const uint32_t n_q = *(volatile uint32_t *)&T.cnt->n[qi];
     const uint32_t n_in = n_q < in.cap ? n_q : in.cap;     // pushes beyond capacity were not stored
+    const uint32_t k0 = T.key[0], k1 = T.key[1];
     // blocks whose first slot lies past the queue end have nothing to refill
     // from once the earlier blocks start: leave before staging the tables
     if ((uint64_t)blockIdx.x * blockDim.x >= n_in) return;
@@ -483,7 +486,7 @@ __global__ void __launch_bounds__(256, KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MIN
             if (!alive) {
                 const uint32_t r = (uint32_t)__popc(need & lt);
                 const uint32_t i = r < rl ? rb + r : (grabbed ? nb + (r - rl) : 0xffffffffu);
-                if (i < n_in) { load_part(in, i, T.k0, T.k1, p); alive = true; }
+                if (i < n_in) { load_part(in, i, k0, k1, p); alive = true; }
             }
             if (grabbed) {
                 const uint32_t from_new = k - rl;
@@ -556,7 +559,7 @@ __global__ void __launch_bounds__(256, KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MIN
 
 struct SQ {
     SampleParams sp;
-    uint32_t k0, k1;
+    const uint32_t *key;    // Philox key in device memory
     uint64_t g0;            // history of the iteration's first particle
     int64_t h0, n;          // its plan position; histories in the iteration
     int64_t plan;           // plan size: position h0 + i lies in batch slot (h0 + i) / plan
@@ -567,6 +570,7 @@ struct SQ {
 template <int MODE>
 __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queue eq)
 {
+    const uint32_t k0 = S.key[0], k1 = S.key[1];
     const unsigned lane = lane_id();
     unsigned lt;
     lanemask_lt(lt);
@@ -586,7 +590,7 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
         if (valid) {
             const int64_t hh = S.h0 + i;
             slot = (uint32_t)(hh / S.plan);
-            sample_history(S.sp, S.k0, S.k1, S.g0 + (uint64_t)i, hh - (int64_t)slot * S.plan, S.z_rel, o);
+            sample_history(S.sp, k0, k1, S.g0 + (uint64_t)i, hh - (int64_t)slot * S.plan, S.z_rel, o);
             src += o.E;
             if (!o.accepted) { rej += o.E; nrej++; }
             else {
@@ -727,6 +731,12 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
         if (nel) atomicAdd(&T.stats->c[2], nel);
         if (nmiss) atomicAdd(&T.stats->c[4], nmiss);
     }
+}
+
+__global__ void k_set_key(uint32_t *key, uint32_t k0, uint32_t k1)
+{
+    key[0] = k0;
+    key[1] = k1;
 }
 
 // ------------------------------------------------------------- tallies ---
@@ -917,6 +927,7 @@ int grid_for(const void *fn, int threads, size_t smem)
 struct Workspace {
     Queue q[4];          // 0 primary photons, 1 annihilation photons, 2 electrons, 3 sorted electrons
     IterCounters *cnt;
+    uint32_t *key;       // Philox key of the run (outside the per-iteration counters)
     void *mem;
 };
 
@@ -941,6 +952,7 @@ cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t)
     char *p = (char *)t->ws;
     W.mem = nullptr;
     W.cnt = (IterCounters *)p;
+    W.key = (uint32_t *)(p + 768);
     p += 1024;
     for (int k = 0; k < 4; ++k) {
         Queue &q = W.q[k];
@@ -953,7 +965,7 @@ cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t)
     return cudaSuccess;
 }
 
-TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, uint64_t seed, IterCounters *cnt)
+TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, const uint32_t *key, IterCounters *cnt)
 {
     TP T;
     T.rhomat = ph->d_rhomat;
@@ -972,7 +984,8 @@ TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, uin
     T.f_e = (float)o.f_e;
     const double sg = o.s_geo > 0 ? o.s_geo : 0.5 * fmin(ph->dx, fmin(ph->dy, ph->dz));
     T.s_geo = (float)sg;
-    T.k0 = (uint32_t)seed; T.k1 = (uint32_t)(seed >> 32);
+    T.key = key;
+    T.ctas_per_sm = o.ctas_per_sm;
     T.stats = t->d_stats;
     T.cnt = cnt;
     return T;
@@ -980,6 +993,7 @@ TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, uin
 
 lsm_status check_opts(lsm_run_opts &o)
 {
+    if (o.ctas_per_sm < 0) return set_arg_error("ctas_per_sm must be >= 0");
     if (o.electron_mode != 0 && o.electron_mode != 1) return set_arg_error("electron_mode must be 0 or 1");
     if (!(o.majorant_factor >= 1.0) || !isfinite(o.majorant_factor)) return set_arg_error("majorant_factor must be >= 1");
     if (!(o.f_e > 0.0 && o.f_e <= 1.0)) return set_arg_error("f_e must be in (0, 1]");
@@ -1002,9 +1016,11 @@ lsm_status drain(const TP &T, Workspace &W, lsm_tally *t, cudaStream_t st)
         cudaFuncSetAttribute(k_transport<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    static int gp = 0, ge = 0;
-    if (!gp) gp = grid_for((const void *)k_transport<MODE, 0>, 256, smem);
-    if (!ge) ge = grid_for((const void *)k_transport<MODE, 1>, 256, smem);
+    static int gp_max = 0, ge_max = 0;
+    if (!gp_max) gp_max = grid_for((const void *)k_transport<MODE, 0>, 256, smem);
+    if (!ge_max) ge_max = grid_for((const void *)k_transport<MODE, 1>, 256, smem);
+    const int cap = T.ctas_per_sm > 0 ? T.ctas_per_sm * sm_count() : (1 << 30);
+    const int gp = std::min(gp_max, cap), ge = std::min(ge_max, cap);
     int tk = timer_begin(2, st);
     k_transport<MODE, 0><<<gp, 256, smem, st>>>(T, W.q[0], 0, W.q[2], W.q[1], 1);
     LSM_LAUNCHED("k_transport<photon>");
@@ -1039,7 +1055,7 @@ lsm_status read_overflow(lsm_tally *t, cudaStream_t st, unsigned long long *out)
 
 }  // namespace
 
-lsm_status fold_batch(lsm_tally *t, cudaStream_t st)
+lsm_status fold_batch(lsm_tally *t, cudaStream_t st, bool count)
 {
     const int64_t n = t->ncell;
     const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
@@ -1048,7 +1064,7 @@ lsm_status fold_batch(lsm_tally *t, cudaStream_t st)
     count_launch();
     timer_end(tk, st);
     LSM_CUDA(cudaGetLastError());
-    t->n_batches++;
+    if (count) t->n_batches++;
     return LSM_OK;
 }
 
@@ -1066,7 +1082,7 @@ lsm_status flush_partials(lsm_tally *t, cudaStream_t st)
 
 // fold k whole-batch slices of the partial tally into S1/S2
 lsm_status fold_slots(lsm_tally *t, int k, cudaStream_t st)
-{
+{   // batches are counted by the caller
     const int64_t n = t->ncell;
     const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
     const int tk = timer_begin(5, st);
@@ -1074,7 +1090,6 @@ lsm_status fold_slots(lsm_tally *t, int k, cudaStream_t st)
     count_launch();
     timer_end(tk, st);
     LSM_CUDA(cudaGetLastError());
-    t->n_batches += k;
     return LSM_OK;
 }
 
@@ -1128,8 +1143,10 @@ lsm_status transport_particles(const lsm_phantom *ph, const lsm_particles *in, i
     if (rc) return rc;
     cudaError_t e = ws_alloc(W, cap, (uint32_t)std::min<int64_t>(8 * (int64_t)cap + (1 << 18), 1u << 28), t);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_transport workspace");
-    TP T = make_tp(ph, t, o, seed, W.cnt);
+    TP T = make_tp(ph, t, o, W.key, W.cnt);
     do {
+        k_set_key<<<1, 1, 0, st>>>(W.key, (uint32_t)seed, (uint32_t)(seed >> 32));
+        count_launch();
         if ((e = cudaMemsetAsync(W.cnt, 0, sizeof(IterCounters), st)) != cudaSuccess) { rc = set_cuda_error(e, "memset"); break; }
         const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
         if (t->mode == 0)
@@ -1178,10 +1195,10 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     if (rc) return rc;
     cudaError_t e = ws_alloc(W, (uint32_t)chunk, (uint32_t)std::min<int64_t>(4 * chunk + (1 << 18), 0xF0000000ll), t);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_run workspace");
-    TP T = make_tp(ph, t, o, seed, W.cnt);
+    TP T = make_tp(ph, t, o, W.key, W.cnt);
     SQ S;
     S.sp = P->sp;
-    S.k0 = T.k0; S.k1 = T.k1;
+    S.key = W.key;
     S.z_rel = (float)(ph->z0 - P->z_phsp);
     S.x0 = (float)ph->x0; S.y0 = (float)ph->y0;
     S.plan = plan;
@@ -1202,21 +1219,84 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         LSM_CUDA(cudaGetLastError());
         return t->mode == 0 ? drain<0>(T, W, t, st) : drain<1>(T, W, t, st);
     };
-    if (multi) {
-        for (int b0 = 0; b0 < o.n_batches && rc == LSM_OK; b0 += bpi) {
-            const int k = std::min(bpi, o.n_batches - b0);
-            rc = iteration((uint64_t)b0 * (uint64_t)plan, 0, (int64_t)k * plan);
-            if (rc == LSM_OK) rc = fold_slots(t, k, st);
-        }
-    } else {
-        for (int b = 0; b < o.n_batches && rc == LSM_OK; ++b) {
-            for (int64_t h0 = 0; h0 < plan && rc == LSM_OK; h0 += chunk) {
-                rc = iteration((uint64_t)b * (uint64_t)plan + (uint64_t)h0, h0, std::min<int64_t>(chunk, plan - h0));
-                if (rc == LSM_OK) rc = flush_partials(t, st);
+    // the whole run's launch sequence (no host synchronisation inside)
+    auto enqueue = [&]() -> lsm_status {
+        lsm_status r = LSM_OK;
+        if (multi) {
+            for (int b0 = 0; b0 < o.n_batches && r == LSM_OK; b0 += bpi) {
+                const int k = std::min(bpi, o.n_batches - b0);
+                r = iteration((uint64_t)b0 * (uint64_t)plan, 0, (int64_t)k * plan);
+                if (r == LSM_OK) r = fold_slots(t, k, st);
             }
-            if (rc == LSM_OK) rc = fold_batch(t, st);
+        } else {
+            for (int b = 0; b < o.n_batches && r == LSM_OK; ++b) {
+                for (int64_t h0 = 0; h0 < plan && r == LSM_OK; h0 += chunk) {
+                    r = iteration((uint64_t)b * (uint64_t)plan + (uint64_t)h0, h0,
+                                  std::min<int64_t>(chunk, plan - h0));
+                    if (r == LSM_OK) r = flush_partials(t, st);
+                }
+                if (r == LSM_OK) r = fold_batch(t, st, false);
+            }
         }
+        return r;
+    };
+    k_set_key<<<1, 1, 0, st>>>(W.key, (uint32_t)seed, (uint32_t)(seed >> 32));
+    count_launch();
+    LSM_CUDA(cudaGetLastError());
+    if (o.use_graph && !timing_enabled()) {
+        // One CUDA graph per (plan, phantom, tally buffers, options): captured
+        // on first use, replayed afterwards with only the key set outside it.
+        // Capture and replay use the tally's own stream (the legacy default
+        // stream cannot be captured), ordered against `st` by events.
+        if (!t->gstream) {
+            cudaStream_t gs = nullptr;
+            LSM_CUDA(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+            cudaEvent_t e1 = nullptr, e2 = nullptr;
+            LSM_CUDA(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+            LSM_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+            t->gstream = gs; t->gev[0] = e1; t->gev[1] = e2;
+        }
+        const cudaStream_t caller = st;
+        st = (cudaStream_t)t->gstream;
+        LSM_CUDA(cudaEventRecord((cudaEvent_t)t->gev[0], caller));
+        LSM_CUDA(cudaStreamWaitEvent(st, (cudaEvent_t)t->gev[0], 0));
+        GraphKey gk = {};
+        gk.psl = P; gk.ph = ph; gk.part = t->d_part; gk.ws = t->ws; gk.batch = t->d_batch;
+        gk.o = o;
+        gk.o.n_batches = o.n_batches;
+        if (!t->gexec || memcmp(&gk, &t->gkey, sizeof(GraphKey)) != 0) {
+            memset(&t->gkey, 0, sizeof(GraphKey));
+            if (t->gexec) { cudaGraphExecDestroy((cudaGraphExec_t)t->gexec); t->gexec = nullptr; }
+            const int64_t l0 = lsm_launch_count();
+            LSM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue();
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (rc == LSM_OK && ce != cudaSuccess) rc = set_cuda_error(ce, "lsm_run: graph capture");
+            if (rc == LSM_OK) {
+                cudaGraphExec_t ge = nullptr;
+                ce = cudaGraphInstantiate(&ge, g, 0);
+                if (ce != cudaSuccess) rc = set_cuda_error(ce, "lsm_run: graph instantiate");
+                else {
+                    t->gexec = ge;
+                    memcpy(&t->gkey, &gk, sizeof(GraphKey));
+                    t->graph_kernels = lsm_launch_count() - l0;
+                }
+            }
+            if (g) cudaGraphDestroy(g);
+            if (rc) return rc;
+        } else {
+            add_launches(t->graph_kernels);
+        }
+        LSM_CUDA(cudaGraphLaunch((cudaGraphExec_t)t->gexec, st));
+        LSM_CUDA(cudaEventRecord((cudaEvent_t)t->gev[1], st));
+        LSM_CUDA(cudaStreamWaitEvent(caller, (cudaEvent_t)t->gev[1], 0));
+        st = caller;
+    } else {
+        rc = enqueue();
+        if (rc) return rc;
     }
+    t->n_batches += o.n_batches;
     if (rc == LSM_OK) rc = read_overflow(t, st, &ovf);
     if (rc) return rc;
     if (ovf > ovf0) return LSM_ERR_OVERFLOW;

@@ -61,7 +61,8 @@ class lsm_tally_desc(C.Structure):
 class lsm_run_opts(C.Structure):
     _fields_ = [("electron_mode", C.c_int32), ("n_batches", C.c_int32),
                 ("majorant_factor", C.c_double), ("f_e", C.c_double), ("s_geo", C.c_double),
-                ("max_steps", C.c_int32), ("chunk", C.c_int32)]
+                ("max_steps", C.c_int32), ("chunk", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("use_graph", C.c_int32)]
 
 
 class lsm_nnls_opts(C.Structure):
@@ -340,12 +341,15 @@ class RunOpts:
     f_e: float = 0.25
     s_geo: float = 0.0
     max_steps: int = 100000
-    chunk: int = 0          # 0: library default, min(plan size, 2^20)
+    chunk: int = 0          # 0: library default (2^23 histories per iteration)
+    ctas_per_sm: int = 0    # 0: as many as fit
+    use_graph: bool = False
 
     def struct(self) -> lsm_run_opts:
         return lsm_run_opts(electron_mode=self.electron_mode, n_batches=self.n_batches,
                             majorant_factor=self.majorant_factor, f_e=self.f_e, s_geo=self.s_geo,
-                            max_steps=self.max_steps, chunk=self.chunk)
+                            max_steps=self.max_steps, chunk=self.chunk, ctas_per_sm=self.ctas_per_sm,
+                            use_graph=int(self.use_graph))
 
 
 def lsm_transport(ph: PhantomHandle, particles: dict, n: int, seed: int, tally: Tally,
