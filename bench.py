@@ -24,6 +24,7 @@ prints the line with the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -65,7 +66,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n-hist", type=int, default=10_000_000)
     p.add_argument("--n-batches", type=int, default=16)
-    p.add_argument("--chunk", type=int, default=0, help="histories per iteration (0: library default)")
+    p.add_argument("--chunk", type=int, default=0, help="histories per iteration (0: autotuned)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="library defaults instead of the tuned iteration size, CTAs per SM and graph replay")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the commissioning (batched) block")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -91,6 +94,15 @@ def slowest_ms(total_ms: float, world: int) -> float:
     t = torch.tensor([total_ms], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def iteration_size(opts, plan: int) -> int:
+    """Histories per sample/transport iteration of lsm_run (whole batches when
+    the plan is smaller than the iteration size)."""
+    chunk = opts.chunk if opts.chunk > 0 else 1 << 23
+    if plan < chunk:
+        return min(opts.n_batches, chunk // plan) * plan
+    return chunk
 
 
 def peaks():
@@ -316,6 +328,15 @@ def main():
     ph.desc = wl.phantom
     tally = lsm.lsm_tally_create(ph)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    tuned = None
+    if not args.no_autotune and args.chunk == 0:
+        # launch parameters picked on this device before the warm-up (untimed)
+        from paper_1503_01725_b300 import autotune
+        psl_t = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)
+        opts, rep = autotune.tune(psl_t, ph, tally, opts, cache_path=None)
+        tuned = {"chunk": opts.chunk, "ctas_per_sm": opts.ctas_per_sm, "use_graph": opts.use_graph,
+                 "candidates": len(rep["trials"])}
+        del psl_t
 
     def step(i):
         psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)
@@ -325,6 +346,9 @@ def main():
         return psl, d, s
 
     clk = ClockSampler(local).start()
+    # kernel-group event timers on from the warm-up on, so that a captured
+    # graph already holds them when the timed steps replay it
+    lsm.lsm_timing_enable(True)
     for i in range(args.warmup):
         step(1000 + i)
     torch.cuda.synchronize()
@@ -332,7 +356,6 @@ def main():
         dist.barrier()
 
     lsm.lsm_timing_read(reset=True)
-    lsm.lsm_timing_enable(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = lsm.lsm_launch_count()
     ms_steps = []
@@ -362,13 +385,14 @@ def main():
 
     # end-to-end through the public API with host buffers
     e2e_s, h2d, d2h = [], 0, 0
+    e2e_opts = dataclasses.replace(opts, use_graph=False)     # one-shot runs: nothing to replay
     for i in range(max(2, min(3, args.steps))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         phh = lsm.lsm_phantom_create(wl.phantom)              # host rho/mat -> device
         psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)   # host model arrays -> device
         tt = lsm.lsm_tally_create(phh)
-        lsm.lsm_run(psl, phh, tt, 5000 + i, opts)
+        lsm.lsm_run(psl, phh, tt, 5000 + i, e2e_opts)
         dose, sig = lsm.lsm_dose(tt, phh, psl.denom / n_plan)  # device -> host
         e2e_s.append(time.perf_counter() - t0)
         h2d = wl.phantom.rho.nbytes + wl.phantom.mat.nbytes + sum(
@@ -423,7 +447,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl.name, "n_hist": args.n_hist, "n_batches": args.n_batches,
-                   "chunk": args.chunk if args.chunk > 0 else min(n_plan, 1 << 20), "phantom": "water 64^3 x 0.25 cm", "field_cm": 10,
+                   "histories_per_iteration": iteration_size(opts, n_plan),
+                   "ctas_per_sm": opts.ctas_per_sm, "cuda_graph": bool(opts.use_graph), "autotuned": tuned,
+                   "phantom": "water 64^3 x 0.25 cm", "field_cm": 10,
                    "sub_sources": 3, "electrons": "CSDA", "parallelism": f"replicas x{world}",
                    "l2": "flushed by a 512 MiB write before each step, outside the timed events"},
         "s_to_1pct": t1, "u_mean_rel_D50": u,

@@ -243,7 +243,9 @@ lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], l
  * of the persistent transport kernels (0 = as many as fit). use_graph != 0:
  * lsm_run captures its launch sequence into a CUDA graph on first use and
  * replays it for later runs with the same plan, phantom, tally and options
- * (the seed may change); ignored while the timers are enabled.
+ * (the seed may change). A graph captured while the event timers are on
+ * holds their events, which are read after every replay; turning the timers
+ * on or off re-captures it.
  */
 typedef struct {
     int32_t electron_mode;

@@ -35,6 +35,7 @@ static std::atomic<long long> g_launches{0};
 struct TimerRec {
     int which;
     cudaEvent_t a, b;
+    long long launches;   // kernels launched between the two events
 };
 static std::mutex g_tm;
 static bool g_timing = false;
@@ -56,6 +57,14 @@ static cudaEvent_t ev_get()
     return e;
 }
 
+static void record(cudaEvent_t e, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+}
+
 int timer_begin(int which, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(g_tm);
@@ -64,7 +73,8 @@ int timer_begin(int which, cudaStream_t st)
     r.which = which;
     r.a = ev_get();
     r.b = ev_get();
-    cudaEventRecord(r.a, st);
+    r.launches = 0;
+    record(r.a, st);
     g_open.push_back(r);
     g_cur_launch0 = g_launches.load();
     return (int)g_open.size() - 1;
@@ -74,8 +84,47 @@ void timer_end(int token, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(g_tm);
     if (token < 0 || token >= (int)g_open.size()) return;
-    cudaEventRecord(g_open[token].b, st);
-    g_cnt[g_open[token].which] += g_launches.load() - g_cur_launch0;
+    record(g_open[token].b, st);
+    g_open[token].launches = g_launches.load() - g_cur_launch0;
+}
+
+// Timers recorded while a stream is captured become event nodes of the graph;
+// they are detached from the open list and resolved after every replay.
+size_t timer_mark()
+{
+    std::lock_guard<std::mutex> lk(g_tm);
+    return g_open.size();
+}
+
+void *timer_detach(size_t from)
+{
+    std::lock_guard<std::mutex> lk(g_tm);
+    if (from >= g_open.size()) return nullptr;
+    auto *v = new std::vector<TimerRec>(g_open.begin() + from, g_open.end());
+    g_open.resize(from);
+    return v;
+}
+
+void timer_replayed(void *set)
+{   // the replay's events have completed (the caller synchronised)
+    if (!set) return;
+    std::lock_guard<std::mutex> lk(g_tm);
+    for (const TimerRec &r : *(std::vector<TimerRec> *)set) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) g_ms[r.which] += t;
+        g_cnt[r.which] += r.launches;
+    }
+}
+
+void timer_free(void *set)
+{
+    if (!set) return;
+    std::lock_guard<std::mutex> lk(g_tm);
+    for (const TimerRec &r : *(std::vector<TimerRec> *)set) {
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    delete (std::vector<TimerRec> *)set;
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -134,6 +183,7 @@ lsm_status lsm_timing_read(double ms[LSM_N_TIMERS], int64_t launches[LSM_N_TIMER
     for (auto &r : lsm::g_open) {
         float t = 0.0f;
         if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) lsm::g_ms[r.which] += t;
+        lsm::g_cnt[r.which] += r.launches;
         lsm::g_pool.push_back(r.a);
         lsm::g_pool.push_back(r.b);
     }
@@ -288,6 +338,7 @@ void lsm_tally_destroy(lsm_tally *t)
     if (t->d_idx) cudaFree(t->d_idx);
     if (t->ws) cudaFree(t->ws);
     if (t->gexec) cudaGraphExecDestroy((cudaGraphExec_t)t->gexec);
+    timer_free(t->gtimers);
     if (t->gstream) {
         cudaStreamSynchronize((cudaStream_t)t->gstream);
         cudaStreamDestroy((cudaStream_t)t->gstream);

@@ -154,6 +154,11 @@ namespace lsm {
 // returns a token that timer_end closes; both are no-ops while disabled.
 int timer_begin(int which, cudaStream_t st);
 void timer_end(int token, cudaStream_t st);
+// timers recorded during a graph capture: detached after it, resolved per replay
+size_t timer_mark();
+void *timer_detach(size_t from);
+void timer_replayed(void *set);
+void timer_free(void *set);
 void count_launch();
 void add_launches(int64_t n);     // kernels launched by a replayed graph
 bool timing_enabled();

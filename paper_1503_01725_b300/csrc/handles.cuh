@@ -34,6 +34,7 @@ struct SampleParams {
 struct GraphKey {
     const void *psl, *ph, *part, *ws, *batch;
     lsm_run_opts o;
+    int timed;            // captured with the event timers on
 };
 
 }  // namespace lsm
@@ -89,4 +90,5 @@ struct lsm_tally {
     int64_t graph_kernels;
     void *gstream;        // stream of graph capture and replay, and its two events
     void *gev[2];
+    void *gtimers;        // event timers inside the graph (when captured with timing on)
 };

@@ -733,10 +733,13 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
     }
 }
 
-__global__ void k_set_key(uint32_t *key, uint32_t k0, uint32_t k1)
+// Philox key of the run, and a snapshot of the overflow counter taken in
+// stream order (the host compares it with the counter after the run)
+__global__ void k_set_key(uint32_t *key, uint32_t k0, uint32_t k1, const unsigned long long *ovf)
 {
     key[0] = k0;
     key[1] = k1;
+    *(unsigned long long *)(key + 2) = *ovf;
 }
 
 // ------------------------------------------------------------- tallies ---
@@ -1045,12 +1048,21 @@ lsm_status drain(const TP &T, Workspace &W, lsm_tally *t, cudaStream_t st)
     return LSM_OK;
 }
 
-// queue overflows so far (run statistics counter 9); synchronises
-lsm_status read_overflow(lsm_tally *t, cudaStream_t st, unsigned long long *out)
+// queue overflows (run statistics counter 9) since k_set_key; synchronises
+lsm_status read_overflow(lsm_tally *t, const Workspace &W, cudaStream_t st, unsigned long long *out)
 {
-    LSM_CUDA(cudaMemcpyAsync(out, &t->d_stats->c[9], 8, cudaMemcpyDeviceToHost, st));
+    unsigned long long v[2] = {0, 0};
+    LSM_CUDA(cudaMemcpyAsync(&v[0], &t->d_stats->c[9], 8, cudaMemcpyDeviceToHost, st));
+    LSM_CUDA(cudaMemcpyAsync(&v[1], W.key + 2, 8, cudaMemcpyDeviceToHost, st));
     LSM_CUDA(cudaStreamSynchronize(st));
+    *out = v[0] - v[1];
     return LSM_OK;
+}
+
+void set_key(const Workspace &W, lsm_tally *t, uint64_t seed, cudaStream_t st)
+{
+    k_set_key<<<1, 1, 0, st>>>(W.key, (uint32_t)seed, (uint32_t)(seed >> 32), &t->d_stats->c[9]);
+    count_launch();
 }
 
 }  // namespace
@@ -1138,15 +1150,12 @@ lsm_status transport_particles(const lsm_phantom *ph, const lsm_particles *in, i
     if (n == 0) return LSM_OK;
     Workspace W = {};
     const uint32_t cap = (uint32_t)std::max<int64_t>(n, 1024);
-    unsigned long long ovf0 = 0, ovf = 0;
-    rc = read_overflow(t, st, &ovf0);
-    if (rc) return rc;
+    unsigned long long ovf = 0;
     cudaError_t e = ws_alloc(W, cap, (uint32_t)std::min<int64_t>(8 * (int64_t)cap + (1 << 18), 1u << 28), t);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_transport workspace");
     TP T = make_tp(ph, t, o, W.key, W.cnt);
     do {
-        k_set_key<<<1, 1, 0, st>>>(W.key, (uint32_t)seed, (uint32_t)(seed >> 32));
-        count_launch();
+        set_key(W, t, seed, st);
         if ((e = cudaMemsetAsync(W.cnt, 0, sizeof(IterCounters), st)) != cudaSuccess) { rc = set_cuda_error(e, "memset"); break; }
         const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
         if (t->mode == 0)
@@ -1159,10 +1168,10 @@ lsm_status transport_particles(const lsm_phantom *ph, const lsm_particles *in, i
         if (rc) break;
         rc = flush_partials(t, st);
         if (rc) break;
-        rc = read_overflow(t, st, &ovf);
+        rc = read_overflow(t, W, st, &ovf);
     } while (0);
     if (rc) return rc;
-    if (ovf > ovf0) return LSM_ERR_OVERFLOW;
+    if (ovf) return LSM_ERR_OVERFLOW;
     return LSM_OK;
 }
 
@@ -1188,9 +1197,7 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     const int64_t chunk = multi ? (int64_t)bpi * plan : (int64_t)o.chunk;
     if (bpi > 255) return set_arg_error("lsm_run: more than 255 batches per iteration");
     Workspace W = {};
-    unsigned long long ovf0 = 0, ovf = 0;
-    rc = read_overflow(t, st, &ovf0);
-    if (rc) return rc;
+    unsigned long long ovf = 0;
     rc = ensure_slots(t, bpi, st);
     if (rc) return rc;
     cudaError_t e = ws_alloc(W, (uint32_t)chunk, (uint32_t)std::min<int64_t>(4 * chunk + (1 << 18), 0xF0000000ll), t);
@@ -1240,10 +1247,10 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         }
         return r;
     };
-    k_set_key<<<1, 1, 0, st>>>(W.key, (uint32_t)seed, (uint32_t)(seed >> 32));
-    count_launch();
+    set_key(W, t, seed, st);
     LSM_CUDA(cudaGetLastError());
-    if (o.use_graph && !timing_enabled()) {
+    bool replayed = false;
+    if (o.use_graph) {
         // One CUDA graph per (plan, phantom, tally buffers, options): captured
         // on first use, replayed afterwards with only the key set outside it.
         // Capture and replay use the tally's own stream (the legacy default
@@ -1260,18 +1267,24 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         st = (cudaStream_t)t->gstream;
         LSM_CUDA(cudaEventRecord((cudaEvent_t)t->gev[0], caller));
         LSM_CUDA(cudaStreamWaitEvent(st, (cudaEvent_t)t->gev[0], 0));
-        GraphKey gk = {};
+        GraphKey gk;
+        memset(&gk, 0, sizeof(GraphKey));
+        gk.timed = timing_enabled() ? 1 : 0;
         gk.psl = P; gk.ph = ph; gk.part = t->d_part; gk.ws = t->ws; gk.batch = t->d_batch;
         gk.o = o;
         gk.o.n_batches = o.n_batches;
         if (!t->gexec || memcmp(&gk, &t->gkey, sizeof(GraphKey)) != 0) {
             memset(&t->gkey, 0, sizeof(GraphKey));
             if (t->gexec) { cudaGraphExecDestroy((cudaGraphExec_t)t->gexec); t->gexec = nullptr; }
+            timer_free(t->gtimers);
+            t->gtimers = nullptr;
             const int64_t l0 = lsm_launch_count();
+            const size_t tm0 = timer_mark();
             LSM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             rc = enqueue();
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamEndCapture(st, &g);
+            void *tset = timer_detach(tm0);
             if (rc == LSM_OK && ce != cudaSuccess) rc = set_cuda_error(ce, "lsm_run: graph capture");
             if (rc == LSM_OK) {
                 cudaGraphExec_t ge = nullptr;
@@ -1281,14 +1294,18 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
                     t->gexec = ge;
                     memcpy(&t->gkey, &gk, sizeof(GraphKey));
                     t->graph_kernels = lsm_launch_count() - l0;
+                    t->gtimers = tset;
+                    tset = nullptr;
                 }
             }
+            timer_free(tset);
             if (g) cudaGraphDestroy(g);
             if (rc) return rc;
         } else {
             add_launches(t->graph_kernels);
         }
         LSM_CUDA(cudaGraphLaunch((cudaGraphExec_t)t->gexec, st));
+        replayed = true;
         LSM_CUDA(cudaEventRecord((cudaEvent_t)t->gev[1], st));
         LSM_CUDA(cudaStreamWaitEvent(caller, (cudaEvent_t)t->gev[1], 0));
         st = caller;
@@ -1297,9 +1314,10 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         if (rc) return rc;
     }
     t->n_batches += o.n_batches;
-    if (rc == LSM_OK) rc = read_overflow(t, st, &ovf);
+    if (rc == LSM_OK) rc = read_overflow(t, W, st, &ovf);
     if (rc) return rc;
-    if (ovf > ovf0) return LSM_ERR_OVERFLOW;
+    if (replayed) timer_replayed(t->gtimers);
+    if (ovf) return LSM_ERR_OVERFLOW;
     return LSM_OK;
 }
 

@@ -438,8 +438,18 @@ TIMER_NAMES = ("psl_build", "sample", "photon", "annihilation_photon", "electron
                "phantom")
 
 
+_timing_on = False
+
+
 def lsm_timing_enable(on: bool = True):
+    global _timing_on
     _check(load_library().lsm_timing_enable(int(on)), "lsm_timing_enable")
+    _timing_on = bool(on)
+
+
+def timing_enabled() -> bool:
+    """Whether the library's per-kernel event timers are on (runs then skip graph replay)."""
+    return _timing_on
 
 
 def lsm_timing_read(reset: bool = True) -> dict:

@@ -267,6 +267,54 @@ def test_graph_replay_matches_direct_runs(L):
     assert not np.allclose(res[(True, 11)], res[(True, 12)])
 
 
+def test_graph_replay_keeps_kernel_timers(L):
+    """Timers captured into the graph are read after every replay: same kernel
+    groups and launch counts as a direct run."""
+    wl = W.workload_full_10x10(100_000)
+    g = L.lsm_build_psl(wl.model, wl.beams, wl.n_hist)
+    ph = L.lsm_phantom_create(wl.phantom)
+    t = L.lsm_tally_create(ph)
+    got = {}
+    L.lsm_timing_enable(True)
+    try:
+        for graph in (False, False, True, True):       # the first run also sizes the tally slices
+            L.lsm_timing_read(reset=True)
+            L.lsm_tally_reset(t)
+            L.lsm_run(g, ph, t, 3, L.RunOpts(n_batches=4, use_graph=graph))
+            got.setdefault(graph, []).append(L.lsm_timing_read(reset=True))
+    finally:
+        L.lsm_timing_enable(False)
+    direct, replays = got[False][1], got[True]
+    for rep in replays:
+        for k in ("sample", "photon", "electron", "tally"):
+            assert rep[k][1] == direct[k][1] > 0, k
+            assert rep[k][0] > 0, k
+
+
+def test_autotune_choice_and_cache(L, tmp_path):
+    from paper_1503_01725_b300 import autotune as A
+    wl = W.workload_full_10x10(400_000)
+    g = L.lsm_build_psl(wl.model, wl.beams, wl.n_hist // 8)
+    ph = L.lsm_phantom_create(wl.phantom)
+    t = L.lsm_tally_create(ph)
+    base = L.RunOpts(n_batches=8)
+    cache = str(tmp_path / "tune.json")
+    cands = A.candidates(wl.n_hist // 8, 8, ctas=(0, 2))
+    o, rep = A.tune(g, ph, t, base, reps=1, cands=cands, cache_path=cache)
+    assert not rep["cached"] and len(rep["trials"]) == len(cands)
+    assert (o.chunk, o.ctas_per_sm, o.use_graph) in cands
+    o2, rep2 = A.tune(g, ph, t, base, cache_path=cache)
+    assert rep2["cached"] and o2 == o
+    # the tuned options change the speed, not the histories
+    L.lsm_tally_reset(t)
+    L.lsm_run(g, ph, t, 9, base)
+    a = L.lsm_tally_read(t)[0]
+    L.lsm_tally_reset(t)
+    L.lsm_run(g, ph, t, 9, o)
+    b = L.lsm_tally_read(t)[0]
+    np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6 * a.max())
+
+
 def test_sample_then_transport_equals_run(L):
     import torch
     wl = W.workload_full_10x10(30_000)

@@ -54,3 +54,14 @@ def test_launch_counter_readable_without_gpu(lib):
     assert lib.lsm_launch_count() >= 0
     lib.lsm_last_error.restype = ctypes.c_char_p
     assert isinstance(lib.lsm_last_error(), bytes)
+
+
+def test_autotune_candidates():
+    from paper_1503_01725_b300 import autotune as A
+    c = A.candidates(625_000, 16, ctas=(0,), graphs=(False,))
+    chunks = [x[0] for x in c]
+    # whole-batch multiples of the plan: 1, 2, 4, 8, 16 batches per iteration
+    assert chunks == [625_000 * k for k in (1, 2, 4, 8, 16)]
+    big = A.candidates(50_000_000, 1, ctas=(0,), graphs=(False,))
+    assert [x[0] for x in big] == [1 << 21, 1 << 22, 1 << 23, 1 << 24]
+    assert all(x[0] <= A.MAX_CHUNK for x in A.candidates(3_000_000, 64))
