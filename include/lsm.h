@@ -362,12 +362,92 @@ lsm_status lsm_commission_static(const double *A, int32_t m, int32_t n, const do
  *   2 photon transport             3 annihilation-photon transport
  *   4 electron transport           5 tally flush and fold
  *   6 NNLS solve                   7 phantom set-up and tables
+ *   8 denoiser 3x3x3 convolutions  9 denoiser pooling, upsampling, input
+ *                                    packing and output head
  * lsm_timing_read synchronises the device, returns milliseconds and launch
  * counts per timer, and clears them when reset != 0. Disabled by default.
  */
-#define LSM_N_TIMERS 8
+#define LSM_N_TIMERS 10
 lsm_status lsm_timing_enable(int on);
 lsm_status lsm_timing_read(double ms[LSM_N_TIMERS], int64_t launches[LSM_N_TIMERS], int reset);
+
+/* ------------------------------------------------------------------------
+ * Dose denoiser. The paper stops at Monte Carlo dose (Sec. 2.3) and states
+ * run times for a target statistical uncertainty (Sec. 3); the denoiser maps a
+ * low-history dose and the phantom density to an estimate of the high-history
+ * dose. Network: a four-level 3D U-Net with widths 16/32/64/128, 3x3x3
+ * zero-padded convolutions with bias and ReLU, 2x2x2 max pooling, nearest 2x
+ * upsampling, skip concatenation (skip channels first) and a 1x1x1 head added
+ * to the input dose (residual). BF16 activations and weights, FP32
+ * accumulation in tensor memory (tcgen05), FP32 output.
+ *
+ * Activation volumes (lsm_vol) are device BF16 arrays laid out
+ * [n][(d+2)(h+2)(w+2)][c_total]: every volume carries a one-voxel zero halo,
+ * voxel (z, y, x) of the interior at padded index ((z+1)(h+2) + y+1)(w+2) + x+1.
+ * The halo must hold zeros; the kernels keep it so. A call uses channels
+ * [c_offset, c_offset + c) of each voxel. c_total and c_offset are multiples of
+ * 8; the base pointer is 16-byte aligned.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    void *data;
+    int32_t n, d, h, w;         /* volumes, interior size */
+    int32_t c_total, c_offset, c;
+} lsm_vol;
+
+/* Bytes of a padded activation volume (n * (d+2)(h+2)(w+2) * c_total * 2). */
+int64_t lsm_vol_bytes(int32_t n, int32_t d, int32_t h, int32_t w, int32_t c_total);
+
+typedef struct lsm_conv3d lsm_conv3d;
+/*
+ * lsm_conv3d_create -- one 3x3x3 convolution layer. weight: host FP32
+ * [c_out][3][3][3][c_in] indexed (dz, dy, dx) (cross-correlation: output
+ * voxel (z,y,x) takes input (z+dz-1, y+dy-1, x+dx-1)); bias: host FP32
+ * [c_out] (NULL = zero). Both are rounded to BF16 and packed into the
+ * tensor-core operand layout on the device; the caller's arrays are not kept.
+ * c_in and c_out in {16, 32, 64, 128}, relu 0/1.
+ * Errors: LSM_ERR_ARG for other sizes or NULL weight.
+ */
+lsm_status lsm_conv3d_create(int32_t c_in, int32_t c_out, int32_t relu, const float *weight, const float *bias,
+                             lsm_conv3d **out, lsm_stream stream);
+void lsm_conv3d_destroy(lsm_conv3d *conv);
+/*
+ * lsm_conv3d_forward -- out[:, c_offset : c_offset + c_out] = act(conv(in) +
+ * bias) over every interior voxel, written as BF16; the halo voxels of those
+ * output channels are written as zero. in->c must equal c_in and out->c
+ * c_out; n, d, h, w must match. Stream-ordered. ctas_per_sm: persistent CTAs
+ * per SM (0 = as many as fit).
+ */
+lsm_status lsm_conv3d_forward(const lsm_conv3d *conv, const lsm_vol *in, const lsm_vol *out, int32_t ctas_per_sm,
+                              lsm_stream stream);
+/* 2x2x2 max pooling (out = in / 2 in every dimension; in->c == out->c). */
+lsm_status lsm_pool3d(const lsm_vol *in, const lsm_vol *out, lsm_stream stream);
+/* Nearest 2x upsampling (out = 2 in in every dimension; in->c == out->c). */
+lsm_status lsm_upsample3d(const lsm_vol *in, const lsm_vol *out, lsm_stream stream);
+
+typedef struct lsm_unet lsm_unet;
+/* Number of FP32 parameters of the network: per conv layer (14, in network
+ * order) its weights [c_out][3][3][3][c_in] then its bias, then the head's 16
+ * weights and its bias. */
+int64_t lsm_unet_param_count(void);
+/* lsm_unet_create -- the network from a host FP32 parameter vector of
+ * lsm_unet_param_count() values (copied and packed; not kept). */
+lsm_status lsm_unet_create(const float *params, int64_t n_params, lsm_unet **out, lsm_stream stream);
+void lsm_unet_destroy(lsm_unet *net);
+/*
+ * lsm_unet_forward -- denoised dose of n volumes [n][d][h][w] (x fastest),
+ * d, h, w multiples of 8. dose and rho: FP32 (dose in any unit, rho in
+ * g/cm^3), out: FP32 in the unit of dose; all three host or device (mem).
+ * The input is normalised by each volume's maximum dose, the network runs in
+ * BF16 with FP32 accumulation, and out = dose + Dmax * head. Activation
+ * buffers are allocated on the first call for a shape and reused.
+ * Stream-ordered for device buffers; synchronises for host buffers.
+ */
+lsm_status lsm_unet_forward(lsm_unet *net, int32_t n, int32_t d, int32_t h, int32_t w, const float *dose,
+                            const float *rho, float *out, lsm_mem mem, lsm_stream stream);
+/* Copy the stored output of conv layer `layer` (0..13) of the last forward
+ * call, interior voxels only, as BF16 [n][d_l][h_l][w_l][c_out] into dst
+ * (host or device). */
+lsm_status lsm_unet_activation(const lsm_unet *net, int32_t layer, void *dst, lsm_mem mem, lsm_stream stream);
 
 /* Library diagnostics. */
 const char *lsm_last_error(void);

@@ -26,6 +26,7 @@ SOURCES = {
     "physics.cu": [],
     "transport.cu": [],
     "nnls.cu": [],
+    "denoise.cu": [],
 }
 
 

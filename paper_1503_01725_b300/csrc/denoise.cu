@@ -1,0 +1,986 @@
+// denoise.cu -- the dose denoiser: a BF16 3D U-Net on the tcgen05 tensor cores.
+//
+// A 3x3x3 convolution is an implicit GEMM D[m][o] = sum_k A[m][k] B[k][o]:
+// m runs over 128 consecutive voxels of the padded volume (one M tile), o over
+// output channels, k over (tap, input channel). Every activation volume keeps
+// a one-voxel zero halo, so each tap is a pure shift of the padded linear voxel
+// index by (dz-1) P + (dy-1) (w+2) + (dx-1), P = (h+2)(w+2). One pipeline stage
+// covers one input-channel chunk and one dz: TMA loads, per 8-channel group,
+// three slabs of 130 voxels (dy = 0, 1, 2, with one voxel of x halo on either
+// side), and the nine (dy, dx) taps of the stage are shared-memory descriptors
+// that start inside those slabs. The stage's weights arrive with one bulk copy,
+// already packed into the operand layout on the host. Accumulators are FP32 in
+// tensor memory, two per CTA so that the epilogue of one tile overlaps the MMAs
+// of the next; the epilogue adds the bias, applies ReLU, writes BF16 and zeroes
+// the halo voxels of the tile.
+//
+// Operand layout in shared memory (no swizzle, K-major): core matrices of 8
+// rows x 16 bytes with rows at a 16-byte pitch; SBO = 128 bytes between 8-row
+// groups, LBO between the two 8-element K halves of one K = 16 MMA.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+// ------------------------------------------------------------------ handles ---
+struct lsm_conv3d {
+    int cin, cout, relu, kc;
+    __nv_bfloat16 *wimg;      // packed operand images [cin/kc][dz][9 taps][cout x kc]
+    float *bias;              // [cout], values rounded to BF16
+};
+
+namespace lsm {
+namespace dn {
+
+constexpr int kTileM = 128;
+constexpr int kSlabVox = kTileM + 2;
+constexpr int kSlabBytes = kSlabVox * 16;       // one 8-channel group of a slab
+constexpr int kSlabPitch = 2176;                // 2080 rounded up to 128 bytes
+constexpr int kThreads = 192;                   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+template <int COUT, int KC>
+struct Cfg {
+    static constexpr int kA = KC / 8 * 3 * kSlabPitch;
+    static constexpr int kB = 9 * COUT * KC * 2;
+    static constexpr int kStage = kA + kB;
+    static constexpr int kFit = 100 * 1024 / kStage;
+    static constexpr int kStages = kFit < 2 ? 2 : (kFit > 8 ? 8 : kFit);
+    static constexpr int kTx = KC / 8 * 3 * kSlabBytes + kB;
+    static constexpr int kAccCols = COUT < 32 ? 32 : COUT;
+    static constexpr int kTmemCols = 2 * kAccCols;
+    static constexpr int kSmem = kStages * kStage + 1024;
+    static_assert(kStage % 128 == 0, "stage alignment");
+};
+
+struct ConvArgs {
+    const __nv_bfloat16 *wimg;
+    const float *bias;
+    __nv_bfloat16 *out;
+    long long lp;             // padded voxels per volume
+    long long l0;             // padded index of the first interior voxel
+    int out_ct, out_co, in_co;
+    int n_kc;
+    int w2, p;                // w + 2, (h + 2)(w + 2)
+    int d, h, w;
+    int tiles_per_vol, n_tiles;
+    int relu;
+    unsigned *err;
+};
+
+// ------------------------------------------------------------ PTX helpers ---
+__device__ __forceinline__ uint32_t s2u(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mb_init(uint64_t *b, unsigned n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s2u(b)), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void mb_expect(uint64_t *b, unsigned tx)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s2u(b)), "r"(tx) : "memory");
+}
+
+__device__ __forceinline__ void mb_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s2u(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mb_test(uint64_t *b, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(s2u(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of parity `parity` to complete. Bounded: after kWaitNs,
+// or when another role has given up, returns false; a timeout sets `code` in
+// *err and the CTA's abort flag.
+__device__ bool mb_wait(uint64_t *b, unsigned parity, volatile int *abort_flag, unsigned *err, unsigned code)
+{
+    if (mb_test(b, parity)) return true;
+    const unsigned long long t0 = gtime();
+    for (;;) {
+        if (mb_test(b, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtime() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicOr(err, code);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(s2u(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(s2u(bar))
+                 : "memory");
+}
+
+// shared-memory matrix descriptor: start, leading and stride byte offsets
+// (16-byte units), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s2u(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------ conv kernel ---
+template <int COUT, int KC>
+__global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ CUtensorMap tin, const ConvArgs a)
+{
+    using C = Cfg<COUT, KC>;
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[C::kStages], empty[C::kStages], accf[2], acce[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const uint32_t sbase = (s2u(dsm) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) {
+            mb_init(&full[s], 1);
+            mb_init(&empty[s], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mb_init(&accf[i], 1);
+            mb_init(&acce[i], 4);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s2u(&tmem_slot)),
+                     "r"(C::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = tmem_slot;
+    const int ksteps = a.n_kc * 3;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tin) : "memory");
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
+                const int vol = t / a.tiles_per_vol;
+                const long long lt = a.l0 + (long long)(t - vol * a.tiles_per_vol) * kTileM;
+                for (int k = 0; k < ksteps; ++k, ++it) {
+                    const int s = it % C::kStages;
+                    if (it >= C::kStages &&
+                        !mb_wait(&empty[s], (unsigned)((it / C::kStages) - 1) & 1u, &abort_flag, a.err, 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    const int kc = k / 3, dz = k - 3 * kc;
+                    const uint32_t sa = sbase + (uint32_t)(s * C::kStage), sb = sa + C::kA;
+                    mb_expect(&full[s], C::kTx);
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const int c1 = (int)(lt - 1 + (long long)(dz - 1) * a.p + (long long)(dy - 1) * a.w2);
+#pragma unroll
+                        for (int g = 0; g < KC / 8; ++g)
+                            tma_load_3d(sa + (uint32_t)((g * 3 + dy) * kSlabPitch), &tin, a.in_co + kc * KC + g * 8,
+                                        c1, vol, &full[s]);
+                    }
+                    bulk_load(sb, a.wimg + (size_t)(kc * 3 + dz) * 9 * COUT * KC, C::kB, &full[s]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            constexpr uint32_t idesc = (1u << 4)      // D: FP32
+                                       | (1u << 7)    // A: BF16
+                                       | (1u << 10)   // B: BF16
+                                       | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+            int it = 0, li = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x, ++li) {
+                const int acc = li & 1;
+                if (li >= 2 && !mb_wait(&acce[acc], (unsigned)((li >> 1) - 1) & 1u, &abort_flag, a.err, 2u)) break;
+                tc_after();
+                const uint32_t d = tmem + (uint32_t)(acc * C::kAccCols);
+                for (int k = 0; k < ksteps; ++k, ++it) {
+                    const int s = it % C::kStages;
+                    if (!mb_wait(&full[s], (unsigned)(it / C::kStages) & 1u, &abort_flag, a.err, 4u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_after();
+                    const uint32_t sa = sbase + (uint32_t)(s * C::kStage), sb = sa + C::kA;
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                            for (int j = 0; j < KC / 16; ++j) {
+                                const uint64_t ad =
+                                    sdesc(sa + (uint32_t)((2 * j * 3 + dy) * kSlabPitch + dx * 16), 3 * kSlabPitch, 128);
+                                const uint64_t bd = sdesc(
+                                    sb + (uint32_t)((dy * 3 + dx) * (COUT * KC * 2) + j * 2 * (COUT * 16)), COUT * 16,
+                                    128);
+                                mma_bf16(d, ad, bd, idesc, (k | dy | dx | j) != 0);
+                            }
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&accf[acc]);
+            }
+        }
+    } else {   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        const int q = warp & 3;
+        int li = 0;
+        for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++li) {
+            const int acc = li & 1;
+            const bool ok = mb_wait(&accf[acc], (unsigned)(li >> 1) & 1u, &abort_flag, a.err, 8u);
+            if (!__all_sync(0xFFFFFFFFu, ok)) break;
+            tc_after();
+            const int vol = t / a.tiles_per_vol;
+            const long long L = a.l0 + (long long)(t - vol * a.tiles_per_vol) * kTileM + 32 * q + lane;
+            const long long zz = L / a.p;
+            const int rem = (int)(L - zz * a.p);
+            const int yy = rem / a.w2, xx = rem - yy * a.w2;
+            const bool inside = zz >= 1 && zz <= a.d && yy >= 1 && yy <= a.h && xx >= 1 && xx <= a.w;
+            const bool write = L < a.lp;
+            __nv_bfloat16 *o = a.out + ((size_t)vol * (size_t)a.lp + (size_t)(write ? L : 0)) * a.out_ct + a.out_co;
+#pragma unroll
+            for (int c0 = 0; c0 < COUT; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * C::kAccCols + c0), r);
+                uint32_t pk[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float v0 = __uint_as_float(r[2 * i]) + __ldg(a.bias + c0 + 2 * i);
+                    float v1 = __uint_as_float(r[2 * i + 1]) + __ldg(a.bias + c0 + 2 * i + 1);
+                    if (a.relu) {
+                        v0 = fmaxf(v0, 0.0f);
+                        v1 = fmaxf(v1, 0.0f);
+                    }
+                    if (!inside) v0 = v1 = 0.0f;
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                    pk[i] = *reinterpret_cast<const uint32_t *>(&h2);
+                }
+                if (write) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(o + c0);
+                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+            }
+            tc_before();
+            __syncwarp();
+            if (lane == 0) mb_arrive(&acce[acc]);
+        }
+    }
+    __syncwarp();
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------- memory-bound kernels ---
+struct VolIdx {
+    int d, h, w;
+    long long lp;
+    int w2, p;
+    __host__ __device__ long long at(int b, int z, int y, int x) const
+    {
+        return (long long)b * lp + (long long)(z + 1) * p + (long long)(y + 1) * w2 + x + 1;
+    }
+};
+
+__host__ __device__ inline VolIdx vidx(int d, int h, int w)
+{
+    VolIdx v;
+    v.d = d; v.h = h; v.w = w;
+    v.w2 = w + 2;
+    v.p = (h + 2) * (w + 2);
+    v.lp = (long long)(d + 2) * v.p;
+    return v;
+}
+
+__device__ __forceinline__ uint4 max8(uint4 a, uint4 b)
+{
+    uint4 r;
+    const __nv_bfloat162 *x = reinterpret_cast<const __nv_bfloat162 *>(&a);
+    const __nv_bfloat162 *y = reinterpret_cast<const __nv_bfloat162 *>(&b);
+    __nv_bfloat162 *z = reinterpret_cast<__nv_bfloat162 *>(&r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) z[i] = __hmax2(x[i], y[i]);
+    return r;
+}
+
+// 2x2x2 max pooling; one thread per (output voxel, 8-channel group)
+__global__ void k_pool2(const __nv_bfloat16 *__restrict__ in, int in_ct, int in_co, __nv_bfloat16 *__restrict__ out,
+                        int out_ct, int out_co, int groups, int n, VolIdx vo, VolIdx vi)
+{
+    const long long total = (long long)n * vo.d * vo.h * vo.w * groups;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i % groups);
+        long long v = i / groups;
+        const int x = (int)(v % vo.w); v /= vo.w;
+        const int y = (int)(v % vo.h); v /= vo.h;
+        const int z = (int)(v % vo.d);
+        const int b = (int)(v / vo.d);
+        uint4 m = make_uint4(0xFF80FF80u, 0xFF80FF80u, 0xFF80FF80u, 0xFF80FF80u);   // -inf
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const long long src = vi.at(b, 2 * z + (c >> 2), 2 * y + ((c >> 1) & 1), 2 * x + (c & 1));
+            m = max8(m, *reinterpret_cast<const uint4 *>(in + src * in_ct + in_co + 8 * g));
+        }
+        *reinterpret_cast<uint4 *>(out + vo.at(b, z, y, x) * out_ct + out_co + 8 * g) = m;
+    }
+}
+
+// nearest 2x upsampling; one thread per (output voxel, 8-channel group)
+__global__ void k_up2(const __nv_bfloat16 *__restrict__ in, int in_ct, int in_co, __nv_bfloat16 *__restrict__ out,
+                      int out_ct, int out_co, int groups, int n, VolIdx vo, VolIdx vi)
+{
+    const long long total = (long long)n * vo.d * vo.h * vo.w * groups;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i % groups);
+        long long v = i / groups;
+        const int x = (int)(v % vo.w); v /= vo.w;
+        const int y = (int)(v % vo.h); v /= vo.h;
+        const int z = (int)(v % vo.d);
+        const int b = (int)(v / vo.d);
+        *reinterpret_cast<uint4 *>(out + vo.at(b, z, y, x) * out_ct + out_co + 8 * g) =
+            *reinterpret_cast<const uint4 *>(in + vi.at(b, z >> 1, y >> 1, x >> 1) * in_ct + in_co + 8 * g);
+    }
+}
+
+// per-volume maximum of a non-negative FP32 dose (float bits compare as ints)
+__global__ void k_dmax(const float *__restrict__ dose, long long per_vol, int n, unsigned *dmax_bits)
+{
+    for (int b = blockIdx.y; b < n; b += gridDim.y) {
+        unsigned m = 0;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per_vol;
+             i += (long long)gridDim.x * blockDim.x)
+            m = max(m, __float_as_uint(fmaxf(dose[(long long)b * per_vol + i], 0.0f)));
+        for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(dmax_bits + b, m);
+    }
+}
+
+// input volume: channel 0 dose / Dmax, channel 1 density, channels 2-15 zero
+__global__ void k_pack_input(const float *__restrict__ dose, const float *__restrict__ rho,
+                             const unsigned *__restrict__ dmax_bits, __nv_bfloat16 *__restrict__ x, int n, VolIdx v)
+{
+    const long long per = (long long)v.d * v.h * v.w, total = per * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / per);
+        long long r = i - (long long)b * per;
+        const int xx = (int)(r % v.w); r /= v.w;
+        const int yy = (int)(r % v.h);
+        const int zz = (int)(r / v.h);
+        const double dm = (double)__uint_as_float(dmax_bits[b]);
+        const double sc = dm > 0.0 ? 1.0 / dm : 0.0;
+        const float d0 = __double2float_rn((double)dose[i] * sc);
+        const __nv_bfloat162 h = __halves2bfloat162(__float2bfloat16_rn(d0), __float2bfloat16_rn(rho[i]));
+        uint4 *dst = reinterpret_cast<uint4 *>(x + v.at(b, zz, yy, xx) * 16);
+        dst[0] = make_uint4(*reinterpret_cast<const uint32_t *>(&h), 0u, 0u, 0u);
+        dst[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// out = dose + Dmax * (sum_c hw[c] d0[c] + hb)
+__global__ void k_head(const __nv_bfloat16 *__restrict__ d0, int ct, const float *__restrict__ hw,
+                       const float *__restrict__ dose, const unsigned *__restrict__ dmax_bits, float *__restrict__ out,
+                       int n, VolIdx v)
+{
+    const long long per = (long long)v.d * v.h * v.w, total = per * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / per);
+        long long r = i - (long long)b * per;
+        const int xx = (int)(r % v.w); r /= v.w;
+        const int yy = (int)(r % v.h);
+        const int zz = (int)(r / v.h);
+        const uint4 *src = reinterpret_cast<const uint4 *>(d0 + v.at(b, zz, yy, xx) * ct);
+        float acc = hw[16];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint4 u = src[k];
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = __bfloat1622float2(h[j]);
+                acc += hw[8 * k + 2 * j] * f.x + hw[8 * k + 2 * j + 1] * f.y;
+            }
+        }
+        out[i] = dose[i] + __uint_as_float(dmax_bits[b]) * acc;
+    }
+}
+
+// interior voxels of channels [co, co + c) -> dense [n][d][h][w][c]
+__global__ void k_extract(const __nv_bfloat16 *__restrict__ in, int ct, int co, int c, __nv_bfloat16 *__restrict__ dst,
+                          int n, VolIdx v)
+{
+    const long long per = (long long)v.d * v.h * v.w, total = per * n * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        long long r = i / c;
+        const int b = (int)(r / per);
+        r -= (long long)b * per;
+        const int xx = (int)(r % v.w); r /= v.w;
+        const int yy = (int)(r % v.h);
+        const int zz = (int)(r / v.h);
+        dst[i] = in[v.at(b, zz, yy, xx) * ct + co + ch];
+    }
+}
+
+// ------------------------------------------------------------------- host ---
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn()
+{
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+    }
+    return fn;
+}
+
+unsigned *g_err_word = nullptr;
+unsigned *err_word()
+{
+    if (!g_err_word) {
+        if (cudaMalloc(&g_err_word, 16) != cudaSuccess) return nullptr;
+        cudaMemset(g_err_word, 0, 16);
+    }
+    return g_err_word;
+}
+
+lsm_status check_vol(const lsm_vol *v, const char *what)
+{
+    char msg[160];
+    if (!v || !v->data) {
+        snprintf(msg, sizeof msg, "%s: NULL volume", what);
+        return set_arg_error(msg);
+    }
+    if (v->n < 1 || v->d < 1 || v->h < 1 || v->w < 1 || v->c_total < 8 || v->c_total % 8 || v->c_offset < 0 ||
+        v->c_offset % 8 || v->c < 8 || v->c % 8 || v->c_offset + v->c > v->c_total ||
+        ((uintptr_t)v->data & 15)) {
+        snprintf(msg, sizeof msg, "%s: bad volume (sizes >= 1; channels multiples of 8 within c_total; 16-byte base)",
+                 what);
+        return set_arg_error(msg);
+    }
+    return LSM_OK;
+}
+
+template <int COUT, int KC>
+lsm_status launch_conv(const CUtensorMap &map, const ConvArgs &a, int ctas_per_sm, cudaStream_t st)
+{
+    using C = Cfg<COUT, KC>;
+    static int occ = 0;
+    if (!occ) {
+        LSM_CUDA(cudaFuncSetAttribute(k_conv3d<COUT, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+        LSM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3d<COUT, KC>, kThreads, C::kSmem));
+        if (occ < 1) occ = 1;
+    }
+    const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+    const int grid = std::max(1, std::min(a.n_tiles, per_sm * sm_count()));
+    k_conv3d<COUT, KC><<<grid, kThreads, C::kSmem, st>>>(map, a);
+    count_launch();
+    LSM_CUDA(cudaGetLastError());
+    return LSM_OK;
+}
+
+int kc_for(int cin, int cout)
+{
+    const int kmax = cout >= 128 ? 16 : 32;
+    return std::min(cin, kmax);
+}
+
+lsm_status conv_forward(const lsm_conv3d *cv, const lsm_vol *in, const lsm_vol *out, int ctas_per_sm,
+                        cudaStream_t st)
+{
+    if (!cv) return set_arg_error("lsm_conv3d_forward: NULL layer");
+    lsm_status rc = check_vol(in, "lsm_conv3d_forward input");
+    if (rc) return rc;
+    if ((rc = check_vol(out, "lsm_conv3d_forward output"))) return rc;
+    if (in->n != out->n || in->d != out->d || in->h != out->h || in->w != out->w)
+        return set_arg_error("lsm_conv3d_forward: input and output sizes differ");
+    if (in->c != cv->cin || out->c != cv->cout) return set_arg_error("lsm_conv3d_forward: channel counts");
+    const VolIdx v = vidx(in->d, in->h, in->w);
+    if (v.lp >= (1ll << 31) - 4096) return set_arg_error("lsm_conv3d_forward: volume too large");
+    EncodeTiled enc = encode_fn();
+    if (!enc) return set_arg_error("lsm_conv3d_forward: cuTensorMapEncodeTiled unavailable");
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)in->c_total, (cuuint64_t)v.lp, (cuuint64_t)in->n};
+    const cuuint64_t strides[2] = {(cuuint64_t)in->c_total * 2, (cuuint64_t)v.lp * in->c_total * 2};
+    const cuuint32_t box[3] = {8, (cuuint32_t)kSlabVox, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, in->data, dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+        char msg[96];
+        snprintf(msg, sizeof msg, "lsm_conv3d_forward: tensor map encoding failed (%d)", (int)cr);
+        return set_arg_error(msg);
+    }
+    unsigned *err = err_word();
+    if (!err) return set_cuda_error(cudaErrorMemoryAllocation, "lsm_conv3d_forward: error word");
+    ConvArgs a;
+    a.wimg = cv->wimg;
+    a.bias = cv->bias;
+    a.out = (__nv_bfloat16 *)out->data;
+    a.lp = v.lp;
+    a.l0 = (long long)v.p + v.w2 + 1;
+    const long long llast = (long long)in->d * v.p + (long long)in->h * v.w2 + in->w;
+    a.tiles_per_vol = (int)((llast - a.l0 + kTileM) / kTileM);
+    a.n_tiles = a.tiles_per_vol * in->n;
+    a.out_ct = out->c_total;
+    a.out_co = out->c_offset;
+    a.in_co = in->c_offset;
+    a.n_kc = cv->cin / cv->kc;
+    a.w2 = v.w2;
+    a.p = v.p;
+    a.d = in->d; a.h = in->h; a.w = in->w;
+    a.relu = cv->relu;
+    a.err = err;
+    const int tk = timer_begin(8, st);
+    lsm_status r = LSM_ERR_ARG;
+    switch (cv->cout * 1000 + cv->kc) {
+    case 16016: r = launch_conv<16, 16>(map, a, ctas_per_sm, st); break;
+    case 16032: r = launch_conv<16, 32>(map, a, ctas_per_sm, st); break;
+    case 32016: r = launch_conv<32, 16>(map, a, ctas_per_sm, st); break;
+    case 32032: r = launch_conv<32, 32>(map, a, ctas_per_sm, st); break;
+    case 64016: r = launch_conv<64, 16>(map, a, ctas_per_sm, st); break;
+    case 64032: r = launch_conv<64, 32>(map, a, ctas_per_sm, st); break;
+    case 128016: r = launch_conv<128, 16>(map, a, ctas_per_sm, st); break;
+    default: set_arg_error("lsm_conv3d_forward: unsupported channel configuration");
+    }
+    timer_end(tk, st);
+    return r;
+}
+
+lsm_status conv_create(int cin, int cout, int relu, const float *w, const float *b, lsm_conv3d **out,
+                       cudaStream_t st)
+{
+    if (!out || !w) return set_arg_error("lsm_conv3d_create: NULL argument");
+    auto okc = [](int c) { return c == 16 || c == 32 || c == 64 || c == 128; };
+    if (!okc(cin) || !okc(cout)) return set_arg_error("lsm_conv3d_create: channels must be 16, 32, 64 or 128");
+    const int kc = kc_for(cin, cout);
+    const size_t nw = (size_t)27 * cin * cout;
+    std::vector<__nv_bfloat16> img(nw);
+    for (int c = 0; c < cin / kc; ++c)
+        for (int dz = 0; dz < 3; ++dz)
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap % 3;
+                const size_t blk = (size_t)((c * 3 + dz) * 9 + tap) * cout * kc;
+                for (int n = 0; n < cout; ++n)
+                    for (int k = 0; k < kc; ++k) {
+                        const size_t off = (size_t)(k / 8) * cout * 8 + (size_t)(n / 8) * 64 + (n % 8) * 8 + (k % 8);
+                        img[blk + off] =
+                            __float2bfloat16_rn(w[((((size_t)n * 3 + dz) * 3 + dy) * 3 + dx) * cin + c * kc + k]);
+                    }
+            }
+    std::vector<float> bias(cout, 0.0f);
+    for (int n = 0; n < cout && b; ++n) bias[n] = __bfloat162float(__float2bfloat16_rn(b[n]));
+    lsm_conv3d *cv = (lsm_conv3d *)calloc(1, sizeof(lsm_conv3d));
+    if (!cv) return set_arg_error("lsm_conv3d_create: out of host memory");
+    cv->cin = cin; cv->cout = cout; cv->relu = relu ? 1 : 0; cv->kc = kc;
+    cudaError_t e = cudaMalloc(&cv->wimg, nw * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&cv->bias, (size_t)cout * 4);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cv->wimg, img.data(), nw * 2, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cv->bias, bias.data(), (size_t)cout * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(cv->wimg);
+        cudaFree(cv->bias);
+        free(cv);
+        return set_cuda_error(e, "lsm_conv3d_create");
+    }
+    *out = cv;
+    return LSM_OK;
+}
+
+void conv_destroy(lsm_conv3d *cv)
+{
+    if (!cv) return;
+    cudaFree(cv->wimg);
+    cudaFree(cv->bias);
+    free(cv);
+}
+
+int grid_1d(long long work)
+{
+    return (int)std::max<long long>(1, std::min<long long>((work + 255) / 256, 16ll * sm_count()));
+}
+
+lsm_status pool_or_up(const lsm_vol *in, const lsm_vol *out, bool up, cudaStream_t st)
+{
+    const char *name = up ? "lsm_upsample3d" : "lsm_pool3d";
+    lsm_status rc = check_vol(in, name);
+    if (rc) return rc;
+    if ((rc = check_vol(out, name))) return rc;
+    const bool sizes = up ? (out->d == 2 * in->d && out->h == 2 * in->h && out->w == 2 * in->w)
+                          : (in->d == 2 * out->d && in->h == 2 * out->h && in->w == 2 * out->w);
+    if (!sizes || in->n != out->n || in->c != out->c) {
+        char msg[96];
+        snprintf(msg, sizeof msg, "%s: sizes must halve/double and channel counts match", name);
+        return set_arg_error(msg);
+    }
+    const VolIdx vi = vidx(in->d, in->h, in->w), vo = vidx(out->d, out->h, out->w);
+    const int groups = in->c / 8;
+    const long long work = (long long)out->n * out->d * out->h * out->w * groups;
+    const int tk = timer_begin(9, st);
+    if (up)
+        k_up2<<<grid_1d(work), 256, 0, st>>>((const __nv_bfloat16 *)in->data, in->c_total, in->c_offset,
+                                              (__nv_bfloat16 *)out->data, out->c_total, out->c_offset, groups, out->n,
+                                              vo, vi);
+    else
+        k_pool2<<<grid_1d(work), 256, 0, st>>>((const __nv_bfloat16 *)in->data, in->c_total, in->c_offset,
+                                                (__nv_bfloat16 *)out->data, out->c_total, out->c_offset, groups,
+                                                out->n, vo, vi);
+    count_launch();
+    timer_end(tk, st);
+    LSM_CUDA(cudaGetLastError());
+    return LSM_OK;
+}
+
+}  // namespace dn
+}  // namespace lsm
+
+// ------------------------------------------------------------------ U-Net ---
+namespace {
+constexpr int kW0 = 16, kW1 = 32, kW2 = 64, kW3 = 128;
+// (c_in, c_out) of the 14 conv layers in network order
+constexpr int kLayers[14][2] = {{16, kW0},      {kW0, kW0}, {kW0, kW1}, {kW1, kW1}, {kW1, kW2},
+                                {kW2, kW2},     {kW2, kW3}, {kW3, kW2}, {2 * kW2, kW2}, {kW2, kW1},
+                                {2 * kW1, kW1}, {kW1, kW0}, {2 * kW0, kW0}, {kW0, kW0}};
+enum Buf { X0, T0, S0, P1, T1, S1, P2, T2, S2, P3, T3, B3, D2A, D2, D1A, D1, D0A, D0, NBUF };
+constexpr int kBufLevel[NBUF] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 2, 2, 1, 1, 0, 0};
+constexpr int kBufCh[NBUF] = {16, kW0, 2 * kW0, kW0, kW1, 2 * kW1, kW1, kW2, 2 * kW2, kW2, kW3, kW2,
+                              kW2, kW1, kW1, kW0, kW0, kW0};
+// conv layer i: input buffer (channel offset 0, all of its channels) and output (buffer, channel offset)
+constexpr int kConvIn[14] = {X0, T0, P1, T1, P2, T2, P3, T3, S2, D2A, S1, D1A, S0, D0A};
+constexpr int kConvOut[14] = {T0, S0, T1, S1, T2, S2, T3, B3, D2A, D2, D1A, D1, D0A, D0};
+
+int64_t param_count()
+{
+    int64_t n = 0;
+    for (auto &l : kLayers) n += 27ll * l[0] * l[1] + l[1];
+    return n + kW0 + 1;
+}
+}  // namespace
+
+struct lsm_unet {
+    lsm_conv3d *conv[14];
+    float *head;              // device [17]
+    int n, d, h, w;           // shape the buffers are allocated for
+    void *arena;
+    lsm_vol vol[NBUF];
+    unsigned *dmax;           // [n] FP32 bits
+    float *io;                // device staging for host calls: dose, rho, out
+    size_t io_cap;
+};
+
+namespace lsm {
+namespace dn {
+
+lsm_status unet_buffers(lsm_unet *u, int n, int d, int h, int w, cudaStream_t st)
+{
+    if (u->arena && u->n == n && u->d == d && u->h == h && u->w == w) return LSM_OK;
+    LSM_CUDA(cudaStreamSynchronize(st));
+    cudaFree(u->arena);
+    cudaFree(u->dmax);
+    u->arena = nullptr;
+    u->dmax = nullptr;
+    size_t off[NBUF], total = 0;
+    for (int b = 0; b < NBUF; ++b) {
+        const int L = kBufLevel[b];
+        off[b] = total;
+        total += ((size_t)lsm_vol_bytes(n, d >> L, h >> L, w >> L, kBufCh[b]) + 255) / 256 * 256;
+    }
+    LSM_CUDA(cudaMalloc(&u->arena, total));
+    LSM_CUDA(cudaMalloc(&u->dmax, (size_t)n * 4));
+    LSM_CUDA(cudaMemsetAsync(u->arena, 0, total, st));
+    for (int b = 0; b < NBUF; ++b) {
+        const int L = kBufLevel[b];
+        lsm_vol &v = u->vol[b];
+        v.data = (char *)u->arena + off[b];
+        v.n = n; v.d = d >> L; v.h = h >> L; v.w = w >> L;
+        v.c_total = kBufCh[b]; v.c_offset = 0; v.c = kBufCh[b];
+    }
+    u->n = n; u->d = d; u->h = h; u->w = w;
+    return LSM_OK;
+}
+
+lsm_vol sub(const lsm_vol &v, int c_offset, int c)
+{
+    lsm_vol r = v;
+    r.c_offset = c_offset;
+    r.c = c;
+    return r;
+}
+
+lsm_status unet_run(lsm_unet *u, const float *dose, const float *rho, float *out, cudaStream_t st)
+{
+    lsm_vol *V = u->vol;
+    const VolIdx v0 = vidx(u->d, u->h, u->w);
+    const long long per = (long long)u->d * u->h * u->w;
+    const int tk = timer_begin(9, st);
+    LSM_CUDA(cudaMemsetAsync(u->dmax, 0, (size_t)u->n * 4, st));
+    k_dmax<<<dim3(grid_1d(per) / 4 + 1, std::min(u->n, 64)), 256, 0, st>>>(dose, per, u->n, u->dmax);
+    count_launch();
+    k_pack_input<<<grid_1d(per * u->n), 256, 0, st>>>(dose, rho, u->dmax, (__nv_bfloat16 *)V[X0].data, u->n, v0);
+    count_launch();
+    timer_end(tk, st);
+    LSM_CUDA(cudaGetLastError());
+    lsm_status rc = LSM_OK;
+    auto conv = [&](int i) -> lsm_status {
+        const lsm_vol in = V[kConvIn[i]];
+        const lsm_vol o = sub(V[kConvOut[i]], 0, kLayers[i][1]);
+        return conv_forward(u->conv[i], &in, &o, 0, st);
+    };
+    auto pool = [&](int from, int to, int c) -> lsm_status {
+        const lsm_vol a = sub(V[from], 0, c);
+        return pool_or_up(&a, &V[to], false, st);
+    };
+    auto up = [&](int from, int to, int c_off) -> lsm_status {
+        const lsm_vol b = sub(V[to], c_off, V[from].c);
+        return pool_or_up(&V[from], &b, true, st);
+    };
+    if (!rc) rc = conv(0);
+    if (!rc) rc = conv(1);
+    if (!rc) rc = pool(S0, P1, kW0);
+    if (!rc) rc = conv(2);
+    if (!rc) rc = conv(3);
+    if (!rc) rc = pool(S1, P2, kW1);
+    if (!rc) rc = conv(4);
+    if (!rc) rc = conv(5);
+    if (!rc) rc = pool(S2, P3, kW2);
+    if (!rc) rc = conv(6);
+    if (!rc) rc = conv(7);
+    if (!rc) rc = up(B3, S2, kW2);
+    if (!rc) rc = conv(8);
+    if (!rc) rc = conv(9);
+    if (!rc) rc = up(D2, S1, kW1);
+    if (!rc) rc = conv(10);
+    if (!rc) rc = conv(11);
+    if (!rc) rc = up(D1, S0, kW0);
+    if (!rc) rc = conv(12);
+    if (!rc) rc = conv(13);
+    if (rc) return rc;
+    const int th = timer_begin(9, st);
+    k_head<<<grid_1d(per * u->n), 256, 0, st>>>((const __nv_bfloat16 *)V[D0].data, V[D0].c_total, u->head, dose,
+                                                u->dmax, out, u->n, v0);
+    count_launch();
+    timer_end(th, st);
+    LSM_CUDA(cudaGetLastError());
+    return LSM_OK;
+}
+
+}  // namespace dn
+}  // namespace lsm
+
+using namespace lsm;
+
+extern "C" {
+
+int64_t lsm_vol_bytes(int32_t n, int32_t d, int32_t h, int32_t w, int32_t c_total)
+{
+    if (n < 1 || d < 1 || h < 1 || w < 1 || c_total < 1) return 0;
+    return (int64_t)n * (d + 2) * (int64_t)(h + 2) * (w + 2) * c_total * 2;
+}
+
+lsm_status lsm_conv3d_create(int32_t c_in, int32_t c_out, int32_t relu, const float *weight, const float *bias,
+                             lsm_conv3d **out, lsm_stream stream)
+{
+    return dn::conv_create(c_in, c_out, relu, weight, bias, out, (cudaStream_t)stream);
+}
+
+void lsm_conv3d_destroy(lsm_conv3d *conv) { dn::conv_destroy(conv); }
+
+lsm_status lsm_conv3d_forward(const lsm_conv3d *conv, const lsm_vol *in, const lsm_vol *out, int32_t ctas_per_sm,
+                              lsm_stream stream)
+{
+    return dn::conv_forward(conv, in, out, ctas_per_sm, (cudaStream_t)stream);
+}
+
+lsm_status lsm_pool3d(const lsm_vol *in, const lsm_vol *out, lsm_stream stream)
+{
+    return dn::pool_or_up(in, out, false, (cudaStream_t)stream);
+}
+
+lsm_status lsm_upsample3d(const lsm_vol *in, const lsm_vol *out, lsm_stream stream)
+{
+    return dn::pool_or_up(in, out, true, (cudaStream_t)stream);
+}
+
+int64_t lsm_unet_param_count(void) { return param_count(); }
+
+lsm_status lsm_unet_create(const float *params, int64_t n_params, lsm_unet **out, lsm_stream stream)
+{
+    if (!params || !out) return set_arg_error("lsm_unet_create: NULL argument");
+    if (n_params != param_count()) return set_arg_error("lsm_unet_create: wrong parameter count");
+    lsm_unet *u = (lsm_unet *)calloc(1, sizeof(lsm_unet));
+    if (!u) return set_arg_error("lsm_unet_create: out of host memory");
+    const cudaStream_t st = (cudaStream_t)stream;
+    const float *p = params;
+    lsm_status rc = LSM_OK;
+    for (int i = 0; i < 14 && !rc; ++i) {
+        const int ci = kLayers[i][0], co = kLayers[i][1];
+        rc = dn::conv_create(ci, co, 1, p, p + 27ll * ci * co, &u->conv[i], st);
+        p += 27ll * ci * co + co;
+    }
+    if (!rc) {
+        cudaError_t e = cudaMalloc(&u->head, 17 * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpy(u->head, p, 17 * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = set_cuda_error(e, "lsm_unet_create");
+    }
+    if (rc) {
+        lsm_unet_destroy(u);
+        return rc;
+    }
+    *out = u;
+    return LSM_OK;
+}
+
+void lsm_unet_destroy(lsm_unet *u)
+{
+    if (!u) return;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 14; ++i) dn::conv_destroy(u->conv[i]);
+    cudaFree(u->head);
+    cudaFree(u->arena);
+    cudaFree(u->dmax);
+    cudaFree(u->io);
+    free(u);
+}
+
+lsm_status lsm_unet_forward(lsm_unet *u, int32_t n, int32_t d, int32_t h, int32_t w, const float *dose,
+                            const float *rho, float *out, lsm_mem mem, lsm_stream stream)
+{
+    if (!u || !dose || !rho || !out) return set_arg_error("lsm_unet_forward: NULL argument");
+    if (n < 1 || d < 8 || h < 8 || w < 8 || d % 8 || h % 8 || w % 8)
+        return set_arg_error("lsm_unet_forward: n >= 1 and d, h, w positive multiples of 8");
+    const cudaStream_t st = (cudaStream_t)stream;
+    lsm_status rc = dn::unet_buffers(u, n, d, h, w, st);
+    if (rc) return rc;
+    const size_t nv = (size_t)n * d * h * w;
+    if (mem == LSM_MEM_DEVICE) return dn::unet_run(u, dose, rho, out, st);
+    if (u->io_cap < nv) {
+        LSM_CUDA(cudaStreamSynchronize(st));
+        cudaFree(u->io);
+        u->io = nullptr;
+        u->io_cap = 0;
+        LSM_CUDA(cudaMalloc(&u->io, 3 * nv * sizeof(float)));
+        u->io_cap = nv;
+    }
+    LSM_CUDA(cudaMemcpyAsync(u->io, dose, nv * 4, cudaMemcpyHostToDevice, st));
+    LSM_CUDA(cudaMemcpyAsync(u->io + nv, rho, nv * 4, cudaMemcpyHostToDevice, st));
+    rc = dn::unet_run(u, u->io, u->io + nv, u->io + 2 * nv, st);
+    if (rc) return rc;
+    LSM_CUDA(cudaMemcpyAsync(out, u->io + 2 * nv, nv * 4, cudaMemcpyDeviceToHost, st));
+    unsigned err = 0;
+    LSM_CUDA(cudaMemcpyAsync(&err, dn::err_word(), 4, cudaMemcpyDeviceToHost, st));
+    LSM_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+        cudaMemsetAsync(dn::err_word(), 0, 4, st);
+        set_arg_error("lsm_unet_forward: a tensor-core pipeline wait timed out");
+        return LSM_ERR_TIMEOUT;
+    }
+    return LSM_OK;
+}
+
+lsm_status lsm_unet_activation(const lsm_unet *u, int32_t layer, void *dst, lsm_mem mem, lsm_stream stream)
+{
+    if (!u || !dst) return set_arg_error("lsm_unet_activation: NULL argument");
+    if (layer < 0 || layer >= 14) return set_arg_error("lsm_unet_activation: layer in 0..13");
+    if (!u->arena) return set_arg_error("lsm_unet_activation: no forward call yet");
+    const cudaStream_t st = (cudaStream_t)stream;
+    const lsm_vol &v = u->vol[kConvOut[layer]];
+    const int c = kLayers[layer][1];
+    const size_t count = (size_t)v.n * v.d * v.h * v.w * c;
+    void *tmp = dst;
+    if (mem == LSM_MEM_HOST) LSM_CUDA(cudaMalloc(&tmp, count * 2));
+    dn::k_extract<<<dn::grid_1d((long long)count), 256, 0, st>>>((const __nv_bfloat16 *)v.data, v.c_total, 0, c,
+                                                                 (__nv_bfloat16 *)tmp, v.n, dn::vidx(v.d, v.h, v.w));
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && mem == LSM_MEM_HOST) {
+        e = cudaMemcpyAsync(dst, tmp, count * 2, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) return set_cuda_error(e, "lsm_unet_activation");
+    return LSM_OK;
+}
+
+}  // extern "C"

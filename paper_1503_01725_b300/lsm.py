@@ -75,6 +75,11 @@ class lsm_nnls_report(C.Structure):
                 ("kkt", C.c_double)]
 
 
+class lsm_vol(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("n", C.c_int32), ("d", C.c_int32), ("h", C.c_int32), ("w", C.c_int32),
+                ("c_total", C.c_int32), ("c_offset", C.c_int32), ("c", C.c_int32)]
+
+
 _EXPORTS = {
     "lsm_build_psl": (C.c_int, [C.POINTER(lsm_psr_model), C.POINTER(lsm_beams), C.c_int64,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.c_void_p]),
@@ -108,6 +113,19 @@ _EXPORTS = {
     "lsm_commission_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                         C.POINTER(lsm_nnls_opts), C.c_void_p, C.POINTER(lsm_nnls_report),
                                         C.c_void_p]),
+    "lsm_vol_bytes": (C.c_int64, [C.c_int32] * 5),
+    "lsm_conv3d_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                    C.POINTER(C.c_void_p), C.c_void_p]),
+    "lsm_conv3d_destroy": (None, [C.c_void_p]),
+    "lsm_conv3d_forward": (C.c_int, [C.c_void_p, C.POINTER(lsm_vol), C.POINTER(lsm_vol), C.c_int32, C.c_void_p]),
+    "lsm_pool3d": (C.c_int, [C.POINTER(lsm_vol), C.POINTER(lsm_vol), C.c_void_p]),
+    "lsm_upsample3d": (C.c_int, [C.POINTER(lsm_vol), C.POINTER(lsm_vol), C.c_void_p]),
+    "lsm_unet_param_count": (C.c_int64, []),
+    "lsm_unet_create": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_void_p), C.c_void_p]),
+    "lsm_unet_destroy": (None, [C.c_void_p]),
+    "lsm_unet_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "lsm_unet_activation": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int, C.c_void_p]),
     "lsm_timing_enable": (C.c_int, [C.c_int]),
     "lsm_timing_read": (C.c_int, [_dp, C.POINTER(C.c_int64), C.c_int]),
     "lsm_last_error": (C.c_char_p, []),
@@ -435,7 +453,7 @@ def lsm_commission_static(A, b, x, method: int = 0, max_iter: int = 0, delta: fl
 
 
 TIMER_NAMES = ("psl_build", "sample", "photon", "annihilation_photon", "electron", "tally", "nnls",
-               "phantom")
+               "phantom", "conv3d", "denoise_other")
 
 
 _timing_on = False
@@ -453,8 +471,8 @@ def timing_enabled() -> bool:
 
 
 def lsm_timing_read(reset: bool = True) -> dict:
-    ms = np.zeros(8)
-    n = np.zeros(8, dtype=np.int64)
+    ms = np.zeros(len(TIMER_NAMES))
+    n = np.zeros(len(TIMER_NAMES), dtype=np.int64)
     _check(_lib.lsm_timing_read(ms.ctypes.data_as(_dp), n.ctypes.data_as(C.POINTER(C.c_int64)), int(reset)),
            "lsm_timing_read")
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(TIMER_NAMES)}
@@ -466,3 +484,100 @@ def lsm_launch_count() -> int:
 
 def exported_symbols() -> list[str]:
     return list(_EXPORTS)
+
+
+# ---------------------------------------------------------------- denoiser ---
+class Conv3d(Handle):
+    _destroy = "lsm_conv3d_destroy"
+
+
+class UNet(Handle):
+    _destroy = "lsm_unet_destroy"
+
+
+def alloc_vol(n: int, d: int, h: int, w: int, c_total: int):
+    """Zeroed padded BF16 activation volume [n][d+2][h+2][w+2][c_total] on the device."""
+    import torch
+    return torch.zeros((n, d + 2, h + 2, w + 2, c_total), dtype=torch.bfloat16, device="cuda")
+
+
+def vol(t, c_offset: int = 0, c: int | None = None) -> lsm_vol:
+    """lsm_vol of a padded activation tensor made by alloc_vol (channels [c_offset, c_offset + c))."""
+    n, d2, h2, w2, ct = t.shape
+    assert t.is_contiguous() and t.dtype.itemsize == 2
+    return lsm_vol(data=t.data_ptr(), n=n, d=d2 - 2, h=h2 - 2, w=w2 - 2, c_total=ct, c_offset=c_offset,
+                   c=ct - c_offset if c is None else c)
+
+
+def lsm_vol_bytes(n: int, d: int, h: int, w: int, c_total: int) -> int:
+    return int(load_library(require_gpu=False).lsm_vol_bytes(n, d, h, w, c_total))
+
+
+def lsm_conv3d_create(c_in: int, c_out: int, weight, bias=None, relu: bool = True, stream=None) -> Conv3d:
+    """weight: [c_out, 3, 3, 3, c_in] (dz, dy, dx), bias: [c_out]; host arrays."""
+    L = load_library()
+    w = np.ascontiguousarray(weight, dtype=np.float32)
+    assert w.shape == (c_out, 3, 3, 3, c_in)
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float32)
+    out = C.c_void_p()
+    _check(L.lsm_conv3d_create(c_in, c_out, int(relu), w.ctypes.data, None if b is None else b.ctypes.data,
+                               C.byref(out), _stream(stream)), "lsm_conv3d_create")
+    h = Conv3d(out)
+    h.c_in, h.c_out = c_in, c_out
+    return h
+
+
+def lsm_conv3d_forward(conv: Conv3d, vin: lsm_vol, vout: lsm_vol, ctas_per_sm: int = 0, stream=None):
+    _check(_lib.lsm_conv3d_forward(conv.ptr, C.byref(vin), C.byref(vout), ctas_per_sm, _stream(stream)),
+           "lsm_conv3d_forward")
+
+
+def lsm_pool3d(vin: lsm_vol, vout: lsm_vol, stream=None):
+    _check(_lib.lsm_pool3d(C.byref(vin), C.byref(vout), _stream(stream)), "lsm_pool3d")
+
+
+def lsm_upsample3d(vin: lsm_vol, vout: lsm_vol, stream=None):
+    _check(_lib.lsm_upsample3d(C.byref(vin), C.byref(vout), _stream(stream)), "lsm_upsample3d")
+
+
+def lsm_unet_param_count() -> int:
+    return int(load_library(require_gpu=False).lsm_unet_param_count())
+
+
+def lsm_unet_create(params, stream=None) -> UNet:
+    L = load_library()
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    out = C.c_void_p()
+    _check(L.lsm_unet_create(p.ctypes.data, p.size, C.byref(out), _stream(stream)), "lsm_unet_create")
+    return UNet(out)
+
+
+def lsm_unet_forward(net: UNet, dose, rho, out=None, stream=None):
+    """Denoised dose. dose, rho: [n, d, h, w] (or [d, h, w]) FP32, both numpy
+    (host call, returns numpy) or both CUDA tensors (stream-ordered, returns
+    a CUDA tensor)."""
+    if isinstance(dose, np.ndarray):
+        d_ = np.ascontiguousarray(dose, dtype=np.float32)
+        r_ = np.ascontiguousarray(rho, dtype=np.float32)
+        shp = d_.shape if d_.ndim == 4 else (1,) + d_.shape
+        o = np.empty(d_.shape, dtype=np.float32)
+        _check(_lib.lsm_unet_forward(net.ptr, *shp, d_.ctypes.data, r_.ctypes.data, o.ctypes.data, LSM_MEM_HOST,
+                                     _stream(stream)), "lsm_unet_forward")
+        return o
+    import torch
+    shp = tuple(dose.shape) if dose.dim() == 4 else (1,) + tuple(dose.shape)
+    assert dose.is_cuda and dose.dtype == torch.float32 and dose.is_contiguous() and rho.is_contiguous()
+    o = torch.empty_like(dose) if out is None else out
+    _check(_lib.lsm_unet_forward(net.ptr, *shp, dose.data_ptr(), rho.data_ptr(), o.data_ptr(), LSM_MEM_DEVICE,
+                                 _stream(stream)), "lsm_unet_forward")
+    return o
+
+
+def lsm_unet_activation(net: UNet, layer: int, shape) -> np.ndarray:
+    """Stored output of conv layer `layer` of the last forward call as float64
+    [n, d_l, h_l, w_l, c_out] (shape given by the caller)."""
+    import torch
+    t = torch.empty(tuple(shape), dtype=torch.bfloat16, device="cuda")
+    _check(_lib.lsm_unet_activation(net.ptr, layer, t.data_ptr(), LSM_MEM_DEVICE, None), "lsm_unet_activation")
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()

@@ -1,0 +1,171 @@
+"""GPU parity of the denoiser kernels (tcgen05 3x3x3 convolution, pooling,
+upsampling, the U-Net forward) against the FP64 oracle in oracle/denoise.py.
+
+Both sides use the same BF16 inputs and weights. A convolution output is the
+FP32 tensor-core sum of K = 27 c_in products rounded once to BF16, so
+|gpu - ref| <= 2^-8 |ref| + 2 K 2^-23 S, S the sum of the magnitudes of all
+terms (oracle.denoise.conv3_abs); pooling and upsampling move stored values and
+are bit-exact."""
+import numpy as np
+import pytest
+
+from oracle import denoise as DN
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1503_01725_b300 import lsm
+    lsm.load_library()
+    return lsm
+
+
+def to_vol(L, x, c_total=None, c_offset=0, fill=0.0):
+    import torch
+    n, d, h, w, c = x.shape
+    t = L.alloc_vol(n, d, h, w, c_total or c)
+    if fill:
+        t[:, 1:-1, 1:-1, 1:-1] = fill
+    t[:, 1:-1, 1:-1, 1:-1, c_offset:c_offset + c] = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16)
+    return t
+
+
+def interior(t, c_offset=0, c=None):
+    c = t.shape[-1] - c_offset if c is None else c
+    return t[:, 1:-1, 1:-1, 1:-1, c_offset:c_offset + c].double().cpu().numpy()
+
+
+def conv_tolerance(x, w, b, ref):
+    k = 27 * w.shape[-1]
+    return 2.0 ** -8 * np.abs(ref) + 2 * k * 2.0 ** -23 * DN.conv3_abs(x, w, b) + 1e-30
+
+
+def rand_bf16(rng, shape, scale=1.0):
+    return DN.bf16_round(rng.standard_normal(shape) * scale)
+
+
+CONFIGS = [(16, 16), (32, 16), (16, 32), (32, 32), (64, 32), (32, 64), (64, 64), (128, 64), (64, 128), (16, 128),
+           (128, 16)]
+
+
+@pytest.mark.parametrize("cin,cout", CONFIGS)
+@pytest.mark.parametrize("relu", [True, False])
+def test_conv3d_matches_oracle(L, cin, cout, relu):
+    import torch
+    rng = np.random.default_rng(cin * 7 + cout + relu)
+    n, d, h, w = 2, 5, 6, 7                    # ragged: tiles straddle rows, planes and volumes
+    x = rand_bf16(rng, (n, d, h, w, cin))
+    wt = rand_bf16(rng, (cout, 3, 3, 3, cin), 1.0 / np.sqrt(27 * cin))
+    b = rand_bf16(rng, cout, 0.1)
+    conv = L.lsm_conv3d_create(cin, cout, wt, b, relu=relu)
+    tin = to_vol(L, x, c_total=cin + 16, c_offset=16, fill=7.0)   # read a channel slice
+    tout = to_vol(L, np.zeros((n, d, h, w, cout)), c_total=cout + 16, c_offset=8, fill=3.0)
+    # halo voxels that lie inside the tiled span (x and y halo of the inner
+    # planes) are written as zero: plant garbage there first
+    tout[:, 2:-2, :, :, 8:8 + cout] = 5.0
+    tout[:, 2:-2, 1:-1, 1:-1, 8:8 + cout] = 0.0
+    L.lsm_conv3d_forward(conv, L.vol(tin, 16, cin), L.vol(tout, 8, cout))
+    torch.cuda.synchronize()
+    got = interior(tout, 8, cout)
+    for i in range(n):
+        ref = DN.conv3(x[i], wt, b, relu)
+        err = np.abs(got[i] - ref)
+        tol = conv_tolerance(x[i], wt, b, ref)
+        assert np.all(err <= tol), (err / tol).max()
+    o = tout.double().cpu().numpy()
+    halo = np.ones(o.shape[:4], bool)
+    halo[:, 1:-1, 1:-1, 1:-1] = False
+    assert not o[halo][:, 8:8 + cout].any()
+    assert np.all(o[~halo][:, :8] == 3.0) and np.all(o[~halo][:, 8 + cout:] == 3.0)
+
+
+def test_conv3d_many_tiles_per_cta(L):
+    """64^3 volume (2178 tiles) on one CTA per SM: every CTA runs ~15 tiles
+    through both tensor-memory accumulators and the stage ring."""
+    import torch
+    rng = np.random.default_rng(11)
+    x = rand_bf16(rng, (1, 64, 64, 64, 32))
+    wt = rand_bf16(rng, (32, 3, 3, 3, 32), 0.03)
+    b = rand_bf16(rng, 32, 0.1)
+    conv = L.lsm_conv3d_create(32, 32, wt, b, relu=True)
+    tin, tout = to_vol(L, x), L.alloc_vol(1, 64, 64, 64, 32)
+    L.lsm_conv3d_forward(conv, L.vol(tin), L.vol(tout), ctas_per_sm=1)
+    torch.cuda.synchronize()
+    got = interior(tout)[0]
+    ref = DN.conv3(x[0], wt, b, True)
+    assert np.all(np.abs(got - ref) <= conv_tolerance(x[0], wt, b, ref))
+
+
+def test_pool_and_upsample_bit_exact(L):
+    import torch
+    rng = np.random.default_rng(12)
+    x = rand_bf16(rng, (2, 6, 4, 8, 24))
+    tin = to_vol(L, x, c_total=32, c_offset=8)
+    tp = L.alloc_vol(2, 3, 2, 4, 24)
+    L.lsm_pool3d(L.vol(tin, 8, 24), L.vol(tp))
+    tu = L.alloc_vol(2, 6, 4, 8, 40)
+    L.lsm_upsample3d(L.vol(tp), L.vol(tu, 16, 24))
+    torch.cuda.synchronize()
+    p = interior(tp)
+    for i in range(2):
+        assert np.array_equal(p[i], DN.pool2(x[i]))
+        assert np.array_equal(interior(tu, 16, 24)[i], DN.up2(DN.pool2(x[i])))
+    assert not interior(tu, 0, 16).any()
+    assert not tu[:, 0].double().abs().sum().item()
+
+
+def _gpu_layer_inputs(acts, x0):
+    """Input of each conv layer built from the GPU's stored activations."""
+    e0, e1, e2 = acts[1], acts[3], acts[5]
+    return [x0, acts[0], DN.pool2(e0), acts[2], DN.pool2(e1), acts[4], DN.pool2(e2), acts[6],
+            np.concatenate([e2, DN.up2(acts[7])], 3), acts[8],
+            np.concatenate([e1, DN.up2(acts[9])], 3), acts[10],
+            np.concatenate([e0, DN.up2(acts[11])], 3), acts[12]]
+
+
+def test_unet_forward_layer_by_layer(L):
+    rng = np.random.default_rng(13)
+    n, d, h, w = 2, 16, 24, 16
+    dose = rng.random((n, d, h, w)).astype(np.float32) * 3.0
+    rho = (0.5 + rng.random((n, d, h, w))).astype(np.float32)
+    params = DN.init_params(3, head_scale=0.05)
+    params[-1] = 0.01
+    net = L.lsm_unet_create(params)
+    out = L.lsm_unet_forward(net, dose, rho)
+    layers, (hw, hb) = DN.unpack_params(params)
+    convs, _ = DN.layer_shapes()
+    for i in range(n):
+        x0, dmax = DN.pack_input(dose[i].astype(np.float64), rho[i].astype(np.float64))
+        acts = []
+        for li, (ci, co) in enumerate(convs):
+            lv = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0][li]
+            a = L.lsm_unet_activation(net, li, (n, d >> lv, h >> lv, w >> lv, co))
+            acts.append(a[i])
+        ins = _gpu_layer_inputs(acts, x0)
+        for li in range(14):
+            wb, bb = DN.bf16_round(layers[li][0]), DN.bf16_round(layers[li][1])
+            ref = DN.conv3(ins[li], wb, bb, True)
+            err = np.abs(acts[li] - ref)
+            tol = conv_tolerance(ins[li], wb, bb, ref)
+            assert np.all(err <= tol), (li, (err / tol).max())
+        # head on the GPU's last activation, FP32 on the device
+        head = dose[i].astype(np.float64) + dmax * (acts[13] @ hw + hb)
+        np.testing.assert_allclose(out[i], head, rtol=1e-5, atol=1e-5 * dmax)
+        # end to end against the oracle's own forward pass (its BF16 roundings can
+        # differ from the GPU's by one unit where FP32 and FP64 sums straddle a
+        # rounding boundary, and such differences propagate)
+        ref = DN.unet_forward(dose[i], rho[i], params)
+        rel = np.linalg.norm(out[i] - ref) / np.linalg.norm(ref - dose[i])
+        assert rel < 0.05
+
+
+def test_unet_device_buffers_and_untrained_identity(L):
+    import torch
+    rng = np.random.default_rng(14)
+    dose = torch.tensor(rng.random((8, 16, 32)), dtype=torch.float32, device="cuda")
+    rho = torch.ones_like(dose)
+    net = L.lsm_unet_create(DN.init_params(4, head_scale=0.0))
+    out = L.lsm_unet_forward(net, dose, rho)
+    torch.cuda.synchronize()
+    assert torch.equal(out, dose)
