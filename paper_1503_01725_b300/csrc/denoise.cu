@@ -5,18 +5,21 @@
 // output channels, k over (tap, input channel). Every activation volume keeps
 // a one-voxel zero halo, so each tap is a pure shift of the padded linear voxel
 // index by (dz-1) P + (dy-1) (w+2) + (dx-1), P = (h+2)(w+2). One pipeline stage
-// covers one input-channel chunk and one dz: TMA loads, per 8-channel group,
-// three slabs of 130 voxels (dy = 0, 1, 2, with one voxel of x halo on either
-// side), and the nine (dy, dx) taps of the stage are shared-memory descriptors
-// that start inside those slabs. The stage's weights arrive with one bulk copy,
+// covers one input-channel chunk (KC channels) and one dz: TMA loads three
+// slabs of 130 voxels x KC channels (dy = 0, 1, 2, one voxel of x halo on
+// either side), and the nine (dy, dx) taps of the stage are shared-memory
+// descriptors that start dx rows into those slabs. The stage's weights arrive with one bulk copy,
 // already packed into the operand layout on the host. Accumulators are FP32 in
 // tensor memory, two per CTA so that the epilogue of one tile overlaps the MMAs
 // of the next; the epilogue adds the bias, applies ReLU, writes BF16 and zeroes
 // the halo voxels of the tile.
 //
-// Operand layout in shared memory (no swizzle, K-major): core matrices of 8
-// rows x 16 bytes with rows at a 16-byte pitch; SBO = 128 bytes between 8-row
-// groups, LBO between the two 8-element K halves of one K = 16 MMA.
+// Operand layouts in shared memory, both K-major: A (activations) in rows of
+// 2 KC bytes with the 32/64/128-byte swizzle that TMA writes (SBO = 8 rows; a
+// K = 16 step advances the start by 32 bytes; the swizzle phase follows the
+// address, so a start shifted by whole rows reads the shifted rows); B
+// (weights) without swizzle, core matrices of 8 rows x 16 bytes, SBO = 128
+// bytes between 8-row groups, LBO between the two 8-element K halves.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
@@ -39,24 +42,29 @@ namespace lsm {
 namespace dn {
 
 constexpr int kTileM = 128;
-constexpr int kSlabVox = kTileM + 2;
-constexpr int kSlabBytes = kSlabVox * 16;       // one 8-channel group of a slab
-constexpr int kSlabPitch = 2176;                // 2080 rounded up to 128 bytes
+constexpr int kSlabVox = kTileM + 2;            // one voxel of x halo either side
 constexpr int kThreads = 192;                   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
+// A slab row is one voxel's KC input channels (2 KC bytes), stored with the
+// matching TMA / UMMA swizzle (32, 64 or 128 bytes); slabs start on 1024-byte
+// boundaries so that the swizzle phase of a row is that of its address.
 template <int COUT, int KC>
 struct Cfg {
-    static constexpr int kA = KC / 8 * 3 * kSlabPitch;
+    static constexpr int kRow = KC * 2;
+    static constexpr int kPitch = (kSlabVox * kRow + 1023) / 1024 * 1024;
+    static constexpr int kA = 3 * kPitch;
     static constexpr int kB = 9 * COUT * KC * 2;
-    static constexpr int kStage = kA + kB;
-    static constexpr int kFit = 100 * 1024 / kStage;
+    static constexpr int kStage = (kA + kB + 1023) / 1024 * 1024;
+    static constexpr int kBudget = kStage <= 50 * 1024 ? 100 * 1024 : 200 * 1024;
+    static constexpr int kFit = kBudget / kStage;
     static constexpr int kStages = kFit < 2 ? 2 : (kFit > 8 ? 8 : kFit);
-    static constexpr int kTx = KC / 8 * 3 * kSlabBytes + kB;
+    static constexpr int kTx = 3 * kSlabVox * kRow + kB;
+    static constexpr uint32_t kSwz = KC == 16 ? 6u : (KC == 32 ? 4u : 2u);   // 32B, 64B, 128B swizzle
     static constexpr int kAccCols = COUT < 32 ? 32 : COUT;
     static constexpr int kTmemCols = 2 * kAccCols;
     static constexpr int kSmem = kStages * kStage + 1024;
-    static_assert(kStage % 128 == 0, "stage alignment");
+    static_assert(KC == 16 || KC == 32 || KC == 64, "channel chunk");
 };
 
 struct ConvArgs {
@@ -146,11 +154,11 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, unsigne
 }
 
 // shared-memory matrix descriptor: start, leading and stride byte offsets
-// (16-byte units), descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+// (16-byte units), descriptor version 1, layout (0 none, 6 32B, 4 64B, 2 128B swizzle)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout = 0)
 {
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
@@ -238,10 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
 #pragma unroll
                     for (int dy = 0; dy < 3; ++dy) {
                         const int c1 = (int)(lt - 1 + (long long)(dz - 1) * a.p + (long long)(dy - 1) * a.w2);
-#pragma unroll
-                        for (int g = 0; g < KC / 8; ++g)
-                            tma_load_3d(sa + (uint32_t)((g * 3 + dy) * kSlabPitch), &tin, a.in_co + kc * KC + g * 8,
-                                        c1, vol, &full[s]);
+                        tma_load_3d(sa + (uint32_t)(dy * C::kPitch), &tin, a.in_co + kc * KC, c1, vol, &full[s]);
                     }
                     bulk_load(sb, a.wimg + (size_t)(kc * 3 + dz) * 9 * COUT * KC, C::kB, &full[s]);
                 }
@@ -274,8 +279,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
                         for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                             for (int j = 0; j < KC / 16; ++j) {
-                                const uint64_t ad =
-                                    sdesc(sa + (uint32_t)((2 * j * 3 + dy) * kSlabPitch + dx * 16), 3 * kSlabPitch, 128);
+                                const uint64_t ad = sdesc(sa + (uint32_t)(dy * C::kPitch + dx * C::kRow + j * 32), 16,
+                                                          8 * C::kRow, C::kSwz);
                                 const uint64_t bd = sdesc(
                                     sb + (uint32_t)((dy * 3 + dx) * (COUT * KC * 2) + j * 2 * (COUT * 16)), COUT * 16,
                                     128);
@@ -559,9 +564,10 @@ lsm_status launch_conv(const CUtensorMap &map, const ConvArgs &a, int ctas_per_s
     return LSM_OK;
 }
 
+// input channels per stage: weights of a stage (9 taps x cout x kc) stay <= 36 KB
 int kc_for(int cin, int cout)
 {
-    const int kmax = cout >= 128 ? 16 : 32;
+    const int kmax = cout >= 128 ? 16 : (cout == 64 ? 32 : 64);
     return std::min(cin, kmax);
 }
 
@@ -582,11 +588,13 @@ lsm_status conv_forward(const lsm_conv3d *cv, const lsm_vol *in, const lsm_vol *
     CUtensorMap map;
     const cuuint64_t dims[3] = {(cuuint64_t)in->c_total, (cuuint64_t)v.lp, (cuuint64_t)in->n};
     const cuuint64_t strides[2] = {(cuuint64_t)in->c_total * 2, (cuuint64_t)v.lp * in->c_total * 2};
-    const cuuint32_t box[3] = {8, (cuuint32_t)kSlabVox, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)cv->kc, (cuuint32_t)kSlabVox, 1};
     const cuuint32_t es[3] = {1, 1, 1};
+    const CUtensorMapSwizzle swz = cv->kc == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                   : cv->kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
     const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, in->data, dims, strides, box, es,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) {
         char msg[96];
         snprintf(msg, sizeof msg, "lsm_conv3d_forward: tensor map encoding failed (%d)", (int)cr);
@@ -617,8 +625,10 @@ lsm_status conv_forward(const lsm_conv3d *cv, const lsm_vol *in, const lsm_vol *
     switch (cv->cout * 1000 + cv->kc) {
     case 16016: r = launch_conv<16, 16>(map, a, ctas_per_sm, st); break;
     case 16032: r = launch_conv<16, 32>(map, a, ctas_per_sm, st); break;
+    case 16064: r = launch_conv<16, 64>(map, a, ctas_per_sm, st); break;
     case 32016: r = launch_conv<32, 16>(map, a, ctas_per_sm, st); break;
     case 32032: r = launch_conv<32, 32>(map, a, ctas_per_sm, st); break;
+    case 32064: r = launch_conv<32, 64>(map, a, ctas_per_sm, st); break;
     case 64016: r = launch_conv<64, 16>(map, a, ctas_per_sm, st); break;
     case 64032: r = launch_conv<64, 32>(map, a, ctas_per_sm, st); break;
     case 128016: r = launch_conv<128, 16>(map, a, ctas_per_sm, st); break;
