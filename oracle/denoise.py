@@ -143,17 +143,22 @@ def pack_input(dose: np.ndarray, rho: np.ndarray):
 
 
 def unet_forward(dose: np.ndarray, rho: np.ndarray, flat_params: np.ndarray, widths=WIDTHS,
-                 return_layers: bool = False):
+                 return_layers: bool = False, rounding: bool = True):
     """Denoised dose [D, H, W] (D, H, W divisible by 8). Every conv3 output is
-    rounded to bfloat16 before use, as stored by the GPU path; the head is
-    evaluated without rounding."""
+    rounded to bfloat16 before use, as stored by the GPU path (rounding=False:
+    plain FP64 throughout, for derivative checks); the head is evaluated
+    without rounding."""
     layers, (hw, hb) = unpack_params(flat_params, widths)
     x, dmax = pack_input(dose, rho)
+    if not rounding:
+        x[..., 0] = np.asarray(dose, dtype=np.float64) / dmax
+        x[..., 1] = rho
+    rnd = bf16_round if rounding else (lambda a: np.asarray(a, dtype=np.float64))
     acts = []
 
     def c(i, t):
         w, b = layers[i]
-        y = bf16_round(conv3(t, bf16_round(w), bf16_round(b), relu=True))
+        y = rnd(conv3(t, rnd(w), rnd(b), relu=True))
         acts.append(y)
         return y
 
@@ -167,3 +172,117 @@ def unet_forward(dose: np.ndarray, rho: np.ndarray, flat_params: np.ndarray, wid
     r = d0 @ np.asarray(hw, dtype=np.float64) + float(hb)
     out = np.asarray(dose, dtype=np.float64) + dmax * r
     return (out, acts) if return_layers else out
+
+
+# ------------------------------------------------------------- gradients ---
+# Training minimises the mean squared error between the denoised dose and a
+# high-history dose, both divided by the input's maximum dose:
+#   loss = mean_v (dose_v / Dmax + head(d0)_v - target_v / Dmax)^2.
+# The derivatives below are those of the FP64 network evaluated at the
+# activations passed in (the rounding of stored activations is not
+# differentiated: it is a storage step, not part of the model).
+
+def conv3_wgrad(x: np.ndarray, gz: np.ndarray) -> np.ndarray:
+    """dloss/dw for out = conv3(x, w): dw[o, dz, dy, dx, c] = sum over voxels
+    of gz[z, y, x, o] * x[z + dz - 1, y + dy - 1, x + dx - 1, c] (zero padding)."""
+    D, H, W, C = x.shape
+    xp = np.pad(np.asarray(x, dtype=np.float64), ((1, 1), (1, 1), (1, 1), (0, 0)))
+    g = np.asarray(gz, dtype=np.float64)
+    dw = np.zeros((g.shape[-1], 3, 3, 3, C))
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                dw[:, dz, dy, dx, :] = np.tensordot(g, xp[dz:dz + D, dy:dy + H, dx:dx + W],
+                                                    axes=([0, 1, 2], [0, 1, 2]))
+    return dw
+
+
+def conv3_dgrad(gz: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """dloss/dx for out = conv3(x, w): the correlation of gz with the weights
+    mirrored in all three axes and transposed in channels."""
+    wf = np.asarray(w, dtype=np.float64)[:, ::-1, ::-1, ::-1, :].transpose(4, 1, 2, 3, 0)
+    return conv3(gz, wf, np.zeros(wf.shape[0]), relu=False)
+
+
+def pool2_backward(x: np.ndarray, gy: np.ndarray) -> np.ndarray:
+    """Gradient of 2x2x2 max pooling: each window's gradient goes to the first
+    voxel (in (dz, dy, dx) order) that holds the window maximum."""
+    D, H, W, C = x.shape
+    y = pool2(x)
+    gx = np.zeros_like(np.asarray(x, dtype=np.float64))
+    taken = np.zeros(y.shape, bool)
+    for dz in range(2):
+        for dy in range(2):
+            for dx in range(2):
+                xs = x[dz::2, dy::2, dx::2]
+                hit = (xs == y) & ~taken
+                gx[dz::2, dy::2, dx::2] = np.where(hit, gy, 0.0)
+                taken |= hit
+    return gx
+
+
+def up2_backward(gy: np.ndarray) -> np.ndarray:
+    """Gradient of nearest 2x upsampling: the sum over each 2x2x2 block."""
+    D, H, W, C = gy.shape
+    return np.asarray(gy, dtype=np.float64).reshape(D // 2, 2, H // 2, 2, W // 2, 2, C).sum(axis=(1, 3, 5))
+
+
+def unet_loss_and_grad(dose, rho, target, flat_params, widths=WIDTHS, rounding: bool = True,
+                       acts=None):
+    """(loss, flat gradient) of the normalised MSE. acts: the 14 stored conv
+    outputs to differentiate at (default: this module's forward pass)."""
+    layers, (hw, hb) = unpack_params(flat_params, widths)
+    rnd = bf16_round if rounding else (lambda a: np.asarray(a, dtype=np.float64))
+    x0, dmax = pack_input(dose, rho)
+    if not rounding:
+        x0[..., 0] = np.asarray(dose, dtype=np.float64) / dmax
+        x0[..., 1] = rho
+    if acts is None:
+        _, acts = unet_forward(dose, rho, flat_params, widths, return_layers=True, rounding=rounding)
+    a = acts
+    e0, e1, e2 = a[1], a[3], a[5]
+    ins = [x0, a[0], pool2(e0), a[2], pool2(e1), a[4], pool2(e2), a[6],
+           np.concatenate([e2, up2(a[7])], 3), a[8],
+           np.concatenate([e1, up2(a[9])], 3), a[10],
+           np.concatenate([e0, up2(a[11])], 3), a[12]]
+    dn = np.asarray(dose, dtype=np.float64) / dmax
+    tn = np.asarray(target, dtype=np.float64) / dmax
+    r = a[13] @ hw + hb
+    res = dn + r - tn
+    nvox = res.size
+    loss = float(np.mean(res ** 2))
+    g_r = 2.0 * res / nvox
+    g_hw = np.tensordot(g_r, a[13], axes=([0, 1, 2], [0, 1, 2]))
+    g_hb = g_r.sum()
+    grads = [None] * 14
+    g_out = {13: g_r[..., None] * hw}
+
+    def layer_back(i, gy):
+        w, _ = layers[i]
+        gz = gy * (a[i] > 0)
+        grads[i] = (conv3_wgrad(ins[i], gz), gz.sum(axis=(0, 1, 2)))
+        return conv3_dgrad(gz, rnd(w)) if i > 0 else None
+
+    c0, c1, c2, _ = widths
+    g = layer_back(13, g_out[13])
+    g = layer_back(12, g)                                  # gradient of cat(e0, up2(d1))
+    g_e0_skip, g_d1 = g[..., :c0], up2_backward(g[..., c0:])
+    g = layer_back(11, g_d1)
+    g = layer_back(10, g)                                  # cat(e1, up2(d2))
+    g_e1_skip, g_d2 = g[..., :c1], up2_backward(g[..., c1:])
+    g = layer_back(9, g_d2)
+    g = layer_back(8, g)                                   # cat(e2, up2(b))
+    g_e2_skip, g_b = g[..., :c2], up2_backward(g[..., c2:])
+    g = layer_back(7, g_b)
+    g = layer_back(6, g)                                   # gradient of pool2(e2)
+    g = layer_back(5, g_e2_skip + pool2_backward(e2, g))
+    g = layer_back(4, g)
+    g = layer_back(3, g_e1_skip + pool2_backward(e1, g))
+    g = layer_back(2, g)
+    g = layer_back(1, g_e0_skip + pool2_backward(e0, g))
+    layer_back(0, g)
+    flat = []
+    for i in range(14):
+        flat += [grads[i][0].ravel(), grads[i][1]]
+    flat += [g_hw, np.array([g_hb])]
+    return loss, np.concatenate(flat)

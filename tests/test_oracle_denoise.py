@@ -117,3 +117,46 @@ def test_untrained_head_returns_input_dose():
     dose = rng.random((8, 8, 8))
     out = DN.unet_forward(dose, np.ones_like(dose), DN.init_params(1, head_scale=0.0))
     np.testing.assert_array_equal(out, dose)
+
+
+def test_gradient_matches_finite_differences():
+    """The oracle's backward pass against central differences of its own FP64
+    loss, on a small network (widths 8) and volume, at random coordinates of
+    every layer and the head."""
+    rng = np.random.default_rng(7)
+    widths = (8, 8, 8, 8)
+    dose = rng.random((8, 8, 16)) + 0.2
+    rho = rng.random((8, 8, 16)) + 0.5
+    target = dose * (1.0 + 0.1 * rng.standard_normal(dose.shape))
+    p = DN.init_params(5, widths, head_scale=0.3)
+    p[:-1] += 0.01 * rng.standard_normal(p.size - 1)          # non-zero biases
+    loss, g = DN.unet_loss_and_grad(dose, rho, target, p, widths, rounding=False)
+    convs, _ = DN.layer_shapes(widths)
+    picks, k = [], 0
+    for ci, co in convs:
+        n = 27 * ci * co
+        lo = k if ci != DN.IN_CHANNELS else k           # first layer: only real input channels matter
+        picks += list(rng.integers(lo, k + n, 3)) + [k + n + int(rng.integers(0, co))]
+        k += n + co
+    picks += [k, k + 3, k + 8]
+    h = 1e-6
+    for j in picks:
+        pp, pm = p.copy(), p.copy()
+        pp[j] += h
+        pm[j] -= h
+        lp = DN.unet_loss_and_grad(dose, rho, target, pp, widths, rounding=False)[0]
+        lm = DN.unet_loss_and_grad(dose, rho, target, pm, widths, rounding=False)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-6 * max(1.0, abs(fd)) + 1e-7, (j, fd, g[j])
+
+
+def test_wgrad_and_dgrad_are_adjoint_of_conv():
+    """<conv3(x, w), gz> = <w, wgrad(x, gz)> = <x, dgrad(gz, w)>."""
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((4, 5, 6, 3))
+    w = rng.standard_normal((2, 3, 3, 3, 3))
+    gz = rng.standard_normal((4, 5, 6, 2))
+    y = DN.conv3(x, w, np.zeros(2), relu=False)
+    a = np.sum(y * gz)
+    np.testing.assert_allclose(np.sum(w * DN.conv3_wgrad(x, gz)), a, rtol=1e-12)
+    np.testing.assert_allclose(np.sum(x * DN.conv3_dgrad(gz, w)), a, rtol=1e-12)
