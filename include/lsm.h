@@ -449,6 +449,29 @@ lsm_status lsm_unet_forward(lsm_unet *net, int32_t n, int32_t d, int32_t h, int3
  * (host or device). */
 lsm_status lsm_unet_activation(const lsm_unet *net, int32_t layer, void *dst, lsm_mem mem, lsm_stream stream);
 
+/*
+ * Training of the denoiser on pairs (low-history dose, density) -> high-history
+ * dose: loss = mean over voxels of (out / Dmax - target / Dmax)^2 with Dmax
+ * the input dose's maximum per volume. One call runs the forward pass, the
+ * gradient of every parameter (BF16 activation gradients, FP32 parameter
+ * gradients; data gradients on the tensor cores) and, when opts->lr > 0, one
+ * Adam step (with bias correction and decoupled weight decay) on the FP32
+ * master parameters, after which the BF16 operand images are repacked.
+ * dose, rho, target: device FP32 [n][d][h][w]; d, h, w multiples of 8.
+ * loss: host pointer (the call then synchronises and reports pipeline
+ * timeouts) or NULL (stream-ordered). opts NULL: gradients only.
+ */
+typedef struct {
+    double lr, beta1, beta2, eps, weight_decay;
+} lsm_adam_opts;
+lsm_status lsm_unet_train_step(lsm_unet *net, int32_t n, int32_t d, int32_t h, int32_t w, const float *dose,
+                               const float *rho, const float *target, const lsm_adam_opts *opts, double *loss,
+                               lsm_stream stream);
+/* Current FP32 parameters (lsm_unet_param_count values, flat order of
+ * lsm_unet_create) and the gradient of the last training step. */
+lsm_status lsm_unet_params(const lsm_unet *net, float *dst, lsm_mem mem, lsm_stream stream);
+lsm_status lsm_unet_grad(const lsm_unet *net, float *dst, lsm_mem mem, lsm_stream stream);
+
 /* Library diagnostics. */
 const char *lsm_last_error(void);
 /* Kernels launched by this library in this process so far. */

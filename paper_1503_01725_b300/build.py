@@ -27,6 +27,7 @@ SOURCES = {
     "transport.cu": [],
     "nnls.cu": [],
     "denoise.cu": [],
+    "train.cu": [],
 }
 
 

@@ -29,14 +29,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "common.cuh"
-
-// ------------------------------------------------------------------ handles ---
-struct lsm_conv3d {
-    int cin, cout, relu, kc;
-    __nv_bfloat16 *wimg;      // packed operand images [cin/kc][dz][9 taps][cout x kc]
-    float *bias;              // [cout], values rounded to BF16
-};
+#include "unet.cuh"
 
 namespace lsm {
 namespace dn {
@@ -346,26 +339,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
 }
 
 // ---------------------------------------------------- memory-bound kernels ---
-struct VolIdx {
-    int d, h, w;
-    long long lp;
-    int w2, p;
-    __host__ __device__ long long at(int b, int z, int y, int x) const
-    {
-        return (long long)b * lp + (long long)(z + 1) * p + (long long)(y + 1) * w2 + x + 1;
-    }
-};
-
-__host__ __device__ inline VolIdx vidx(int d, int h, int w)
-{
-    VolIdx v;
-    v.d = d; v.h = h; v.w = w;
-    v.w2 = w + 2;
-    v.p = (h + 2) * (w + 2);
-    v.lp = (long long)(d + 2) * v.p;
-    return v;
-}
-
 __device__ __forceinline__ uint4 max8(uint4 a, uint4 b)
 {
     uint4 r;
@@ -661,19 +634,34 @@ lsm_status conv_create(int cin, int cout, int relu, const float *w, const float 
             }
     std::vector<float> bias(cout, 0.0f);
     for (int n = 0; n < cout && b; ++n) bias[n] = __bfloat162float(__float2bfloat16_rn(b[n]));
-    lsm_conv3d *cv = (lsm_conv3d *)calloc(1, sizeof(lsm_conv3d));
-    if (!cv) return set_arg_error("lsm_conv3d_create: out of host memory");
-    cv->cin = cin; cv->cout = cout; cv->relu = relu ? 1 : 0; cv->kc = kc;
-    cudaError_t e = cudaMalloc(&cv->wimg, nw * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&cv->bias, (size_t)cout * 4);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cv->wimg, img.data(), nw * 2, cudaMemcpyHostToDevice, st);
+    lsm_conv3d *cv = nullptr;
+    lsm_status rc = conv_alloc(cin, cout, relu, &cv);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(cv->wimg, img.data(), nw * 2, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(cv->bias, bias.data(), (size_t)cout * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
-        cudaFree(cv->wimg);
-        cudaFree(cv->bias);
-        free(cv);
+        conv_destroy(cv);
         return set_cuda_error(e, "lsm_conv3d_create");
+    }
+    *out = cv;
+    return LSM_OK;
+}
+
+// a layer's device buffers (weights image and bias), contents unset
+lsm_status conv_alloc(int cin, int cout, int relu, lsm_conv3d **out)
+{
+    auto okc = [](int c) { return c == 16 || c == 32 || c == 64 || c == 128; };
+    if (!okc(cin) || !okc(cout)) return set_arg_error("lsm_conv3d: channels must be 16, 32, 64 or 128");
+    lsm_conv3d *cv = (lsm_conv3d *)calloc(1, sizeof(lsm_conv3d));
+    if (!cv) return set_arg_error("lsm_conv3d: out of host memory");
+    cv->cin = cin; cv->cout = cout; cv->relu = relu ? 1 : 0; cv->kc = kc_for(cin, cout);
+    cudaError_t e = cudaMalloc(&cv->wimg, (size_t)27 * cin * cout * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&cv->bias, (size_t)cout * 4);
+    if (e == cudaSuccess) e = cudaMemset(cv->bias, 0, (size_t)cout * 4);
+    if (e != cudaSuccess) {
+        conv_destroy(cv);
+        return set_cuda_error(e, "lsm_conv3d: device memory");
     }
     *out = cv;
     return LSM_OK;
@@ -725,40 +713,6 @@ lsm_status pool_or_up(const lsm_vol *in, const lsm_vol *out, bool up, cudaStream
 
 }  // namespace dn
 }  // namespace lsm
-
-// ------------------------------------------------------------------ U-Net ---
-namespace {
-constexpr int kW0 = 16, kW1 = 32, kW2 = 64, kW3 = 128;
-// (c_in, c_out) of the 14 conv layers in network order
-constexpr int kLayers[14][2] = {{16, kW0},      {kW0, kW0}, {kW0, kW1}, {kW1, kW1}, {kW1, kW2},
-                                {kW2, kW2},     {kW2, kW3}, {kW3, kW2}, {2 * kW2, kW2}, {kW2, kW1},
-                                {2 * kW1, kW1}, {kW1, kW0}, {2 * kW0, kW0}, {kW0, kW0}};
-enum Buf { X0, T0, S0, P1, T1, S1, P2, T2, S2, P3, T3, B3, D2A, D2, D1A, D1, D0A, D0, NBUF };
-constexpr int kBufLevel[NBUF] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 2, 2, 1, 1, 0, 0};
-constexpr int kBufCh[NBUF] = {16, kW0, 2 * kW0, kW0, kW1, 2 * kW1, kW1, kW2, 2 * kW2, kW2, kW3, kW2,
-                              kW2, kW1, kW1, kW0, kW0, kW0};
-// conv layer i: input buffer (channel offset 0, all of its channels) and output (buffer, channel offset)
-constexpr int kConvIn[14] = {X0, T0, P1, T1, P2, T2, P3, T3, S2, D2A, S1, D1A, S0, D0A};
-constexpr int kConvOut[14] = {T0, S0, T1, S1, T2, S2, T3, B3, D2A, D2, D1A, D1, D0A, D0};
-
-int64_t param_count()
-{
-    int64_t n = 0;
-    for (auto &l : kLayers) n += 27ll * l[0] * l[1] + l[1];
-    return n + kW0 + 1;
-}
-}  // namespace
-
-struct lsm_unet {
-    lsm_conv3d *conv[14];
-    float *head;              // device [17]
-    int n, d, h, w;           // shape the buffers are allocated for
-    void *arena;
-    lsm_vol vol[NBUF];
-    unsigned *dmax;           // [n] FP32 bits
-    float *io;                // device staging for host calls: dose, rho, out
-    size_t io_cap;
-};
 
 namespace lsm {
 namespace dn {
@@ -846,7 +800,7 @@ lsm_status unet_run(lsm_unet *u, const float *dose, const float *rho, float *out
     if (!rc) rc = up(D1, S0, kW0);
     if (!rc) rc = conv(12);
     if (!rc) rc = conv(13);
-    if (rc) return rc;
+    if (rc || !out) return rc;
     const int th = timer_begin(9, st);
     k_head<<<grid_1d(per * u->n), 256, 0, st>>>((const __nv_bfloat16 *)V[D0].data, V[D0].c_total, u->head, dose,
                                                 u->dmax, out, u->n, v0);
@@ -893,27 +847,26 @@ lsm_status lsm_upsample3d(const lsm_vol *in, const lsm_vol *out, lsm_stream stre
     return dn::pool_or_up(in, out, true, (cudaStream_t)stream);
 }
 
-int64_t lsm_unet_param_count(void) { return param_count(); }
+int64_t lsm_unet_param_count(void) { return dn::param_count(); }
 
 lsm_status lsm_unet_create(const float *params, int64_t n_params, lsm_unet **out, lsm_stream stream)
 {
     if (!params || !out) return set_arg_error("lsm_unet_create: NULL argument");
-    if (n_params != param_count()) return set_arg_error("lsm_unet_create: wrong parameter count");
+    if (n_params != dn::param_count()) return set_arg_error("lsm_unet_create: wrong parameter count");
     lsm_unet *u = (lsm_unet *)calloc(1, sizeof(lsm_unet));
     if (!u) return set_arg_error("lsm_unet_create: out of host memory");
     const cudaStream_t st = (cudaStream_t)stream;
-    const float *p = params;
     lsm_status rc = LSM_OK;
+    cudaError_t e = cudaMalloc(&u->params, (size_t)n_params * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u->params, params, (size_t)n_params * sizeof(float),
+                                              cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rc = set_cuda_error(e, "lsm_unet_create");
+    u->head = u->params ? u->params + dn::layer_offset(14) : nullptr;
     for (int i = 0; i < 14 && !rc; ++i) {
-        const int ci = kLayers[i][0], co = kLayers[i][1];
-        rc = dn::conv_create(ci, co, 1, p, p + 27ll * ci * co, &u->conv[i], st);
-        p += 27ll * ci * co + co;
+        rc = dn::conv_alloc(dn::kLayers[i][0], dn::kLayers[i][1], 1, &u->conv[i]);
+        if (!rc) rc = dn::pack_layer(u, i, st);
     }
-    if (!rc) {
-        cudaError_t e = cudaMalloc(&u->head, 17 * sizeof(float));
-        if (e == cudaSuccess) e = cudaMemcpy(u->head, p, 17 * sizeof(float), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) rc = set_cuda_error(e, "lsm_unet_create");
-    }
+    if (!rc && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = set_cuda_error(e, "lsm_unet_create");
     if (rc) {
         lsm_unet_destroy(u);
         return rc;
@@ -927,7 +880,8 @@ void lsm_unet_destroy(lsm_unet *u)
     if (!u) return;
     cudaDeviceSynchronize();
     for (int i = 0; i < 14; ++i) dn::conv_destroy(u->conv[i]);
-    cudaFree(u->head);
+    dn::train_free(u->train);
+    cudaFree(u->params);
     cudaFree(u->arena);
     cudaFree(u->dmax);
     cudaFree(u->io);
@@ -975,8 +929,8 @@ lsm_status lsm_unet_activation(const lsm_unet *u, int32_t layer, void *dst, lsm_
     if (layer < 0 || layer >= 14) return set_arg_error("lsm_unet_activation: layer in 0..13");
     if (!u->arena) return set_arg_error("lsm_unet_activation: no forward call yet");
     const cudaStream_t st = (cudaStream_t)stream;
-    const lsm_vol &v = u->vol[kConvOut[layer]];
-    const int c = kLayers[layer][1];
+    const lsm_vol &v = u->vol[dn::kConvOut[layer]];
+    const int c = dn::kLayers[layer][1];
     const size_t count = (size_t)v.n * v.d * v.h * v.w * c;
     void *tmp = dst;
     if (mem == LSM_MEM_HOST) LSM_CUDA(cudaMalloc(&tmp, count * 2));

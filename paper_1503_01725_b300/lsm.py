@@ -80,6 +80,11 @@ class lsm_vol(C.Structure):
                 ("c_total", C.c_int32), ("c_offset", C.c_int32), ("c", C.c_int32)]
 
 
+class lsm_adam_opts(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("weight_decay", C.c_double)]
+
+
 _EXPORTS = {
     "lsm_build_psl": (C.c_int, [C.POINTER(lsm_psr_model), C.POINTER(lsm_beams), C.c_int64,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.c_void_p]),
@@ -126,6 +131,11 @@ _EXPORTS = {
     "lsm_unet_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "lsm_unet_activation": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int, C.c_void_p]),
+    "lsm_unet_train_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.POINTER(lsm_adam_opts), C.POINTER(C.c_double),
+                                      C.c_void_p]),
+    "lsm_unet_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "lsm_unet_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "lsm_timing_enable": (C.c_int, [C.c_int]),
     "lsm_timing_read": (C.c_int, [_dp, C.POINTER(C.c_int64), C.c_int]),
     "lsm_last_error": (C.c_char_p, []),
@@ -581,3 +591,31 @@ def lsm_unet_activation(net: UNet, layer: int, shape) -> np.ndarray:
     _check(_lib.lsm_unet_activation(net.ptr, layer, t.data_ptr(), LSM_MEM_DEVICE, None), "lsm_unet_activation")
     torch.cuda.synchronize()
     return t.double().cpu().numpy()
+
+
+def lsm_unet_train_step(net: UNet, dose, rho, target, lr: float = 0.0, beta1: float = 0.9, beta2: float = 0.999,
+                        eps: float = 1e-8, weight_decay: float = 0.0, sync: bool = True, stream=None):
+    """One training step on CUDA tensors [n, d, h, w] (or [d, h, w]); lr = 0:
+    gradients only. Returns the loss (synchronising) or None when sync is False."""
+    import torch
+    shp = tuple(dose.shape) if dose.dim() == 4 else (1,) + tuple(dose.shape)
+    for t in (dose, rho, target):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == dose.numel()
+    o = lsm_adam_opts(lr=lr, beta1=beta1, beta2=beta2, eps=eps, weight_decay=weight_decay)
+    loss = C.c_double(0.0)
+    _check(_lib.lsm_unet_train_step(net.ptr, *shp, dose.data_ptr(), rho.data_ptr(), target.data_ptr(),
+                                    C.byref(o), C.byref(loss) if sync else None, _stream(stream)),
+           "lsm_unet_train_step")
+    return loss.value if sync else None
+
+
+def lsm_unet_params(net: UNet) -> np.ndarray:
+    out = np.empty(lsm_unet_param_count(), dtype=np.float32)
+    _check(_lib.lsm_unet_params(net.ptr, out.ctypes.data, LSM_MEM_HOST, None), "lsm_unet_params")
+    return out
+
+
+def lsm_unet_grad(net: UNet) -> np.ndarray:
+    out = np.empty(lsm_unet_param_count(), dtype=np.float32)
+    _check(_lib.lsm_unet_grad(net.ptr, out.ctypes.data, LSM_MEM_HOST, None), "lsm_unet_grad")
+    return out

@@ -169,3 +169,74 @@ def test_unet_device_buffers_and_untrained_identity(L):
     out = L.lsm_unet_forward(net, dose, rho)
     torch.cuda.synchronize()
     assert torch.equal(out, dose)
+
+
+def _acts(L, net, n, d, h, w):
+    convs, _ = DN.layer_shapes()
+    lv = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0]
+    return [L.lsm_unet_activation(net, i, (n, d >> lv[i], h >> lv[i], w >> lv[i], co))
+            for i, (ci, co) in enumerate(convs)]
+
+
+def test_training_gradient_matches_oracle(L):
+    """Gradients of one training step (lr = 0) against the oracle's backward
+    pass taken at the GPU's own stored activations. Activation gradients are
+    stored in BF16 on the GPU (about 2^-8 relative per store, compounding over
+    the 14 layers), so each layer's gradient is compared in relative L2 norm
+    and direction; the head's gradient is an FP32 sum and is compared tightly."""
+    import torch
+    rng = np.random.default_rng(21)
+    n, d, h, w = 1, 16, 16, 24
+    dose = (rng.random((n, d, h, w)) * 2 + 0.1).astype(np.float32)
+    rho = (0.5 + rng.random((n, d, h, w))).astype(np.float32)
+    target = (dose * (1 + 0.2 * rng.standard_normal(dose.shape))).astype(np.float32)
+    params = DN.init_params(6, head_scale=0.1)
+    params[:-17] += 0.002 * rng.standard_normal(params.size - 17)
+    net = L.lsm_unet_create(params)
+    t = [torch.tensor(a, device="cuda") for a in (dose, rho, target)]
+    loss = L.lsm_unet_train_step(net, *t, lr=0.0)
+    g = L.lsm_unet_grad(net).astype(np.float64)
+    acts = [a[0] for a in _acts(L, net, n, d, h, w)]
+    p32 = params.astype(np.float32).astype(np.float64)
+    lo, go = DN.unet_loss_and_grad(dose[0].astype(np.float64), rho[0].astype(np.float64),
+                                   target[0].astype(np.float64), p32, acts=acts)
+    assert loss == pytest.approx(lo, rel=1e-4)
+    convs, (hc, _) = DN.layer_shapes()
+    k = 0
+    for i, (ci, co) in enumerate(convs):
+        nw = 27 * ci * co
+        for part in (slice(k, k + nw), slice(k + nw, k + nw + co)):
+            a, b = g[part], go[part]
+            if i == 0 and part.stop == k + nw:
+                a = a.reshape(co, 27, ci)[..., :2].ravel()      # only the real input channels
+                b = b.reshape(co, 27, ci)[..., :2].ravel()
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
+            assert rel < 0.05 and cos > 0.998, (i, rel, cos)
+        k += nw + co
+    np.testing.assert_allclose(g[k:], go[k:], rtol=2e-3, atol=1e-6 * np.abs(go[k:]).max())
+
+
+def test_training_reduces_loss(L):
+    """Adam steps on a fixed pair lower the loss: the target is a smoothed,
+    rescaled copy of the input, a mapping the network can represent."""
+    import torch
+    from scipy import ndimage
+    rng = np.random.default_rng(22)
+    n, d, h, w = 2, 16, 16, 16
+    zz, yy, xx = np.meshgrid(*[np.linspace(-1, 1, s) for s in (d, h, w)], indexing="ij")
+    clean = np.exp(-(xx ** 2 + yy ** 2) * 3) * np.exp(-0.5 * (zz + 1))
+    dose = np.stack([clean, 0.7 * clean]) * (1 + 0.3 * rng.standard_normal((n, d, h, w)))
+    dose = dose.clip(0).astype(np.float32)
+    target = (0.6 * np.stack([ndimage.uniform_filter(x, 3) for x in dose])).astype(np.float32)
+    rho = np.ones_like(dose)
+    net = L.lsm_unet_create(DN.init_params(7, head_scale=0.01))
+    t = [torch.tensor(a, device="cuda") for a in (dose, rho, target)]
+    losses = [L.lsm_unet_train_step(net, *t, lr=3e-3) for _ in range(80)]
+    assert losses[-1] < 0.3 * losses[0], losses[::10]
+    p = L.lsm_unet_params(net)
+    assert np.all(np.isfinite(p))
+    # inference with the trained parameters agrees with the training forward pass
+    out = L.lsm_unet_forward(net, dose, rho)
+    err = np.mean(((out - target) / dose.reshape(n, -1).max(1)[:, None, None, None]) ** 2)
+    assert err < losses[0]
