@@ -472,6 +472,32 @@ lsm_status lsm_unet_train_step(lsm_unet *net, int32_t n, int32_t d, int32_t h, i
 lsm_status lsm_unet_params(const lsm_unet *net, float *dst, lsm_mem mem, lsm_stream stream);
 lsm_status lsm_unet_grad(const lsm_unet *net, float *dst, lsm_mem mem, lsm_stream stream);
 
+/*
+ * Judging a dose estimate against a reference (the denoiser's error against
+ * plain high-history Monte Carlo). Arrays are FP32 [d][h][w] (x fastest),
+ * host or device (mem); the results are returned on the host (synchronises).
+ *
+ * lsm_gamma -- global gamma index (Low, Harms, Mutic & Purdy, Med. Phys. 25,
+ * 656, 1998): over reference voxels above threshold * max(ref), the fraction
+ * with min over points r of |r - r_ref|^2/dta^2 + (eval(r) - ref)^2 /
+ * (dose_crit * max(ref))^2 <= 1, eval interpolated trilinearly (edge values
+ * continued outside), r on a grid of step step_mm within the DTA sphere.
+ * voxel_mm: (z, y, x) voxel size. n_roi (optional): voxels evaluated.
+ * pass_map (optional, same memory kind, d*h*w bytes): 0 outside the region,
+ * 3 pass, 2 fail.
+ */
+lsm_status lsm_gamma(const float *eval, const float *ref, int32_t d, int32_t h, int32_t w, const double voxel_mm[3],
+                     double dose_crit, double dta_mm, double threshold, double step_mm, lsm_mem mem,
+                     double *pass_rate, int64_t *n_roi, unsigned char *pass_map, lsm_stream stream);
+/*
+ * lsm_dose_error -- RMS relative error of est against ref over voxels with
+ * ref > level * max(ref); with sigma_ref (optional) the reference's own mean
+ * relative variance is subtracted: sqrt(max(mean(((est-ref)/ref)^2) -
+ * mean((sigma_ref/ref)^2), 0)).
+ */
+lsm_status lsm_dose_error(const float *est, const float *ref, const float *sigma_ref, int64_t n, double level,
+                          lsm_mem mem, double *rms_rel, lsm_stream stream);
+
 /* Library diagnostics. */
 const char *lsm_last_error(void);
 /* Kernels launched by this library in this process so far. */

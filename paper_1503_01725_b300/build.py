@@ -28,6 +28,7 @@ SOURCES = {
     "nnls.cu": [],
     "denoise.cu": [],
     "train.cu": [],
+    "eval.cu": [],
 }
 
 

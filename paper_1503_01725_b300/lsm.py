@@ -136,6 +136,10 @@ _EXPORTS = {
                                       C.c_void_p]),
     "lsm_unet_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "lsm_unet_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "lsm_gamma": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _dp, C.c_double, C.c_double,
+                            C.c_double, C.c_double, C.c_int, _dp, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p]),
+    "lsm_dose_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, _dp,
+                                 C.c_void_p]),
     "lsm_timing_enable": (C.c_int, [C.c_int]),
     "lsm_timing_read": (C.c_int, [_dp, C.POINTER(C.c_int64), C.c_int]),
     "lsm_last_error": (C.c_char_p, []),
@@ -619,3 +623,52 @@ def lsm_unet_grad(net: UNet) -> np.ndarray:
     out = np.empty(lsm_unet_param_count(), dtype=np.float32)
     _check(_lib.lsm_unet_grad(net.ptr, out.ctypes.data, LSM_MEM_HOST, None), "lsm_unet_grad")
     return out
+
+
+def _arr_ptr(a):
+    """(pointer, memory kind) of a float32 array: numpy (host) or CUDA tensor (device)."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float32 and a.flags.c_contiguous
+        return a.ctypes.data, LSM_MEM_HOST
+    assert a.is_cuda and a.is_contiguous()
+    return a.data_ptr(), LSM_MEM_DEVICE
+
+
+def lsm_gamma(ev, ref, voxel_mm, dose_crit: float = 0.02, dta_mm: float = 2.0, threshold: float = 0.1,
+              step_mm: float = 0.5, pass_map: bool = False, stream=None):
+    """Global gamma pass rate of ev against ref ([d, h, w] float32, both numpy
+    or both CUDA tensors). Returns (pass_rate, n_roi[, pass_map])."""
+    if isinstance(ev, np.ndarray):
+        ev = np.ascontiguousarray(ev, dtype=np.float32)
+        ref = np.ascontiguousarray(ref, dtype=np.float32)
+    pe, mem = _arr_ptr(ev)
+    pr, _ = _arr_ptr(ref)
+    d, h, w = ev.shape
+    vox = (C.c_double * 3)(*voxel_mm)
+    rate, nroi = C.c_double(0.0), C.c_int64(0)
+    pm = None
+    if pass_map:
+        if mem == LSM_MEM_HOST:
+            pm = np.zeros((d, h, w), dtype=np.uint8)
+            pmp = pm.ctypes.data
+        else:
+            import torch
+            pm = torch.zeros((d, h, w), dtype=torch.uint8, device="cuda")
+            pmp = pm.data_ptr()
+    _check(_lib.lsm_gamma(pe, pr, d, h, w, vox, dose_crit, dta_mm, threshold, step_mm, mem, C.byref(rate),
+                          C.byref(nroi), pmp if pass_map else None, _stream(stream)), "lsm_gamma")
+    return (rate.value, nroi.value, pm) if pass_map else (rate.value, nroi.value)
+
+
+def lsm_dose_error(est, ref, sigma_ref=None, level: float = 0.5, stream=None) -> float:
+    if isinstance(est, np.ndarray):
+        est = np.ascontiguousarray(est, dtype=np.float32)
+        ref = np.ascontiguousarray(ref, dtype=np.float32)
+        sigma_ref = None if sigma_ref is None else np.ascontiguousarray(sigma_ref, dtype=np.float32)
+    pe, mem = _arr_ptr(est)
+    pr, _ = _arr_ptr(ref)
+    ps = None if sigma_ref is None else _arr_ptr(sigma_ref)[0]
+    out = C.c_double(0.0)
+    n = est.size if isinstance(est, np.ndarray) else est.numel()
+    _check(_lib.lsm_dose_error(pe, pr, ps, n, level, mem, C.byref(out), _stream(stream)), "lsm_dose_error")
+    return out.value

@@ -283,3 +283,24 @@ def commissioning_truth(n_psr: int, seed: int = 3, zero_frac: float = 0.05) -> n
     x = rng.uniform(0.8, 1.2, n_psr)
     x[rng.random(n_psr) < zero_frac] = 0.0
     return x
+
+
+DENOISE_CASES = 200               # seeded phantoms and fields: 0-179 training, 180-199 test
+DENOISE_TRAIN = range(0, 180)
+DENOISE_TEST = range(180, 200)
+
+
+def workload_denoise(case: int, n_hist: int = 1_000_000) -> Workload:
+    """Denoiser pair `case`: a 128^3 phantom at 0.25 cm (a quarter of the cases
+    plain water, the rest water with seeded slabs and spheres), one square field
+    of 4-20 cm, the three-sub-source model with rings to 3.2 cm. The pair is
+    this workload run with n_hist = 1e6 (input) and 1e8 (target)."""
+    rng = np.random.default_rng(5000 + case)
+    field_cm = float(rng.uniform(4.0, 20.0))
+    if rng.random() < 0.25:
+        ph = water_phantom(128, 128, 128, 0.25)
+    else:
+        ph = heterogeneous_phantom(128, 128, 128, 0.25, seed=7000 + case, n_slabs=int(rng.integers(0, 5)),
+                                   n_spheres=int(rng.integers(2, 13)))
+    return Workload(f"denoise-{case}", psr_model(10, 10, 0.32, seed=3), beams(square_field(field_cm)), ph,
+                    n_hist, 1, 9000 + case, extra={"field_cm": field_cm})
