@@ -71,6 +71,7 @@ def parse():
                    help="library defaults instead of the tuned iteration size, CTAs per SM and graph replay")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the commissioning (batched) block")
+    p.add_argument("--no-denoised", action="store_true", help="skip the denoised-dose block")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
@@ -269,6 +270,68 @@ def commissioning_block(lsm, W, reps: int = 3, n_batches: int = 16):
             "nnls": out}
 
 
+def conv_gflop(d: int, h: int, w: int) -> float:
+    """Algorithmic FLOPs of the network's 14 3x3x3 convolutions (2 per MAC)."""
+    from paper_1503_01725_b300 import denoiser as DZ
+    lv = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0]
+    return sum(2.0 * 27 * ci * co * (d >> l) * (h >> l) * (w >> l) for (ci, co), l in zip(DZ.LAYERS, lv)) / 1e9
+
+
+def denoised_block(lsm, reps: int = 5, case: int = 192):
+    """Denoised dose on a held-out 128^3 case (Sec. 3 run-time comparison at
+    equal error): MC at 1e6 histories plus the network, against plain MC,
+    both judged by a 1e9-history run of the same case."""
+    import torch
+    from paper_1503_01725_b300 import denoiser as DZ
+    from paper_1503_01725_b300 import workloads as W
+    net = DZ.load()
+    p = DZ.generate([case], n_lo=1_000_000, n_hi=1_000_000, n_ref=1_000_000_000)[0]
+    wl = W.workload_denoise(case)
+    ph = lsm.lsm_phantom_create(wl.phantom)
+    keep = (p["rho"] >= DZ.RHO_MIN).float()
+    t_mc, t_net, t_conv, u_lo, u_den, g_den = [], [], [], [], [], []
+    for r in range(reps + 1):
+        lo, _, ms = DZ.mc_dose(wl, 1_000_000, 777 + r, ph=ph)
+        lo = (lo * keep).contiguous()
+        lsm.lsm_timing_read(reset=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        den = lsm.lsm_unet_forward(net, lo, p["rho"])
+        b.record()
+        torch.cuda.synchronize()
+        tm = lsm.lsm_timing_read(reset=True)
+        if r == 0:
+            continue                                   # warm-up (buffers, graph of the MC run)
+        t_mc.append(ms)
+        t_net.append(a.elapsed_time(b))
+        t_conv.append(tm["conv3d"][0])
+        u_lo.append(lsm.lsm_dose_error(lo, p["ref"], p["s_ref"], level=0.5))
+        u_den.append(lsm.lsm_dose_error(den, p["ref"], p["s_ref"], level=0.5))
+        g_den.append(lsm.lsm_gamma(den, p["ref"], (2.5, 2.5, 2.5), 0.02, 2.0, 0.1)[0])
+    T_mc, T_net, T_conv = (float(np.median(x)) / 1e3 for x in (t_mc, t_net, t_conv))
+    ulo, uden = float(np.mean(u_lo)), float(np.mean(u_den))
+    t_den = T_mc + T_net
+    t_plain_same_err = T_mc * (ulo / uden) ** 2
+    gf = conv_gflop(128, 128, 128)
+    hbm, kind = peaks()
+    try:
+        with open(PEAKS_PATH) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+            bkind = "measured bf16_tflops (burst: the network is timed alone)"
+    except Exception:
+        bf16, bkind = 1800.0, "fallback"
+    ach = gf / T_conv / 1e3
+    return {"workload": f"denoise-{case} 128^3 (field {wl.extra['field_cm']:.1f} cm), weights unet128.npz",
+            "judge": "1e9-history MC of the same case", "s_mc_1e6": T_mc, "s_network": T_net,
+            "s_denoised": t_den, "u_rms_mc_1e6": ulo, "u_rms_denoised": uden,
+            "gamma_2pct_2mm_denoised": float(np.mean(g_den)),
+            "s_to_1pct_plain": T_mc * (ulo / 0.01) ** 2,
+            "s_plain_to_denoised_error": t_plain_same_err, "speedup_at_equal_error": t_plain_same_err / t_den,
+            "roofline": {"bound": "tensor", "kernel": "k_conv3d (14 layers)", "achieved": ach, "peak": bf16,
+                         "unit": "TFLOP/s", "frac": ach / bf16, "peak_source": bkind,
+                         "algorithmic_gflop": gf, "s_conv": T_conv}}
+
+
 def run_reference(args, rank, world):
     """The CPU oracle, as it stands, timed on this host (reference arm)."""
     from paper_1503_01725_b300 import workloads as W
@@ -436,6 +499,11 @@ def main():
     batched = None
     if not args.no_batched:
         batched = commissioning_block(lsm, W)
+    denoised = None
+    if not args.no_denoised:
+        lsm.lsm_timing_enable(True)
+        denoised = denoised_block(lsm)
+        lsm.lsm_timing_enable(False)
     cpu = None
     if not args.no_cpu_baseline:
         rate, n_done, el = cpu_oracle_rate(wl, args.cpu_seconds)
@@ -458,6 +526,7 @@ def main():
                           "real": st["real"], "esteps": st["esteps"], "rejected": st["rejected"]},
         "roofline": roofline,
         "batched": batched,
+        "denoised": denoised,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "histories/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
