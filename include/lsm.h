@@ -412,10 +412,11 @@ lsm_status lsm_conv3d_create(int32_t c_in, int32_t c_out, int32_t relu, const fl
 void lsm_conv3d_destroy(lsm_conv3d *conv);
 /*
  * lsm_conv3d_forward -- out[:, c_offset : c_offset + c_out] = act(conv(in) +
- * bias) over every interior voxel, written as BF16; the halo voxels of those
- * output channels are written as zero. in->c must equal c_in and out->c
- * c_out; n, d, h, w must match. Stream-ordered. ctas_per_sm: persistent CTAs
- * per SM (0 = as many as fit).
+ * bias) over every interior voxel, written as BF16. Interior rows are written
+ * whole (their two x-halo voxels as zero); the other halo voxels are read as
+ * the zero padding and left unchanged, so both volumes must hold a zero halo.
+ * in->c must equal c_in and out->c c_out; n, d, h, w must match.
+ * Stream-ordered. ctas_per_sm: persistent CTAs per SM (0 = as many as fit).
  */
 lsm_status lsm_conv3d_forward(const lsm_conv3d *conv, const lsm_vol *in, const lsm_vol *out, int32_t ctas_per_sm,
                               lsm_stream stream);

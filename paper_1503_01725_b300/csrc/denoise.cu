@@ -580,8 +580,10 @@ lsm_status conv_forward(const lsm_conv3d *cv, const lsm_vol *in, const lsm_vol *
     a.bias = cv->bias;
     a.out = (__nv_bfloat16 *)out->data;
     a.lp = v.lp;
-    a.l0 = (long long)v.p + v.w2 + 1;
-    const long long llast = (long long)in->d * v.p + (long long)in->h * v.w2 + in->w;
+    // tiled span: from the x halo before the first interior voxel to the one
+    // after the last, so that interior rows are written whole
+    a.l0 = (long long)v.p + v.w2;
+    const long long llast = (long long)in->d * v.p + (long long)in->h * v.w2 + in->w + 1;
     a.tiles_per_vol = (int)((llast - a.l0 + kTileM) / kTileM);
     a.n_tiles = a.tiles_per_vol * in->n;
     a.out_ct = out->c_total;
