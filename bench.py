@@ -396,7 +396,10 @@ def main():
         # launch parameters picked on this device before the warm-up (untimed)
         from paper_1503_01725_b300 import autotune
         psl_t = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)
-        opts, rep = autotune.tune(psl_t, ph, tally, opts, cache_path=None)
+        # the step rebuilds its plan, so a run graph (captured per plan) would be
+        # re-captured every step: tune without graph replay
+        cands = autotune.candidates(n_plan, args.n_batches, graphs=(False,))
+        opts, rep = autotune.tune(psl_t, ph, tally, opts, cache_path=None, cands=cands)
         tuned = {"chunk": opts.chunk, "ctas_per_sm": opts.ctas_per_sm, "use_graph": opts.use_graph,
                  "candidates": len(rep["trials"])}
         del psl_t
@@ -429,8 +432,9 @@ def main():
         for i in range(args.steps):
             flush.fill_(i & 0xFF)                      # L2 flush outside the timed events
             ev[i][0].record(stream)
-            _, d, s = step(i)
+            res = step(i)
             ev[i][1].record(stream)
+            _, d, s = res          # the previous step's plan is released after the end event
             torch.cuda.synchronize()
             ms_steps.append(ev[i][0].elapsed_time(ev[i][1]))
             u_vals.append(u_mean_rel(d.cpu().numpy(), s.cpu().numpy()))

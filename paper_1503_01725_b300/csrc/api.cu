@@ -128,6 +128,11 @@ void timer_free(void *set)
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t next_uid()
+{
+    static std::atomic<unsigned long long> n{0};
+    return (uint64_t)n.fetch_add(1, std::memory_order_relaxed) + 1;
+}
 void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 bool timing_enabled()
 {

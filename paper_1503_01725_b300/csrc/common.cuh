@@ -91,9 +91,11 @@ struct Stream {
 // --------------------------------------------------------- particle queue ---
 // SoA queue of particles waiting for transport, phantom-local coordinates
 // (x - x0, y - y0, z - z0). pb = psr | beam << 16.
+// A particle queue: three 16-byte words per particle, (x, y, z, E),
+// (u, v, w, stream id bits), (history lo, history hi, PSR | beam << 16 |
+// slot << 20, unused), so that a particle moves as one 48-byte record.
 struct Queue {
-    float *x, *y, *z, *u, *v, *w, *E;
-    uint32_t *glo, *ghi, *sid, *pb;
+    float4 *rec;
     uint32_t cap;
 };
 
@@ -152,6 +154,8 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 namespace lsm {
 // Event timers around kernel groups (see lsm_timing_enable). timer_begin
 // returns a token that timer_end closes; both are no-ops while disabled.
+// a new process-wide unique id (plans and phantoms)
+uint64_t next_uid();
 int timer_begin(int which, cudaStream_t st);
 void timer_end(int token, cudaStream_t st);
 // timers recorded during a graph capture: detached after it, resolved per replay

@@ -32,7 +32,8 @@ struct SampleParams {
 
 // What a captured run graph depends on besides the seed.
 struct GraphKey {
-    const void *psl, *ph, *part, *ws, *batch;
+    uint64_t psl, ph;     // creation ids of the plan and the phantom
+    const void *part, *ws, *batch;
     lsm_run_opts o;
     int timed;            // captured with the event timers on
 };
@@ -41,6 +42,7 @@ struct GraphKey {
 
 struct lsm_psl {
     int device;
+    uint64_t uid;         // unique per created plan (graph-cache key; addresses can be reused)
     void *arena;          // every device array below lives in this one allocation
     int n_e, n_r, n_xy, n_beams, per_psr;
     double dr, z_phsp, sigma_s, e_lo[3], de[3];
@@ -62,6 +64,7 @@ struct lsm_psl {
 
 struct lsm_phantom {
     int device;
+    uint64_t uid;         // unique per created phantom
     int nx, ny, nz;
     double dx, dy, dz, x0, y0, z0;
     float *d_rho;         // density

@@ -170,6 +170,8 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     const int64_t n = (int64_t)D->nx * D->ny * D->nz;
     if (n >= ((int64_t)1 << 31)) return set_arg_error("lsm_phantom_create: more than 2^31 voxels");
     lsm_phantom *P = (lsm_phantom *)calloc(1, sizeof(lsm_phantom));
+    if (!P) return set_arg_error("lsm_phantom_create: out of host memory");
+    P->uid = next_uid();
     cudaGetDevice(&P->device);
     P->nx = D->nx; P->ny = D->ny; P->nz = D->nz;
     P->dx = D->dx; P->dy = D->dy; P->dz = D->dz; P->x0 = D->x0; P->y0 = D->y0; P->z0 = D->z0;

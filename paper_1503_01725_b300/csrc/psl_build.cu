@@ -497,6 +497,8 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
             if (per_psr_hist[k] < 0) return set_arg_error("lsm_build_psl: negative per-PSR history count");
 
     lsm_psl *P = (lsm_psl *)calloc(1, sizeof(lsm_psl));
+    if (!P) return set_arg_error("lsm_build_psl: out of host memory");
+    P->uid = next_uid();
     cudaGetDevice(&P->device);
     P->n_e = ne; P->n_r = nr; P->n_xy = nxy; P->n_beams = nb; P->per_psr = per_psr_hist != nullptr;
     P->dr = M->dr; P->z_phsp = M->z_phsp; P->sigma_s = M->sigma_s;

@@ -218,11 +218,13 @@ struct Part {
 
 __device__ __forceinline__ void load_part(const Queue &q, uint32_t i, uint32_t k0, uint32_t k1, Part &p)
 {
-    p.x = q.x[i]; p.y = q.y[i]; p.z = q.z[i];
-    p.u = q.u[i]; p.v = q.v[i]; p.w = q.w[i]; p.E = q.E[i];
+    const float4 a = q.rec[3 * (size_t)i], b = q.rec[3 * (size_t)i + 1], c = q.rec[3 * (size_t)i + 2];
+    p.x = a.x; p.y = a.y; p.z = a.z; p.E = a.w;
+    p.u = b.x; p.v = b.y; p.w = b.z;
     p.rng.k0 = k0; p.rng.k1 = k1;
-    p.rng.glo = q.glo[i]; p.rng.ghi = q.ghi[i]; p.rng.sid = q.sid[i]; p.rng.ctr = 0;
-    p.pb = q.pb[i];
+    p.rng.glo = __float_as_uint(c.x); p.rng.ghi = __float_as_uint(c.y); p.rng.sid = __float_as_uint(b.w);
+    p.rng.ctr = 0;
+    p.pb = __float_as_uint(c.z);
     p.steps = 0;
     p.vc = -1;
     p.rc = 0.0f;
@@ -233,8 +235,10 @@ __device__ __forceinline__ void store_part(const Queue &q, uint32_t i, float x, 
                                            float v, float w, float E, uint32_t glo, uint32_t ghi, uint32_t sid,
                                            uint32_t pb)
 {
-    q.x[i] = x; q.y[i] = y; q.z[i] = z; q.u[i] = u; q.v[i] = v; q.w[i] = w; q.E[i] = E;
-    q.glo[i] = glo; q.ghi[i] = ghi; q.sid[i] = sid; q.pb[i] = pb;
+    float4 *r = q.rec + 3 * (size_t)i;
+    r[0] = make_float4(x, y, z, E);
+    r[1] = make_float4(u, v, w, __uint_as_float(sid));
+    r[2] = make_float4(__uint_as_float(glo), __uint_as_float(ghi), __uint_as_float(pb), 0.0f);
 }
 
 // Append one particle from divergent code: one atomic per coalesced group.
@@ -821,7 +825,7 @@ __global__ void k_ebin_count(Queue e, IterCounters *cnt)
     __syncthreads();
     const uint32_t n = min(*(volatile uint32_t *)&cnt->n[2], e.cap);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        atomicAdd(&h[ebin_key(e.E[i])], 1u);
+        atomicAdd(&h[ebin_key(e.rec[3 * (size_t)i].w)], 1u);
     __syncthreads();
     for (int i = threadIdx.x; i < kEBins; i += blockDim.x)
         if (h[i]) atomicAdd(&cnt->bins[i], h[i]);
@@ -843,7 +847,8 @@ __global__ void k_ebin_scatter(Queue e, Queue o, IterCounters *cnt)
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
         const uint32_t i = base + threadIdx.x;
         if (i >= n) break;
-        const int key = ebin_key(e.E[i]);
+        const float4 a = e.rec[3 * (size_t)i], b = e.rec[3 * (size_t)i + 1], c = e.rec[3 * (size_t)i + 2];
+        const int key = ebin_key(a.w);
         // one cursor update per group of lanes sharing a bin
         const unsigned grp = __match_any_sync(__activemask(), key);
         const int leader = __ffs(grp) - 1;
@@ -853,8 +858,10 @@ __global__ void k_ebin_scatter(Queue e, Queue o, IterCounters *cnt)
         unsigned lt;
         lanemask_lt(lt);
         slot += __popc(grp & lt);
-        store_part(o, slot, e.x[i], e.y[i], e.z[i], e.u[i], e.v[i], e.w[i], e.E[i], e.glo[i], e.ghi[i], e.sid[i],
-                   e.pb[i]);
+        float4 *r = o.rec + 3 * (size_t)slot;
+        r[0] = a;
+        r[1] = b;
+        r[2] = c;
     }
 }
 
@@ -945,7 +952,7 @@ cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t)
         t->ws = nullptr;
         size_t total = 1024;
         const uint32_t c2[4] = {chunk, 2 * chunk, ecap, ecap};
-        for (int k = 0; k < 4; ++k) total += (size_t)c2[k] * 44 + 11 * 256;
+        for (int k = 0; k < 4; ++k) total += (size_t)c2[k] * 48 + 256;
         cudaError_t e = cudaMalloc(&t->ws, total);
         if (e != cudaSuccess) return e;
         t->ws_chunk = chunk;
@@ -960,10 +967,8 @@ cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t)
     for (int k = 0; k < 4; ++k) {
         Queue &q = W.q[k];
         q.cap = caps[k];
-        float **f[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
-        for (int j = 0; j < 7; ++j) { *f[j] = (float *)p; p += ((size_t)caps[k] * 4 + 255) / 256 * 256; }
-        uint32_t **u[4] = {&q.glo, &q.ghi, &q.sid, &q.pb};
-        for (int j = 0; j < 4; ++j) { *u[j] = (uint32_t *)p; p += ((size_t)caps[k] * 4 + 255) / 256 * 256; }
+        q.rec = (float4 *)p;
+        p += ((size_t)caps[k] * 48 + 255) / 256 * 256;
     }
     return cudaSuccess;
 }
@@ -1270,7 +1275,7 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         GraphKey gk;
         memset(&gk, 0, sizeof(GraphKey));
         gk.timed = timing_enabled() ? 1 : 0;
-        gk.psl = P; gk.ph = ph; gk.part = t->d_part; gk.ws = t->ws; gk.batch = t->d_batch;
+        gk.psl = P->uid; gk.ph = ph->uid; gk.part = t->d_part; gk.ws = t->ws; gk.batch = t->d_batch;
         gk.o = o;
         gk.o.n_batches = o.n_batches;
         if (!t->gexec || memcmp(&gk, &t->gkey, sizeof(GraphKey)) != 0) {

@@ -267,6 +267,27 @@ def test_graph_replay_matches_direct_runs(L):
     assert not np.allclose(res[(True, 11)], res[(True, 12)])
 
 
+def test_graph_cache_tells_plans_apart(L):
+    """A plan built after another was freed may reuse its addresses; the graph
+    of the first must not be replayed for the second."""
+    wl = W.workload_full_10x10(100_000)
+    ph = L.lsm_phantom_create(wl.phantom)
+    t = L.lsm_tally_create(ph)
+    g1 = L.lsm_build_psl(wl.model, wl.beams, 25_000)
+    L.lsm_run(g1, ph, t, 5, L.RunOpts(n_batches=4, use_graph=True))
+    del g1
+    g2 = L.lsm_build_psl(wl.model, W.beams(W.square_field(5.0)), 20_000)
+    L.lsm_tally_reset(t)
+    L.lsm_run(g2, ph, t, 5, L.RunOpts(n_batches=4, use_graph=True))
+    a, _, _ = L.lsm_tally_read(t)
+    led, st = L.lsm_tally_ledger(t)
+    assert st["histories"] == 4 * 20_000
+    L.lsm_tally_reset(t)
+    L.lsm_run(g2, ph, t, 5, L.RunOpts(n_batches=4, use_graph=False))
+    b, _, _ = L.lsm_tally_read(t)
+    np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6 * b.max())
+
+
 def test_graph_replay_keeps_kernel_timers(L):
     """Timers captured into the graph are read after every replay: same kernel
     groups and launch counts as a direct run."""
