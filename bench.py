@@ -48,9 +48,10 @@ FALLBACK_HBM_GBS = 6400.0
 #   electron transport: per CSDA step one density load (4 B) + one tally update
 #     (4 B read + 4 B write), per electron the queue read (44 B).
 # DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# on a reduced case of this workload; profiles/transport_3src-10x10-water64.md.
+# on a reduced case of this workload (2e6 histories: 91.9 MB over 1,550,866
+# photons; 51.1 MB over 4,941,500 electron steps); profiles/transport_3src-10x10-water64.md.
 # Valid for the kernels as profiled; set to None when they change.
-TRAFFIC_PER_UNIT = {"photon": ("photons", 57.6), "electron": ("esteps", 9.55)}
+TRAFFIC_PER_UNIT = {"photon": ("photons", 59.3), "electron": ("esteps", 10.33)}
 B_SAMPLE_PER_HIST = 68.0
 B_FLIGHT = 4.0
 B_QUEUE = 44.0

@@ -100,15 +100,12 @@ struct Queue {
 };
 
 // Counters of one sample/transport iteration (device memory, zeroed per iteration).
-constexpr int kEBins = 64;                // log-energy bins of the electron counting sort
 
 struct IterCounters {
-    uint32_t n[4];      // queue fill: 0 primary photons, 1 annihilation photons, 2 electrons,
-                        // 3 electrons sorted by descending energy
+    uint32_t n[4];      // queue fill: 0 primary photons, 1 annihilation photons, 2 electrons
     uint32_t head[4];   // refill cursors of the persistent transport kernels
     uint32_t overflow;  // electrons deposited in place because the queue was full
     uint32_t pad;       // table-staging timeout flag
-    uint32_t bins[kEBins];   // electron energy histogram, then bin cursors
 };
 
 // Run-long statistics and the FP64 energy ledger.
