@@ -117,6 +117,9 @@ typedef struct {
  */
 lsm_status lsm_build_psl(const lsm_psr_model *model, const lsm_beams *beams, int64_t n_hist,
                          const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream);
+/* Releases the plan; its device memory returns to the pool in the order of
+ * the legacy default stream. Work using the plan on non-blocking streams must
+ * have completed. */
 void lsm_psl_destroy(lsm_psl *psl);
 
 /* info: [n_xy, n_entries, plan size (histories per pass), per_psr flag];

@@ -508,8 +508,9 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     P->ncell = ncell;
 
     // One device allocation holds every table of the plan and the scratch of
-    // the build (released only by lsm_psl_destroy): cudaMalloc/cudaFree calls
-    // synchronise the device, so a build makes one of each.
+    // the build (released only by lsm_psl_destroy). It is stream-ordered
+    // (cudaMallocAsync from the device's memory pool): a build neither waits
+    // for the device nor makes the device wait for it.
     const size_t nbse = (size_t)nb * 3 * ne;
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
@@ -525,8 +526,8 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     const size_t o_res = take(64), o_dkb = take((size_t)npsr * nb * 8), o_rank = take((size_t)ncell * 4);
     char *base = nullptr;
     {
-        cudaError_t e_ = cudaMalloc((void **)&base, off);
-        if (e_ != cudaSuccess) { free_psl(P); return set_cuda_error(e_, "lsm_build_psl: cudaMalloc"); }
+        cudaError_t e_ = cudaMallocAsync((void **)&base, off, st);
+        if (e_ != cudaSuccess) { free_psl(P); return set_cuda_error(e_, "lsm_build_psl: cudaMallocAsync"); }
     }
     P->arena = base;
     double *d_in = (double *)(base + o_in);
@@ -664,10 +665,13 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
 #undef CKL
 }
 
+// The arena returns to the pool in the order of the legacy default stream,
+// i.e. after the work already queued on the blocking streams; work that uses
+// the plan on other streams must be complete (lsm_psl_destroy's contract).
 lsm_status free_psl(lsm_psl *P)
 {
     if (!P) return LSM_OK;
-    if (P->arena) cudaFree(P->arena);
+    if (P->arena) cudaFreeAsync(P->arena, 0);
     free(P);
     return LSM_OK;
 }
