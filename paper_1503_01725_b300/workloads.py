@@ -304,3 +304,45 @@ def workload_denoise(case: int, n_hist: int = 1_000_000) -> Workload:
                                    n_spheres=int(rng.integers(2, 13)))
     return Workload(f"denoise-{case}", psr_model(10, 10, 0.32, seed=3), beams(square_field(field_cm)), ph,
                     n_hist, 1, 9000 + case, extra={"field_cm": field_cm})
+
+
+def pslfile_records(seed: int, n_xy: int = 20, dr: float = 0.25, n_e: int = 10, mean_per_cell: float = 40.0,
+                    z_phsp: float = Z_PHSP) -> dict:
+    """Synthetic PSL-file contents, grouped by cell c = (stype * n_xy + iy) *
+    n_xy + ix: per-cell counts ~ Poisson(mean_per_cell * ring profile),
+    positions uniform in the cell on the phase-space plane, directions from
+    the target (z = 0) with a sub-source-dependent Gaussian spread (0.002,
+    0.03, 0.06 rad), energies uniform in (0.2, 6.2) MeV; sub-source 2 are
+    electrons. Returns float32 x y u v w E, int type, psr, stype, ebin, cell
+    (file order) and the index `starts` [3 n_xy^2 + 1]."""
+    rng = np.random.default_rng(seed)
+    n_r = n_xy // 2
+    npsl = n_xy * n_xy
+    c = np.arange(npsl)
+    iy, ix = c // n_xy, c % n_xy
+    r = np.hypot((ix - n_r + 0.5) * dr, (iy - n_r + 0.5) * dr)
+    prof = np.exp(-0.5 * (r / (0.6 * n_r * dr)) ** 2)
+    lam = np.concatenate([mean_per_cell * prof * f for f in (1.0, 0.5, 0.1)])
+    counts = rng.poisson(lam).astype(np.int64)
+    cell = np.repeat(np.arange(3 * npsl), counts)
+    n = len(cell)
+    s = cell // npsl
+    j = cell % npsl
+    x = (j % n_xy - n_r + rng.random(n)) * dr
+    y = (j // n_xy - n_r + rng.random(n)) * dr
+    spread = np.array([0.002, 0.03, 0.06])[s]
+    ax = np.arctan2(x, z_phsp) + spread * rng.standard_normal(n)
+    ay = np.arctan2(y, z_phsp) + spread * rng.standard_normal(n)
+    ta, tb = np.tan(ax), np.tan(ay)
+    d = np.sqrt(ta * ta + tb * tb + 1.0)
+    ebin = rng.integers(0, n_e, n)
+    ring = np.minimum((np.hypot(x, y) / dr).astype(np.int64), n_r - 1)
+    return {
+        "x": x.astype(np.float32), "y": y.astype(np.float32),
+        "u": (ta / d).astype(np.float32), "v": (tb / d).astype(np.float32), "w": (1.0 / d).astype(np.float32),
+        "E": (0.2 + 6.0 * rng.random(n)).astype(np.float32),
+        "type": (s == 2).astype(np.int64), "stype": s, "ebin": ebin,
+        "psr": (s * n_e + ebin) * n_r + ring, "cell": cell,
+        "starts": np.concatenate([[0], np.cumsum(counts)]).astype(np.int64),
+        "n_xy": n_xy, "dr": dr, "n_e": n_e, "z_phsp": z_phsp,
+    }
