@@ -73,6 +73,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the commissioning (batched) block")
     p.add_argument("--no-denoised", action="store_true", help="skip the denoised-dose block")
+    p.add_argument("--no-pslfile", action="store_true", help="skip the PSL-file comparator block")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
@@ -333,6 +334,95 @@ def denoised_block(lsm, reps: int = 5, case: int = 192):
                          "algorithmic_gflop": gf, "s_conv": T_conv}}
 
 
+def _fs_type(path: str) -> str:
+    """File-system type of the mount holding `path` (from /proc/mounts)."""
+    best, kind = "", "unknown"
+    try:
+        with open("/proc/mounts") as f:
+            for ln in f:
+                parts = ln.split()
+                if len(parts) >= 3 and path.startswith(parts[1]) and len(parts[1]) > len(best):
+                    best, kind = parts[1], parts[2]
+    except OSError:
+        pass
+    return kind
+
+
+def pslfile_block(lsm, W, n_file: int = 1 << 24, n_batches: int = 10):
+    """The comparator of Table 1: dose from PSL files on disk (read, copy to
+    the GPU, translate there, transport) against particles sampled on the fly
+    from the analytic model, at equal histories, for a 10x10 and a 2x2 cm2
+    field. The file holds every history of a 40x40 cm2 plan of the same
+    model; each field reads the records of the PSL cells it includes."""
+    import torch
+    wl = W.workload_full_10x10()
+    ph = lsm.lsm_phantom_create(wl.phantom)
+    d = tempfile.mkdtemp(prefix="lsm_pslfile_")
+    path = os.path.join(d, "open40.psl")
+    try:
+        open_plan = lsm.lsm_build_psl(wl.model, W.beams(W.square_field(40.0)), n_file)
+        t0 = time.perf_counter()
+        lsm.lsm_pslfile_write(open_plan, 4242, path)
+        t_write = time.perf_counter() - t0
+        del open_plan
+        fields = {}
+        stream = torch.cuda.current_stream()
+        for size in (10.0, 2.0):
+            beams = W.beams(W.square_field(size))
+            field = lsm.lsm_build_psl(wl.model, beams, 1000)
+            t = lsm.lsm_tally_create(ph)
+            opts = lsm.RunOpts(n_batches=n_batches)
+            lsm.lsm_pslfile_run(path, field, ph, t, 1, n_batches=n_batches, opts=opts)     # warm-up
+            runs = {}
+            for cold in (True, False):
+                lsm.lsm_tally_reset(t)
+                lsm.lsm_timing_read(reset=True)
+                st = lsm.lsm_pslfile_run(path, field, ph, t, 2, n_batches=n_batches, cold=cold, opts=opts)
+                tm = lsm.lsm_timing_read(reset=True)
+                runs["cold" if cold else "page_cache"] = {
+                    "s_total": st["t_total_s"], "s_read": st["t_read_s"], "s_copy": st["t_copy_s"],
+                    "s_translate": tm["sample"][0] / 1e3,
+                    "s_transport": (tm["photon"][0] + tm["annihilation_photon"][0] + tm["electron"][0]) / 1e3,
+                    "GB_read": st["bytes"] / 1e9, "cache_dropped": bool(st["cold"])}
+            n = int(st["records"])
+            # the analytic source at the same histories: plan build + sampled run
+            lsm.lsm_tally_reset(t)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = lsm.lsm_build_psl(wl.model, beams, n)
+            torch.cuda.synchronize()
+            t_init = time.perf_counter() - t0
+            lsm.lsm_run(g, ph, t, 3, opts)                                               # warm-up
+            lsm.lsm_tally_reset(t)
+            lsm.lsm_timing_read(reset=True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a.record(stream)
+            lsm.lsm_run(g, ph, t, 4, opts)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t_run = time.perf_counter() - t0
+            tm = lsm.lsm_timing_read(reset=True)
+            cold = runs["cold"]
+            fields[f"{size:g}x{size:g}"] = {
+                "histories": n, "psl_files": runs,
+                "analytic": {"s_total": t_init + t_run, "s_src_init": t_init, "s_run_events": a.elapsed_time(b) / 1e3,
+                             "s_gen_translate": tm["sample"][0] / 1e3,
+                             "s_transport": (tm["photon"][0] + tm["annihilation_photon"][0] + tm["electron"][0]) / 1e3},
+                "speedup_analytic_vs_cold_files": cold["s_total"] / (t_init + t_run),
+                "read_share_cold": cold["s_read"] / cold["s_total"]}
+        return {"file": {"records": n_file, "GB": os.path.getsize(path) / 1e9, "s_write": t_write,
+                         "fs": _fs_type(d), "plan": "40x40 cm2, all PSLs"},
+                "n_batches": n_batches, "fields": fields}
+    finally:
+        try:
+            os.remove(path)
+        except OSError:
+            pass
+        os.rmdir(d)
+
+
 def run_reference(args, rank, world):
     """The CPU oracle, as it stands, timed on this host (reference arm)."""
     from paper_1503_01725_b300 import workloads as W
@@ -509,6 +599,11 @@ def main():
         lsm.lsm_timing_enable(True)
         denoised = denoised_block(lsm)
         lsm.lsm_timing_enable(False)
+    pslfile = None
+    if not args.no_pslfile:
+        lsm.lsm_timing_enable(True)
+        pslfile = pslfile_block(lsm, W)
+        lsm.lsm_timing_enable(False)
     cpu = None
     if not args.no_cpu_baseline:
         rate, n_done, el = cpu_oracle_rate(wl, args.cpu_seconds)
@@ -532,6 +627,7 @@ def main():
         "roofline": roofline,
         "batched": batched,
         "denoised": denoised,
+        "pslfile": pslfile,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "histories/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},

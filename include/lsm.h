@@ -11,7 +11,8 @@
  *     lsm_last_error(). LSM_ERR_OVERFLOW / LSM_ERR_TIMEOUT: the GPU work ran to
  *     completion but a bounded resource (a particle queue, a step cap, a
  *     bounded wait) was exhausted; results are complete except for the counted
- *     events, which were handled as documented at the call.
+ *     events, which were handled as documented at the call. LSM_ERR_IO: a
+ *     file could not be opened, read or written (the message names it).
  *   - Handles (lsm_psl, lsm_phantom, lsm_tally) are opaque, created and owned
  *     by the library, and must be released with the matching *_destroy. A
  *     handle lives on the device that was current when it was created.
@@ -42,7 +43,8 @@ typedef enum {
     LSM_ERR_CUDA = 2,
     LSM_ERR_OVERFLOW = 3,
     LSM_ERR_TIMEOUT = 4,
-    LSM_ERR_NOT_CONVERGED = 5
+    LSM_ERR_NOT_CONVERGED = 5,
+    LSM_ERR_IO = 6
 } lsm_status;
 
 typedef enum { LSM_MEM_HOST = 0, LSM_MEM_DEVICE = 1 } lsm_mem;
@@ -501,6 +503,68 @@ lsm_status lsm_gamma(const float *eval, const float *ref, int32_t d, int32_t h, 
  */
 lsm_status lsm_dose_error(const float *est, const float *ref, const float *sigma_ref, int64_t n, double level,
                           lsm_mem mem, double *rms_rel, lsm_stream stream);
+
+/*
+ * PSL files -- the comparator source model of Table 1 (Sec. 3.1): particles
+ * stored on disk grouped by phase-spacelet, read for a field, copied to the
+ * GPU and translated there, instead of being sampled on the fly.
+ *
+ * File layout (little endian): a 4096-byte header
+ *   char magic[8] = "LSMPSLF1"; uint32 version = 1; uint32 record_bytes = 32;
+ *   int32 n_xy, n_e, n_r, 0; double dr, z_phsp, w_record, denom;
+ *   int64 n_records, index_offset, data_offset; uint64 seed;
+ * then at index_offset int64 start[3 n_xy n_xy + 1]: records of PSL cell
+ * c = (stype * n_xy + iy) * n_xy + ix are [start[c], start[c+1]); then at
+ * data_offset (a multiple of 4096) n_records records of 32 bytes:
+ *   float x, y (cm, on the phase-space plane), u, v, w, E (MeV);
+ *   uint32 psr | type << 16 (type 0 photon, 1 electron); uint32 stype | ebin << 8.
+ * Every record stands for source weight w_record = denom / n_records.
+ */
+typedef struct {
+    int64_t records;      /* records read (all passes) */
+    int64_t bytes;        /* bytes read from the file */
+    int64_t chunks;       /* chunks transported */
+    double t_read_s;      /* time the reader thread spent in read calls */
+    double t_copy_s;      /* host-to-device copy time (events on the copy stream) */
+    double t_total_s;     /* wall time of the whole call */
+    double dose_scale;    /* scale for lsm_dose: n_batches * w_record */
+    int32_t cold;         /* the file's page cache was dropped before reading */
+    int32_t pad;
+} lsm_pslfile_stats;
+
+/*
+ * lsm_pslfile_write -- sample every history of `plan` (a whole-source,
+ * single-beam plan, normally with the jaws wide open) at the phase-space
+ * plane (lsm_sample with z_surface = z_phsp and key `seed`) and write them as
+ * a PSL file at `path`, grouped by PSL cell. Synchronises. n_written
+ * (optional) receives the record count. Errors: LSM_ERR_ARG for a per-PSR or
+ * multi-beam plan or a plan above 2^28 histories; LSM_ERR_IO if the file
+ * cannot be written.
+ */
+lsm_status lsm_pslfile_write(const lsm_psl *plan, uint64_t seed, const char *path, int64_t *n_written,
+                             lsm_stream stream);
+
+/*
+ * lsm_pslfile_run -- dose from a PSL file for the field of `field` (a
+ * whole-source single-beam plan on the file's PSL grid; only its inclusion
+ * table and jaws are used). The records of the PSL cells that the field's
+ * sampling areas include (primary cells for sub-source 0, scatter/electron
+ * cells for 1 and 2) are read from disk by a reader thread into pinned
+ * buffers, copied to the GPU on a copy stream, and for each chunk a kernel
+ * applies the jaw test at the upper jaw surfaces, flies the particle to the
+ * phantom surface and queues it for the same photon/electron transport as
+ * lsm_run. Included record j of pass p is history p * N + j (N included
+ * records per pass) and falls in batch slot j mod n_batches; every pass ends
+ * by folding n_batches batches into the tally. Pass p > 0 reuses the same
+ * records with new transport streams. opts->chunk: records per chunk (0 = 2^22).
+ * cold != 0: drop the file's cached pages first (fdatasync + fadvise), so
+ * that reads come from storage. stats (optional) as above.
+ * Errors: LSM_ERR_ARG on a file/plan mismatch or bad counts; LSM_ERR_IO on
+ * read errors; LSM_ERR_OVERFLOW as lsm_run.
+ */
+lsm_status lsm_pslfile_run(const char *path, const lsm_psl *field, const lsm_phantom *ph, lsm_tally *tally,
+                           uint64_t seed, int32_t n_batches, int32_t n_passes, int32_t cold,
+                           const lsm_run_opts *opts, lsm_pslfile_stats *stats, lsm_stream stream);
 
 /* Library diagnostics. */
 const char *lsm_last_error(void);

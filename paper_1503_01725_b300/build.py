@@ -29,6 +29,7 @@ SOURCES = {
     "denoise.cu": [],
     "train.cu": [],
     "eval.cu": [],
+    "pslfile.cu": [],
 }
 
 

@@ -152,6 +152,12 @@ lsm_status set_arg_error(const char *msg)
     return LSM_ERR_ARG;
 }
 
+lsm_status set_io_error(const char *what, const char *path, int err)
+{
+    snprintf(g_err, sizeof(g_err), "%s %s: %s", what, path ? path : "(null)", err ? strerror(err) : "short transfer");
+    return LSM_ERR_IO;
+}
+
 int sm_count()
 {
     static int n = 0;

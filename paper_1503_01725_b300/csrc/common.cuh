@@ -165,6 +165,7 @@ void add_launches(int64_t n);     // kernels launched by a replayed graph
 bool timing_enabled();
 lsm_status set_cuda_error(cudaError_t e, const char *where);
 lsm_status set_arg_error(const char *msg);
+lsm_status set_io_error(const char *what, const char *path, int err);
 int sm_count();
 }  // namespace lsm
 

@@ -38,6 +38,22 @@ struct GraphKey {
     int timed;            // captured with the event timers on
 };
 
+// One record of a PSL particle file: a particle on the phase-space plane.
+struct PslRec {
+    float x, y, u, v, w, E;
+    uint32_t tag;         // PSR index | particle type << 16 (0 photon, 1 electron)
+    uint32_t info;        // sub-source | energy bin << 8
+};
+static_assert(sizeof(PslRec) == 32, "PSL file record layout");
+
+// Jaw test and flight to the phantom of PSL-file particles for one beam.
+struct PslGeom {
+    float jaw[4];         // ylo, yhi, xlo, xhi of the opening on the upper jaw surfaces
+    float zy_rel, zx_rel; // upper jaw surfaces - phase-space plane
+    float z_rel;          // phantom surface - phase-space plane
+    float x0, y0;         // phantom corner on the surface plane
+};
+
 }  // namespace lsm
 
 struct lsm_psl {

@@ -750,6 +750,95 @@ __global__ void k_set_key(uint32_t *key, uint32_t k0, uint32_t k1, const unsigne
     *(unsigned long long *)(key + 2) = *ovf;
 }
 
+// ------------------------------------------------------ PSL-file source ---
+// Particles read from PSL files (the comparator source model of Table 1):
+// jaw test at the upper jaw surfaces, straight flight to the phantom surface,
+// then the same compaction into the photon and electron queues as the
+// sampler's. Record i of the chunk is history g0 + i and position i0 + i of
+// the pass, which puts it in batch slot (i0 + i) mod nb. The test and the
+// flight are written as single-precision roundings in a fixed order (no
+// contraction), so that the accept and miss decisions are reproducible.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_pslfile_enqueue(const PslRec *__restrict__ rec, int64_t n, uint64_t g0,
+                                                         int64_t i0, int nb, PslGeom G, TP T, Queue pq, Queue eq)
+{
+    const unsigned lane = lane_id();
+    unsigned lt;
+    lanemask_lt(lt);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double src = 0.0, rej = 0.0, esc = 0.0;
+    Acc A = {0.0, 0.0, 0.0f, 0ull, 0ull, 0ull, 0ull};
+    unsigned long long nph = 0, nel = 0, nrej = 0, nmiss = 0;
+    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        bool in = false, is_e = false;
+        float lx = 0.0f, ly = 0.0f, u = 0.0f, v = 0.0f, w = 1.0f, E = 0.0f;
+        uint32_t tag = 0;
+        if (i < n) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(rec + i);
+            const float4 a = __ldg(r4), b = __ldg(r4 + 1);
+            const float x = a.x, y = a.y;
+            u = a.z; v = a.w; w = b.x; E = b.y;
+            tag = __float_as_uint(b.z);
+            is_e = (tag >> 16) == 1u;
+            const float iw = __fdiv_rn(1.0f, w);
+            const float yJ = __fadd_rn(y, __fmul_rn(__fmul_rn(G.zy_rel, v), iw));
+            const float xJ = __fadd_rn(x, __fmul_rn(__fmul_rn(G.zx_rel, u), iw));
+            src += E;
+            if (!(yJ >= G.jaw[0] && yJ <= G.jaw[1] && xJ >= G.jaw[2] && xJ <= G.jaw[3])) {
+                rej += E;
+                nrej++;
+            } else {
+                lx = __fsub_rn(__fadd_rn(x, __fmul_rn(__fmul_rn(G.z_rel, u), iw)), G.x0);
+                ly = __fsub_rn(__fadd_rn(y, __fmul_rn(__fmul_rn(G.z_rel, v), iw)), G.y0);
+                in = voxel(T, lx, ly, 0.0f) >= 0;
+                if (!in) { esc += E; nmiss++; }
+            }
+        }
+        const bool local_e = in && is_e && T.electron_mode == 0;
+        const unsigned mp = __ballot_sync(0xffffffffu, in && !is_e);
+        const unsigned me = __ballot_sync(0xffffffffu, in && is_e && !local_e);
+        uint32_t bp = 0, be = 0;
+        if (lane == 0) {
+            if (mp) bp = atomicAdd(&T.cnt->n[0], (uint32_t)__popc(mp));
+            if (me) be = atomicAdd(&T.cnt->n[2], (uint32_t)__popc(me));
+        }
+        bp = __shfl_sync(0xffffffffu, bp, 0);
+        be = __shfl_sync(0xffffffffu, be, 0);
+        if (in) {
+            const uint64_t g = g0 + (uint64_t)i;
+            const uint32_t pb = pb_make(tag & 0xFFFFu, 0u, (uint32_t)((i0 + i) % nb));
+            if (!is_e) {
+                nph++;
+                store_part(pq, bp + __popc(mp & lt), lx, ly, 0.0f, u, v, w, E, (uint32_t)g, (uint32_t)(g >> 32), 1u,
+                           pb);
+            } else {
+                nel++;
+                if (local_e)
+                    deposit<MODE>(T, A, voxel(T, lx, ly, 0.0f), E, pb);
+                else
+                    store_part(eq, be + __popc(me & lt), lx, ly, 0.0f, u, v, w, E, (uint32_t)g, (uint32_t)(g >> 32),
+                               1u, pb);
+            }
+        }
+    }
+    src = warp_sum(src); rej = warp_sum(rej); esc = warp_sum(esc);
+    const double dep = warp_sum(A.dep + (double)A.dep32);
+    nph = warp_sum_u64(nph); nel = warp_sum_u64(nel); nrej = warp_sum_u64(nrej); nmiss = warp_sum_u64(nmiss);
+    if (lane == 0) {
+        atomicAdd(&T.stats->ledger[0], src);
+        if (rej != 0.0) atomicAdd(&T.stats->ledger[1], rej);
+        if (esc != 0.0) atomicAdd(&T.stats->ledger[2], esc);
+        if (dep != 0.0) atomicAdd(&T.stats->ledger[3], dep);
+        if (nph) atomicAdd(&T.stats->c[1], nph);
+        if (nel) atomicAdd(&T.stats->c[2], nel);
+        if (nrej) atomicAdd(&T.stats->c[3], nrej);
+        if (nmiss) atomicAdd(&T.stats->c[4], nmiss);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&T.stats->c[0], (unsigned long long)n);
+}
+
 // ------------------------------------------------------------- tallies ---
 
 __global__ void k_flush(float *__restrict__ part, double *__restrict__ batch, int64_t n)
@@ -1116,6 +1205,75 @@ lsm_status transport_particles(const lsm_phantom *ph, const lsm_particles *in, i
     if (rc) return rc;
     if (ovf) return LSM_ERR_OVERFLOW;
     return LSM_OK;
+}
+
+// PSL-file runs: one workspace for the whole run; every chunk of records is
+// enqueued and transported in stream order without host synchronisation, its
+// deposits landing in the batch slot of each record; a pass ends by folding
+// the nb slots into S1/S2 as nb batches.
+struct PslFileRun {
+    Workspace W;
+    TP T;
+    lsm_tally *t;
+    int nb;
+};
+
+lsm_status pslfile_begin(const lsm_phantom *ph, lsm_tally *t, const lsm_run_opts *opts, int64_t cap, int nb,
+                         uint64_t seed, cudaStream_t st, PslFileRun **out)
+{
+    *out = nullptr;
+    if (t->nvox != (int64_t)ph->nx * ph->ny * ph->nz) return set_arg_error("lsm_pslfile_run: tally of another phantom");
+    if (t->mode != 0) return set_arg_error("lsm_pslfile_run: needs a dose (mode 0) tally");
+    if (nb < 1 || nb > 255) return set_arg_error("lsm_pslfile_run: 1 <= n_batches <= 255");
+    if (cap < 1 || cap > (1 << 24)) return set_arg_error("lsm_pslfile_run: 1 <= chunk <= 2^24");
+    lsm_run_opts o = *opts;
+    lsm_status rc = check_opts(o);
+    if (rc) return rc;
+    rc = ensure_slots(t, nb, st);
+    if (rc) return rc;
+    PslFileRun *R = new PslFileRun();
+    const uint32_t c = (uint32_t)std::max<int64_t>(cap, 1024);
+    cudaError_t e = ws_alloc(R->W, c, (uint32_t)std::min<int64_t>(4 * (int64_t)c + (1 << 18), 0xF0000000ll), t);
+    if (e != cudaSuccess) { delete R; return set_cuda_error(e, "lsm_pslfile_run workspace"); }
+    R->T = make_tp(ph, t, o, R->W.key, R->W.cnt);
+    R->t = t;
+    R->nb = nb;
+    set_key(R->W, t, seed, st);
+    *out = R;
+    return LSM_OK;
+}
+
+lsm_status pslfile_chunk(PslFileRun *R, const void *d_rec, int64_t n, uint64_t g0, int64_t i0, const PslGeom &G,
+                         cudaStream_t st)
+{
+    if (n <= 0) return LSM_OK;
+    if (n > (int64_t)R->W.q[0].cap) return set_arg_error("lsm_pslfile_run: chunk larger than the workspace");
+    LSM_CUDA(cudaMemsetAsync(R->W.cnt, 0, sizeof(IterCounters), st));
+    const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
+    const int tk = timer_begin(1, st);
+    k_pslfile_enqueue<0><<<g, 256, 0, st>>>((const PslRec *)d_rec, n, g0, i0, R->nb, G, R->T, R->W.q[0], R->W.q[2]);
+    count_launch();
+    timer_end(tk, st);
+    LSM_CUDA(cudaGetLastError());
+    return drain<0>(R->T, R->W, R->t, st);
+}
+
+lsm_status pslfile_end_pass(PslFileRun *R, cudaStream_t st)
+{
+    lsm_status rc = fold_slots(R->t, R->nb, st);
+    if (rc == LSM_OK) R->t->n_batches += R->nb;
+    return rc;
+}
+
+// releases the run; returns LSM_ERR_OVERFLOW if a queue filled up (synchronises)
+lsm_status pslfile_finish(PslFileRun *R, cudaStream_t st)
+{
+    if (!R) return LSM_OK;
+    unsigned long long ovf = 0;
+    lsm_status rc = read_overflow(R->t, R->W, st, &ovf);
+    delete R;
+    if (rc) return rc;
+    return ovf ? LSM_ERR_OVERFLOW : LSM_OK;
 }
 
 lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint64_t seed,

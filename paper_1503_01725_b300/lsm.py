@@ -16,10 +16,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblsm.so")
 
-LSM_OK, LSM_ERR_ARG, LSM_ERR_CUDA, LSM_ERR_OVERFLOW, LSM_ERR_TIMEOUT, LSM_ERR_NOT_CONVERGED = range(6)
+LSM_OK, LSM_ERR_ARG, LSM_ERR_CUDA, LSM_ERR_OVERFLOW, LSM_ERR_TIMEOUT, LSM_ERR_NOT_CONVERGED, LSM_ERR_IO = range(7)
 LSM_MEM_HOST, LSM_MEM_DEVICE = 0, 1
 _STATUS = {1: "LSM_ERR_ARG", 2: "LSM_ERR_CUDA", 3: "LSM_ERR_OVERFLOW", 4: "LSM_ERR_TIMEOUT",
-           5: "LSM_ERR_NOT_CONVERGED"}
+           5: "LSM_ERR_NOT_CONVERGED", 6: "LSM_ERR_IO"}
 
 _dp = C.POINTER(C.c_double)
 
@@ -78,6 +78,12 @@ class lsm_nnls_report(C.Structure):
 class lsm_vol(C.Structure):
     _fields_ = [("data", C.c_void_p), ("n", C.c_int32), ("d", C.c_int32), ("h", C.c_int32), ("w", C.c_int32),
                 ("c_total", C.c_int32), ("c_offset", C.c_int32), ("c", C.c_int32)]
+
+
+class lsm_pslfile_stats(C.Structure):
+    _fields_ = [("records", C.c_int64), ("bytes", C.c_int64), ("chunks", C.c_int64), ("t_read_s", C.c_double),
+                ("t_copy_s", C.c_double), ("t_total_s", C.c_double), ("dose_scale", C.c_double),
+                ("cold", C.c_int32), ("pad", C.c_int32)]
 
 
 class lsm_adam_opts(C.Structure):
@@ -140,6 +146,10 @@ _EXPORTS = {
                             C.c_double, C.c_double, C.c_int, _dp, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p]),
     "lsm_dose_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, _dp,
                                  C.c_void_p]),
+    "lsm_pslfile_write": (C.c_int, [C.c_void_p, C.c_uint64, C.c_char_p, C.POINTER(C.c_int64), C.c_void_p]),
+    "lsm_pslfile_run": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_int32,
+                                  C.c_int32, C.c_int32, C.POINTER(lsm_run_opts), C.POINTER(lsm_pslfile_stats),
+                                  C.c_void_p]),
     "lsm_timing_enable": (C.c_int, [C.c_int]),
     "lsm_timing_read": (C.c_int, [_dp, C.POINTER(C.c_int64), C.c_int]),
     "lsm_last_error": (C.c_char_p, []),
@@ -397,6 +407,30 @@ def lsm_run(psl: PSL, ph: PhantomHandle, tally: Tally, seed: int, opts: RunOpts 
     o = (opts or RunOpts()).struct()
     return _check(_lib.lsm_run(psl.ptr, ph.ptr, tally.ptr, seed, C.byref(o), _stream(stream)), "lsm_run",
                   ok=(LSM_OK, LSM_ERR_OVERFLOW))
+
+
+def lsm_pslfile_write(psl: PSL, seed: int, path: str, stream=None) -> int:
+    """Write every history of the (whole-source, single-beam) plan as a PSL
+    file of 32-byte records grouped by PSL cell; returns the record count."""
+    n = C.c_int64(0)
+    _check(_lib.lsm_pslfile_write(psl.ptr, seed, os.fsencode(path), C.byref(n), _stream(stream)),
+           "lsm_pslfile_write")
+    return int(n.value)
+
+
+def lsm_pslfile_run(path: str, field: PSL, ph: PhantomHandle, tally: Tally, seed: int, n_batches: int = 10,
+                    n_passes: int = 1, cold: bool = False, opts: RunOpts | None = None, stream=None) -> dict:
+    """Dose from the PSL file for the field of `field`; returns the run's
+    statistics (records, bytes, chunks, t_read_s, t_copy_s, t_total_s,
+    dose_scale, cold, status)."""
+    o = (opts or RunOpts()).struct()
+    st = lsm_pslfile_stats()
+    rc = _check(_lib.lsm_pslfile_run(os.fsencode(path), field.ptr, ph.ptr, tally.ptr, seed, n_batches, n_passes,
+                                     int(cold), C.byref(o), C.byref(st), _stream(stream)),
+                "lsm_pslfile_run", ok=(LSM_OK, LSM_ERR_OVERFLOW))
+    out = {k: getattr(st, k) for k, _ in lsm_pslfile_stats._fields_ if k != "pad"}
+    out["status"] = rc
+    return out
 
 
 def lsm_dose(t: Tally, ph: PhantomHandle, scale: float, device: bool = False, stream=None):
