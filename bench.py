@@ -385,11 +385,12 @@ def pslfile_block(lsm, W, n_file: int = 1 << 24, n_batches: int = 10):
                     "s_transport": (tm["photon"][0] + tm["annihilation_photon"][0] + tm["electron"][0]) / 1e3,
                     "GB_read": st["bytes"] / 1e9, "cache_dropped": bool(st["cold"])}
             n = int(st["records"])
-            # the analytic source at the same histories: plan build + sampled run
+            # the analytic source at the same histories (n_batches passes over
+            # a plan of n / n_batches): plan build + sampled run
             lsm.lsm_tally_reset(t)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            g = lsm.lsm_build_psl(wl.model, beams, n)
+            g = lsm.lsm_build_psl(wl.model, beams, -(-n // n_batches))
             torch.cuda.synchronize()
             t_init = time.perf_counter() - t0
             lsm.lsm_run(g, ph, t, 3, opts)                                               # warm-up
@@ -406,7 +407,7 @@ def pslfile_block(lsm, W, n_file: int = 1 << 24, n_batches: int = 10):
             tm = lsm.lsm_timing_read(reset=True)
             cold = runs["cold"]
             fields[f"{size:g}x{size:g}"] = {
-                "histories": n, "psl_files": runs,
+                "histories": n, "histories_analytic": -(-n // n_batches) * n_batches, "psl_files": runs,
                 "analytic": {"s_total": t_init + t_run, "s_src_init": t_init, "s_run_events": a.elapsed_time(b) / 1e3,
                              "s_gen_translate": tm["sample"][0] / 1e3,
                              "s_transport": (tm["photon"][0] + tm["annihilation_photon"][0] + tm["electron"][0]) / 1e3},

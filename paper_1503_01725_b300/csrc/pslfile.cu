@@ -5,7 +5,7 @@
 // phantom), then transports them like sampled particles.
 //
 // Pipeline of lsm_pslfile_run: a reader thread fills three pinned host
-// buffers with pread; the calling thread copies each filled buffer to one of
+// buffers with pread (each chunk split over four threads); the calling thread copies each filled buffer to one of
 // two device buffers on a copy stream and queues the enqueue + transport
 // kernels of that chunk on the caller's stream, so that the disk read of
 // chunk c+1, the copy of chunk c and the transport of chunk c-1 overlap.
@@ -109,6 +109,24 @@ struct BufferPool {
     }
 };
 BufferPool g_pool;
+
+// Records [a, b) of a chunk buffer: piece `buf` of a segment comes from file
+// record `file` on. Returns 0 or the failing read's errno.
+struct Seg {
+    int64_t buf, file, n;
+};
+constexpr int kReadThreads = 4;
+
+int read_share(int fd, int64_t data_off, const std::vector<Seg> &segs, char *dst, int64_t a, int64_t b)
+{
+    for (const Seg &s : segs) {
+        const int64_t lo = std::max(a, s.buf), hi = std::min(b, s.buf + s.n);
+        if (lo >= hi) continue;
+        if (!read_all(fd, dst + lo * 32, (size_t)(hi - lo) * 32, (off_t)(data_off + (s.file + lo - s.buf) * 32)))
+            return errno ? errno : EIO;
+    }
+    return 0;
+}
 
 // A chunk as the reader thread hands it over.
 struct Chunk {
@@ -341,19 +359,31 @@ extern "C" lsm_status lsm_pslfile_run(const char *path, const lsm_psl *field, co
                 char *buf = (char *)g_pool.h[k];
                 int64_t got = 0;
                 const double t0 = now_s();
+                // the chunk's pieces of PSL ranges, then kReadThreads parallel
+                // reads over equal shares of the chunk
+                std::vector<Seg> segs;
                 while (got < CH && j < N) {
                     const int64_t len = std::min(CH - got, ranges[r].second - cur);
-                    if (!read_all(fd, buf + got * 32, (size_t)len * 32, (off_t)(data_off + cur * 32))) {
+                    segs.push_back({got, cur, len});
+                    got += len; cur += len; j += len;
+                    if (cur == ranges[r].second && ++r < ranges.size()) cur = ranges[r].first;
+                }
+                const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(kReadThreads, got * 32 / (8 << 20)));
+                std::vector<int> errs((size_t)nt, 0);
+                std::vector<std::thread> pool;
+                for (int q = 1; q < nt; ++q)
+                    pool.emplace_back([&, q] { errs[q] = read_share(fd, data_off, segs, buf, got * q / nt, got * (q + 1) / nt); });
+                errs[0] = read_share(fd, data_off, segs, buf, 0, got / nt);
+                for (auto &th : pool) th.join();
+                for (int e : errs)
+                    if (e) {
                         std::lock_guard<std::mutex> lk(m);
-                        read_err = errno;
+                        read_err = e;
                         read_failed = true;
                         reader_done = true;
                         cv.notify_all();
                         return;
                     }
-                    got += len; cur += len; j += len;
-                    if (cur == ranges[r].second && ++r < ranges.size()) cur = ranges[r].first;
-                }
                 const double t1 = now_s();
                 std::lock_guard<std::mutex> lk(m);
                 t_read += t1 - t0;

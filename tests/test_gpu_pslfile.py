@@ -9,8 +9,9 @@ Bars:
   records are the oracle's sampled particles on the phase-space plane
   (sampling tolerances);
 * the dose from a PSL file agrees statistically with the dose sampled on the
-  fly for the same field (|z| < 3 on >= 99% of voxels above 10% of the
-  maximum, mean within 1%).
+  fly for the same field: |z| < 3 on >= 98.5% of voxels above 20% of the
+  maximum (20-batch sigmas), mean within 0.5%, and the energy entering and
+  deposited per unit source weight within 0.2% and 0.5%.
 """
 import os
 import struct
@@ -207,25 +208,37 @@ def test_writer_matches_oracle_plan_and_sampler(L, tmp_path):
 
 
 def test_pslfile_dose_matches_sampled_source(L, tmp_path):
-    wl = W.workload_full_10x10(2_000_000)
+    model = W.psr_model(10, 10, 0.25, seed=2)
+    beams = W.beams(W.square_field(10.0))
+    wph = W.water_phantom(32, 32, 32, 0.5)
     # the file: every history of a wide-open (40x40) plan
-    open_plan = L.lsm_build_psl(wl.model, W.beams(W.square_field(40.0)), 6_000_000)
+    open_plan = L.lsm_build_psl(model, W.beams(W.square_field(40.0)), 8_000_000)
     path = str(tmp_path / "open.psl")
     L.lsm_pslfile_write(open_plan, 77, path)
-    ph = L.lsm_phantom_create(wl.phantom)
-    field = L.lsm_build_psl(wl.model, wl.beams, 1000)
+    ph = L.lsm_phantom_create(wph)
+    field = L.lsm_build_psl(model, beams, 1000)
     t1 = L.lsm_tally_create(ph)
-    st = L.lsm_pslfile_run(path, field, ph, t1, 5, n_batches=10, cold=True)
+    st = L.lsm_pslfile_run(path, field, ph, t1, 5, n_batches=20, cold=True)
     d1, s1 = L.lsm_dose(t1, ph, st["dose_scale"])
-    # the same field sampled on the fly with as many histories as were read
-    g = L.lsm_build_psl(wl.model, wl.beams, st["records"])
+    led1, _ = L.lsm_tally_ledger(t1)
+    # the same field sampled on the fly, 20 batches of half the records each
+    # (10x the file's histories, so that the comparison is dominated by the
+    # file's own uncertainty)
+    g = L.lsm_build_psl(model, beams, st["records"] // 2)
     t2 = L.lsm_tally_create(ph)
-    L.lsm_run(g, ph, t2, 6, L.RunOpts(n_batches=10))
+    L.lsm_run(g, ph, t2, 6, L.RunOpts(n_batches=20))
     info, denom = L.lsm_psl_info(g)
-    d2, s2 = L.lsm_dose(t2, ph, denom / info["plan_size"])
-    sel = d2 > 0.1 * d2.max()
+    scale2 = denom / info["plan_size"]
+    d2, s2 = L.lsm_dose(t2, ph, scale2)
+    led2, _ = L.lsm_tally_ledger(t2)
+    # energy per unit source weight entering and deposited: same expectation
+    w_rec = st["dose_scale"] / 20
+    assert led1["source"] * w_rec == pytest.approx(led2["source"] / 20 * scale2, rel=2e-3)
+    assert led1["deposited"] * w_rec == pytest.approx(led2["deposited"] / 20 * scale2, rel=5e-3)
+    sel = d2 > 0.2 * d2.max()
     z = (d1 - d2)[sel] / np.sqrt(s1[sel] ** 2 + s2[sel] ** 2 + 1e-300)
-    assert np.mean(np.abs(z) < 3) >= 0.99, np.mean(np.abs(z) < 3)
-    assert abs(d1[sel].mean() / d2[sel].mean() - 1) < 0.01
+    # 20-batch sigma estimates give t-like tails: P(|t_19| > 3) = 0.7%
+    assert np.mean(np.abs(z) < 3) >= 0.985, np.mean(np.abs(z) < 3)
+    assert abs(d1[sel].mean() / d2[sel].mean() - 1) < 0.005
     assert st["t_total_s"] >= st["t_read_s"] > 0 and st["t_copy_s"] > 0
     os.remove(path)
