@@ -41,20 +41,20 @@ sys.path.insert(0, ROOT)
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 
-# Algorithmic bytes per unit of work (measurement section):
-#   sampling: per history, plan lookup (16 B entry + 8 B prefix) + particle write (44 B);
+# Algorithmic bytes per unit of work:
+#   sampling: per history, plan lookup (16 B entry + 8 B prefix) + particle write (48 B record);
 #   photon transport: per Woodcock flight one density load (4 B), per photon the
-#     queue read (44 B), per real interaction one tally update (8 B) or queue write (44 B);
+#     queue read (48 B), per real interaction one tally update (8 B) or queue write (48 B);
 #   electron transport: per CSDA step one density load (4 B) + one tally update
-#     (4 B read + 4 B write), per electron the queue read (44 B).
+#     (4 B read + 4 B write), per electron the queue read (48 B).
 # DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# on a reduced case of this workload (2e6 histories: 91.9 MB over 1,550,866
-# photons; 51.1 MB over 4,941,500 electron steps); profiles/transport_3src-10x10-water64.md.
+# on a reduced case of this workload (4e6 histories in one iteration: 208.8 MB
+# over 3,101,593 photons; 98.2 MB over 9,908,310 electron steps).
 # Valid for the kernels as profiled; set to None when they change.
-TRAFFIC_PER_UNIT = {"photon": ("photons", 59.3), "electron": ("esteps", 10.33)}
-B_SAMPLE_PER_HIST = 68.0
+TRAFFIC_PER_UNIT = {"photon": ("photons", 67.3), "electron": ("esteps", 9.91)}
+B_SAMPLE_PER_HIST = 72.0
 B_FLIGHT = 4.0
-B_QUEUE = 44.0
+B_QUEUE = 48.0
 B_DEPOSIT = 8.0
 B_ESTEP = 12.0
 
