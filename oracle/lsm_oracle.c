@@ -15,7 +15,12 @@
  *     and jaw rejection at the upper jaw surfaces;
  *   - the loop order of Sec. 2.1.3 (sub-source, energy bin outer, PSL inner);
  *   - the PSR-indexed basis-dose tally of Sec. 2.2.2 (3D index array, 2D dose
- *     array [row][PSR], secondaries inherit the PSR index).
+ *     array [row][PSR], secondaries inherit the PSR index);
+ *   - multi-beam plans (step S1 loops over beams; the prostate and H&N cases of
+ *     Table 1): each beam turned by its gantry angle about the isocentre, the
+ *     particle entering the phantom where its straight line meets the voxel box
+ *     (the geometry is the textbook rotation and slab test; the paper gives no
+ *     formula).
  *
  * The paper does not describe its transport physics (Sec. 2.3 gives only the
  * 200 keV electron and 50 keV photon cutoffs). This file therefore implements
@@ -198,6 +203,8 @@ typedef struct {
     double sad, z_jaw_y, z_jaw_x;  /* upper surfaces of the Y and X jaws */
     int32_t n_beams;
     const double *jaws;            /* [n_beams][4]: x1 x2 y1 y2 at the isocentre plane */
+    const double *gantry;          /* NULL, or [n_beams] gantry angles (radians) */
+    double iso[3];                 /* isocentre in phantom coordinates (with gantry) */
 } or_beams;
 
 typedef struct {
@@ -206,6 +213,8 @@ typedef struct {
     or_model M;                    /* pointers borrowed for the plan's lifetime */
     double sad, z_jaw_y, z_jaw_x;
     double *jaws;                  /* copy [n_beams][4] */
+    int rotated;                   /* gantry angles given */
+    double gantry[16], iso[3];
     double *wpsl;                  /* [3][n_e][n_xy][n_xy] normalised PSL weight */
     int32_t *tag_r0;               /* [n_xy][n_xy] lower ring of the interpolation */
     double *tag_l0;                /* [n_xy][n_xy] lambda of the lower ring */
@@ -323,6 +332,9 @@ OR_API void *or_plan_build(const or_model *M, const or_beams *B, int64_t n_hist,
     P->sad = B->sad; P->z_jaw_y = B->z_jaw_y; P->z_jaw_x = B->z_jaw_x;
     P->jaws = (double *)malloc(sizeof(double) * 4 * (size_t)nb);
     memcpy(P->jaws, B->jaws, sizeof(double) * 4 * (size_t)nb);
+    P->rotated = B->gantry != NULL;
+    for (int b = 0; b < nb && b < 16; ++b) P->gantry[b] = B->gantry ? B->gantry[b] : 0.0;
+    for (int k = 0; k < 3; ++k) P->iso[k] = B->gantry ? B->iso[k] : (k == 2 ? B->sad : 0.0);
     size_t npsl = (size_t)nxy * nxy;
     P->wpsl = (double *)calloc(3 * (size_t)ne * npsl, sizeof(double));
     P->tag_r0 = (int32_t *)calloc(npsl, 4);
@@ -985,6 +997,41 @@ static void electron_track(tctx *T, part_t *p)
  * electron steps. cons[2]: max per-history |balance| / E_source, step-cap hits.
  * per_hist (may be NULL): [n_batches*n_hist] energy deposited per history.
  */
+/*
+ * Gantry rotation of a beam (the plan's beam geometry): a beam-frame point q
+ * (target at the origin, axis +z, isocentre at (0, 0, sad)) lies at
+ * iso + R (q - (0, 0, sad)) in phantom coordinates, R turning by the gantry
+ * angle g about y: R (a, b, c) = (a cos g + c sin g, b, -a sin g + c cos g).
+ * The particle leaves the phase-space plane at (xp, yp, z_phsp) along
+ * (u, v, w) and enters the phantom where that straight line first meets the
+ * voxel box (Kay-Kajiya slabs); it starts 1e-4 cm past that point.
+ * Returns 0 and fills pos/dir (phantom coordinates), or 1 on a miss.
+ */
+OR_API int or_beam_entry(const double iso[3], double sad, double z_phsp, double g, const double p_plane[2],
+                         const double dir[3], const double box_lo[3], const double box_hi[3], double pos[3],
+                         double d[3])
+{
+    double c = cos(g), sn = sin(g);
+    double qx = p_plane[0], qy = p_plane[1], qz = z_phsp - sad;
+    double p[3] = {iso[0] + qx * c + qz * sn, iso[1] + qy, iso[2] - qx * sn + qz * c};
+    d[0] = dir[0] * c + dir[2] * sn; d[1] = dir[1]; d[2] = -dir[0] * sn + dir[2] * c;
+    double tn = 0.0, tf = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0) {
+            double t1 = (box_lo[a] - p[a]) / d[a], t2 = (box_hi[a] - p[a]) / d[a];
+            double lo = t1 < t2 ? t1 : t2, hi = t1 < t2 ? t2 : t1;
+            if (lo > tn) tn = lo;
+            if (hi < tf) tf = hi;
+        } else if (p[a] < box_lo[a] || p[a] > box_hi[a]) {
+            return 1;
+        }
+    }
+    if (!(tn <= tf)) return 1;
+    double t = tn + 1e-4;
+    for (int a = 0; a < 3; ++a) pos[a] = p[a] + t * d[a];
+    return 0;
+}
+
 OR_API int or_run(const void *h, const or_phantom *Ph, const or_opts *O, uint64_t seed,
                   double *s1, double *s2, double *ledger, int64_t *stats, double *cons,
                   double *per_hist)
@@ -1024,7 +1071,18 @@ OR_API int or_run(const void *h, const or_phantom *Ph, const or_opts *O, uint64_
                 p.type = o.type; p.psr = o.psr; p.beam = o.beam;
                 stream_init(&p.rng, seed, g, 1u);
                 p.have = 0;
-                int vox = voxel_of(Ph, p.x, p.y, p.z);
+                int vox = -1;
+                if (!P->rotated) {
+                    vox = voxel_of(Ph, p.x, p.y, p.z);
+                } else {
+                    double lo[3] = {Ph->x0, Ph->y0, Ph->z0};
+                    double hi[3] = {Ph->x0 + Ph->nx * Ph->dx, Ph->y0 + Ph->ny * Ph->dy, Ph->z0 + Ph->nz * Ph->dz};
+                    double pp[2] = {o.xp, o.yp}, dir[3] = {o.up, o.vp, o.wp}, pos[3], d[3];
+                    if (or_beam_entry(P->iso, P->sad, P->M.z_phsp, P->gantry[o.beam], pp, dir, lo, hi, pos, d) == 0) {
+                        p.x = pos[0]; p.y = pos[1]; p.z = pos[2]; p.u = d[0]; p.v = d[1]; p.w = d[2];
+                        vox = voxel_of(Ph, p.x, p.y, p.z);
+                    }
+                }
                 if (vox < 0) { T.esc += p.E; stats[4]++; }
                 else {
                     if (p.type) stats[2]++; else stats[1]++;

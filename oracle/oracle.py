@@ -39,7 +39,7 @@ class _Model(C.Structure):
 
 class _Beams(C.Structure):
     _fields_ = [("sad", C.c_double), ("z_jaw_y", C.c_double), ("z_jaw_x", C.c_double),
-                ("n_beams", C.c_int32), ("jaws", _dp)]
+                ("n_beams", C.c_int32), ("jaws", _dp), ("gantry", _dp), ("iso", C.c_double * 3)]
 
 
 class _Phantom(C.Structure):
@@ -85,6 +85,8 @@ def lib():
         L.or_plan_build.argtypes = [C.POINTER(_Model), C.POINTER(_Beams), C.c_int64,
                                     C.POINTER(C.c_int64)]
         L.or_plan_free.argtypes = [C.c_void_p]
+        L.or_beam_entry.restype = C.c_int
+        L.or_beam_entry.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
         L.or_plan_sizes.argtypes = [C.c_void_p, C.POINTER(C.c_int64), _dp]
         L.or_plan_copy.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.or_sample.restype = C.c_int
@@ -148,7 +150,14 @@ def _model_struct(m, keep):
 def _beams_struct(b, keep):
     j = np.ascontiguousarray(b.jaws, dtype=np.float64)
     keep.append(j)
-    return _Beams(sad=b.sad, z_jaw_y=b.z_jaw_y, z_jaw_x=b.z_jaw_x, n_beams=b.n_beams, jaws=_ptr(j))
+    g = None
+    if getattr(b, "gantry", None) is not None:
+        ga = np.ascontiguousarray(b.gantry, dtype=np.float64)
+        keep.append(ga)
+        g = _ptr(ga)
+    iso = getattr(b, "iso", (0.0, 0.0, b.sad))
+    return _Beams(sad=b.sad, z_jaw_y=b.z_jaw_y, z_jaw_x=b.z_jaw_x, n_beams=b.n_beams, jaws=_ptr(j), gantry=g,
+                  iso=(C.c_double * 3)(*iso))
 
 
 def _phantom_struct(ph, keep):
@@ -216,6 +225,17 @@ class Plan:
         if getattr(self, "h", None):
             lib().or_plan_free(self.h)
             self.h = None
+
+
+def beam_entry(iso, sad: float, z_phsp: float, gantry: float, p_plane, direction, box_lo, box_hi):
+    """Where a particle leaving the phase-space plane of a beam turned by
+    `gantry` about the isocentre enters the voxel box (phantom coordinates):
+    (position, direction), or None when it misses the box."""
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (iso, p_plane, direction, box_lo, box_hi)]
+    pos, d = np.zeros(3), np.zeros(3)
+    rc = lib().or_beam_entry(_ptr(a[0]), sad, z_phsp, gantry, _ptr(a[1]), _ptr(a[2]), _ptr(a[3]), _ptr(a[4]),
+                             _ptr(pos), _ptr(d))
+    return None if rc else (pos, d)
 
 
 def sample(plan: Plan, seed: int, g0: int, n: int, z_surf: float = 100.0) -> dict:

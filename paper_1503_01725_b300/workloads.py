@@ -67,6 +67,8 @@ class Beams:
     sad: float = SAD
     z_jaw_y: float = Z_JAW_Y
     z_jaw_x: float = Z_JAW_X
+    gantry: np.ndarray | None = None   # (n_beams,) radians about the y axis through iso; None: no rotation
+    iso: tuple = (0.0, 0.0, SAD)       # isocentre in phantom coordinates (used with gantry)
 
     @property
     def n_beams(self) -> int:
@@ -288,6 +290,86 @@ def commissioning_truth(n_psr: int, seed: int = 3, zero_frac: float = 0.05) -> n
 DENOISE_CASES = 200               # seeded phantoms and fields: 0-179 training, 180-199 test
 DENOISE_TRAIN = range(0, 180)
 DENOISE_TEST = range(180, 200)
+
+
+def _box_around_iso(nx: int, ny: int, nz: int, voxel: float, iso=(0.0, 0.0, SAD)):
+    """Air-filled voxel box centred on the isocentre, with voxel-centre
+    coordinates (Z, Y, X) for drawing anatomy into it."""
+    x0, y0, z0 = iso[0] - 0.5 * nx * voxel, iso[1] - 0.5 * ny * voxel, iso[2] - 0.5 * nz * voxel
+    rho = np.full((nz, ny, nx), 0.0012, dtype=np.float32)
+    mat = np.zeros((nz, ny, nx), dtype=np.uint8)
+    ph = Phantom(nx, ny, nz, voxel, voxel, voxel, x0, y0, z0, rho, mat)
+    z = z0 + (np.arange(nz) + 0.5) * voxel
+    y = y0 + (np.arange(ny) + 0.5) * voxel
+    x = x0 + (np.arange(nx) + 0.5) * voxel
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return ph, Z - iso[2], Y - iso[1], X - iso[0]
+
+
+def pelvis_phantom(nx: int = 80, ny: int = 48, nz: int = 64, voxel: float = 0.5) -> Phantom:
+    """CT-like pelvis around the isocentre (0, 0, 100), coordinates relative
+    to it: elliptic body 34 x 22 cm (x, z) with a 1.5 cm fat layer (0.92),
+    soft tissue 1.03 inside, femoral heads (bone 1.45, r 2.6 cm at x = +-9),
+    a pelvic ring (bone 1.35, 1 cm thick), a sacrum (bone 1.5) behind, a
+    rectal air pocket (r 1 cm) and a bladder (water 1.0); air (0.0012) around.
+    Slices along y fade the bones by |y| (a 24 cm long section)."""
+    ph, Z, Y, X = _box_around_iso(nx, ny, nz, voxel)
+    body = (X / 17.0) ** 2 + (Z / 11.0) ** 2 <= 1.0
+    inner = (X / 15.5) ** 2 + (Z / 9.5) ** 2 <= 1.0
+    ph.rho[body] = 0.92
+    ph.rho[inner] = 1.03
+    ring = inner & ((X / 13.0) ** 2 + (Z / 8.0) ** 2 >= 1.0) & ((X / 14.0) ** 2 + (Z / 9.0) ** 2 <= 1.0) & \
+        (np.abs(Y) < 6.0)
+    heads = ((np.abs(X) - 9.0) ** 2 + Z ** 2 + (Y / 1.5) ** 2) <= 2.6 ** 2
+    sacrum = (X ** 2 + (Z - 6.5) ** 2 <= 2.2 ** 2) & (np.abs(Y) < 8.0)
+    bladder = (X ** 2 + ((Z + 3.0) / 0.8) ** 2 + (Y / 1.2) ** 2) <= 3.0 ** 2
+    rectum = (X ** 2 + (Z - 3.0) ** 2 <= 1.0) & (np.abs(Y) < 5.0)
+    for sel, r, m in ((ring, 1.35, 1), (heads, 1.45, 1), (sacrum, 1.5, 1), (bladder, 1.0, 0), (rectum, 0.0012, 0)):
+        ph.rho[sel] = r
+        ph.mat[sel] = m
+    return ph
+
+
+def hn_phantom(nx: int = 48, ny: int = 48, nz: int = 48, voxel: float = 0.5) -> Phantom:
+    """CT-like head-and-neck section around the isocentre (0, 0, 100): elliptic
+    neck 15 x 13 cm (x, z) of soft tissue 1.04, a cervical spine (bone 1.6,
+    r 1.4 cm) behind the centre, a trachea (air, r 0.9 cm) in front, a mandible
+    arc (bone 1.7) at the front over half the section; air around."""
+    ph, Z, Y, X = _box_around_iso(nx, ny, nz, voxel)
+    neck = (X / 7.5) ** 2 + (Z / 6.5) ** 2 <= 1.0
+    ph.rho[neck] = 1.04
+    spine = X ** 2 + (Z - 3.0) ** 2 <= 1.4 ** 2
+    trachea = X ** 2 + (Z + 2.5) ** 2 <= 0.9 ** 2
+    jaw = neck & ((X / 6.0) ** 2 + (Z / 5.0) ** 2 >= 1.0) & ((X / 6.8) ** 2 + (Z / 5.8) ** 2 <= 1.0) & (Z < 0) & \
+        (Y > 0)
+    for sel, r, m in ((spine, 1.6, 1), (trachea, 0.0012, 0), (jaw, 1.7, 1)):
+        ph.rho[sel] = r
+        ph.mat[sel] = m
+    return ph
+
+
+def gantry_beams(angles_deg, field_cm: float, iso=(0.0, 0.0, SAD)) -> Beams:
+    """Equal square fields at the given gantry angles about the isocentre."""
+    b = beams(*[square_field(field_cm) for _ in angles_deg])
+    b.gantry = np.deg2rad(np.asarray(angles_deg, dtype=np.float64))
+    b.iso = tuple(float(v) for v in iso)
+    return b
+
+
+def workload_prostate_7beam(n_hist: int = 10_000_000) -> Workload:
+    """Seven coplanar 8x8 cm2 beams every 360/7 degrees on the pelvis phantom
+    (the prostate layout of Table 1), 3 sub-sources, CSDA electrons."""
+    angles = [k * 360.0 / 7 for k in range(7)]
+    return Workload("prostate-7beam-pelvis80x48x64", psr_model(10, 10, 0.25, seed=2), gantry_beams(angles, 8.0),
+                    pelvis_phantom(), n_hist, 1, 7)
+
+
+def workload_hn_6beam(n_hist: int = 10_000_000) -> Workload:
+    """Six coplanar 6x6 cm2 beams every 60 degrees on the head-and-neck
+    phantom (the H&N layout of Table 1), 3 sub-sources, CSDA electrons."""
+    angles = [k * 60.0 for k in range(6)]
+    return Workload("hn-6beam-neck48", psr_model(10, 10, 0.25, seed=2), gantry_beams(angles, 6.0), hn_phantom(),
+                    n_hist, 1, 8)
 
 
 def workload_denoise(case: int, n_hist: int = 1_000_000) -> Workload:
