@@ -87,11 +87,23 @@ typedef struct {
  * isocentre plane z = sad; the Y and X jaws have their upper surfaces at
  * z_jaw_y and z_jaw_x (z_phsp < z_jaw < sad). jaws: host [n_beams][4]
  * (x1, x2, y1, y2). 1 <= n_beams <= 16.
+ * gantry: NULL, or host [n_beams] gantry angles (radians, |angle| <= 4 pi).
+ * With NULL, the beam frame is the phantom frame (every beam along +z, the
+ * phantom's top face z0 facing the source). Otherwise beam b is turned about
+ * the axis through iso (phantom coordinates, cm) parallel to y: a point q of
+ * the beam frame (target at the origin, axis +z, isocentre at (0, 0, sad))
+ * sits at iso + R_b (q - (0, 0, sad)), R_b (a, b, c) = (a cos g + c sin g, b,
+ * -a sin g + c cos g), so the beam axis runs along (sin g, 0, cos g). A
+ * particle then enters the phantom wherever its ray first meets the voxel box
+ * (and is counted as missing it otherwise); the box must not reach the
+ * phase-space plane of any beam.
  */
 typedef struct {
     double sad, z_jaw_y, z_jaw_x;
     int32_t n_beams;
     const double *jaws;
+    const double *gantry;
+    double iso[3];
 } lsm_beams;
 
 /*

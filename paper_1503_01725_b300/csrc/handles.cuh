@@ -28,6 +28,11 @@ struct SampleParams {
     float pitch, z_phsp, sigma_s;
     float e_lo[3], de[3];
     float zy_rel, zx_rel;      // jaw plane minus phase-space plane
+    // gantry rotation (rotated != 0): per beam (cos g, sin g), the isocentre
+    // in phantom coordinates and the source-to-isocentre distance
+    const float2 *rot;
+    float iso[3], sad;
+    int rotated;
 };
 
 // What a captured run graph depends on besides the seed.
@@ -63,6 +68,8 @@ struct lsm_psl {
     int n_e, n_r, n_xy, n_beams, per_psr;
     double dr, z_phsp, sigma_s, e_lo[3], de[3];
     double sad, z_jaw_y, z_jaw_x;
+    int rotated;
+    double gantry[16], iso[3];
     double denom;
     int64_t plan_size, n_ent, ncell;
     double *d_w, *d_wpsl, *d_scale, *d_jaws, *d_area, *d_escale;

@@ -488,7 +488,11 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
         if (!(j[0] < j[1]) || !(j[2] < j[3]) || !isfinite(j[0]) || !isfinite(j[1]) || !isfinite(j[2]) ||
             !isfinite(j[3]))
             return set_arg_error("lsm_build_psl: jaws need x1 < x2 and y1 < y2");
+        if (B->gantry && !(fabs(B->gantry[b]) <= 4.0 * kPiD))
+            return set_arg_error("lsm_build_psl: gantry angles must be finite, |angle| <= 4 pi");
     }
+    if (B->gantry && !(isfinite(B->iso[0]) && isfinite(B->iso[1]) && isfinite(B->iso[2])))
+        return set_arg_error("lsm_build_psl: isocentre must be finite");
     const int nb = B->n_beams;
     const int npsr = 3 * ne * nr;
     if (!per_psr_hist && n_hist < 1) return set_arg_error("lsm_build_psl: n_hist must be >= 1");
@@ -504,6 +508,9 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     P->dr = M->dr; P->z_phsp = M->z_phsp; P->sigma_s = M->sigma_s;
     for (int s = 0; s < 3; ++s) { P->e_lo[s] = M->e_lo[s]; P->de[s] = M->de[s]; }
     P->sad = B->sad; P->z_jaw_y = B->z_jaw_y; P->z_jaw_x = B->z_jaw_x;
+    P->rotated = B->gantry != nullptr;
+    for (int b = 0; b < nb; ++b) P->gantry[b] = B->gantry ? B->gantry[b] : 0.0;
+    for (int k = 0; k < 3; ++k) P->iso[k] = B->gantry ? B->iso[k] : (k == 2 ? B->sad : 0.0);
     const int64_t ncell = P->per_psr ? (int64_t)npsr * nb * npsl : (int64_t)nb * 3 * ne * npsl;
     P->ncell = ncell;
 
@@ -524,6 +531,7 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     const size_t o_rem = take((size_t)ncell * 8), o_cst = take((size_t)(ncell + 1) * 8);
     const size_t o_eidx = take((size_t)(ncell + 1) * 8), o_parts = take(nbse * 8);
     const size_t o_res = take(64), o_dkb = take((size_t)npsr * nb * 8), o_rank = take((size_t)ncell * 4);
+    const size_t o_rot = take((size_t)nb * sizeof(float2));
     char *base = nullptr;
     {
         cudaError_t e_ = cudaMallocAsync((void **)&base, off, st);
@@ -577,6 +585,11 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
         if (per_psr_hist) memcpy(h, per_psr_hist, (size_t)npsr * 8);
     }
     CK(cudaMemcpyAsync(d_in, hin.data(), hin.size() * 8, cudaMemcpyHostToDevice, st));
+    {
+        float2 hrot[16];
+        for (int b = 0; b < nb; ++b) hrot[b] = make_float2((float)cos(P->gantry[b]), (float)sin(P->gantry[b]));
+        CK(cudaMemcpyAsync(base + o_rot, hrot, (size_t)nb * sizeof(float2), cudaMemcpyHostToDevice, st));
+    }
     CK(cudaMemsetAsync(d_denom, 0, 64, st));
 
     if ((size_t)npsl * 8 > 48 * 1024)
@@ -659,6 +672,10 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     for (int s = 0; s < 3; ++s) { sp.e_lo[s] = (float)M->e_lo[s]; sp.de[s] = (float)M->de[s]; }
     sp.zy_rel = (float)(B->z_jaw_y - M->z_phsp);
     sp.zx_rel = (float)(B->z_jaw_x - M->z_phsp);
+    sp.rot = (const float2 *)(base + o_rot);
+    for (int k = 0; k < 3; ++k) sp.iso[k] = (float)P->iso[k];
+    sp.sad = (float)B->sad;
+    sp.rotated = P->rotated;
     *out = P;
     return LSM_OK;
 #undef CK

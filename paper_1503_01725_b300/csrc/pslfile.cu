@@ -249,8 +249,8 @@ extern "C" lsm_status lsm_pslfile_run(const char *path, const lsm_psl *field, co
     if (!path || !field || !ph || !t || !opts) return set_arg_error("lsm_pslfile_run: NULL argument");
     if (n_batches < 1 || n_batches > 255) return set_arg_error("lsm_pslfile_run: 1 <= n_batches <= 255");
     if (n_passes < 1) return set_arg_error("lsm_pslfile_run: n_passes >= 1");
-    if (field->per_psr || field->n_beams != 1)
-        return set_arg_error("lsm_pslfile_run: the field must be a whole-source single-beam plan");
+    if (field->per_psr || field->n_beams != 1 || field->rotated)
+        return set_arg_error("lsm_pslfile_run: the field must be a whole-source single-beam plan without gantry");
     cudaStream_t st = (cudaStream_t)stream;
     Fd f;
     f.fd = open(path, O_RDONLY);

@@ -573,7 +573,45 @@ struct SQ {
     int64_t plan;           // plan size: position h0 + i lies in batch slot (h0 + i) / plan
     float z_rel;            // phantom surface - z_phsp
     float x0, y0;           // phantom corner on the surface plane
+    float z0, lz;           // phantom corner z and depth (rotated beams)
 };
+
+// Rotated beams: the particle's ray from the phase-space plane, turned into
+// phantom coordinates about the isocentre, meets the voxel box [0, lx] x
+// [0, ly] x [0, lz] (slab method); the particle starts 1e-4 cm past the entry
+// point. Returns false when the ray misses the box. Phantom-local position
+// and direction out.
+__device__ __forceinline__ bool enter_box(const SQ &S, const TP &T, const SrcParticle &o, float &px, float &py,
+                                          float &pz, float &du, float &dv, float &dw)
+{
+    const float2 cs = __ldg(S.sp.rot + o.beam);
+    const float qz = S.sp.z_phsp - S.sp.sad;                 // plane relative to the isocentre
+    const float p0 = S.sp.iso[0] + o.xp * cs.x + qz * cs.y - S.x0;
+    const float p1 = S.sp.iso[1] + o.yp - S.y0;
+    const float p2 = S.sp.iso[2] - o.xp * cs.y + qz * cs.x - S.z0;
+    du = o.u * cs.x + o.w * cs.y;
+    dv = o.v;
+    dw = o.w * cs.x - o.u * cs.y;
+    const float p[3] = {p0, p1, p2}, d[3] = {du, dv, dw}, L[3] = {T.lx, T.ly, S.lz};
+    float tn = 0.0f, tf = 3.0e38f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0f) {
+            const float id = 1.0f / d[a];
+            const float t1 = (0.0f - p[a]) * id, t2 = (L[a] - p[a]) * id;
+            tn = fmaxf(tn, fminf(t1, t2));
+            tf = fminf(tf, fmaxf(t1, t2));
+        } else if (p[a] < 0.0f || p[a] > L[a]) {
+            tf = -1.0f;
+        }
+    }
+    if (!(tn <= tf)) return false;
+    const float t = tn + 1e-4f;
+    px = p0 + t * du;
+    py = p1 + t * dv;
+    pz = p2 + t * dw;
+    return voxel(T, px, py, pz) >= 0;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queue eq)
@@ -594,7 +632,7 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
         o.stype = 0;
         uint32_t slot = 0;
         bool in = false;
-        float lx = 0.0f, ly = 0.0f;
+        float lx = 0.0f, ly = 0.0f, lz = 0.0f;
         if (valid) {
             const int64_t hh = S.h0 + i;
             slot = (uint32_t)(hh / S.plan);
@@ -602,8 +640,14 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
             src += o.E;
             if (!o.accepted) { rej += o.E; nrej++; }
             else {
-                lx = o.x - S.x0; ly = o.y - S.y0;
-                in = voxel(T, lx, ly, 0.0f) >= 0;       // crosses the phantom's top face
+                if (!S.sp.rotated) {
+                    lx = o.x - S.x0; ly = o.y - S.y0;
+                    in = voxel(T, lx, ly, 0.0f) >= 0;   // crosses the phantom's top face
+                } else {
+                    float du, dv, dw;
+                    in = enter_box(S, T, o, lx, ly, lz, du, dv, dw);
+                    o.u = du; o.v = dv; o.w = dw;
+                }
                 if (!in) { esc += o.E; nmiss++; }
             }
         }
@@ -623,14 +667,14 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
             const uint32_t pb = pb_make((uint32_t)o.psr, (uint32_t)o.beam, slot);
             if (!is_e) {
                 nph++;
-                store_part(pq, bp + __popc(mp & lt), lx, ly, 0.0f, o.u, o.v, o.w, o.E, (uint32_t)g,
+                store_part(pq, bp + __popc(mp & lt), lx, ly, lz, o.u, o.v, o.w, o.E, (uint32_t)g,
                            (uint32_t)(g >> 32), 1u, pb);
             } else {
                 nel++;
                 if (local_e) {
-                    deposit<MODE>(T, A, voxel(T, lx, ly, 0.0f), o.E, pb);
+                    deposit<MODE>(T, A, voxel(T, lx, ly, lz), o.E, pb);
                 } else {
-                    store_part(eq, be + __popc(me & lt), lx, ly, 0.0f, o.u, o.v, o.w, o.E, (uint32_t)g,
+                    store_part(eq, be + __popc(me & lt), lx, ly, lz, o.u, o.v, o.w, o.E, (uint32_t)g,
                                (uint32_t)(g >> 32), 1u, pb);
                 }
             }
@@ -1309,6 +1353,7 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     S.key = W.key;
     S.z_rel = (float)(ph->z0 - P->z_phsp);
     S.x0 = (float)ph->x0; S.y0 = (float)ph->y0;
+    S.z0 = (float)ph->z0; S.lz = (float)(ph->nz * ph->dz);
     S.plan = plan;
     static int gs0 = 0, gs1 = 0;
     if (!gs0) gs0 = grid_for((const void *)k_sample_queue<0>, 256, 0);

@@ -39,7 +39,7 @@ class lsm_psr_model(C.Structure):
 
 class lsm_beams(C.Structure):
     _fields_ = [("sad", C.c_double), ("z_jaw_y", C.c_double), ("z_jaw_x", C.c_double),
-                ("n_beams", C.c_int32), ("jaws", _dp)]
+                ("n_beams", C.c_int32), ("jaws", _dp), ("gantry", _dp), ("iso", C.c_double * 3)]
 
 
 class lsm_particles(C.Structure):
@@ -238,8 +238,16 @@ def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None)
                        **{k: a.ctypes.data_as(_dp) for k, a in
                           zip(("w", "mix_c", "mix_mu", "mix_sa", "mix_sb", "e_sa", "e_sb"), keep)})
     jaws = _f64(beams.jaws)
+    gantry = getattr(beams, "gantry", None)
+    gp = None
+    if gantry is not None:
+        ga = _f64(gantry)
+        keep.append(ga)
+        gp = ga.ctypes.data_as(_dp)
+    iso = getattr(beams, "iso", (0.0, 0.0, beams.sad))
     bs = lsm_beams(sad=beams.sad, z_jaw_y=beams.z_jaw_y, z_jaw_x=beams.z_jaw_x,
-                   n_beams=beams.n_beams, jaws=jaws.ctypes.data_as(_dp))
+                   n_beams=beams.n_beams, jaws=jaws.ctypes.data_as(_dp), gantry=gp,
+                   iso=(C.c_double * 3)(*iso))
     pp = None
     if per_psr_hist is not None:
         ppa = np.ascontiguousarray(per_psr_hist, dtype=np.int64)
