@@ -74,6 +74,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the commissioning (batched) block")
     p.add_argument("--no-denoised", action="store_true", help="skip the denoised-dose block")
     p.add_argument("--no-pslfile", action="store_true", help="skip the PSL-file comparator block")
+    p.add_argument("--no-multibeam", action="store_true", help="skip the multi-beam plan block")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
@@ -332,6 +333,51 @@ def denoised_block(lsm, reps: int = 5, case: int = 192):
             "roofline": {"bound": "tensor", "kernel": "k_conv3d (14 layers)", "achieved": ach, "peak": bf16,
                          "unit": "TFLOP/s", "frac": ach / bf16, "peak_source": bkind,
                          "algorithmic_gflop": gf, "s_conv": T_conv}}
+
+
+def multibeam_block(lsm, W, opts, n_hist: int = 10_000_000, n_batches: int = 16, reps: int = 5):
+    """Multi-beam plans of Table 1 (7-beam prostate, 6-beam head and neck) on
+    CT-like phantoms: the whole plan (PSL build + run over all beams) per
+    step, event-timed, as histories/s and the projected time for 1e9 source
+    particles (the paper's T_total column for its analytic source)."""
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream()
+    for wl in (W.workload_prostate_7beam(n_hist), W.workload_hn_6beam(n_hist)):
+        ph = lsm.lsm_phantom_create(wl.phantom)
+        tally = lsm.lsm_tally_create(ph)
+        n_plan = n_hist // n_batches
+        o = lsm.RunOpts(electron_mode=1, n_batches=n_batches, chunk=opts.chunk, ctas_per_sm=opts.ctas_per_sm)
+
+        def step(seed):
+            lsm.lsm_tally_reset(tally)
+            psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)
+            lsm.lsm_run(psl, ph, tally, seed, o)
+            return psl
+
+        for r in range(3):
+            step(100 + r)
+        lsm.lsm_timing_read(reset=True)
+        ms = []
+        for r in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            psl = step(200 + r)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        tm = lsm.lsm_timing_read(reset=True)
+        led, st = lsm.lsm_tally_ledger(tally)
+        d, sg = lsm.lsm_dose(tally, ph, psl.denom / n_plan)
+        t = float(np.median(ms)) / 1e3
+        out[wl.name] = {
+            "beams": wl.beams.n_beams, "field_cm": float(wl.beams.jaws[0, 1] - wl.beams.jaws[0, 0]),
+            "histories": n_plan * n_batches, "ms": t * 1e3, "histories_per_s": n_plan * n_batches / t,
+            "s_per_1e9": t * 1e9 / (n_plan * n_batches), "u_mean_rel_D50": u_mean_rel(d, sg),
+            "entering_fraction": (st["photons"] + st["electrons"]) / max(st["histories"], 1),
+            "kernels_ms": {k: round(v[0] / reps, 4) for k, v in tm.items() if v[0] > 0}}
+    return out
 
 
 def _fs_type(path: str) -> str:
@@ -600,6 +646,11 @@ def main():
         lsm.lsm_timing_enable(True)
         denoised = denoised_block(lsm)
         lsm.lsm_timing_enable(False)
+    multibeam = None
+    if not args.no_multibeam:
+        lsm.lsm_timing_enable(True)
+        multibeam = multibeam_block(lsm, W, opts)
+        lsm.lsm_timing_enable(False)
     pslfile = None
     if not args.no_pslfile:
         lsm.lsm_timing_enable(True)
@@ -628,6 +679,7 @@ def main():
         "roofline": roofline,
         "batched": batched,
         "denoised": denoised,
+        "multibeam": multibeam,
         "pslfile": pslfile,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "histories/s", "h2d_bytes_per_step": int(h2d),
