@@ -7,9 +7,10 @@ difference normalised by the measured dose maximum (Eq. 10-11); high-gradient
 regions (build-up, penumbra) by the distance to agreement: at a measured
 point x, the smallest |x - y| over positions y where the calculated curve
 takes the measured value D_m(x). The calculated curve between its sample
-points is the straight-line interpolation. The split into regions follows
-AAPM TG-53 as the paper does: build-up = depths shallower than the measured
-dose maximum; penumbra = 80-120 % of the geometric field half-width at that
+points is the straight-line interpolation, continued along its end segments
+beyond the first and last points. The split into regions follows
+AAPM TG-53 as the paper does: build-up = depths shallower than the first
+depth where the measured dose reaches 99 % of its maximum; penumbra = 80-120 % of the geometric field half-width at that
 depth, inner and outer beam inside and outside it.
 """
 from __future__ import annotations
@@ -27,19 +28,24 @@ def rms_max(calc, meas, dmax_m: float):
 
 def dta_point(x: float, m: float, pos, calc) -> float:
     """Distance to agreement at position x for measured value m: minimum of
-    |x - y| over y on the piecewise-linear calculated curve with C(y) = m;
-    inf when the curve never takes the value m."""
+    |x - y| over y with C(y) = m, C the calculated curve, straight between its
+    sample points and continued along its first and last segments beyond the
+    end points (a depth-dose curve starts at the surface, half a voxel above
+    its first sample); inf when C never takes the value m."""
     best = math.inf
+    last = len(pos) - 2
     for j in range(len(pos) - 1):
         c0, c1 = float(calc[j]), float(calc[j + 1])
         y0, y1 = float(pos[j]), float(pos[j + 1])
-        if (c0 - m) * (c1 - m) > 0.0:
-            continue
         if c0 == c1:                       # a flat segment at the value m: nearest point of it
+            if c0 != m:
+                continue
             dist = 0.0 if y0 <= x <= y1 else min(abs(x - y0), abs(x - y1))
         else:
-            y = y0 + (m - c0) / (c1 - c0) * (y1 - y0)
-            dist = abs(x - y)
+            t = (m - c0) / (c1 - c0)
+            if not ((0.0 <= t <= 1.0) or (j == 0 and t < 0.0) or (j == last and t > 1.0)):
+                continue
+            dist = abs(x - (y0 + t * (y1 - y0)))
         best = min(best, dist)
     return best
 
@@ -64,8 +70,10 @@ def compare(pos, calc, meas, lo: float, hi: float, dmax_m: float, use_abs: bool 
 
 def depth_regions(depth, pdd_meas):
     """(build-up limits, beyond-build-up limits) in depth: the build-up ends
-    at the depth of the measured maximum."""
-    d_max = float(np.asarray(depth)[int(np.argmax(pdd_meas))])
+    at the first depth where the measured dose reaches 99 % of its maximum
+    (the maximum of a noisy, flat-topped curve can sit centimetres deeper)."""
+    m = np.asarray(pdd_meas, np.float64)
+    d_max = float(np.asarray(depth)[int(np.argmax(m >= 0.99 * m.max()))])
     return (-math.inf, d_max), (d_max, math.inf)
 
 
