@@ -75,6 +75,7 @@ def parse():
     p.add_argument("--no-denoised", action="store_true", help="skip the denoised-dose block")
     p.add_argument("--no-pslfile", action="store_true", help="skip the PSL-file comparator block")
     p.add_argument("--no-multibeam", action="store_true", help="skip the multi-beam plan block")
+    p.add_argument("--no-validation", action="store_true", help="skip the commissioning validation loop")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
@@ -333,6 +334,25 @@ def denoised_block(lsm, reps: int = 5, case: int = 192):
             "roofline": {"bound": "tensor", "kernel": "k_conv3d (14 layers)", "achieved": ach, "peak": bf16,
                          "unit": "TFLOP/s", "frac": ach / bf16, "peak_source": bkind,
                          "algorithmic_gflop": gf, "s_conv": T_conv}}
+
+
+def commission_validation_block(lsm):
+    """The commissioning validation loop of Sec. 3.2 (Tables 2-3): PSR doses
+    of the 40x40 and 5x5 fields, Eq. 8 by gradient projection, doses of five
+    fields for the commissioned and the uncommissioned model against the
+    synthetic linac's, timed end to end."""
+    import torch
+    from paper_1503_01725_b300 import commission as CM
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = CM.run()
+    torch.cuda.synchronize()
+    return {"case": "water 52x52x30 cm (0.5 cm), 360 PSRs; fields 40/20/10/5/2 cm, commissioned on 40 and 5",
+            "s_total": time.perf_counter() - t0, "seconds": rep["seconds"], "histories": rep["histories"],
+            "nnls_iterations": rep["nnls"]["iterations"], "factor_rel_err": rep["factor_rel_err"],
+            "table": CM.summary(rep),
+            "output_factor_max_rel_diff": {"commissioned": rep["output_factors"]["max_rel_diff_commissioned"],
+                                           "reference": rep["output_factors"]["max_rel_diff_reference"]}}
 
 
 def multibeam_block(lsm, W, opts, n_hist: int = 10_000_000, n_batches: int = 16, reps: int = 5):
@@ -646,6 +666,9 @@ def main():
         lsm.lsm_timing_enable(True)
         denoised = denoised_block(lsm)
         lsm.lsm_timing_enable(False)
+    validation = None
+    if not args.no_validation:
+        validation = commission_validation_block(lsm)
     multibeam = None
     if not args.no_multibeam:
         lsm.lsm_timing_enable(True)
@@ -679,6 +702,7 @@ def main():
         "roofline": roofline,
         "batched": batched,
         "denoised": denoised,
+        "commissioning_validation": validation,
         "multibeam": multibeam,
         "pslfile": pslfile,
         "cpu_baseline": cpu,

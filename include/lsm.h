@@ -517,6 +517,25 @@ lsm_status lsm_dose_error(const float *est, const float *ref, const float *sigma
                           lsm_mem mem, double *rms_rel, lsm_stream stream);
 
 /*
+ * lsm_curve_compare -- the dose comparison of the commissioning validation
+ * (Sec. 3.2): a calculated curve against a measured one, both sampled at the
+ * same n positions `pos` (ascending, cm; a depth-dose curve or a lateral
+ * profile), over the points with lo <= pos < hi (lo <= |pos| < hi when
+ * use_abs != 0):
+ *   out[0] RMS (Eq. 10) = sqrt(mean((calc - meas)^2)) / dmax_m,
+ *   out[1] Max (Eq. 11) = max |calc - meas| / dmax_m (fractions, not percent),
+ *   out[2], out[3] mean and max distance to agreement (cm): at a measured
+ *     point x, min |x - y| over y where the calculated curve, linear between
+ *     its points and continued along its first and last segments beyond the
+ *     end points, equals meas(x); points where it never does are left out,
+ *   out[4] points compared, out[5] points left out of the DTA figures.
+ * Arrays float32 in `mem`; synchronises. Errors: LSM_ERR_ARG for n < 2,
+ * n > 2^20 or dmax_m <= 0.
+ */
+lsm_status lsm_curve_compare(const float *pos, const float *calc, const float *meas, int32_t n, double lo, double hi,
+                             int32_t use_abs, double dmax_m, lsm_mem mem, double out[6], lsm_stream stream);
+
+/*
  * PSL files -- the comparator source model of Table 1 (Sec. 3.1): particles
  * stored on disk grouped by phase-spacelet, read for a field, copied to the
  * GPU and translated there, instead of being sampled on the fly.

@@ -119,6 +119,62 @@ __global__ void k_dose_err(const float *__restrict__ est, const float *__restric
 int grid_for_n(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 16ll * sm_count())); }
 
 // device copies of host arrays when mem is HOST; released by the caller
+// Curve comparison (Eq. 10-11 and distance to agreement, Sec. 3.2) in one
+// CTA: each thread takes measured points, searches every segment of the
+// piecewise-linear calculated curve for the measured value, and the CTA
+// reduces sum of squares, max |difference|, DTA sum / max and counts.
+__global__ void k_curve(const float *__restrict__ pos, const float *__restrict__ calc, const float *__restrict__ meas,
+                        int n, double lo, double hi, int use_abs, double *out)
+{
+    double ss = 0.0, mx = 0.0, dsum = 0.0, dmax = 0.0;
+    int cnt = 0, nocross = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = pos[i], key = use_abs ? fabs(x) : x;
+        if (!(key >= lo && key < hi)) continue;
+        const double m = meas[i], d = (double)calc[i] - m;
+        ss += d * d;
+        mx = fmax(mx, fabs(d));
+        ++cnt;
+        double best = INFINITY;
+        for (int j = 0; j + 1 < n; ++j) {
+            const double c0 = calc[j], c1 = calc[j + 1], y0 = pos[j], y1 = pos[j + 1];
+            double dist;
+            if (c0 == c1) {
+                if (c0 != m) continue;
+                dist = (y0 <= x && x <= y1) ? 0.0 : fmin(fabs(x - y0), fabs(x - y1));
+            } else {
+                // the end segments continue beyond the first and last points
+                const double t = (m - c0) / (c1 - c0);
+                if (!((t >= 0.0 && t <= 1.0) || (j == 0 && t < 0.0) || (j == n - 2 && t > 1.0))) continue;
+                dist = fabs(x - (y0 + t * (y1 - y0)));
+            }
+            best = fmin(best, dist);
+        }
+        if (isinf(best)) ++nocross;
+        else { dsum += best; dmax = fmax(dmax, best); }
+    }
+    __shared__ double sh[4][256];
+    __shared__ int shc[2][256];
+    sh[0][threadIdx.x] = ss; sh[1][threadIdx.x] = mx; sh[2][threadIdx.x] = dsum; sh[3][threadIdx.x] = dmax;
+    shc[0][threadIdx.x] = cnt; shc[1][threadIdx.x] = nocross;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + o]);
+            sh[2][threadIdx.x] += sh[2][threadIdx.x + o];
+            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + o]);
+            shc[0][threadIdx.x] += shc[0][threadIdx.x + o];
+            shc[1][threadIdx.x] += shc[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][0]; out[1] = sh[1][0]; out[2] = sh[2][0]; out[3] = sh[3][0];
+        out[4] = shc[0][0]; out[5] = shc[1][0];
+    }
+}
+
 struct Staged {
     std::vector<void *> bufs;
     ~Staged()
@@ -247,6 +303,38 @@ lsm_status lsm_dose_error(const float *est, const float *ref, const float *sigma
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_dose_error");
     const double cnt = sums[2] > 0 ? sums[2] : 1.0;
     *rms_rel = sqrt(std::max(sums[0] / cnt - sums[1] / cnt, 0.0));
+    return LSM_OK;
+}
+
+lsm_status lsm_curve_compare(const float *pos, const float *calc, const float *meas, int32_t n, double lo, double hi,
+                             int32_t use_abs, double dmax_m, lsm_mem mem, double out[6], lsm_stream stream)
+{
+    if (!pos || !calc || !meas || !out) return set_arg_error("lsm_curve_compare: NULL argument");
+    if (n < 2 || n > (1 << 20) || !(dmax_m > 0)) return set_arg_error("lsm_curve_compare: 2 <= n <= 2^20, dmax_m > 0");
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    Staged S;
+    const float *dp = S.put(pos, n, mem, st, e);
+    const float *dc = S.put(calc, n, mem, st, e);
+    const float *dm = S.put(meas, n, mem, st, e);
+    double *work = nullptr, r[6] = {0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMalloc(&work, 6 * sizeof(double));
+    if (e == cudaSuccess) {
+        k_curve<<<1, 256, 0, st>>>(dp, dc, dm, n, lo, hi, use_abs, work);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r, work, sizeof(r), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(work);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsm_curve_compare");
+    const double cnt = r[4], fin = r[4] - r[5];
+    out[0] = cnt > 0 ? sqrt(r[0] / cnt) / dmax_m : 0.0;
+    out[1] = r[1] / dmax_m;
+    out[2] = fin > 0 ? r[2] / fin : 0.0;
+    out[3] = r[3];
+    out[4] = r[4];
+    out[5] = r[5];
     return LSM_OK;
 }
 

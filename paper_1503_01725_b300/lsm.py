@@ -146,6 +146,8 @@ _EXPORTS = {
                             C.c_double, C.c_double, C.c_int, _dp, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p]),
     "lsm_dose_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, _dp,
                                  C.c_void_p]),
+    "lsm_curve_compare": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double,
+                                    C.c_int32, C.c_double, C.c_int, _dp, C.c_void_p]),
     "lsm_pslfile_write": (C.c_int, [C.c_void_p, C.c_uint64, C.c_char_p, C.POINTER(C.c_int64), C.c_void_p]),
     "lsm_pslfile_run": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_int32,
                                   C.c_int32, C.c_int32, C.POINTER(lsm_run_opts), C.POINTER(lsm_pslfile_stats),
@@ -415,6 +417,29 @@ def lsm_run(psl: PSL, ph: PhantomHandle, tally: Tally, seed: int, opts: RunOpts 
     o = (opts or RunOpts()).struct()
     return _check(_lib.lsm_run(psl.ptr, ph.ptr, tally.ptr, seed, C.byref(o), _stream(stream)), "lsm_run",
                   ok=(LSM_OK, LSM_ERR_OVERFLOW))
+
+
+def lsm_curve_compare(pos, calc, meas, lo: float = -np.inf, hi: float = np.inf, dmax_m: float | None = None,
+                      use_abs: bool = False, stream=None) -> dict:
+    """Eq. 10-11 RMS/Max and distance to agreement of a calculated curve
+    against a measured one (host or CUDA float32 arrays of equal length)."""
+    dev = hasattr(pos, "is_cuda") and pos.is_cuda
+    if dev:
+        arrs = [a.contiguous().float() for a in (pos, calc, meas)]
+        ptrs = [a.data_ptr() for a in arrs]
+        if dmax_m is None:
+            dmax_m = float(arrs[2].max())
+    else:
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (pos, calc, meas)]
+        ptrs = [a.ctypes.data for a in arrs]
+        if dmax_m is None:
+            dmax_m = float(arrs[2].max())
+    out = np.zeros(6)
+    _check(_lib.lsm_curve_compare(ptrs[0], ptrs[1], ptrs[2], len(arrs[0]), float(lo), float(hi), int(use_abs),
+                                  float(dmax_m), LSM_MEM_DEVICE if dev else LSM_MEM_HOST,
+                                  out.ctypes.data_as(_dp), _stream(stream)), "lsm_curve_compare")
+    return {"rms": out[0], "max": out[1], "dta_mean": out[2], "dta_max": out[3], "points": int(out[4]),
+            "no_crossing": int(out[5])}
 
 
 def lsm_pslfile_write(psl: PSL, seed: int, path: str, stream=None) -> int:
