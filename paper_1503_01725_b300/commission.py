@@ -44,11 +44,11 @@ class Case:
 
 
 def validation_case(nx: int = 104, nz: int = 60, voxel: float = 0.5, n_r: int = 12, dr: float = 0.35,
-                    seed: int = 3) -> Case:
+                    seed: int = 3, model: W.PSRModel | None = None) -> Case:
     """Water 52 x 52 x 30 cm (0.5 cm voxels) at SSD 100 cm and a 360-PSR model
     (3 sub-sources x 10 energy bins x 12 rings of 0.35 cm: the plane out to
-    4.2 cm, 21 cm at the isocentre)."""
-    model = W.psr_model(10, n_r, dr, seed=seed)
+    4.2 cm, 21 cm at the isocentre), or the given model."""
+    model = model if model is not None else W.psr_model(10, n_r, dr, seed=seed)
     ph = W.water_phantom(nx, nx, nz, voxel)
     idx, n_rows = W.commissioning_index(ph, DEPTHS)
     cy = cx = nx // 2
@@ -189,7 +189,7 @@ def run(case: Case | None = None, *, n_large: float = 2e9, hist_lo: int = 20_000
         fields[f"{f:g}x{f:g}"] = {"commissioned": compare_field(case, f, calc[f], meas[f]),
                                   "reference": compare_field(case, f, ref[f], meas[f])}
     return {
-        "x": x, "x_true": x_true, "nnls": rep,
+        "x": x, "x_true": x_true, "nnls": rep, "model": m_com,
         "factor_rel_err": float(np.linalg.norm(x - x_true) / np.linalg.norm(x_true)),
         "fields": fields,
         "output_factors": {"measured": of_meas, "commissioned": of_com, "reference": of_ref,
@@ -199,6 +199,15 @@ def run(case: Case | None = None, *, n_large: float = 2e9, hist_lo: int = 20_000
                       "per_model": int(sum(field_histories(f, n_large) // 8 * 8 for f in FIELDS))},
         "seconds": {"basis": t_basis, "fit": t_fit, "validation_doses": t_val},
     }
+
+
+def write_phase_space(model: W.PSRModel, path: str, n_records: int, seed: int = 1, open_field_cm: float = 40.0):
+    """A phase-space file of the (commissioned) model for other Monte Carlo
+    codes (Sec. 4): every history of a wide-open plan sampled on the
+    phase-space plane and written grouped by PSL cell (lsm_pslfile_write).
+    Returns the record count."""
+    plan = lsm.lsm_build_psl(model, W.beams(W.square_field(open_field_cm)), n_records)
+    return lsm.lsm_pslfile_write(plan, seed, path)
 
 
 def summary(rep: dict) -> dict:

@@ -147,6 +147,18 @@ def psr_model(n_e: int = 10, n_r: int = 10, dr: float = 0.25, *,
                     e_sa=e_sa, e_sb=e_sb)
 
 
+def fff_model(n_e: int = 10, n_r: int = 12, dr: float = 0.35, *, seed: int = 5) -> PSRModel:
+    """A flattening-filter-free variant: no scatter-photon sub-source (its
+    weights are zero), primary photons peaked on the axis (ring weights times
+    exp(-r / 2 cm) on the phase-space plane), 1.5 % contamination electrons."""
+    m = psr_model(n_e, n_r, dr, weights=(0.985, 0.0, 0.015), seed=seed)
+    rc = (np.arange(n_r) + 0.5) * dr
+    w = m.w.copy()
+    w[0] *= np.exp(-rc / 2.0)[None, :]
+    w[0] *= 0.985 / w[0].sum()
+    return m.with_weights(w / w.sum())
+
+
 def primary_only_model(n_e: int = 20, n_r: int = 10, dr: float = 0.2, *,
                        sigma_s: float = 0.1, seed: int = 1) -> PSRModel:
     """Primary-photon sub-source only: 20 bins over 0.25-6 MeV, 10 rings of 0.2 cm."""

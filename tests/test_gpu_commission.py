@@ -70,3 +70,78 @@ def test_validation_loop_improves_on_the_reference_model(L):
         assert c["crossline@10"]["inner_rms"] < 1.2 * r["crossline@10"]["inner_rms"], f
     s = CM.summary(rep)
     assert s["commissioned"]["pdd_rms_pct"][1] < s["reference"]["pdd_rms_pct"][1]
+
+
+def test_fff_dose_matches_oracle(L):
+    from oracle import oracle as O
+    from paper_1503_01725_b300 import workloads as W
+    m = W.fff_model()
+    beams = W.beams(W.square_field(8.0))
+    ph = W.water_phantom(32, 32, 32, 0.5)
+    n, nb = 100_000, 8
+    g = L.lsm_build_psl(m, beams, n)
+    parts = L.lsm_sample(g, 3, 0, n, W.SSD)
+    info = parts["info"].cpu().numpy()
+    assert not np.any((info[:, 0] & 0xFF) == 1)          # no scatter photons
+    phh = L.lsm_phantom_create(ph)
+    t = L.lsm_tally_create(phh)
+    L.lsm_run(g, phh, t, 5, L.RunOpts(n_batches=nb))
+    s1, s2, _ = L.lsm_tally_read(t)
+    r = O.run(O.Plan(m, beams, n), ph, 5, n_batches=nb, electron_mode=1)
+    dg, sg = O.dose_and_sigma(s1, s2, nb)
+    do, so = O.dose_and_sigma(r["s1"].ravel(), r["s2"].ravel(), nb)
+    sel = do > 0.1 * do.max()
+    z = (dg - do)[sel] / np.sqrt(sg[sel] ** 2 + so[sel] ** 2 + 1e-300)
+    assert np.mean(np.abs(z) < 3) >= 0.99
+    assert abs(dg[sel].mean() / do[sel].mean() - 1) < 0.01
+
+
+def test_fff_validation_loop(L):
+    from paper_1503_01725_b300 import commission as CM
+    from paper_1503_01725_b300 import workloads as W
+    rep = CM.run(CM.validation_case(model=W.fff_model()), n_large=2e9, hist_hi=4_000_000)
+    # the scatter columns are empty: their factors stay at the starting value
+    n = rep["x"].size
+    assert n == 2 * 10 * 12 + 10
+    better = [v["commissioned"]["pdd"]["rms"] < v["reference"]["pdd"]["rms"] for v in rep["fields"].values()]
+    assert sum(better) >= 4, better
+    s = CM.summary(rep)
+    assert s["commissioned"]["inline10_inner_rms_pct"][1] < s["reference"]["inline10_inner_rms_pct"][1]
+
+
+def test_phase_space_file_from_commissioned_weights(L, tmp_path):
+    """The commissioned model written as a phase-space file (Sec. 4) gives the
+    commissioned model's dose when read back for a 10x10 field."""
+    from oracle import oracle as O
+    from oracle import pslfile as P
+    from paper_1503_01725_b300 import commission as CM
+    from paper_1503_01725_b300 import workloads as W
+    case = CM.validation_case()
+    rep = CM.run(case, n_large=4e8, hist_hi=1_000_000)
+    mc = rep["model"]
+    path = str(tmp_path / "commissioned.psl")
+    n = CM.write_phase_space(mc, path, 12_000_000, seed=9)
+    assert n == 12_000_000
+    # the file's index is the oracle plan's per-cell counts of the commissioned model
+    with open(path, "rb") as f:
+        head = f.read(4096 + 8 * (3 * 24 * 24 + 1))
+    starts = np.frombuffer(head, "<i8", 3 * 24 * 24 + 1, 4096)
+    o = O.Plan(mc, W.beams(W.square_field(40.0)), n)
+    assert np.array_equal(starts, P.cell_starts(o.count[0].sum(axis=1)))
+    # dose of a 10x10 field read from the file against the model sampled on
+    # the fly with 10x the histories (z-test with 20-batch sigmas)
+    ph = L.lsm_phantom_create(case.phantom)
+    beams = W.beams(W.square_field(10.0))
+    field = L.lsm_build_psl(mc, beams, 1000)
+    t = L.lsm_tally_create(ph)
+    st = L.lsm_pslfile_run(path, field, ph, t, 3, n_batches=20)
+    d1, s1 = L.lsm_dose(t, ph, st["dose_scale"])
+    g = L.lsm_build_psl(mc, beams, st["records"] // 2)
+    t2 = L.lsm_tally_create(ph)
+    L.lsm_run(g, ph, t2, 4, L.RunOpts(n_batches=20))
+    info, denom = L.lsm_psl_info(g)
+    d2, s2 = L.lsm_dose(t2, ph, denom / info["plan_size"])
+    sel = d2 > 0.2 * d2.max()
+    z = (d1 - d2)[sel] / np.sqrt(s1[sel] ** 2 + s2[sel] ** 2 + 1e-300)
+    assert np.mean(np.abs(z) < 3) >= 0.985, np.mean(np.abs(z) < 3)
+    assert abs(d1[sel].mean() / d2[sel].mean() - 1) < 0.005
