@@ -59,9 +59,16 @@ struct TP {
     int ctas_per_sm;           // transport grid: CTAs per SM (0: as many as fit)
 };
 
-constexpr int kTableBytes = 2 * kGrid * 16 + kGrid * 4 + kKnE * kKnU * 4;   // 52 KB
+constexpr int kTableBytes = 2 * kGrid * 16 + kGrid * 4 + kKnE * kKnU * 4;   // 52 KB: photons
+constexpr int kXsBytes = 2 * kGrid * 16;                                      // 32 KB: electrons
 
 // resident CTAs per SM the transport kernels are compiled for (register budget)
+#ifndef LSM_PHOTON_THREADS
+#define LSM_PHOTON_THREADS 256
+#endif
+#ifndef LSM_ELECTRON_THREADS
+#define LSM_ELECTRON_THREADS 256
+#endif
 #ifndef LSM_PHOTON_MINB
 #define LSM_PHOTON_MINB 4
 #endif
@@ -74,15 +81,17 @@ constexpr int kTableBytes = 2 * kGrid * 16 + kGrid * 4 + kKnE * kKnU * 4;   // 5
 // Stage the interaction tables into shared memory with one bulk asynchronous
 // copy (cp.async.bulk, completion on an mbarrier). The wait is bounded; on
 // timeout the block reports through *err and runs from global memory.
+template <bool FULL>
 __device__ __forceinline__ bool stage_tables(float4 *s_xs, const float4 *g_xs, const float *g_mumax,
                                              uint64_t *mbar, unsigned *err)
 {
+    constexpr uint32_t bytes = FULL ? (uint32_t)kTableBytes : (uint32_t)kXsBytes;
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(mbar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTableBytes)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                      : "memory");
         const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(s_xs);
         const uint32_t d1 = (uint32_t)__cvta_generic_to_shared(s_xs + 2 * kGrid);
@@ -90,10 +99,11 @@ __device__ __forceinline__ bool stage_tables(float4 *s_xs, const float4 *g_xs, c
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d0),
             "l"(g_xs), "r"(2 * kGrid * 16), "r"(bar)
             : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d1),
-            "l"(g_mumax), "r"(kGrid * 4 + kKnE * kKnU * 4), "r"(bar)
-            : "memory");
+        if (FULL)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d1),
+                "l"(g_mumax), "r"(kGrid * 4 + kKnE * kKnU * 4), "r"(bar)
+                : "memory");
     }
     __syncthreads();
     uint32_t done = 0;
@@ -216,8 +226,10 @@ struct Part {
     Stream rng;
     uint32_t pb;
     int steps;
-    int vc;        // voxel whose (sign-coded) density is held in rc, -1 if none
+    int vc;        // voxel whose (sign-coded) density is held in rc, -1 if none (photons: the current voxel)
     float rc;
+    int dv;        // electrons: voxel of the deposit not yet written, -1 if none
+    float de;      // and its energy (consecutive steps in one voxel add up here)
 };
 
 __device__ __forceinline__ void load_part(const Queue &q, uint32_t i, uint32_t k0, uint32_t k1, Part &p)
@@ -232,6 +244,8 @@ __device__ __forceinline__ void load_part(const Queue &q, uint32_t i, uint32_t k
     p.steps = 0;
     p.vc = -1;
     p.rc = 0.0f;
+    p.dv = -1;
+    p.de = 0.0f;
     p.rng.have = 0;
 }
 
@@ -278,7 +292,7 @@ template <int MODE>
 __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t, Acc &A, Part &p,
                             const Queue &eq, const Queue *pq, Pend &pe, bool &pend)
 {
-    int vox = voxel(T, p.x, p.y, p.z);
+    int vox = p.vc >= 0 ? p.vc : voxel(T, p.x, p.y, p.z);
     if (vox < 0) { A.esc += p.E; return false; }
     if (p.E < kCutG) { deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
     if (++p.steps > T.max_steps) { A.cap++; deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
@@ -287,7 +301,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     float tf;
     tab_pos(T.inv_dlnE, p.E, ti, tf);
     const float mm = (mumax_t[ti] + tf * (mumax_t[ti + 1] - mumax_t[ti])) * T.maj;
-    const float s = -__logf(u01(r.x)) * __frcp_rn(mm);
+    const float s = __fdividef(-__logf(u01(r.x)), mm);
     p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
     A.flights++;
     vox = voxel(T, p.x, p.y, p.z);
@@ -296,6 +310,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     // depend on the density: compute it while the load is in flight
     p.rng.prefetch();
     if (vox < 0) { A.esc += p.E; return false; }
+    p.vc = vox;                    // the photon stays here until its next flight
     const int m = rm < 0.0f;
     const float rho = fabsf(rm);
     const float4 c = lerp4(xs + m * kGrid, ti, tf);
@@ -364,14 +379,38 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     return false;
 }
 
+// An electron deposits about twice per voxel: deposits into the voxel of the
+// previous one are added in a register and written when the voxel changes or
+// the electron ends.
+template <int MODE>
+__device__ __forceinline__ void edep(const TP &T, Acc &A, Part &p, int vox, float e)
+{
+    if (vox == p.dv) { p.de += e; return; }
+    if (p.dv >= 0) deposit<MODE>(T, A, p.dv, p.de, p.pb);
+    p.dv = vox;
+    p.de = e;
+}
+
+template <int MODE>
+__device__ __forceinline__ void eflush(const TP &T, Acc &A, Part &p)
+{
+    if (p.dv >= 0) deposit<MODE>(T, A, p.dv, p.de, p.pb);
+    p.dv = -1;
+}
+
 // One CSDA step. Returns false when the electron's history ends.
 template <int MODE>
 __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
 {
     const int vox = voxel(T, p.x, p.y, p.z);
-    if (vox < 0) { A.esc += p.E; return false; }
-    if (p.E < kCutE) { deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
-    if (++p.steps > T.max_steps) { A.cap++; deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
+    if (vox < 0) { eflush<MODE>(T, A, p); A.esc += p.E; return false; }
+    if (p.E < kCutE) { edep<MODE>(T, A, p, vox, p.E); eflush<MODE>(T, A, p); return false; }
+    if (++p.steps > T.max_steps) {
+        A.cap++;
+        edep<MODE>(T, A, p, vox, p.E);
+        eflush<MODE>(T, A, p);
+        return false;
+    }
     // an electron takes about two steps per voxel: reuse the density loaded
     // for this voxel at the end of the previous step
     const float rm = vox == p.vc ? p.rc : __ldg(T.rhomat + vox);
@@ -389,7 +428,7 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
     const float dE = fminf(c1.w * rho * ds, p.E);
     const float hs = 0.5f * ds;
     const int vm = voxel(T, p.x + hs * p.u, p.y + hs * p.v, p.z + hs * p.w);
-    if (vm >= 0) deposit<MODE>(T, A, vm, dE, p.pb);
+    if (vm >= 0) edep<MODE>(T, A, p, vm, dE);
     else A.esc += dE;
     A.esteps++;
     const float E0 = p.E;
@@ -443,7 +482,8 @@ __device__ void flush_acc(const TP &T, const Acc &A)
 // Persistent transport kernel with per-lane refill from queue `qi`.
 // KIND 0: photons (Woodcock), KIND 1: electrons (CSDA).
 template <int MODE, int KIND>
-__global__ void __launch_bounds__(256, KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MINB) k_transport(TP T, Queue in, int qi, Queue eq, Queue pq, int has_pq)
+__global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREADS,
+                                  KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MINB) k_transport(TP T, Queue in, int qi, Queue eq, Queue pq, int has_pq)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -455,7 +495,7 @@ __global__ void __launch_bounds__(256, KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MIN
     if ((uint64_t)blockIdx.x * blockDim.x >= n_in) return;
     float4 *s_xs = reinterpret_cast<float4 *>(smem);
     float *s_mm = reinterpret_cast<float *>(smem + 2 * kGrid * 16);
-    const bool staged = stage_tables(s_xs, T.xs, T.mumax, &mbar, &T.cnt->pad);
+    const bool staged = stage_tables<KIND == 0>(s_xs, T.xs, T.mumax, &mbar, &T.cnt->pad);
     const float4 *xs = staged ? s_xs : T.xs;
     const float *mm = staged ? s_mm : T.mumax;
     uint32_t *head = &T.cnt->head[qi];
@@ -469,7 +509,14 @@ __global__ void __launch_bounds__(256, KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MIN
     // them to its lanes as they fall idle; [rb, rb + rl) is the unused part
     // of the reservation (warp-uniform). Slots are handed out in queue order,
     // so once a handed-out slot lies past the end, every later one does too.
-    constexpr uint32_t kGrab = 32;
+#ifndef LSM_GRAB_DIV
+#define LSM_GRAB_DIV 8
+#endif
+    // a reservation is 32-256 slots, about 1/LSM_GRAB_DIV of a warp's share of
+    // the queue: few enough atomics and long enough prefetch lead, fine enough
+    // that the queue's end leaves little imbalance
+    const uint32_t share = n_in / (gridDim.x * (blockDim.x >> 5) * LSM_GRAB_DIV);
+    const uint32_t kGrab = share >= 256 ? 256u : (share >= 128 ? 128u : (share >= 64 ? 64u : 32u));
     uint32_t rb = 0, rl = 0;
     bool exhausted = false;
     // output reservation for the electrons photons create: [ob, ob + ol)
@@ -490,6 +537,15 @@ __global__ void __launch_bounds__(256, KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MIN
                 nb = __shfl_sync(0xffffffffu, nb, 0);
                 grabbed = true;
                 if (nb + kGrab >= n_in) exhausted = true;
+                // the reservation's records are handed out over the next few
+                // steps: start moving them from DRAM into L2 now (one 128-byte
+                // line per lane, inside the queue's filled part)
+                if (nb < n_in) {
+                    const size_t bytes = (size_t)(min(nb + kGrab, n_in) - nb) * 48;
+                    const size_t off = (size_t)lane * 128;
+                    if (off < bytes)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"((const char *)(in.rec + 3 * (size_t)nb) + off));
+                }
             }
             if (!alive) {
                 const uint32_t r = (uint32_t)__popc(need & lt);
@@ -1095,29 +1151,29 @@ lsm_status check_opts(lsm_run_opts &o)
 template <int MODE>
 lsm_status drain(const TP &T, Workspace &W, lsm_tally *t, cudaStream_t st)
 {
-    const size_t smem = (size_t)kTableBytes;
+    const size_t smem = (size_t)kTableBytes, smem_e = (size_t)kXsBytes;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_transport<MODE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_transport<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_transport<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e);
         attr = true;
     }
     static int gp_max = 0, ge_max = 0;
-    if (!gp_max) gp_max = grid_for((const void *)k_transport<MODE, 0>, 256, smem);
-    if (!ge_max) ge_max = grid_for((const void *)k_transport<MODE, 1>, 256, smem);
+    if (!gp_max) gp_max = grid_for((const void *)k_transport<MODE, 0>, LSM_PHOTON_THREADS, smem);
+    if (!ge_max) ge_max = grid_for((const void *)k_transport<MODE, 1>, LSM_ELECTRON_THREADS, smem_e);
     const int cap = T.ctas_per_sm > 0 ? T.ctas_per_sm * sm_count() : (1 << 30);
     const int gp = std::min(gp_max, cap), ge = std::min(ge_max, cap);
     int tk = timer_begin(2, st);
-    k_transport<MODE, 0><<<gp, 256, smem, st>>>(T, W.q[0], 0, W.q[2], W.q[1], 1);
+    k_transport<MODE, 0><<<gp, LSM_PHOTON_THREADS, smem, st>>>(T, W.q[0], 0, W.q[2], W.q[1], 1);
     LSM_LAUNCHED("k_transport<photon>");
     timer_end(tk, st);
     tk = timer_begin(3, st);
-    k_transport<MODE, 0><<<gp, 256, smem, st>>>(T, W.q[1], 1, W.q[2], W.q[1], 0);
+    k_transport<MODE, 0><<<gp, LSM_PHOTON_THREADS, smem, st>>>(T, W.q[1], 1, W.q[2], W.q[1], 0);
     LSM_LAUNCHED("k_transport<annihilation photon>");
     timer_end(tk, st);
     if (T.electron_mode) {
         tk = timer_begin(4, st);
-        k_transport<MODE, 1><<<ge, 256, smem, st>>>(T, W.q[2], 2, W.q[2], W.q[1], 0);
+        k_transport<MODE, 1><<<ge, LSM_ELECTRON_THREADS, smem_e, st>>>(T, W.q[2], 2, W.q[2], W.q[1], 0);
         LSM_LAUNCHED("k_transport<electron>");
         timer_end(tk, st);
     }
