@@ -39,12 +39,63 @@ __device__ __forceinline__ double psl_radius(int ix, int iy, int n_r, double p)
     return sqrt(xc * xc + yc * yc);
 }
 
-// Steps 1-4 per (sub-source, energy bin) block: one CTA per block.
-__global__ void k_psl_weights(const double *__restrict__ w, int n_e, int n_r, double dr,
-                              double *__restrict__ wpsl, double *__restrict__ block_scale,
-                              int32_t *__restrict__ tag_r0, double *__restrict__ tag_l0)
+struct Geom {
+    const double *jaws;
+    int n_beams;
+    double z_phsp, sad, z_jaw_x, z_jaw_y;
+};
+
+// Sampling areas of beam b on the phase-space plane: a[0..3] primary, a[4..7]
+// scatter/electrons (xa, xb, ya, yb).
+__device__ __forceinline__ void beam_area(const Geom &G, int b, double a[8])
 {
-    const int blk = blockIdx.x;               // s * n_e + e
+    const double x1 = G.jaws[4 * b], x2 = G.jaws[4 * b + 1], y1 = G.jaws[4 * b + 2], y2 = G.jaws[4 * b + 3];
+    const double k = G.z_phsp / G.sad;                // primary: opening scaled to the plane
+    a[0] = x1 * k; a[1] = x2 * k; a[2] = y1 * k; a[3] = y2 * k;
+    const double cx = 0.5 * (x1 + x2), cy = 0.5 * (y1 + y2);
+    const double fx = (G.sad - G.z_phsp) / (G.sad - G.z_jaw_x), fy = (G.sad - G.z_phsp) / (G.sad - G.z_jaw_y);
+    const double kx = G.z_jaw_x / G.sad, ky = G.z_jaw_y / G.sad;
+    a[4] = cx + (x1 * kx - cx) * fx;                  // scatter/electrons: back projection
+    a[5] = cx + (x2 * kx - cx) * fx;
+    a[6] = cy + (y1 * ky - cy) * fy;
+    a[7] = cy + (y2 * ky - cy) * fy;
+}
+
+// Areas (and the single-precision jaw limits in the jaw planes for the
+// rejection test), one thread per beam.
+__device__ __forceinline__ void write_areas(const Geom &G, int b, double *__restrict__ area,
+                                            float *__restrict__ jaws_f)
+{
+    double a[8];
+    beam_area(G, b, a);
+    for (int k = 0; k < 8; ++k) area[8 * b + k] = a[k];
+    const double x1 = G.jaws[4 * b], x2 = G.jaws[4 * b + 1], y1 = G.jaws[4 * b + 2], y2 = G.jaws[4 * b + 3];
+    jaws_f[4 * b + 0] = (float)(y1 * G.z_jaw_y / G.sad);
+    jaws_f[4 * b + 1] = (float)(y2 * G.z_jaw_y / G.sad);
+    jaws_f[4 * b + 2] = (float)(x1 * G.z_jaw_x / G.sad);
+    jaws_f[4 * b + 3] = (float)(x2 * G.z_jaw_x / G.sad);
+}
+
+// PSL inclusion of cell i = (beam, class, PSL): positive-area overlap with the
+// class's sampling area.
+__device__ __forceinline__ void incl_cell(const Geom &G, int n_r, double p, int64_t i, uint8_t *__restrict__ incl)
+{
+    const int nxy = 2 * n_r, npsl = nxy * nxy;
+    const int j = (int)(i % npsl), bc = (int)(i / npsl);
+    const int iy = j / nxy, ix = j % nxy;
+    double area[8];
+    beam_area(G, bc >> 1, area);
+    const double *a = area + 4 * (bc & 1);
+    const double xl = (double)(ix - n_r) * p, xh = (double)(ix - n_r + 1) * p;
+    const double yl = (double)(iy - n_r) * p, yh = (double)(iy - n_r + 1) * p;
+    incl[i] = (uint8_t)(xh > a[0] && xl < a[1] && yh > a[2] && yl < a[3]);
+}
+
+// Steps 1-4 per (sub-source, energy bin) block: one CTA per block.
+__device__ __forceinline__ void psl_weights_block(int blk, const double *__restrict__ w, int n_e, int n_r, double dr,
+                                                  double *__restrict__ wpsl, double *__restrict__ block_scale,
+                                                  int32_t *__restrict__ tag_r0, double *__restrict__ tag_l0)
+{
     const int nxy = 2 * n_r, npsl = nxy * nxy;
     const double *W = w + (size_t)blk * n_r;
     double *out = wpsl + (size_t)blk * npsl;
@@ -81,44 +132,53 @@ __global__ void k_psl_weights(const double *__restrict__ w, int n_e, int n_r, do
     for (int j = threadIdx.x; j < npsl; j += blockDim.x) out[j] = out[j] * sc;
 }
 
-// Sampling areas on the phase-space plane, one thread per beam.
-__global__ void k_areas(const double *__restrict__ jaws, int n_beams, double z_phsp, double sad,
-                        double z_jaw_x, double z_jaw_y, double *__restrict__ area,
-                        float *__restrict__ jaws_f)
-{
-    const int b = threadIdx.x;
-    if (b >= n_beams) return;
-    const double x1 = jaws[4 * b], x2 = jaws[4 * b + 1], y1 = jaws[4 * b + 2], y2 = jaws[4 * b + 3];
-    double *a = area + 8 * b;
-    const double k = z_phsp / sad;                    // primary: opening scaled to the plane
-    a[0] = x1 * k; a[1] = x2 * k; a[2] = y1 * k; a[3] = y2 * k;
-    const double cx = 0.5 * (x1 + x2), cy = 0.5 * (y1 + y2);
-    const double fx = (sad - z_phsp) / (sad - z_jaw_x), fy = (sad - z_phsp) / (sad - z_jaw_y);
-    const double kx = z_jaw_x / sad, ky = z_jaw_y / sad;
-    a[4] = cx + (x1 * kx - cx) * fx;                  // scatter/electrons: back projection
-    a[5] = cx + (x2 * kx - cx) * fx;
-    a[6] = cy + (y1 * ky - cy) * fy;
-    a[7] = cy + (y2 * ky - cy) * fy;
-    // jaw limits in the jaw planes for the rejection test (single precision)
-    jaws_f[4 * b + 0] = (float)(y1 * z_jaw_y / sad);
-    jaws_f[4 * b + 1] = (float)(y2 * z_jaw_y / sad);
-    jaws_f[4 * b + 2] = (float)(x1 * z_jaw_x / sad);
-    jaws_f[4 * b + 3] = (float)(x2 * z_jaw_x / sad);
-}
+__device__ __forceinline__ void dir_tables_one(const double *__restrict__ mc, const double *__restrict__ mmu,
+                                               const double *__restrict__ msa, const double *__restrict__ msb,
+                                               const double *__restrict__ esa, const double *__restrict__ esb, int i,
+                                               unsigned long long *__restrict__ thr, float4 *__restrict__ mix,
+                                               float2 *__restrict__ esig);
 
-// PSL inclusion: positive-area overlap with the sampling area.
-__global__ void k_incl(const double *__restrict__ area, int n_beams, int n_r, double p,
-                       uint8_t *__restrict__ incl)
+struct SetupArgs {
+    const double *w;
+    int n_e, n_r;
+    double dr;
+    double *wpsl, *block_scale;
+    int32_t *tag_r0;
+    double *tag_l0;
+    Geom G;
+    double *area;
+    float *jaws_f;
+    uint8_t *incl;
+    int n_incl_blocks;
+    const double *mc, *mmu, *msa, *msb, *esa, *esb;
+    int nes;
+    unsigned long long *thr;
+    float4 *mix;
+    float2 *esig;
+};
+
+// One launch for the independent set-up work of a plan, by block: the PSL
+// weights of each (sub-source, energy) block, the sampling areas and PSL
+// inclusion of every beam, and the direction tables.
+__global__ void k_setup(SetupArgs A)
 {
-    const int nxy = 2 * n_r, npsl = nxy * nxy;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n_beams * 2 * npsl) return;
-    const int j = (int)(i % npsl), bc = (int)(i / npsl);
-    const int iy = j / nxy, ix = j % nxy;
-    const double *a = area + 4 * bc;
-    const double xl = (double)(ix - n_r) * p, xh = (double)(ix - n_r + 1) * p;
-    const double yl = (double)(iy - n_r) * p, yh = (double)(iy - n_r + 1) * p;
-    incl[i] = (uint8_t)(xh > a[0] && xl < a[1] && yh > a[2] && yl < a[3]);
+    const int nw = 3 * A.n_e;
+    int blk = blockIdx.x;
+    if (blk < nw) {
+        psl_weights_block(blk, A.w, A.n_e, A.n_r, A.dr, A.wpsl, A.block_scale, A.tag_r0, A.tag_l0);
+        return;
+    }
+    blk -= nw;
+    if (blk < A.n_incl_blocks) {
+        const int npsl = 4 * A.n_r * A.n_r;
+        const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
+        if (blk == 0 && (int)threadIdx.x < A.G.n_beams) write_areas(A.G, threadIdx.x, A.area, A.jaws_f);
+        if (i < (int64_t)A.G.n_beams * 2 * npsl) incl_cell(A.G, A.n_r, A.dr, i, A.incl);
+        return;
+    }
+    blk -= A.n_incl_blocks;
+    const int i = blk * blockDim.x + threadIdx.x;
+    if (i < A.nes) dir_tables_one(A.mc, A.mmu, A.msa, A.msb, A.esa, A.esb, i, A.thr, A.mix, A.esig);
 }
 
 // ------------------------------------------------ whole-source plan (Eq. 3) --
@@ -143,25 +203,28 @@ __global__ void k_eq3_parts(const double *__restrict__ wpsl, const uint8_t *__re
     }
 }
 
-__global__ void k_eq3_denom(const double *__restrict__ parts, int n, double *__restrict__ denom)
-{
-    double D = 0.0;
-    for (int i = 0; i < n; ++i) D += parts[i];
-    *denom = D;
-}
-
+// Eq. 3 floors. The denominator is the sequential sum of the partial sums
+// in (beam, sub-source, energy) order, formed by every block (block 0 stores it).
 __global__ void k_eq3_floor(const double *__restrict__ wpsl, const uint8_t *__restrict__ incl,
-                            int n_e, int npsl, int64_t ncell, int64_t n_hist,
-                            const double *__restrict__ denom, int64_t *__restrict__ count,
+                            int n_e, int npsl, int64_t ncell, int64_t n_hist, const double *__restrict__ parts,
+                            int n_parts, double *__restrict__ denom, int64_t *__restrict__ count,
                             double *__restrict__ rem, unsigned long long *__restrict__ floor_sum)
 {
+    __shared__ double s_D;
+    if (threadIdx.x == 0) {
+        double D = 0.0;
+        for (int k = 0; k < n_parts; ++k) D += parts[k];
+        s_D = D;
+        if (blockIdx.x == 0) *denom = D;
+    }
+    __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     long long f = 0;
     if (i < ncell) {
         const int j = (int)(i % npsl);
         const int64_t bse = i / npsl;
         const int e = (int)(bse % n_e), s = (int)((bse / n_e) % 3), b = (int)(bse / (3 * n_e));
-        const double D = *denom;
+        const double D = s_D;
         const bool inc = incl[(size_t)(b * 2 + (s ? 1 : 0)) * npsl + j] != 0;
         const double q = (inc && D > 0.0) ? ((double)n_hist * wpsl[((size_t)s * n_e + e) * npsl + j]) / D
                                           : 0.0;
@@ -186,12 +249,8 @@ __global__ void k_eq3_floor(const double *__restrict__ wpsl, const uint8_t *__re
 // lower loop index) get one more particle. Zero remainders always rank after
 // every positive one, in index order, so only positive remainders are ranked
 // against each other; a zero cell's rank is n_pos + (zero cells before it).
-__global__ void k_pos_compact(const double *__restrict__ rem, const int64_t *__restrict__ pos_idx, int64_t ncell,
-                              double *__restrict__ posrem)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ncell && rem[i] > 0.0) posrem[pos_idx[i]] = rem[i];
-}
+// (the positions come from k_scan_pos below, which also compacts the
+// positive remainders and clears the rank counters)
 
 // rank[p] += #{q : posrem[q] > posrem[p], or equal with q < p} over one tile
 // of 256 candidates p and 1024 competitors q; the grid covers all tile pairs.
@@ -301,17 +360,16 @@ __global__ void k_psr_counts(const double *__restrict__ w, const double *__restr
 
 // ------------------------------------------------------ scans and entries --
 
-// Single-CTA exclusive scan of v(i) over [0, n); out[n] = total.
-template <class F>
-__global__ void k_scan(F f, int64_t n, int64_t *__restrict__ out)
+// Positive remainders: exclusive positions pos_idx (pos_idx[n] = count), the
+// remainders compacted in index order, and rank[] cleared -- one CTA.
+__global__ void k_scan_pos(const double *__restrict__ rem, int64_t n, int64_t *__restrict__ pos_idx,
+                           double *__restrict__ posrem, int *__restrict__ rank)
 {
-    __shared__ long long part[1024];
     const int T = blockDim.x;
     const int64_t seg = (n + T - 1) / T;
     const int64_t a = (int64_t)threadIdx.x * seg, bnd = a + seg < n ? a + seg : n;
     long long s = 0;
-    for (int64_t i = a; i < bnd; ++i) s += f(i);
-    // exclusive block scan of the per-thread sums (T = 1024 = 32 warps)
+    for (int64_t i = a; i < bnd; ++i) { s += rem[i] > 0.0 ? 1 : 0; rank[i] = 0; }
     __shared__ long long wsum[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     long long incl = s;
@@ -327,28 +385,58 @@ __global__ void k_scan(F f, int64_t n, int64_t *__restrict__ out)
             const long long v = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += v;
         }
-        wsum[lane] = w;                       // inclusive over warps
-        if (lane == 31) out[n] = w;
+        wsum[lane] = w;
+        if (lane == 31) pos_idx[n] = w;
     }
     __syncthreads();
-    part[threadIdx.x] = incl - s + (wid ? wsum[wid - 1] : 0);
-    __syncthreads();
-    long long run = part[threadIdx.x];
-    for (int64_t i = a; i < bnd; ++i) { out[i] = run; run += f(i); }
+    long long run = incl - s + (wid ? wsum[wid - 1] : 0);
+    for (int64_t i = a; i < bnd; ++i) {
+        pos_idx[i] = run;
+        const double r = rem[i];
+        if (r > 0.0) posrem[run++] = r;
+    }
 }
 
-struct CountOf {
-    const int64_t *c;
-    __device__ long long operator()(int64_t i) const { return c[i]; }
-};
-struct Positive {
-    const double *r;
-    __device__ long long operator()(int64_t i) const { return r[i] > 0.0 ? 1 : 0; }
-};
-struct NonZero {
-    const int64_t *c;
-    __device__ long long operator()(int64_t i) const { return c[i] > 0 ? 1 : 0; }
-};
+// Plan prefix of the counts (cstart) and entry index of the non-empty cells
+// (eidx) in one pass of one CTA, and the plan end start[n_ent] = total.
+__global__ void k_scan_counts(const int64_t *__restrict__ count, int64_t n, int64_t *__restrict__ cstart,
+                              int64_t *__restrict__ eidx, int64_t *__restrict__ start)
+{
+    const int T = blockDim.x;
+    const int64_t seg = (n + T - 1) / T;
+    const int64_t a = (int64_t)threadIdx.x * seg, bnd = a + seg < n ? a + seg : n;
+    long long s = 0, z = 0;
+    for (int64_t i = a; i < bnd; ++i) { const long long c = count[i]; s += c; z += c > 0 ? 1 : 0; }
+    __shared__ long long ws[32], wz[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long is = s, iz = z;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, is, o), u = __shfl_up_sync(0xffffffffu, iz, o);
+        if (lane >= o) { is += v; iz += u; }
+    }
+    if (lane == 31) { ws[wid] = is; wz[wid] = iz; }
+    __syncthreads();
+    if (wid == 0) {
+        long long x = lane < (T >> 5) ? ws[lane] : 0, y = lane < (T >> 5) ? wz[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long v = __shfl_up_sync(0xffffffffu, x, o), u = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) { x += v; y += u; }
+        }
+        ws[lane] = x;
+        wz[lane] = y;
+        if (lane == 31) { cstart[n] = x; eidx[n] = y; start[y] = x; }
+    }
+    __syncthreads();
+    long long rs = is - s + (wid ? ws[wid - 1] : 0), rz = iz - z + (wid ? wz[wid - 1] : 0);
+    for (int64_t i = a; i < bnd; ++i) {
+        const long long c = count[i];
+        cstart[i] = rs;
+        eidx[i] = rz;
+        rs += c;
+        rz += c > 0 ? 1 : 0;
+    }
+}
+
 
 __device__ unsigned long long thresh32(double p)
 {
@@ -414,21 +502,14 @@ __global__ void k_entries(const int64_t *__restrict__ count, const int64_t *__re
     escale[q] = sc;
 }
 
-__global__ void k_entries_end(const int64_t *__restrict__ cstart, int64_t ncell,
-                              const int64_t *__restrict__ eidx, int64_t *__restrict__ start)
-{
-    start[eidx[ncell]] = cstart[ncell];
-}
 
 // scatter-mixture component thresholds and single-precision direction tables
-__global__ void k_dir_tables(const double *__restrict__ mc, const double *__restrict__ mmu,
-                             const double *__restrict__ msa, const double *__restrict__ msb,
-                             const double *__restrict__ esa, const double *__restrict__ esb, int n,
-                             unsigned long long *__restrict__ thr, float4 *__restrict__ mix,
-                             float2 *__restrict__ esig)
+__device__ __forceinline__ void dir_tables_one(const double *__restrict__ mc, const double *__restrict__ mmu,
+                                               const double *__restrict__ msa, const double *__restrict__ msb,
+                                               const double *__restrict__ esa, const double *__restrict__ esb, int i,
+                                               unsigned long long *__restrict__ thr, float4 *__restrict__ mix,
+                                               float2 *__restrict__ esig)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     const double *c = mc + 3 * i;
     const double tot = c[0] + c[1] + c[2];
     thr[2 * i] = thresh32(c[0] / tot);
@@ -570,10 +651,23 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
         if (e_ != cudaSuccess) { free_psl(P); return set_cuda_error(e_, where); } \
     } while (0)
 
-    // host inputs packed into one copy
-    std::vector<double> hin(nw + 4 * nm + 2 * nes + 4 * (size_t)nb + (size_t)npsr, 0.0);
+    // host inputs packed into one copy from pinned memory (a copy from
+    // pageable memory would first wait for the stream's earlier work); the
+    // staging buffer is reused by this thread's next build, which starts only
+    // after this build's final synchronisation
+    const size_t n_in = nw + 4 * nm + 2 * nes + 4 * (size_t)nb + (size_t)npsr;
+    static thread_local double *hbuf = nullptr;
+    static thread_local size_t hcap = 0;
+    if (hcap < n_in + 16) {
+        if (hbuf) cudaFreeHost(hbuf);
+        hbuf = nullptr;
+        hcap = 0;
+        CK(cudaMallocHost((void **)&hbuf, (n_in + 16) * sizeof(double)));
+        hcap = n_in + 16;
+    }
     {
-        double *h = hin.data();
+        double *h = hbuf;
+        memset(h, 0, n_in * sizeof(double));
         memcpy(h, M->w, nw * 8); h += nw;
         memcpy(h, M->mix_c, nm * 8); h += nm;
         memcpy(h, M->mix_mu, nm * 8); h += nm;
@@ -584,29 +678,30 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
         memcpy(h, B->jaws, (size_t)nb * 32); h += 4 * nb;
         if (per_psr_hist) memcpy(h, per_psr_hist, (size_t)npsr * 8);
     }
-    CK(cudaMemcpyAsync(d_in, hin.data(), hin.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_in, hbuf, n_in * 8, cudaMemcpyHostToDevice, st));
     {
-        float2 hrot[16];
+        float2 *hrot = (float2 *)(hbuf + n_in);       // 16 beams x 8 bytes in the 16 spare slots
         for (int b = 0; b < nb; ++b) hrot[b] = make_float2((float)cos(P->gantry[b]), (float)sin(P->gantry[b]));
         CK(cudaMemcpyAsync(base + o_rot, hrot, (size_t)nb * sizeof(float2), cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemsetAsync(d_denom, 0, 64, st));
 
-    if ((size_t)npsl * 8 > 48 * 1024)
-        CK(cudaFuncSetAttribute(k_psl_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, npsl * 8));
-    k_psl_weights<<<3 * ne, 256, (size_t)npsl * 8, st>>>(P->d_w, ne, nr, M->dr, P->d_wpsl, P->d_scale,
-                                                         P->d_tag_r0, P->d_tag_l0);
-    CKL("k_psl_weights");
-    k_areas<<<1, 32, 0, st>>>(P->d_jaws, nb, M->z_phsp, B->sad, B->z_jaw_x, B->z_jaw_y, P->d_area, P->d_jaws_f);
-    CKL("k_areas");
     {
-        const int64_t n = (int64_t)nb * 2 * npsl;
-        k_incl<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P->d_area, nb, nr, M->dr, P->d_incl);
-        CKL("k_incl");
+        SetupArgs A;
+        A.w = P->d_w; A.n_e = ne; A.n_r = nr; A.dr = M->dr;
+        A.wpsl = P->d_wpsl; A.block_scale = P->d_scale; A.tag_r0 = P->d_tag_r0; A.tag_l0 = P->d_tag_l0;
+        A.G.jaws = P->d_jaws; A.G.n_beams = nb; A.G.z_phsp = M->z_phsp; A.G.sad = B->sad;
+        A.G.z_jaw_x = B->z_jaw_x; A.G.z_jaw_y = B->z_jaw_y;
+        A.area = P->d_area; A.jaws_f = P->d_jaws_f; A.incl = P->d_incl;
+        A.n_incl_blocks = (int)(((int64_t)nb * 2 * npsl + 255) / 256);
+        A.mc = d_mc; A.mmu = d_mmu; A.msa = d_msa; A.msb = d_msb; A.esa = d_esa; A.esb = d_esb;
+        A.nes = (int)nes; A.thr = P->d_mixthr; A.mix = P->d_mix; A.esig = P->d_esig;
+        const unsigned grid = (unsigned)(3 * ne + A.n_incl_blocks + (int)((nes + 255) / 256));
+        if ((size_t)npsl * 8 > 48 * 1024)
+            CK(cudaFuncSetAttribute(k_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, npsl * 8));
+        k_setup<<<grid, 256, (size_t)npsl * 8, st>>>(A);
+        CKL("k_setup");
     }
-    k_dir_tables<<<(unsigned)((nes + 127) / 128), 128, 0, st>>>(d_mc, d_mmu, d_msa, d_msb, d_esa, d_esb,
-                                                                (int)nes, P->d_mixthr, P->d_mix, P->d_esig);
-    CKL("k_dir_tables");
 
     if (!per_psr_hist) {
         const int nb3 = (int)nbse;
@@ -614,18 +709,13 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
             CK(cudaFuncSetAttribute(k_eq3_parts, cudaFuncAttributeMaxDynamicSharedMemorySize, npsl * 8));
         k_eq3_parts<<<nb3, 256, (size_t)npsl * 8, st>>>(P->d_wpsl, P->d_incl, nb, ne, npsl, d_parts);
         CKL("k_eq3_parts");
-        k_eq3_denom<<<1, 1, 0, st>>>(d_parts, nb3, d_denom);
-        CKL("k_eq3_denom");
         const unsigned g = (unsigned)((ncell + 255) / 256);
-        k_eq3_floor<<<g, 256, 0, st>>>(P->d_wpsl, P->d_incl, ne, npsl, ncell, n_hist, d_denom, P->d_count,
-                                       d_rem, d_fsum);
+        k_eq3_floor<<<g, 256, 0, st>>>(P->d_wpsl, P->d_incl, ne, npsl, ncell, n_hist, d_parts, nb3, d_denom,
+                                       P->d_count, d_rem, d_fsum);
         CKL("k_eq3_floor");
         // d_cstart / d_eidx serve as scratch here; they are recomputed below
-        k_scan<<<1, 1024, 0, st>>>(Positive{d_rem}, ncell, d_cstart);
-        CKL("k_scan");
-        k_pos_compact<<<g, 256, 0, st>>>(d_rem, d_cstart, ncell, (double *)d_eidx);
-        CKL("k_pos_compact");
-        CK(cudaMemsetAsync(d_rank, 0, (size_t)ncell * 4, st));
+        k_scan_pos<<<1, 1024, 0, st>>>(d_rem, ncell, d_cstart, (double *)d_eidx, d_rank);
+        CKL("k_scan_pos");
         k_eq3_rank_tiles<<<dim3(g, (unsigned)((ncell + 1023) / 1024)), 256, 0, st>>>((const double *)d_eidx, d_cstart,
                                                                                     ncell, d_rank);
         CKL("k_eq3_rank_tiles");
@@ -638,16 +728,12 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
                                                    P->d_count, d_dkb);
         CKL("k_psr_counts");
     }
-    k_scan<<<1, 1024, 0, st>>>(CountOf{P->d_count}, ncell, d_cstart);
-    CKL("k_scan");
-    k_scan<<<1, 1024, 0, st>>>(NonZero{P->d_count}, ncell, d_eidx);
-    CKL("k_scan");
+    k_scan_counts<<<1, 1024, 0, st>>>(P->d_count, ncell, d_cstart, d_eidx, P->d_start);
+    CKL("k_scan_counts");
     k_entries<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(P->d_count, d_cstart, d_eidx, ncell, P->per_psr, nb, ne,
                                                               nr, P->d_w, P->d_tag_r0, P->d_tag_l0, d_dkb, d_nk,
                                                               P->d_start, P->d_ent, P->d_escale);
     CKL("k_entries");
-    k_entries_end<<<1, 1, 0, st>>>(d_cstart, ncell, d_eidx, P->d_start);
-    CKL("k_entries_end");
     // the host needs the plan size and the denominator: one read, one synchronisation
     int64_t res[3] = {0, 0, 0};
     CK(cudaMemcpyAsync(&res[0], d_denom, 8, cudaMemcpyDeviceToHost, st));

@@ -27,11 +27,47 @@ __device__ __forceinline__ int64_t find_entry(const int64_t *__restrict__ start,
 
 __device__ __forceinline__ void lanemask_lt(unsigned &m) { asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m)); }
 
+// The same search for a warp whose lanes hold plan positions (valid lanes
+// first): when they are consecutive, one 32-way search finds the first lane's
+// entry and every lane walks forward from it (a warp spans a few entries);
+// otherwise each lane searches alone. All 32 lanes must call it.
+__device__ __forceinline__ int64_t find_entry_warp(const int64_t *__restrict__ start, int64_t n_ent, int64_t h,
+                                                   bool valid)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    if (vm == 0u) return 0;
+    const int nv = __popc(vm);
+    const int64_t h0 = __shfl_sync(0xffffffffu, h, 0);
+    const int64_t hl = __shfl_sync(0xffffffffu, h, nv - 1);
+    if ((vm & 1u) == 0u || hl - h0 != (int64_t)(nv - 1)) return valid ? find_entry(start, n_ent, h) : 0;
+    int64_t lo = 0, hi = n_ent - 1;            // start[lo] <= h0 < start[hi + 1]
+    while (hi - lo >= 32) {
+        const int64_t step = (hi - lo + 32) / 32;
+        const int64_t piv = lo + (int64_t)lane * step;
+        const bool le = piv <= hi && __ldg(start + piv) <= h0;
+        const unsigned b = __ballot_sync(0xffffffffu, le);
+        const int top = 31 - __clz(b);          // lane 0's pivot is lo, always <= h0
+        lo = lo + (int64_t)top * step;
+        const int64_t nh = lo + step - 1;
+        hi = nh < hi ? nh : hi;
+    }
+    {
+        const int64_t piv = lo + lane;
+        const bool le = piv <= hi && __ldg(start + piv) <= h0;
+        lo += 31 - __clz(__ballot_sync(0xffffffffu, le));
+    }
+    int64_t k = lo;
+    if (valid)
+        for (int it = 0; it < 32 && k + 1 < n_ent && __ldg(start + k + 1) <= h; ++it) ++k;
+    return k;
+}
+
 // One history: plan position h of history g; z_rel = phantom surface - z_phsp.
 __device__ __forceinline__ void sample_history(const SampleParams &P, uint32_t k0, uint32_t k1, uint64_t g,
-                                               int64_t h, float z_rel, SrcParticle &o)
+                                               int64_t h, float z_rel, SrcParticle &o, int64_t k = -1)
 {
-    const int64_t k = find_entry(P.start, P.n_ent, h);
+    if (k < 0) k = find_entry(P.start, P.n_ent, h);
     const EntryRec en = P.ent[k];
     const uint32_t glo = (uint32_t)g, ghi = (uint32_t)(g >> 32);
     const uint4 a = philox4x32_10(k0, k1, glo, ghi, 0u, 0u);

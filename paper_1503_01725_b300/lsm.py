@@ -231,15 +231,33 @@ class Tally(Handle):
     _destroy = "lsm_tally_destroy"
 
 
-def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None) -> PSL:
-    L = load_library()
-    keep = [_f64(getattr(model, k)) for k in ("w", "mix_c", "mix_mu", "mix_sa", "mix_sb", "e_sa", "e_sb")]
+_MODEL_KEYS = ("w", "mix_c", "mix_mu", "mix_sa", "mix_sb", "e_sa", "e_sb")
+_marshal_cache: dict = {}
+
+
+def _marshal(model, beams):
+    """ctypes views of a model and beam set. When every array is already
+    contiguous float64 the structs point at the caller's arrays and are
+    reused for the same objects (keyed by the identity of the objects and of
+    every array they hold, and by their scalar fields); otherwise they point
+    at fresh copies."""
+    arrays = [getattr(model, k) for k in _MODEL_KEYS] + [beams.jaws, getattr(beams, "gantry", None)]
+    key = (id(model), id(beams)) + tuple(id(a) for a in arrays) + (
+        model.n_e, model.n_r, model.dr, model.z_phsp, model.sigma_s, tuple(np.ravel(model.e_lo)),
+        tuple(np.ravel(model.de)), beams.sad, beams.z_jaw_y, beams.z_jaw_x, beams.n_beams,
+        tuple(getattr(beams, "iso", ())))
+    hit = _marshal_cache.get(key)
+    if hit is not None:
+        return hit[0], hit[1]
+    exact = all(a is None or (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous)
+                for a in arrays)
+    keep = [_f64(a) for a in arrays[:7]]
     ms = lsm_psr_model(n_e=model.n_e, n_r=model.n_r, dr=model.dr, z_phsp=model.z_phsp,
                        sigma_s=model.sigma_s, e_lo=(C.c_double * 3)(*model.e_lo),
                        de=(C.c_double * 3)(*model.de),
-                       **{k: a.ctypes.data_as(_dp) for k, a in
-                          zip(("w", "mix_c", "mix_mu", "mix_sa", "mix_sb", "e_sa", "e_sb"), keep)})
+                       **{k: a.ctypes.data_as(_dp) for k, a in zip(_MODEL_KEYS, keep)})
     jaws = _f64(beams.jaws)
+    keep.append(jaws)
     gantry = getattr(beams, "gantry", None)
     gp = None
     if gantry is not None:
@@ -250,6 +268,18 @@ def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None)
     bs = lsm_beams(sad=beams.sad, z_jaw_y=beams.z_jaw_y, z_jaw_x=beams.z_jaw_x,
                    n_beams=beams.n_beams, jaws=jaws.ctypes.data_as(_dp), gantry=gp,
                    iso=(C.c_double * 3)(*iso))
+    ms._keep, bs._keep = keep, (model, beams, arrays)
+    if exact:
+        if len(_marshal_cache) > 64:
+            _marshal_cache.clear()
+        _marshal_cache[key] = (ms, bs)
+    return ms, bs
+
+
+def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None) -> PSL:
+    L = load_library()
+    ms, bs = _marshal(model, beams)
+    keep = []
     pp = None
     if per_psr_hist is not None:
         ppa = np.ascontiguousarray(per_psr_hist, dtype=np.int64)
