@@ -152,6 +152,32 @@ lsm_status set_arg_error(const char *msg)
     return LSM_ERR_ARG;
 }
 
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t st)
+{
+    // keep up to 64 GiB of freed blocks in the pool of each device that allocates
+    static std::mutex m;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lk(m);
+        if (!done[dev]) {
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t thr = 64ull << 30;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+            done[dev] = true;
+        }
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
+void dev_free(void *p)
+{
+    if (p) cudaFreeAsync(p, 0);
+}
+
 lsm_status set_io_error(const char *what, const char *path, int err)
 {
     snprintf(g_err, sizeof(g_err), "%s %s: %s", what, path ? path : "(null)", err ? strerror(err) : "short transfer");
@@ -306,13 +332,13 @@ lsm_status lsm_tally_create(const lsm_phantom *ph, const lsm_tally_desc *d, lsm_
     cudaStream_t st = S(stream);
     cudaError_t e = cudaSuccess;
     do {
-        if ((e = cudaMalloc(&t->d_part, (size_t)ncell * 4 + 16)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&t->d_batch, (size_t)ncell * 8 + 16)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&t->d_s1, (size_t)ncell * 8 + 16)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&t->d_s2, (size_t)ncell * 8 + 16)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&t->d_stats, sizeof(RunStats))) != cudaSuccess) break;
+        if ((e = dev_malloc((void **)&t->d_part, (size_t)ncell * 4 + 16, st)) != cudaSuccess) break;
+        if ((e = dev_malloc((void **)&t->d_batch, (size_t)ncell * 8 + 16, st)) != cudaSuccess) break;
+        if ((e = dev_malloc((void **)&t->d_s1, (size_t)ncell * 8 + 16, st)) != cudaSuccess) break;
+        if ((e = dev_malloc((void **)&t->d_s2, (size_t)ncell * 8 + 16, st)) != cudaSuccess) break;
+        if ((e = dev_malloc((void **)&t->d_stats, sizeof(RunStats), st)) != cudaSuccess) break;
         if (d->mode == 1) {
-            if ((e = cudaMalloc(&t->d_idx, (size_t)nvox * 2)) != cudaSuccess) break;
+            if ((e = dev_malloc((void **)&t->d_idx, (size_t)nvox * 2, st)) != cudaSuccess) break;
             e = cudaMemcpyAsync(t->d_idx, d->idx3d, (size_t)nvox * 2,
                                 d->idx3d_mem == LSM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) break;
@@ -321,12 +347,12 @@ lsm_status lsm_tally_create(const lsm_phantom *ph, const lsm_tally_desc *d, lsm_
         if ((e = cudaMemsetAsync(t->d_batch, 0, (size_t)ncell * 8, st)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(t->d_s1, 0, (size_t)ncell * 8, st)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(t->d_s2, 0, (size_t)ncell * 8, st)) != cudaSuccess) break;
-        if ((e = cudaMemsetAsync(t->d_stats, 0, sizeof(RunStats), st)) != cudaSuccess) break;
-        e = cudaStreamSynchronize(st);
+        e = cudaMemsetAsync(t->d_stats, 0, sizeof(RunStats), st);
     } while (0);
     if (e != cudaSuccess) {
-        cudaFree(t->d_part); cudaFree(t->d_batch); cudaFree(t->d_s1); cudaFree(t->d_s2); cudaFree(t->d_stats);
-        cudaFree(t->d_idx);
+        cudaStreamSynchronize(st);
+        dev_free(t->d_part); dev_free(t->d_batch); dev_free(t->d_s1); dev_free(t->d_s2); dev_free(t->d_stats);
+        dev_free(t->d_idx);
         free(t);
         return set_cuda_error(e, "lsm_tally_create");
     }
@@ -342,16 +368,18 @@ lsm_status lsm_tally_create(const lsm_phantom *ph, const lsm_tally_desc *d, lsm_
     return LSM_OK;
 }
 
+// The tally's memory returns to the pool in the order of the legacy default
+// stream; its own graph stream is drained first.
 void lsm_tally_destroy(lsm_tally *t)
 {
     if (!t) return;
-    cudaFree(t->d_part); cudaFree(t->d_batch); cudaFree(t->d_s1); cudaFree(t->d_s2); cudaFree(t->d_stats);
-    if (t->d_idx) cudaFree(t->d_idx);
-    if (t->ws) cudaFree(t->ws);
+    if (t->gstream) cudaStreamSynchronize((cudaStream_t)t->gstream);
+    dev_free(t->d_part); dev_free(t->d_batch); dev_free(t->d_s1); dev_free(t->d_s2); dev_free(t->d_stats);
+    dev_free(t->d_idx);
+    dev_free(t->ws);
     if (t->gexec) cudaGraphExecDestroy((cudaGraphExec_t)t->gexec);
     timer_free(t->gtimers);
     if (t->gstream) {
-        cudaStreamSynchronize((cudaStream_t)t->gstream);
         cudaStreamDestroy((cudaStream_t)t->gstream);
         cudaEventDestroy((cudaEvent_t)t->gev[0]);
         cudaEventDestroy((cudaEvent_t)t->gev[1]);

@@ -166,6 +166,12 @@ bool timing_enabled();
 lsm_status set_cuda_error(cudaError_t e, const char *where);
 lsm_status set_arg_error(const char *msg);
 lsm_status set_io_error(const char *what, const char *path, int err);
+// Device memory from the device's stream-ordered pool (freed memory stays in
+// the pool for the next allocation instead of going back to the driver):
+// dev_malloc orders the allocation on `st`; dev_free returns it in the order
+// of the legacy default stream (work on other streams must be complete).
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p);
 int sm_count();
 }  // namespace lsm
 

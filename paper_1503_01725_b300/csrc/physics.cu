@@ -16,6 +16,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "handles.cuh"
 
 namespace lsm {
@@ -148,16 +150,60 @@ __global__ void k_check_phantom(const float *__restrict__ rho, const uint8_t *__
 
 }  // namespace
 
+// The phantom's memory returns to the pool in the order of the legacy
+// default stream.
 void free_phantom(lsm_phantom *P)
 {
     if (!P) return;
-    if (P->d_rho) cudaFree(P->d_rho);
-    if (P->d_mat) cudaFree(P->d_mat);
-    if (P->d_rhomat) cudaFree(P->d_rhomat);
-    if (P->d_xs) cudaFree(P->d_xs);
-    if (P->d_mumax) cudaFree(P->d_mumax);
+    dev_free(P->d_rho);
+    dev_free(P->d_mat);
+    dev_free(P->d_rhomat);
+    dev_free(P->d_xs);
+    dev_free(P->d_mumax);
     free(P);
 }
+
+namespace {
+// The cross-section and inverse Klein-Nishina tables depend on no phantom:
+// computed once per device and copied into each phantom.
+struct SharedTables {
+    float4 *xs = nullptr;        // [2][kGrid]
+    double *mutot = nullptr;     // [2][kGrid]
+    float *kn = nullptr;         // [kKnE][kKnU]
+};
+std::mutex g_tab_m;
+SharedTables g_tab[64];
+
+cudaError_t shared_tables(cudaStream_t st, SharedTables **out)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_tab_m);
+    SharedTables &T = g_tab[dev];
+    if (!T.xs) {
+        SharedTables n;
+        cudaError_t e = cudaMalloc(&n.xs, 2 * kGrid * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc(&n.mutot, 2 * kGrid * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&n.kn, kKnE * kKnU * 4);
+        if (e == cudaSuccess) {
+            k_tables<<<(2 * kGrid + 127) / 128, 128, 0, st>>>(n.xs, n.mutot);
+            count_launch();
+            k_kn_table<<<(kKnE * kKnU + 127) / 128, 128, 0, st>>>(n.kn);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFree(n.xs); cudaFree(n.mutot); cudaFree(n.kn);
+            return e;
+        }
+        T = n;
+    }
+    *out = &T;
+    return cudaSuccess;
+}
+}  // namespace
 
 lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStream_t st)
 {
@@ -184,19 +230,21 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     do {                                                                                \
         e = (call);                                                                     \
         if (e != cudaSuccess) {                                                         \
-            cudaFree(d_mutot); cudaFree(d_bits); free_phantom(P);                       \
+            cudaStreamSynchronize(st); dev_free(d_bits); free_phantom(P);              \
             return set_cuda_error(e, #call);                                            \
         }                                                                               \
     } while (0)
 #define CKL(name) do { count_launch(); CK(cudaGetLastError()); } while (0)
-    CK(cudaMalloc(&P->d_rho, n * 4));
-    CK(cudaMalloc(&P->d_mat, n));
-    CK(cudaMalloc(&P->d_rhomat, n * 4));
-    CK(cudaMalloc(&P->d_xs, 2 * kGrid * sizeof(float4)));
+    SharedTables *tab = nullptr;
+    CK(shared_tables(st, &tab));
+    d_mutot = tab->mutot;
+    CK(dev_malloc((void **)&P->d_rho, n * 4, st));
+    CK(dev_malloc((void **)&P->d_mat, n, st));
+    CK(dev_malloc((void **)&P->d_rhomat, n * 4, st));
+    CK(dev_malloc((void **)&P->d_xs, 2 * kGrid * sizeof(float4), st));
     // majorant followed by the inverse-KN table: staged into shared memory by one copy
-    CK(cudaMalloc(&P->d_mumax, kGrid * 4 + kKnE * kKnU * 4));
-    CK(cudaMalloc(&d_mutot, 2 * kGrid * 8));
-    CK(cudaMalloc(&d_bits, 16));
+    CK(dev_malloc((void **)&P->d_mumax, kGrid * 4 + kKnE * kKnU * 4, st));
+    CK(dev_malloc((void **)&d_bits, 16, st));
     CK(cudaMemcpyAsync(P->d_rho, D->rho, n * 4, kind, st));
     CK(cudaMemcpyAsync(P->d_mat, D->mat, n, kind, st));
     CK(cudaMemsetAsync(d_bits, 0, 16, st));
@@ -207,17 +255,14 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     CKL("k_rho_max");
     k_rhomat<<<g, 256, 0, st>>>(P->d_rho, P->d_mat, n, P->d_rhomat);
     CKL("k_rhomat");
-    k_tables<<<(2 * kGrid + 127) / 128, 128, 0, st>>>(P->d_xs, d_mutot);
-    CKL("k_tables");
+    CK(cudaMemcpyAsync(P->d_xs, tab->xs, 2 * kGrid * sizeof(float4), cudaMemcpyDeviceToDevice, st));
     k_majorant<<<(kGrid + 127) / 128, 128, 0, st>>>(d_mutot, d_bits, P->d_mumax);
     CKL("k_majorant");
-    k_kn_table<<<(kKnE * kKnU + 127) / 128, 128, 0, st>>>(P->d_mumax + kGrid);
-    CKL("k_kn_table");
+    CK(cudaMemcpyAsync(P->d_mumax + kGrid, tab->kn, kKnE * kKnU * 4, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(bits, d_bits, 12, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    cudaFree(d_mutot);
-    cudaFree(d_bits);
-    d_mutot = nullptr; d_bits = nullptr;
+    dev_free(d_bits);
+    d_bits = nullptr;
     if (bits[2]) {
         free_phantom(P);
         return set_arg_error("lsm_phantom_create: densities must be in [1e-4, 25] and materials in {0, 1}");

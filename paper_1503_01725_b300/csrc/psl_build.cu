@@ -398,9 +398,10 @@ __global__ void k_scan_pos(const double *__restrict__ rem, int64_t n, int64_t *_
 }
 
 // Plan prefix of the counts (cstart) and entry index of the non-empty cells
-// (eidx) in one pass of one CTA, and the plan end start[n_ent] = total.
+// (eidx) in one pass of one CTA, and the plan end start[n_ent] = total;
+// (n_ent, total) also go to res[0..1] for the host.
 __global__ void k_scan_counts(const int64_t *__restrict__ count, int64_t n, int64_t *__restrict__ cstart,
-                              int64_t *__restrict__ eidx, int64_t *__restrict__ start)
+                              int64_t *__restrict__ eidx, int64_t *__restrict__ start, int64_t *__restrict__ res)
 {
     const int T = blockDim.x;
     const int64_t seg = (n + T - 1) / T;
@@ -424,7 +425,7 @@ __global__ void k_scan_counts(const int64_t *__restrict__ count, int64_t n, int6
         }
         ws[lane] = x;
         wz[lane] = y;
-        if (lane == 31) { cstart[n] = x; eidx[n] = y; start[y] = x; }
+        if (lane == 31) { cstart[n] = x; eidx[n] = y; start[y] = x; res[0] = y; res[1] = x; }
     }
     __syncthreads();
     long long rs = is - s + (wid ? ws[wid - 1] : 0), rz = iz - z + (wid ? wz[wid - 1] : 0);
@@ -658,12 +659,12 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     const size_t n_in = nw + 4 * nm + 2 * nes + 4 * (size_t)nb + (size_t)npsr;
     static thread_local double *hbuf = nullptr;
     static thread_local size_t hcap = 0;
-    if (hcap < n_in + 16) {
+    if (hcap < n_in + 24) {
         if (hbuf) cudaFreeHost(hbuf);
         hbuf = nullptr;
         hcap = 0;
-        CK(cudaMallocHost((void **)&hbuf, (n_in + 16) * sizeof(double)));
-        hcap = n_in + 16;
+        CK(cudaMallocHost((void **)&hbuf, (n_in + 24) * sizeof(double)));
+        hcap = n_in + 24;
     }
     {
         double *h = hbuf;
@@ -728,19 +729,18 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
                                                    P->d_count, d_dkb);
         CKL("k_psr_counts");
     }
-    k_scan_counts<<<1, 1024, 0, st>>>(P->d_count, ncell, d_cstart, d_eidx, P->d_start);
+    k_scan_counts<<<1, 1024, 0, st>>>(P->d_count, ncell, d_cstart, d_eidx, P->d_start, (int64_t *)(base + o_res + 16));
     CKL("k_scan_counts");
     k_entries<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(P->d_count, d_cstart, d_eidx, ncell, P->per_psr, nb, ne,
                                                               nr, P->d_w, P->d_tag_r0, P->d_tag_l0, d_dkb, d_nk,
                                                               P->d_start, P->d_ent, P->d_escale);
     CKL("k_entries");
     // the host needs the plan size and the denominator: one read, one synchronisation
-    int64_t res[3] = {0, 0, 0};
-    CK(cudaMemcpyAsync(&res[0], d_denom, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&res[1], d_eidx + ncell, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&res[2], d_cstart + ncell, 8, cudaMemcpyDeviceToHost, st));
+    // (denominator, floor sum, n_ent, total) are contiguous: one copy into pinned memory
+    int64_t *res = (int64_t *)(hbuf + n_in + 16);
+    CK(cudaMemcpyAsync(res, base + o_res, 32, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    const int64_t n_ent = res[1], total = res[2];
+    const int64_t n_ent = res[2], total = res[3];
     if (n_ent < 1 || total < 1) {
         free_psl(P);
         return set_arg_error("lsm_build_psl: the sampling areas hold no PSL with non-zero weight");

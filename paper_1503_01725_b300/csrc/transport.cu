@@ -1079,18 +1079,18 @@ struct Workspace {
 };
 
 // Queues live in one allocation cached on the tally and reused by later runs.
-cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t)
+cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t, cudaStream_t st)
 {
     if (t->ws && t->ws_chunk >= chunk && t->ws_ecap >= ecap) {
         chunk = t->ws_chunk;
         ecap = t->ws_ecap;
     } else {
-        if (t->ws) cudaFree(t->ws);
+        if (t->ws) cudaFreeAsync(t->ws, st);
         t->ws = nullptr;
         size_t total = 1024;
         const uint32_t c2[3] = {chunk, 2 * chunk, ecap};
         for (int k = 0; k < 3; ++k) total += (size_t)c2[k] * 48 + 256;
-        cudaError_t e = cudaMalloc(&t->ws, total);
+        cudaError_t e = dev_malloc(&t->ws, total, st);
         if (e != cudaSuccess) return e;
         t->ws_chunk = chunk;
         t->ws_ecap = ecap;
@@ -1246,11 +1246,10 @@ lsm_status ensure_slots(lsm_tally *t, int slots, cudaStream_t st)
     if (slots <= t->part_slots) return LSM_OK;
     lsm_status rc = flush_partials(t, st);
     if (rc) return rc;
-    LSM_CUDA(cudaStreamSynchronize(st));
     float *np = nullptr;
-    LSM_CUDA(cudaMalloc(&np, (size_t)slots * t->ncell * 4 + 16));
+    LSM_CUDA(dev_malloc((void **)&np, (size_t)slots * t->ncell * 4 + 16, st));
     LSM_CUDA(cudaMemsetAsync(np, 0, (size_t)slots * t->ncell * 4, st));
-    cudaFree(t->d_part);
+    LSM_CUDA(cudaFreeAsync(t->d_part, st));
     t->d_part = np;
     t->part_slots = slots;
     return LSM_OK;
@@ -1286,7 +1285,7 @@ lsm_status transport_particles(const lsm_phantom *ph, const lsm_particles *in, i
     Workspace W = {};
     const uint32_t cap = (uint32_t)std::max<int64_t>(n, 1024);
     unsigned long long ovf = 0;
-    cudaError_t e = ws_alloc(W, cap, (uint32_t)std::min<int64_t>(8 * (int64_t)cap + (1 << 18), 1u << 28), t);
+    cudaError_t e = ws_alloc(W, cap, (uint32_t)std::min<int64_t>(8 * (int64_t)cap + (1 << 18), 1u << 28), t, st);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_transport workspace");
     TP T = make_tp(ph, t, o, W.key, W.cnt);
     do {
@@ -1336,7 +1335,7 @@ lsm_status pslfile_begin(const lsm_phantom *ph, lsm_tally *t, const lsm_run_opts
     if (rc) return rc;
     PslFileRun *R = new PslFileRun();
     const uint32_t c = (uint32_t)std::max<int64_t>(cap, 1024);
-    cudaError_t e = ws_alloc(R->W, c, (uint32_t)std::min<int64_t>(4 * (int64_t)c + (1 << 18), 0xF0000000ll), t);
+    cudaError_t e = ws_alloc(R->W, c, (uint32_t)std::min<int64_t>(4 * (int64_t)c + (1 << 18), 0xF0000000ll), t, st);
     if (e != cudaSuccess) { delete R; return set_cuda_error(e, "lsm_pslfile_run workspace"); }
     R->T = make_tp(ph, t, o, R->W.key, R->W.cnt);
     R->t = t;
@@ -1404,7 +1403,7 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     unsigned long long ovf = 0;
     rc = ensure_slots(t, bpi, st);
     if (rc) return rc;
-    cudaError_t e = ws_alloc(W, (uint32_t)chunk, (uint32_t)std::min<int64_t>(4 * chunk + (1 << 18), 0xF0000000ll), t);
+    cudaError_t e = ws_alloc(W, (uint32_t)chunk, (uint32_t)std::min<int64_t>(4 * chunk + (1 << 18), 0xF0000000ll), t, st);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_run workspace");
     TP T = make_tp(ph, t, o, W.key, W.cnt);
     SQ S;
@@ -1536,7 +1535,7 @@ lsm_status dose_impl(const lsm_tally *t, const lsm_phantom *ph, double scale, do
     double *dd = dose, *ds = sigma;
     void *tmp = nullptr;
     if (mem == LSM_MEM_HOST) {
-        LSM_CUDA(cudaMalloc(&tmp, (size_t)n * 16));
+        LSM_CUDA(dev_malloc(&tmp, (size_t)n * 16, st));
         dd = (double *)tmp;
         ds = sigma ? dd + n : nullptr;
     }
@@ -1549,7 +1548,7 @@ lsm_status dose_impl(const lsm_tally *t, const lsm_phantom *ph, double scale, do
         if (e == cudaSuccess && sigma) e = cudaMemcpyAsync(sigma, ds, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    if (tmp) cudaFree(tmp);
+    if (tmp) cudaFreeAsync(tmp, st);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_dose");
     return LSM_OK;
 }
@@ -1564,7 +1563,7 @@ lsm_status basis_impl(const lsm_tally *t, const lsm_psl *P, const lsm_phantom *p
     const int64_t ncell = (int64_t)nb * nr * npsr;
     char *tmp = nullptr;
     const size_t bytes = (size_t)npsr * nb * 8 + (size_t)nr * 8 + (mem == LSM_MEM_HOST ? (size_t)ncell * 8 : 0) + 64;
-    LSM_CUDA(cudaMalloc(&tmp, bytes));
+    LSM_CUDA(dev_malloc((void **)&tmp, bytes, st));
     double *cs = (double *)tmp, *rm = cs + (size_t)npsr * nb;
     double *dA = mem == LSM_MEM_HOST ? rm + nr : A;
     cudaError_t e = cudaMemsetAsync(tmp, 0, (size_t)npsr * nb * 8 + (size_t)nr * 8, st);
@@ -1586,7 +1585,7 @@ lsm_status basis_impl(const lsm_tally *t, const lsm_psl *P, const lsm_phantom *p
         e = cudaMemcpyAsync(A, dA, (size_t)ncell * 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    cudaFree(tmp);
+    cudaFreeAsync(tmp, st);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_basis_matrix");
     return LSM_OK;
 }

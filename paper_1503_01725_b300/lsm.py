@@ -351,8 +351,9 @@ def lsm_phantom_create(ph, stream=None) -> PhantomHandle:
     import torch
     rho = ph.rho if isinstance(ph.rho, torch.Tensor) else np.ascontiguousarray(ph.rho, dtype=np.float32)
     mat = ph.mat if isinstance(ph.mat, torch.Tensor) else np.ascontiguousarray(ph.mat, dtype=np.uint8)
-    dev = isinstance(rho, torch.Tensor)
-    ptr = (lambda a: a.data_ptr()) if dev else (lambda a: a.ctypes.data)
+    dev = isinstance(rho, torch.Tensor) and rho.is_cuda
+    # torch tensors (device, or host e.g. pinned) by data pointer, numpy arrays by their buffer
+    ptr = (lambda a: a.data_ptr()) if isinstance(rho, torch.Tensor) else (lambda a: a.ctypes.data)
     d = lsm_phantom_desc(nx=ph.nx, ny=ph.ny, nz=ph.nz, dx=ph.dx, dy=ph.dy, dz=ph.dz, x0=ph.x0, y0=ph.y0,
                          z0=ph.z0, rho=ptr(rho), mat=ptr(mat),
                          mem=LSM_MEM_DEVICE if dev else LSM_MEM_HOST)
@@ -496,9 +497,16 @@ def lsm_pslfile_run(path: str, field: PSL, ph: PhantomHandle, tally: Tally, seed
     return out
 
 
-def lsm_dose(t: Tally, ph: PhantomHandle, scale: float, device: bool = False, stream=None):
-    """Dose per source particle (MeV/g) and its batch sigma."""
+def lsm_dose(t: Tally, ph: PhantomHandle, scale: float, device: bool = False, stream=None, out=None):
+    """Dose per source particle (MeV/g) and its batch sigma. out: optional
+    (dose, sigma) host float64 torch tensors of nvox elements (e.g. pinned)
+    to receive them."""
     n = ph.desc.nvox
+    if out is not None:
+        d, s = out
+        _check(_lib.lsm_dose(t.ptr, ph.ptr, scale, d.data_ptr(), s.data_ptr(), LSM_MEM_HOST, _stream(stream)),
+               "lsm_dose")
+        return d, s
     if device:
         import torch
         d = torch.empty(n, dtype=torch.float64, device="cuda")
