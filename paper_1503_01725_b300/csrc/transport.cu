@@ -226,7 +226,7 @@ struct Part {
     Stream rng;
     uint32_t pb;
     int steps;
-    int vc;        // voxel whose (sign-coded) density is held in rc, -1 if none (photons: the current voxel)
+    int vc;        // electrons: voxel whose (sign-coded) density is held in rc, -1 if none
     float rc;
     int dv;        // electrons: voxel of the deposit not yet written, -1 if none
     float de;      // and its energy (consecutive steps in one voxel add up here)
@@ -292,7 +292,7 @@ template <int MODE>
 __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t, Acc &A, Part &p,
                             const Queue &eq, const Queue *pq, Pend &pe, bool &pend)
 {
-    int vox = p.vc >= 0 ? p.vc : voxel(T, p.x, p.y, p.z);
+    int vox = voxel(T, p.x, p.y, p.z);
     if (vox < 0) { A.esc += p.E; return false; }
     if (p.E < kCutG) { deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
     if (++p.steps > T.max_steps) { A.cap++; deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
@@ -310,7 +310,6 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     // depend on the density: compute it while the load is in flight
     p.rng.prefetch();
     if (vox < 0) { A.esc += p.E; return false; }
-    p.vc = vox;                    // the photon stays here until its next flight
     const int m = rm < 0.0f;
     const float rho = fabsf(rm);
     const float4 c = lerp4(xs + m * kGrid, ti, tf);
