@@ -562,10 +562,16 @@ def main():
                  "candidates": len(rep["trials"])}
         del psl_t
 
+    # the step is queued without host synchronisation: the plan build does
+    # not wait for its results (read when the dose scale is needed, by then
+    # long done) and the run does not wait for its overflow counter
+    # (checked from the run statistics after the timed steps)
+    step_opts = dataclasses.replace(opts, no_sync=True)
+
     def step(i):
-        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)
+        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True)
         lsm.lsm_tally_reset(tally)
-        lsm.lsm_run(psl, ph, tally, seed0 + i, opts)
+        lsm.lsm_run(psl, ph, tally, seed0 + i, step_opts)
         d, s = lsm.lsm_dose(tally, ph, psl.denom / n_plan, device=True)
         return psl, d, s
 
@@ -705,7 +711,8 @@ def main():
         "s_to_1pct": t1, "u_mean_rel_D50": u,
         "kernels_ms_per_step": {k: round(v, 4) for k, v in per_step.items() if v > 0},
         "work_per_step": {"photons": st["photons"], "electrons": st["electrons"], "flights": st["flights"],
-                          "real": st["real"], "esteps": st["esteps"], "rejected": st["rejected"]},
+                          "real": st["real"], "esteps": st["esteps"], "rejected": st["rejected"],
+                          "queue_overflows": st["overflows"]},
         "roofline": roofline,
         "batched": batched,
         "denoised": denoised,

@@ -131,6 +131,16 @@ typedef struct {
  */
 lsm_status lsm_build_psl(const lsm_psr_model *model, const lsm_beams *beams, int64_t n_hist,
                          const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream);
+/*
+ * lsm_build_psl_async -- lsm_build_psl without waiting for the build: returns
+ * once its kernels are queued on `stream`. The plan's results (entries, the
+ * Eq. 3 denominator) are read on the first call that needs them on the host
+ * (lsm_psl_info, lsm_psl_copy, lsm_sample, a synchronising lsm_run), which is
+ * also where an empty sampling area is reported (LSM_ERR_ARG). Argument
+ * errors are returned at once. Per-PSR plans are built synchronously.
+ */
+lsm_status lsm_build_psl_async(const lsm_psr_model *model, const lsm_beams *beams, int64_t n_hist,
+                               const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream);
 /* Releases the plan; its device memory returns to the pool in the order of
  * the legacy default stream. Work using the plan on non-blocking streams must
  * have completed. */
@@ -262,7 +272,10 @@ lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], l
  * replays it for later runs with the same plan, phantom, tally and options
  * (the seed may change). A graph captured while the event timers are on
  * holds their events, which are read after every replay; turning the timers
- * on or off re-captures it.
+ * on or off re-captures it. no_sync != 0: lsm_run returns once the run is
+ * queued, without waiting for it: queue overflows stay counted in the tally
+ * statistics (stats[9]) instead of being returned, and an empty plan from
+ * lsm_build_psl_async runs no history and is reported by lsm_psl_info.
  */
 typedef struct {
     int32_t electron_mode;
@@ -272,6 +285,7 @@ typedef struct {
     int32_t chunk;
     int32_t ctas_per_sm;
     int32_t use_graph;
+    int32_t no_sync;
 } lsm_run_opts;
 
 /*

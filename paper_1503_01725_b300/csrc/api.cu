@@ -12,8 +12,10 @@
 
 namespace lsm {
 
-lsm_status build_psl(const lsm_psr_model *, const lsm_beams *, int64_t, const int64_t *, lsm_psl **, cudaStream_t);
+lsm_status build_psl(const lsm_psr_model *, const lsm_beams *, int64_t, const int64_t *, lsm_psl **, cudaStream_t,
+                     bool);
 lsm_status free_psl(lsm_psl *);
+lsm_status resolve_psl(lsm_psl *);
 lsm_status create_phantom(const lsm_phantom_desc *, lsm_phantom **, cudaStream_t);
 void free_phantom(lsm_phantom *);
 lsm_status sample_public(const lsm_psl *, uint64_t, uint64_t, int64_t, double, const lsm_particles *, cudaStream_t);
@@ -239,7 +241,16 @@ lsm_status lsm_build_psl(const lsm_psr_model *model, const lsm_beams *beams, int
                          const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream)
 {
     const int tk = timer_begin(0, S(stream));
-    lsm_status rc = build_psl(model, beams, n_hist, per_psr_hist, out, S(stream));
+    lsm_status rc = build_psl(model, beams, n_hist, per_psr_hist, out, S(stream), false);
+    timer_end(tk, S(stream));
+    return rc;
+}
+
+lsm_status lsm_build_psl_async(const lsm_psr_model *model, const lsm_beams *beams, int64_t n_hist,
+                               const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream)
+{
+    const int tk = timer_begin(0, S(stream));
+    lsm_status rc = build_psl(model, beams, n_hist, per_psr_hist, out, S(stream), true);
     timer_end(tk, S(stream));
     return rc;
 }
@@ -249,6 +260,8 @@ void lsm_psl_destroy(lsm_psl *psl) { free_psl(psl); }
 lsm_status lsm_psl_info(const lsm_psl *P, int64_t info[4], double *denom)
 {
     if (!P || !info) return set_arg_error("lsm_psl_info: NULL argument");
+    lsm_status r = resolve_psl(const_cast<lsm_psl *>(P));
+    if (r) return r;
     info[0] = P->n_xy; info[1] = P->n_ent; info[2] = P->plan_size; info[3] = P->per_psr;
     if (denom) *denom = P->denom;
     return LSM_OK;
@@ -257,6 +270,8 @@ lsm_status lsm_psl_info(const lsm_psl *P, int64_t info[4], double *denom)
 lsm_status lsm_psl_copy(const lsm_psl *P, int which, void *dst)
 {
     if (!P || !dst) return set_arg_error("lsm_psl_copy: NULL argument");
+    lsm_status r = resolve_psl(const_cast<lsm_psl *>(P));
+    if (r) return r;
     const size_t npsl = (size_t)P->n_xy * P->n_xy;
     LSM_CUDA(cudaDeviceSynchronize());
     switch (which) {

@@ -23,7 +23,7 @@ struct SampleParams {
     const float4 *mix;         // [n_e][n_r][3] (mu, sigma_alpha, sigma_beta, 0)
     const float2 *esig;        // [n_e][n_r]
     const float *jaws_f;       // [n_beams][4] jaw limits in the jaw planes: ylo yhi xlo xhi
-    int64_t n_ent;
+    const int64_t *n_ent;      // device: entries of the plan (written by the build's last scan)
     int n_e, n_r;
     float pitch, z_phsp, sigma_s;
     float e_lo[3], de[3];
@@ -70,6 +70,11 @@ struct lsm_psl {
     double sad, z_jaw_y, z_jaw_x;
     int rotated;
     double gantry[16], iso[3];
+    // the build's results (denominator, floor sum, n_ent, total) land in
+    // h_res (pinned) when event `done` completes; `resolved` once read
+    void *done;
+    int64_t *h_res;
+    int resolved, empty;
     double denom;
     int64_t plan_size, n_ent, ncell;
     double *d_w, *d_wpsl, *d_scale, *d_jaws, *d_area, *d_escale;

@@ -13,6 +13,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "handles.cuh"
@@ -532,8 +533,56 @@ bool finite_nonneg(const double *a, size_t n)
 
 lsm_status free_psl(lsm_psl *p);
 
+namespace {
+// Pinned 32-byte result slots, one per plan: the build's final copy lands
+// there asynchronously. Taken from 1024-slot slabs that are never released.
+std::mutex g_slot_m;
+std::vector<int64_t *> g_free_slots;
+
+int64_t *take_slot()
+{
+    std::lock_guard<std::mutex> lk(g_slot_m);
+    if (g_free_slots.empty()) {
+        int64_t *slab = nullptr;
+        if (cudaMallocHost((void **)&slab, 1024 * 32) != cudaSuccess) return nullptr;
+        for (int i = 1023; i >= 0; --i) g_free_slots.push_back(slab + 4 * i);
+    }
+    int64_t *p = g_free_slots.back();
+    g_free_slots.pop_back();
+    return p;
+}
+
+void give_slot(int64_t *p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_slot_m);
+    g_free_slots.push_back(p);
+}
+}  // namespace
+
+// Wait for the build's results and check them (once).
+lsm_status resolve_psl(lsm_psl *P)
+{
+    if (P->resolved) {
+        if (P->empty) return set_arg_error("lsm_build_psl: the sampling areas hold no PSL with non-zero weight");
+        return LSM_OK;
+    }
+    LSM_CUDA(cudaEventSynchronize((cudaEvent_t)P->done));
+    const int64_t *res = P->h_res;
+    const int64_t n_ent = res[2], total = res[3];
+    P->resolved = 1;
+    if (n_ent < 1 || total < 1) {
+        P->empty = 1;
+        return set_arg_error("lsm_build_psl: the sampling areas hold no PSL with non-zero weight");
+    }
+    if (!P->per_psr) memcpy(&P->denom, &res[0], 8);
+    P->n_ent = n_ent;
+    P->plan_size = total;
+    return LSM_OK;
+}
+
 lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
-                     const int64_t *per_psr_hist, lsm_psl **out, cudaStream_t st)
+                     const int64_t *per_psr_hist, lsm_psl **out, cudaStream_t st, bool async)
 {
     if (!M || !B || !out) return set_arg_error("lsm_build_psl: NULL argument");
     *out = nullptr;
@@ -735,25 +784,30 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
                                                               nr, P->d_w, P->d_tag_r0, P->d_tag_l0, d_dkb, d_nk,
                                                               P->d_start, P->d_ent, P->d_escale);
     CKL("k_entries");
-    // the host needs the plan size and the denominator: one read, one synchronisation
-    // (denominator, floor sum, n_ent, total) are contiguous: one copy into pinned memory
-    int64_t *res = (int64_t *)(hbuf + n_in + 16);
-    CK(cudaMemcpyAsync(res, base + o_res, 32, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    const int64_t n_ent = res[2], total = res[3];
-    if (n_ent < 1 || total < 1) {
-        free_psl(P);
-        return set_arg_error("lsm_build_psl: the sampling areas hold no PSL with non-zero weight");
+    // (denominator, floor sum, n_ent, total) are contiguous: one copy into the
+    // plan's pinned slot, then the plan's completion event
+    P->h_res = take_slot();
+    if (!P->h_res) { free_psl(P); return set_arg_error("lsm_build_psl: out of pinned host memory"); }
+    {
+        cudaEvent_t ev = nullptr;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        P->done = ev;
     }
-    if (n_ent >= (int64_t)1 << 31) { free_psl(P); return set_arg_error("lsm_build_psl: plan too large"); }
-    memcpy(&P->denom, &res[0], 8);
-    if (per_psr_hist) P->denom = 0.0;
-    P->n_ent = n_ent;
-    P->plan_size = total;
+    CK(cudaMemcpyAsync(P->h_res, base + o_res, 32, cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord((cudaEvent_t)P->done, st));
+    P->denom = 0.0;
+    P->n_ent = -1;
+    // a whole-source plan distributes exactly n_hist histories unless its
+    // areas are empty (reported when the results are read)
+    P->plan_size = per_psr_hist ? -1 : n_hist;
+    if (!async || per_psr_hist) {
+        const lsm_status r = resolve_psl(P);
+        if (r) { free_psl(P); return r; }
+    }
 
     SampleParams &sp = P->sp;
     sp.start = P->d_start; sp.ent = P->d_ent; sp.mixthr = P->d_mixthr; sp.mix = P->d_mix; sp.esig = P->d_esig;
-    sp.jaws_f = P->d_jaws_f; sp.n_ent = n_ent; sp.n_e = ne; sp.n_r = nr;
+    sp.jaws_f = P->d_jaws_f; sp.n_ent = (const int64_t *)(base + o_res + 16); sp.n_e = ne; sp.n_r = nr;
     sp.pitch = (float)M->dr; sp.z_phsp = (float)M->z_phsp; sp.sigma_s = (float)M->sigma_s;
     for (int s = 0; s < 3; ++s) { sp.e_lo[s] = (float)M->e_lo[s]; sp.de[s] = (float)M->de[s]; }
     sp.zy_rel = (float)(B->z_jaw_y - M->z_phsp);
@@ -774,6 +828,12 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
 lsm_status free_psl(lsm_psl *P)
 {
     if (!P) return LSM_OK;
+    if (P->done) {
+        // the result copy must have landed before the slot is reused
+        cudaEventSynchronize((cudaEvent_t)P->done);
+        cudaEventDestroy((cudaEvent_t)P->done);
+    }
+    give_slot(P->h_res);
     if (P->arena) cudaFreeAsync(P->arena, 0);
     free(P);
     return LSM_OK;

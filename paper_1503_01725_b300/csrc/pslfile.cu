@@ -27,6 +27,7 @@
 
 namespace lsm {
 lsm_status sample_public(const lsm_psl *, uint64_t, uint64_t, int64_t, double, const lsm_particles *, cudaStream_t);
+lsm_status resolve_psl(lsm_psl *);
 struct PslFileRun;
 lsm_status pslfile_begin(const lsm_phantom *, lsm_tally *, const lsm_run_opts *, int64_t, int, uint64_t,
                          cudaStream_t, PslFileRun **);
@@ -142,6 +143,10 @@ extern "C" lsm_status lsm_pslfile_write(const lsm_psl *P, uint64_t seed, const c
 {
     if (!P || !path) return set_arg_error("lsm_pslfile_write: NULL argument");
     if (P->per_psr || P->n_beams != 1) return set_arg_error("lsm_pslfile_write: needs a whole-source single-beam plan");
+    {
+        const lsm_status r = resolve_psl(const_cast<lsm_psl *>(P));
+        if (r) return r;
+    }
     const int64_t M = P->plan_size;
     if (M < 1 || M > ((int64_t)1 << 28)) return set_arg_error("lsm_pslfile_write: 1 <= plan size <= 2^28");
     cudaStream_t st = (cudaStream_t)stream;

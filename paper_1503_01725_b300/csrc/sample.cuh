@@ -67,7 +67,7 @@ __device__ __forceinline__ int64_t find_entry_warp(const int64_t *__restrict__ s
 __device__ __forceinline__ void sample_history(const SampleParams &P, uint32_t k0, uint32_t k1, uint64_t g,
                                                int64_t h, float z_rel, SrcParticle &o, int64_t k = -1)
 {
-    if (k < 0) k = find_entry(P.start, P.n_ent, h);
+    if (k < 0) k = find_entry(P.start, __ldg(P.n_ent), h);
     const EntryRec en = P.ent[k];
     const uint32_t glo = (uint32_t)g, ghi = (uint32_t)(g >> 32);
     const uint4 a = philox4x32_10(k0, k1, glo, ghi, 0u, 0u);

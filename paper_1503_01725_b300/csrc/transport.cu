@@ -672,6 +672,10 @@ __device__ __forceinline__ bool enter_box(const SQ &S, const TP &T, const SrcPar
 template <int MODE>
 __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queue eq)
 {
+    // a plan whose sampling areas hold no weight has no entries: nothing to
+    // sample (the host reports it when it reads the plan's results)
+    const int64_t n_ent = __ldg(S.sp.n_ent);
+    if (n_ent < 1) return;
     const uint32_t k0 = S.key[0], k1 = S.key[1];
     const unsigned lane = lane_id();
     unsigned lt;
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
         const int64_t hh = S.h0 + i;
         slot = valid ? (uint32_t)(hh / S.plan) : 0u;
         const int64_t hpos = hh - (int64_t)slot * S.plan;
-        const int64_t ek = find_entry_warp(S.sp.start, S.sp.n_ent, hpos, valid);
+        const int64_t ek = find_entry_warp(S.sp.start, n_ent, hpos, valid);
         if (valid) {
             sample_history(S.sp, k0, k1, S.g0 + (uint64_t)i, hpos, S.z_rel, o, ek);
             src += o.E;
@@ -1254,10 +1258,16 @@ lsm_status ensure_slots(lsm_tally *t, int slots, cudaStream_t st)
     return LSM_OK;
 }
 
+lsm_status resolve_psl(lsm_psl *P);
+
 lsm_status sample_public(const lsm_psl *P, uint64_t seed, uint64_t g0, int64_t n, double z_surf,
                          const lsm_particles *out, cudaStream_t st)
 {
     if (!P || !out) return set_arg_error("lsm_sample: NULL argument");
+    {
+        const lsm_status r = resolve_psl(const_cast<lsm_psl *>(P));
+        if (r) return r;
+    }
     if (n < 0) return set_arg_error("lsm_sample: n < 0");
     if (n == 0) return LSM_OK;
     if (!out->x || !out->y || !out->z || !out->u || !out->v || !out->w || !out->E || !out->hist || !out->psr ||
@@ -1517,9 +1527,18 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         if (rc) return rc;
     }
     t->n_batches += o.n_batches;
-    if (rc == LSM_OK) rc = read_overflow(t, W, st, &ovf);
+    if (o.no_sync) {                        // overflows stay counted in the run statistics
+        if (replayed && t->gtimers) {       // a replay's timer events are read once complete
+            LSM_CUDA(cudaStreamSynchronize(st));
+            timer_replayed(t->gtimers);
+        }
+        return LSM_OK;
+    }
+    rc = read_overflow(t, W, st, &ovf);
     if (rc) return rc;
     if (replayed) timer_replayed(t->gtimers);
+    rc = resolve_psl(const_cast<lsm_psl *>(P));
+    if (rc) return rc;
     if (ovf) return LSM_ERR_OVERFLOW;
     return LSM_OK;
 }
@@ -1557,6 +1576,10 @@ lsm_status basis_impl(const lsm_tally *t, const lsm_psl *P, const lsm_phantom *p
 {
     if (!t || !P || !ph || !A) return set_arg_error("lsm_basis_matrix: NULL argument");
     if (t->mode != 1 || !P->per_psr) return set_arg_error("lsm_basis_matrix: needs a basis tally and a per-PSR plan");
+    {
+        const lsm_status r = resolve_psl(const_cast<lsm_psl *>(P));
+        if (r) return r;
+    }
     if (t->n_batches < 1) return set_arg_error("lsm_basis_matrix: no batch folded yet");
     const int npsr = t->n_psr, nb = t->n_beams, nr = t->n_rows;
     const int64_t ncell = (int64_t)nb * nr * npsr;

@@ -62,7 +62,7 @@ class lsm_run_opts(C.Structure):
     _fields_ = [("electron_mode", C.c_int32), ("n_batches", C.c_int32),
                 ("majorant_factor", C.c_double), ("f_e", C.c_double), ("s_geo", C.c_double),
                 ("max_steps", C.c_int32), ("chunk", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("no_sync", C.c_int32)]
 
 
 class lsm_nnls_opts(C.Structure):
@@ -94,6 +94,8 @@ class lsm_adam_opts(C.Structure):
 _EXPORTS = {
     "lsm_build_psl": (C.c_int, [C.POINTER(lsm_psr_model), C.POINTER(lsm_beams), C.c_int64,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.c_void_p]),
+    "lsm_build_psl_async": (C.c_int, [C.POINTER(lsm_psr_model), C.POINTER(lsm_beams), C.c_int64,
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.c_void_p]),
     "lsm_psl_destroy": (None, [C.c_void_p]),
     "lsm_psl_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), _dp]),
     "lsm_psl_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -220,7 +222,20 @@ class Handle:
 
 
 class PSL(Handle):
+    """A plan. `info` and `denom` are read from the library on first use (for
+    a plan from the asynchronous build that waits for the build only)."""
     _destroy = "lsm_psl_destroy"
+
+    @property
+    def info(self):
+        if getattr(self, "_info", None) is None:
+            self._info, self._denom = lsm_psl_info(self)
+        return self._info
+
+    @property
+    def denom(self):
+        self.info
+        return self._denom
 
 
 class PhantomHandle(Handle):
@@ -276,7 +291,9 @@ def _marshal(model, beams):
     return ms, bs
 
 
-def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None) -> PSL:
+def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None, async_: bool = False) -> PSL:
+    """Plan of `model` and `beams` (Sec. 2.1). async_: return once the build
+    is queued (lsm_build_psl_async); its results are read on first use."""
     L = load_library()
     ms, bs = _marshal(model, beams)
     keep = []
@@ -286,11 +303,10 @@ def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None)
         keep.append(ppa)
         pp = ppa.ctypes.data_as(C.POINTER(C.c_int64))
     out = C.c_void_p()
-    _check(L.lsm_build_psl(C.byref(ms), C.byref(bs), int(n_hist), pp, C.byref(out), _stream(stream)),
-           "lsm_build_psl")
+    fn = L.lsm_build_psl_async if async_ else L.lsm_build_psl
+    _check(fn(C.byref(ms), C.byref(bs), int(n_hist), pp, C.byref(out), _stream(stream)), "lsm_build_psl")
     h = PSL(out)
     h.model, h.beams = model, beams
-    h.info, h.denom = lsm_psl_info(h)
     return h
 
 
@@ -427,12 +443,13 @@ class RunOpts:
     chunk: int = 0          # 0: library default (2^23 histories per iteration)
     ctas_per_sm: int = 0    # 0: as many as fit
     use_graph: bool = False
+    no_sync: bool = False   # return once queued; overflows stay in the run statistics
 
     def struct(self) -> lsm_run_opts:
         return lsm_run_opts(electron_mode=self.electron_mode, n_batches=self.n_batches,
                             majorant_factor=self.majorant_factor, f_e=self.f_e, s_geo=self.s_geo,
                             max_steps=self.max_steps, chunk=self.chunk, ctas_per_sm=self.ctas_per_sm,
-                            use_graph=int(self.use_graph))
+                            use_graph=int(self.use_graph), no_sync=int(self.no_sync))
 
 
 def lsm_transport(ph: PhantomHandle, particles: dict, n: int, seed: int, tally: Tally,

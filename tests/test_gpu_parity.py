@@ -427,3 +427,42 @@ def test_commission_device_inputs_and_errors(L):
     np.testing.assert_allclose(x_h, np.linspace(0.5, 1.5, 8), atol=1e-9)
     with pytest.raises(L.LSMError):
         L.lsm_commission(np.zeros((5, 2000)), np.zeros(5))
+
+
+def test_async_build_and_unsynchronised_run_match_the_synchronous_ones(L):
+    import torch
+    wl = W.workload_full_10x10(200_000)
+    ph = L.lsm_phantom_create(wl.phantom)
+    out = []
+    for async_, no_sync in ((False, False), (True, True), (True, False)):
+        g = L.lsm_build_psl(wl.model, wl.beams, wl.n_hist // 4, async_=async_)
+        t = L.lsm_tally_create(ph)
+        rc = L.lsm_run(g, ph, t, 17, L.RunOpts(n_batches=4, no_sync=no_sync))
+        assert rc == L.LSM_OK
+        torch.cuda.synchronize()
+        s1, s2, nb = L.lsm_tally_read(t)
+        led, st = L.lsm_tally_ledger(t)
+        out.append((s1, nb, st, g.info, g.denom))
+    for s1, nb, st, info, denom in out[1:]:
+        assert nb == out[0][1] and info == out[0][3] and denom == out[0][4]
+        assert st["histories"] == out[0][2]["histories"] and st["photons"] == out[0][2]["photons"]
+        np.testing.assert_allclose(s1, out[0][0], rtol=1e-4, atol=1e-6 * out[0][0].max())
+
+
+def test_async_build_reports_an_empty_plan_when_read(L):
+    import torch
+    wl = W.workload_full_10x10(10_000)
+    far = W.beams(W.square_field(1.0, cx=60.0, cy=60.0))    # outside every PSL's sampling reach
+    with pytest.raises(L.LSMError, match="non-zero weight"):
+        L.lsm_build_psl(wl.model, far, 1000)
+    g = L.lsm_build_psl(wl.model, far, 1000, async_=True)    # queued; nothing checked yet
+    ph = L.lsm_phantom_create(wl.phantom)
+    t = L.lsm_tally_create(ph)
+    assert L.lsm_run(g, ph, t, 1, L.RunOpts(n_batches=2, no_sync=True)) == L.LSM_OK
+    torch.cuda.synchronize()
+    led, st = L.lsm_tally_ledger(t)
+    assert st["histories"] == 0 and led["deposited"] == 0.0
+    with pytest.raises(L.LSMError, match="non-zero weight"):
+        L.lsm_psl_info(g)
+    with pytest.raises(L.LSMError, match="non-zero weight"):
+        L.lsm_run(g, ph, t, 1, L.RunOpts(n_batches=2))
