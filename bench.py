@@ -367,11 +367,12 @@ def multibeam_block(lsm, W, opts, n_hist: int = 10_000_000, n_batches: int = 16,
         ph = lsm.lsm_phantom_create(wl.phantom)
         tally = lsm.lsm_tally_create(ph)
         n_plan = n_hist // n_batches
-        o = lsm.RunOpts(electron_mode=1, n_batches=n_batches, chunk=opts.chunk, ctas_per_sm=opts.ctas_per_sm)
+        o = lsm.RunOpts(electron_mode=1, n_batches=n_batches, chunk=opts.chunk, ctas_per_sm=opts.ctas_per_sm,
+                        no_sync=True)
 
         def step(seed):
             lsm.lsm_tally_reset(tally)
-            psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)
+            psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True)
             lsm.lsm_run(psl, ph, tally, seed, o)
             return psl
 
@@ -618,7 +619,7 @@ def main():
     # the phantom from pinned host arrays, builds the plan from the host model,
     # runs, and reads the dose and its sigma back into pinned host memory
     e2e_s, h2d, d2h = [], 0, 0
-    e2e_opts = dataclasses.replace(opts, use_graph=False)     # one-shot runs: nothing to replay
+    e2e_opts = dataclasses.replace(opts, use_graph=False, no_sync=True)   # one-shot runs: nothing to replay
     host_ph = W.Phantom(**{**wl.phantom.__dict__, "rho": torch.from_numpy(wl.phantom.rho).pin_memory(),
                            "mat": torch.from_numpy(wl.phantom.mat).pin_memory()})
     out_d = torch.empty(wl.phantom.nvox, dtype=torch.float64).pin_memory()
@@ -628,7 +629,7 @@ def main():
         t0 = time.perf_counter()
         phh = lsm.lsm_phantom_create(host_ph)                  # host rho/mat -> device
         phh.desc = wl.phantom
-        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)   # host model arrays -> device
+        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True)   # host model arrays -> device
         tt = lsm.lsm_tally_create(phh)
         lsm.lsm_run(psl, phh, tt, 5000 + i, e2e_opts)
         dose, sig = lsm.lsm_dose(tt, phh, psl.denom / n_plan, out=(out_d, out_s))  # device -> host
