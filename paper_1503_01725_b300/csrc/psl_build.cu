@@ -246,51 +246,93 @@ __global__ void k_eq3_floor(const double *__restrict__ wpsl, const uint8_t *__re
     }
 }
 
-// Largest remainders: the `left` cells of highest remainder (ties to the
-// lower loop index) get one more particle. Zero remainders always rank after
-// every positive one, in index order, so only positive remainders are ranked
-// against each other; a zero cell's rank is n_pos + (zero cells before it).
-// (the positions come from k_scan_pos below, which also compacts the
-// positive remainders and clears the rank counters)
-
-// rank[p] += #{q : posrem[q] > posrem[p], or equal with q < p} over one tile
-// of 256 candidates p and 1024 competitors q; the grid covers all tile pairs.
-// Remainders are finite and >= 0, so they order exactly as their IEEE bit
-// patterns read as unsigned integers: the comparisons run on the integer
-// pipes instead of B300's narrow FP64 pipe.
-__global__ void k_eq3_rank_tiles(const double *__restrict__ posrem, const int64_t *__restrict__ pos_idx,
-                                 int64_t ncell, int *__restrict__ rank)
+// Largest remainders: the `left` cells of highest remainder, ties to the
+// lower loop index, get one more particle. Remainders are finite and >= 0, so
+// they order exactly as their IEEE bit patterns read as unsigned integers. One
+// CTA finds the left-th largest key by an 8-pass most-significant-digit radix
+// select (256-bin histograms of the keys that match the digits chosen so far),
+// then adds one to every cell with a larger key and to the first `need` cells,
+// in loop order, whose key equals it.
+__global__ void __launch_bounds__(1024) k_eq3_select(const double *__restrict__ rem, int64_t n, int64_t n_hist,
+                                                     const unsigned long long *__restrict__ floor_sum,
+                                                     const double *__restrict__ denom, int64_t *__restrict__ count)
 {
-    __shared__ unsigned long long tile[1024];
-    const int64_t n_pos = pos_idx[ncell];
-    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x, q0 = (int64_t)blockIdx.y * 1024;
-    if (p0 >= n_pos || q0 >= n_pos) return;
-    const unsigned long long *bits = reinterpret_cast<const unsigned long long *>(posrem);
-    for (int t = threadIdx.x; t < 1024; t += blockDim.x) tile[t] = (q0 + t < n_pos) ? bits[q0 + t] : 0ull;
-    __syncthreads();
-    const int64_t p = p0 + threadIdx.x;
-    if (p >= n_pos) return;
-    const unsigned long long rp = bits[p];
-    const int lim = (int)((n_pos - q0) < 1024 ? (n_pos - q0) : 1024);
-    const int tie_end = (p > q0) ? (int)((p - q0) < lim ? (p - q0) : lim) : 0;   // q < p inside this tile
-    int c = 0;
-    for (int t = 0; t < lim; ++t) c += tile[t] > rp;
-    for (int t = 0; t < tie_end; ++t) c += tile[t] == rp;
-    if (c) atomicAdd(rank + p, c);
-}
-
-__global__ void k_eq3_apply(const double *__restrict__ rem, const int64_t *__restrict__ pos_idx,
-                            const int *__restrict__ rank, int64_t ncell, int64_t n_hist,
-                            const unsigned long long *__restrict__ floor_sum, const double *__restrict__ denom,
-                            int64_t *__restrict__ count)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncell) return;
-    const int64_t n_pos = pos_idx[ncell], pi = pos_idx[i];
-    const int64_t r = rem[i] > 0.0 ? (int64_t)rank[pi] : n_pos + (i - pi);
     // an empty sampling area (denominator 0) distributes nothing
-    const int64_t left = (*denom > 0.0 ? n_hist : 0) - (int64_t)(*floor_sum);
-    if (r < left) count[i] += 1;
+    const long long left = (*denom > 0.0 ? n_hist : 0) - (long long)(*floor_sum);
+    if (left <= 0) return;
+    const unsigned long long *key = reinterpret_cast<const unsigned long long *>(rem);
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_pre;
+    __shared__ long long s_k;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) { s_pre = 0ull; s_k = left; }
+    unsigned long long mask = 0ull;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        if (tid < 256) hist[tid] = 0u;
+        __syncthreads();
+        const unsigned long long pre = s_pre;
+        for (int64_t i = tid; i < n; i += blockDim.x) {
+            const unsigned long long k = key[i];
+            if ((k & mask) == pre) atomicAdd(&hist[(unsigned)(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (wid == 0) {
+            // lane l holds bins [8 l, 8 l + 8); suffix sums from the top bin down
+            unsigned c[8], loc = 0;
+            for (int j = 0; j < 8; ++j) { c[j] = hist[8 * lane + j]; loc += c[j]; }
+            unsigned suf = loc;                      // inclusive suffix over lanes >= lane
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_down_sync(0xffffffffu, suf, o);
+                if (lane + o < 32) suf += v;
+            }
+            const long long k = s_k;
+            long long above = (long long)(suf - loc); // keys in bins above this lane's
+            int found = -1;
+            long long rest = 0;
+            for (int j = 7; j >= 0; --j) {
+                if (found < 0 && above < k && above + (long long)c[j] >= k) { found = 8 * lane + j; rest = k - above; }
+                above += c[j];
+            }
+            const unsigned hit = __ballot_sync(0xffffffffu, found >= 0);
+            const int src = __ffs(hit) - 1;
+            const int bin = __shfl_sync(0xffffffffu, found, src);
+            const long long kk = __shfl_sync(0xffffffffu, rest, src);
+            if (lane == 0) { s_pre = pre | ((unsigned long long)bin << shift); s_k = kk; }
+        }
+        mask |= 255ull << shift;
+        __syncthreads();
+    }
+    const unsigned long long v = s_pre;             // the left-th largest key
+    const long long need = s_k;                      // cells with key == v that get one more
+    // scan of the (key == v) flags in loop order over per-thread segments
+    const int T = blockDim.x;
+    const int64_t seg = (n + T - 1) / T;
+    const int64_t a = (int64_t)tid * seg, bnd = a + seg < n ? a + seg : n;
+    long long s = 0;
+    for (int64_t i = a; i < bnd; ++i) s += key[i] == v ? 1 : 0;
+    __shared__ long long wsum[32];
+    long long inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = lane < (T >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    long long run = inc - s + (wid ? wsum[wid - 1] : 0);
+    for (int64_t i = a; i < bnd; ++i) {
+        const unsigned long long k = key[i];
+        if (k > v) count[i] += 1;
+        else if (k == v) { if (run < need) count[i] += 1; ++run; }
+    }
 }
 
 // ------------------------------------------------- per-PSR basis-run plans --
@@ -360,43 +402,6 @@ __global__ void k_psr_counts(const double *__restrict__ w, const double *__restr
 }
 
 // ------------------------------------------------------ scans and entries --
-
-// Positive remainders: exclusive positions pos_idx (pos_idx[n] = count), the
-// remainders compacted in index order, and rank[] cleared -- one CTA.
-__global__ void k_scan_pos(const double *__restrict__ rem, int64_t n, int64_t *__restrict__ pos_idx,
-                           double *__restrict__ posrem, int *__restrict__ rank)
-{
-    const int T = blockDim.x;
-    const int64_t seg = (n + T - 1) / T;
-    const int64_t a = (int64_t)threadIdx.x * seg, bnd = a + seg < n ? a + seg : n;
-    long long s = 0;
-    for (int64_t i = a; i < bnd; ++i) { s += rem[i] > 0.0 ? 1 : 0; rank[i] = 0; }
-    __shared__ long long wsum[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    long long incl = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        long long w = lane < (T >> 5) ? wsum[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long v = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += v;
-        }
-        wsum[lane] = w;
-        if (lane == 31) pos_idx[n] = w;
-    }
-    __syncthreads();
-    long long run = incl - s + (wid ? wsum[wid - 1] : 0);
-    for (int64_t i = a; i < bnd; ++i) {
-        pos_idx[i] = run;
-        const double r = rem[i];
-        if (r > 0.0) posrem[run++] = r;
-    }
-}
 
 // Plan prefix of the counts (cstart) and entry index of the non-empty cells
 // (eidx) in one pass of one CTA, and the plan end start[n_ent] = total;
@@ -661,7 +666,7 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     const size_t o_esc = take((size_t)ncell * 8);
     const size_t o_rem = take((size_t)ncell * 8), o_cst = take((size_t)(ncell + 1) * 8);
     const size_t o_eidx = take((size_t)(ncell + 1) * 8), o_parts = take(nbse * 8);
-    const size_t o_res = take(64), o_dkb = take((size_t)npsr * nb * 8), o_rank = take((size_t)ncell * 4);
+    const size_t o_res = take(64), o_dkb = take((size_t)npsr * nb * 8);
     const size_t o_rot = take((size_t)nb * sizeof(float2));
     char *base = nullptr;
     {
@@ -687,7 +692,6 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     double *d_denom = (double *)(base + o_res);
     unsigned long long *d_fsum = (unsigned long long *)(base + o_res + 8);
     double *d_dkb = (double *)(base + o_dkb);
-    int *d_rank = (int *)(base + o_rank);
 
 #define CK(call)                                                 \
     do {                                                         \
@@ -763,14 +767,8 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
         k_eq3_floor<<<g, 256, 0, st>>>(P->d_wpsl, P->d_incl, ne, npsl, ncell, n_hist, d_parts, nb3, d_denom,
                                        P->d_count, d_rem, d_fsum);
         CKL("k_eq3_floor");
-        // d_cstart / d_eidx serve as scratch here; they are recomputed below
-        k_scan_pos<<<1, 1024, 0, st>>>(d_rem, ncell, d_cstart, (double *)d_eidx, d_rank);
-        CKL("k_scan_pos");
-        k_eq3_rank_tiles<<<dim3(g, (unsigned)((ncell + 1023) / 1024)), 256, 0, st>>>((const double *)d_eidx, d_cstart,
-                                                                                    ncell, d_rank);
-        CKL("k_eq3_rank_tiles");
-        k_eq3_apply<<<g, 256, 0, st>>>(d_rem, d_cstart, d_rank, ncell, n_hist, d_fsum, d_denom, P->d_count);
-        CKL("k_eq3_apply");
+        k_eq3_select<<<1, 1024, 0, st>>>(d_rem, ncell, n_hist, d_fsum, d_denom, P->d_count);
+        CKL("k_eq3_select");
     } else {
         const size_t smem = (size_t)npsl * 24;
         if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_psr_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
