@@ -213,6 +213,9 @@ typedef struct {
 } lsm_phantom_desc;
 
 lsm_status lsm_phantom_create(const lsm_phantom_desc *desc, lsm_phantom **out, lsm_stream stream);
+/* Releases the phantom; its device memory returns to the device's memory
+ * pool in the order of the legacy default stream (no device-wide wait). Work
+ * using it on non-blocking streams must have completed. */
 void lsm_phantom_destroy(lsm_phantom *ph);
 /* Copy the interaction tables to host (synchronises): out float
  * [2 materials][1024][4] = (mu_compton, mu_photo, mu_pair in cm^2/g, S_col in
@@ -240,6 +243,10 @@ typedef struct {
 
 lsm_status lsm_tally_create(const lsm_phantom *ph, const lsm_tally_desc *desc, lsm_tally **out,
                             lsm_stream stream);
+/* Releases the tally (and its transport workspace) to the device's memory
+ * pool in the order of the legacy default stream; its own graph stream is
+ * drained first. Work using it on other non-blocking streams must have
+ * completed. */
 void lsm_tally_destroy(lsm_tally *t);
 /* Zero every sum, counter and the energy ledger. */
 lsm_status lsm_tally_reset(lsm_tally *t, lsm_stream stream);
