@@ -466,3 +466,29 @@ def test_async_build_reports_an_empty_plan_when_read(L):
         L.lsm_psl_info(g)
     with pytest.raises(L.LSMError, match="non-zero weight"):
         L.lsm_run(g, ph, t, 1, L.RunOpts(n_batches=2))
+
+
+def test_repeated_create_run_destroy_reuses_pooled_memory(L):
+    """Phantoms, plans, tallies and workspaces come from the stream-ordered
+    pool: a request loop neither grows device memory nor changes results."""
+    import torch
+    wl = W.workload_full_10x10(100_000)
+    ref = None
+    free0 = None
+    for i in range(8):
+        ph = L.lsm_phantom_create(wl.phantom)
+        g = L.lsm_build_psl(wl.model, wl.beams, wl.n_hist // 2, async_=(i % 2 == 1))
+        t = L.lsm_tally_create(ph)
+        L.lsm_run(g, ph, t, 5, L.RunOpts(n_batches=2, chunk=1 << 20, no_sync=(i % 2 == 1)))
+        d, _ = L.lsm_dose(t, ph, g.denom / (wl.n_hist // 2))
+        if ref is None:
+            ref = d
+        else:
+            np.testing.assert_allclose(d, ref, rtol=1e-4, atol=1e-6 * ref.max())
+        del t, g, ph
+        torch.cuda.synchronize()
+        free = torch.cuda.mem_get_info()[0]
+        if i == 2:
+            free0 = free
+        elif i > 2:
+            assert free >= free0 - (64 << 20), (i, free0, free)
