@@ -256,6 +256,13 @@ lsm_status lsm_tally_end_batch(lsm_tally *t, lsm_stream stream);
  * batches. Synchronises when mem is HOST. */
 lsm_status lsm_tally_read(lsm_tally *t, double *s1, double *s2, lsm_mem mem, int32_t *n_batches,
                           lsm_stream stream);
+/* lsm_tally_load -- restore a checkpoint: S1, S2 (double [cells] in `mem`),
+ * the folded batch count and, optionally, the ledger and statistics as
+ * lsm_tally_ledger returns them (NULL: zero). The partial slices and the open
+ * batch are cleared. Stream-ordered (host arrays are read before it returns).
+ * Errors: LSM_ERR_ARG for a NULL tally or S1/S2, or n_batches < 0. */
+lsm_status lsm_tally_load(lsm_tally *t, const double *s1, const double *s2, int32_t n_batches,
+                          const double ledger[4], const int64_t stats[10], lsm_mem mem, lsm_stream stream);
 /* ledger (MeV): source, rejected, escaped (incl. missed), deposited.
  * stats: histories, accepted photons, accepted electrons, rejected, missed,
  * Woodcock flights, real photon interactions, electron steps, step-cap hits,
@@ -283,6 +290,12 @@ lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], l
  * queued, without waiting for it: queue overflows stay counted in the tally
  * statistics (stats[9]) instead of being returned, and an empty plan from
  * lsm_build_psl_async runs no history and is reported by lsm_psl_info.
+ * first_batch: index of the run's first batch; pass b of the run uses the
+ * histories of batch first_batch + b, so a run of B batches equals runs of
+ * B1 and B - B1 batches (the second with first_batch = B1) with the tally
+ * saved and restored in between (lsm_tally_read / lsm_tally_ledger, then
+ * lsm_tally_load): the checkpoint of a dose calculation is its tally sums,
+ * its statistics and the next batch index.
  */
 typedef struct {
     int32_t electron_mode;
@@ -293,6 +306,7 @@ typedef struct {
     int32_t ctas_per_sm;
     int32_t use_graph;
     int32_t no_sync;
+    int64_t first_batch;
 } lsm_run_opts;
 
 /*

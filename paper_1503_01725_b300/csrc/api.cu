@@ -435,6 +435,28 @@ lsm_status lsm_tally_read(lsm_tally *t, double *s1, double *s2, lsm_mem mem, int
     return LSM_OK;
 }
 
+lsm_status lsm_tally_load(lsm_tally *t, const double *s1, const double *s2, int32_t n_batches,
+                          const double ledger[4], const int64_t stats[10], lsm_mem mem, lsm_stream stream)
+{
+    if (!t || !s1 || !s2) return set_arg_error("lsm_tally_load: NULL argument");
+    if (n_batches < 0) return set_arg_error("lsm_tally_load: n_batches < 0");
+    cudaStream_t st = S(stream);
+    const cudaMemcpyKind k = mem == LSM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    LSM_CUDA(cudaMemcpyAsync(t->d_s1, s1, (size_t)t->ncell * 8, k, st));
+    LSM_CUDA(cudaMemcpyAsync(t->d_s2, s2, (size_t)t->ncell * 8, k, st));
+    LSM_CUDA(cudaMemsetAsync(t->d_part, 0, (size_t)t->part_slots * t->ncell * 4, st));
+    LSM_CUDA(cudaMemsetAsync(t->d_batch, 0, (size_t)t->ncell * 8, st));
+    RunStats h;
+    memset(&h, 0, sizeof(h));
+    if (ledger) for (int i = 0; i < 4; ++i) h.ledger[i] = ledger[i];
+    if (stats) for (int i = 0; i < 10; ++i) h.c[i] = (unsigned long long)stats[i];
+    LSM_CUDA(cudaMemcpyAsync(t->d_stats, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    // the host arrays (and the statistics staged above) are read before returning
+    LSM_CUDA(cudaStreamSynchronize(st));
+    t->n_batches = n_batches;
+    return LSM_OK;
+}
+
 lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], lsm_stream stream)
 {
     if (!t) return set_arg_error("lsm_tally_ledger: NULL tally");

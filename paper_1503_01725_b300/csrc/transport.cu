@@ -1149,6 +1149,7 @@ lsm_status check_opts(lsm_run_opts &o)
     if (o.chunk <= 0) o.chunk = 1 << 23;
     if (o.chunk > (1 << 24)) return set_arg_error("chunk must be <= 2^24");
     if (o.n_batches < 1) o.n_batches = 1;
+    if (o.first_batch < 0) return set_arg_error("first_batch must be >= 0");
     return LSM_OK;
 }
 
@@ -1445,13 +1446,13 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         if (multi) {
             for (int b0 = 0; b0 < o.n_batches && r == LSM_OK; b0 += bpi) {
                 const int k = std::min(bpi, o.n_batches - b0);
-                r = iteration((uint64_t)b0 * (uint64_t)plan, 0, (int64_t)k * plan);
+                r = iteration((uint64_t)(o.first_batch + b0) * (uint64_t)plan, 0, (int64_t)k * plan);
                 if (r == LSM_OK) r = fold_slots(t, k, st);
             }
         } else {
             for (int b = 0; b < o.n_batches && r == LSM_OK; ++b) {
                 for (int64_t h0 = 0; h0 < plan && r == LSM_OK; h0 += chunk) {
-                    r = iteration((uint64_t)b * (uint64_t)plan + (uint64_t)h0, h0,
+                    r = iteration((uint64_t)(o.first_batch + b) * (uint64_t)plan + (uint64_t)h0, h0,
                                   std::min<int64_t>(chunk, plan - h0));
                     if (r == LSM_OK) r = flush_partials(t, st);
                 }

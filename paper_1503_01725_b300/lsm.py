@@ -62,7 +62,7 @@ class lsm_run_opts(C.Structure):
     _fields_ = [("electron_mode", C.c_int32), ("n_batches", C.c_int32),
                 ("majorant_factor", C.c_double), ("f_e", C.c_double), ("s_geo", C.c_double),
                 ("max_steps", C.c_int32), ("chunk", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("use_graph", C.c_int32), ("no_sync", C.c_int32)]
+                ("use_graph", C.c_int32), ("no_sync", C.c_int32), ("first_batch", C.c_int64)]
 
 
 class lsm_nnls_opts(C.Structure):
@@ -112,6 +112,8 @@ _EXPORTS = {
     "lsm_tally_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                  C.POINTER(C.c_int32), C.c_void_p]),
     "lsm_tally_ledger": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.c_void_p]),
+    "lsm_tally_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, _dp, C.POINTER(C.c_int64), C.c_int,
+                                 C.c_void_p]),
     "lsm_transport": (C.c_int, [C.c_void_p, C.POINTER(lsm_particles), C.c_int64, C.c_uint64,
                                 C.c_void_p, C.POINTER(lsm_run_opts), C.c_void_p]),
     "lsm_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(lsm_run_opts),
@@ -422,6 +424,24 @@ def lsm_tally_read(t: Tally, stream=None):
     return s1, s2, nb.value
 
 
+def lsm_tally_load(t: Tally, s1, s2, n_batches: int, ledger=None, stats=None, stream=None):
+    """Restore a checkpoint (S1, S2, folded batches, optional ledger and
+    statistics dicts as lsm_tally_ledger returns them)."""
+    a1, a2 = _f64(s1), _f64(s2)
+    led = None
+    st = None
+    if ledger is not None:
+        led = np.array([ledger[k] for k in ("source", "rejected", "escaped", "deposited")], dtype=np.float64)
+    if stats is not None:
+        keys = ["histories", "photons", "electrons", "rejected", "missed", "flights", "real", "esteps",
+                "cap_hits", "overflows"]
+        st = np.array([stats[k] for k in keys], dtype=np.int64)
+    _check(_lib.lsm_tally_load(t.ptr, a1.ctypes.data, a2.ctypes.data, int(n_batches),
+                               led.ctypes.data_as(_dp) if led is not None else None,
+                               st.ctypes.data_as(C.POINTER(C.c_int64)) if st is not None else None,
+                               LSM_MEM_HOST, _stream(stream)), "lsm_tally_load")
+
+
 def lsm_tally_ledger(t: Tally, stream=None):
     led = np.zeros(4)
     st = np.zeros(10, dtype=np.int64)
@@ -444,12 +464,14 @@ class RunOpts:
     ctas_per_sm: int = 0    # 0: as many as fit
     use_graph: bool = False
     no_sync: bool = False   # return once queued; overflows stay in the run statistics
+    first_batch: int = 0    # batch index of the run's first pass (resume from a checkpoint)
 
     def struct(self) -> lsm_run_opts:
         return lsm_run_opts(electron_mode=self.electron_mode, n_batches=self.n_batches,
                             majorant_factor=self.majorant_factor, f_e=self.f_e, s_geo=self.s_geo,
                             max_steps=self.max_steps, chunk=self.chunk, ctas_per_sm=self.ctas_per_sm,
-                            use_graph=int(self.use_graph), no_sync=int(self.no_sync))
+                            use_graph=int(self.use_graph), no_sync=int(self.no_sync),
+                            first_batch=int(self.first_batch))
 
 
 def lsm_transport(ph: PhantomHandle, particles: dict, n: int, seed: int, tally: Tally,

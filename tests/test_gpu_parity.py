@@ -492,3 +492,33 @@ def test_repeated_create_run_destroy_reuses_pooled_memory(L):
             free0 = free
         elif i > 2:
             assert free >= free0 - (64 << 20), (i, free0, free)
+
+
+def test_checkpoint_and_resume_equal_the_uninterrupted_run(L):
+    wl = W.workload_full_10x10(160_000)
+    n_plan = wl.n_hist // 8
+    g = L.lsm_build_psl(wl.model, wl.beams, n_plan)
+    ph = L.lsm_phantom_create(wl.phantom)
+    full = L.lsm_tally_create(ph)
+    L.lsm_run(g, ph, full, 21, L.RunOpts(n_batches=8))
+    s1, s2, nb = L.lsm_tally_read(full)
+    led, st = L.lsm_tally_ledger(full)
+    # the same 8 batches as 3 + checkpoint + 5
+    t1 = L.lsm_tally_create(ph)
+    L.lsm_run(g, ph, t1, 21, L.RunOpts(n_batches=3))
+    c1, c2, cb = L.lsm_tally_read(t1)
+    cled, cst = L.lsm_tally_ledger(t1)
+    del t1
+    t2 = L.lsm_tally_create(ph)
+    L.lsm_tally_load(t2, c1, c2, cb, cled, cst)
+    L.lsm_run(g, ph, t2, 21, L.RunOpts(n_batches=5, first_batch=3))
+    r1, r2, rb = L.lsm_tally_read(t2)
+    rled, rst = L.lsm_tally_ledger(t2)
+    assert rb == nb == 8
+    for k in ("histories", "photons", "electrons", "rejected", "missed", "flights", "real", "esteps"):
+        assert rst[k] == st[k], k
+    np.testing.assert_allclose(r1, s1, rtol=1e-5, atol=1e-7 * s1.max())
+    np.testing.assert_allclose(r2, s2, rtol=1e-4, atol=1e-7 * s2.max())
+    np.testing.assert_allclose(rled["source"], led["source"], rtol=1e-12)
+    with pytest.raises(L.LSMError, match="LSM_ERR_ARG"):
+        L.lsm_run(g, ph, t2, 21, L.RunOpts(n_batches=1, first_batch=-1))
