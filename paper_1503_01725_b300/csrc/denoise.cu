@@ -44,20 +44,30 @@ constexpr unsigned long long kWaitNs = 2000000000ull;
 // boundaries so that the swizzle phase of a row is that of its address.
 template <int COUT, int KC>
 struct Cfg {
+    // fused (conv_fused): one MMA per (dz, dy, K step) covers the three dx
+    // taps as N = 3 cout; each 128-row A tile is four 32-voxel boxes that
+    // overlap by two voxels, so that every epilogue warp sums its outputs'
+    // three dx contributions from its own TMEM lanes (30 outputs per warp)
+    static constexpr bool kFused = conv_fused(COUT, KC);
     static constexpr int kRow = KC * 2;
-    static constexpr int kPitch = (kSlabVox * kRow + 1023) / 1024 * 1024;
+    static constexpr int kSlabRows = kFused ? 128 : kSlabVox;
+    static constexpr int kPitch = (kSlabRows * kRow + 1023) / 1024 * 1024;
     static constexpr int kA = 3 * kPitch;
     static constexpr int kB = 9 * COUT * KC * 2;
     static constexpr int kStage = (kA + kB + 1023) / 1024 * 1024;
     static constexpr int kBudget = kStage <= 50 * 1024 ? 100 * 1024 : 200 * 1024;
     static constexpr int kFit = kBudget / kStage;
     static constexpr int kStages = kFit < 2 ? 2 : (kFit > 8 ? 8 : kFit);
-    static constexpr int kTx = 3 * kSlabVox * kRow + kB;
+    static constexpr int kTx = 3 * kSlabRows * kRow + kB;
     static constexpr uint32_t kSwz = KC == 16 ? 6u : (KC == 32 ? 4u : 2u);   // 32B, 64B, 128B swizzle
-    static constexpr int kAccCols = COUT < 32 ? 32 : COUT;
-    static constexpr int kTmemCols = 2 * kAccCols;
+    static constexpr int kN = kFused ? 3 * COUT : COUT;
+    static constexpr int kAccCols = kFused ? (3 * COUT + 31) / 32 * 32 : (COUT < 32 ? 32 : COUT);
+    static constexpr int kTmemCols = 2 * kAccCols <= 64 ? 64 : (2 * kAccCols <= 128 ? 128 : (2 * kAccCols <= 256 ? 256 : 512));
+    static constexpr int kTileOut = kFused ? 120 : kTileM;   // output voxels per tile
     static constexpr int kSmem = kStages * kStage + 1024;
     static_assert(KC == 16 || KC == 32 || KC == 64, "channel chunk");
+    static_assert(2 * kAccCols <= kTmemCols && kTmemCols <= 512, "tensor memory columns");
+    static_assert(kN % 16 == 0 && kN <= 256, "MMA N");
 };
 
 struct ConvArgs {
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
             bool ok = true;
             for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
                 const int vol = t / a.tiles_per_vol;
-                const long long lt = a.l0 + (long long)(t - vol * a.tiles_per_vol) * kTileM;
+                const long long lt = a.l0 + (long long)(t - vol * a.tiles_per_vol) * C::kTileOut;
                 for (int k = 0; k < ksteps; ++k, ++it) {
                     const int s = it % C::kStages;
                     if (it >= C::kStages &&
@@ -239,7 +249,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
 #pragma unroll
                     for (int dy = 0; dy < 3; ++dy) {
                         const int c1 = (int)(lt - 1 + (long long)(dz - 1) * a.p + (long long)(dy - 1) * a.w2);
-                        tma_load_3d(sa + (uint32_t)(dy * C::kPitch), &tin, a.in_co + kc * KC, c1, vol, &full[s]);
+                        if constexpr (C::kFused) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)   // rows 32 q .. 32 q + 31: voxels c1 + 30 q ..
+                                tma_load_3d(sa + (uint32_t)(dy * C::kPitch + q * 32 * C::kRow), &tin,
+                                            a.in_co + kc * KC, c1 + 30 * q, vol, &full[s]);
+                        } else {
+                            tma_load_3d(sa + (uint32_t)(dy * C::kPitch), &tin, a.in_co + kc * KC, c1, vol, &full[s]);
+                        }
                     }
                     bulk_load(sb, a.wimg + (size_t)(kc * 3 + dz) * 9 * COUT * KC, C::kB, &full[s]);
                 }
@@ -250,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
             constexpr uint32_t idesc = (1u << 4)      // D: FP32
                                        | (1u << 7)    // A: BF16
                                        | (1u << 10)   // B: BF16
-                                       | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+                                       | ((uint32_t)(C::kN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
             int it = 0, li = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x, ++li) {
@@ -266,19 +283,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
                     }
                     tc_after();
                     const uint32_t sa = sbase + (uint32_t)(s * C::kStage), sb = sa + C::kA;
+                    if constexpr (C::kFused) {
+                        // the dx taps are N groups of one operand: A starts at row 0
 #pragma unroll
-                    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                        for (int dx = 0; dx < 3; ++dx)
+                        for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                             for (int j = 0; j < KC / 16; ++j) {
-                                const uint64_t ad = sdesc(sa + (uint32_t)(dy * C::kPitch + dx * C::kRow + j * 32), 16,
-                                                          8 * C::kRow, C::kSwz);
+                                const uint64_t ad =
+                                    sdesc(sa + (uint32_t)(dy * C::kPitch + j * 32), 16, 8 * C::kRow, C::kSwz);
                                 const uint64_t bd = sdesc(
-                                    sb + (uint32_t)((dy * 3 + dx) * (COUT * KC * 2) + j * 2 * (COUT * 16)), COUT * 16,
+                                    sb + (uint32_t)(dy * (3 * COUT * KC * 2) + j * 2 * (3 * COUT * 16)), 3 * COUT * 16,
                                     128);
-                                mma_bf16(d, ad, bd, idesc, (k | dy | dx | j) != 0);
+                                mma_bf16(d, ad, bd, idesc, (k | dy | j) != 0);
                             }
+                    } else {
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                                for (int j = 0; j < KC / 16; ++j) {
+                                    const uint64_t ad = sdesc(sa + (uint32_t)(dy * C::kPitch + dx * C::kRow + j * 32),
+                                                              16, 8 * C::kRow, C::kSwz);
+                                    const uint64_t bd = sdesc(
+                                        sb + (uint32_t)((dy * 3 + dx) * (COUT * KC * 2) + j * 2 * (COUT * 16)),
+                                        COUT * 16, 128);
+                                    mma_bf16(d, ad, bd, idesc, (k | dy | dx | j) != 0);
+                                }
+                    }
                     mma_commit(&empty[s]);
                 }
                 if (ok) mma_commit(&accf[acc]);
@@ -293,7 +325,52 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
             if (!__all_sync(0xFFFFFFFFu, ok)) break;
             tc_after();
             const int vol = t / a.tiles_per_vol;
-            const long long L = a.l0 + (long long)(t - vol * a.tiles_per_vol) * kTileM + 32 * q + lane;
+            const long long lt = a.l0 + (long long)(t - vol * a.tiles_per_vol) * C::kTileOut;
+            if constexpr (C::kFused) {
+                // lane j of quarter q holds row 32 q + j = input voxel lt - 1 + 30 q + j;
+                // output lt + 30 q + j (j < 30) = P0[j] + P1[j + 1] + P2[j + 2]
+                const long long L = lt + 30 * q + lane;
+                const long long zz = L / a.p;
+                const int rem = (int)(L - zz * a.p);
+                const int yy = rem / a.w2, xx = rem - yy * a.w2;
+                const bool inside = zz >= 1 && zz <= a.d && yy >= 1 && yy <= a.h && xx >= 1 && xx <= a.w;
+                const bool write = lane < 30 && L < a.lp;
+                __nv_bfloat16 *o = a.out + ((size_t)vol * (size_t)a.lp + (size_t)(write ? L : 0)) * a.out_ct + a.out_co;
+                const uint32_t row = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * C::kAccCols);
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    uint32_t r0[16], r1[16], r2[16];
+                    tmem_ld16(row + (uint32_t)c0, r0);
+                    tmem_ld16(row + (uint32_t)(COUT + c0), r1);
+                    tmem_ld16(row + (uint32_t)(2 * COUT + c0), r2);
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float v[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int c = 2 * i + h;
+                            const float p1 = __shfl_down_sync(0xFFFFFFFFu, __uint_as_float(r1[c]), 1);
+                            const float p2 = __shfl_down_sync(0xFFFFFFFFu, __uint_as_float(r2[c]), 2);
+                            float x = __uint_as_float(r0[c]) + p1 + p2 + __ldg(a.bias + c0 + c);
+                            if (a.relu) x = fmaxf(x, 0.0f);
+                            v[h] = inside ? x : 0.0f;
+                        }
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[0], v[1]);
+                        pk[i] = *reinterpret_cast<const uint32_t *>(&h2);
+                    }
+                    if (write) {
+                        uint4 *dst = reinterpret_cast<uint4 *>(o + c0);
+                        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    }
+                }
+                tc_before();
+                __syncwarp();
+                if (lane == 0) mb_arrive(&acce[acc]);
+                continue;
+            }
+            const long long L = lt + 32 * q + lane;
             const long long zz = L / a.p;
             const int rem = (int)(L - zz * a.p);
             const int yy = rem / a.w2, xx = rem - yy * a.w2;
@@ -561,7 +638,8 @@ lsm_status conv_forward(const lsm_conv3d *cv, const lsm_vol *in, const lsm_vol *
     CUtensorMap map;
     const cuuint64_t dims[3] = {(cuuint64_t)in->c_total, (cuuint64_t)v.lp, (cuuint64_t)in->n};
     const cuuint64_t strides[2] = {(cuuint64_t)in->c_total * 2, (cuuint64_t)v.lp * in->c_total * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)cv->kc, (cuuint32_t)kSlabVox, 1};
+    const bool fused = conv_fused(cv->cout, cv->kc);
+    const cuuint32_t box[3] = {(cuuint32_t)cv->kc, (cuuint32_t)(fused ? 32 : kSlabVox), 1};
     const cuuint32_t es[3] = {1, 1, 1};
     const CUtensorMapSwizzle swz = cv->kc == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
                                    : cv->kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
@@ -584,7 +662,8 @@ lsm_status conv_forward(const lsm_conv3d *cv, const lsm_vol *in, const lsm_vol *
     // after the last, so that interior rows are written whole
     a.l0 = (long long)v.p + v.w2;
     const long long llast = (long long)in->d * v.p + (long long)in->h * v.w2 + in->w + 1;
-    a.tiles_per_vol = (int)((llast - a.l0 + kTileM) / kTileM);
+    const int tile_out = fused ? 120 : kTileM;      // Cfg<>::kTileOut
+    a.tiles_per_vol = (int)((llast - a.l0 + tile_out) / tile_out);
     a.n_tiles = a.tiles_per_vol * in->n;
     a.out_ct = out->c_total;
     a.out_co = out->c_offset;
@@ -626,13 +705,10 @@ lsm_status conv_create(int cin, int cout, int relu, const float *w, const float 
         for (int dz = 0; dz < 3; ++dz)
             for (int tap = 0; tap < 9; ++tap) {
                 const int dy = tap / 3, dx = tap % 3;
-                const size_t blk = (size_t)((c * 3 + dz) * 9 + tap) * cout * kc;
                 for (int n = 0; n < cout; ++n)
-                    for (int k = 0; k < kc; ++k) {
-                        const size_t off = (size_t)(k / 8) * cout * 8 + (size_t)(n / 8) * 64 + (n % 8) * 8 + (k % 8);
-                        img[blk + off] =
+                    for (int k = 0; k < kc; ++k)
+                        img[wimg_offset(cout, kc, c, dz, dy, dx, n, k)] =
                             __float2bfloat16_rn(w[((((size_t)n * 3 + dz) * 3 + dy) * 3 + dx) * cin + c * kc + k]);
-                    }
             }
     std::vector<float> bias(cout, 0.0f);
     for (int n = 0; n < cout && b; ++n) bias[n] = __bfloat162float(__float2bfloat16_rn(b[n]));

@@ -41,16 +41,9 @@ __global__ void k_pack(const float *__restrict__ w, int cin, int cout, int kc, i
         const int o = (int)(r / 27);
         const int dz = tap27 / 9, dy = (tap27 / 3) % 3, dx = tap27 % 3;
         const bf16 v = __float2bfloat16_rn(w[i]);
-        {
-            const int chunk = c / kc, k = c % kc;
-            const long long blk = (long long)((chunk * 3 + dz) * 9 + dy * 3 + dx) * cout * kc;
-            img[blk + (k / 8) * cout * 8 + (o / 8) * 64 + (o % 8) * 8 + (k % 8)] = v;
-        }
-        if (img_t) {
-            const int chunk = o / kc_t, k = o % kc_t;
-            const long long blk = (long long)((chunk * 3 + (2 - dz)) * 9 + (2 - dy) * 3 + (2 - dx)) * cin * kc_t;
-            img_t[blk + (k / 8) * cin * 8 + (c / 8) * 64 + (c % 8) * 8 + (k % 8)] = v;
-        }
+        img[wimg_offset(cout, kc, c / kc, dz, dy, dx, o, c % kc)] = v;
+        // the data-gradient layer: input and output channels swapped, taps mirrored
+        if (img_t) img_t[wimg_offset(cin, kc_t, o / kc_t, 2 - dz, 2 - dy, 2 - dx, c, o % kc_t)] = v;
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cout; i += gridDim.x * blockDim.x)
         bias[i] = bf(__float2bfloat16_rn(b[i]));

@@ -7,6 +7,32 @@
 
 #include "common.cuh"
 
+// Layers whose three dx taps share one MMA (N = 3 cout): cout <= 64 and at
+// least 32 input channels per stage. With 16 channels per stage the twelve
+// small boxes per stage this needs cost more than the MMAs they save
+// (measured on the 16-channel layers at 128^3).
+__host__ __device__ constexpr bool conv_fused(int cout, int kc) { return cout <= 64 && kc >= 32; }
+
+// Element offset of weight (output channel n, input channel chunk * kc + k,
+// tap dz, dy, dx) in a layer's BF16 operand image. The image holds, per
+// (channel chunk, dz), the stage's 9 taps x cout x kc weights in the K-major
+// core-matrix layout of the MMA's B operand (8 rows x 8 K elements of 16
+// bytes; rows step 128 bytes per 8-row group, the two 8-element K halves of
+// a 16-wide K step are n_rows x 16 bytes apart). Fused layers (conv_fused)
+// put the three dx taps of one (dz, dy) side by side as one operand of
+// 3 cout rows (row dx cout + n), so that one MMA covers them.
+__host__ __device__ __forceinline__ size_t wimg_offset(int cout, int kc, int chunk, int dz, int dy, int dx, int n,
+                                                       int k)
+{
+    if (conv_fused(cout, kc)) {
+        const size_t blk = (size_t)((chunk * 3 + dz) * 3 + dy) * 3 * cout * kc;
+        const int rows = 3 * cout, r = dx * cout + n;
+        return blk + (size_t)(k / 8) * rows * 8 + (size_t)(r / 8) * 64 + (r % 8) * 8 + (k % 8);
+    }
+    const size_t blk = (size_t)((chunk * 3 + dz) * 9 + dy * 3 + dx) * cout * kc;
+    return blk + (size_t)(k / 8) * cout * 8 + (size_t)(n / 8) * 64 + (n % 8) * 8 + (k % 8);
+}
+
 struct lsm_conv3d {
     int cin, cout, relu, kc;
     __nv_bfloat16 *wimg;      // packed operand images [cin/kc][dz][9 taps][cout x kc]
