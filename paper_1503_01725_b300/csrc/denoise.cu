@@ -603,8 +603,20 @@ lsm_status launch_conv(const CUtensorMap &map, const ConvArgs &a, int ctas_per_s
     static int occ = 0;
     if (!occ) {
         LSM_CUDA(cudaFuncSetAttribute(k_conv3d<COUT, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
-        LSM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3d<COUT, KC>, kThreads, C::kSmem));
-        if (occ < 1) occ = 1;
+        // The occupancy query answers 1 for any kernel holding tcgen05
+        // instructions, whatever it uses; count the resident CTAs from the
+        // shared memory, the 512 tensor-memory columns, registers and warps.
+        cudaFuncAttributes fa;
+        LSM_CUDA(cudaFuncGetAttributes(&fa, k_conv3d<COUT, KC>));
+        int dev = 0, smem_sm = 0, rsv = 0;
+        LSM_CUDA(cudaGetDevice(&dev));
+        LSM_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        LSM_CUDA(cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+        const int by_smem = smem_sm / (C::kSmem + (int)fa.sharedSizeBytes + rsv);
+        const int by_tmem = 512 / C::kTmemCols;
+        const int by_regs = 65536 / (((fa.numRegs + 7) / 8 * 8) * kThreads);
+        const int by_warps = 64 / (kThreads / 32);
+        occ = std::max(1, std::min(std::min(by_smem, by_tmem), std::min(by_regs, by_warps)));
     }
     const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
     const int grid = std::max(1, std::min(a.n_tiles, per_sm * sm_count()));
