@@ -15,8 +15,9 @@ Metric: histories/s (source histories including jaw-rejected ones, per second
 of device time) and seconds to 1% dose uncertainty, t_1% = T (u / 0.01)^2 with
 u the mean batch relative standard deviation over voxels above 50% of Dmax.
 
---impl reference times the CPU oracle (plain single-threaded FP64 C) on a
-bounded sample of the same workload on this host's cores.
+--impl reference times the CPU oracle (plain single-threaded FP64 C, one
+process per host core on disjoint seeds) on a bounded sample of the same
+workload.
 Under torchrun (N > 1) every rank runs the same workload with its own Philox
 key (independent histories, no data-path collective: weak scaling); rank 0
 prints the line with the slowest rank's time.
@@ -202,6 +203,60 @@ def cpu_oracle_rate(wl, seconds: float, per_step_hist: int = 100_000):
         if el >= seconds:
             break
     return done / el, done, el
+
+
+_ORACLE = None
+
+
+def _oracle_init(wl, per: int, electron_mode: int):
+    """Pool initializer: each process loads the oracle and builds the plan once."""
+    global _ORACLE
+    from oracle import oracle as O
+    _ORACLE = (O, O.Plan(wl.model, wl.beams, per), wl.phantom, electron_mode)
+
+
+def _oracle_pass(seed: int) -> int:
+    """One pass of the plan with the given seed (independent histories)."""
+    O, plan, ph, em = _ORACLE
+    O.run(plan, ph, seed, n_batches=1, electron_mode=em)
+    return seed
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_pool(wl, per: int, electron_mode: int):
+    """Processes (started with spawn, so that none is forked from a process
+    holding a CUDA context) that run the oracle on disjoint seeds, one per
+    host core (at most 64)."""
+    import multiprocessing as mp
+    n = max(1, min(64, host_cores()))
+    pool = mp.get_context("spawn").Pool(n, initializer=_oracle_init, initargs=(wl, per, electron_mode))
+    pool.map(_oracle_pass, range(900, 900 + n), chunksize=1)     # every process has loaded the oracle
+    return pool, n
+
+
+def cpu_oracle_rate_all_cores(wl, seconds: float, per: int = 100_000):
+    """Oracle histories/s on all host cores: rounds of one 1e5-history pass
+    per process with fresh seeds until `seconds` have passed."""
+    pool, n = oracle_pool(wl, per, wl.electron_mode)
+    try:
+        done, seed, t0 = 0, 2000, time.perf_counter()
+        while True:
+            pool.map(_oracle_pass, range(seed, seed + n), chunksize=1)
+            done += n * per
+            seed += n
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+    finally:
+        pool.terminate()
+        pool.join()
+    return done / el, done, el, n
 
 
 def commissioning_block(lsm, W, reps: int = 3, n_batches: int = 16):
@@ -497,25 +552,29 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = W.workload_full_10x10(args.n_hist)
-    from oracle import oracle as O
     per = 50_000
-    plan = O.Plan(wl.model, wl.beams, per)
-    for i in range(args.warmup):
-        O.run(plan, wl.phantom, 10 + i, n_batches=1, electron_mode=1)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        O.run(plan, wl.phantom, 100 + i, n_batches=1, electron_mode=1)
-    el = time.perf_counter() - t0
-    rate = per * args.steps / el
+    pool, n = oracle_pool(wl, per, wl.electron_mode)
+    try:
+        for i in range(args.warmup):
+            pool.map(_oracle_pass, range(10 + i * n, 10 + (i + 1) * n), chunksize=1)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            pool.map(_oracle_pass, range(100_000 + i * n, 100_000 + (i + 1) * n), chunksize=1)
+        el = time.perf_counter() - t0
+    finally:
+        pool.terminate()
+        pool.join()
+    rate = n * per * args.steps / el
     line = {
         "impl": "reference", "metric": "histories/s", "value": rate, "unit": "histories/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "n_hist_workload": args.n_hist,
-                   "sample": f"{per} histories per step (one pass of a {per}-history plan of the same workload)"},
-        "cpu_baseline": {"value": rate, "unit": "histories/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} x {per} histories"},
+                   "sample": f"{n} x {per} histories per step (one pass of a {per}-history plan of the same "
+                             f"workload in each of {n} processes, disjoint seeds)"},
+        "cpu_baseline": {"value": rate, "unit": "histories/s", "cores": n, "kind": "oracle",
+                         "sample": f"{args.steps} x {n} x {per} histories"},
         "e2e": {"value": rate, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -672,6 +731,19 @@ def main():
                 "peak_source": f"{hbm_kind} hbm_gbs",
                 "algorithmic_bytes_per_step": units[dom]}
 
+    # the tally-update ceiling: FP32 atomics to scattered cells of a tally the
+    # size of this run's batch slots, against the transport's step rates
+    # (each Woodcock flight or CSDA step makes at most one tally update)
+    n_cells = wl.phantom.nvox * args.n_batches
+    peak_at = lsm.lsm_l2_atomic_peak(n_cells)
+    l2_atomics = {"peak_atomics_per_s": peak_at, "cells": n_cells,
+                  "source": "lsm_l2_atomic_peak (FP32 atomicAdd, result unused, LCG-scattered cells)"}
+    for k, units_k in (("photon", st["flights"]), ("electron", st["esteps"])):
+        if per_step.get(k, 0) > 0:
+            r = units_k / (per_step[k] / 1e3)
+            l2_atomics[f"{k}_steps_per_s"] = r
+            l2_atomics[f"{k}_frac"] = r / peak_at if peak_at > 0 else None
+
     batched = None
     if not args.no_batched:
         batched = commissioning_block(lsm, W)
@@ -695,9 +767,13 @@ def main():
         lsm.lsm_timing_enable(False)
     cpu = None
     if not args.no_cpu_baseline:
-        rate, n_done, el = cpu_oracle_rate(wl, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "histories/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n_done} histories as 1e5-history plans of the same workload, {el:.1f} s"}
+        rate, n_done, el, n_proc = cpu_oracle_rate_all_cores(wl, args.cpu_seconds)
+        rate1, n_done1, el1 = cpu_oracle_rate(wl, args.cpu_seconds / 3)
+        cpu = {"value": rate, "unit": "histories/s", "cores": n_proc, "kind": "oracle",
+               "sample": f"{n_done} histories as 1e5-history plans of the same workload in {n_proc} processes "
+                         f"(disjoint seeds), {el:.1f} s",
+               "one_core": {"value": rate1, "cores": 1,
+                            "sample": f"{n_done1} histories as 1e5-history plans, {el1:.1f} s"}}
     line = {
         "metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -715,6 +791,7 @@ def main():
                           "real": st["real"], "esteps": st["esteps"], "rejected": st["rejected"],
                           "queue_overflows": st["overflows"]},
         "roofline": roofline,
+        "l2_atomics": l2_atomics,
         "batched": batched,
         "denoised": denoised,
         "commissioning_validation": validation,

@@ -571,6 +571,20 @@ lsm_status lsm_curve_compare(const float *pos, const float *calc, const float *m
                              int32_t use_abs, double dmax_m, lsm_mem mem, double out[6], lsm_stream stream);
 
 /*
+ * lsm_l2_atomic_peak -- the ceiling for the tally updates of transport: the
+ * rate of FP32 atomic adds whose result is unused, to pseudo-random cells of a
+ * device array of n_cells floats (each thread walks a linear congruential
+ * sequence and maps it to a cell), over a grid of 8 CTAs per SM. A device
+ * buffer of n_cells floats is allocated and freed inside the call; two warm-up
+ * launches, then `reps` launches of 256 x 256 atomics per thread timed with
+ * CUDA events on `stream`. *atomics_per_s: atomic operations per second.
+ * Synchronises. Errors: LSM_ERR_ARG for a NULL output, n_cells outside
+ * [1, 2^31] or reps outside [1, 1000]; LSM_ERR_CUDA when allocation or a launch
+ * fails.
+ */
+lsm_status lsm_l2_atomic_peak(int64_t n_cells, int32_t reps, double *atomics_per_s, lsm_stream stream);
+
+/*
  * PSL files -- the comparator source model of Table 1 (Sec. 3.1): particles
  * stored on disk grouped by phase-spacelet, read for a field, copied to the
  * GPU and translated there, instead of being sampled on the fly.

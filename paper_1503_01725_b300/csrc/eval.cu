@@ -192,6 +192,19 @@ struct Staged {
     }
 };
 
+// FP32 atomic adds, result unused, at pseudo-random cells: thread i walks the
+// LCG x -> 1664525 x + 1013904223 (mod 2^32; Numerical Recipes, Sec. 7.1) from
+// x = i and maps each state to a cell by a 32x32 -> high-32 multiply, as the
+// transport's tally updates land on scattered voxels
+__global__ void k_atomic_peak(float *__restrict__ cells, uint32_t n_cells, int per_thread)
+{
+    uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = 0; i < per_thread; ++i) {
+        x = x * 1664525u + 1013904223u;
+        atomicAdd(cells + __umulhi(x, n_cells), 1.0f);
+    }
+}
+
 }  // namespace
 }  // namespace lsm
 
@@ -335,6 +348,44 @@ lsm_status lsm_curve_compare(const float *pos, const float *calc, const float *m
     out[3] = r[3];
     out[4] = r[4];
     out[5] = r[5];
+    return LSM_OK;
+}
+
+lsm_status lsm_l2_atomic_peak(int64_t n_cells, int32_t reps, double *atomics_per_s, lsm_stream stream)
+{
+    if (!atomics_per_s) return set_arg_error("lsm_l2_atomic_peak: NULL argument");
+    if (n_cells < 1 || n_cells > (1ll << 31) || reps < 1 || reps > 1000)
+        return set_arg_error("lsm_l2_atomic_peak: 1 <= n_cells <= 2^31, 1 <= reps <= 1000");
+    const cudaStream_t st = (cudaStream_t)stream;
+    constexpr int kThreads = 256, kPer = 256;
+    const int grid = 8 * sm_count();
+    const double per_launch = (double)grid * kThreads * kPer;
+    float *cells = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.0f;
+    cudaError_t e = dev_malloc((void **)&cells, (size_t)n_cells * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cells, 0, (size_t)n_cells * 4, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {   // warm-up
+        k_atomic_peak<<<grid, kThreads, 0, st>>>(cells, (uint32_t)n_cells, kPer);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) {
+        k_atomic_peak<<<grid, kThreads, 0, st>>>(cells, (uint32_t)n_cells, kPer);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (cells) dev_free(cells);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsm_l2_atomic_peak");
+    *atomics_per_s = ms > 0.0f ? per_launch * reps / (ms * 1e-3) : 0.0;
     return LSM_OK;
 }
 

@@ -150,6 +150,7 @@ _EXPORTS = {
                             C.c_double, C.c_double, C.c_int, _dp, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p]),
     "lsm_dose_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, _dp,
                                  C.c_void_p]),
+    "lsm_l2_atomic_peak": (C.c_int, [C.c_int64, C.c_int32, _dp, C.c_void_p]),
     "lsm_curve_compare": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double,
                                     C.c_int32, C.c_double, C.c_int, _dp, C.c_void_p]),
     "lsm_pslfile_write": (C.c_int, [C.c_void_p, C.c_uint64, C.c_char_p, C.POINTER(C.c_int64), C.c_void_p]),
@@ -487,6 +488,14 @@ def lsm_run(psl: PSL, ph: PhantomHandle, tally: Tally, seed: int, opts: RunOpts 
     o = (opts or RunOpts()).struct()
     return _check(_lib.lsm_run(psl.ptr, ph.ptr, tally.ptr, seed, C.byref(o), _stream(stream)), "lsm_run",
                   ok=(LSM_OK, LSM_ERR_OVERFLOW))
+
+
+def lsm_l2_atomic_peak(n_cells: int, reps: int = 10, stream=None) -> float:
+    """FP32 atomic adds per second (result unused) to pseudo-random cells of
+    an n_cells array: the ceiling of the transport's tally updates."""
+    out = C.c_double(0.0)
+    _check(_lib.lsm_l2_atomic_peak(int(n_cells), int(reps), C.byref(out), _stream(stream)), "lsm_l2_atomic_peak")
+    return out.value
 
 
 def lsm_curve_compare(pos, calc, meas, lo: float = -np.inf, hi: float = np.inf, dmax_m: float | None = None,

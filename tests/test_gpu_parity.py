@@ -14,6 +14,8 @@ Bars:
 * dose: |z| < 3 on >= 99% of voxels above 10% of the maximum and mean dose
   within 0.5%, z = (D_gpu - D_oracle) / sqrt(s_gpu^2 + s_oracle^2).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -522,3 +524,15 @@ def test_checkpoint_and_resume_equal_the_uninterrupted_run(L):
     np.testing.assert_allclose(rled["source"], led["source"], rtol=1e-12)
     with pytest.raises(L.LSMError, match="LSM_ERR_ARG"):
         L.lsm_run(g, ph, t2, 21, L.RunOpts(n_batches=1, first_batch=-1))
+
+
+def test_l2_atomic_peak(L):
+    # the tally-update ceiling the bench reports transport step rates against:
+    # a finite rate well above the transport's own steps per second
+    r = L.lsm_l2_atomic_peak(64 ** 3 * 16, reps=3)
+    assert math.isfinite(r) and r > 1e10
+    small = L.lsm_l2_atomic_peak(1, reps=1)            # every update on one cell: contention, still positive
+    assert 0 < small < r
+    for bad in ((0, 1), (2 ** 31 + 1, 1), (1024, 0), (1024, 1001)):
+        with pytest.raises(L.LSMError, match="LSM_ERR_ARG"):
+            L.lsm_l2_atomic_peak(*bad)
