@@ -70,7 +70,7 @@ constexpr int kXsBytes = 2 * kGrid * 16;                                      //
 #define LSM_ELECTRON_THREADS 256
 #endif
 #ifndef LSM_PHOTON_MINB
-#define LSM_PHOTON_MINB 4
+#define LSM_PHOTON_MINB 3
 #endif
 #ifndef LSM_ELECTRON_MINB
 #define LSM_ELECTRON_MINB 5
