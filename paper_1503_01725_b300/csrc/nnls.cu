@@ -5,7 +5,8 @@
 // k_gram forms G = A^T A and c = A^T b (FP64 CUDA cores). Two solvers then run
 // in one CTA of 1024 threads with G resident in L2:
 //   * active set (Lawson & Hanson 1974): the passive-set least squares is
-//     solved by a Cholesky factorisation of G restricted to the passive set;
+//     solved through a Cholesky factor of G restricted to the passive set,
+//     updated as variables enter or leave (O(k^2) per change);
 //   * gradient projection with Armijo's rule (Sec. 2.2.4):
 //     x <- max(0, x - s grad F), s = s_bar beta^j for the first j with
 //     F(x_new) <= F(x) + sigma grad F . (x_new - x); stop when the relative
@@ -107,68 +108,146 @@ struct NnlsOut {
     double objective;
 };
 
-// Cholesky solve of G[P,P] z_P = c_P into z (z = 0 outside P); k = |P|, idx = P in order.
-// L: scratch k x k. Returns false if the restricted Gram matrix is not positive definite.
-__device__ bool chol_solve(const double *__restrict__ G, int n, const int *idx, int k, const double *c,
-                           double *L, double *z, double *y, double *red)
+// The passive set's factor: G[P,P] = L L^T for P = ord[0..k) in the order
+// the variables entered, L lower triangular, column-major with leading
+// dimension n (element (i, j), i >= j, at L[j n + i]); invd[i] = 1 / L(i, i).
+// Lawson and Hanson's iteration adds or drops one variable at a time, so the
+// factor is extended by one row (a forward substitution) or has a row and
+// column deleted (a rank-one update of the trailing block, Givens form) in
+// O(k^2) instead of being refactored in O(k^3). The triangular work runs on
+// one warp; only warp-level synchronisation is needed inside it.
+
+// Column j of the factor, indexable by row i >= j. Packed (shared memory):
+// the lower triangle column after column, column j holding rows j..n-1;
+// otherwise (global memory) leading dimension n.
+template <bool PK>
+__device__ __forceinline__ double *lcol(double *L, int n, int j)
 {
-    for (int t = threadIdx.x; t < k * k; t += kT) {
-        const int i = t / k, l = t % k;
-        L[t] = G[(size_t)idx[i] * n + idx[l]];
-    }
-    __syncthreads();
-    __shared__ int fail;
-    if (threadIdx.x == 0) fail = 0;
-    __syncthreads();
+    return PK ? L + (size_t)j * n - (size_t)j * (j + 1) / 2 : L + (size_t)j * n;
+}
+
+// r <- L^-1 r over the first k entries
+template <bool PK>
+__device__ void warp_forward(double *__restrict__ L, int n, int k, const double *invd, double *r)
+{
+    const int lane = threadIdx.x & 31;
     for (int j = 0; j < k; ++j) {
-        if (threadIdx.x == 0) {
-            const double d = L[j * k + j];
-            if (!(d > 0.0)) fail = 1;
-            L[j * k + j] = sqrt(d > 0.0 ? d : 1.0);
-        }
-        __syncthreads();
-        if (fail) return false;
-        const double djj = L[j * k + j];
-        for (int i = j + 1 + threadIdx.x; i < k; i += kT) L[i * k + j] /= djj;
-        __syncthreads();
-        const int rem = k - j - 1;
-        for (int t = threadIdx.x; t < rem * rem; t += kT) {
-            const int i = j + 1 + t / rem, l = j + 1 + t % rem;
-            if (l <= i) L[i * k + l] -= L[i * k + j] * L[l * k + j];
-        }
-        __syncthreads();
+        const double rj = r[j] * invd[j];
+        __syncwarp();
+        if (lane == 0) r[j] = rj;
+        const double *col = lcol<PK>(L, n, j);
+        for (int i = j + 1 + lane; i < k; i += 32) r[i] -= col[i] * rj;
+        __syncwarp();
     }
-    // forward: L y = c_P
-    for (int i = 0; i < k; ++i) {
-        double s = 0.0;
-        for (int l = threadIdx.x; l < i; l += kT) s += L[i * k + l] * y[l];
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) y[i] = (c[idx[i]] - s) / L[i * k + i];
-        __syncthreads();
-    }
-    // backward: L^T zP = y
+}
+
+// z <- L^-T y over the first k entries
+template <bool PK>
+__device__ void warp_backward(double *__restrict__ L, int n, int k, const double *invd, const double *y, double *z)
+{
+    const int lane = threadIdx.x & 31;
     for (int i = k - 1; i >= 0; --i) {
+        const double *col = lcol<PK>(L, n, i);
         double s = 0.0;
-        for (int l = i + 1 + threadIdx.x; l < k; l += kT) s += L[l * k + i] * z[idx[l]];
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) z[idx[i]] = (y[i] - s) / L[i * k + i];
-        __syncthreads();
+        for (int l = i + 1 + lane; l < k; l += 32) s += col[l] * z[l];
+        s = warp_sum(s);
+        if (lane == 0) z[i] = (y[i] - s) * invd[i];
+        __syncwarp();
     }
+}
+
+// Append variable t (position k); false when G restricted to P + {t} is not
+// positive definite (the new pivot is not > 0). r: scratch of k doubles.
+template <bool PK>
+__device__ bool warp_add(const double *__restrict__ G, double *L, int n, int k, int *ord, double *invd, int t,
+                         double *r)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < k; i += 32) r[i] = G[(size_t)ord[i] * n + t];
+    __syncwarp();
+    warp_forward<PK>(L, n, k, invd, r);
+    double s = 0.0;
+    for (int i = lane; i < k; i += 32) s += r[i] * r[i];
+    s = warp_sum(s);
+    const double d = G[(size_t)t * n + t] - s;
+    if (!(d > 0.0)) return false;
+    for (int j = lane; j < k; j += 32) lcol<PK>(L, n, j)[k] = r[j];
+    if (lane == 0) {
+        const double dd = sqrt(d);
+        lcol<PK>(L, n, k)[k] = dd;
+        invd[k] = 1.0 / dd;
+        ord[k] = t;
+    }
+    __syncwarp();
     return true;
 }
 
+// Drop position q of k: delete row and column q, then restore the trailing
+// block's factor with the rank-one update L33 L33^T + v v^T, v the deleted
+// column below the diagonal. v: scratch of k doubles.
+template <bool PK>
+__device__ void warp_remove(double *L, int n, int k, int *ord, double *invd, int q, double *v)
+{
+    const int lane = threadIdx.x & 31;
+    const int m = k - 1 - q;
+    for (int i = lane; i < m; i += 32) v[i] = lcol<PK>(L, n, q)[q + 1 + i];
+    __syncwarp();
+    for (int j = 0; j < q; ++j) {          // columns left of q lose row q
+        double *col = lcol<PK>(L, n, j);
+        for (int i0 = q + 1; i0 < k; i0 += 32) {
+            const int i = i0 + lane;
+            const double val = i < k ? col[i] : 0.0;
+            __syncwarp();
+            if (i < k) col[i - 1] = val;
+            __syncwarp();
+        }
+    }
+    for (int j = q + 1; j < k; ++j) {      // columns right of q move up and left
+        const double *src = lcol<PK>(L, n, j);
+        double *dst = lcol<PK>(L, n, j - 1);
+        for (int i = j + lane; i < k; i += 32) dst[i - 1] = src[i];
+        __syncwarp();
+    }
+    if (lane == 0)
+        for (int p = q; p + 1 < k; ++p) ord[p] = ord[p + 1];
+    __syncwarp();
+    for (int c = 0; c < m; ++c) {          // Givens form of the rank-one update
+        double *col = lcol<PK>(L, n, q + c);
+        const double lcc = col[q + c], vc = v[c];
+        const double r = sqrt(lcc * lcc + vc * vc);
+        const double ics = lcc / r, sn = vc / lcc, cs = r / lcc;
+        __syncwarp();
+        if (lane == 0) {
+            col[q + c] = r;
+            invd[q + c] = 1.0 / r;
+        }
+        for (int i = c + 1 + lane; i < m; i += 32) {
+            const double lic = (col[q + i] + sn * v[i]) * ics;
+            col[q + i] = lic;
+            v[i] = cs * v[i] - sn * lic;
+        }
+        __syncwarp();
+    }
+}
+
+// PK: the factor packed in shared memory after the other arrays (when it
+// fits); otherwise in the global scratch Lg (n x n).
+template <bool PK>
 __global__ void __launch_bounds__(kT) k_lawson_hanson(const double *__restrict__ G, const double *__restrict__ cg,
-                                                      int n, double tol_scale, int max_iter, double *__restrict__ L,
+                                                      int n, double tol_scale, int max_iter, double *__restrict__ Lg,
                                                       double *__restrict__ xout, NnlsOut *out)
 {
     extern __shared__ double sm[];
-    double *x = sm, *w = sm + n, *z = sm + 2 * n, *y = sm + 3 * n, *c = sm + 4 * n;
-    int *P = (int *)(sm + 5 * n), *idx = P + n;
+    double *x = sm, *w = sm + n, *z = sm + 2 * n, *y = sm + 3 * n, *c = sm + 4 * n, *invd = sm + 5 * n,
+           *zf = sm + 6 * n;
+    int *P = (int *)(sm + 7 * n), *ord = P + n;
+    double *L = PK ? sm + 8 * n : Lg;       // 7 n doubles + 2 n ints = 8 n doubles
     __shared__ double red[33];
     __shared__ int redi[33];
     __shared__ int s_k, s_status;
+    const bool w0 = threadIdx.x < 32;
     for (int j = threadIdx.x; j < n; j += kT) { x[j] = 0.0; P[j] = 0; c[j] = cg[j]; w[j] = cg[j]; }
-    if (threadIdx.x == 0) s_status = 0;
+    if (threadIdx.x == 0) { s_status = 0; s_k = 0; }
     // tolerance 10 eps ||G||_1 max(m, n) (Lawson & Hanson's test on the dual)
     double cmax = 0.0;
     for (int j = threadIdx.x; j < n; j += kT) {
@@ -198,27 +277,32 @@ __global__ void __launch_bounds__(kT) k_lawson_hanson(const double *__restrict__
         double best;
         const int t = block_argmax(bj >= 0 ? bv : -INFINITY, bj, red, redi, &best);
         if (t < 0 || !(best > tol) || it >= max_iter) break;
-        if (threadIdx.x == 0) P[t] = 1;
+        if (w0) {
+            const int k = s_k;
+            const bool ok = warp_add<PK>(G, L, n, k, ord, invd, t, y);
+            if (threadIdx.x == 0) {
+                if (ok) { P[t] = 1; s_k = k + 1; }
+                else s_status = 2;
+            }
+        }
         __syncthreads();
+        if (s_status) break;
         for (;;) {
             ++it;
-            if (threadIdx.x == 0) {
-                int k = 0;
-                for (int j = 0; j < n; ++j)
-                    if (P[j]) idx[k++] = j;
-                s_k = k;
-            }
+            const int k = s_k;
             for (int j = threadIdx.x; j < n; j += kT) z[j] = 0.0;
             __syncthreads();
-            const int k = s_k;
-            if (!chol_solve(G, n, idx, k, c, L, z, y, red)) {
-                if (threadIdx.x == 0) s_status = 2;
-                __syncthreads();
-                break;
+            if (w0) {   // z_P = G[P,P]^-1 c_P through the factor
+                for (int i = threadIdx.x; i < k; i += 32) y[i] = c[ord[i]];
+                __syncwarp();
+                warp_forward<PK>(L, n, k, invd, y);
+                warp_backward<PK>(L, n, k, invd, y, zf);
+                for (int i = threadIdx.x; i < k; i += 32) z[ord[i]] = zf[i];
             }
+            __syncthreads();
             // all passive z positive?
             int bad = 0;
-            for (int q = threadIdx.x; q < k; q += kT) bad |= !(z[idx[q]] > 0.0);
+            for (int q = threadIdx.x; q < k; q += kT) bad |= !(z[ord[q]] > 0.0);
             bad = __syncthreads_or(bad);
             if (!bad) {
                 for (int j = threadIdx.x; j < n; j += kT) x[j] = z[j];
@@ -227,7 +311,7 @@ __global__ void __launch_bounds__(kT) k_lawson_hanson(const double *__restrict__
             }
             double a = INFINITY;
             for (int q = threadIdx.x; q < k; q += kT) {
-                const int j = idx[q];
+                const int j = ord[q];
                 if (!(z[j] > 0.0)) a = fmin(a, x[j] / (x[j] - z[j]));
             }
             for (int o = 16; o > 0; o >>= 1) a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
@@ -246,15 +330,27 @@ __global__ void __launch_bounds__(kT) k_lawson_hanson(const double *__restrict__
                 if (!P[j]) x[j] = 0.0;
             }
             __syncthreads();
+            if (w0) {   // drop the variables that left P from the factor, last position first
+                int kk = k;
+                for (int q = k - 1; q >= 0; --q)
+                    if (!P[ord[q]]) { warp_remove<PK>(L, n, kk, ord, invd, q, y); --kk; }
+                if (threadIdx.x == 0) s_k = kk;
+            }
+            __syncthreads();
             if (it >= max_iter) break;
         }
         if (s_status) break;
-        // w = c - G x
-        for (int j = threadIdx.x; j < n; j += kT) {
-            double s = 0.0;
-            const double *g = G + (size_t)j * n;
-            for (int l = 0; l < n; ++l) s += g[l] * x[l];
-            w[j] = c[j] - s;
+        // w = c - G x, x zero outside P (G symmetric: row ord[q] read along j)
+        {
+            const int k = s_k;
+            for (int j = threadIdx.x; j < n; j += kT) {
+                double s = 0.0;
+                for (int q = 0; q < k; ++q) {
+                    const int l = ord[q];
+                    s += G[(size_t)l * n + j] * x[l];
+                }
+                w[j] = c[j] - s;
+            }
         }
         __syncthreads();
     }
@@ -382,6 +478,29 @@ __global__ void __launch_bounds__(kT) k_nnls_report(const double *__restrict__ A
     }
 }
 
+// The active-set kernel for n unknowns: the factor goes to shared memory
+// when its packed lower triangle fits beside the other arrays.
+cudaError_t launch_lawson_hanson(const double *G, const double *c, int n, double tol_scale, int max_iter, double *L,
+                                 double *x, NnlsOut *out, cudaStream_t st)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const size_t base = (size_t)n * 8 * 8, packed = base + (size_t)n * (n + 1) / 2 * 8;
+    if (packed + 1024 <= (size_t)optin) {
+        e = cudaFuncSetAttribute(k_lawson_hanson<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)packed);
+        if (e != cudaSuccess) return e;
+        k_lawson_hanson<true><<<1, kT, packed, st>>>(G, c, n, tol_scale, max_iter, L, x, out);
+    } else {
+        e = cudaFuncSetAttribute(k_lawson_hanson<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base);
+        if (e != cudaSuccess) return e;
+        k_lawson_hanson<false><<<1, kT, base, st>>>(G, c, n, tol_scale, max_iter, L, x, out);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 lsm_status commission(const double *A, int32_t m, int32_t n, const double *b, lsm_mem mem,
@@ -426,12 +545,8 @@ lsm_status commission(const double *A, int32_t m, int32_t n, const double *b, ls
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         if (o.method == 0) {
-            const size_t smem = (size_t)n * 8 * 5 + (size_t)n * 4 * 2;
-            cudaFuncSetAttribute(k_lawson_hanson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             const double tol_scale = 10.0 * 2.220446049250313e-16 * (m > n ? m : n);
-            k_lawson_hanson<<<1, kT, smem, st>>>(G, c, n, tol_scale, o.max_iter, L, dx, dout);
-            count_launch();
-            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            if ((e = launch_lawson_hanson(G, c, n, tol_scale, o.max_iter, L, dx, dout, st)) != cudaSuccess) break;
         } else {
             // starting point: x (use_x0) or all ones (the uncommissioned weights)
             std::vector<double> x0((size_t)n, 1.0);
@@ -554,11 +669,8 @@ extern "C" lsm_status lsm_commission_static(const double *A, int32_t m, int32_t 
     k_gram<<<gb, dim3(32, 8), 0, st>>>(A, b, m, n, G, c);
     LSM_LAUNCHED("k_gram");
     if (o.method == 0) {
-        const size_t smem = (size_t)n * 8 * 5 + (size_t)n * 4 * 2;
-        LSM_CUDA(cudaFuncSetAttribute(k_lawson_hanson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const double tol_scale = 10.0 * 2.220446049250313e-16 * (m > n ? m : n);
-        k_lawson_hanson<<<1, kT, smem, st>>>(G, c, n, tol_scale, o.max_iter, L, x, dout);
-        LSM_LAUNCHED("k_lawson_hanson");
+        LSM_CUDA(launch_lawson_hanson(G, c, n, tol_scale, o.max_iter, L, x, dout, st));
     } else {
         if (!o.use_x0) {
             k_fill<<<(n + 255) / 256, 256, 0, st>>>(x, 1.0, n);

@@ -399,6 +399,23 @@ def test_commission_active_set_parity(L, seed):
     assert rep["objective"] == pytest.approx(N.objective(A, b, xo), rel=1e-9)
 
 
+@pytest.mark.parametrize("seed", [0, 2, 3, 6])
+def test_commission_active_set_drops_variables(L, seed):
+    """Correlated columns (rank-3 structure plus noise): variables enter the
+    passive set and later leave it (one or two removals for these seeds), so
+    the passive-set factor has rows and columns deleted as well as added."""
+    rng = np.random.default_rng(1000 + seed)
+    m, n = 40, 20
+    base = rng.standard_normal((m, 3))
+    A = base @ rng.standard_normal((3, n)) + 0.2 * rng.standard_normal((m, n))
+    b = A @ rng.standard_normal(n) + rng.standard_normal(m)
+    x, rep = L.lsm_commission(A, b, method=0)
+    xo, it_o = N.lawson_hanson(A, b)
+    np.testing.assert_allclose(x, xo, atol=1e-8 * max(1.0, np.abs(xo).max()))
+    assert rep["iterations"] == it_o
+    assert rep["objective"] == pytest.approx(N.objective(A, b, xo), rel=1e-9)
+
+
 def test_commission_projected_gradient(L):
     """Sec. 2.2.4 on an inconsistent problem (F* > 0, so the relative change of
     F goes to zero and the stopping rule fires); the limit is the NNLS minimiser."""
