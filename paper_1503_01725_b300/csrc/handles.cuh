@@ -98,6 +98,7 @@ struct lsm_phantom {
     float *d_rho;         // density
     uint8_t *d_mat;
     float *d_rhomat;      // density, negated for material class 1 (one load per voxel)
+    double *d_inv_mass;   // 1 / (rho V) per voxel (g^-1): the dose is the deposit times it
     float4 *d_xs;         // [2][kGrid]
     float *d_mumax;       // [kGrid] majorant at factor 1
     double rho_max[2];

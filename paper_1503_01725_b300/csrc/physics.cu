@@ -130,12 +130,15 @@ __global__ void k_majorant(const double *__restrict__ mutot, const unsigned *__r
     mumax[j] = (float)(v * (1.0 + 1.0 / 65536.0));
 }
 
-__global__ void k_rhomat(const float *__restrict__ rho, const uint8_t *__restrict__ mat, int64_t n,
-                         float *__restrict__ rhomat)
+__global__ void k_rhomat(const float *__restrict__ rho, const uint8_t *__restrict__ mat, int64_t n, double vol,
+                         float *__restrict__ rhomat, double *__restrict__ inv_mass)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        rhomat[i] = mat[i] ? -rho[i] : rho[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float r = rho[i];
+        rhomat[i] = mat[i] ? -r : r;
+        inv_mass[i] = 1.0 / ((double)r * vol);
+    }
 }
 
 __global__ void k_check_phantom(const float *__restrict__ rho, const uint8_t *__restrict__ mat, int64_t n,
@@ -158,6 +161,7 @@ void free_phantom(lsm_phantom *P)
     dev_free(P->d_rho);
     dev_free(P->d_mat);
     dev_free(P->d_rhomat);
+    dev_free(P->d_inv_mass);
     dev_free(P->d_xs);
     dev_free(P->d_mumax);
     free(P);
@@ -241,6 +245,7 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     CK(dev_malloc((void **)&P->d_rho, n * 4, st));
     CK(dev_malloc((void **)&P->d_mat, n, st));
     CK(dev_malloc((void **)&P->d_rhomat, n * 4, st));
+    CK(dev_malloc((void **)&P->d_inv_mass, n * 8, st));
     CK(dev_malloc((void **)&P->d_xs, 2 * kGrid * sizeof(float4), st));
     // majorant followed by the inverse-KN table: staged into shared memory by one copy
     CK(dev_malloc((void **)&P->d_mumax, kGrid * 4 + kKnE * kKnU * 4, st));
@@ -253,7 +258,7 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     CKL("k_check_phantom");
     k_rho_max<<<g, 256, 0, st>>>(P->d_rho, P->d_mat, n, d_bits);
     CKL("k_rho_max");
-    k_rhomat<<<g, 256, 0, st>>>(P->d_rho, P->d_mat, n, P->d_rhomat);
+    k_rhomat<<<g, 256, 0, st>>>(P->d_rho, P->d_mat, n, D->dx * D->dy * D->dz, P->d_rhomat, P->d_inv_mass);
     CKL("k_rhomat");
     CK(cudaMemcpyAsync(P->d_xs, tab->xs, 2 * kGrid * sizeof(float4), cudaMemcpyDeviceToDevice, st));
     k_majorant<<<(kGrid + 127) / 128, 128, 0, st>>>(d_mutot, d_bits, P->d_mumax);

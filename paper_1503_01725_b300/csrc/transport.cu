@@ -970,23 +970,47 @@ __global__ void k_flush(float *__restrict__ part, double *__restrict__ batch, in
 
 // Iterations that hold k whole batches: fold each FP32 batch slice straight
 // into the running sums and clear it.
+// x + y = s + e exactly (Knuth's TwoSum; no operation may be contracted)
+__device__ __forceinline__ void two_sum(float x, float y, float &s, float &e)
+{
+    s = __fadd_rn(x, y);
+    const float yv = __fsub_rn(s, x);
+    e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, yv)), __fsub_rn(y, yv));
+}
+
+// The slots' sum and sum of squares per cell, added to the FP64 totals. Each
+// is accumulated in FP32 as a value and a running sum of the rounding errors
+// of its additions (cascaded summation, Ogita, Rump & Oishi, SIAM J. Sci.
+// Comput. 26, 2005), the squares split exactly into product and error by one
+// FMA; the pair is converted to FP64 once per cell. The error relative to the
+// sum of magnitudes is about (k 2^-24)^2, and a cell costs a few FP64
+// operations instead of three per slot (this GPU's FP64 pipe is narrow).
 __global__ void k_fold_slots(float *__restrict__ part, double *__restrict__ s1, double *__restrict__ s2,
                              int64_t ncell, int k)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride) {
-        double a1 = 0.0, a2 = 0.0;
+        float a = 0.0f, ae = 0.0f, q2 = 0.0f, qe = 0.0f;
         bool any = false;
         for (int q = 0; q < k; ++q) {
             const float v = part[(size_t)q * ncell + c];
             if (v != 0.0f) {
-                a1 += v;
-                a2 += (double)v * (double)v;
+                float t, e;
+                two_sum(a, v, t, e);
+                a = t;
+                ae = __fadd_rn(ae, e);
+                const float sq = __fmul_rn(v, v), sqe = __fmaf_rn(v, v, -sq);
+                two_sum(q2, sq, t, e);
+                q2 = t;
+                qe = __fadd_rn(qe, __fadd_rn(e, sqe));
                 part[(size_t)q * ncell + c] = 0.0f;
                 any = true;
             }
         }
-        if (any) { s1[c] += a1; s2[c] += a2; }
+        if (any) {
+            s1[c] += (double)a + (double)ae;
+            s2[c] += (double)q2 + (double)qe;
+        }
     }
 }
 
@@ -1008,19 +1032,21 @@ __global__ void k_fold(double *__restrict__ batch, double *__restrict__ s1, doub
 // ---------------------------------------------------------- normalisation ---
 
 // dose per source particle (MeV/g) and its batch standard deviation
-__global__ void k_dose(const double *__restrict__ s1, const double *__restrict__ s2, const float *__restrict__ rho,
-                       int64_t n, int B, double scale, double vol, double *__restrict__ dose,
-                       double *__restrict__ sigma)
+// dose = S1 / B * scale / m and sigma = sqrt(B var) / B * scale / m, with
+// var = max(S2 - S1^2 / B, 0) / (B - 1) the batch variance and m = rho V;
+// written as dose = S1 f_d / m, sigma = sqrt(max(S2 - S1^2 / B, 0) f_v) scale / m
+// (f_d = scale / B, f_v = 1 / (B (B - 1)), 0 for B = 1) with 1 / m stored per
+// voxel, so that a voxel costs one FP64 square root and no division
+__global__ void k_dose(const double *__restrict__ s1, const double *__restrict__ s2,
+                       const double *__restrict__ inv_mass, int64_t n, double inv_b, double f_d, double f_v,
+                       double scale, double *__restrict__ dose, double *__restrict__ sigma)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double m = (double)rho[i] * vol;
+        const double im = inv_mass[i];
         const double a = s1[i];
-        dose[i] = a / B * scale / m;
-        if (sigma) {
-            const double var = B > 1 ? fmax(s2[i] - a * a / B, 0.0) / (B - 1) : 0.0;
-            sigma[i] = sqrt(B * var) / B * scale / m;
-        }
+        dose[i] = a * f_d * im;
+        if (sigma) sigma[i] = sqrt(fmax(s2[i] - a * a * inv_b, 0.0) * f_v) * scale * im;
     }
 }
 
@@ -1559,7 +1585,9 @@ lsm_status dose_impl(const lsm_tally *t, const lsm_phantom *ph, double scale, do
         ds = sigma ? dd + n : nullptr;
     }
     const int g = (int)std::min<int64_t>((n + 255) / 256, 8 * sm_count());
-    k_dose<<<g, 256, 0, st>>>(t->d_s1, t->d_s2, ph->d_rho, n, t->n_batches, scale, ph->dx * ph->dy * ph->dz, dd, ds);
+    const int B = t->n_batches;
+    k_dose<<<g, 256, 0, st>>>(t->d_s1, t->d_s2, ph->d_inv_mass, n, 1.0 / B, scale / B,
+                              B > 1 ? 1.0 / ((double)B * (B - 1)) : 0.0, scale, dd, ds);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && mem == LSM_MEM_HOST) {

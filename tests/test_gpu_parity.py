@@ -553,3 +553,25 @@ def test_l2_atomic_peak(L):
     for bad in ((0, 1), (2 ** 31 + 1, 1), (1024, 0), (1024, 1001)):
         with pytest.raises(L.LSMError, match="LSM_ERR_ARG"):
             L.lsm_l2_atomic_peak(*bad)
+
+
+@pytest.mark.parametrize("nb", [1, 4])
+def test_dose_and_sigma_from_the_tally(L, nb):
+    # lsm_dose against its definition from the tally sums: D = S1 / B * scale /
+    # (rho V), sigma = sqrt(B var) / B * scale / (rho V), var the batch variance
+    # max(S2 - S1^2 / B, 0) / (B - 1) (0 for one batch); FP64 to rounding
+    model = W.psr_model(6, 10, 0.25, seed=2)
+    ph = W.pelvis_phantom(24, 20, 16, 1.0)
+    phh = L.lsm_phantom_create(ph)
+    g = L.lsm_build_psl(model, W.gantry_beams([0.0, 90.0], 8.0), 20_000)
+    t = L.lsm_tally_create(phh)
+    L.lsm_run(g, phh, t, 3, L.RunOpts(electron_mode=1, n_batches=nb))
+    s1, s2, b = L.lsm_tally_read(t)
+    assert b == nb
+    scale = 0.37
+    d, s = L.lsm_dose(t, phh, scale)
+    m = ph.rho.ravel().astype(np.float64) * (ph.dx * ph.dy * ph.dz)
+    var = np.clip(s2 - s1 * s1 / nb, 0.0, None) / (nb - 1) if nb > 1 else np.zeros_like(s1)
+    np.testing.assert_allclose(d.ravel(), s1 / nb * scale / m, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(s.ravel(), np.sqrt(nb * var) / nb * scale / m, rtol=1e-13, atol=1e-300)
+    assert (d > 0).sum() > 100 and (nb == 1 or (s > 0).sum() > 100)
