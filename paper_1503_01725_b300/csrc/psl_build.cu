@@ -706,19 +706,31 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
     } while (0)
 
     // host inputs packed into one copy from pinned memory (a copy from
-    // pageable memory would first wait for the stream's earlier work); the
-    // staging buffer is reused by this thread's next build, which starts only
-    // after this build's final synchronisation
+    // pageable memory would first wait for the stream's earlier work). Each
+    // thread keeps a ring of four staging buffers, each with an event recorded
+    // after the copies out of it: a buffer is refilled only once its copies
+    // have run, so that builds queued without host synchronisation behind
+    // other work never overwrite inputs still waiting to be copied.
     const size_t n_in = nw + 4 * nm + 2 * nes + 4 * (size_t)nb + (size_t)npsr;
-    static thread_local double *hbuf = nullptr;
-    static thread_local size_t hcap = 0;
-    if (hcap < n_in + 24) {
-        if (hbuf) cudaFreeHost(hbuf);
-        hbuf = nullptr;
-        hcap = 0;
-        CK(cudaMallocHost((void **)&hbuf, (n_in + 24) * sizeof(double)));
-        hcap = n_in + 24;
+    struct Stage {
+        double *buf;
+        size_t cap;
+        cudaEvent_t copied;
+    };
+    static thread_local Stage ring[4] = {};
+    static thread_local int ring_next = 0;
+    Stage &sg = ring[ring_next];
+    ring_next = (ring_next + 1) & 3;
+    if (sg.copied) CK(cudaEventSynchronize(sg.copied));
+    if (!sg.copied) CK(cudaEventCreateWithFlags(&sg.copied, cudaEventDisableTiming));
+    if (sg.cap < n_in + 24) {
+        if (sg.buf) cudaFreeHost(sg.buf);
+        sg.buf = nullptr;
+        sg.cap = 0;
+        CK(cudaMallocHost((void **)&sg.buf, (n_in + 24) * sizeof(double)));
+        sg.cap = n_in + 24;
     }
+    double *const hbuf = sg.buf;
     {
         double *h = hbuf;
         memset(h, 0, n_in * sizeof(double));
@@ -738,6 +750,7 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
         for (int b = 0; b < nb; ++b) hrot[b] = make_float2((float)cos(P->gantry[b]), (float)sin(P->gantry[b]));
         CK(cudaMemcpyAsync(base + o_rot, hrot, (size_t)nb * sizeof(float2), cudaMemcpyHostToDevice, st));
     }
+    CK(cudaEventRecord(sg.copied, st));
     CK(cudaMemsetAsync(d_denom, 0, 64, st));
 
     {

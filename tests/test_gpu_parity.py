@@ -468,6 +468,32 @@ def test_async_build_and_unsynchronised_run_match_the_synchronous_ones(L):
         np.testing.assert_allclose(s1, out[0][0], rtol=1e-4, atol=1e-6 * out[0][0].max())
 
 
+def test_async_builds_queued_behind_work_keep_their_inputs(L):
+    """Five plans of different models and fields built without host
+    synchronisation while a long run holds the stream: each plan equals the
+    synchronous build of its own inputs (the host staging buffers are not
+    reused before their copies have run)."""
+    import torch
+    wl = W.workload_full_10x10(10_000_000)       # a run of about 2 ms holds the stream
+    ph = L.lsm_phantom_create(wl.phantom)
+    cases = [(W.psr_model(6, 10, 0.25, seed=s), W.beams(W.square_field(f))) for s, f in
+             ((1, 4.0), (2, 10.0), (3, 6.0), (4, 8.0), (5, 2.0))]
+    want = []
+    for m, b in cases:
+        g = L.lsm_build_psl(m, b, 50_000)
+        want.append((g.info, g.denom, L.lsm_psl_copy(g, 0), L.lsm_psl_copy(g, 3)))
+    torch.cuda.synchronize()
+    t = L.lsm_tally_create(ph)
+    g0 = L.lsm_build_psl(wl.model, wl.beams, wl.n_hist // 2)
+    L.lsm_run(g0, ph, t, 5, L.RunOpts(n_batches=2, no_sync=True))      # queued, still running
+    got = [L.lsm_build_psl(m, b, 50_000, async_=True) for m, b in cases]
+    torch.cuda.synchronize()
+    for g, (info, denom, w0, c3) in zip(got, want):
+        assert g.info == info and g.denom == denom
+        np.testing.assert_array_equal(L.lsm_psl_copy(g, 0), w0)
+        np.testing.assert_array_equal(L.lsm_psl_copy(g, 3), c3)
+
+
 def test_async_build_reports_an_empty_plan_when_read(L):
     import torch
     wl = W.workload_full_10x10(10_000)
