@@ -357,6 +357,9 @@ lsm_status lsm_tally_create(const lsm_phantom *ph, const lsm_tally_desc *d, lsm_
             e = cudaMemcpyAsync(t->d_idx, d->idx3d, (size_t)nvox * 2,
                                 d->idx3d_mem == LSM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) break;
+            // a host array is read before returning, also when it is pinned
+            // (a copy from pinned memory would otherwise run later)
+            if (d->idx3d_mem == LSM_MEM_HOST && (e = cudaStreamSynchronize(st)) != cudaSuccess) break;
         }
         if ((e = cudaMemsetAsync(t->d_part, 0, (size_t)ncell * 4, st)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(t->d_batch, 0, (size_t)ncell * 8, st)) != cudaSuccess) break;
