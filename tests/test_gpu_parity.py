@@ -494,6 +494,40 @@ def test_async_builds_queued_behind_work_keep_their_inputs(L):
         np.testing.assert_array_equal(L.lsm_psl_copy(g, 3), c3)
 
 
+def test_runs_on_two_streams_match_serial_runs(L):
+    """Two dose calculations queued on two CUDA streams (phantom from host
+    arrays, unsynchronised plan build and run, read-back of each while the
+    other runs) give the results of the same calculations run one after the
+    other: counters equal, sums to FP32 atomic ordering."""
+    import torch
+    wl = W.workload_full_10x10(2_000_000)
+    n_plan = wl.n_hist // 4
+
+    def job(seed, stream):
+        ph = L.lsm_phantom_create(wl.phantom, stream=stream)
+        g = L.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True, stream=stream)
+        t = L.lsm_tally_create(ph, stream=stream)
+        L.lsm_run(g, ph, t, seed, L.RunOpts(n_batches=4, no_sync=True), stream=stream)
+        return ph, g, t, stream
+
+    def read(j):
+        ph, g, t, stream = j
+        d, s = L.lsm_dose(t, ph, 1.0, stream=stream)
+        led, st = L.lsm_tally_ledger(t, stream=stream)
+        return d, s, st
+
+    serial = [read(job(seed, torch.cuda.current_stream())) for seed in (41, 42)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    j0 = job(41, streams[0])
+    j1 = job(42, streams[1])
+    both = [read(j0), read(j1)]
+    for (d, s, st), (d0, s0, st0) in zip(both, serial):
+        for k in ("histories", "photons", "electrons", "rejected", "flights", "real", "esteps"):
+            assert st[k] == st0[k], k
+        np.testing.assert_allclose(d, d0, rtol=1e-4, atol=1e-6 * d0.max())
+        np.testing.assert_allclose(s, s0, rtol=1e-3, atol=1e-5 * s0.max())
+
+
 def test_async_build_reports_an_empty_plan_when_read(L):
     import torch
     wl = W.workload_full_10x10(10_000)
