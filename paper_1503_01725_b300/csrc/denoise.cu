@@ -807,10 +807,19 @@ lsm_status pool_or_up(const lsm_vol *in, const lsm_vol *out, bool up, cudaStream
 namespace lsm {
 namespace dn {
 
+void unet_drop_graph(lsm_unet *u)
+{
+    if (u->gexec) cudaGraphExecDestroy((cudaGraphExec_t)u->gexec);
+    u->gexec = nullptr;
+    u->g_warm = 0;
+    u->g_kernels = 0;
+}
+
 lsm_status unet_buffers(lsm_unet *u, int n, int d, int h, int w, cudaStream_t st)
 {
     if (u->arena && u->n == n && u->d == d && u->h == h && u->w == w) return LSM_OK;
     LSM_CUDA(cudaStreamSynchronize(st));
+    unet_drop_graph(u);                       // it holds the old buffers' addresses
     cudaFree(u->arena);
     cudaFree(u->dmax);
     u->arena = nullptr;
@@ -856,40 +865,86 @@ lsm_status unet_run(lsm_unet *u, const float *dose, const float *rho, float *out
     count_launch();
     timer_end(tk, st);
     LSM_CUDA(cudaGetLastError());
+    auto middle = [&](cudaStream_t s) -> lsm_status {
+        lsm_status r = LSM_OK;
+        auto conv = [&](int i) -> lsm_status {
+            const lsm_vol in = V[kConvIn[i]];
+            const lsm_vol o = sub(V[kConvOut[i]], 0, kLayers[i][1]);
+            return conv_forward(u->conv[i], &in, &o, 0, s);
+        };
+        auto pool = [&](int from, int to, int c) -> lsm_status {
+            const lsm_vol a = sub(V[from], 0, c);
+            return pool_or_up(&a, &V[to], false, s);
+        };
+        auto up = [&](int from, int to, int c_off) -> lsm_status {
+            const lsm_vol b = sub(V[to], c_off, V[from].c);
+            return pool_or_up(&V[from], &b, true, s);
+        };
+        if (!r) r = conv(0);
+        if (!r) r = conv(1);
+        if (!r) r = pool(S0, P1, kW0);
+        if (!r) r = conv(2);
+        if (!r) r = conv(3);
+        if (!r) r = pool(S1, P2, kW1);
+        if (!r) r = conv(4);
+        if (!r) r = conv(5);
+        if (!r) r = pool(S2, P3, kW2);
+        if (!r) r = conv(6);
+        if (!r) r = conv(7);
+        if (!r) r = up(B3, S2, kW2);
+        if (!r) r = conv(8);
+        if (!r) r = conv(9);
+        if (!r) r = up(D2, S1, kW1);
+        if (!r) r = conv(10);
+        if (!r) r = conv(11);
+        if (!r) r = up(D1, S0, kW0);
+        if (!r) r = conv(12);
+        if (!r) r = conv(13);
+        return r;
+    };
     lsm_status rc = LSM_OK;
-    auto conv = [&](int i) -> lsm_status {
-        const lsm_vol in = V[kConvIn[i]];
-        const lsm_vol o = sub(V[kConvOut[i]], 0, kLayers[i][1]);
-        return conv_forward(u->conv[i], &in, &o, 0, st);
-    };
-    auto pool = [&](int from, int to, int c) -> lsm_status {
-        const lsm_vol a = sub(V[from], 0, c);
-        return pool_or_up(&a, &V[to], false, st);
-    };
-    auto up = [&](int from, int to, int c_off) -> lsm_status {
-        const lsm_vol b = sub(V[to], c_off, V[from].c);
-        return pool_or_up(&V[from], &b, true, st);
-    };
-    if (!rc) rc = conv(0);
-    if (!rc) rc = conv(1);
-    if (!rc) rc = pool(S0, P1, kW0);
-    if (!rc) rc = conv(2);
-    if (!rc) rc = conv(3);
-    if (!rc) rc = pool(S1, P2, kW1);
-    if (!rc) rc = conv(4);
-    if (!rc) rc = conv(5);
-    if (!rc) rc = pool(S2, P3, kW2);
-    if (!rc) rc = conv(6);
-    if (!rc) rc = conv(7);
-    if (!rc) rc = up(B3, S2, kW2);
-    if (!rc) rc = conv(8);
-    if (!rc) rc = conv(9);
-    if (!rc) rc = up(D2, S1, kW1);
-    if (!rc) rc = conv(10);
-    if (!rc) rc = conv(11);
-    if (!rc) rc = up(D1, S0, kW0);
-    if (!rc) rc = conv(12);
-    if (!rc) rc = conv(13);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LSM_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (timing_enabled() || !u->g_warm || cap != cudaStreamCaptureStatusNone) {
+        // per-kernel timers need the direct launches; the first pass on new
+        // buffers runs directly too (one-time attribute and table set-up); a
+        // caller capturing its own graph gets the layers as its own nodes
+        rc = middle(st);
+        if (!rc) u->g_warm = 1;
+    } else {
+        if (!u->gexec) {
+            cudaStream_t cs = nullptr;
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            const int64_t c0 = lsm_launch_count();
+            cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            lsm_status r = LSM_OK;
+            if (e == cudaSuccess) {
+                r = middle(cs);
+                e = cudaStreamEndCapture(cs, &g);
+            }
+            const int64_t captured = lsm_launch_count() - c0;
+            add_launches(-captured);           // counted when replayed
+            if (e == cudaSuccess && !r && g) e = cudaGraphInstantiate(&ex, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (cs) cudaStreamDestroy(cs);
+            if (e == cudaSuccess && !r && ex) {
+                u->gexec = ex;
+                u->g_kernels = captured;
+            } else {
+                if (ex) cudaGraphExecDestroy(ex);
+                cudaGetLastError();
+                u->g_warm = 0;                 // capture failed: direct launches from now on
+            }
+        }
+        if (u->gexec) {
+            LSM_CUDA(cudaGraphLaunch((cudaGraphExec_t)u->gexec, st));
+            add_launches(u->g_kernels);
+        } else {
+            rc = middle(st);
+        }
+    }
     if (rc || !out) return rc;
     const int th = timer_begin(9, st);
     k_head<<<grid_1d(per * u->n), 256, 0, st>>>((const __nv_bfloat16 *)V[D0].data, V[D0].c_total, u->head, dose,
@@ -969,6 +1024,7 @@ void lsm_unet_destroy(lsm_unet *u)
 {
     if (!u) return;
     cudaDeviceSynchronize();
+    dn::unet_drop_graph(u);
     for (int i = 0; i < 14; ++i) dn::conv_destroy(u->conv[i]);
     dn::train_free(u->train);
     cudaFree(u->params);

@@ -125,11 +125,18 @@ struct lsm_unet {
     float *io;                    // device staging for host calls: dose, rho, out
     size_t io_cap;
     UNetTrain *train;
+    // the layers between input packing and the output head (convolutions,
+    // pooling, upsampling) touch only the activation buffers: captured once
+    // per buffer allocation as a CUDA graph and replayed
+    void *gexec;                  // cudaGraphExec_t, or null
+    int g_warm;                   // a direct pass has run on these buffers (one-time set-up done)
+    int64_t g_kernels;            // kernels in the graph
 };
 
 namespace lsm {
 namespace dn {
 lsm_status unet_buffers(lsm_unet *u, int n, int d, int h, int w, cudaStream_t st);
+void unet_drop_graph(lsm_unet *u);
 lsm_status unet_run(lsm_unet *u, const float *dose, const float *rho, float *out, cudaStream_t st);
 lsm_status pack_layer(lsm_unet *u, int i, cudaStream_t st);
 void train_free(UNetTrain *t);

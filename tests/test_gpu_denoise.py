@@ -242,6 +242,46 @@ def test_training_reduces_loss(L):
     assert err < losses[0]
 
 
+def test_replayed_forward_graph_follows_weights_and_shapes(L):
+    """The layers between input packing and the head run as a captured CUDA
+    graph from the second forward on: repeated forwards are identical; after
+    training steps change the weights, the replayed graph gives what a fresh
+    network with the new parameters gives; a new shape rebuilds it."""
+    import torch
+    rng = np.random.default_rng(5)
+    n, d, h, w = 1, 16, 16, 24
+    dose = rng.random((n, d, h, w)).astype(np.float32)
+    rho = (0.5 + rng.random((n, d, h, w))).astype(np.float32)
+    target = (0.8 * dose).astype(np.float32)
+    net = L.lsm_unet_create(DN.init_params(9, head_scale=0.05))
+    outs = [L.lsm_unet_forward(net, dose, rho) for _ in range(3)]   # direct, captured + replayed, replayed
+    np.testing.assert_array_equal(outs[1], outs[0])
+    np.testing.assert_array_equal(outs[2], outs[0])
+    t = [torch.tensor(a, device="cuda") for a in (dose, rho, target)]
+    for _ in range(3):
+        L.lsm_unet_train_step(net, *t, lr=1e-2)
+    after = L.lsm_unet_forward(net, dose, rho)
+    fresh = L.lsm_unet_create(L.lsm_unet_params(net))
+    np.testing.assert_array_equal(after, L.lsm_unet_forward(fresh, dose, rho))
+    assert np.abs(after - outs[0]).max() > 0
+    # a caller capturing the forward into its own graph gets the same result
+    s_ = torch.cuda.Stream()
+    dd, rr = torch.tensor(dose, device="cuda"), torch.tensor(rho, device="cuda")
+    o_ = torch.empty_like(dd)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s_):
+        L.lsm_unet_forward(net, dd, rr, out=o_, stream=s_)
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(o_.cpu().numpy(), after)
+    # another shape: new buffers, a new graph
+    d2 = rng.random((2, 8, 16, 16)).astype(np.float32)
+    r2 = np.ones_like(d2)
+    a2 = [L.lsm_unet_forward(net, d2, r2) for _ in range(3)]
+    np.testing.assert_array_equal(a2[2], a2[0])
+    np.testing.assert_array_equal(L.lsm_unet_forward(net, dose, rho), after)
+
+
 def test_gamma_and_dose_error_match_oracle(L):
     from oracle import gamma as G
     rng = np.random.default_rng(23)
