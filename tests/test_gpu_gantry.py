@@ -80,3 +80,24 @@ def test_prostate_and_hn_layouts_run(L):
         # the beams converge at the isocentre: its dose exceeds the body's mean dose
         body = wl.phantom.rho > 0.5
         assert c > 1.5 * d[body].mean(), wl.name
+
+
+def test_sixteen_beams_the_maximum(L):
+    # sixteen rotated beams (the limit): the plan's counts bit-exact against the
+    # oracle's Eq. 3 over all beams, the run's counters as the oracle's
+    model = W.psr_model(6, 10, 0.25, seed=2)
+    beams = W.gantry_beams([k * 22.5 for k in range(16)], 4.0)
+    ph = W.pelvis_phantom(40, 24, 32, 1.0)
+    n = 32_000
+    g = L.lsm_build_psl(model, beams, n)
+    plan = O.Plan(model, beams, n)
+    np.testing.assert_array_equal(L.lsm_psl_copy(g, 3), plan.count)
+    s1, s2, b, led, st = _gpu_run(L, model, beams, ph, n, 13, 4)
+    r = O.run(plan, ph, 13, n_batches=4, electron_mode=1)
+    for k in ("histories", "rejected"):
+        assert st[k] == r["stats"][k], k
+    for k in ("photons", "electrons", "missed"):
+        assert abs(st[k] - r["stats"][k]) <= 1e-3 * st["histories"] + 2, k
+    np.testing.assert_allclose(led["source"], r["ledger"]["source"], rtol=1e-6)
+    with pytest.raises(L.LSMError, match="LSM_ERR_ARG"):
+        L.lsm_build_psl(model, W.gantry_beams([k * 20.0 for k in range(17)], 4.0), n)
