@@ -1432,9 +1432,10 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     // iterations inside one batch.
     const int64_t plan = P->plan_size;
     const bool multi = plan < (int64_t)o.chunk;
-    const int bpi = multi ? (int)std::min<int64_t>(o.n_batches, (int64_t)o.chunk / plan) : 1;
+    // (at most 255 batches per iteration: a particle carries its batch slot in
+    // 8 bits; more batches take more iterations)
+    const int bpi = multi ? (int)std::min<int64_t>(std::min<int64_t>(o.n_batches, 255), (int64_t)o.chunk / plan) : 1;
     const int64_t chunk = multi ? (int64_t)bpi * plan : (int64_t)o.chunk;
-    if (bpi > 255) return set_arg_error("lsm_run: more than 255 batches per iteration");
     Workspace W = {};
     unsigned long long ovf = 0;
     rc = ensure_slots(t, bpi, st);

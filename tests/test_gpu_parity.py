@@ -528,6 +528,29 @@ def test_runs_on_two_streams_match_serial_runs(L):
         np.testing.assert_allclose(s, s0, rtol=1e-3, atol=1e-5 * s0.max())
 
 
+def test_more_batches_than_an_iteration_holds(L):
+    """300 batches of a small plan: an iteration holds at most 255 batch slots
+    (a particle carries its slot in 8 bits), so the run takes 255 + 45; the
+    result equals the same run with one batch per iteration."""
+    wl = W.workload_full_10x10(300 * 1000)
+    ph = L.lsm_phantom_create(wl.phantom)
+    g = L.lsm_build_psl(wl.model, wl.beams, 1000)
+    out = []
+    for chunk in (0, 1000):                 # library default (2^23): 255 + 45; one batch per iteration
+        t = L.lsm_tally_create(ph)
+        assert L.lsm_run(g, ph, t, 3, L.RunOpts(n_batches=300, chunk=chunk)) == L.LSM_OK
+        s1, s2, nb = L.lsm_tally_read(t)
+        led, st = L.lsm_tally_ledger(t)
+        out.append((s1, s2, nb, st))
+    (a1, a2, na, sa), (b1, b2, nb_, sb) = out
+    assert na == nb_ == 300
+    for k in ("histories", "photons", "electrons", "rejected", "flights", "real", "esteps"):
+        assert sa[k] == sb[k], k
+    assert sa["histories"] == 300_000
+    np.testing.assert_allclose(a1, b1, rtol=1e-4, atol=1e-6 * b1.max())
+    np.testing.assert_allclose(a2, b2, rtol=1e-3, atol=1e-6 * b2.max())
+
+
 def test_async_build_reports_an_empty_plan_when_read(L):
     import torch
     wl = W.workload_full_10x10(10_000)
