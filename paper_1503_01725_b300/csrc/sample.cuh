@@ -82,13 +82,19 @@ __device__ __forceinline__ void sample_history(const SampleParams &P, uint32_t k
     const int s = en.stype, e = en.ebin;
     const float E = P.e_lo[s] + ((float)e + u01(a.z)) * P.de[s];
 
-    // ring that holds the sampled radius (S4)
+    // ring that holds the sampled radius (S4): the largest kk < n_r with
+    // r2 >= (kk pf)^2, both products rounded as written. The test is monotone
+    // in kk, so an estimate from r / pf is corrected by single steps until it
+    // is the largest kk passing (the estimate only saves steps)
     const float r2 = __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y));
-    int ring = 0;
-    for (int kk = 1; kk < P.n_r; ++kk) {
+    auto inside = [&](int kk) {
         const float ek = __fmul_rn((float)kk, pf);
-        if (r2 >= __fmul_rn(ek, ek)) ring = kk;
-    }
+        return r2 >= __fmul_rn(ek, ek);
+    };
+    int ring = r2 > 0.0f ? (int)__fdividef(r2 * rsqrtf(r2), pf) : 0;
+    ring = min(max(ring, 0), P.n_r - 1);
+    while (ring + 1 < P.n_r && inside(ring + 1)) ++ring;
+    while (ring > 0 && !inside(ring)) --ring;
 
     // Box-Muller pair
     const float rad = sqrtf(-2.0f * __logf(u01(b.x)));
