@@ -105,12 +105,14 @@ __device__ __forceinline__ void sample_history(const SampleParams &P, uint32_t k
     // PSR index carried for the basis tally
     const int R = en.fixed_ring >= 0 ? en.fixed_ring : (b.z < en.thr ? (int)en.r0 : (int)en.r0 + 1);
 
+    // radius and its reciprocal from one reciprocal square root
+    const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    const float r = r2 * rinv;
     float u0, v0, w0;
     int comp = -1;
     if (s == 0) {
         // Eq. 4-5: Gaussian focal spot, direction to (r, 0, z_phsp) in the local frame
         const float xs = P.sigma_s * n1, ys = P.sigma_s * n2;
-        const float r = sqrtf(x * x + y * y);
         const float dxs = r - xs;
         const float inv = rsqrtf(dxs * dxs + ys * ys + P.z_phsp * P.z_phsp);
         u0 = dxs * inv; v0 = -ys * inv; w0 = P.z_phsp * inv;
@@ -134,9 +136,8 @@ __device__ __forceinline__ void sample_history(const SampleParams &P, uint32_t k
         u0 = ta * inv; v0 = tb * inv; w0 = inv;
     }
     // rotate the local frame (u along the radius) by the polar angle of (x, y)
-    const float r = sqrtf(x * x + y * y);
     float c = 1.0f, sv = 0.0f;
-    if (r > 0.0f) { const float ir = 1.0f / r; c = x * ir; sv = y * ir; }
+    if (r2 > 0.0f) { c = x * rinv; sv = y * rinv; }
     const float u = u0 * c - v0 * sv, v = u0 * sv + v0 * c, w = w0;
 
     // jaw rejection at the upper jaw surfaces, straight flight to the phantom
