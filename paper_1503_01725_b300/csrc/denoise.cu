@@ -905,12 +905,12 @@ lsm_status unet_run(lsm_unet *u, const float *dose, const float *rho, float *out
     lsm_status rc = LSM_OK;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     LSM_CUDA(cudaStreamIsCapturing(st, &cap));
-    if (timing_enabled() || !u->g_warm || cap != cudaStreamCaptureStatusNone) {
+    if (timing_enabled() || u->g_warm != 1 || cap != cudaStreamCaptureStatusNone) {
         // per-kernel timers need the direct launches; the first pass on new
         // buffers runs directly too (one-time attribute and table set-up); a
         // caller capturing its own graph gets the layers as its own nodes
         rc = middle(st);
-        if (!rc) u->g_warm = 1;
+        if (!rc && u->g_warm == 0) u->g_warm = 1;
     } else {
         if (!u->gexec) {
             cudaStream_t cs = nullptr;
@@ -935,7 +935,7 @@ lsm_status unet_run(lsm_unet *u, const float *dose, const float *rho, float *out
             } else {
                 if (ex) cudaGraphExecDestroy(ex);
                 cudaGetLastError();
-                u->g_warm = 0;                 // capture failed: direct launches from now on
+                u->g_warm = -1;                // capture failed: direct launches for these buffers
             }
         }
         if (u->gexec) {

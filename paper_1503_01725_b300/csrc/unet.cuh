@@ -129,7 +129,8 @@ struct lsm_unet {
     // pooling, upsampling) touch only the activation buffers: captured once
     // per buffer allocation as a CUDA graph and replayed
     void *gexec;                  // cudaGraphExec_t, or null
-    int g_warm;                   // a direct pass has run on these buffers (one-time set-up done)
+    int g_warm;                   // 1: a direct pass has run on these buffers (one-time set-up done);
+                                  // -1: capture failed, launch directly
     int64_t g_kernels;            // kernels in the graph
 };
 
