@@ -795,7 +795,13 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "traffic_unit": "bytes per step",
                 "peak_source": f"{hbm_kind} hbm_gbs",
-                "algorithmic_bytes_per_step": units[dom]}
+                "algorithmic_bytes_per_step": units[dom],
+                # every kernel group of the step on the same terms (algorithmic
+                # bytes per step over its event-timed time per step)
+                "by_kernel": {k: {"ms_per_step": per_step[k], "algorithmic_bytes_per_step": units[k],
+                                  "achieved": units[k] / (per_step[k] / 1e3) / 1e9,
+                                  "frac": units[k] / (per_step[k] / 1e3) / 1e9 / hbm}
+                              for k in ("sample", "photon", "electron") if per_step.get(k, 0) > 0}}
 
     # the tally-update ceiling: FP32 atomics to scattered cells of a tally the
     # size of this run's batch slots, against the transport's step rates
