@@ -263,6 +263,22 @@ lsm_status lsm_tally_read(lsm_tally *t, double *s1, double *s2, lsm_mem mem, int
  * Errors: LSM_ERR_ARG for a NULL tally or S1/S2, or n_batches < 0. */
 lsm_status lsm_tally_load(lsm_tally *t, const double *s1, const double *s2, int32_t n_batches,
                           const double ledger[4], const int64_t stats[10], lsm_mem mem, lsm_stream stream);
+/*
+ * lsm_tally_history_ledger -- a test mode: attach (ledger != NULL) or detach
+ * (NULL) a per-history energy ledger to a dose (mode 0) tally. While attached,
+ * lsm_run on this tally adds, for each history g with 0 <= g - first_history <
+ * n_hist (h = g - first_history), the energy of its source particle to
+ * ledger[2h] and every deposited, escaped or jaw-rejected energy of the
+ * particles it leads to (all generations) to ledger[2h + 1], so that
+ * ledger[2h + 1] = ledger[2h] checks energy conservation history by history.
+ * ledger: device memory, FP64 [n_hist][2], owned and zeroed by the caller,
+ * 8-byte aligned; it must stay valid while attached. The run uses separate
+ * kernel instances (graph replay off); other calls (lsm_transport,
+ * lsm_pslfile_run) ignore the ledger. Errors: LSM_ERR_ARG for a NULL tally, a
+ * basis tally, n_hist < 1, first_history < 0 or a misaligned buffer.
+ */
+lsm_status lsm_tally_history_ledger(lsm_tally *t, double *ledger, int64_t n_hist, int64_t first_history);
+
 /* ledger (MeV): source, rejected, escaped (incl. missed), deposited.
  * stats: histories, accepted photons, accepted electrons, rejected, missed,
  * Woodcock flights, real photon interactions, electron steps, step-cap hits,

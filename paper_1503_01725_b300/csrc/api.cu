@@ -460,6 +460,24 @@ lsm_status lsm_tally_load(lsm_tally *t, const double *s1, const double *s2, int3
     return LSM_OK;
 }
 
+lsm_status lsm_tally_history_ledger(lsm_tally *t, double *ledger, int64_t n_hist, int64_t first_history)
+{
+    if (!t) return set_arg_error("lsm_tally_history_ledger: NULL tally");
+    if (!ledger) {
+        t->hl = nullptr;
+        t->hl_n = 0;
+        t->hl_g0 = 0;
+        return LSM_OK;
+    }
+    if (t->mode != 0) return set_arg_error("lsm_tally_history_ledger: needs a dose (mode 0) tally");
+    if (n_hist < 1 || first_history < 0 || (((uintptr_t)ledger) & 7))
+        return set_arg_error("lsm_tally_history_ledger: n_hist >= 1, first_history >= 0, 8-byte aligned buffer");
+    t->hl = ledger;
+    t->hl_n = n_hist;
+    t->hl_g0 = (uint64_t)first_history;
+    return LSM_OK;
+}
+
 lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], lsm_stream stream)
 {
     if (!t) return set_arg_error("lsm_tally_ledger: NULL tally");

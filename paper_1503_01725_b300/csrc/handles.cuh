@@ -123,4 +123,7 @@ struct lsm_tally {
     void *gstream;        // stream of graph capture and replay, and its two events
     void *gev[2];
     void *gtimers;        // event timers inside the graph (when captured with timing on)
+    double *hl;           // per-history energy ledger (test mode; caller's device buffer) or null
+    uint64_t hl_g0;       // history of its entry 0
+    int64_t hl_n;         // histories it holds
 };

@@ -57,6 +57,11 @@ struct TP {
     RunStats *stats;
     IterCounters *cnt;
     int ctas_per_sm;           // transport grid: CTAs per SM (0: as many as fit)
+    // per-history energy ledger (MODE 2 kernels only): hl[2h] source energy,
+    // hl[2h + 1] deposited + escaped + rejected energy of history hl_g0 + h
+    double *hl;
+    uint64_t hl_g0;
+    int64_t hl_n;
 };
 
 constexpr int kTableBytes = 2 * kGrid * 16 + kGrid * 4 + kKnE * kKnU * 4;   // 52 KB: photons
@@ -175,12 +180,26 @@ struct Acc {
     unsigned long long flights, real, esteps, cap;
 };
 
+// MODE 0: dose tally; MODE 1: basis tally; MODE 2: dose tally plus the
+// per-history energy ledger (a test mode: its own kernel instances, so the
+// ledger costs the other modes nothing)
 template <int MODE>
-__device__ __forceinline__ void deposit(const TP &T, Acc &A, int vox, float e, uint32_t pb)
+__device__ __forceinline__ void hl_add(const TP &T, uint32_t glo, uint32_t ghi, int which, double e)
+{
+    if constexpr (MODE == 2) {
+        const uint64_t h = ((((uint64_t)ghi) << 32) | glo) - T.hl_g0;
+        if (h < (uint64_t)T.hl_n) atomicAdd(T.hl + 2 * h + which, e);
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void deposit(const TP &T, Acc &A, int vox, float e, uint32_t pb, uint32_t glo,
+                                        uint32_t ghi)
 {
     A.dep32 += e;
+    hl_add<MODE>(T, glo, ghi, 1, e);
     float *slice = T.part + (size_t)pb_slot(pb) * T.ncell;
-    if (MODE == 0) {
+    if (MODE != 1) {
         atomicAdd(slice + vox, e);
     } else {
         // rows, PSRs and beams are checked so that caller-supplied particles
@@ -274,13 +293,13 @@ __device__ __forceinline__ void spawn_electron(const TP &T, Acc &A, const Queue 
                                                float u, float v, float w, uint32_t sid, int vox)
 {
     if (T.electron_mode == 0 || Te < kCutE) {
-        deposit<MODE>(T, A, vox, Te, p.pb);
+        deposit<MODE>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
         return;
     }
     const uint32_t slot = push_slot(&T.cnt->n[2]);
     if (slot >= eq.cap) {
         atomicAdd(&T.stats->c[9], 1ull);
-        deposit<MODE>(T, A, vox, Te, p.pb);
+        deposit<MODE>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
         return;
     }
     store_part(eq, slot, p.x, p.y, p.z, u, v, w, Te, p.rng.glo, p.rng.ghi, sid, p.pb);
@@ -293,9 +312,9 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
                             const Queue &eq, const Queue *pq, Pend &pe, bool &pend)
 {
     int vox = voxel(T, p.x, p.y, p.z);
-    if (vox < 0) { A.esc += p.E; return false; }
-    if (p.E < kCutG) { deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
-    if (++p.steps > T.max_steps) { A.cap++; deposit<MODE>(T, A, vox, p.E, p.pb); return false; }
+    if (vox < 0) { A.esc += p.E; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
+    if (p.E < kCutG) { deposit<MODE>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
+    if (++p.steps > T.max_steps) { A.cap++; deposit<MODE>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
     const uint4 r = p.rng.next();
     int ti;
     float tf;
@@ -309,7 +328,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     // the block of the next draw (next flight or the Compton block) does not
     // depend on the density: compute it while the load is in flight
     p.rng.prefetch();
-    if (vox < 0) { A.esc += p.E; return false; }
+    if (vox < 0) { A.esc += p.E; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
     const int m = rm < 0.0f;
     const float rho = fabsf(rm);
     const float4 c = lerp4(xs + m * kGrid, ti, tf);
@@ -338,7 +357,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
             pe = Pend{p.x, p.y, p.z, ex, ey, ez, Te, p.rng.child_id(0), vox};
             pend = true;
         } else {
-            deposit<MODE>(T, A, vox, Te, p.pb);
+            deposit<MODE>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
         }
         p.E = E1; p.u = u; p.v = v; p.w = w;
         return true;
@@ -349,7 +368,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
             pe = Pend{p.x, p.y, p.z, p.u, p.v, p.w, p.E, p.rng.child_id(0), vox};
             pend = true;
         } else {
-            deposit<MODE>(T, A, vox, p.E, p.pb);
+            deposit<MODE>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi);
         }
         return false;
     }
@@ -373,7 +392,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
             store_part(*pq, slot, p.x, p.y, p.z, sg * ax, sg * ay, sg * az, kMe, p.rng.glo, p.rng.ghi,
                        p.rng.child_id(2 + h), p.pb);
         else
-            deposit<MODE>(T, A, vox, kMe, p.pb);
+            deposit<MODE>(T, A, vox, kMe, p.pb, p.rng.glo, p.rng.ghi);
     }
     return false;
 }
@@ -385,7 +404,7 @@ template <int MODE>
 __device__ __forceinline__ void edep(const TP &T, Acc &A, Part &p, int vox, float e)
 {
     if (vox == p.dv) { p.de += e; return; }
-    if (p.dv >= 0) deposit<MODE>(T, A, p.dv, p.de, p.pb);
+    if (p.dv >= 0) deposit<MODE>(T, A, p.dv, p.de, p.pb, p.rng.glo, p.rng.ghi);
     p.dv = vox;
     p.de = e;
 }
@@ -393,7 +412,7 @@ __device__ __forceinline__ void edep(const TP &T, Acc &A, Part &p, int vox, floa
 template <int MODE>
 __device__ __forceinline__ void eflush(const TP &T, Acc &A, Part &p)
 {
-    if (p.dv >= 0) deposit<MODE>(T, A, p.dv, p.de, p.pb);
+    if (p.dv >= 0) deposit<MODE>(T, A, p.dv, p.de, p.pb, p.rng.glo, p.rng.ghi);
     p.dv = -1;
 }
 
@@ -403,7 +422,7 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
 {
     // (reusing the previous step's end voxel here measured 1.6x slower)
     const int vox = voxel(T, p.x, p.y, p.z);
-    if (vox < 0) { eflush<MODE>(T, A, p); A.esc += p.E; return false; }
+    if (vox < 0) { eflush<MODE>(T, A, p); A.esc += p.E; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
     if (p.E < kCutE) { edep<MODE>(T, A, p, vox, p.E); eflush<MODE>(T, A, p); return false; }
     if (++p.steps > T.max_steps) {
         A.cap++;
@@ -429,7 +448,7 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
     const float hs = 0.5f * ds;
     const int vm = voxel(T, p.x + hs * p.u, p.y + hs * p.v, p.z + hs * p.w);
     if (vm >= 0) edep<MODE>(T, A, p, vm, dE);
-    else A.esc += dE;
+    else { A.esc += dE; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, dE); }
     A.esteps++;
     const float E0 = p.E;
     p.x += ds * p.u; p.y += ds * p.v; p.z += ds * p.w;
@@ -594,7 +613,7 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
                                    pb_keep);
                     } else {
                         atomicAdd(&T.stats->c[9], 1ull);
-                        deposit<MODE>(T, A, pe.vox, pe.E, pb_keep);
+                        deposit<MODE>(T, A, pe.vox, pe.E, pb_keep, p.rng.glo, p.rng.ghi);
                         A.dep += A.dep32;
                         A.dep32 = 0.0f;
                     }
@@ -699,8 +718,10 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
         const int64_t ek = find_entry_warp(S.sp.start, n_ent, hpos, valid);
         if (valid) {
             sample_history(S.sp, k0, k1, S.g0 + (uint64_t)i, hpos, S.z_rel, o, ek);
+            const uint64_t gh = S.g0 + (uint64_t)i;
             src += o.E;
-            if (!o.accepted) { rej += o.E; nrej++; }
+            hl_add<MODE>(T, (uint32_t)gh, (uint32_t)(gh >> 32), 0, o.E);
+            if (!o.accepted) { rej += o.E; nrej++; hl_add<MODE>(T, (uint32_t)gh, (uint32_t)(gh >> 32), 1, o.E); }
             else {
                 if (!S.sp.rotated) {
                     lx = o.x - S.x0; ly = o.y - S.y0;
@@ -710,7 +731,7 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
                     in = enter_box(S, T, o, lx, ly, lz, du, dv, dw);
                     o.u = du; o.v = dv; o.w = dw;
                 }
-                if (!in) { esc += o.E; nmiss++; }
+                if (!in) { esc += o.E; nmiss++; hl_add<MODE>(T, (uint32_t)gh, (uint32_t)(gh >> 32), 1, o.E); }
             }
         }
         const bool is_e = o.stype == 2;
@@ -734,7 +755,7 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
             } else {
                 nel++;
                 if (local_e) {
-                    deposit<MODE>(T, A, voxel(T, lx, ly, lz), o.E, pb);
+                    deposit<MODE>(T, A, voxel(T, lx, ly, lz), o.E, pb, (uint32_t)g, (uint32_t)(g >> 32));
                 } else {
                     store_part(eq, be + __popc(me & lt), lx, ly, lz, o.u, o.v, o.w, o.E, (uint32_t)g,
                                (uint32_t)(g >> 32), 1u, pb);
@@ -828,7 +849,7 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
             } else {
                 nel++;
                 if (local_e)
-                    deposit<MODE>(T, A, voxel(T, lx, ly, lz), P.E[i], pb);
+                    deposit<MODE>(T, A, voxel(T, lx, ly, lz), P.E[i], pb, 0u, 0u);
                 else
                     store_part(eq, be + __popc(me & lt), lx, ly, lz, P.u[i], P.v[i], P.w[i], P.E[i],
                                (uint32_t)g, (uint32_t)(g >> 32), 1u, pb);
@@ -922,7 +943,7 @@ __global__ void __launch_bounds__(256) k_pslfile_enqueue(const PslRec *__restric
             } else {
                 nel++;
                 if (local_e)
-                    deposit<MODE>(T, A, voxel(T, lx, ly, 0.0f), E, pb);
+                    deposit<MODE>(T, A, voxel(T, lx, ly, 0.0f), E, pb, 0u, 0u);
                 else
                     store_part(eq, be + __popc(me & lt), lx, ly, 0.0f, u, v, w, E, (uint32_t)g, (uint32_t)(g >> 32),
                                1u, pb);
@@ -1142,6 +1163,9 @@ cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t, 
 TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, const uint32_t *key, IterCounters *cnt)
 {
     TP T;
+    T.hl = t->hl;
+    T.hl_g0 = t->hl_g0;
+    T.hl_n = t->hl_n;
     T.rhomat = ph->d_rhomat;
     T.nx = ph->nx; T.ny = ph->ny; T.nz = ph->nz;
     T.inv_dx = (float)(1.0 / ph->dx); T.inv_dy = (float)(1.0 / ph->dy); T.inv_dz = (float)(1.0 / ph->dz);
@@ -1424,6 +1448,10 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     if (t->nvox != (int64_t)ph->nx * ph->ny * ph->nz) return set_arg_error("lsm_run: tally of another phantom");
     if (t->mode == 1 && (t->n_beams != P->n_beams || t->n_psr != 3 * P->n_e * P->n_r))
         return set_arg_error("lsm_run: basis tally shape does not match the plan");
+    // a per-history energy ledger (test mode) selects the MODE 2 kernels, run
+    // directly (a captured graph holds the kernels of one mode)
+    const int kmode = t->mode == 1 ? 1 : (t->hl ? 2 : 0);
+    if (t->hl) o.use_graph = 0;
     // Iteration size. The paper iterates M histories at a time (Sec. 2.1.3);
     // B300 keeps ~2e5 lanes resident, so an iteration should hold millions of
     // histories for its longest tracks not to dominate. Plans smaller than
@@ -1450,22 +1478,24 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     S.x0 = (float)ph->x0; S.y0 = (float)ph->y0;
     S.z0 = (float)ph->z0; S.lz = (float)(ph->nz * ph->dz);
     S.plan = plan;
-    static int gs0 = 0, gs1 = 0;
+    static int gs0 = 0, gs1 = 0, gs2 = 0;
     if (!gs0) gs0 = grid_for((const void *)k_sample_queue<0>, 256, 0);
     if (!gs1) gs1 = grid_for((const void *)k_sample_queue<1>, 256, 0);
+    if (!gs2) gs2 = grid_for((const void *)k_sample_queue<2>, 256, 0);
     auto iteration = [&](uint64_t g0, int64_t h0, int64_t n) -> lsm_status {
         S.g0 = g0;
         S.h0 = h0;
         S.n = n;
         LSM_CUDA(cudaMemsetAsync(W.cnt, 0, sizeof(IterCounters), st));
-        const int gs = (int)std::min<int64_t>((S.n + 255) / 256, t->mode == 0 ? gs0 : gs1);
+        const int gs = (int)std::min<int64_t>((S.n + 255) / 256, kmode == 0 ? gs0 : (kmode == 1 ? gs1 : gs2));
         const int tk = timer_begin(1, st);
-        if (t->mode == 0) k_sample_queue<0><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
-        else k_sample_queue<1><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
+        if (kmode == 0) k_sample_queue<0><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
+        else if (kmode == 1) k_sample_queue<1><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
+        else k_sample_queue<2><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
         count_launch();
         timer_end(tk, st);
         LSM_CUDA(cudaGetLastError());
-        return t->mode == 0 ? drain<0>(T, W, t, st) : drain<1>(T, W, t, st);
+        return kmode == 0 ? drain<0>(T, W, t, st) : (kmode == 1 ? drain<1>(T, W, t, st) : drain<2>(T, W, t, st));
     };
     // the whole run's launch sequence (no host synchronisation inside)
     auto enqueue = [&]() -> lsm_status {

@@ -151,6 +151,7 @@ _EXPORTS = {
     "lsm_dose_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, _dp,
                                  C.c_void_p]),
     "lsm_l2_atomic_peak": (C.c_int, [C.c_int64, C.c_int32, _dp, C.c_void_p]),
+    "lsm_tally_history_ledger": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
     "lsm_curve_compare": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double,
                                     C.c_int32, C.c_double, C.c_int, _dp, C.c_void_p]),
     "lsm_pslfile_write": (C.c_int, [C.c_void_p, C.c_uint64, C.c_char_p, C.POINTER(C.c_int64), C.c_void_p]),
@@ -406,6 +407,22 @@ def lsm_tally_create(ph: PhantomHandle, mode: int = 0, idx3d=None, n_rows: int =
     t.mode, t.n_rows, t.n_psr, t.n_beams = mode, n_rows, n_psr, n_beams
     t.ncell = ph.desc.nvox if mode == 0 else n_beams * n_rows * n_psr
     return t
+
+
+def lsm_tally_history_ledger(t: Tally, buf=None, first_history: int = 0):
+    """Test mode: attach a per-history energy ledger (a zeroed CUDA float64
+    tensor of shape [n_hist, 2]: source energy, then deposited + escaped +
+    rejected energy of history first_history + h) to a dose tally; None
+    detaches it."""
+    if buf is None:
+        _check(_lib.lsm_tally_history_ledger(t.ptr, None, 0, 0), "lsm_tally_history_ledger")
+        t.hl = None
+        return
+    assert buf.is_cuda and buf.dtype.is_floating_point and buf.element_size() == 8 and buf.is_contiguous()
+    assert buf.dim() == 2 and buf.shape[1] == 2
+    _check(_lib.lsm_tally_history_ledger(t.ptr, buf.data_ptr(), buf.shape[0], int(first_history)),
+           "lsm_tally_history_ledger")
+    t.hl = buf                                   # kept alive while attached
 
 
 def lsm_tally_reset(t: Tally, stream=None):

@@ -626,6 +626,49 @@ def test_checkpoint_and_resume_equal_the_uninterrupted_run(L):
         L.lsm_run(g, ph, t2, 21, L.RunOpts(n_batches=1, first_batch=-1))
 
 
+def test_energy_is_conserved_history_by_history(L):
+    """Per-history ledger (test mode): for every history of a three-sub-source
+    CSDA run on a heterogeneous phantom, the deposited + escaped + rejected
+    energy of all its particles equals its source particle's energy (FP32
+    transport arithmetic: within 1e-4); totals equal the run ledger's; the
+    ledger kernels tally as the production ones (same counters, same dose to
+    FP32 atomic order)."""
+    import torch
+    wl = W.workload_full_10x10(40_000)
+    ph = W.pelvis_phantom(40, 24, 32, 1.0)
+    phh = L.lsm_phantom_create(ph)
+    g = L.lsm_build_psl(wl.model, W.gantry_beams([0.0, 120.0], 8.0), 20_000)
+    nb = 2
+    t = L.lsm_tally_create(phh)
+    buf = torch.zeros((20_000 * nb, 2), dtype=torch.float64, device="cuda")
+    L.lsm_tally_history_ledger(t, buf, first_history=0)
+    assert L.lsm_run(g, phh, t, 9, L.RunOpts(n_batches=nb)) == L.LSM_OK
+    hl = buf.cpu().numpy()
+    src, acc = hl[:, 0], hl[:, 1]
+    assert (src > 0).all()
+    np.testing.assert_allclose(acc, src, rtol=1e-4, atol=0)
+    led, st = L.lsm_tally_ledger(t)
+    assert abs(src.sum() / led["source"] - 1) < 1e-9
+    assert abs(acc.sum() / (led["rejected"] + led["escaped"] + led["deposited"]) - 1) < 1e-6
+    s1, _, _ = L.lsm_tally_read(t)
+    t2 = L.lsm_tally_create(phh)
+    L.lsm_run(g, phh, t2, 9, L.RunOpts(n_batches=nb))
+    r1, _, _ = L.lsm_tally_read(t2)
+    led2, st2 = L.lsm_tally_ledger(t2)
+    for k in ("histories", "photons", "electrons", "rejected", "missed", "flights", "real", "esteps"):
+        assert st[k] == st2[k], k
+    np.testing.assert_allclose(s1, r1, rtol=1e-4, atol=1e-6 * r1.max())
+    # detached: the tally runs the production kernels again
+    L.lsm_tally_history_ledger(t, None)
+    L.lsm_tally_reset(t)
+    assert L.lsm_run(g, phh, t, 9, L.RunOpts(n_batches=nb)) == L.LSM_OK
+    with pytest.raises(L.LSMError, match="LSM_ERR_ARG"):
+        idx, n_rows = W.commissioning_index(W.water_phantom(16, 16, 16, 0.5))
+        tb = L.lsm_tally_create(L.lsm_phantom_create(W.water_phantom(16, 16, 16, 0.5)), mode=1, idx3d=idx,
+                                n_rows=n_rows, n_psr=300)
+        L.lsm_tally_history_ledger(tb, buf)
+
+
 def test_l2_atomic_peak(L):
     # the tally-update ceiling the bench reports transport step rates against:
     # a finite rate well above the transport's own steps per second
