@@ -601,6 +601,18 @@ lsm_status lsm_curve_compare(const float *pos, const float *calc, const float *m
 lsm_status lsm_l2_atomic_peak(int64_t n_cells, int32_t reps, double *atomics_per_s, lsm_stream stream);
 
 /*
+ * lsm_philox_blocks -- the random-number contract (Philox4x32-10, Salmon et
+ * al., SC 2011) as the device evaluates it, for checking against other
+ * implementations: out[4 i .. 4 i + 3] = the block at key (seed lo, seed hi)
+ * and counter (g lo, g hi, stream_id, draw) for history g = first_history + i,
+ * i < n. Stream id 0 is source sampling, 1 a primary's transport. out: n x 4
+ * uint32 in `mem` (host: synchronises). Errors: LSM_ERR_ARG for a NULL output
+ * or n outside [1, 2^28].
+ */
+lsm_status lsm_philox_blocks(uint64_t seed, uint64_t first_history, uint32_t stream_id, uint32_t draw, int64_t n,
+                             uint32_t *out, lsm_mem mem, lsm_stream stream);
+
+/*
  * PSL files -- the comparator source model of Table 1 (Sec. 3.1): particles
  * stored on disk grouped by phase-spacelet, read for a field, copied to the
  * GPU and translated there, instead of being sampled on the fly.

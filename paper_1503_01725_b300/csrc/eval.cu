@@ -205,6 +205,23 @@ __global__ void k_atomic_peak(float *__restrict__ cells, uint32_t n_cells, int p
     }
 }
 
+// Philox4x32-10 blocks of the transport's streams: block i at counter
+// (g lo, g hi, stream id, draw) for history g = g0 + i
+// (four 32-bit stores: the caller's array needs only 4-byte alignment)
+__global__ void k_philox(uint32_t k0, uint32_t k1, uint64_t g0, uint32_t sid, uint32_t draw, int64_t n,
+                         uint32_t *__restrict__ out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t g = g0 + (uint64_t)i;
+        const uint4 r = philox4x32_10(k0, k1, (uint32_t)g, (uint32_t)(g >> 32), sid, draw);
+        out[4 * i] = r.x;
+        out[4 * i + 1] = r.y;
+        out[4 * i + 2] = r.z;
+        out[4 * i + 3] = r.w;
+    }
+}
+
 }  // namespace
 }  // namespace lsm
 
@@ -386,6 +403,30 @@ lsm_status lsm_l2_atomic_peak(int64_t n_cells, int32_t reps, double *atomics_per
     if (cells) dev_free(cells);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_l2_atomic_peak");
     *atomics_per_s = ms > 0.0f ? per_launch * reps / (ms * 1e-3) : 0.0;
+    return LSM_OK;
+}
+
+lsm_status lsm_philox_blocks(uint64_t seed, uint64_t first_history, uint32_t stream_id, uint32_t draw, int64_t n,
+                             uint32_t *out, lsm_mem mem, lsm_stream stream)
+{
+    if (!out) return set_arg_error("lsm_philox_blocks: NULL argument");
+    if (n < 1 || n > (1ll << 28)) return set_arg_error("lsm_philox_blocks: 1 <= n <= 2^28");
+    const cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *d = out;
+    cudaError_t e = cudaSuccess;
+    if (mem == LSM_MEM_HOST) e = dev_malloc((void **)&d, (size_t)n * 16, st);
+    if (e == cudaSuccess) {
+        k_philox<<<grid_for_n(n), 256, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32), first_history, stream_id,
+                                               draw, n, d);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && mem == LSM_MEM_HOST) {
+        e = cudaMemcpyAsync(out, d, (size_t)n * 16, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (mem == LSM_MEM_HOST && d) dev_free(d);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsm_philox_blocks");
     return LSM_OK;
 }
 

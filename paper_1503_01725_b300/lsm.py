@@ -152,6 +152,8 @@ _EXPORTS = {
                                  C.c_void_p]),
     "lsm_l2_atomic_peak": (C.c_int, [C.c_int64, C.c_int32, _dp, C.c_void_p]),
     "lsm_tally_history_ledger": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
+    "lsm_philox_blocks": (C.c_int, [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, C.c_void_p, C.c_int,
+                                    C.c_void_p]),
     "lsm_curve_compare": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double,
                                     C.c_int32, C.c_double, C.c_int, _dp, C.c_void_p]),
     "lsm_pslfile_write": (C.c_int, [C.c_void_p, C.c_uint64, C.c_char_p, C.POINTER(C.c_int64), C.c_void_p]),
@@ -407,6 +409,15 @@ def lsm_tally_create(ph: PhantomHandle, mode: int = 0, idx3d=None, n_rows: int =
     t.mode, t.n_rows, t.n_psr, t.n_beams = mode, n_rows, n_psr, n_beams
     t.ncell = ph.desc.nvox if mode == 0 else n_beams * n_rows * n_psr
     return t
+
+
+def lsm_philox_blocks(seed: int, first_history: int, stream_id: int, draw: int, n: int, stream=None) -> np.ndarray:
+    """The device's Philox4x32-10 blocks for histories first_history ..
+    first_history + n - 1 at (stream_id, draw): uint32 [n, 4] on the host."""
+    out = np.zeros((n, 4), dtype=np.uint32)
+    _check(_lib.lsm_philox_blocks(int(seed), int(first_history), int(stream_id), int(draw), int(n),
+                                  out.ctypes.data, LSM_MEM_HOST, _stream(stream)), "lsm_philox_blocks")
+    return out
 
 
 def lsm_tally_history_ledger(t: Tally, buf=None, first_history: int = 0):

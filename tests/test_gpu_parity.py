@@ -701,3 +701,21 @@ def test_dose_and_sigma_from_the_tally(L, nb):
     np.testing.assert_allclose(d.ravel(), s1 / nb * scale / m, rtol=1e-14, atol=0)
     np.testing.assert_allclose(s.ravel(), np.sqrt(nb * var) / nb * scale / m, rtol=1e-13, atol=1e-300)
     assert (d > 0).sum() > 100 and (nb == 1 or (s > 0).sum() > 100)
+
+
+def test_device_philox_equals_the_oracle(L):
+    # the device's Philox4x32-10 against the oracle's (itself pinned to
+    # PyTorch's engine): every word of blocks at several histories, stream ids
+    # and draws, including a history above 2^32 and a seed using both halves
+    rng = np.random.default_rng(4)
+    for seed, g0, sid, draw in ((0, 0, 0, 0), (0x1234_5678_9ABC_DEF0, 7, 1, 3),
+                                (2 ** 63 + 5, 2 ** 32 - 3, 0x8000_0001, 2 ** 31 + 9), (42, 10 ** 12, 77, 0)):
+        n = 257
+        got = L.lsm_philox_blocks(seed, g0, sid, draw, n)
+        for i in list(range(8)) + list(rng.integers(0, n, 16)) + [n - 1]:
+            g = g0 + int(i)
+            want = O.philox4x32_10([seed & 0xFFFFFFFF, seed >> 32],
+                                   [g & 0xFFFFFFFF, g >> 32, sid, draw])
+            np.testing.assert_array_equal(got[i], want, err_msg=str((seed, g, sid, draw)))
+    with pytest.raises(L.LSMError, match="LSM_ERR_ARG"):
+        L.lsm_philox_blocks(1, 0, 0, 0, 0)
