@@ -73,6 +73,47 @@ def test_full_sampling_on_scattered_histories(L, full_run):
                                        err_msg=k)
 
 
+def test_full_sampling_geometry_over_every_history(L, full_run):
+    """Every one of the 1e7 sampled histories of the benchmark plan, on the
+    GPU: the straight line through the particle's surface position and
+    direction crosses the phase-space plane inside its plan entry's PSL
+    square; accepted particles (also those that miss the phantom) pass both
+    jaw openings (given at the isocentre, scaled to each plane); rejected ones
+    do not pass both. Tolerance 1e-3 cm (FP32 positions after an 80 cm flight)."""
+    import torch
+    wl, n_plan, g, _ = full_run
+    m, b = wl.model, wl.beams
+    ent = torch.tensor(L.lsm_psl_copy(g, 5), device="cuda", dtype=torch.int64)   # beam stype ebin ix iy ring
+    x1, x2, y1, y2 = (float(v) for v in b.jaws[0])
+    tol, pitch, n_r = 1e-3, float(m.dr), int(m.n_r)
+    chunk = 2_500_000
+    n_acc = n_rej = 0
+    for g0 in range(0, N_FULL, chunk):
+        out = L.lsm_sample(g, wl.seed, g0, chunk, W.SSD)
+        x, y, u, v, w = (out[k].double() for k in ("x", "y", "u", "v", "w"))
+        e = ent[out["info"][:, 3].long()]
+
+        def at(z):
+            t = (z - W.SSD) / w
+            return x + t * u, y + t * v
+
+        xp, yp = at(W.Z_PHSP)
+        lox, loy = (e[:, 3] - n_r).double() * pitch, (e[:, 4] - n_r).double() * pitch
+        assert bool(((xp >= lox - tol) & (xp <= lox + pitch + tol)).all())
+        assert bool(((yp >= loy - tol) & (yp <= loy + pitch + tol)).all())
+        xj, _ = at(b.z_jaw_x)
+        _, yj = at(b.z_jaw_y)
+        sx, sy = b.z_jaw_x / b.sad, b.z_jaw_y / b.sad
+        inside = (xj >= x1 * sx - tol) & (xj <= x2 * sx + tol) & (yj >= y1 * sy - tol) & (yj <= y2 * sy + tol)
+        deep = (xj > x1 * sx + tol) & (xj < x2 * sx - tol) & (yj > y1 * sy + tol) & (yj < y2 * sy - tol)
+        acc = out["status"] != 1
+        assert bool(inside[acc].all())
+        assert not bool(deep[~acc].any())
+        n_acc += int(acc.sum())
+        n_rej += int((~acc).sum())
+    assert n_acc + n_rej == N_FULL and n_rej > 0 and n_acc > 0
+
+
 def test_full_energy_ledger(full_run):
     _, _, _, (s1, s2, nb, led, st, rc) = full_run
     assert rc == 0 and nb == B_FULL
