@@ -220,3 +220,36 @@ def test_batched_basis_equals_single_run_decomposition(L):
     tk_ = Ak.reshape(wl.beams.n_beams, -1).sum(axis=1)
     tw_ = Aw.reshape(wl.beams.n_beams, -1).sum(axis=1)
     np.testing.assert_allclose(tk_, tw_, rtol=0.03)
+
+
+def test_commissioning_system_active_set_against_the_oracle(L):
+    """Eq. 8 at the commissioning size: A from the batched basis runs of 300
+    PSRs x 3 fields (electron PSRs grouped per energy bin: 1518 x 210), b from
+    an independent run times known weights with 0.5 % noise. The GPU's active
+    set equals the oracle's Lawson-Hanson solution to 1e-9 with the same
+    iteration count, and its KKT residual is below 1e-10 |A^T b|."""
+    from oracle import nnls as N
+    wl = W.workload_commissioning()
+    m = wl.model
+    ph = L.lsm_phantom_create(wl.phantom)
+    idx, n_rows = W.commissioning_index(wl.phantom)
+    t = L.lsm_tally_create(ph, mode=1, idx3d=idx, n_rows=n_rows, n_psr=m.n_psr, n_beams=wl.beams.n_beams)
+    n_ph = 2 * m.n_e * m.n_r
+
+    def grouped(seed):
+        g = L.lsm_build_psl(m, wl.beams, per_psr_hist=wl.extra["n_k"])
+        L.lsm_tally_reset(t)
+        L.lsm_run(g, ph, t, seed, L.RunOpts(electron_mode=1, n_batches=4))
+        A = L.lsm_basis_matrix(t, g, ph)
+        return np.concatenate([A[:, :n_ph], A[:, n_ph:].reshape(A.shape[0], m.n_e, m.n_r).sum(axis=2)], axis=1)
+
+    A, A2 = grouped(1), grouped(999)
+    x_true = W.commissioning_truth(A.shape[1])
+    b = A2 @ x_true * (1 + 0.005 * np.random.default_rng(3).standard_normal(A.shape[0]))
+    sc = 1.0 / np.abs(b).max()
+    A, b = A * sc, b * sc
+    x, rep = L.lsm_commission(A, b, method=0)
+    xo, it_o = N.lawson_hanson(A, b)
+    assert rep["converged"] and rep["iterations"] == it_o
+    np.testing.assert_allclose(x, xo, atol=1e-9 * np.abs(xo).max())
+    assert rep["kkt"] < 1e-10 * np.linalg.norm(A.T @ b)
