@@ -253,13 +253,8 @@ __global__ void k_eq3_floor(const double *__restrict__ wpsl, const uint8_t *__re
 // select (256-bin histograms of the keys that match the digits chosen so far),
 // then adds one to every cell with a larger key and to the first `need` cells,
 // in loop order, whose key equals it.
-__global__ void __launch_bounds__(1024) k_eq3_select(const double *__restrict__ rem, int64_t n, int64_t n_hist,
-                                                     const unsigned long long *__restrict__ floor_sum,
-                                                     const double *__restrict__ denom, int64_t *__restrict__ count)
+__device__ void eq3_select_apply(const double *__restrict__ rem, int64_t n, long long left, int64_t *__restrict__ count)
 {
-    // an empty sampling area (denominator 0) distributes nothing
-    const long long left = (*denom > 0.0 ? n_hist : 0) - (long long)(*floor_sum);
-    if (left <= 0) return;
     const unsigned long long *key = reinterpret_cast<const unsigned long long *>(rem);
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_pre;
@@ -335,6 +330,24 @@ __global__ void __launch_bounds__(1024) k_eq3_select(const double *__restrict__ 
     }
 }
 
+__device__ void scan_counts_block(const int64_t *__restrict__ count, int64_t n, int64_t *__restrict__ cstart,
+                                  int64_t *__restrict__ eidx, int64_t *__restrict__ start, int64_t *__restrict__ res);
+
+// One CTA: the largest remainders, then (the counts final) the exclusive
+// scans of the counts that place the plan's entries, in one launch.
+__global__ void __launch_bounds__(1024) k_eq3_select(const double *__restrict__ rem, int64_t n, int64_t n_hist,
+                                                     const unsigned long long *__restrict__ floor_sum,
+                                                     const double *__restrict__ denom, int64_t *__restrict__ count,
+                                                     int64_t *__restrict__ cstart, int64_t *__restrict__ eidx,
+                                                     int64_t *__restrict__ start, int64_t *__restrict__ res)
+{
+    // an empty sampling area (denominator 0) distributes nothing
+    const long long left = (*denom > 0.0 ? n_hist : 0) - (long long)(*floor_sum);
+    if (left > 0) eq3_select_apply(rem, n, left, count);      // uniform over the block
+    __syncthreads();
+    scan_counts_block(count, n, cstart, eidx, start, res);
+}
+
 // ------------------------------------------------- per-PSR basis-run plans --
 
 // One CTA per (PSR k, beam b): weights of PSR k's share, Eq. 3 within the run.
@@ -406,8 +419,8 @@ __global__ void k_psr_counts(const double *__restrict__ w, const double *__restr
 // Plan prefix of the counts (cstart) and entry index of the non-empty cells
 // (eidx) in one pass of one CTA, and the plan end start[n_ent] = total;
 // (n_ent, total) also go to res[0..1] for the host.
-__global__ void k_scan_counts(const int64_t *__restrict__ count, int64_t n, int64_t *__restrict__ cstart,
-                              int64_t *__restrict__ eidx, int64_t *__restrict__ start, int64_t *__restrict__ res)
+__device__ void scan_counts_block(const int64_t *__restrict__ count, int64_t n, int64_t *__restrict__ cstart,
+                                  int64_t *__restrict__ eidx, int64_t *__restrict__ start, int64_t *__restrict__ res)
 {
     const int T = blockDim.x;
     const int64_t seg = (n + T - 1) / T;
@@ -442,6 +455,12 @@ __global__ void k_scan_counts(const int64_t *__restrict__ count, int64_t n, int6
         rs += c;
         rz += c > 0 ? 1 : 0;
     }
+}
+
+__global__ void k_scan_counts(const int64_t *__restrict__ count, int64_t n, int64_t *__restrict__ cstart,
+                              int64_t *__restrict__ eidx, int64_t *__restrict__ start, int64_t *__restrict__ res)
+{
+    scan_counts_block(count, n, cstart, eidx, start, res);
 }
 
 
@@ -780,7 +799,8 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
         k_eq3_floor<<<g, 256, 0, st>>>(P->d_wpsl, P->d_incl, ne, npsl, ncell, n_hist, d_parts, nb3, d_denom,
                                        P->d_count, d_rem, d_fsum);
         CKL("k_eq3_floor");
-        k_eq3_select<<<1, 1024, 0, st>>>(d_rem, ncell, n_hist, d_fsum, d_denom, P->d_count);
+        k_eq3_select<<<1, 1024, 0, st>>>(d_rem, ncell, n_hist, d_fsum, d_denom, P->d_count, d_cstart, d_eidx,
+                                         P->d_start, (int64_t *)(base + o_res + 16));
         CKL("k_eq3_select");
     } else {
         const size_t smem = (size_t)npsl * 24;
@@ -789,8 +809,11 @@ lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
                                                    P->d_count, d_dkb);
         CKL("k_psr_counts");
     }
-    k_scan_counts<<<1, 1024, 0, st>>>(P->d_count, ncell, d_cstart, d_eidx, P->d_start, (int64_t *)(base + o_res + 16));
-    CKL("k_scan_counts");
+    if (per_psr_hist) {      // (the whole-source plan's scans ran in k_eq3_select)
+        k_scan_counts<<<1, 1024, 0, st>>>(P->d_count, ncell, d_cstart, d_eidx, P->d_start,
+                                          (int64_t *)(base + o_res + 16));
+        CKL("k_scan_counts");
+    }
     k_entries<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(P->d_count, d_cstart, d_eidx, ncell, P->per_psr, nb, ne,
                                                               nr, P->d_w, P->d_tag_r0, P->d_tag_l0, d_dkb, d_nk,
                                                               P->d_start, P->d_ent, P->d_escale);
