@@ -259,8 +259,9 @@ __device__ void eq3_select_apply(const double *__restrict__ rem, int64_t n, long
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_pre;
     __shared__ long long s_k;
+    __shared__ int s_all;     // every key of the chosen bin is taken: the selection is the keys >= s_pre
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) { s_pre = 0ull; s_k = left; }
+    if (tid == 0) { s_pre = 0ull; s_k = left; s_all = 0; }
     unsigned long long mask = 0ull;
     for (int shift = 56; shift >= 0; shift -= 8) {
         if (tid < 256) hist[tid] = 0u;
@@ -284,18 +285,37 @@ __device__ void eq3_select_apply(const double *__restrict__ rem, int64_t n, long
             long long above = (long long)(suf - loc); // keys in bins above this lane's
             int found = -1;
             long long rest = 0;
+            unsigned cf = 0;
             for (int j = 7; j >= 0; --j) {
-                if (found < 0 && above < k && above + (long long)c[j] >= k) { found = 8 * lane + j; rest = k - above; }
+                if (found < 0 && above < k && above + (long long)c[j] >= k) {
+                    found = 8 * lane + j;
+                    rest = k - above;
+                    cf = c[j];
+                }
                 above += c[j];
             }
             const unsigned hit = __ballot_sync(0xffffffffu, found >= 0);
             const int src = __ffs(hit) - 1;
             const int bin = __shfl_sync(0xffffffffu, found, src);
             const long long kk = __shfl_sync(0xffffffffu, rest, src);
-            if (lane == 0) { s_pre = pre | ((unsigned long long)bin << shift); s_k = kk; }
+            const unsigned cb = __shfl_sync(0xffffffffu, cf, src);
+            if (lane == 0) {
+                s_pre = pre | ((unsigned long long)bin << shift);
+                s_k = kk;
+                // the bin's keys are all taken: keys above the prefix were taken
+                // by earlier digits, the rest lie below it
+                if ((long long)cb == kk) s_all = 1;
+            }
         }
         mask |= 255ull << shift;
         __syncthreads();
+        if (s_all) break;
+    }
+    if (s_all) {
+        const unsigned long long thr = s_pre;
+        for (int64_t i = tid; i < n; i += blockDim.x)
+            if (key[i] >= thr) count[i] += 1;
+        return;
     }
     const unsigned long long v = s_pre;             // the left-th largest key
     const long long need = s_k;                      // cells with key == v that get one more
