@@ -703,6 +703,20 @@ def main():
         reps.append(time.perf_counter() - t0)
         del prev, job
     e2e_rate = world * args.n_hist * n_pipe / statistics.median(reps)
+    # leave nothing of the end-to-end steps behind: their handles freed, and
+    # the memory pool (grown by two concurrent workspaces) trimmed back, so
+    # that the device-timed steps start from the state they run in
+    del host_ph, outs, streams
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
+    try:
+        from cuda.bindings import runtime as _rt
+        _err, _pool = _rt.cudaDeviceGetDefaultMemPool(local)
+        _rt.cudaMemPoolTrimTo(_pool, 0)
+        torch.cuda.synchronize()
+    except Exception:
+        pass
 
     clk = ClockSampler(local).start()
     # kernel-group event timers on from the warm-up on, so that a captured
