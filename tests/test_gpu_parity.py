@@ -719,3 +719,35 @@ def test_device_philox_equals_the_oracle(L):
             np.testing.assert_array_equal(got[i], want, err_msg=str((seed, g, sid, draw)))
     with pytest.raises(L.LSMError, match="LSM_ERR_ARG"):
         L.lsm_philox_blocks(1, 0, 0, 0, 0)
+
+
+def test_transport_cutoffs_are_the_papers(L):
+    # the cutoffs of tests/golden/paper_values.txt (Sec. 3.1: 200 keV electrons,
+    # 50 keV photons) on the device: a particle just below its cutoff deposits
+    # where it enters (no Woodcock flight, no CSDA step); just above, it moves
+    import os
+    import torch
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                vals[line.split()[0]] = float(line.split()[1])
+    ph = W.water_phantom(16, 16, 16, 0.5)
+    phh = L.lsm_phantom_create(ph)
+    for kind, cut, counter in ((0, vals["photon_cutoff"], "flights"), (1, vals["electron_cutoff"], "esteps")):
+        for E, moves in ((cut * (1 - 1e-5), False), (cut * (1 + 1e-3), True)):
+            p = L.alloc_particles(1)
+            for k, v in (("x", ph.x0 + 4.0), ("y", ph.y0 + 4.0), ("z", ph.z0), ("u", 0.0), ("v", 0.0), ("w", 1.0),
+                         ("E", E)):
+                p[k].fill_(v)
+            p["hist"].fill_(0)
+            p["psr"].fill_(0)
+            p["beam"].fill_(0)
+            p["type"].fill_(kind)
+            p["status"].fill_(0)
+            t = L.lsm_tally_create(phh)
+            L.lsm_transport(phh, p, 1, 5, t, L.RunOpts(electron_mode=1))
+            torch.cuda.synchronize()
+            led, st = L.lsm_tally_ledger(t)
+            assert (st[counter] > 0) == moves, (kind, E, st[counter])
+            assert led["deposited"] + led["escaped"] == pytest.approx(E, rel=1e-5)
