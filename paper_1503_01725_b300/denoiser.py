@@ -37,9 +37,11 @@ def mc_dose(wl: W.Workload, n_hist: int, seed: int, n_batches: int = 16, ph=None
     n_plan = n_hist // n_batches
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan)
+    # queued without host waits: the plan's results are read when the dose
+    # scale needs them, the run leaves its overflow count in the statistics
+    psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True)
     tally = lsm.lsm_tally_create(ph)
-    lsm.lsm_run(psl, ph, tally, seed, lsm.RunOpts(electron_mode=wl.electron_mode, n_batches=n_batches))
+    lsm.lsm_run(psl, ph, tally, seed, lsm.RunOpts(electron_mode=wl.electron_mode, n_batches=n_batches, no_sync=True))
     d, s = lsm.lsm_dose(tally, ph, psl.denom / n_plan, device=True)
     b.record()
     torch.cuda.synchronize()
