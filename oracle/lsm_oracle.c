@@ -873,6 +873,52 @@ static void kn_sample(stream_t *st, double k, double *eta_out, double *phi_out)
     *phi_out = 2.0 * PI_D * u01(q[1]);
 }
 
+/* One Compton event at photon energy E travelling along (u, v, w): the
+ * scattered photon's energy E1 = E / eta and direction d1 (polar cos theta =
+ * 1 - (eta - 1) / k about the old direction, azimuth phi), eta drawn from the
+ * inverse Klein-Nishina CDF; the recoil electron (kinetic energy E - E1) moves
+ * along the momentum the photon gave up, E * u_old - E1 * u_new (photon
+ * momenta E / c and E1 / c, so the electron's direction is their difference). */
+static void compton_event(stream_t *st, double E, double u, double v, double w, double *E1,
+                          double d1[3], double de[3])
+{
+    double k = E / ME, eta, phi;
+    kn_sample(st, k, &eta, &phi);
+    double cost = 1.0 - (eta - 1.0) / k;
+    double e1 = E / eta;
+    double un = u, vn = v, wn = w;
+    rotate_dir(&un, &vn, &wn, cost, phi);
+    double ex = E * u - e1 * un, ey = E * v - e1 * vn, ez = E * w - e1 * wn;
+    double en = sqrt(ex * ex + ey * ey + ez * ez);
+    if (en > 0.0) { ex /= en; ey /= en; ez /= en; } else { ex = u; ey = v; ez = w; }
+    *E1 = e1;
+    d1[0] = un; d1[1] = vn; d1[2] = wn;
+    de[0] = ex; de[1] = ey; de[2] = ez;
+}
+
+/* Gaussian multiple-scattering deflection after a CSDA step of length ds
+ * (cm) through density rho of material m, for an electron of kinetic energy
+ * E0 at the start of the step: the step is t = rho ds / X0 radiation lengths,
+ * theta0 the Highland width of each projected angle, and the deflection the
+ * polar angle of a two-dimensional Gaussian of per-plane width theta0, i.e.
+ * theta = theta0 sqrt(-2 ln u1) (Rayleigh), azimuth 2 pi u2.  One Philox block
+ * serves two deflections: words 0-1, then words 2-3 at the next one. */
+static void ms_deflect(part_t *p, double E0, double rho, double ds, int m)
+{
+    uint32_t ua, ub;
+    if (p->have) {
+        ua = p->hold[0]; ub = p->hold[1]; p->have = 0;
+    } else {
+        uint32_t r[4];
+        draw(&p->rng, r);
+        ua = r[0]; ub = r[1]; p->hold[0] = r[2]; p->hold[1] = r[3]; p->have = 1;
+    }
+    double th0 = or_highland(E0, rho * ds / X0G[m]);
+    double th = th0 * sqrt(-2.0 * log(u01(ua)));
+    if (th > PI_D) th = PI_D;
+    rotate_dir(&p->u, &p->v, &p->w, cos(th), 2.0 * PI_D * u01(ub));
+}
+
 static void photon_track(tctx *T, part_t *p)
 {
     const or_phantom *Ph = T->Ph;
@@ -900,19 +946,10 @@ static void photon_track(tctx *T, part_t *p)
         T->n_real++;
         double t = u01(r[2]) * mut;
         if (t <= muC) {
-            /* Compton: E'/E from the inverse Klein-Nishina CDF */
-            double k = p->E / ME, eta, cost, phi;
-            kn_sample(&p->rng, k, &eta, &phi);
-            cost = 1.0 - (eta - 1.0) / k;
-            double E1 = p->E / eta;
-            double u = p->u, v = p->v, w = p->w;
-            rotate_dir(&u, &v, &w, cost, phi);
-            /* electron direction from momentum conservation */
-            double ex = p->E * p->u - E1 * u, ey = p->E * p->v - E1 * v, ez = p->E * p->w - E1 * w;
-            double en = sqrt(ex * ex + ey * ey + ez * ez);
-            if (en > 0.0) { ex /= en; ey /= en; ez /= en; } else { ex = p->u; ey = p->v; ez = p->w; }
-            spawn_electron(T, p, p->E - E1, ex, ey, ez, child_id(&p->rng, 0), vox);
-            p->E = E1; p->u = u; p->v = v; p->w = w;
+            double E1, d1[3], de[3];
+            compton_event(&p->rng, p->E, p->u, p->v, p->w, &E1, d1, de);
+            spawn_electron(T, p, p->E - E1, de[0], de[1], de[2], child_id(&p->rng, 0), vox);
+            p->E = E1; p->u = d1[0]; p->v = d1[1]; p->w = d1[2];
         } else if (t <= muC + muP) {
             /* photoelectric: the electron takes the photon energy and direction */
             spawn_electron(T, p, p->E, p->u, p->v, p->w, child_id(&p->rng, 0), vox);
@@ -970,21 +1007,7 @@ static void electron_track(tctx *T, part_t *p)
         double E0 = p->E;
         p->x += ds * p->u; p->y += ds * p->v; p->z += ds * p->w;
         p->E -= dE;
-        if (p->E >= E_CUT_E && !O->ms_off) {
-            /* one block serves two deflections: words 0-1, then words 2-3 */
-            uint32_t ua, ub;
-            if (p->have) {
-                ua = p->hold[0]; ub = p->hold[1]; p->have = 0;
-            } else {
-                uint32_t r[4];
-                draw(&p->rng, r);
-                ua = r[0]; ub = r[1]; p->hold[0] = r[2]; p->hold[1] = r[3]; p->have = 1;
-            }
-            double th0 = or_highland(E0, rho * ds / X0G[m]);
-            double th = th0 * sqrt(-2.0 * log(u01(ua)));
-            if (th > PI_D) th = PI_D;
-            rotate_dir(&p->u, &p->v, &p->w, cos(th), 2.0 * PI_D * u01(ub));
-        }
+        if (p->E >= E_CUT_E && !O->ms_off) ms_deflect(p, E0, rho, ds, m);
     }
 }
 
@@ -1185,4 +1208,39 @@ OR_API void or_electron_path(const or_phantom *Ph, const or_opts *O, double E, u
     out[0] = p.z - z0;
     out[1] = T.dep;
     free(T.acc);
+}
+
+/* Pin helper: n Compton events of photons of energy E along d0 through the
+ * transport's own event code (history i, primary transport stream); out
+ * [n][8] = (E1, photon direction[3], electron kinetic energy, electron
+ * direction[3]). */
+OR_API void or_compton_events(double E, const double d0[3], uint64_t seed, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        stream_t st;
+        stream_init(&st, seed, (uint64_t)i, 1u);
+        double E1, d1[3], de[3];
+        compton_event(&st, E, d0[0], d0[1], d0[2], &E1, d1, de);
+        double *o = out + 8 * i;
+        o[0] = E1; o[1] = d1[0]; o[2] = d1[1]; o[3] = d1[2];
+        o[4] = E - E1; o[5] = de[0]; o[6] = de[1]; o[7] = de[2];
+    }
+}
+
+/* Pin helper: n independent multiple-scattering deflections (history i) of an
+ * electron of energy E0 moving along d0 after one step of length ds through
+ * density rho of material m, through the transport's own deflection code;
+ * out [n][3] = new direction.  Each uses the first half of a fresh block. */
+OR_API void or_ms_deflections(double E0, double rho, double ds, int m, const double d0[3],
+                              uint64_t seed, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        part_t p;
+        memset(&p, 0, sizeof(p));
+        p.u = d0[0]; p.v = d0[1]; p.w = d0[2]; p.E = E0; p.type = 1;
+        stream_init(&p.rng, seed, (uint64_t)i, 1u);
+        p.have = 0;
+        ms_deflect(&p, E0, rho, ds, m);
+        out[3 * i] = p.u; out[3 * i + 1] = p.v; out[3 * i + 2] = p.w;
+    }
 }

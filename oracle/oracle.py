@@ -68,40 +68,48 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(LIB_PATH)
-        L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
-        for f in ("or_kn_sigma",):
-            getattr(L, f).restype = C.c_double
-            getattr(L, f).argtypes = [C.c_double]
-        L.or_kn_cdf.restype = C.c_double
-        L.or_kn_cdf.argtypes = [C.c_double, C.c_double]
-        L.or_mu_mass.restype = C.c_double
-        L.or_mu_mass.argtypes = [C.c_double, C.c_int, C.c_int]
-        L.or_scol_mass.restype = C.c_double
-        L.or_scol_mass.argtypes = [C.c_double, C.c_int]
-        L.or_highland.restype = C.c_double
-        L.or_highland.argtypes = [C.c_double, C.c_double]
-        L.or_plan_build.restype = C.c_void_p
-        L.or_plan_build.argtypes = [C.POINTER(_Model), C.POINTER(_Beams), C.c_int64,
-                                    C.POINTER(C.c_int64)]
-        L.or_plan_free.argtypes = [C.c_void_p]
-        L.or_beam_entry.restype = C.c_int
-        L.or_beam_entry.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
-        L.or_plan_sizes.argtypes = [C.c_void_p, C.POINTER(C.c_int64), _dp]
-        L.or_plan_copy.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
-        L.or_sample.restype = C.c_int
-        L.or_sample.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64, C.c_double,
-                                _dp, C.POINTER(C.c_int32), _dp]
-        L.or_run.restype = C.c_int
-        L.or_run.argtypes = [C.c_void_p, C.POINTER(_Phantom), C.POINTER(_Opts), C.c_uint64,
-                             _dp, _dp, _dp, C.POINTER(C.c_int64), _dp, _dp]
-        L.or_first_collision.argtypes = [C.POINTER(_Phantom), C.POINTER(_Opts), C.c_double,
-                                         C.c_uint64, C.c_int64, _dp]
-        L.or_kn_samples.argtypes = [C.c_double, C.c_uint64, C.c_int64, _dp]
-        L.or_electron_path.argtypes = [C.POINTER(_Phantom), C.POINTER(_Opts), C.c_double,
-                                       C.c_uint64, _dp]
-        _lib = L
+        _lib = load(LIB_PATH)
     return _lib
+
+
+def load(path: str):
+    """Open an oracle shared object at ``path`` and declare its signatures."""
+    L = C.CDLL(path)
+    L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+    for f in ("or_kn_sigma",):
+        getattr(L, f).restype = C.c_double
+        getattr(L, f).argtypes = [C.c_double]
+    L.or_kn_cdf.restype = C.c_double
+    L.or_kn_cdf.argtypes = [C.c_double, C.c_double]
+    L.or_mu_mass.restype = C.c_double
+    L.or_mu_mass.argtypes = [C.c_double, C.c_int, C.c_int]
+    L.or_scol_mass.restype = C.c_double
+    L.or_scol_mass.argtypes = [C.c_double, C.c_int]
+    L.or_highland.restype = C.c_double
+    L.or_highland.argtypes = [C.c_double, C.c_double]
+    L.or_plan_build.restype = C.c_void_p
+    L.or_plan_build.argtypes = [C.POINTER(_Model), C.POINTER(_Beams), C.c_int64,
+                                C.POINTER(C.c_int64)]
+    L.or_plan_free.argtypes = [C.c_void_p]
+    L.or_beam_entry.restype = C.c_int
+    L.or_beam_entry.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.or_plan_sizes.argtypes = [C.c_void_p, C.POINTER(C.c_int64), _dp]
+    L.or_plan_copy.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+    L.or_sample.restype = C.c_int
+    L.or_sample.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64, C.c_double,
+                            _dp, C.POINTER(C.c_int32), _dp]
+    L.or_run.restype = C.c_int
+    L.or_run.argtypes = [C.c_void_p, C.POINTER(_Phantom), C.POINTER(_Opts), C.c_uint64,
+                         _dp, _dp, _dp, C.POINTER(C.c_int64), _dp, _dp]
+    L.or_first_collision.argtypes = [C.POINTER(_Phantom), C.POINTER(_Opts), C.c_double,
+                                     C.c_uint64, C.c_int64, _dp]
+    L.or_kn_samples.argtypes = [C.c_double, C.c_uint64, C.c_int64, _dp]
+    L.or_electron_path.argtypes = [C.POINTER(_Phantom), C.POINTER(_Opts), C.c_double,
+                                   C.c_uint64, _dp]
+    L.or_compton_events.argtypes = [C.c_double, _dp, C.c_uint64, C.c_int64, _dp]
+    L.or_ms_deflections.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, _dp,
+                                    C.c_uint64, C.c_int64, _dp]
+    return L
 
 
 # ---------------------------------------------------------------------------
@@ -312,6 +320,24 @@ def electron_path(phantom, E: float, seed: int = 0, **opts) -> tuple[float, floa
     out = np.zeros(2)
     lib().or_electron_path(C.byref(ps), C.byref(os_), E, seed, _ptr(out))
     return float(out[0]), float(out[1])
+
+
+def compton_events(E: float, d0, seed: int, n: int) -> np.ndarray:
+    """n Compton events of photons of energy E along d0 through the transport's
+    event code: [n][8] = (E', photon direction, electron T, electron direction)."""
+    d = np.ascontiguousarray(d0, dtype=np.float64)
+    out = np.zeros((n, 8))
+    lib().or_compton_events(E, _ptr(d), seed, n, _ptr(out))
+    return out
+
+
+def ms_deflections(E0: float, rho: float, ds: float, mat: int, d0, seed: int, n: int) -> np.ndarray:
+    """n multiple-scattering deflections of an electron of energy E0 along d0
+    after one CSDA step ds in density rho of material class mat: [n][3]."""
+    d = np.ascontiguousarray(d0, dtype=np.float64)
+    out = np.zeros((n, 3))
+    lib().or_ms_deflections(E0, rho, ds, mat, _ptr(d), seed, n, _ptr(out))
+    return out
 
 
 def dose_and_sigma(s1: np.ndarray, s2: np.ndarray, n_batches: int):

@@ -503,6 +503,123 @@ def test_csda_path_length_matches_range_integral():
         assert dep == pytest.approx(E, rel=1e-12)
 
 
+def _frame(d0):
+    """Orthonormal (e1, e2) perpendicular to the unit vector d0."""
+    d0 = np.asarray(d0, float) / np.linalg.norm(d0)
+    a = np.array([1.0, 0.0, 0.0]) if abs(d0[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = np.cross(d0, a)
+    e1 /= np.linalg.norm(e1)
+    return d0, e1, np.cross(d0, e1)
+
+
+def _polar_azimuth(d, d0):
+    """Angle between each row of d and d0 (by atan2, exact near 0) and its
+    azimuth about d0 in a fixed perpendicular frame."""
+    d0, e1, e2 = _frame(d0)
+    c = d @ d0
+    s = np.linalg.norm(np.cross(d, d0), axis=1)
+    return np.arctan2(s, c), np.arctan2(d @ e2, d @ e1)
+
+
+# Radiation length of liquid water, 36.08 g/cm2 (Particle Data Group, atomic and
+# nuclear properties of materials); the Highland width (Highland 1975, Lynch and
+# Dahl 1991 form) is theta0 = 13.6 MeV / (beta c p) sqrt(t) (1 + 0.038 ln t).
+X0_WATER = 36.08
+
+
+def _highland_pdg(E, t):
+    pc = np.sqrt(E * (E + 2 * ME))
+    beta = pc / (E + ME)
+    return 13.6 / (beta * pc) * np.sqrt(t) * (1 + 0.038 * np.log(t))
+
+
+@pytest.mark.parametrize("E0,rho,ds,d0", [
+    (1.0, 1.0, 0.125, (0.0, 0.0, 1.0)),         # water, axial (the rotation's pole branch)
+    (3.0, 1.04, 0.125, (0.3, -0.5, 0.81)),      # soft tissue, oblique direction
+    (0.5, 0.26, 0.25, (0.0, 0.0, -1.0)),        # lung, backward pole
+    (6.0, 1.0, 0.05, (-0.7, 0.7, 0.1)),         # thin step, nearly horizontal
+])
+def test_multiple_scattering_deflection_is_gaussian_with_highland_width(E0, rho, ds, d0):
+    """The CSDA step's deflection: each projected angle ~ N(0, theta0^2) with the
+    Highland theta0 of t = rho ds / X0 (water's published X0), so the space angle
+    is Rayleigh(theta0) and the azimuth about the old direction uniform.  A
+    polar draw missing sqrt(2), theta0 taken as a half-normal polar width, a
+    wrong radiation length or a rotation that does not turn by the drawn angle
+    each fail one of these."""
+    n = 40_000
+    t = rho * ds / X0_WATER
+    th0 = _highland_pdg(E0, t)
+    assert O.highland(E0, t) == pytest.approx(th0, rel=1e-12)
+    d0 = np.asarray(d0, float) / np.linalg.norm(d0)
+    d = O.ms_deflections(E0, rho, ds, 0, d0, 11, n)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-12)
+    th, ph = _polar_azimuth(d, d0)
+    ks = stats.kstest(th, "rayleigh", args=(0, th0))
+    assert ks.pvalue > 1e-4, (ks, th0)
+    assert stats.kstest(ph, "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-4
+    for proj in (th * np.cos(ph), th * np.sin(ph)):
+        assert stats.kstest(proj / th0, "norm").pvalue > 1e-4
+        # variance of a Gaussian sample: sd of s^2 / th0^2 is sqrt(2/n)
+        assert abs(proj.var() / th0 ** 2 - 1) < 4 * np.sqrt(2.0 / n)
+    # mean square space angle is 2 theta0^2 (two projected planes)
+    assert abs(np.mean(th ** 2) / (2 * th0 ** 2) - 1) < 4 * np.sqrt(1.0 / n)
+
+
+def test_multiple_scattering_width_follows_material_radiation_length():
+    """Bone's deflection uses the bone class's radiation length (21.68 g/cm2, a
+    stated synthetic constant): the Rayleigh scale differs from water's at the
+    same mass thickness by sqrt(X0_water / X0_bone) up to the log term."""
+    n = 40_000
+    E0, rho, ds = 2.0, 1.85, 0.1
+    th0 = _highland_pdg(E0, rho * ds / 21.68)
+    d = O.ms_deflections(E0, rho, ds, 1, (0.0, 0.0, 1.0), 12, n)
+    th, _ = _polar_azimuth(d, (0.0, 0.0, 1.0))
+    assert stats.kstest(th, "rayleigh", args=(0, th0)).pvalue > 1e-4
+    assert stats.kstest(th, "rayleigh", args=(0, _highland_pdg(E0, rho * ds / X0_WATER))).pvalue < 1e-6
+
+
+@pytest.mark.parametrize("E,d0", [
+    (0.1, (0.0, 0.0, 1.0)),
+    (0.5, (0.2, 0.4, -0.894)),
+    (2.0, (0.0, 0.0, -1.0)),
+    (6.0, (0.6, -0.3, 0.742)),
+])
+def test_compton_recoil_electron_kinematics(E, d0):
+    """Each Compton event against the two-body kinematics of a photon on a free
+    electron at rest: E' = E / (1 + k (1 - cos theta)) with theta the photon's
+    turn; the recoil electron takes T = E - E' and leaves in the scattering plane
+    on the opposite side of the incident direction (azimuth + pi) at the angle
+    phi with cot phi = (1 + k) tan(theta / 2).  A reversed momentum balance
+    (electron along E' u' - E u) puts it at pi - phi with the photon's azimuth and
+    fails every direction check."""
+    n = 20_000
+    k = E / ME
+    d0 = np.asarray(d0, float) / np.linalg.norm(d0)
+    ev = O.compton_events(E, d0, 21, n)
+    E1, d1, T, de = ev[:, 0], ev[:, 1:4], ev[:, 4], ev[:, 5:8]
+    d0n = np.asarray(d0, float) / np.linalg.norm(d0)
+    assert np.allclose(np.linalg.norm(d1, axis=1), 1, atol=1e-12)
+    assert np.allclose(np.linalg.norm(de, axis=1), 1, atol=1e-12)
+    assert np.all(E1 >= E / (1 + 2 * k) * (1 - 1e-12)) and np.all(E1 <= E * (1 + 1e-12))
+    assert np.allclose(T, E - E1, rtol=0, atol=1e-15 * E)
+    th, phg = _polar_azimuth(d1, d0n)
+    assert np.allclose(E1, E / (1 + k * (1 - np.cos(th))), rtol=1e-9)
+    phe_polar, phe_az = _polar_azimuth(de, d0n)
+    sel = th > 1e-3
+    with np.errstate(divide="ignore"):
+        lhs = 1.0 / np.tan(phe_polar[sel])
+    rhs = (1 + k) * np.tan(th[sel] / 2)
+    assert np.allclose(lhs, rhs, rtol=1e-6), np.max(np.abs(lhs / rhs - 1))
+    dphi = np.angle(np.exp(1j * (phe_az[sel] - phg[sel] - np.pi)))
+    assert np.max(np.abs(dphi)) < 1e-6
+    # coplanar with the incident and scattered photon directions
+    trip = np.einsum("ij,ij->i", de, np.cross(d0n, d1))
+    assert np.max(np.abs(trip)) < 1e-9
+    # the electron moves forward (0 <= phi <= pi/2), the photon azimuth is uniform
+    assert np.all(de @ d0n >= -1e-12)
+    assert stats.kstest(phg, "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-4
+
+
 @pytest.fixture(scope="module")
 def small_dose():
     wl = W.workload_full_10x10(4000)
