@@ -301,14 +301,11 @@ def commissioning_block(lsm, W, reps: int = 3, n_batches: int = 16):
     sel &= S1 > 0
     u_A = float(np.mean(sig.reshape(A.shape)[sel] / S1[sel]))
     t_basis = float(np.median(ms)) / 1e3
-    # group electron PSRs (sub-source 2) per energy bin: 200 photon PSRs + 10 units
-    n_ph = 2 * m.n_e * m.n_r
-    Ae = A[:, n_ph:].reshape(A.shape[0], m.n_e, m.n_r).sum(axis=2)
-    Ag = np.concatenate([A[:, :n_ph], Ae], axis=1)
+    # electron PSRs (sub-source 2) grouped per energy bin: 200 photon PSRs + 10 units
+    Ag = lsm.lsm_basis_matrix(tally, psl, ph, units=True)
     # synthetic measurement from an independent basis run, known weights, 0.5 % noise
     basis(999)
-    A2 = lsm.lsm_basis_matrix(tally, psl, ph)
-    A2g = np.concatenate([A2[:, :n_ph], A2[:, n_ph:].reshape(A.shape[0], m.n_e, m.n_r).sum(axis=2)], axis=1)
+    A2g = lsm.lsm_basis_matrix(tally, psl, ph, units=True)
     x_true = W.commissioning_truth(Ag.shape[1])
     rng = np.random.default_rng(3)
     bvec = A2g @ x_true * (1 + 0.005 * rng.standard_normal(Ag.shape[0]))
@@ -634,8 +631,11 @@ def main():
     # (checked from the run statistics after the timed steps)
     step_opts = dataclasses.replace(opts, no_sync=True)
 
+    # the linac's PSR model is loaded once, like the phantom (lsm_model_create)
+    model_h = lsm.lsm_model_create(wl.model)
+
     def step(i):
-        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True)
+        psl = lsm.lsm_build_psl(model_h, wl.beams, n_plan, async_=True)
         lsm.lsm_tally_reset(tally)
         lsm.lsm_run(psl, ph, tally, seed0 + i, step_opts)
         d, s = lsm.lsm_dose(tally, ph, psl.denom / n_plan, device=True)
@@ -658,7 +658,7 @@ def main():
     def e2e_enqueue(i, stream):
         phh = lsm.lsm_phantom_create(host_ph, stream=stream)          # host rho/mat -> device
         phh.desc = wl.phantom
-        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True, stream=stream)   # host model -> device
+        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True, stream=stream)   # host model -> handle -> device
         tt = lsm.lsm_tally_create(phh, stream=stream)
         lsm.lsm_run(psl, phh, tt, 5000 + i, e2e_opts, stream=stream)
         return phh, psl, tt, stream

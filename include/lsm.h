@@ -50,6 +50,7 @@ typedef enum {
 typedef enum { LSM_MEM_HOST = 0, LSM_MEM_DEVICE = 1 } lsm_mem;
 
 typedef void *lsm_stream;              /* cudaStream_t */
+typedef struct lsm_model lsm_model;
 typedef struct lsm_psl lsm_psl;
 typedef struct lsm_phantom lsm_phantom;
 typedef struct lsm_tally lsm_tally;
@@ -81,6 +82,32 @@ typedef struct {
     double e_lo[3], de[3];
     const double *w, *mix_c, *mix_mu, *mix_sa, *mix_sb, *e_sa, *e_sb;
 } lsm_psr_model;
+
+/*
+ * lsm_model_create -- the PSR model of Sec. 2.1.1 as a library handle: checks
+ * `psr` against the ranges above and keeps its own host copy of every array
+ * (the caller's arrays may be freed or changed afterwards without affecting
+ * the handle). Plans are built from the handle (lsm_build_psl); a plan does
+ * not refer to its model once the build call has returned, so the model may
+ * be destroyed while plans built from it are still in use. A commissioned
+ * model (Sec. 2.2.4: the PSR weights W_R scaled by x) is a new handle.
+ * Errors: LSM_ERR_ARG (NULL pointers or a value out of range; *out = NULL).
+ */
+lsm_status lsm_model_create(const lsm_psr_model *psr, lsm_model **out);
+void lsm_model_destroy(lsm_model *model);
+/*
+ * lsm_model_commission -- Sec. 2.2.4: the commissioned model, a new handle
+ * whose PSR weights are W_R x_R. x (host, n_x values >= 0): either one factor
+ * per PSR (n_x = 3 n_e n_r, in PSR order (s n_e + e) n_r + R), or the solution
+ * of Eq. 8 over lsm_basis_matrix_units' columns (n_x = 2 n_e n_r + n_e: the
+ * photon PSRs, then one factor per electron energy bin, applied to all rings
+ * of that bin). Every other parameter is the model's.
+ * Errors: LSM_ERR_ARG (NULL pointers, another n_x, a negative or non-finite x).
+ */
+lsm_status lsm_model_commission(const lsm_model *model, const double *x, int32_t n_x, lsm_model **out);
+/* lsm_model_weights -- copy the model's PSR weights W_R to host memory w
+ * (double [3][n_e][n_r]), e.g. the commissioned weights. */
+lsm_status lsm_model_weights(const lsm_model *model, double *w);
 
 /*
  * Beams of a plan (step S1). Jaw edges x1 < x2, y1 < y2 are given at the
@@ -126,10 +153,11 @@ typedef struct {
  *     particle of such a run carries PSR index k.
  * The plan is periodic: history g uses plan position g mod (plan size), so a
  * run of B passes is B statistically independent batches.
- * Errors: LSM_ERR_ARG on invalid model/beams, n_hist < 1 (whole-source), an
- * empty sampling area, or a plan larger than 2^31 entries.
+ * model: a handle from lsm_model_create (read only during the call).
+ * Errors: LSM_ERR_ARG on a NULL model, invalid beams, n_hist < 1
+ * (whole-source), an empty sampling area, or a plan larger than 2^31 entries.
  */
-lsm_status lsm_build_psl(const lsm_psr_model *model, const lsm_beams *beams, int64_t n_hist,
+lsm_status lsm_build_psl(const lsm_model *model, const lsm_beams *beams, int64_t n_hist,
                          const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream);
 /*
  * lsm_build_psl_async -- lsm_build_psl without waiting for the build: returns
@@ -139,7 +167,7 @@ lsm_status lsm_build_psl(const lsm_psr_model *model, const lsm_beams *beams, int
  * also where an empty sampling area is reported (LSM_ERR_ARG). Argument
  * errors are returned at once. Per-PSR plans are built synchronously.
  */
-lsm_status lsm_build_psl_async(const lsm_psr_model *model, const lsm_beams *beams, int64_t n_hist,
+lsm_status lsm_build_psl_async(const lsm_model *model, const lsm_beams *beams, int64_t n_hist,
                                const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream);
 /* Releases the plan; its device memory returns to the pool in the order of
  * the legacy default stream. Work using the plan on non-blocking streams must
@@ -312,6 +340,11 @@ lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], l
  * saved and restored in between (lsm_tally_read / lsm_tally_ledger, then
  * lsm_tally_load): the checkpoint of a dose calculation is its tally sums,
  * its statistics and the next batch index.
+ * e_queue_cap: capacity of the secondary-electron queue in particles (0 =
+ * 4 chunk + 2^18, which no run of the stated physics fills); a smaller queue
+ * bounds the workspace's memory, and electrons created once it is full are
+ * deposited where they are created, counted in stats[9] and reported as
+ * LSM_ERR_OVERFLOW (the energy balance still holds).
  */
 typedef struct {
     int32_t electron_mode;
@@ -323,15 +356,20 @@ typedef struct {
     int32_t use_graph;
     int32_t no_sync;
     int64_t first_batch;
+    int32_t e_queue_cap;
+    int32_t reserved;
 } lsm_run_opts;
 
 /*
  * lsm_transport -- transport the accepted particles (status 0) of `in`
  * (device SoA of n records, as written by lsm_sample with the same seed) and
  * every secondary they create, depositing into `tally`'s open batch. Each
- * particle draws from its own Philox stream: primaries use stream 1 of their
- * history; a particle created at an interaction uses the stream id given by
- * its parent's block at counter (draw index | 2^31).
+ * particle draws from its own Philox stream (key = seed, counter = (history
+ * lo, history hi, stream id, draw index)): primaries use stream id 1; a
+ * particle created at an interaction takes as stream id MurmurHash3's fmix32
+ * finaliser of its parent's stream id combined with the parent's draw counter
+ * and the child's slot (pair event: electron 0, positron 1, annihilation
+ * photons 2 and 3), ids below 2 shifted up by 2 (0 and 1 are reserved).
  * Errors: LSM_ERR_ARG on mismatched handles; LSM_ERR_OVERFLOW when the
  * secondary-electron queue filled up (the excess electrons were deposited at
  * their creation point and counted in stats[9]).
@@ -368,6 +406,19 @@ lsm_status lsm_dose(const lsm_tally *t, const lsm_phantom *ph, double scale, dou
 lsm_status lsm_basis_matrix(const lsm_tally *t, const lsm_psl *psl, const lsm_phantom *ph,
                             const uint16_t *idx3d, lsm_mem idx3d_mem, double *A, lsm_mem mem,
                             lsm_stream stream);
+
+/*
+ * lsm_basis_matrix_units -- the basis matrix over the unknowns of Eq. 8
+ * (Sec. 2.2.3): one column per photon PSR (primary and scatter, as
+ * lsm_basis_matrix), then one column per electron energy bin e, the sum of the
+ * n_r electron PSR columns of that bin (the "effective electron unit": the
+ * electron PSRs are too weak to be commissioned one by one). A: double
+ * [n_beams n_rows][2 n_e n_r + n_e] in `mem` (rows as lsm_basis_matrix). The
+ * tally's PSR count must be 3 n_e n_r of the plan's model.
+ * Errors: as lsm_basis_matrix.
+ */
+lsm_status lsm_basis_matrix_units(const lsm_tally *t, const lsm_psl *psl, const lsm_phantom *ph, double *A,
+                                  lsm_mem mem, lsm_stream stream);
 
 /*
  * lsm_commission -- Eq. 8: x = argmin_{x >= 0} ||A x - b||^2 in FP64 on the
@@ -411,8 +462,13 @@ lsm_status lsm_commission(const double *A, int32_t m, int32_t n, const double *b
  * A (double [m][n], row-major), b (double [m]) and x (double [n]) are all
  * DEVICE pointers; x receives the solution (and is the projected-gradient
  * start when opts->use_x0 != 0, else it is set to 1). report is host memory
- * and may be NULL. The first call on a device looks up the array's device
- * address (once per device). Every call shares the one array, which keeps the
+ * and may be NULL; A, b or x that is not device or managed memory returns
+ * LSM_ERR_ARG (checked with cudaPointerGetAttributes). The first call on a
+ * device looks up the array's device address (once per device, with that
+ * device current) and keeps it for the life of the process: it assumes the
+ * device's primary context is never reset (after cudaDeviceReset the array may
+ * sit elsewhere; do not call this entry point again in that process). Make the
+ * first call before any stream capture. Every call shares the one array, which keeps the
  * previous call's contents: calls that overlap on the GPU (other streams or
  * host threads) race and must be serialised by the caller. Calls no
  * cudaMalloc or cudaFree. Synchronises the stream before returning.
@@ -435,6 +491,29 @@ lsm_status lsm_commission_static(const double *A, int32_t m, int32_t n, const do
  * lsm_timing_read synchronises the device, returns milliseconds and launch
  * counts per timer, and clears them when reset != 0. Disabled by default.
  */
+/*
+ * lsm_set_wait_limits -- bounds of the library's device-side waits, for
+ * tests of the give-up paths and for hosts that want failures reported
+ * sooner. Values < 0 keep the current setting.
+ *   stage_polls: polls of the mbarrier on which a transport CTA waits for its
+ *     interaction tables to arrive in shared memory (default 2^22). When they
+ *     run out, the CTA reads the tables from global memory instead (the same
+ *     values: results are unchanged), sets the run's fallback flag (see
+ *     lsm_run_fallbacks) and, before it exits, waits for its copy to land.
+ *     0 gives up at once.
+ *   conv_wait_ns: the 3x3x3 convolution kernels' wait on each pipeline
+ *     barrier (default 2e9 ns). When it runs out, the CTA stops, waits for its
+ *     own copies and tensor-core operations in flight (a fixed 100 ms bound),
+ *     releases its tensor memory and sets an error word that the next
+ *     synchronising denoiser call returns as LSM_ERR_TIMEOUT.
+ * Applies to launches queued after the call (captured graphs keep the
+ * values they were captured with).
+ */
+lsm_status lsm_set_wait_limits(int64_t stage_polls, int64_t conv_wait_ns);
+/* Number of transport CTAs that fell back to global-memory tables since the
+ * last reset (synchronises the device); reset != 0 clears it. */
+lsm_status lsm_run_fallbacks(int64_t *count, int reset);
+
 #define LSM_N_TIMERS 10
 lsm_status lsm_timing_enable(int on);
 lsm_status lsm_timing_read(double ms[LSM_N_TIMERS], int64_t launches[LSM_N_TIMERS], int reset);

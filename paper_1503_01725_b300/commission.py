@@ -4,12 +4,12 @@
    (40x40 and 5x5 cm2 open fields, SSD 100 cm) filling the PSR-indexed tally
    at the measurement points: the central-axis depth dose and the inline and
    crossline profiles at 1.5, 10 and 20 cm depth. Electron PSRs are grouped
-   per energy bin (Sec. 2.2.3).
+   per energy bin (Sec. 2.2.3) by lsm_basis_matrix_units.
 2. "Measurements": the doses of a linac whose PSR weights differ from the
    model's by known correction factors (a synthetic stand-in: no measured data
    exist here), computed by the same engine at high statistics.
 3. The correction factors from Eq. 8 (NNLS on the GPU), the commissioned
-   model W' = x W, and the doses of five open fields (40, 20, 10, 5, 2 cm)
+   model W' = x W (lsm_model_commission), and the doses of five open fields (40, 20, 10, 5, 2 cm)
    for the commissioned and the uncommissioned ("reference") model.
 4. The comparison of Sec. 3.2: depth doses (build-up: distance to agreement;
    beyond: RMS and maximum difference, Eq. 10-11) and profiles (inner and
@@ -65,20 +65,6 @@ def truth_factors(model: W.PSRModel, seed: int = 3) -> np.ndarray:
     """Known per-unit correction factors of the synthetic linac (photon PSRs,
     then one per electron energy bin)."""
     return W.commissioning_truth(2 * model.n_e * model.n_r + model.n_e, seed=seed)
-
-
-def expand(model: W.PSRModel, x: np.ndarray) -> np.ndarray:
-    """Per-PSR weights x W from per-unit factors (electron PSRs of one energy
-    bin share a factor)."""
-    n_ph = 2 * model.n_e * model.n_r
-    f = np.concatenate([x[:n_ph], np.repeat(x[n_ph:], model.n_r)])
-    return (f * model.w.reshape(-1)).reshape(model.w.shape)
-
-
-def group_electrons(model: W.PSRModel, A: np.ndarray) -> np.ndarray:
-    n_ph = 2 * model.n_e * model.n_r
-    return np.concatenate([A[:, :n_ph], A[:, n_ph:].reshape(A.shape[0], model.n_e, model.n_r).sum(axis=2)],
-                          axis=1)
 
 
 def field_histories(field_cm: float, n_large: float) -> int:
@@ -149,16 +135,18 @@ def run(case: Case | None = None, *, n_large: float = 2e9, hist_lo: int = 20_000
     w = m.w.reshape(-1)
     n_k = np.clip(np.round(w / w.max() * hist_hi), hist_lo, hist_hi).astype(np.int64)
     beams = W.beams(*[W.square_field(f) for f in COMMISSION_FIELDS])
-    psl = lsm.lsm_build_psl(m, beams, per_psr_hist=n_k)
+    mh = lsm.lsm_model_create(m)
+    psl = lsm.lsm_build_psl(mh, beams, per_psr_hist=n_k)
     tb = lsm.lsm_tally_create(ph, mode=1, idx3d=case.idx, n_rows=case.n_rows, n_psr=m.n_psr,
                               n_beams=beams.n_beams)
     lsm.lsm_run(psl, ph, tb, seed, lsm.RunOpts(electron_mode=1, n_batches=basis_batches))
-    A = group_electrons(m, lsm.lsm_basis_matrix(tb, psl, ph))
+    # columns: photon PSRs, then one effective electron unit per energy bin (Sec. 2.2.3)
+    A = lsm.lsm_basis_matrix(tb, psl, ph, units=True)
     torch.cuda.synchronize()
     t_basis = time.perf_counter() - t0
     # 2. measurements of the synthetic linac
     x_true = truth_factors(m)
-    m_true = m.with_weights(expand(m, x_true))
+    m_true = lsm.lsm_model_commission(mh, x_true)
     meas = {f: field_rows(ph, case, m_true, f, field_histories(f, n_large), seed + 100 + k)[0]
             for k, f in enumerate(FIELDS)}
     # 3. Eq. 8 on the two commissioning fields (rows beam-major, as A)
@@ -168,13 +156,13 @@ def run(case: Case | None = None, *, n_large: float = 2e9, hist_lo: int = 20_000
     # gradient projection from the uncommissioned weights (x = 1), Sec. 2.2.4
     x, rep = lsm.lsm_commission(A * scale, b * scale, method=method, max_iter=max_iter, delta=delta)
     t_fit = time.perf_counter() - t1
-    m_com = m.with_weights(expand(m, x))
+    m_com = lsm.lsm_model_commission(mh, x)
     t2 = time.perf_counter()
     calc = {f: field_rows(ph, case, m_com, f, field_histories(f, n_large), seed + 200 + k)[0]
             for k, f in enumerate(FIELDS)}
     torch.cuda.synchronize()
     t_val = time.perf_counter() - t2
-    ref = {f: field_rows(ph, case, m, f, field_histories(f, n_large), seed + 300 + k)[0]
+    ref = {f: field_rows(ph, case, mh, f, field_histories(f, n_large), seed + 300 + k)[0]
            for k, f in enumerate(FIELDS)}
     # 4. comparison
     # output factor: axis dose over 9-11 cm depth relative to the 10x10 field's
@@ -189,7 +177,8 @@ def run(case: Case | None = None, *, n_large: float = 2e9, hist_lo: int = 20_000
         fields[f"{f:g}x{f:g}"] = {"commissioned": compare_field(case, f, calc[f], meas[f]),
                                   "reference": compare_field(case, f, ref[f], meas[f])}
     return {
-        "x": x, "x_true": x_true, "nnls": rep, "model": m_com,
+        "x": x, "x_true": x_true, "nnls": rep, "model_handle": m_com,
+        "model": m.with_weights(lsm.lsm_model_weights(m_com)),
         "factor_rel_err": float(np.linalg.norm(x - x_true) / np.linalg.norm(x_true)),
         "fields": fields,
         "output_factors": {"measured": of_meas, "commissioned": of_com, "reference": of_ref,

@@ -12,7 +12,16 @@
 
 namespace lsm {
 
-lsm_status build_psl(const lsm_psr_model *, const lsm_beams *, int64_t, const int64_t *, lsm_psl **, cudaStream_t,
+lsm_status model_create(const lsm_psr_model *, lsm_model **);
+lsm_status read_fallbacks(int64_t *, int);
+extern int g_stage_polls;
+namespace dn {
+extern unsigned long long g_conv_wait_ns;
+}
+void model_destroy(lsm_model *);
+lsm_status model_commission(const lsm_model *, const double *, int32_t, lsm_model **);
+lsm_status model_weights(const lsm_model *, double *);
+lsm_status build_psl(const lsm_model *, const lsm_beams *, int64_t, const int64_t *, lsm_psl **, cudaStream_t,
                      bool);
 lsm_status free_psl(lsm_psl *);
 lsm_status resolve_psl(lsm_psl *);
@@ -26,7 +35,7 @@ lsm_status fold_batch(lsm_tally *, cudaStream_t, bool);
 lsm_status flush_partials(lsm_tally *, cudaStream_t);
 lsm_status dose_impl(const lsm_tally *, const lsm_phantom *, double, double *, double *, lsm_mem, cudaStream_t);
 lsm_status basis_impl(const lsm_tally *, const lsm_psl *, const lsm_phantom *, const uint16_t *, lsm_mem, double *,
-                      lsm_mem, cudaStream_t);
+                      lsm_mem, cudaStream_t, bool);
 lsm_status commission(const double *, int32_t, int32_t, const double *, lsm_mem, const lsm_nnls_opts *, double *,
                       lsm_nnls_report *, cudaStream_t);
 
@@ -237,7 +246,21 @@ lsm_status lsm_timing_read(double ms[LSM_N_TIMERS], int64_t launches[LSM_N_TIMER
 
 int64_t lsm_launch_count(void) { return (int64_t)lsm::g_launches.load(); }
 
-lsm_status lsm_build_psl(const lsm_psr_model *model, const lsm_beams *beams, int64_t n_hist,
+lsm_status lsm_set_wait_limits(int64_t stage_polls, int64_t conv_wait_ns)
+{
+    if (stage_polls > (1ll << 30)) return set_arg_error("lsm_set_wait_limits: stage_polls <= 2^30");
+    if (stage_polls >= 0) lsm::g_stage_polls = (int)stage_polls;
+    if (conv_wait_ns >= 0) lsm::dn::g_conv_wait_ns = (unsigned long long)conv_wait_ns;
+    return LSM_OK;
+}
+
+lsm_status lsm_run_fallbacks(int64_t *count, int reset) { return read_fallbacks(count, reset); }
+
+lsm_status lsm_model_create(const lsm_psr_model *psr, lsm_model **out) { return model_create(psr, out); }
+
+void lsm_model_destroy(lsm_model *model) { model_destroy(model); }
+
+lsm_status lsm_build_psl(const lsm_model *model, const lsm_beams *beams, int64_t n_hist,
                          const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream)
 {
     const int tk = timer_begin(0, S(stream));
@@ -246,7 +269,7 @@ lsm_status lsm_build_psl(const lsm_psr_model *model, const lsm_beams *beams, int
     return rc;
 }
 
-lsm_status lsm_build_psl_async(const lsm_psr_model *model, const lsm_beams *beams, int64_t n_hist,
+lsm_status lsm_build_psl_async(const lsm_model *model, const lsm_beams *beams, int64_t n_hist,
                                const int64_t *per_psr_hist, lsm_psl **out, lsm_stream stream)
 {
     const int tk = timer_begin(0, S(stream));
@@ -510,8 +533,21 @@ lsm_status lsm_dose(const lsm_tally *t, const lsm_phantom *ph, double scale, dou
 lsm_status lsm_basis_matrix(const lsm_tally *t, const lsm_psl *psl, const lsm_phantom *ph, const uint16_t *idx3d,
                             lsm_mem idx3d_mem, double *A, lsm_mem mem, lsm_stream stream)
 {
-    return basis_impl(t, psl, ph, idx3d, idx3d_mem, A, mem, S(stream));
+    return basis_impl(t, psl, ph, idx3d, idx3d_mem, A, mem, S(stream), false);
 }
+
+lsm_status lsm_basis_matrix_units(const lsm_tally *t, const lsm_psl *psl, const lsm_phantom *ph, double *A,
+                                  lsm_mem mem, lsm_stream stream)
+{
+    return basis_impl(t, psl, ph, nullptr, LSM_MEM_DEVICE, A, mem, S(stream), true);
+}
+
+lsm_status lsm_model_commission(const lsm_model *model, const double *x, int32_t n_x, lsm_model **out)
+{
+    return model_commission(model, x, n_x, out);
+}
+
+lsm_status lsm_model_weights(const lsm_model *model, double *w) { return model_weights(model, w); }
 
 lsm_status lsm_commission(const double *A, int32_t m, int32_t n, const double *b, lsm_mem mem,
                           const lsm_nnls_opts *opts, double *x, lsm_nnls_report *report, lsm_stream stream)

@@ -37,7 +37,8 @@ namespace dn {
 constexpr int kTileM = 128;
 constexpr int kSlabVox = kTileM + 2;            // one voxel of x halo either side
 constexpr int kThreads = 192;                   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-constexpr unsigned long long kWaitNs = 2000000000ull;
+// drain bound after a give-up: copies and MMAs in flight finish in microseconds
+constexpr unsigned long long kDrainNs = 100000000ull;
 
 // A slab row is one voxel's KC input channels (2 KC bytes), stored with the
 // matching TMA / UMMA swizzle (32, 64 or 128 bytes); slabs start on 1024-byte
@@ -83,6 +84,7 @@ struct ConvArgs {
     int tiles_per_vol, n_tiles;
     int relu;
     unsigned *err;
+    unsigned long long wait_ns;   // bound of each pipeline wait (lsm_set_wait_limits)
 };
 
 // ------------------------------------------------------------ PTX helpers ---
@@ -121,20 +123,37 @@ __device__ __forceinline__ bool mb_test(uint64_t *b, unsigned parity)
     return ok != 0;
 }
 
-// Wait for the phase of parity `parity` to complete. Bounded: after kWaitNs,
+// Wait for the phase of parity `parity` to complete. Bounded: after wait_ns,
 // or when another role has given up, returns false; a timeout sets `code` in
 // *err and the CTA's abort flag.
-__device__ bool mb_wait(uint64_t *b, unsigned parity, volatile int *abort_flag, unsigned *err, unsigned code)
+__device__ bool mb_wait(uint64_t *b, unsigned parity, volatile int *abort_flag, unsigned *err, unsigned code,
+                        unsigned long long wait_ns)
 {
     if (mb_test(b, parity)) return true;
     const unsigned long long t0 = gtime();
     for (;;) {
         if (mb_test(b, parity)) return true;
         if (*abort_flag) return false;
-        if (gtime() - t0 > kWaitNs) {
+        if (gtime() - t0 > wait_ns) {
             *abort_flag = 1;
             atomicOr(err, code);
             return false;
+        }
+    }
+}
+
+// After the pipeline stops (normally or after a give-up): wait, bounded by
+// kDrainNs and ignoring the abort flag, for a phase the CTA's own copies or
+// tensor-core operations will complete, so that none is in flight when the
+// CTA releases its tensor memory and exits. A drain that runs out sets 16.
+__device__ void mb_drain(uint64_t *b, unsigned parity, unsigned *err)
+{
+    if (mb_test(b, parity)) return;
+    const unsigned long long t0 = gtime();
+    while (!mb_test(b, parity)) {
+        if (gtime() - t0 > kDrainNs) {
+            atomicOr(err, 16u);
+            return;
         }
     }
 }
@@ -199,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
 {
     using C = Cfg<COUT, KC>;
     extern __shared__ uint8_t dsm[];
-    __shared__ __align__(8) uint64_t full[C::kStages], empty[C::kStages], accf[2], acce[2];
+    __shared__ __align__(8) uint64_t full[C::kStages], empty[C::kStages], accf[2], acce[2], mma_done;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     const uint32_t sbase = (s2u(dsm) + 1023u) & ~1023u;
@@ -213,6 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
             mb_init(&accf[i], 1);
             mb_init(&acce[i], 4);
         }
+        mb_init(&mma_done, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -239,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
                 for (int k = 0; k < ksteps; ++k, ++it) {
                     const int s = it % C::kStages;
                     if (it >= C::kStages &&
-                        !mb_wait(&empty[s], (unsigned)((it / C::kStages) - 1) & 1u, &abort_flag, a.err, 1u)) {
+                        !mb_wait(&empty[s], (unsigned)((it / C::kStages) - 1) & 1u, &abort_flag, a.err, 1u, a.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -261,6 +281,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
                     bulk_load(sb, a.wimg + (size_t)(kc * 3 + dz) * 9 * COUT * KC, C::kB, &full[s]);
                 }
             }
+            // loads issued (it of them) land before the CTA moves on: the
+            // newest phase of each stage's full barrier (already complete
+            // unless the pipeline stopped early)
+            for (int j = it > C::kStages ? it - C::kStages : 0; j < it; ++j)
+                mb_drain(&full[j % C::kStages], (unsigned)(j / C::kStages) & 1u, a.err);
         }
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issuer
@@ -272,12 +297,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
             bool ok = true;
             for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x, ++li) {
                 const int acc = li & 1;
-                if (li >= 2 && !mb_wait(&acce[acc], (unsigned)((li >> 1) - 1) & 1u, &abort_flag, a.err, 2u)) break;
+                if (li >= 2 && !mb_wait(&acce[acc], (unsigned)((li >> 1) - 1) & 1u, &abort_flag, a.err, 2u, a.wait_ns))
+                    break;
                 tc_after();
                 const uint32_t d = tmem + (uint32_t)(acc * C::kAccCols);
                 for (int k = 0; k < ksteps; ++k, ++it) {
                     const int s = it % C::kStages;
-                    if (!mb_wait(&full[s], (unsigned)(it / C::kStages) & 1u, &abort_flag, a.err, 4u)) {
+                    if (!mb_wait(&full[s], (unsigned)(it / C::kStages) & 1u, &abort_flag, a.err, 4u, a.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -315,13 +341,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3d(const __grid_constant__ 
                 }
                 if (ok) mma_commit(&accf[acc]);
             }
+            // every MMA this thread issued has completed before tensor memory is released
+            mma_commit(&mma_done);
+            mb_drain(&mma_done, 0u, a.err);
         }
     } else {   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
         const int q = warp & 3;
         int li = 0;
         for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++li) {
             const int acc = li & 1;
-            const bool ok = mb_wait(&accf[acc], (unsigned)(li >> 1) & 1u, &abort_flag, a.err, 8u);
+            const bool ok = mb_wait(&accf[acc], (unsigned)(li >> 1) & 1u, &abort_flag, a.err, 8u, a.wait_ns);
             if (!__all_sync(0xFFFFFFFFu, ok)) break;
             tc_after();
             const int vol = t / a.tiles_per_vol;
@@ -569,6 +598,9 @@ EncodeTiled encode_fn()
     return fn;
 }
 
+// bound of each pipeline wait of the convolution kernels (lsm_set_wait_limits)
+unsigned long long g_conv_wait_ns = 2000000000ull;
+
 unsigned *g_err_word = nullptr;
 unsigned *err_word()
 {
@@ -686,6 +718,7 @@ lsm_status conv_forward(const lsm_conv3d *cv, const lsm_vol *in, const lsm_vol *
     a.d = in->d; a.h = in->h; a.w = in->w;
     a.relu = cv->relu;
     a.err = err;
+    a.wait_ns = g_conv_wait_ns;
     const int tk = timer_begin(8, st);
     lsm_status r = LSM_ERR_ARG;
     switch (cv->cout * 1000 + cv->kc) {

@@ -61,6 +61,13 @@ struct PslGeom {
 
 }  // namespace lsm
 
+// A validated PSR model (lsm_model_create): a library-owned host copy of the
+// caller's arrays, which the plan builds read.
+struct lsm_model {
+    lsm_psr_model m;      // array pointers point into `data`
+    double *data;
+};
+
 struct lsm_psl {
     int device;
     uint64_t uid;         // unique per created plan (graph-cache key; addresses can be reused)

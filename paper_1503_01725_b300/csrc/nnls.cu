@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "handles.cuh"
@@ -610,7 +611,11 @@ constexpr size_t kStaticDoubles = 2 * kStaticGram + kStaticMaxN + 16;
 
 static __device__ __align__(256) double g_nnls_scratch[kStaticDoubles];
 
-// device address of g_nnls_scratch per device, looked up once per device
+// Device address of g_nnls_scratch per device, looked up once per device on
+// the first call with that device current. The cache assumes one CUDA context
+// per device for the life of the process (the runtime's primary context): after
+// cudaDeviceReset the module may be loaded again at another address, so a
+// process that resets a device must not call lsm_commission_static afterwards.
 std::mutex g_scratch_mu;
 double *g_scratch_ptr[64] = {};
 
@@ -618,6 +623,23 @@ __global__ void k_fill(double *__restrict__ x, double v, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = v;
+}
+
+// A, b and x must be memory the GPU addresses directly (device or managed
+// allocations). cudaPointerGetAttributes allocates nothing; a host pointer
+// would otherwise reach the kernels and fault.
+lsm_status check_device_pointer(const void *p, const char *what)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_arg_error((std::string("lsm_commission_static: ") + what + " is not a device pointer").c_str());
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return set_arg_error((std::string("lsm_commission_static: ") + what +
+                              " must be device or managed memory (got host or unregistered memory)").c_str());
+    return LSM_OK;
 }
 
 lsm_status scratch_address(double **out)
@@ -649,6 +671,9 @@ extern "C" lsm_status lsm_commission_static(const double *A, int32_t m, int32_t 
     if (!A || !b || !x || m < 1 || n < 1) return set_arg_error("lsm_commission_static: NULL pointer or empty problem");
     if (n > kStaticMaxN)
         return set_arg_error("lsm_commission_static: at most 256 unknowns fit the fixed scratch; use lsm_commission");
+    if (lsm_status pc = check_device_pointer(A, "A")) return pc;
+    if (lsm_status pc = check_device_pointer(b, "b")) return pc;
+    if (lsm_status pc = check_device_pointer(x, "x")) return pc;
     lsm_nnls_opts o = {0, 0, 1e-12, 1e-4, 0.5, 0};
     if (opts) o = *opts;
     if (o.method != 0 && o.method != 1) return set_arg_error("lsm_commission_static: method must be 0 or 1");

@@ -625,36 +625,106 @@ lsm_status resolve_psl(lsm_psl *P)
     return LSM_OK;
 }
 
-lsm_status build_psl(const lsm_psr_model *M, const lsm_beams *B, int64_t n_hist,
-                     const int64_t *per_psr_hist, lsm_psl **out, cudaStream_t st, bool async)
+// Validation of a PSR model (the ranges stated at lsm_psr_model).
+static lsm_status validate_model(const lsm_psr_model *M)
 {
-    if (!M || !B || !out) return set_arg_error("lsm_build_psl: NULL argument");
-    *out = nullptr;
     if (M->n_e < 1 || M->n_e > 64 || M->n_r < 1 || M->n_r > 32)
-        return set_arg_error("lsm_build_psl: need 1 <= n_e <= 64 and 1 <= n_r <= 32");
-    if (!(M->dr > 0) || !(M->z_phsp > 0) || !(M->sigma_s >= 0) || !isfinite(M->sigma_s))
-        return set_arg_error("lsm_build_psl: dr, z_phsp must be > 0 and sigma_s >= 0");
+        return set_arg_error("lsm_model_create: need 1 <= n_e <= 64 and 1 <= n_r <= 32");
+    if (!(M->dr > 0) || !(M->z_phsp > 0) || !(M->sigma_s >= 0) || !isfinite(M->sigma_s) || !isfinite(M->dr) ||
+        !isfinite(M->z_phsp))
+        return set_arg_error("lsm_model_create: dr, z_phsp must be > 0 and sigma_s >= 0");
     for (int s = 0; s < 3; ++s)
-        if (!(M->de[s] > 0) || !isfinite(M->e_lo[s]) || M->e_lo[s] < 0)
-            return set_arg_error("lsm_build_psl: energy bins must have de > 0, e_lo >= 0");
+        if (!(M->de[s] > 0) || !isfinite(M->de[s]) || !isfinite(M->e_lo[s]) || M->e_lo[s] < 0)
+            return set_arg_error("lsm_model_create: energy bins must have de > 0, e_lo >= 0");
     if (!M->w || !M->mix_c || !M->mix_mu || !M->mix_sa || !M->mix_sb || !M->e_sa || !M->e_sb)
-        return set_arg_error("lsm_build_psl: NULL model array");
-    const int ne = M->n_e, nr = M->n_r, nxy = 2 * nr, npsl = nxy * nxy;
+        return set_arg_error("lsm_model_create: NULL model array");
+    const int ne = M->n_e, nr = M->n_r;
     const size_t nw = 3 * (size_t)ne * nr, nm = (size_t)ne * nr * 3, nes = (size_t)ne * nr;
-    if (!finite_nonneg(M->w, nw)) return set_arg_error("lsm_build_psl: PSR weights must be finite, >= 0");
-    if (!finite_nonneg(M->mix_c, nm)) return set_arg_error("lsm_build_psl: mixture weights must be >= 0");
+    if (!finite_nonneg(M->w, nw)) return set_arg_error("lsm_model_create: PSR weights must be finite, >= 0");
+    if (!finite_nonneg(M->mix_c, nm)) return set_arg_error("lsm_model_create: mixture weights must be >= 0");
     for (size_t i = 0; i < nes; ++i) {
         const double *c = M->mix_c + 3 * i;
-        if (!(c[0] + c[1] + c[2] > 0)) return set_arg_error("lsm_build_psl: mixture weights sum to 0");
+        if (!(c[0] + c[1] + c[2] > 0)) return set_arg_error("lsm_model_create: mixture weights sum to 0");
         for (int k = 0; k < 3; ++k) {
             const double mu = M->mix_mu[3 * i + k], sa = M->mix_sa[3 * i + k], sb = M->mix_sb[3 * i + k];
             if (!(sa >= 0) || !(sb >= 0) || !(fabs(mu) + 5.8 * sa < 0.5 * kPiD) || !(5.8 * sb < 0.5 * kPiD))
-                return set_arg_error("lsm_build_psl: scatter direction mixture out of range");
+                return set_arg_error("lsm_model_create: scatter direction mixture out of range");
         }
         if (!(M->e_sa[i] >= 0) || !(M->e_sb[i] >= 0) || !(5.8 * M->e_sa[i] < 0.5 * kPiD) ||
             !(5.8 * M->e_sb[i] < 0.5 * kPiD))
-            return set_arg_error("lsm_build_psl: electron direction widths out of range");
+            return set_arg_error("lsm_model_create: electron direction widths out of range");
     }
+    return LSM_OK;
+}
+
+lsm_status model_create(const lsm_psr_model *M, lsm_model **out)
+{
+    if (!M || !out) return set_arg_error("lsm_model_create: NULL argument");
+    *out = nullptr;
+    if (lsm_status rc = validate_model(M)) return rc;
+    const size_t nw = 3 * (size_t)M->n_e * M->n_r, nm = (size_t)M->n_e * M->n_r * 3, nes = (size_t)M->n_e * M->n_r;
+    lsm_model *h = (lsm_model *)calloc(1, sizeof(lsm_model));
+    double *d = (double *)malloc((nw + 4 * nm + 2 * nes) * sizeof(double));
+    if (!h || !d) { free(h); free(d); return set_arg_error("lsm_model_create: out of host memory"); }
+    h->m = *M;
+    h->data = d;
+    auto put = [&](const double *src, size_t n) { memcpy(d, src, n * sizeof(double)); const double *p = d; d += n; return p; };
+    h->m.w = put(M->w, nw);
+    h->m.mix_c = put(M->mix_c, nm);
+    h->m.mix_mu = put(M->mix_mu, nm);
+    h->m.mix_sa = put(M->mix_sa, nm);
+    h->m.mix_sb = put(M->mix_sb, nm);
+    h->m.e_sa = put(M->e_sa, nes);
+    h->m.e_sb = put(M->e_sb, nes);
+    *out = h;
+    return LSM_OK;
+}
+
+void model_destroy(lsm_model *h)
+{
+    if (!h) return;
+    free(h->data);
+    free(h);
+}
+
+lsm_status model_weights(const lsm_model *h, double *w)
+{
+    if (!h || !w) return set_arg_error("lsm_model_weights: NULL argument");
+    memcpy(w, h->m.w, (size_t)3 * h->m.n_e * h->m.n_r * sizeof(double));
+    return LSM_OK;
+}
+
+// The commissioned model (Sec. 2.2.4): PSR weights W_R scaled by the fitted
+// factors x, either one per PSR (3 n_e n_r) or one per unknown of Eq. 8
+// (2 n_e n_r photon PSRs, then one per electron energy bin applied to every
+// ring of that bin).
+lsm_status model_commission(const lsm_model *h, const double *x, int32_t n_x, lsm_model **out)
+{
+    if (!h || !x || !out) return set_arg_error("lsm_model_commission: NULL argument");
+    *out = nullptr;
+    const int ne = h->m.n_e, nr = h->m.n_r, n_ph = 2 * ne * nr;
+    if (n_x != 3 * ne * nr && n_x != n_ph + ne)
+        return set_arg_error("lsm_model_commission: x needs 3 n_e n_r (per PSR) or 2 n_e n_r + n_e (per unit) values");
+    for (int i = 0; i < n_x; ++i)
+        if (!(x[i] >= 0) || !isfinite(x[i])) return set_arg_error("lsm_model_commission: x must be finite, >= 0");
+    std::vector<double> w((size_t)3 * ne * nr);
+    for (int k = 0; k < 3 * ne * nr; ++k) {
+        const double f = n_x == 3 * ne * nr ? x[k] : (k < n_ph ? x[k] : x[n_ph + (k - n_ph) / nr]);
+        w[k] = h->m.w[k] * f;
+    }
+    lsm_psr_model m = h->m;
+    m.w = w.data();
+    return model_create(&m, out);
+}
+
+lsm_status build_psl(const lsm_model *Mh, const lsm_beams *B, int64_t n_hist,
+                     const int64_t *per_psr_hist, lsm_psl **out, cudaStream_t st, bool async)
+{
+    if (!Mh || !B || !out) return set_arg_error("lsm_build_psl: NULL argument");
+    *out = nullptr;
+    const lsm_psr_model *M = &Mh->m;     // validated by lsm_model_create
+    const int ne = M->n_e, nr = M->n_r, nxy = 2 * nr, npsl = nxy * nxy;
+    const size_t nw = 3 * (size_t)ne * nr, nm = (size_t)ne * nr * 3, nes = (size_t)ne * nr;
     if (B->n_beams < 1 || B->n_beams > 16 || !B->jaws) return set_arg_error("lsm_build_psl: 1..16 beams");
     if (!(B->sad > B->z_jaw_x && B->z_jaw_x > M->z_phsp && B->sad > B->z_jaw_y && B->z_jaw_y > M->z_phsp))
         return set_arg_error("lsm_build_psl: need z_phsp < jaw planes < sad");

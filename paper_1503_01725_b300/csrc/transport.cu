@@ -57,6 +57,7 @@ struct TP {
     RunStats *stats;
     IterCounters *cnt;
     int ctas_per_sm;           // transport grid: CTAs per SM (0: as many as fit)
+    int stage_polls;           // mbarrier polls before a CTA falls back to global-memory tables
     // per-history energy ledger (MODE 2 kernels only): hl[2h] source energy,
     // hl[2h + 1] deposited + escaped + rejected energy of history hl_g0 + h
     double *hl;
@@ -83,12 +84,17 @@ constexpr int kXsBytes = 2 * kGrid * 16;                                      //
 // radiation lengths (g/cm^2): water-like 36.08, bone 21.68
 
 // ---------------------------------------------------------------- tables ---
+// CTAs that gave up waiting for their tables (lsm_run_fallbacks)
+__device__ unsigned long long g_stage_fallbacks;
+
 // Stage the interaction tables into shared memory with one bulk asynchronous
-// copy (cp.async.bulk, completion on an mbarrier). The wait is bounded; on
-// timeout the block reports through *err and runs from global memory.
+// copy (cp.async.bulk, completion on an mbarrier). The wait is bounded by
+// `polls`; when it runs out the block reports through *err and the fallback
+// counter and runs from global memory (drain_stage, before it exits, waits
+// for the copy that is still in flight).
 template <bool FULL>
 __device__ __forceinline__ bool stage_tables(float4 *s_xs, const float4 *g_xs, const float *g_mumax,
-                                             uint64_t *mbar, unsigned *err)
+                                             uint64_t *mbar, unsigned *err, int polls)
 {
     constexpr uint32_t bytes = FULL ? (uint32_t)kTableBytes : (uint32_t)kXsBytes;
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(mbar);
@@ -112,7 +118,7 @@ __device__ __forceinline__ bool stage_tables(float4 *s_xs, const float4 *g_xs, c
     }
     __syncthreads();
     uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
+    for (int it = 0; it < polls && !done; ++it) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
@@ -120,8 +126,28 @@ __device__ __forceinline__ bool stage_tables(float4 *s_xs, const float4 *g_xs, c
             : "memory");
     }
     const int all = __syncthreads_and(done);
-    if (!all && threadIdx.x == 0) atomicOr(err, 1u);
+    if (!all && threadIdx.x == 0) {
+        atomicOr(err, 1u);
+        atomicAdd(&g_stage_fallbacks, 1ull);
+    }
     return all != 0;
+}
+
+// A CTA that fell back must not exit while its bulk copy may still be writing
+// its shared memory: thread 0 waits for the copy to land (at most 2^26 polls;
+// the copy of 52 KB takes microseconds).
+__device__ __forceinline__ void drain_stage(uint64_t *mbar)
+{
+    if (threadIdx.x != 0) return;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(mbar);
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 26) && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+    }
 }
 
 __device__ __forceinline__ void tab_pos(float inv_dlnE, float E, int &i, float &f)
@@ -286,6 +312,22 @@ __device__ __forceinline__ uint32_t push_slot(uint32_t *counter)
     if (g.thread_rank() == 0) base = atomicAdd(counter, (uint32_t)g.size());
     base = g.shfl(base, 0);
     return base + g.thread_rank();
+}
+
+// An electron entering the phantom from the source (or a caller's particle
+// list): queued, or, when the electron queue is full (a run with a small
+// e_queue_cap), deposited in the voxel where it enters and counted.
+template <int MODE>
+__device__ __forceinline__ void enqueue_source_electron(const TP &T, Acc &A, const Queue &eq, uint32_t slot, float lx,
+                                                        float ly, float lz, float u, float v, float w, float E,
+                                                        uint32_t glo, uint32_t ghi, uint32_t pb)
+{
+    if (slot < eq.cap) {
+        store_part(eq, slot, lx, ly, lz, u, v, w, E, glo, ghi, 1u, pb);
+    } else {
+        atomicAdd(&T.stats->c[9], 1ull);
+        deposit<MODE>(T, A, voxel(T, lx, ly, lz), E, pb, glo, ghi);
+    }
 }
 
 template <int MODE>
@@ -514,7 +556,7 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
     if ((uint64_t)blockIdx.x * blockDim.x >= n_in) return;
     float4 *s_xs = reinterpret_cast<float4 *>(smem);
     float *s_mm = reinterpret_cast<float *>(smem + 2 * kGrid * 16);
-    const bool staged = stage_tables<KIND == 0>(s_xs, T.xs, T.mumax, &mbar, &T.cnt->pad);
+    const bool staged = stage_tables<KIND == 0>(s_xs, T.xs, T.mumax, &mbar, &T.cnt->pad, T.stage_polls);
     const float4 *xs = staged ? s_xs : T.xs;
     const float *mm = staged ? s_mm : T.mumax;
     uint32_t *head = &T.cnt->head[qi];
@@ -636,6 +678,7 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
             store_part(eq, ob + lane, -1.0f, -1.0f, -1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0u, 0u, 2u, 0u);
     }
     flush_acc(T, A);
+    if (!staged) drain_stage(&mbar);
 }
 
 // ------------------------------------------------------------ sampling ---
@@ -757,8 +800,8 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
                 if (local_e) {
                     deposit<MODE>(T, A, voxel(T, lx, ly, lz), o.E, pb, (uint32_t)g, (uint32_t)(g >> 32));
                 } else {
-                    store_part(eq, be + __popc(me & lt), lx, ly, lz, o.u, o.v, o.w, o.E, (uint32_t)g,
-                               (uint32_t)(g >> 32), 1u, pb);
+                    enqueue_source_electron<MODE>(T, A, eq, be + __popc(me & lt), lx, ly, lz, o.u, o.v, o.w, o.E,
+                                                  (uint32_t)g, (uint32_t)(g >> 32), pb);
                 }
             }
         }
@@ -851,8 +894,8 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
                 if (local_e)
                     deposit<MODE>(T, A, voxel(T, lx, ly, lz), P.E[i], pb, 0u, 0u);
                 else
-                    store_part(eq, be + __popc(me & lt), lx, ly, lz, P.u[i], P.v[i], P.w[i], P.E[i],
-                               (uint32_t)g, (uint32_t)(g >> 32), 1u, pb);
+                    enqueue_source_electron<MODE>(T, A, eq, be + __popc(me & lt), lx, ly, lz, P.u[i], P.v[i],
+                                                  P.w[i], P.E[i], (uint32_t)g, (uint32_t)(g >> 32), pb);
             }
         }
     }
@@ -945,8 +988,8 @@ __global__ void __launch_bounds__(256) k_pslfile_enqueue(const PslRec *__restric
                 if (local_e)
                     deposit<MODE>(T, A, voxel(T, lx, ly, 0.0f), E, pb, 0u, 0u);
                 else
-                    store_part(eq, be + __popc(me & lt), lx, ly, 0.0f, u, v, w, E, (uint32_t)g, (uint32_t)(g >> 32),
-                               1u, pb);
+                    enqueue_source_electron<MODE>(T, A, eq, be + __popc(me & lt), lx, ly, 0.0f, u, v, w, E,
+                                                  (uint32_t)g, (uint32_t)(g >> 32), pb);
             }
         }
     }
@@ -1087,6 +1130,36 @@ __global__ void k_basis(const double *__restrict__ s1, const double *__restrict_
     }
 }
 
+// The same matrix with the electron PSRs of each energy bin summed into one
+// column (the effective electron unit of Sec. 2.2.3): columns [0, n_ph) are
+// the photon PSRs, column n_ph + e the n_r electron PSRs of bin e added in
+// ring order.
+__global__ void k_basis_units(const double *__restrict__ s1, const double *__restrict__ cell_scale,
+                              const double *__restrict__ row_mass, int n_rows, int n_psr, int n_ph, int n_r,
+                              int n_beams, int B, double *__restrict__ A)
+{
+    const int n_col = n_ph + (n_psr - n_ph) / n_r;
+    const int64_t n = (int64_t)n_beams * n_rows * n_col;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int j = (int)(i % n_col);
+        const int64_t br = i / n_col;
+        const int row = (int)(br % n_rows), b = (int)(br / n_rows);
+        const double m = row_mass[row];
+        const double *s = s1 + br * n_psr;
+        double v = 0.0;
+        if (m > 0.0) {
+            if (j < n_ph) {
+                v = s[j] / B * cell_scale[(size_t)j * n_beams + b] / m;
+            } else {
+                const int k0 = n_ph + (j - n_ph) * n_r;
+                for (int R = 0; R < n_r; ++R) v += s[k0 + R] / B * cell_scale[(size_t)(k0 + R) * n_beams + b] / m;
+            }
+        }
+        A[i] = v;
+    }
+}
+
 // per (PSR, beam) scale of a per-PSR plan, gathered from the entry table
 __global__ void k_cell_scale(const EntryRec *__restrict__ ent, const double *__restrict__ escale, int64_t n_ent,
                              int n_e, int n_r, int n_beams, double *__restrict__ cell_scale)
@@ -1110,6 +1183,22 @@ __global__ void k_row_mass(const uint16_t *__restrict__ idx, const float *__rest
 }
 
 // ------------------------------------------------------------ host side ---
+
+// polls of a transport CTA's table-staging wait (lsm_set_wait_limits)
+int g_stage_polls = 1 << 22;
+
+lsm_status read_fallbacks(int64_t *count, int reset)
+{
+    unsigned long long v = 0;
+    LSM_CUDA(cudaDeviceSynchronize());
+    LSM_CUDA(cudaMemcpyFromSymbol(&v, g_stage_fallbacks, sizeof(v)));
+    if (count) *count = (int64_t)v;
+    if (reset) {
+        v = 0;
+        LSM_CUDA(cudaMemcpyToSymbol(g_stage_fallbacks, &v, sizeof(v)));
+    }
+    return LSM_OK;
+}
 
 namespace {
 
@@ -1160,6 +1249,13 @@ cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t, 
     return cudaSuccess;
 }
 
+// A run's secondary-electron queue capacity: the workspace's, or less when
+// the run asks for a smaller queue (e_queue_cap).
+void cap_equeue(Workspace &W, const lsm_run_opts &o)
+{
+    if (o.e_queue_cap > 0 && (uint32_t)o.e_queue_cap < W.q[2].cap) W.q[2].cap = (uint32_t)o.e_queue_cap;
+}
+
 TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, const uint32_t *key, IterCounters *cnt)
 {
     TP T;
@@ -1184,6 +1280,7 @@ TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, con
     T.s_geo = (float)sg;
     T.key = key;
     T.ctas_per_sm = o.ctas_per_sm;
+    T.stage_polls = g_stage_polls;
     T.stats = t->d_stats;
     T.cnt = cnt;
     return T;
@@ -1200,6 +1297,7 @@ lsm_status check_opts(lsm_run_opts &o)
     if (o.chunk > (1 << 24)) return set_arg_error("chunk must be <= 2^24");
     if (o.n_batches < 1) o.n_batches = 1;
     if (o.first_batch < 0) return set_arg_error("first_batch must be >= 0");
+    if (o.e_queue_cap < 0) return set_arg_error("e_queue_cap must be >= 0");
     return LSM_OK;
 }
 
@@ -1347,6 +1445,7 @@ lsm_status transport_particles(const lsm_phantom *ph, const lsm_particles *in, i
     unsigned long long ovf = 0;
     cudaError_t e = ws_alloc(W, cap, (uint32_t)std::min<int64_t>(8 * (int64_t)cap + (1 << 18), 1u << 28), t, st);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_transport workspace");
+    cap_equeue(W, o);
     TP T = make_tp(ph, t, o, W.key, W.cnt);
     do {
         set_key(W, t, seed, st);
@@ -1397,6 +1496,7 @@ lsm_status pslfile_begin(const lsm_phantom *ph, lsm_tally *t, const lsm_run_opts
     const uint32_t c = (uint32_t)std::max<int64_t>(cap, 1024);
     cudaError_t e = ws_alloc(R->W, c, (uint32_t)std::min<int64_t>(4 * (int64_t)c + (1 << 18), 0xF0000000ll), t, st);
     if (e != cudaSuccess) { delete R; return set_cuda_error(e, "lsm_pslfile_run workspace"); }
+    cap_equeue(R->W, o);
     R->T = make_tp(ph, t, o, R->W.key, R->W.cnt);
     R->t = t;
     R->nb = nb;
@@ -1470,6 +1570,7 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     if (rc) return rc;
     cudaError_t e = ws_alloc(W, (uint32_t)chunk, (uint32_t)std::min<int64_t>(4 * chunk + (1 << 18), 0xF0000000ll), t, st);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_run workspace");
+    cap_equeue(W, o);
     TP T = make_tp(ph, t, o, W.key, W.cnt);
     SQ S;
     S.sp = P->sp;
@@ -1632,9 +1733,11 @@ lsm_status dose_impl(const lsm_tally *t, const lsm_phantom *ph, double scale, do
 }
 
 lsm_status basis_impl(const lsm_tally *t, const lsm_psl *P, const lsm_phantom *ph, const uint16_t *idx3d,
-                      lsm_mem idx_mem, double *A, lsm_mem mem, cudaStream_t st)
+                      lsm_mem idx_mem, double *A, lsm_mem mem, cudaStream_t st, bool units)
 {
     if (!t || !P || !ph || !A) return set_arg_error("lsm_basis_matrix: NULL argument");
+    if (units && t->n_psr != 3 * P->n_e * P->n_r)
+        return set_arg_error("lsm_basis_matrix_units: the tally's PSR count must be 3 n_e n_r of the plan");
     if (t->mode != 1 || !P->per_psr) return set_arg_error("lsm_basis_matrix: needs a basis tally and a per-PSR plan");
     {
         const lsm_status r = resolve_psl(const_cast<lsm_psl *>(P));
@@ -1642,7 +1745,8 @@ lsm_status basis_impl(const lsm_tally *t, const lsm_psl *P, const lsm_phantom *p
     }
     if (t->n_batches < 1) return set_arg_error("lsm_basis_matrix: no batch folded yet");
     const int npsr = t->n_psr, nb = t->n_beams, nr = t->n_rows;
-    const int64_t ncell = (int64_t)nb * nr * npsr;
+    const int n_ph = 2 * P->n_e * P->n_r, n_col = units ? n_ph + P->n_e : npsr;
+    const int64_t ncell = (int64_t)nb * nr * n_col;
     char *tmp = nullptr;
     const size_t bytes = (size_t)npsr * nb * 8 + (size_t)nr * 8 + (mem == LSM_MEM_HOST ? (size_t)ncell * 8 : 0) + 64;
     LSM_CUDA(dev_malloc((void **)&tmp, bytes, st));
@@ -1659,7 +1763,10 @@ lsm_status basis_impl(const lsm_tally *t, const lsm_psl *P, const lsm_phantom *p
         k_row_mass<<<g, 256, 0, st>>>(didx, ph->d_rho, t->nvox, nr, ph->dx * ph->dy * ph->dz, rm);
         count_launch();
         const int g2 = (int)std::min<int64_t>((ncell + 255) / 256, 8 * sm_count());
-        k_basis<<<g2, 256, 0, st>>>(t->d_s1, cs, rm, nr, npsr, nb, t->n_batches, dA);
+        if (units)
+            k_basis_units<<<g2, 256, 0, st>>>(t->d_s1, cs, rm, nr, npsr, n_ph, P->n_r, nb, t->n_batches, dA);
+        else
+            k_basis<<<g2, 256, 0, st>>>(t->d_s1, cs, rm, nr, npsr, nb, t->n_batches, dA);
         count_launch();
         e = cudaGetLastError();
     }

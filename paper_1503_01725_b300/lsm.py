@@ -62,7 +62,8 @@ class lsm_run_opts(C.Structure):
     _fields_ = [("electron_mode", C.c_int32), ("n_batches", C.c_int32),
                 ("majorant_factor", C.c_double), ("f_e", C.c_double), ("s_geo", C.c_double),
                 ("max_steps", C.c_int32), ("chunk", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("use_graph", C.c_int32), ("no_sync", C.c_int32), ("first_batch", C.c_int64)]
+                ("use_graph", C.c_int32), ("no_sync", C.c_int32), ("first_batch", C.c_int64),
+                ("e_queue_cap", C.c_int32), ("reserved", C.c_int32)]
 
 
 class lsm_nnls_opts(C.Structure):
@@ -92,9 +93,14 @@ class lsm_adam_opts(C.Structure):
 
 
 _EXPORTS = {
-    "lsm_build_psl": (C.c_int, [C.POINTER(lsm_psr_model), C.POINTER(lsm_beams), C.c_int64,
+    "lsm_model_create": (C.c_int, [C.POINTER(lsm_psr_model), C.POINTER(C.c_void_p)]),
+    "lsm_model_destroy": (None, [C.c_void_p]),
+    "lsm_model_commission": (C.c_int, [C.c_void_p, _dp, C.c_int32, C.POINTER(C.c_void_p)]),
+    "lsm_model_weights": (C.c_int, [C.c_void_p, _dp]),
+    "lsm_basis_matrix_units": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "lsm_build_psl": (C.c_int, [C.c_void_p, C.POINTER(lsm_beams), C.c_int64,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.c_void_p]),
-    "lsm_build_psl_async": (C.c_int, [C.POINTER(lsm_psr_model), C.POINTER(lsm_beams), C.c_int64,
+    "lsm_build_psl_async": (C.c_int, [C.c_void_p, C.POINTER(lsm_beams), C.c_int64,
                                       C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.c_void_p]),
     "lsm_psl_destroy": (None, [C.c_void_p]),
     "lsm_psl_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), _dp]),
@@ -162,6 +168,8 @@ _EXPORTS = {
                                   C.c_void_p]),
     "lsm_timing_enable": (C.c_int, [C.c_int]),
     "lsm_timing_read": (C.c_int, [_dp, C.POINTER(C.c_int64), C.c_int]),
+    "lsm_set_wait_limits": (C.c_int, [C.c_int64, C.c_int64]),
+    "lsm_run_fallbacks": (C.c_int, [C.POINTER(C.c_int64), C.c_int]),
     "lsm_last_error": (C.c_char_p, []),
     "lsm_launch_count": (C.c_int64, []),
 }
@@ -244,6 +252,20 @@ class PSL(Handle):
         return self._denom
 
 
+class Model(Handle):
+    """A PSR model held by the library (lsm_model_create). `source` is the
+    Python model it was made from (its shapes are used to size plan tables)."""
+    _destroy = "lsm_model_destroy"
+
+    _SHAPE = ("n_e", "n_r", "n_psr", "dr", "z_phsp", "sigma_s", "e_lo", "de")
+
+    def __getattr__(self, name):
+        src = self.__dict__.get("source")
+        if src is None or name not in Model._SHAPE:
+            raise AttributeError(name)
+        return getattr(src, name)
+
+
 class PhantomHandle(Handle):
     _destroy = "lsm_phantom_destroy"
 
@@ -297,11 +319,39 @@ def _marshal(model, beams):
     return ms, bs
 
 
-def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None, async_: bool = False) -> PSL:
-    """Plan of `model` and `beams` (Sec. 2.1). async_: return once the build
-    is queued (lsm_build_psl_async); its results are read on first use."""
+def lsm_model_create(model) -> Model:
+    """Library handle of a PSR model (Sec. 2.1.1): validated and copied; later
+    changes to `model`'s arrays do not reach the handle."""
     L = load_library()
-    ms, bs = _marshal(model, beams)
+    ms, _ = _marshal(model, _NO_BEAMS)
+    out = C.c_void_p()
+    _check(L.lsm_model_create(C.byref(ms), C.byref(out)), "lsm_model_create")
+    h = Model(out)
+    h.source = model
+    return h
+
+
+class _NoBeams:
+    sad = z_jaw_y = z_jaw_x = 0.0
+    n_beams = 0
+    jaws = np.zeros((0, 4))
+
+
+_NO_BEAMS = _NoBeams()
+
+
+def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None, async_: bool = False) -> PSL:
+    """Plan of `model` and `beams` (Sec. 2.1). `model` is a Model handle, or a
+    plain model for which a handle is made for this call only. async_: return
+    once the build is queued (lsm_build_psl_async); its results are read on
+    first use."""
+    L = load_library()
+    if isinstance(model, Model):
+        mh = model
+        model = mh.source
+    else:
+        mh = lsm_model_create(model)
+    _, bs = _marshal(model, beams)
     keep = []
     pp = None
     if per_psr_hist is not None:
@@ -310,7 +360,7 @@ def lsm_build_psl(model, beams, n_hist: int = 0, per_psr_hist=None, stream=None,
         pp = ppa.ctypes.data_as(C.POINTER(C.c_int64))
     out = C.c_void_p()
     fn = L.lsm_build_psl_async if async_ else L.lsm_build_psl
-    _check(fn(C.byref(ms), C.byref(bs), int(n_hist), pp, C.byref(out), _stream(stream)), "lsm_build_psl")
+    _check(fn(mh.ptr, C.byref(bs), int(n_hist), pp, C.byref(out), _stream(stream)), "lsm_build_psl")
     h = PSL(out)
     h.model, h.beams = model, beams
     return h
@@ -494,13 +544,14 @@ class RunOpts:
     use_graph: bool = False
     no_sync: bool = False   # return once queued; overflows stay in the run statistics
     first_batch: int = 0    # batch index of the run's first pass (resume from a checkpoint)
+    e_queue_cap: int = 0    # secondary-electron queue capacity (0: 4 chunk + 2^18)
 
     def struct(self) -> lsm_run_opts:
         return lsm_run_opts(electron_mode=self.electron_mode, n_batches=self.n_batches,
                             majorant_factor=self.majorant_factor, f_e=self.f_e, s_geo=self.s_geo,
                             max_steps=self.max_steps, chunk=self.chunk, ctas_per_sm=self.ctas_per_sm,
                             use_graph=int(self.use_graph), no_sync=int(self.no_sync),
-                            first_batch=int(self.first_batch))
+                            first_batch=int(self.first_batch), e_queue_cap=int(self.e_queue_cap))
 
 
 def lsm_transport(ph: PhantomHandle, particles: dict, n: int, seed: int, tally: Tally,
@@ -516,6 +567,18 @@ def lsm_run(psl: PSL, ph: PhantomHandle, tally: Tally, seed: int, opts: RunOpts 
     o = (opts or RunOpts()).struct()
     return _check(_lib.lsm_run(psl.ptr, ph.ptr, tally.ptr, seed, C.byref(o), _stream(stream)), "lsm_run",
                   ok=(LSM_OK, LSM_ERR_OVERFLOW))
+
+
+def lsm_set_wait_limits(stage_polls: int = -1, conv_wait_ns: int = -1):
+    """Bounds of the device-side waits (negative: unchanged); see the header."""
+    _check(load_library().lsm_set_wait_limits(int(stage_polls), int(conv_wait_ns)), "lsm_set_wait_limits")
+
+
+def lsm_run_fallbacks(reset: bool = False) -> int:
+    """Transport CTAs that read their tables from global memory since the last reset."""
+    n = C.c_int64(0)
+    _check(load_library().lsm_run_fallbacks(C.byref(n), int(reset)), "lsm_run_fallbacks")
+    return n.value
 
 
 def lsm_l2_atomic_peak(n_cells: int, reps: int = 10, stream=None) -> float:
@@ -598,11 +661,42 @@ def lsm_dose(t: Tally, ph: PhantomHandle, scale: float, device: bool = False, st
     return d.reshape(shp), s.reshape(shp)
 
 
-def lsm_basis_matrix(t: Tally, psl: PSL, ph: PhantomHandle, stream=None) -> np.ndarray:
+def lsm_basis_matrix(t: Tally, psl: PSL, ph: PhantomHandle, stream=None, units: bool = False) -> np.ndarray:
+    """Basis matrix of Sec. 2.2.2 on the host; units=True: over the unknowns
+    of Eq. 8 (photon PSRs, then one effective electron unit per energy bin,
+    Sec. 2.2.3; lsm_basis_matrix_units)."""
+    if units:
+        m = psl.model
+        A = np.zeros((t.n_beams * t.n_rows, 2 * m.n_e * m.n_r + m.n_e))
+        _check(_lib.lsm_basis_matrix_units(t.ptr, psl.ptr, ph.ptr, A.ctypes.data, LSM_MEM_HOST, _stream(stream)),
+               "lsm_basis_matrix_units")
+        return A
     A = np.zeros((t.n_beams * t.n_rows, t.n_psr))
     _check(_lib.lsm_basis_matrix(t.ptr, psl.ptr, ph.ptr, None, LSM_MEM_DEVICE, A.ctypes.data, LSM_MEM_HOST,
                                  _stream(stream)), "lsm_basis_matrix")
     return A
+
+
+def lsm_model_weights(model: "Model") -> np.ndarray:
+    """The handle's PSR weights, [3][n_e][n_r] (host copy)."""
+    L = load_library()
+    w = np.zeros((3, model.n_e, model.n_r))
+    _check(L.lsm_model_weights(model.ptr, w.ctypes.data_as(_dp)), "lsm_model_weights")
+    return w
+
+
+def lsm_model_commission(model, x) -> "Model":
+    """Commissioned model (Sec. 2.2.4): a new handle with PSR weights W_R x_R;
+    x per PSR or per unknown of Eq. 8 (photon PSRs, electron units)."""
+    L = load_library()
+    mh = model if isinstance(model, Model) else lsm_model_create(model)
+    xa = _f64(x).ravel()
+    out = C.c_void_p()
+    _check(L.lsm_model_commission(mh.ptr, xa.ctypes.data_as(_dp), int(xa.size), C.byref(out)),
+           "lsm_model_commission")
+    h = Model(out)
+    h.source = mh.source
+    return h
 
 
 def lsm_commission(A, b, method: int = 0, max_iter: int = 0, delta: float = 1e-12, sigma: float = 1e-4,
@@ -635,8 +729,16 @@ def lsm_commission_static(A, b, x, method: int = 0, max_iter: int = 0, delta: fl
     """Allocation-free Eq. 8 solve for callers that cannot allocate device
     memory: A (m x n), b (m) and x (n, output) are CUDA float64 tensors the
     caller owns; n <= 256."""
+    import torch
     L = load_library()
+    for name, t in (("A", A), ("b", b), ("x", x)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise LSMError(LSM_ERR_ARG, "lsm_commission_static", f"{name} must be a contiguous CUDA float64 tensor")
+    if A.dim() != 2:
+        raise LSMError(LSM_ERR_ARG, "lsm_commission_static", "A must be 2-D (m x n)")
     m, n = A.shape
+    if b.numel() != m or x.numel() != n:
+        raise LSMError(LSM_ERR_ARG, "lsm_commission_static", f"b needs {m} and x {n} elements")
     o = lsm_nnls_opts(method=method, max_iter=max_iter, delta=delta, armijo_sigma=sigma, armijo_beta=beta,
                       use_x0=int(use_x0))
     rep = lsm_nnls_report()

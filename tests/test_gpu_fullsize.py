@@ -241,7 +241,11 @@ def test_commissioning_system_active_set_against_the_oracle(L):
         L.lsm_tally_reset(t)
         L.lsm_run(g, ph, t, seed, L.RunOpts(electron_mode=1, n_batches=4))
         A = L.lsm_basis_matrix(t, g, ph)
-        return np.concatenate([A[:, :n_ph], A[:, n_ph:].reshape(A.shape[0], m.n_e, m.n_r).sum(axis=2)], axis=1)
+        Au = L.lsm_basis_matrix(t, g, ph, units=True)
+        # the library's electron units equal the column sums of the per-PSR matrix
+        Ah = np.concatenate([A[:, :n_ph], A[:, n_ph:].reshape(A.shape[0], m.n_e, m.n_r).sum(axis=2)], axis=1)
+        np.testing.assert_allclose(Au, Ah, rtol=1e-13, atol=1e-300)
+        return Au
 
     A, A2 = grouped(1), grouped(999)
     x_true = W.commissioning_truth(A.shape[1])

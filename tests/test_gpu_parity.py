@@ -72,6 +72,31 @@ def test_per_psr_plan_bit_exact(L):
     assert np.array_equal(L.lsm_psl_copy(g, 6), o.ent_scale)
 
 
+def test_model_handle_plans_equal_the_oracle(L):
+    """A plan built from a model handle equals the oracle's plan of the same
+    model; the commissioned handle (lsm_model_commission with per-unit
+    factors: photon PSRs, then one factor per electron energy bin) builds the
+    oracle's plan of the model whose weights are W_R x_R, bit for bit."""
+    m, b, n = _models()[1]
+    mh = L.lsm_model_create(m)
+    g = L.lsm_build_psl(mh, b, n)
+    o = O.Plan(m, b, n)
+    assert g.denom == o.denom and np.array_equal(L.lsm_psl_copy(g, 3), o.count)
+    n_ph = 2 * m.n_e * m.n_r
+    x = np.random.default_rng(8).uniform(0.7, 1.3, n_ph + m.n_e)
+    x[5] = 0.0
+    mc = L.lsm_model_commission(mh, x)
+    wc = m.w.reshape(-1) * np.concatenate([x[:n_ph], np.repeat(x[n_ph:], m.n_r)])
+    assert np.array_equal(L.lsm_model_weights(mc).ravel(), wc)
+    del mh                                  # a handle's plans do not need the handle that built them
+    gc = L.lsm_build_psl(mc, b, n)
+    oc = O.Plan(m.with_weights(wc.reshape(m.w.shape)), b, n)
+    assert gc.denom == oc.denom
+    assert np.array_equal(L.lsm_psl_copy(gc, 0), oc.wpsl)
+    assert np.array_equal(L.lsm_psl_copy(gc, 3), oc.count)
+    assert np.array_equal(L.lsm_psl_copy(gc, 5), oc.entries)
+
+
 def test_empty_sampling_area_is_an_argument_error(L):
     m = W.psr_model(3, 4, 0.25, seed=1)
     with pytest.raises(L.LSMError) as e:
