@@ -755,6 +755,7 @@ typedef struct {
     const uint16_t *idx3d;   /* basis mode: 0 none, else row + 1 */
     int32_t n_rows;          /* rows per beam */
     int32_t n_psr;
+    int64_t first_batch;     /* pass bt of the run draws the histories of batch first_batch + bt */
 } or_opts;
 
 typedef struct {
@@ -1012,7 +1013,8 @@ static void electron_track(tctx *T, part_t *p)
 }
 
 /*
- * Run n_batches passes over the plan (histories g = b * n_hist + h).
+ * Run n_batches passes over the plan (histories g = (first_batch + b) * n_hist + h:
+ * a run of B batches equals runs over disjoint batch ranges, summed).
  * s1/s2: per tally cell, the sum over batches of the batch total and of its
  * square (energy in MeV). ledger[4]: source, rejected, escaped (incl. missing
  * the phantom), deposited energy. stats[8]: histories, accepted photons,
@@ -1060,7 +1062,7 @@ OR_API int or_run(const void *h, const or_phantom *Ph, const or_opts *O, uint64_
                   double *per_hist)
 {
     const or_plan *P = (const or_plan *)h;
-    if (!P || P->n_ent <= 0 || O->n_batches < 1) return 1;
+    if (!P || P->n_ent <= 0 || O->n_batches < 1 || O->first_batch < 0) return 1;
     size_t nvox = (size_t)Ph->nx * Ph->ny * Ph->nz;
     size_t ncell = O->tally_mode == 0 ? nvox : (size_t)P->n_beams * O->n_rows * O->n_psr;
     tctx T;
@@ -1080,7 +1082,7 @@ OR_API int or_run(const void *h, const or_phantom *Ph, const or_opts *O, uint64_
     (void)batch_scale;
     for (int bt = 0; bt < O->n_batches; ++bt) {
         for (int64_t hh = 0; hh < P->n_hist; ++hh) {
-            uint64_t g = (uint64_t)bt * (uint64_t)P->n_hist + (uint64_t)hh;
+            uint64_t g = (uint64_t)(O->first_batch + bt) * (uint64_t)P->n_hist + (uint64_t)hh;
             or_src o;
             sample_one(P, seed, g, Ph->z0, &o);
             stats[0]++;
@@ -1122,7 +1124,7 @@ OR_API int or_run(const void *h, const or_phantom *Ph, const or_opts *O, uint64_
             ledger[1] += rej; ledger[2] += T.esc; ledger[3] += T.dep;
             double bal = fabs(o.E - (rej + T.esc + T.dep)) / o.E;
             if (bal > cons[0]) cons[0] = bal;
-            if (per_hist) per_hist[g] = T.dep;
+            if (per_hist) per_hist[(int64_t)bt * P->n_hist + hh] = T.dep;
         }
         for (size_t c = 0; c < ncell; ++c) {
             s1[c] += T.acc[c];

@@ -54,7 +54,8 @@ class _Opts(C.Structure):
                 ("n_batches", C.c_int32), ("compton_only", C.c_int32),
                 ("majorant_factor", C.c_double), ("f_e", C.c_double), ("s_geo", C.c_double),
                 ("ms_off", C.c_int32), ("max_steps", C.c_int32),
-                ("idx3d", C.POINTER(C.c_uint16)), ("n_rows", C.c_int32), ("n_psr", C.c_int32)]
+                ("idx3d", C.POINTER(C.c_uint16)), ("n_rows", C.c_int32), ("n_psr", C.c_int32),
+                ("first_batch", C.c_int64)]
 
 
 def _ptr(a, ct=C.c_double):
@@ -179,7 +180,7 @@ def _phantom_struct(ph, keep):
 
 def _opts_struct(keep, *, electron_mode=1, tally_mode=0, n_batches=1, compton_only=0,
                  majorant_factor=1.0, f_e=0.25, s_geo=0.0, ms_off=0, max_steps=100000,
-                 idx3d=None, n_rows=0, n_psr=0):
+                 idx3d=None, n_rows=0, n_psr=0, first_batch=0):
     ip = None
     if idx3d is not None:
         a = np.ascontiguousarray(idx3d, dtype=np.uint16)
@@ -188,7 +189,7 @@ def _opts_struct(keep, *, electron_mode=1, tally_mode=0, n_batches=1, compton_on
     return _Opts(electron_mode=electron_mode, tally_mode=tally_mode, n_batches=n_batches,
                  compton_only=compton_only, majorant_factor=majorant_factor, f_e=f_e,
                  s_geo=s_geo, ms_off=ms_off, max_steps=max_steps, idx3d=ip, n_rows=n_rows,
-                 n_psr=n_psr)
+                 n_psr=n_psr, first_batch=first_batch)
 
 
 class Plan:

@@ -218,7 +218,25 @@ __device__ __forceinline__ void hl_add(const TP &T, uint32_t glo, uint32_t ghi, 
     }
 }
 
-template <int MODE>
+// FP32 add to a tally cell in L2. KEEP: the line is marked evict-last (an L2
+// cache-policy hint), so that the partial slices stay resident while the
+// particle queues stream through L2: the photon passes' deposits (local
+// electrons below the cutoff, photons below theirs) otherwise miss L2 and their
+// line fetches back up the memory pipeline behind the queue traffic (measured
+// on the 64^3, 16-slice tally: photon pass 0.65 -> 0.51 ms).
+template <bool KEEP>
+__device__ __forceinline__ void tally_add(float *cell, float e)
+{
+    if constexpr (KEEP) {
+        uint64_t pol;
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+        asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(cell), "f"(e), "l"(pol) : "memory");
+    } else {
+        atomicAdd(cell, e);
+    }
+}
+
+template <int MODE, bool KEEP = false>
 __device__ __forceinline__ void deposit(const TP &T, Acc &A, int vox, float e, uint32_t pb, uint32_t glo,
                                         uint32_t ghi)
 {
@@ -226,14 +244,14 @@ __device__ __forceinline__ void deposit(const TP &T, Acc &A, int vox, float e, u
     hl_add<MODE>(T, glo, ghi, 1, e);
     float *slice = T.part + (size_t)pb_slot(pb) * T.ncell;
     if (MODE != 1) {
-        atomicAdd(slice + vox, e);
+        tally_add<KEEP>(slice + vox, e);
     } else {
         // rows, PSRs and beams are checked so that caller-supplied particles
         // or index arrays can never write outside the basis tally
         const int row = T.idx[vox];
         const uint32_t beam = pb_beam(pb), k = pb_psr(pb);
         if (row && row <= T.n_rows && k < (uint32_t)T.n_psr && beam < (uint32_t)T.n_beams)
-            atomicAdd(slice + ((size_t)beam * T.n_rows + (row - 1)) * T.n_psr + k, e);
+            tally_add<KEEP>(slice + ((size_t)beam * T.n_rows + (row - 1)) * T.n_psr + k, e);
     }
 }
 
@@ -335,13 +353,13 @@ __device__ __forceinline__ void spawn_electron(const TP &T, Acc &A, const Queue 
                                                float u, float v, float w, uint32_t sid, int vox)
 {
     if (T.electron_mode == 0 || Te < kCutE) {
-        deposit<MODE>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
+        deposit<MODE, true>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
         return;
     }
     const uint32_t slot = push_slot(&T.cnt->n[2]);
     if (slot >= eq.cap) {
         atomicAdd(&T.stats->c[9], 1ull);
-        deposit<MODE>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
+        deposit<MODE, true>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
         return;
     }
     store_part(eq, slot, p.x, p.y, p.z, u, v, w, Te, p.rng.glo, p.rng.ghi, sid, p.pb);
@@ -355,8 +373,8 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
 {
     int vox = voxel(T, p.x, p.y, p.z);
     if (vox < 0) { A.esc += p.E; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
-    if (p.E < kCutG) { deposit<MODE>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
-    if (++p.steps > T.max_steps) { A.cap++; deposit<MODE>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
+    if (p.E < kCutG) { deposit<MODE, true>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
+    if (++p.steps > T.max_steps) { A.cap++; deposit<MODE, true>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
     const uint4 r = p.rng.next();
     int ti;
     float tf;
@@ -399,7 +417,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
             pe = Pend{p.x, p.y, p.z, ex, ey, ez, Te, p.rng.child_id(0), vox};
             pend = true;
         } else {
-            deposit<MODE>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
+            deposit<MODE, true>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
         }
         p.E = E1; p.u = u; p.v = v; p.w = w;
         return true;
@@ -410,7 +428,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
             pe = Pend{p.x, p.y, p.z, p.u, p.v, p.w, p.E, p.rng.child_id(0), vox};
             pend = true;
         } else {
-            deposit<MODE>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi);
+            deposit<MODE, true>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi);
         }
         return false;
     }
@@ -434,7 +452,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
             store_part(*pq, slot, p.x, p.y, p.z, sg * ax, sg * ay, sg * az, kMe, p.rng.glo, p.rng.ghi,
                        p.rng.child_id(2 + h), p.pb);
         else
-            deposit<MODE>(T, A, vox, kMe, p.pb, p.rng.glo, p.rng.ghi);
+            deposit<MODE, true>(T, A, vox, kMe, p.pb, p.rng.glo, p.rng.ghi);
     }
     return false;
 }
@@ -655,7 +673,7 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
                                    pb_keep);
                     } else {
                         atomicAdd(&T.stats->c[9], 1ull);
-                        deposit<MODE>(T, A, pe.vox, pe.E, pb_keep, p.rng.glo, p.rng.ghi);
+                        deposit<MODE, true>(T, A, pe.vox, pe.E, pb_keep, p.rng.glo, p.rng.ghi);
                         A.dep += A.dep32;
                         A.dep32 = 0.0f;
                     }

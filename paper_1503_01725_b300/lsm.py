@@ -494,10 +494,22 @@ def lsm_tally_end_batch(t: Tally, stream=None):
     _check(_lib.lsm_tally_end_batch(t.ptr, _stream(stream)), "lsm_tally_end_batch")
 
 
-def lsm_tally_read(t: Tally, stream=None):
+def lsm_tally_read(t: Tally, stream=None, out=None):
+    """S1, S2 and the folded batch count; into host arrays, or (out) into two
+    contiguous CUDA float64 tensors of ncell elements (stream-ordered)."""
+    nb = C.c_int32()
+    if out is not None:
+        import torch
+        s1, s2 = out
+        for a in (s1, s2):
+            if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+                    and a.numel() == t.ncell):
+                raise LSMError(LSM_ERR_ARG, "lsm_tally_read", "out needs two contiguous CUDA float64 tensors")
+        _check(_lib.lsm_tally_read(t.ptr, s1.data_ptr(), s2.data_ptr(), LSM_MEM_DEVICE, C.byref(nb),
+                                   _stream(stream)), "lsm_tally_read")
+        return s1, s2, nb.value
     s1 = np.zeros(t.ncell)
     s2 = np.zeros(t.ncell)
-    nb = C.c_int32()
     _check(_lib.lsm_tally_read(t.ptr, s1.ctypes.data, s2.ctypes.data, LSM_MEM_HOST, C.byref(nb),
                                _stream(stream)), "lsm_tally_read")
     return s1, s2, nb.value
@@ -505,8 +517,16 @@ def lsm_tally_read(t: Tally, stream=None):
 
 def lsm_tally_load(t: Tally, s1, s2, n_batches: int, ledger=None, stats=None, stream=None):
     """Restore a checkpoint (S1, S2, folded batches, optional ledger and
-    statistics dicts as lsm_tally_ledger returns them)."""
-    a1, a2 = _f64(s1), _f64(s2)
+    statistics dicts as lsm_tally_ledger returns them). S1, S2: host arrays or
+    contiguous CUDA float64 tensors."""
+    dev = hasattr(s1, "is_cuda") and s1.is_cuda
+    if dev:
+        for a in (s1, s2):
+            if not (a.is_cuda and str(a.dtype) == "torch.float64" and a.is_contiguous() and a.numel() == t.ncell):
+                raise LSMError(LSM_ERR_ARG, "lsm_tally_load", "S1, S2 must be contiguous CUDA float64 tensors")
+        a1, a2 = s1, s2
+    else:
+        a1, a2 = _f64(s1), _f64(s2)
     led = None
     st = None
     if ledger is not None:
@@ -515,10 +535,12 @@ def lsm_tally_load(t: Tally, s1, s2, n_batches: int, ledger=None, stats=None, st
         keys = ["histories", "photons", "electrons", "rejected", "missed", "flights", "real", "esteps",
                 "cap_hits", "overflows"]
         st = np.array([stats[k] for k in keys], dtype=np.int64)
-    _check(_lib.lsm_tally_load(t.ptr, a1.ctypes.data, a2.ctypes.data, int(n_batches),
+    p1 = a1.data_ptr() if dev else a1.ctypes.data
+    p2 = a2.data_ptr() if dev else a2.ctypes.data
+    _check(_lib.lsm_tally_load(t.ptr, p1, p2, int(n_batches),
                                led.ctypes.data_as(_dp) if led is not None else None,
                                st.ctypes.data_as(C.POINTER(C.c_int64)) if st is not None else None,
-                               LSM_MEM_HOST, _stream(stream)), "lsm_tally_load")
+                               LSM_MEM_DEVICE if dev else LSM_MEM_HOST, _stream(stream)), "lsm_tally_load")
 
 
 def lsm_tally_ledger(t: Tally, stream=None):
