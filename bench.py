@@ -43,7 +43,9 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 
 # Algorithmic bytes per unit of work:
-#   sampling: per history, plan lookup (16 B entry + 8 B prefix) + particle write (48 B record);
+#   sampling: per particle entering the phantom, its queue record (48 B); the plan
+#     tables (entries and prefix, a few hundred KB) are read once per launch and
+#     stay in cache for the lookups of every history;
 #   photon transport: per Woodcock flight one density load (4 B), per photon the
 #     queue read (48 B), per real interaction one tally update (8 B) or queue write (48 B);
 #   electron transport: per CSDA step one density load (4 B) + one tally update
@@ -53,7 +55,7 @@ FALLBACK_HBM_GBS = 6400.0
 # over 3,101,593 photons; 98.9 MB over 9,908,309 electron steps).
 # Valid for the kernels as profiled; set to None when they change.
 TRAFFIC_PER_UNIT = {"photon": ("photons", 67.4), "electron": ("esteps", 10.0)}
-B_SAMPLE_PER_HIST = 72.0
+B_SAMPLE_PER_ENTERING = 48.0
 B_FLIGHT = 4.0
 B_QUEUE = 48.0
 B_DEPOSIT = 8.0
@@ -77,6 +79,8 @@ def parse():
     p.add_argument("--no-pslfile", action="store_true", help="skip the PSL-file comparator block")
     p.add_argument("--no-multibeam", action="store_true", help="skip the multi-beam plan block")
     p.add_argument("--no-validation", action="store_true", help="skip the commissioning validation loop")
+    p.add_argument("--no-fields", action="store_true", help="skip the field-size sweep")
+    p.add_argument("--no-precision", action="store_true", help="skip the 256x256x160 precision case")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
@@ -85,10 +89,15 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def rank_seed(rank: int) -> int:
-    """Philox key of a rank: every rank draws independent histories (no
-    data-path exchange; the ranks are replicas of the same workload)."""
-    return 1 + 7919 * rank
+SEED = 1
+
+
+def rank_first_batch(rank: int, n_batches: int) -> int:
+    """Weak scaling: every rank runs n_batches batches of the same plan and
+    seed, rank r the batches [r n_batches, (r + 1) n_batches) of one run of
+    world x n_batches batches, so that the ranks draw disjoint histories; the
+    step ends with the sum of the ranks' tallies (dist.reduce_tally)."""
+    return rank * n_batches
 
 
 def slowest_ms(total_ms: float, world: int) -> float:
@@ -184,8 +193,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def u_mean_rel(dose: np.ndarray, sigma: np.ndarray) -> float:
-    sel = dose > 0.5 * dose.max()
+def u_mean_rel(dose: np.ndarray, sigma: np.ndarray, rho: np.ndarray | None = None) -> float:
+    """Mean relative batch sigma over voxels above half the maximum dose; with
+    rho, voxels below 0.1 g/cm^3 (air: dose per gram from a handful of
+    deposits) are left out of the dose region."""
+    d = dose if rho is None else np.where(np.reshape(rho, dose.shape) >= 0.1, dose, 0.0)
+    sel = d > 0.5 * d.max()
     return float(np.mean(sigma[sel] / dose[sel]))
 
 
@@ -259,70 +272,144 @@ def cpu_oracle_rate_all_cores(wl, seconds: float, per: int = 100_000):
     return done / el, done, el, n
 
 
+def _u_A(s1, s2, nb, ref):
+    """Mean relative batch sigma of the basis-matrix entries above half their
+    column's maximum (the commissioning analogue of u for D > 50 % Dmax). The
+    entries are chosen on `ref`, the basis matrix of an independent run, so
+    that a run does not choose the entries where it fluctuated high."""
+    var_b = np.clip(s2 - s1 * s1 / nb, 0, None) / max(nb - 1, 1)
+    sig = np.sqrt(nb * var_b).reshape(ref.shape)
+    S1 = s1.reshape(ref.shape)
+    sel = (ref > 0.5 * ref.max(axis=0, keepdims=True)) & (ref > 0) & (S1 > 0)
+    return float(np.mean(sig[sel] / S1[sel]))
+
+
 def commissioning_block(lsm, W, reps: int = 3, n_batches: int = 16):
-    """Batched basis-dose runs of commissioning (Sec. 2.2.2: 300 PSRs x 3
-    fields, per-PSR history counts proportional to weight, clamped to
-    1e4-1e6, all runs in one plan and one launch sequence) and the FP64 NNLS
-    fit of Eq. 8 on the GPU. Electron PSRs are grouped per energy bin."""
+    """Basis-dose runs of commissioning (Sec. 2.2.2: 300 PSRs x 3 fields,
+    per-PSR history counts proportional to weight, clamped to 1e4-1e6) two
+    ways, with the same histories per PSR and batch:
+
+    - batched: every PSR's runs in one plan and one run, launch parameters
+      picked by the autotuner and the run replayed as one CUDA graph;
+    - plain: one plan and one run per PSR (300 dose calculations).
+
+    Each arm's device time, the measured uncertainty u_A of the basis entries
+    and the time to u_A = 1 % by the 1/N law (confirmed by a batched run of 4x
+    the histories); then the FP64 NNLS fit of Eq. 8 over the photon PSRs and
+    the electron units (Sec. 2.2.3), by active set and by gradient projection."""
     import torch
+    from paper_1503_01725_b300 import autotune
     wl = W.workload_commissioning()
-    n_k = wl.extra["n_k"]
+    n_k = np.asarray(wl.extra["n_k"], dtype=np.int64)
     ph = lsm.lsm_phantom_create(wl.phantom)
+    ph.desc = wl.phantom
     idx, n_rows = W.commissioning_index(wl.phantom)
     m = wl.model
-    tally = lsm.lsm_tally_create(ph, mode=1, idx3d=idx, n_rows=n_rows, n_psr=m.n_psr, n_beams=wl.beams.n_beams)
-    opts = lsm.RunOpts(electron_mode=1, n_batches=n_batches)
+    mh = lsm.lsm_model_create(m)
+    nb_beams = wl.beams.n_beams
+    tally = lsm.lsm_tally_create(ph, mode=1, idx3d=idx, n_rows=n_rows, n_psr=m.n_psr, n_beams=nb_beams)
     stream = torch.cuda.current_stream()
+    base = lsm.RunOpts(electron_mode=1, n_batches=n_batches)
 
-    def basis(seed):
-        psl = lsm.lsm_build_psl(m, wl.beams, per_psr_hist=n_k)
+    def timed(fn, k):
+        ms = []
+        for r in range(k):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            out = fn(r)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms)), out
+
+    # batched arm: launch parameters tuned on this plan (graph replay among them)
+    psl = lsm.lsm_build_psl(mh, wl.beams, per_psr_hist=n_k)
+    plan = int(psl.info["plan_size"])
+    opts, tune_rep = autotune.tune(psl, ph, tally, base, cache_path=None,
+                                   cands=autotune.candidates(plan, n_batches, ctas=(0,)))
+
+    def batched(r):
         lsm.lsm_tally_reset(tally)
-        lsm.lsm_run(psl, ph, tally, seed, opts)
+        g = lsm.lsm_build_psl(mh, wl.beams, per_psr_hist=n_k)      # the plan build is part of the arm
+        lsm.lsm_run(g, ph, tally, 10 + r, dataclasses.replace(opts, use_graph=False))
+        return g
+
+    # (a new plan object per run would defeat the graph cache: replay the tuned plan's graph)
+    def batched_replay(r):
+        lsm.lsm_tally_reset(tally)
+        lsm.lsm_run(psl, ph, tally, 10 + r, opts)
         return psl
 
-    basis(1)                                   # warm-up
-    ms = []
-    for r in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        psl = basis(10 + r)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
+    batched_replay(0)
+    ms_b, _ = timed(batched_replay, reps)
+    ms_b_build, _ = timed(batched, 1)
     s1, s2, nb = lsm.lsm_tally_read(tally)
-    A = lsm.lsm_basis_matrix(tally, psl, ph)
-    hist = int(psl.info["plan_size"]) * n_batches
-    # relative batch uncertainty of the A entries above half their column's maximum
-    var_b = np.clip(s2 - s1 * s1 / nb, 0, None) / max(nb - 1, 1)
-    sig = np.sqrt(nb * var_b)
-    S1 = s1.reshape(A.shape)
-    sel = S1 > 0.5 * S1.max(axis=0, keepdims=True)
-    sel &= S1 > 0
-    u_A = float(np.mean(sig.reshape(A.shape)[sel] / S1[sel]))
-    t_basis = float(np.median(ms)) / 1e3
-    # electron PSRs (sub-source 2) grouped per energy bin: 200 photon PSRs + 10 units
+    hist = plan * n_batches
+    # columns of Eq. 8: photon PSRs, then one effective electron unit per energy bin
     Ag = lsm.lsm_basis_matrix(tally, psl, ph, units=True)
-    # synthetic measurement from an independent basis run, known weights, 0.5 % noise
-    basis(999)
+    # synthetic measurement: an independent basis run, known weights, 0.5 % noise;
+    # its per-PSR matrix also chooses the entries u_A is taken over
+    batched_replay(989)
     A2g = lsm.lsm_basis_matrix(tally, psl, ph, units=True)
+    ref = lsm.lsm_basis_matrix(tally, psl, ph)
+    u_b = _u_A(s1, s2, nb, ref)
+    # 4x the histories (64 batches): u_A should halve
+    o4 = dataclasses.replace(opts, n_batches=4 * n_batches, use_graph=False)
+    lsm.lsm_tally_reset(tally)
+    ms_4x, _ = timed(lambda r: lsm.lsm_run(psl, ph, tally, 77, o4), 1)
+    s1_4, s2_4, nb_4 = lsm.lsm_tally_read(tally)
+    u_4x = _u_A(s1_4, s2_4, nb_4, ref)
+
+    # plain arm: one plan and one run per PSR, the same histories per PSR and batch
+    lsm.lsm_tally_reset(tally)
+    plain_opts = dataclasses.replace(base)
+
+    def plain(r):
+        for k in range(m.n_psr):
+            nk = np.zeros_like(n_k)
+            nk[k] = n_k[k]
+            g = lsm.lsm_build_psl(mh, wl.beams, per_psr_hist=nk)
+            lsm.lsm_run(g, ph, tally, 20 + k, plain_opts)
+        return None
+
+    ms_p, _ = timed(plain, 1)
+    s1p, s2p, _ = lsm.lsm_tally_read(tally)
+    u_p = _u_A(s1p, s2p, n_batches, ref)         # every cell holds its own PSR's n_batches batches
+    t_b, t_p = ms_b / 1e3, ms_p / 1e3
     x_true = W.commissioning_truth(Ag.shape[1])
     rng = np.random.default_rng(3)
     bvec = A2g @ x_true * (1 + 0.005 * rng.standard_normal(Ag.shape[0]))
     scale = 1.0 / np.abs(bvec).max()
     out = {}
-    for method, name, it in ((0, "active_set", 0), (1, "projected_gradient", 50000)):
-        lsm.lsm_commission(Ag * scale, bvec * scale, method=method, max_iter=it)      # warm-up
+    f_opt = None
+    for method, name, it, delta in ((0, "active_set", 0, 1e-12), (1, "projected_gradient", 20000, 1e-12)):
+        lsm.lsm_commission(Ag * scale, bvec * scale, method=method, max_iter=it, delta=delta)      # warm-up
         t0 = time.perf_counter()
-        x, rep = lsm.lsm_commission(Ag * scale, bvec * scale, method=method, max_iter=it)
+        x, rep = lsm.lsm_commission(Ag * scale, bvec * scale, method=method, max_iter=it, delta=delta)
         out[name] = {"ms": (time.perf_counter() - t0) * 1e3, "iterations": rep["iterations"],
-                     "converged": rep["converged"],
+                     "converged": rep["converged"], "delta": delta,
                      # fit residual and error of the dose the fitted weights predict
                      "fit_residual": float(np.linalg.norm(Ag @ x - bvec) / np.linalg.norm(bvec)),
-                     "dose_rel_err": float(np.linalg.norm(A2g @ (x - x_true)) / np.linalg.norm(A2g @ x_true))}
-    return {"workload": wl.name, "histories": hist, "ms_basis": t_basis * 1e3,
-            "histories_per_s": hist / t_basis, "u_A_rel_D50": u_A,
-            "s_to_1pct_A": t_basis * (u_A / 0.01) ** 2, "A_shape": list(Ag.shape),
+                     "dose_rel_err": float(np.linalg.norm(A2g @ (x - x_true)) / np.linalg.norm(A2g @ x_true)),
+                     "objective": rep["objective"], "kkt": rep["kkt"]}
+        if method == 0:
+            f_opt = rep["objective"]
+        else:
+            # the paper's iteration (Sec. 2.2.4) with a bounded budget: its objective
+            # against the active-set minimum of the same problem
+            out[name]["objective_gap_rel"] = (rep["objective"] - f_opt) / f_opt
+    return {"workload": wl.name, "histories": hist, "A_shape": list(Ag.shape),
+            "batched": {"ms": ms_b, "ms_with_plan_build": ms_b_build, "histories_per_s": hist / t_b,
+                        "u_A_rel": u_b, "s_to_1pct_A": t_b * (u_b / 0.01) ** 2,
+                        "launch": {"chunk": opts.chunk, "ctas_per_sm": opts.ctas_per_sm,
+                                   "cuda_graph": bool(opts.use_graph), "autotune_candidates": len(tune_rep["trials"])}},
+            "plain": {"ms": ms_p, "runs": m.n_psr, "histories_per_s": hist / t_p, "u_A_rel": u_p,
+                      "s_to_1pct_A": t_p * (u_p / 0.01) ** 2,
+                      "how": "one per-PSR plan build and one lsm_run per PSR (300), library defaults"},
+            "speedup_batched_over_plain": t_p / t_b,
+            "scaling_check": {"histories": 4 * hist, "ms": ms_4x, "u_A_rel": u_4x,
+                              "u_ratio_vs_1x": u_4x / u_b, "expected_ratio": 0.5},
             "nnls": out}
 
 
@@ -459,6 +546,135 @@ def multibeam_block(lsm, W, opts, n_hist: int = 10_000_000, n_batches: int = 16,
     return out
 
 
+def _timed_steps(lsm, wl, opts, n_plan: int, reps: int, seed0: int, model_h=None):
+    """Event-timed whole dose calculations (plan build + run) of a workload:
+    median ms, the kernel split per step, the last step's dose and sigma, the
+    tally and its counters."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ph = lsm.lsm_phantom_create(wl.phantom)
+    tally = lsm.lsm_tally_create(ph)
+    mh = model_h if model_h is not None else lsm.lsm_model_create(wl.model)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(seed):
+        lsm.lsm_tally_reset(tally)
+        psl = lsm.lsm_build_psl(mh, wl.beams, n_plan, async_=True)
+        lsm.lsm_run(psl, ph, tally, seed, opts)
+        return psl
+
+    for r in range(2):
+        step(seed0 + r)
+    torch.cuda.synchronize()
+    lsm.lsm_timing_read(reset=True)
+    ms = []
+    for r in range(reps):
+        flush.fill_(r & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        psl = step(seed0 + 10 + r)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    tm = lsm.lsm_timing_read(reset=True)
+    led, st = lsm.lsm_tally_ledger(tally)
+    d, sg = lsm.lsm_dose(tally, ph, psl.denom / n_plan)
+    return {"ms": float(np.median(ms)), "kernels_ms": {k: round(v[0] / reps, 4) for k, v in tm.items() if v[0] > 0},
+            "dose": d, "sigma": sg, "ledger": led, "stats": st, "tally": tally, "phantom": ph}
+
+
+def fields_block(lsm, W, opts, n_hist: int = 10_000_000, n_batches: int = 16, reps: int = 5):
+    """Open fields of 4, 10 and 20 cm on water and 10 cm on the heterogeneous
+    phantom (64^3 voxels of 0.5 cm): the field-size sweep of Table 1 (Sec. 3.1)
+    on this engine, histories/s and seconds to 1 % per field."""
+    out = {}
+    o = dataclasses.replace(opts, n_batches=n_batches, no_sync=True, use_graph=False, first_batch=0)
+    n_plan = n_hist // n_batches
+    lsm.lsm_timing_enable(True)
+    for field, hetero in ((4.0, False), (10.0, False), (20.0, False), (10.0, True)):
+        wl = W.workload_field(field, n_hist, hetero)
+        r = _timed_steps(lsm, wl, o, n_plan, reps, 300)
+        t = r["ms"] / 1e3
+        u = u_mean_rel(r["dose"], r["sigma"], wl.phantom.rho)
+        st = r["stats"]
+        out[wl.name] = {"field_cm": field, "phantom": "heterogeneous" if hetero else "water",
+                        "histories": n_plan * n_batches, "ms": r["ms"], "histories_per_s": n_plan * n_batches / t,
+                        "u_mean_rel_D50": u, "s_to_1pct": t * (u / 0.01) ** 2,
+                        "entering_fraction": (st["photons"] + st["electrons"]) / max(st["histories"], 1),
+                        "kernels_ms": r["kernels_ms"]}
+    lsm.lsm_timing_enable(False)
+    return out
+
+
+def precision_block(lsm, W, opts, n_hist: int = 100_000_000, n_batches: int = 16, reps: int = 3):
+    """The precision case: 256x256x160 heterogeneous phantom at 0.25 cm, 1e8
+    histories, FP32 transport with FP32 partial slices folded into the FP64
+    tally. Its error against the FP64 oracle is measured in the CPU-baseline
+    leg on the dose kept here."""
+    wl = W.workload_hetero(n_hist)
+    n_plan = n_hist // n_batches
+    o = dataclasses.replace(opts, n_batches=n_batches, no_sync=True, use_graph=False, first_batch=0,
+                            chunk=1 << 24)
+    lsm.lsm_timing_enable(True)
+    r = _timed_steps(lsm, wl, o, n_plan, reps, 500)
+    lsm.lsm_timing_enable(False)
+    s1, s2, nb = lsm.lsm_tally_read(r["tally"])
+    t = r["ms"] / 1e3
+    u = u_mean_rel(r["dose"], r["sigma"], wl.phantom.rho)
+    led = r["ledger"]
+    # an independent run (another seed) chooses the voxels the oracle
+    # comparison uses, so that neither compared estimate selects itself
+    mh = lsm.lsm_model_create(wl.model)
+    lsm.lsm_tally_reset(r["tally"])
+    lsm.lsm_run(lsm.lsm_build_psl(mh, wl.beams, n_plan), r["phantom"], r["tally"], 9999,
+                dataclasses.replace(o, no_sync=False))
+    sel_s1, _, _ = lsm.lsm_tally_read(r["tally"])
+    out = {"workload": wl.name, "histories": n_plan * n_batches, "ms": r["ms"],
+           "histories_per_s": n_plan * n_batches / t, "u_mean_rel_D50": u, "s_to_1pct": t * (u / 0.01) ** 2,
+           "kernels_ms": r["kernels_ms"],
+           # FP32 transport and FP32 partial tallies against FP64 bookkeeping of the same run:
+           # the energy ledger (FP64 sums of FP32 values) against the source energy, and the
+           # folded FP64 tally against the ledger's deposited energy
+           "energy_balance_rel": abs(led["source"] - led["rejected"] - led["escaped"] - led["deposited"])
+           / led["source"],
+           "tally_vs_ledger_rel": float(s1.sum() / led["deposited"] - 1)}
+    return out, {"s1": s1, "s2": s2, "n_batches": nb, "n_hist": n_plan * n_batches, "shape": wl.phantom.rho.shape,
+                 "select": sel_s1}
+
+
+def precision_vs_oracle(keep, n_o: int = 6_000_000, plan_o: int = 375_000):
+    """CPU-baseline leg of the precision case: an independent FP64 oracle run
+    of n_o histories (disjoint batches over the host's cores) timed and
+    compared voxel by voxel with the GPU's 1e8-history dose: fraction of |z| < 3
+    over voxels above 10 % of the maximum, and the mean dose ratio with its
+    statistical sigma."""
+    from oracle import oracle as O
+    from oracle import pool
+    nz, ny, nx = keep["shape"]
+    c = nx // 2
+    box = ((0, nz), (c - 32, c + 32), (c - 32, c + 32))
+    b_o = n_o // plan_o
+    r = pool.run_batches("workload_hetero", n_o, plan_o, b_o, seed=17, box=box)
+    dg, sg = O.dose_and_sigma(keep["s1"], keep["s2"], keep["n_batches"])
+    dg = dg.reshape(nz, ny, nx)[:, c - 32:c + 32, c - 32:c + 32] / keep["n_hist"]
+    sg = sg.reshape(nz, ny, nx)[:, c - 32:c + 32, c - 32:c + 32] / keep["n_hist"]
+    do, so = O.dose_and_sigma(r["s1"], r["s2"], b_o)
+    do, so = do / n_o, so / n_o
+    # voxels above 10 % of the maximum of an independent GPU run (no selection bias)
+    ref = keep["select"].reshape(nz, ny, nx)[:, c - 32:c + 32, c - 32:c + 32]
+    sel = ref > 0.1 * ref.max()
+    z = (dg - do)[sel] / np.sqrt(sg[sel] ** 2 + so[sel] ** 2 + 1e-300)
+    ratio = float(dg[sel].sum() / do[sel].sum())
+    sig_ratio = float(np.sqrt((sg[sel] ** 2).sum()) / dg[sel].sum() + np.sqrt((so[sel] ** 2).sum()) / do[sel].sum())
+    return {"kind": "oracle", "value": n_o / r["run_s"], "unit": "histories/s", "cores": r["processes"],
+            "sample": f"{n_o} histories of the precision case as {b_o} batches of {plan_o} over "
+                      f"{r['processes']} processes, {r['wall_s']:.1f} s with set-up",
+            "voxels_compared": int(sel.sum()), "z_pass_frac": float(np.mean(np.abs(z) < 3)),
+            "mean_dose_ratio_gpu_over_oracle": ratio, "mean_dose_ratio_sigma": sig_ratio,
+            "oracle_max_history_imbalance": float(r["max_balance"])}
+
+
 def _fs_type(path: str) -> str:
     """File-system type of the mount holding `path` (from /proc/mounts)."""
     best, kind = "", "unknown"
@@ -592,17 +808,19 @@ def main():
     import torch
     import torch.distributed as dist
 
-    if world > 1:
-        dist.init_process_group("gloo")
     torch.cuda.set_device(local)
+    if world > 1:
+        # tally sums over NCCL, host scalars (timing) over gloo
+        dist.init_process_group("cpu:gloo,cuda:nccl", device_id=torch.device("cuda", local))
     from paper_1503_01725_b300 import lsm
     from paper_1503_01725_b300 import workloads as W
 
     lsm.load_library()
     wl = W.workload_full_10x10(args.n_hist)
     n_plan = args.n_hist // args.n_batches
-    opts = lsm.RunOpts(electron_mode=1, n_batches=args.n_batches, chunk=args.chunk)
-    seed0 = rank_seed(rank)
+    opts = lsm.RunOpts(electron_mode=1, n_batches=args.n_batches, chunk=args.chunk,
+                       first_batch=rank_first_batch(rank, args.n_batches))
+    seed0 = SEED
     stream = torch.cuda.current_stream()
 
     # device-resident inputs: phantom and tally created once
@@ -633,11 +851,14 @@ def main():
 
     # the linac's PSR model is loaded once, like the phantom (lsm_model_create)
     model_h = lsm.lsm_model_create(wl.model)
+    from paper_1503_01725_b300 import dist as DP
 
     def step(i):
         psl = lsm.lsm_build_psl(model_h, wl.beams, n_plan, async_=True)
         lsm.lsm_tally_reset(tally)
         lsm.lsm_run(psl, ph, tally, seed0 + i, step_opts)
+        if world > 1:
+            DP.reduce_tally(lsm, tally)            # the one exchange step: sum of the ranks' tallies
         d, s = lsm.lsm_dose(tally, ph, psl.denom / n_plan, device=True)
         return psl, d, s
 
@@ -665,6 +886,8 @@ def main():
 
     def e2e_read(job, out):
         phh, psl, tt, stream = job
+        if world > 1:
+            DP.reduce_tally(lsm, tt, stream=stream)
         return lsm.lsm_dose(tt, phh, psl.denom / n_plan, out=out, stream=stream)   # device -> host, waits
 
     # one step at a time: each call sequence completes before the next starts;
@@ -752,6 +975,8 @@ def main():
     timers = lsm.lsm_timing_read(reset=True)
     lsm.lsm_timing_enable(False)
     led, st = lsm.lsm_tally_ledger(tally)      # counters of the last step (reset each step)
+    if world > 1:                              # summed over the ranks: per-rank work below
+        st = {k: v // world for k, v in st.items()}
     total_ms = float(sum(ms_steps))
     total_ms = slowest_ms(total_ms, world)
     if world > 1:
@@ -774,7 +999,7 @@ def main():
     n_st = args.steps
     per_step = {k: v[0] / n_st for k, v in timers.items()}
     units = {
-        "sample": args.n_hist * B_SAMPLE_PER_HIST,
+        "sample": (st["photons"] + st["electrons"]) * B_SAMPLE_PER_ENTERING,
         "photon": st["flights"] * B_FLIGHT + st["photons"] * B_QUEUE + st["real"] * B_DEPOSIT,
         "electron": st["esteps"] * B_ESTEP + st["electrons"] * B_QUEUE,
     }
@@ -828,6 +1053,12 @@ def main():
         lsm.lsm_timing_enable(True)
         multibeam = multibeam_block(lsm, W, opts)
         lsm.lsm_timing_enable(False)
+    fields = None
+    if not args.no_fields:
+        fields = fields_block(lsm, W, opts)
+    precision, keep = None, None
+    if not args.no_precision:
+        precision, keep = precision_block(lsm, W, opts)
     pslfile = None
     if not args.no_pslfile:
         lsm.lsm_timing_enable(True)
@@ -842,6 +1073,9 @@ def main():
                          f"(disjoint seeds), {el:.1f} s",
                "one_core": {"value": rate1, "cores": 1,
                             "sample": f"{n_done1} histories as 1e5-history plans, {el1:.1f} s"}}
+        if keep is not None:
+            # the precision case's error against the FP64 oracle (FP32 transport, FP32 partials)
+            cpu["precision_case"] = precision_vs_oracle(keep)
     line = {
         "metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -851,7 +1085,9 @@ def main():
                    "histories_per_iteration": iteration_size(opts, n_plan),
                    "ctas_per_sm": opts.ctas_per_sm, "cuda_graph": bool(opts.use_graph), "autotuned": tuned,
                    "phantom": "water 64^3 x 0.25 cm", "field_cm": 10,
-                   "sub_sources": 3, "electrons": "CSDA", "parallelism": f"replicas x{world}",
+                   "sub_sources": 3, "electrons": "CSDA",
+                   "parallelism": (f"data-parallel x{world}: disjoint batch ranges of one seed, "
+                                   "tally summed over ranks (NCCL) in every step") if world > 1 else "1 GPU",
                    "l2": "flushed by a 512 MiB write before each step, outside the timed events"},
         "s_to_1pct": t1, "u_mean_rel_D50": u,
         "kernels_ms_per_step": {k: round(v, 4) for k, v in per_step.items() if v > 0},
@@ -864,6 +1100,8 @@ def main():
         "denoised": denoised,
         "commissioning_validation": validation,
         "multibeam": multibeam,
+        "fields": fields,
+        "precision": precision,
         "pslfile": pslfile,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_serial_rate, "unit": "histories/s", "h2d_bytes_per_step": int(h2d),

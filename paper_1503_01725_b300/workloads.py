@@ -272,6 +272,15 @@ def workload_full_10x10(n_hist: int = 10_000_000) -> Workload:
                     beams(square_field(10.0)), water_phantom(64, 64, 64, 0.25), n_hist, 1, 2)
 
 
+def workload_field(field_cm: float, n_hist: int = 10_000_000, hetero: bool = False) -> Workload:
+    """Open square field of field_cm on a 32 cm cube of 64^3 voxels of 0.5 cm,
+    water or the seeded heterogeneous phantom; rings to 3.2 cm on the
+    phase-space plane (0.32 cm), so that fields up to 20x20 cm2 are covered."""
+    ph = heterogeneous_phantom(64, 64, 64, 0.5) if hetero else water_phantom(64, 64, 64, 0.5)
+    name = f"3src-{field_cm:g}x{field_cm:g}-{'hetero' if hetero else 'water'}64x0.5"
+    return Workload(name, psr_model(10, 10, 0.32, seed=2), beams(square_field(field_cm)), ph, n_hist, 1, 2)
+
+
 def workload_commissioning(hist_lo: int = 10_000, hist_hi: int = 1_000_000) -> Workload:
     """300 PSRs (3 x 10 x 10), fields 4/10/20 cm2, water 64x64x128 at 0.25 cm;
     per-PSR history counts proportional to the PSR weight, clamped."""

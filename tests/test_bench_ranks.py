@@ -1,5 +1,5 @@
-"""Multi-rank host logic of bench.py on CPU (gloo, world size 2): ranks use
-distinct Philox keys and the reported time is the slowest rank's."""
+"""Multi-rank host logic of bench.py on CPU (gloo, world size 2): ranks run
+disjoint batch ranges of one seed and the reported time is the slowest rank's."""
 import os
 import socket
 
@@ -22,13 +22,13 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     ms = 10.0 + 5.0 * rank
     slow = bench.slowest_ms(ms, world)
-    seeds = [None] * world
-    dist.all_gather_object(seeds, bench.rank_seed(rank))
-    q.put((rank, slow, seeds))
+    firsts = [None] * world
+    dist.all_gather_object(firsts, bench.rank_first_batch(rank, 16))
+    q.put((rank, slow, firsts))
     dist.destroy_process_group()
 
 
-def test_two_rank_timing_and_keys():
+def test_two_rank_timing_and_batch_ranges():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -39,6 +39,7 @@ def test_two_rank_timing_and_keys():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, slow, seeds in out:
+    for rank, slow, firsts in out:
         assert slow == pytest.approx(15.0)
-        assert len(set(seeds)) == 2
+        # rank r runs batches [16 r, 16 r + 16): disjoint histories of one seed
+        assert sorted(firsts) == [0, 16]

@@ -145,10 +145,15 @@ def test_full_dose_against_oracle_batches(full_run):
     assert abs(dg[sel].mean() / do[sel].mean() - 1) < 0.005
 
 
-def test_full_heterogeneous_phantom(L):
-    """256x256x160 heterogeneous phantom at 0.25 cm, 1e8 histories (FP32
-    transport, FP32 partial tallies flushed to FP64): energy balance at full
-    size, and dose against an oracle run of the first 2e5 histories."""
+def test_precision_case_voxel_parity(L):
+    """The precision case: 256x256x160 heterogeneous phantom at 0.25 cm, 1e8
+    histories in the benchmark's launch configuration (one run of 16 batches:
+    FP32 transport, FP32 partial slices folded into FP64 sums). Energy balances
+    at full size, and the dose matches an independent FP64 oracle run of 1.2e7
+    histories (32 batches spread over the host's cores) voxel by voxel: |z| < 3
+    on at least 99 % of the voxels above 10 % of the maximum and the mean dose
+    within 0.5 %."""
+    from oracle import pool
     wl = W.workload_hetero(100_000_000)
     n_plan = wl.n_hist // 16
     g = L.lsm_build_psl(wl.model, wl.beams, n_plan)
@@ -159,19 +164,40 @@ def test_full_heterogeneous_phantom(L):
     led, st = L.lsm_tally_ledger(t)
     assert rc == 0 and st["histories"] == wl.n_hist and st["overflows"] == 0
     assert led["source"] == pytest.approx(led["rejected"] + led["escaped"] + led["deposited"], rel=1e-6)
-    # oracle: a 100k-history plan of the same workload, 2 batches; compare depth-dose
-    # of the central column region (summed over a 2x2 cm block to get oracle statistics)
-    o = O.Plan(wl.model, wl.beams, 100_000)
-    r = O.run(o, wl.phantom, 17, n_batches=2, electron_mode=1)
-    D = O.Plan(wl.model, wl.beams, 100_000).denom
-    dg = s1.reshape(ph.desc.nz, ph.desc.ny, ph.desc.nx) / (nb * n_plan) * D
-    do = r["s1"] / (2 * 100_000) * D
-    c = ph.desc.nx // 2
-    prof_g = dg[:, c - 4:c + 4, c - 4:c + 4].sum(axis=(1, 2))
-    prof_o = do[:, c - 4:c + 4, c - 4:c + 4].sum(axis=(1, 2))
-    sel = prof_o > 0.2 * prof_o.max()
-    # energy per history deposited along the central column agrees within the oracle's statistics
-    assert abs(prof_g[sel].sum() / prof_o[sel].sum() - 1) < 0.03
+    P = wl.phantom
+    c = P.nx // 2
+    box = ((0, P.nz), (c - 32, c + 32), (c - 32, c + 32))       # +-8 cm around the 10x10 field
+    # 1.2e7 oracle histories in 32 batches: voxels near 10 % of the maximum
+    # then collect enough deposits per batch for their batch sigma to hold
+    n_o, plan_o, b_o = 12_000_000, 375_000, 32
+    r = pool.run_batches("workload_hetero", n_o, plan_o, b_o, seed=17, box=box)
+    assert r["max_balance"] < 1e-12 and int(r["stats"][0]) == n_o
+    # energy per history in each voxel and its batch sigma, both sides
+    dg_full, sg_full = O.dose_and_sigma(s1, s2, nb)
+    dg_full = dg_full.reshape(P.nz, P.ny, P.nx) / wl.n_hist
+    sg_full = sg_full.reshape(P.nz, P.ny, P.nx) / wl.n_hist
+    do, so = O.dose_and_sigma(r["s1"], r["s2"], b_o)
+    do, so = do / n_o, so / n_o
+    (z0, z1), (y0, y1), (x0, x1) = box
+    dg, sg = dg_full[z0:z1, y0:y1, x0:x1], sg_full[z0:z1, y0:y1, x0:x1]
+    # the box holds every voxel above 10 % of the maximum
+    outside = dg_full.copy()
+    outside[z0:z1, y0:y1, x0:x1] = 0
+    assert outside.max() < 0.1 * dg_full.max()
+    # voxels chosen on an independent GPU run (another seed): choosing them on
+    # either compared estimate favours voxels where it fluctuated high and
+    # biases the mean ratio (by a few percent when chosen on the oracle)
+    L.lsm_tally_reset(t)
+    L.lsm_run(g, ph, t, wl.seed + 1000, L.RunOpts(electron_mode=1, n_batches=16))
+    ref = L.lsm_tally_read(t)[0].reshape(P.nz, P.ny, P.nx)[z0:z1, y0:y1, x0:x1]
+    sel = ref > 0.1 * ref.max()
+    assert sel.sum() > 50_000
+    z = (dg - do)[sel] / np.sqrt(sg[sel] ** 2 + so[sel] ** 2 + 1e-300)
+    frac = float(np.mean(np.abs(z) < 3))
+    mean_rel = float(dg[sel].sum() / do[sel].sum() - 1)
+    hi = (dg > 0.5 * dg.max())[sel]
+    assert frac >= 0.99, (frac, float(np.mean(np.abs(z[hi]) < 3)), float(np.mean(np.abs(z[~hi]) < 3)), mean_rel)
+    assert abs(mean_rel) < 0.005, mean_rel
 
 
 def test_batched_basis_equals_single_run_decomposition(L):
