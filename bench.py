@@ -18,9 +18,11 @@ u the mean batch relative standard deviation over voxels above 50% of Dmax.
 --impl reference times the CPU oracle (plain single-threaded FP64 C, one
 process per host core on disjoint seeds) on a bounded sample of the same
 workload.
-Under torchrun (N > 1) every rank runs the same workload with its own Philox
-key (independent histories, no data-path collective: weak scaling); rank 0
-prints the line with the slowest rank's time.
+Under torchrun (N > 1) every rank runs the same workload on its own range of
+batches of one seed (disjoint histories: weak scaling), and every step ends
+with the one exchange step of the method, the sum of the ranks' tallies over
+NCCL (paper_1503_01725_b300.dist); rank 0 prints the line with the slowest
+rank's time.
 """
 from __future__ import annotations
 
@@ -471,7 +473,22 @@ def denoised_block(lsm, reps: int = 5, case: int = 192):
     except Exception:
         bf16, bkind = 1800.0, "fallback"
     ach = gf / T_conv / 1e3
+    # every held-out case (20, fields 4-20 cm), each judged by its own 1e9-history run
+    rows = []
+    for c in W.DENOISE_TEST:
+        q = DZ.generate([c], n_lo=1_000_000, n_hi=1_000_000, n_ref=1_000_000_000)[0]
+        dq = lsm.lsm_unet_forward(net, q["lo"], q["rho"])
+        rows.append({"case": c, "field_cm": round(float(q["field_cm"]), 2),
+                     "gamma": lsm.lsm_gamma(dq, q["ref"], (2.5, 2.5, 2.5), 0.02, 2.0, 0.1)[0],
+                     "u_rms": lsm.lsm_dose_error(dq, q["ref"], q["s_ref"], level=0.5),
+                     "gamma_mc_1e6": lsm.lsm_gamma(q["lo"], q["ref"], (2.5, 2.5, 2.5), 0.02, 2.0, 0.1)[0]})
+    held_out = {"cases": len(rows), "gamma_mean": float(np.mean([r["gamma"] for r in rows])),
+                "gamma_min": float(min(r["gamma"] for r in rows)),
+                "cases_gamma_ge_99": int(sum(r["gamma"] >= 0.99 for r in rows)),
+                "u_rms_mean": float(np.mean([r["u_rms"] for r in rows])),
+                "u_rms_max": float(max(r["u_rms"] for r in rows)), "per_case": rows}
     return {"workload": f"denoise-{case} 128^3 (field {wl.extra['field_cm']:.1f} cm), weights unet128.npz",
+            "held_out_20": held_out,
             "judge": "1e9-history MC of the same case", "s_mc_1e6": T_mc, "s_network": T_net,
             "s_denoised": t_den, "u_rms_mc_1e6": ulo, "u_rms_denoised": uden,
             "gamma_2pct_2mm_denoised": float(np.mean(g_den)),

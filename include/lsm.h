@@ -619,6 +619,16 @@ lsm_status lsm_unet_train_step(lsm_unet *net, int32_t n, int32_t d, int32_t h, i
  * lsm_unet_create) and the gradient of the last training step. */
 lsm_status lsm_unet_params(const lsm_unet *net, float *dst, lsm_mem mem, lsm_stream stream);
 lsm_status lsm_unet_grad(const lsm_unet *net, float *dst, lsm_mem mem, lsm_stream stream);
+/*
+ * lsm_unet_set_wgrad -- where lsm_unet_train_step computes the convolutions'
+ * weight gradients: 1 (default) on the tensor cores (a tcgen05 GEMM over
+ * voxels: M = (tap, input channel), N = output channels, BF16 operands from
+ * channel-major copies of the layer input and output gradient, FP32
+ * accumulation in tensor memory), 0 on the CUDA cores (FP32). Both read the
+ * same BF16 activations and accumulate in FP32. Process-wide.
+ * Errors: LSM_ERR_ARG for another value.
+ */
+lsm_status lsm_unet_set_wgrad(int tensor_cores);
 
 /*
  * Judging a dose estimate against a reference (the denoiser's error against

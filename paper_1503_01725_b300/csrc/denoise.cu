@@ -158,6 +158,15 @@ __device__ void mb_drain(uint64_t *b, unsigned parity, unsigned *err)
     }
 }
 
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(s2u(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
                                             uint64_t *bar)
 {
@@ -832,6 +841,323 @@ lsm_status pool_or_up(const lsm_vol *in, const lsm_vol *out, bool up, cudaStream
     timer_end(tk, st);
     LSM_CUDA(cudaGetLastError());
     return LSM_OK;
+}
+
+// ------------------------------------------ weight gradient on tcgen05 ---
+// dW[o][t][c] = sum over interior voxels v of gz[v][o] x[v + off_t][c], t =
+// (dz, dy, dx). The contraction runs over voxels, so voxels are the MMA's K.
+// The activations are voxel-major (channels contiguous), while the operands
+// below are K-major, and a tap's offset off_t = (dz-1)P + (dy-1)(w+2) + dx-1
+// is not a multiple of the 8 voxels (16 bytes) a TMA start or a matrix
+// descriptor can move by. So a transposition pass first writes channel-major
+// copies in a layout L8 whose row pitch W8 = roundup(w + 2, 8) and plane pitch
+// P8 = (h + 2) W8 are multiples of 8: three copies of x, copy k holding the
+// value at L8 index u + k - 1 (the dx shift), and one of gz. Tap t's operand
+// then starts at u0 + (dz-1) P8 + (dy-1) W8, a multiple of 8 when u0 is.
+//
+// GEMM: M = 128 rows of (tap, input channel) pairs (128 / cin taps per row
+// tile, 27 taps in ceil(27 cin / 128) tiles), N = cout, K = voxels in chunks
+// of 64 (one 128-byte swizzled row per operand row). A CTA owns one row tile
+// and a range of chunks of one volume: TMA loads (128 / cin boxes for A, one
+// for B per stage), one thread issues the MMAs into one TMEM accumulator,
+// four warps read it at the end and add it to dW with FP32 atomics.
+
+struct L8 {
+    int d, h, w, w8;
+    long long p8, lq;         // plane pitch, voxels per volume copy
+};
+
+inline L8 l8_of(int d, int h, int w)
+{
+    L8 q;
+    q.d = d; q.h = h; q.w = w;
+    q.w8 = (w + 2 + 7) / 8 * 8;
+    q.p8 = (long long)(h + 2) * q.w8;
+    q.lq = (long long)(d + 2) * q.p8;
+    return q;
+}
+
+// out[((b ncopy + k) c + ch) lq + u] = in at the L8 index u + shift_k (shift_k
+// = k - 1 with three copies, 0 with one) if that voxel is interior, else 0.
+// A CTA transposes 64 consecutive u of one (volume, copy) for all c channels
+// through shared memory, reading 16-byte channel groups and writing 128-byte
+// voxel rows.
+__global__ void __launch_bounds__(256) k_chmajor(const __nv_bfloat16 *__restrict__ in, int ct, int co, int c, VolIdx v,
+                                                 L8 q, int ncopy, __nv_bfloat16 *__restrict__ out)
+{
+    __shared__ __nv_bfloat16 tile[64 * (128 + 2)];
+    const int pitch = c + 2;
+    const long long u0 = (long long)blockIdx.x * 64;
+    const int k = blockIdx.y % ncopy, b = blockIdx.y / ncopy;
+    const int shift = ncopy == 3 ? k - 1 : 0;
+    const int groups = c / 8;
+    for (int i = threadIdx.x; i < 64 * groups; i += blockDim.x) {
+        const int uu = i / groups, g = i - uu * groups;
+        const long long u = u0 + uu + shift;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (u >= 0 && u < q.lq && u0 + uu < q.lq) {
+            const long long z = u / q.p8, r = u - z * q.p8;
+            const int y = (int)(r / q.w8), x = (int)(r - (long long)y * q.w8);
+            if (z >= 1 && z <= q.d && y >= 1 && y <= q.h && x >= 1 && x <= q.w) {
+                const long long src = (long long)b * v.lp + z * v.p + (long long)y * v.w2 + x;
+                val = *reinterpret_cast<const uint4 *>(in + src * ct + co + g * 8);
+            }
+        }
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&val);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tile[uu * pitch + g * 8 + j] = e[j];
+    }
+    __syncthreads();
+    __nv_bfloat16 *o = out + ((long long)blockIdx.y * c) * q.lq + u0;
+    for (int i = threadIdx.x; i < 32 * c; i += blockDim.x) {
+        const int ch = i / 32, pr = i - ch * 32;      // voxels 2 pr, 2 pr + 1 of channel ch
+        if (u0 + 2 * pr + 1 < q.lq) {
+            __nv_bfloat162 two;
+            two.x = tile[(2 * pr) * pitch + ch];
+            two.y = tile[(2 * pr + 1) * pitch + ch];
+            *reinterpret_cast<__nv_bfloat162 *>(o + (long long)ch * q.lq + 2 * pr) = two;
+        }
+    }
+}
+
+template <int COUT, int CIN>
+struct WgCfg {
+    static constexpr int kTpt = 128 / CIN;                  // taps per row tile
+    static constexpr int kMt = (27 + kTpt - 1) / kTpt;      // row tiles
+    static constexpr int kA = 128 * 128;                    // 128 rows x 64 voxels, BF16
+    static constexpr int kB = COUT * 128;
+    static constexpr int kStage = kA + kB;                  // multiple of 1024
+    static constexpr int kStages = kStage <= 20 * 1024 ? 5 : 4;
+    static constexpr int kTx = kA + kB;
+    static constexpr int kCols = COUT < 32 ? 32 : COUT;     // TMEM columns (power of 2)
+    static constexpr int kSmem = kStages * kStage + 1024;
+    static_assert(CIN == 16 || CIN == 32 || CIN == 64 || CIN == 128, "cin");
+    static_assert(COUT % 16 == 0 && COUT <= 128, "cout");
+};
+
+struct WgArgs {
+    float *dw;                // [cout][27][cin], accumulated
+    L8 q;
+    long long u_first;        // first chunk start (multiple of 64)
+    int n_chunks;             // chunks of 64 voxels per volume
+    int ksplit;               // CTAs per (volume, row tile)
+    unsigned *err;
+    unsigned long long wait_ns;
+};
+
+template <int COUT, int CIN>
+__global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant__ CUtensorMap mx,
+                                                        const __grid_constant__ CUtensorMap mg, const WgArgs a)
+{
+    using C = WgCfg<COUT, CIN>;
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[C::kStages], empty[C::kStages], accf, mma_done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const uint32_t sbase = (s2u(dsm) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ks = blockIdx.x % a.ksplit;
+    const int mt = (blockIdx.x / a.ksplit) % C::kMt;
+    const int vol = blockIdx.x / (a.ksplit * C::kMt);
+    const int per = (a.n_chunks + a.ksplit - 1) / a.ksplit;
+    const int c0 = ks * per, c1 = min(a.n_chunks, c0 + per);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) {
+            mb_init(&full[s], 1);
+            mb_init(&empty[s], 1);
+        }
+        mb_init(&accf, 1);
+        mb_init(&mma_done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s2u(&tmem_slot)),
+                     "r"(C::kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = tmem_slot;
+    const int nk = c1 > c0 ? c1 - c0 : 0;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&mx) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&mg) : "memory");
+            int it = 0;
+            for (; it < nk; ++it) {
+                const int s = it % C::kStages;
+                if (it >= C::kStages &&
+                    !mb_wait(&empty[s], (unsigned)((it / C::kStages) - 1) & 1u, &abort_flag, a.err, 1u, a.wait_ns))
+                    break;
+                const uint32_t sa = sbase + (uint32_t)(s * C::kStage), sb = sa + C::kA;
+                const long long u0 = a.u_first + (long long)(c0 + it) * 64;
+                mb_expect(&full[s], C::kTx);
+#pragma unroll
+                for (int k = 0; k < C::kTpt; ++k) {
+                    // rows of taps past the 27th (last row tile) load tap 26's
+                    // box again; the epilogue drops them
+                    const int t = min(mt * C::kTpt + k, 26);
+                    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+                    const int ux = (int)(u0 + (long long)(dz - 1) * a.q.p8 + (long long)(dy - 1) * a.q.w8);
+                    const int row = (vol * 3 + dx) * CIN;
+                    tma_load_2d(sa + (uint32_t)(k * CIN * 128), &mx, ux, row, &full[s]);
+                }
+                tma_load_2d(sb, &mg, (int)u0, vol * COUT, &full[s]);
+            }
+            for (int j = it > C::kStages ? it - C::kStages : 0; j < it; ++j)
+                mb_drain(&full[j % C::kStages], (unsigned)(j / C::kStages) & 1u, a.err);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            constexpr uint32_t idesc = (1u << 4)      // D: FP32
+                                       | (1u << 7)    // A: BF16
+                                       | (1u << 10)   // B: BF16
+                                       | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            bool ok = true;
+            for (int it = 0; it < nk; ++it) {
+                const int s = it % C::kStages;
+                if (!mb_wait(&full[s], (unsigned)(it / C::kStages) & 1u, &abort_flag, a.err, 4u, a.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                tc_after();
+                const uint32_t sa = sbase + (uint32_t)(s * C::kStage), sb = sa + C::kA;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mma_bf16(tmem, sdesc(sa + (uint32_t)(j * 32), 16, 1024, 2u), sdesc(sb + (uint32_t)(j * 32), 16, 1024, 2u),
+                             idesc, (it | j) != 0);
+                mma_commit(&empty[s]);
+            }
+            if (ok && nk > 0) mma_commit(&accf);
+            mma_commit(&mma_done);
+            mb_drain(&mma_done, 0u, a.err);
+        }
+    } else if (nk > 0) {   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        const int q = warp & 3;
+        const bool ok = mb_wait(&accf, 0u, &abort_flag, a.err, 8u, a.wait_ns);
+        if (__all_sync(0xFFFFFFFFu, ok)) {
+            tc_after();
+            const int R = mt * 128 + 32 * q + lane;
+            const int t = R / CIN, c = R % CIN;
+#pragma unroll
+            for (int o0 = 0; o0 < COUT; o0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)o0, r);
+                if (t < 27) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        atomicAdd(a.dw + ((size_t)(o0 + i) * 27 + t) * CIN + c, __uint_as_float(r[i]));
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kCols) : "memory");
+    }
+}
+
+template <int COUT, int CIN>
+lsm_status launch_wgrad_tc(const CUtensorMap &mx, const CUtensorMap &mg, WgArgs a, int n, cudaStream_t st)
+{
+    using C = WgCfg<COUT, CIN>;
+    static int occ = 0;
+    if (!occ) {
+        LSM_CUDA(cudaFuncSetAttribute(k_wgrad_tc<COUT, CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+        // resident CTAs counted from shared memory, TMEM columns, registers and
+        // warps (the occupancy query answers 1 for kernels holding tcgen05)
+        cudaFuncAttributes fa;
+        LSM_CUDA(cudaFuncGetAttributes(&fa, k_wgrad_tc<COUT, CIN>));
+        int dev = 0, smem_sm = 0, rsv = 0;
+        LSM_CUDA(cudaGetDevice(&dev));
+        LSM_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        LSM_CUDA(cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+        const int by_smem = smem_sm / (C::kSmem + (int)fa.sharedSizeBytes + rsv);
+        const int by_tmem = 512 / C::kCols;
+        const int by_regs = 65536 / (((fa.numRegs + 7) / 8 * 8) * kThreads);
+        occ = std::max(1, std::min(std::min(by_smem, by_tmem), std::min(by_regs, 64 / (kThreads / 32))));
+    }
+    const int target = occ * sm_count();
+    a.ksplit = std::max(1, std::min(a.n_chunks, target / (C::kMt * n)));
+    const int grid = a.ksplit * C::kMt * n;
+    k_wgrad_tc<COUT, CIN><<<grid, kThreads, C::kSmem, st>>>(mx, mg, a);
+    count_launch();
+    LSM_CUDA(cudaGetLastError());
+    return LSM_OK;
+}
+
+// dW += the weight gradient of a 3x3x3 layer (cin -> cout) from its input x
+// (a channel slice) and its ReLU-masked output gradient gz, on the tensor cores.
+lsm_status wgrad_tc(const lsm_vol &gz, const lsm_vol &x, int cin, int cout, float *dw, cudaStream_t st)
+{
+    const VolIdx v = vidx(x.d, x.h, x.w);
+    const L8 q = l8_of(x.d, x.h, x.w);
+    const int n = x.n;
+    if (q.lq >= (1ll << 30) || (long long)n * 3 * cin > (1 << 20)) return set_arg_error("wgrad: volume too large");
+    EncodeTiled enc = encode_fn();
+    if (!enc) return set_arg_error("wgrad: cuTensorMapEncodeTiled unavailable");
+    unsigned *err = err_word();
+    if (!err) return set_cuda_error(cudaErrorMemoryAllocation, "wgrad: error word");
+    const size_t nx = (size_t)n * 3 * cin * q.lq, ng = (size_t)n * cout * q.lq;
+    __nv_bfloat16 *xt = nullptr;
+    LSM_CUDA(dev_malloc((void **)&xt, (nx + ng) * sizeof(__nv_bfloat16) + 256, st));
+    __nv_bfloat16 *gt = xt + nx;
+    const unsigned gx = (unsigned)((q.lq + 63) / 64);
+    k_chmajor<<<dim3(gx, (unsigned)(n * 3)), 256, 0, st>>>((const __nv_bfloat16 *)x.data, x.c_total, x.c_offset, cin,
+                                                           v, q, 3, xt);
+    count_launch();
+    k_chmajor<<<dim3(gx, (unsigned)n), 256, 0, st>>>((const __nv_bfloat16 *)gz.data, gz.c_total, gz.c_offset, cout, v,
+                                                     q, 1, gt);
+    count_launch();
+    cudaError_t ce = cudaGetLastError();
+    lsm_status r = LSM_OK;
+    CUtensorMap mx, mg;
+    const cuuint32_t es[2] = {1, 1};
+    const cuuint64_t dx_[2] = {(cuuint64_t)q.lq, (cuuint64_t)n * 3 * cin};
+    const cuuint64_t dg_[2] = {(cuuint64_t)q.lq, (cuuint64_t)n * cout};
+    const cuuint64_t str[1] = {(cuuint64_t)q.lq * 2};
+    const cuuint32_t bx[2] = {64, (cuuint32_t)cin}, bg[2] = {64, (cuuint32_t)cout};
+    if (ce != cudaSuccess) {
+        r = set_cuda_error(ce, "wgrad: transposition");
+    } else if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xt, dx_, str, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+               enc(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, gt, dg_, str, bg, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        r = set_arg_error("wgrad: tensor map encoding failed");
+    } else {
+        WgArgs a;
+        a.dw = dw;
+        a.q = q;
+        const long long u_lo = q.p8 + q.w8 + 1, u_hi = (long long)x.d * q.p8 + (long long)x.h * q.w8 + x.w;
+        a.u_first = u_lo / 64 * 64;
+        a.n_chunks = (int)((u_hi + 1 - a.u_first + 63) / 64);
+        a.ksplit = 1;
+        a.err = err;
+        a.wait_ns = g_conv_wait_ns;
+        switch (cout * 1000 + cin) {
+        case 16016: r = launch_wgrad_tc<16, 16>(mx, mg, a, n, st); break;
+        case 16032: r = launch_wgrad_tc<16, 32>(mx, mg, a, n, st); break;
+        case 32016: r = launch_wgrad_tc<32, 16>(mx, mg, a, n, st); break;
+        case 32032: r = launch_wgrad_tc<32, 32>(mx, mg, a, n, st); break;
+        case 32064: r = launch_wgrad_tc<32, 64>(mx, mg, a, n, st); break;
+        case 64032: r = launch_wgrad_tc<64, 32>(mx, mg, a, n, st); break;
+        case 64064: r = launch_wgrad_tc<64, 64>(mx, mg, a, n, st); break;
+        case 64128: r = launch_wgrad_tc<64, 128>(mx, mg, a, n, st); break;
+        case 128064: r = launch_wgrad_tc<128, 64>(mx, mg, a, n, st); break;
+        default: r = set_arg_error("wgrad: unsupported channel configuration");
+        }
+    }
+    cudaFreeAsync(xt, st);
+    return r;
 }
 
 }  // namespace dn

@@ -389,6 +389,9 @@ lsm_status train_alloc(lsm_unet *u, int n, int d, int h, int w, cudaStream_t st)
     return LSM_OK;
 }
 
+// weight gradients on the tensor cores (wgrad_tc, default) or on the CUDA cores
+int g_wgrad_tc = 1;
+
 lsm_status wgrad(const lsm_vol &gz, const lsm_vol &x, int cin, int cout, float *dw, cudaStream_t st)
 {
     const VolIdx v = vidx(x.d, x.h, x.w);
@@ -458,7 +461,8 @@ lsm_status train_step(lsm_unet *u, int n, int d, int h, int w, const float *dose
                       256, 0, st>>>((const bf16 *)gz.data, gz.c_total, co, n, vv,
                                     T->grad + layer_offset(i) + 27ll * ci * co);
         count_launch();
-        lsm_status r = wgrad(gz, V[kConvIn[i]], ci, co, T->grad + layer_offset(i), st);
+        lsm_status r = g_wgrad_tc ? wgrad_tc(gz, V[kConvIn[i]], ci, co, T->grad + layer_offset(i), st)
+                                  : wgrad(gz, V[kConvIn[i]], ci, co, T->grad + layer_offset(i), st);
         timer_end(t0, st);
         if (r) return r;
         LSM_CUDA(cudaGetLastError());
@@ -573,6 +577,13 @@ lsm_status lsm_unet_grad(const lsm_unet *net, float *dst, lsm_mem mem, lsm_strea
     LSM_CUDA(cudaMemcpyAsync(dst, net->train->grad, (size_t)dn::param_count() * 4,
                              mem == LSM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     if (mem == LSM_MEM_HOST) LSM_CUDA(cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+lsm_status lsm_unet_set_wgrad(int tensor_cores)
+{
+    if (tensor_cores != 0 && tensor_cores != 1) return set_arg_error("lsm_unet_set_wgrad: 0 or 1");
+    dn::g_wgrad_tc = tensor_cores;
     return LSM_OK;
 }
 

@@ -79,7 +79,7 @@ constexpr int kXsBytes = 2 * kGrid * 16;                                      //
 #define LSM_PHOTON_MINB 3
 #endif
 #ifndef LSM_ELECTRON_MINB
-#define LSM_ELECTRON_MINB 5
+#define LSM_ELECTRON_MINB 4
 #endif
 // radiation lengths (g/cm^2): water-like 36.08, bone 21.68
 
@@ -478,7 +478,7 @@ __device__ __forceinline__ void eflush(const TP &T, Acc &A, Part &p)
 
 // One CSDA step. Returns false when the electron's history ends.
 template <int MODE>
-__device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
+__device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p, const uint4 &blk, bool &blk_used)
 {
     // (reusing the previous step's end voxel here measured 1.6x slower)
     const int vox = voxel(T, p.x, p.y, p.z);
@@ -527,7 +527,16 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p)
             ub = u01(p.rng.pre.w);
             p.rng.have = 0;
         } else {
-            const uint4 r = p.rng.next();
+            // the block at the stream's counter, computed by the caller for
+            // the warp's two steps at once (one of them needs it at most)
+            uint4 r;
+            if (!blk_used) {
+                r = blk;
+                ++p.rng.ctr;
+                blk_used = true;
+            } else {
+                r = p.rng.next();
+            }
             ua = u01(r.x);
             ub = u01(r.y);
             p.rng.pre = r;
@@ -643,7 +652,14 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
         if (!__any_sync(0xffffffffu, alive)) break;
         if constexpr (KIND == 1) {
             if (alive) {
-                alive = electron_step<MODE>(T, xs, A, p);
+                // two CSDA steps per pass of the loop: each consumes two words
+                // of a Philox block, so together they need at most one new
+                // block, computed here for all live lanes at once instead of
+                // by whichever lanes happen to need one at each step
+                const uint4 blk = philox4x32_10(p.rng.k0, p.rng.k1, p.rng.glo, p.rng.ghi, p.rng.sid, p.rng.ctr);
+                bool used = false;
+                alive = electron_step<MODE>(T, xs, A, p, blk, used);
+                if (alive) alive = electron_step<MODE>(T, xs, A, p, blk, used);
                 if (!alive) { A.dep += A.dep32; A.dep32 = 0.0f; }
             }
         } else {

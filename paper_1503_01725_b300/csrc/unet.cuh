@@ -98,6 +98,7 @@ int kc_for(int cin, int cout);
 lsm_status pool_or_up(const lsm_vol *in, const lsm_vol *out, bool up, cudaStream_t st);
 int grid_1d(long long work);
 unsigned *err_word();
+lsm_status wgrad_tc(const lsm_vol &gz, const lsm_vol &x, int cin, int cout, float *dw, cudaStream_t st);
 
 }  // namespace dn
 }  // namespace lsm

@@ -97,10 +97,13 @@ def init_params(seed: int = 0, head_scale: float = 0.0) -> np.ndarray:
     return p
 
 
-def train(pairs, epochs: int = 12, lr: float = 1e-3, seed: int = 0, log=print):
+def train(pairs, epochs: int = 12, lr: float = 1e-3, seed: int = 0, log=print, transpose: bool = False):
     """Adam over the training pairs: one volume per step, shuffled each epoch,
-    random x/y mirroring of input and target together, cosine-decayed learning
-    rate. Returns (network, mean loss per epoch, seconds)."""
+    random x/y mirroring of input and target together (and, with transpose,
+    random exchange of x and y: the square fields and the ring-symmetric source
+    make the transposed case a valid case up to the X/Y jaw heights),
+    cosine-decayed learning rate. Returns (network, mean loss per epoch,
+    seconds)."""
     import torch
     net = lsm.lsm_unet_create(init_params(seed, head_scale=0.01))
     rng = np.random.default_rng(seed)
@@ -113,6 +116,8 @@ def train(pairs, epochs: int = 12, lr: float = 1e-3, seed: int = 0, log=print):
             dims = [d for d, f in ((1, rng.random() < 0.5), (2, rng.random() < 0.5)) if f]
             if dims:
                 lo, hi, rho = (torch.flip(t, dims).contiguous() for t in (lo, hi, rho))
+            if transpose and rng.random() < 0.5:
+                lo, hi, rho = (t.transpose(1, 2).contiguous() for t in (lo, hi, rho))
             lr_k = lr * 0.5 * (1.0 + np.cos(np.pi * k / steps))
             losses.append(lsm.lsm_unet_train_step(net, lo, rho, hi, lr=lr_k))
             k += 1
@@ -160,6 +165,7 @@ def main():
     ap.add_argument("--n-ref", type=int, default=1_000_000_000, help="judge histories for the test cases")
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--transpose", action="store_true", help="also exchange x and y at random in training")
     a = ap.parse_args()
     lsm.load_library()
     n_test = max(1, a.cases // 10)
@@ -170,11 +176,11 @@ def main():
     te = generate(test_ids, a.n_lo, a.n_hi, a.n_ref)
     t_gen = time.time() - t0
     print(f"generated {len(tr) + len(te)} pairs in {t_gen:.0f} s", flush=True)
-    net, hist, t_train = train(tr, a.epochs, a.lr)
+    net, hist, t_train = train(tr, a.epochs, a.lr, transpose=a.transpose)
     rows = evaluate(net, te)
     params = lsm.lsm_unet_params(net)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
-    np.savez(a.out, params=params, epochs=a.epochs, lr=a.lr, n_lo=a.n_lo, n_hi=a.n_hi,
+    np.savez(a.out, params=params, epochs=a.epochs, lr=a.lr, n_lo=a.n_lo, n_hi=a.n_hi, transpose=a.transpose,
              train_cases=np.array(train_ids), test_cases=np.array(test_ids), loss=np.array(hist))
     summary = {k: float(np.mean([r[k] for r in rows])) for k in rows[0] if k not in ("field_cm", "case")}
     summary["gamma_min_denoised"] = float(min(r["denoised_gamma"] for r in rows))

@@ -152,6 +152,7 @@ _EXPORTS = {
                                       C.c_void_p]),
     "lsm_unet_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "lsm_unet_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "lsm_unet_set_wgrad": (C.c_int, [C.c_int]),
     "lsm_gamma": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _dp, C.c_double, C.c_double,
                             C.c_double, C.c_double, C.c_int, _dp, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p]),
     "lsm_dose_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, _dp,
@@ -861,6 +862,11 @@ def lsm_upsample3d(vin: lsm_vol, vout: lsm_vol, stream=None):
 
 def lsm_unet_param_count() -> int:
     return int(load_library(require_gpu=False).lsm_unet_param_count())
+
+
+def lsm_unet_set_wgrad(tensor_cores: bool = True):
+    """Weight gradients of training on the tensor cores (default) or the CUDA cores."""
+    _check(load_library().lsm_unet_set_wgrad(int(bool(tensor_cores))), "lsm_unet_set_wgrad")
 
 
 def lsm_unet_create(params, stream=None) -> UNet:

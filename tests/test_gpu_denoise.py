@@ -217,6 +217,45 @@ def test_training_gradient_matches_oracle(L):
     np.testing.assert_allclose(g[k:], go[k:], rtol=2e-3, atol=1e-6 * np.abs(go[k:]).max())
 
 
+@pytest.mark.parametrize("shape", [(1, 16, 16, 24), (2, 24, 40, 16), (1, 64, 64, 64)])
+def test_tensor_core_weight_gradients_equal_cuda_core_ones(L, shape):
+    """The tcgen05 weight gradient (GEMM over voxels on channel-major copies)
+    against the FP32 CUDA-core one on the same training step: both multiply the
+    same BF16 values (exact in FP32) and differ only in the order of the FP32
+    sums, layer by layer. Shapes with ragged rows, two volumes, several row
+    tiles and chunk splits."""
+    import torch
+    n, d, h, w = shape
+    rng = np.random.default_rng(23)
+    dose = (rng.random(shape) * 2 + 0.1).astype(np.float32)
+    rho = (0.5 + rng.random(shape)).astype(np.float32)
+    target = (dose * (1 + 0.2 * rng.standard_normal(shape))).astype(np.float32)
+    params = DN.init_params(8, head_scale=0.1)
+    t = [torch.tensor(a, device="cuda") for a in (dose, rho, target)]
+    grads = []
+    try:
+        for tc in (False, True):
+            L.lsm_unet_set_wgrad(tc)
+            net = L.lsm_unet_create(params)
+            L.lsm_unet_train_step(net, *t, lr=0.0)
+            grads.append(L.lsm_unet_grad(net).astype(np.float64))
+    finally:
+        L.lsm_unet_set_wgrad(True)
+    g0, g1 = grads
+    convs, _ = DN.layer_shapes()
+    k = 0
+    for i, (ci, co) in enumerate(convs):
+        nw = 27 * ci * co
+        a, b = g1[k:k + nw], g0[k:k + nw]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel < 2e-5, (i, ci, co, rel)
+        # bias and head: the same kernels in both modes (FP32 atomics: order only)
+        b1, b0 = g1[k + nw:k + nw + co], g0[k + nw:k + nw + co]
+        np.testing.assert_allclose(b1, b0, rtol=1e-5, atol=1e-5 * np.abs(b0).max())
+        k += nw + co
+    np.testing.assert_allclose(g1[k:], g0[k:], rtol=1e-5, atol=1e-5 * np.abs(g0[k:]).max())
+
+
 def test_training_reduces_loss(L):
     """Adam steps on a fixed pair lower the loss: the target is a smoothed,
     rescaled copy of the input, a mapping the network can represent."""
