@@ -345,6 +345,12 @@ lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], l
  * bounds the workspace's memory, and electrons created once it is full are
  * deposited where they are created, counted in stats[9] and reported as
  * LSM_ERR_OVERFLOW (the energy balance still holds).
+ * streams: 1 (0 = 1) or 2. With 2, when an iteration holds several whole
+ * batches, its batches are split into two halves with their own particle
+ * queues, sampled and transported on two CUDA streams (the second one owned
+ * by the tally), so that one half's passes run on the SMs the other half's
+ * passes leave idle while their queues drain; the halves tally into different
+ * batch slots. Results are those of streams = 1 (the same histories).
  */
 typedef struct {
     int32_t electron_mode;
@@ -357,7 +363,7 @@ typedef struct {
     int32_t no_sync;
     int64_t first_batch;
     int32_t e_queue_cap;
-    int32_t reserved;
+    int32_t streams;
 } lsm_run_opts;
 
 /*

@@ -415,9 +415,16 @@ void lsm_tally_destroy(lsm_tally *t)
 {
     if (!t) return;
     if (t->gstream) cudaStreamSynchronize((cudaStream_t)t->gstream);
+    if (t->pstream) cudaStreamSynchronize((cudaStream_t)t->pstream);
     dev_free(t->d_part); dev_free(t->d_batch); dev_free(t->d_s1); dev_free(t->d_s2); dev_free(t->d_stats);
     dev_free(t->d_idx);
     dev_free(t->ws);
+    dev_free(t->ws2);
+    if (t->pstream) {
+        cudaStreamDestroy((cudaStream_t)t->pstream);
+        cudaEventDestroy((cudaEvent_t)t->pev[0]);
+        cudaEventDestroy((cudaEvent_t)t->pev[1]);
+    }
     if (t->gexec) cudaGraphExecDestroy((cudaGraphExec_t)t->gexec);
     timer_free(t->gtimers);
     if (t->gstream) {

@@ -38,7 +38,7 @@ struct SampleParams {
 // What a captured run graph depends on besides the seed.
 struct GraphKey {
     uint64_t psl, ph;     // creation ids of the plan and the phantom
-    const void *part, *ws, *batch;
+    const void *part, *ws, *batch, *ws2;
     lsm_run_opts o;
     int timed;            // captured with the event timers on
 };
@@ -124,6 +124,10 @@ struct lsm_tally {
     int n_batches;
     void *ws;             // cached particle queues of lsm_run / lsm_transport
     uint32_t ws_chunk, ws_ecap;
+    void *ws2;            // queues of the second half-iteration (lsm_run_opts.streams = 2)
+    uint32_t ws2_chunk, ws2_ecap;
+    void *pstream;        // its stream, and the fork and join events
+    void *pev[2];
     void *gexec;          // captured run graph (cudaGraphExec_t) and what it was captured for
     lsm::GraphKey gkey;
     int64_t graph_kernels;

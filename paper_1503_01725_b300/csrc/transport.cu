@@ -1251,25 +1251,27 @@ struct Workspace {
     void *mem;
 };
 
-// Queues live in one allocation cached on the tally and reused by later runs.
-cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t, cudaStream_t st)
+// Queues live in one allocation cached on the tally and reused by later runs
+// (a second one for the second half-iteration of two-stream runs).
+cudaError_t ws_alloc_at(Workspace &W, uint32_t chunk, uint32_t ecap, void *&mem, uint32_t &mem_chunk,
+                        uint32_t &mem_ecap, cudaStream_t st)
 {
-    if (t->ws && t->ws_chunk >= chunk && t->ws_ecap >= ecap) {
-        chunk = t->ws_chunk;
-        ecap = t->ws_ecap;
+    if (mem && mem_chunk >= chunk && mem_ecap >= ecap) {
+        chunk = mem_chunk;
+        ecap = mem_ecap;
     } else {
-        if (t->ws) cudaFreeAsync(t->ws, st);
-        t->ws = nullptr;
+        if (mem) cudaFreeAsync(mem, st);
+        mem = nullptr;
         size_t total = 1024;
         const uint32_t c2[3] = {chunk, 2 * chunk, ecap};
         for (int k = 0; k < 3; ++k) total += (size_t)c2[k] * 48 + 256;
-        cudaError_t e = dev_malloc(&t->ws, total, st);
+        cudaError_t e = dev_malloc(&mem, total, st);
         if (e != cudaSuccess) return e;
-        t->ws_chunk = chunk;
-        t->ws_ecap = ecap;
+        mem_chunk = chunk;
+        mem_ecap = ecap;
     }
     const uint32_t caps[3] = {chunk, 2 * chunk, ecap};
-    char *p = (char *)t->ws;
+    char *p = (char *)mem;
     W.mem = nullptr;
     W.cnt = (IterCounters *)p;
     W.key = (uint32_t *)(p + 768);
@@ -1281,6 +1283,11 @@ cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t, 
         p += ((size_t)caps[k] * 48 + 255) / 256 * 256;
     }
     return cudaSuccess;
+}
+
+cudaError_t ws_alloc(Workspace &W, uint32_t chunk, uint32_t ecap, lsm_tally *t, cudaStream_t st)
+{
+    return ws_alloc_at(W, chunk, ecap, t->ws, t->ws_chunk, t->ws_ecap, st);
 }
 
 // A run's secondary-electron queue capacity: the workspace's, or less when
@@ -1332,6 +1339,8 @@ lsm_status check_opts(lsm_run_opts &o)
     if (o.n_batches < 1) o.n_batches = 1;
     if (o.first_batch < 0) return set_arg_error("first_batch must be >= 0");
     if (o.e_queue_cap < 0) return set_arg_error("e_queue_cap must be >= 0");
+    if (o.streams == 0) o.streams = 1;
+    if (o.streams != 1 && o.streams != 2) return set_arg_error("streams must be 1 or 2");
     return LSM_OK;
 }
 
@@ -1617,20 +1626,53 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
     if (!gs0) gs0 = grid_for((const void *)k_sample_queue<0>, 256, 0);
     if (!gs1) gs1 = grid_for((const void *)k_sample_queue<1>, 256, 0);
     if (!gs2) gs2 = grid_for((const void *)k_sample_queue<2>, 256, 0);
-    auto iteration = [&](uint64_t g0, int64_t h0, int64_t n) -> lsm_status {
-        S.g0 = g0;
-        S.h0 = h0;
-        S.n = n;
-        LSM_CUDA(cudaMemsetAsync(W.cnt, 0, sizeof(IterCounters), st));
-        const int gs = (int)std::min<int64_t>((S.n + 255) / 256, kmode == 0 ? gs0 : (kmode == 1 ? gs1 : gs2));
-        const int tk = timer_begin(1, st);
-        if (kmode == 0) k_sample_queue<0><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
-        else if (kmode == 1) k_sample_queue<1><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
-        else k_sample_queue<2><<<gs, 256, 0, st>>>(S, T, W.q[0], W.q[2]);
+    // Two-stream runs (streams = 2, several batches per iteration): each
+    // iteration's batches are split into two halves with their own queues,
+    // sampled and transported on two streams, so that each half's passes
+    // fill the SMs the other half's passes leave idle at the end of their
+    // queues; the halves tally into different batch slots, and the slots are
+    // folded once both are done.
+    const bool two = o.streams == 2 && multi && bpi >= 2;
+    Workspace W2 = {};
+    TP T2 = T;
+    SQ S2 = S;
+    cudaStream_t s2 = nullptr;
+    if (two) {
+        const int64_t half = (int64_t)((bpi + 1) / 2) * plan;
+        e = ws_alloc_at(W2, (uint32_t)half, (uint32_t)std::min<int64_t>(4 * half + (1 << 18), 0xF0000000ll), t->ws2,
+                        t->ws2_chunk, t->ws2_ecap, st);
+        if (e != cudaSuccess) return set_cuda_error(e, "lsm_run second workspace");
+        cap_equeue(W2, o);
+        T2 = make_tp(ph, t, o, W2.key, W2.cnt);
+        S2.key = W2.key;
+        if (!t->pstream) {
+            cudaStream_t ps = nullptr;
+            LSM_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+            cudaEvent_t e1 = nullptr, e2 = nullptr;
+            LSM_CUDA(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+            LSM_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+            t->pstream = ps; t->pev[0] = e1; t->pev[1] = e2;
+        }
+        s2 = (cudaStream_t)t->pstream;
+    }
+    auto iteration_on = [&](Workspace &Wx, const TP &Tx, SQ &Sx, cudaStream_t sx, uint64_t g0, int64_t h0,
+                            int64_t n) -> lsm_status {
+        Sx.g0 = g0;
+        Sx.h0 = h0;
+        Sx.n = n;
+        LSM_CUDA(cudaMemsetAsync(Wx.cnt, 0, sizeof(IterCounters), sx));
+        const int gs = (int)std::min<int64_t>((Sx.n + 255) / 256, kmode == 0 ? gs0 : (kmode == 1 ? gs1 : gs2));
+        const int tk = timer_begin(1, sx);
+        if (kmode == 0) k_sample_queue<0><<<gs, 256, 0, sx>>>(Sx, Tx, Wx.q[0], Wx.q[2]);
+        else if (kmode == 1) k_sample_queue<1><<<gs, 256, 0, sx>>>(Sx, Tx, Wx.q[0], Wx.q[2]);
+        else k_sample_queue<2><<<gs, 256, 0, sx>>>(Sx, Tx, Wx.q[0], Wx.q[2]);
         count_launch();
-        timer_end(tk, st);
+        timer_end(tk, sx);
         LSM_CUDA(cudaGetLastError());
-        return kmode == 0 ? drain<0>(T, W, t, st) : (kmode == 1 ? drain<1>(T, W, t, st) : drain<2>(T, W, t, st));
+        return kmode == 0 ? drain<0>(Tx, Wx, t, sx) : (kmode == 1 ? drain<1>(Tx, Wx, t, sx) : drain<2>(Tx, Wx, t, sx));
+    };
+    auto iteration = [&](uint64_t g0, int64_t h0, int64_t n) -> lsm_status {
+        return iteration_on(W, T, S, st, g0, h0, n);
     };
     // the whole run's launch sequence (no host synchronisation inside)
     auto enqueue = [&]() -> lsm_status {
@@ -1638,7 +1680,20 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         if (multi) {
             for (int b0 = 0; b0 < o.n_batches && r == LSM_OK; b0 += bpi) {
                 const int k = std::min(bpi, o.n_batches - b0);
-                r = iteration((uint64_t)(o.first_batch + b0) * (uint64_t)plan, 0, (int64_t)k * plan);
+                const uint64_t g0 = (uint64_t)(o.first_batch + b0) * (uint64_t)plan;
+                if (two && k >= 2) {
+                    const int ka = (k + 1) / 2;
+                    LSM_CUDA(cudaEventRecord((cudaEvent_t)t->pev[0], st));
+                    LSM_CUDA(cudaStreamWaitEvent(s2, (cudaEvent_t)t->pev[0], 0));
+                    r = iteration_on(W, T, S, st, g0, 0, (int64_t)ka * plan);
+                    if (r == LSM_OK)
+                        r = iteration_on(W2, T2, S2, s2, g0 + (uint64_t)ka * plan, (int64_t)ka * plan,
+                                         (int64_t)(k - ka) * plan);
+                    LSM_CUDA(cudaEventRecord((cudaEvent_t)t->pev[1], s2));
+                    LSM_CUDA(cudaStreamWaitEvent(st, (cudaEvent_t)t->pev[1], 0));
+                } else {
+                    r = iteration(g0, 0, (int64_t)k * plan);
+                }
                 if (r == LSM_OK) r = fold_slots(t, k, st);
             }
         } else {
@@ -1654,6 +1709,7 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         return r;
     };
     set_key(W, t, seed, st);
+    if (two) set_key(W2, t, seed, st);
     LSM_CUDA(cudaGetLastError());
     bool replayed = false;
     if (o.use_graph) {
@@ -1677,6 +1733,7 @@ lsm_status run_plan(const lsm_psl *P, const lsm_phantom *ph, lsm_tally *t, uint6
         memset(&gk, 0, sizeof(GraphKey));
         gk.timed = timing_enabled() ? 1 : 0;
         gk.psl = P->uid; gk.ph = ph->uid; gk.part = t->d_part; gk.ws = t->ws; gk.batch = t->d_batch;
+        gk.ws2 = t->ws2;
         gk.o = o;
         gk.o.n_batches = o.n_batches;
         if (!t->gexec || memcmp(&gk, &t->gkey, sizeof(GraphKey)) != 0) {

@@ -97,21 +97,29 @@ def init_params(seed: int = 0, head_scale: float = 0.0) -> np.ndarray:
     return p
 
 
-def train(pairs, epochs: int = 12, lr: float = 1e-3, seed: int = 0, log=print, transpose: bool = False):
+def train(pairs, epochs: int = 12, lr: float = 1e-3, seed: int = 0, log=print, transpose: bool = False,
+          small_field_power: float = 0.0):
     """Adam over the training pairs: one volume per step, shuffled each epoch,
     random x/y mirroring of input and target together (and, with transpose,
     random exchange of x and y: the square fields and the ring-symmetric source
     make the transposed case a valid case up to the X/Y jaw heights),
-    cosine-decayed learning rate. Returns (network, mean loss per epoch,
-    seconds)."""
+    cosine-decayed learning rate. With small_field_power p > 0 an epoch draws
+    its cases with replacement, with probability proportional to field_cm^-p
+    (small fields, whose penumbrae are a larger part of the dose, come up more
+    often). Returns (network, mean loss per epoch, seconds)."""
     import torch
     net = lsm.lsm_unet_create(init_params(seed, head_scale=0.01))
     rng = np.random.default_rng(seed)
     steps, k, hist = epochs * len(pairs), 0, []
     t0 = time.time()
+    prob = None
+    if small_field_power > 0:
+        f = np.array([p["field_cm"] for p in pairs], dtype=np.float64) ** -small_field_power
+        prob = f / f.sum()
     for ep in range(epochs):
         losses = []
-        for i in rng.permutation(len(pairs)):
+        order = rng.permutation(len(pairs)) if prob is None else rng.choice(len(pairs), len(pairs), p=prob)
+        for i in order:
             lo, hi, rho = pairs[i]["lo"], pairs[i]["hi"], pairs[i]["rho"]
             dims = [d for d, f in ((1, rng.random() < 0.5), (2, rng.random() < 0.5)) if f]
             if dims:
@@ -166,6 +174,8 @@ def main():
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--report", default=None)
     ap.add_argument("--transpose", action="store_true", help="also exchange x and y at random in training")
+    ap.add_argument("--small-field-power", type=float, default=0.0,
+                    help="draw training cases with probability proportional to field_cm^-p")
     a = ap.parse_args()
     lsm.load_library()
     n_test = max(1, a.cases // 10)
@@ -176,11 +186,12 @@ def main():
     te = generate(test_ids, a.n_lo, a.n_hi, a.n_ref)
     t_gen = time.time() - t0
     print(f"generated {len(tr) + len(te)} pairs in {t_gen:.0f} s", flush=True)
-    net, hist, t_train = train(tr, a.epochs, a.lr, transpose=a.transpose)
+    net, hist, t_train = train(tr, a.epochs, a.lr, transpose=a.transpose, small_field_power=a.small_field_power)
     rows = evaluate(net, te)
     params = lsm.lsm_unet_params(net)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     np.savez(a.out, params=params, epochs=a.epochs, lr=a.lr, n_lo=a.n_lo, n_hi=a.n_hi, transpose=a.transpose,
+             small_field_power=a.small_field_power,
              train_cases=np.array(train_ids), test_cases=np.array(test_ids), loss=np.array(hist))
     summary = {k: float(np.mean([r[k] for r in rows])) for k in rows[0] if k not in ("field_cm", "case")}
     summary["gamma_min_denoised"] = float(min(r["denoised_gamma"] for r in rows))

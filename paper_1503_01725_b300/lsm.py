@@ -63,7 +63,7 @@ class lsm_run_opts(C.Structure):
                 ("majorant_factor", C.c_double), ("f_e", C.c_double), ("s_geo", C.c_double),
                 ("max_steps", C.c_int32), ("chunk", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("use_graph", C.c_int32), ("no_sync", C.c_int32), ("first_batch", C.c_int64),
-                ("e_queue_cap", C.c_int32), ("reserved", C.c_int32)]
+                ("e_queue_cap", C.c_int32), ("streams", C.c_int32)]
 
 
 class lsm_nnls_opts(C.Structure):
@@ -568,13 +568,15 @@ class RunOpts:
     no_sync: bool = False   # return once queued; overflows stay in the run statistics
     first_batch: int = 0    # batch index of the run's first pass (resume from a checkpoint)
     e_queue_cap: int = 0    # secondary-electron queue capacity (0: 4 chunk + 2^18)
+    streams: int = 1        # 2: an iteration's batches as two halves on two CUDA streams
 
     def struct(self) -> lsm_run_opts:
         return lsm_run_opts(electron_mode=self.electron_mode, n_batches=self.n_batches,
                             majorant_factor=self.majorant_factor, f_e=self.f_e, s_geo=self.s_geo,
                             max_steps=self.max_steps, chunk=self.chunk, ctas_per_sm=self.ctas_per_sm,
                             use_graph=int(self.use_graph), no_sync=int(self.no_sync),
-                            first_batch=int(self.first_batch), e_queue_cap=int(self.e_queue_cap))
+                            first_batch=int(self.first_batch), e_queue_cap=int(self.e_queue_cap),
+                            streams=int(self.streams))
 
 
 def lsm_transport(ph: PhantomHandle, particles: dict, n: int, seed: int, tally: Tally,

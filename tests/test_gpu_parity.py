@@ -72,6 +72,32 @@ def test_per_psr_plan_bit_exact(L):
     assert np.array_equal(L.lsm_psl_copy(g, 6), o.ent_scale)
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_two_stream_iterations_equal_one_stream(L, graph):
+    """streams = 2 splits an iteration's batches into two halves on two CUDA
+    streams: the same histories, so every integer counter equals the
+    one-stream run and the dose agrees up to the order of the FP32 tally
+    additions; with graph replay too (the capture forks and joins the second
+    stream), and an odd batch count (halves of 3 and 2)."""
+    wl = W.workload_full_10x10(400_000)
+    wl.phantom = W.water_phantom(32, 32, 32, 0.5)
+    g = L.lsm_build_psl(wl.model, wl.beams, 40_000)
+    ph = L.lsm_phantom_create(wl.phantom)
+    out = []
+    for streams in (1, 2):
+        t = L.lsm_tally_create(ph)
+        o = L.RunOpts(electron_mode=1, n_batches=5, chunk=200_000, streams=streams, use_graph=graph)
+        for rep in range(2 if graph else 1):          # second run replays the graph
+            L.lsm_tally_reset(t)
+            assert L.lsm_run(g, ph, t, 77, o) == L.LSM_OK
+        s1, s2, nb = L.lsm_tally_read(t)
+        out.append((s1, s2, nb, L.lsm_tally_ledger(t)[1]))
+    (a1, a2, an, ast), (b1, b2, bn, bst) = out
+    assert an == bn == 5 and ast == bst
+    np.testing.assert_allclose(b1, a1, rtol=2e-5, atol=1e-6 * a1.max())
+    np.testing.assert_allclose(b2, a2, rtol=5e-5, atol=1e-6 * a2.max())
+
+
 def test_model_handle_plans_equal_the_oracle(L):
     """A plan built from a model handle equals the oracle's plan of the same
     model; the commissioned handle (lsm_model_commission with per-unit
