@@ -406,7 +406,9 @@ def commissioning_block(lsm, W, reps: int = 3, n_batches: int = 16):
             "batched": {"ms": ms_b, "ms_with_plan_build": ms_b_build, "histories_per_s": hist / t_b,
                         "u_A_rel": u_b, "s_to_1pct_A": t_b * (u_b / 0.01) ** 2,
                         "launch": {"chunk": opts.chunk, "ctas_per_sm": opts.ctas_per_sm,
-                                   "cuda_graph": bool(opts.use_graph), "autotune_candidates": len(tune_rep["trials"])}},
+                                   "cuda_graph": bool(opts.use_graph), "autotune_candidates": len(tune_rep["trials"]),
+                                   "autotune_trials_ms": [[t["chunk"], int(t["use_graph"]), round(t["ms"], 2)]
+                                                          for t in tune_rep["trials"]]}},
             "plain": {"ms": ms_p, "runs": m.n_psr, "histories_per_s": hist / t_p, "u_A_rel": u_p,
                       "s_to_1pct_A": t_p * (u_p / 0.01) ** 2,
                       "how": "one per-PSR plan build and one lsm_run per PSR (300), library defaults"},
