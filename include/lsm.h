@@ -376,6 +376,10 @@ typedef struct {
  * finaliser of its parent's stream id combined with the parent's draw counter
  * and the child's slot (pair event: electron 0, positron 1, annihilation
  * photons 2 and 3), ids below 2 shifted up by 2 (0 and 1 are reserved).
+ * A photon draws one block per Woodcock flight (word 0 flight length, word 1
+ * the collision: u mu_max above mu_total is virtual, below it selects Compton,
+ * photoelectric or pair; words 2-3 a Compton event's eta and azimuth) and one
+ * more per pair event; an electron draws half a block per deflection.
  * Errors: LSM_ERR_ARG on mismatched handles; LSM_ERR_OVERFLOW when the
  * secondary-electron queue filled up (the excess electrons were deposited at
  * their creation point and counted in stats[9]).

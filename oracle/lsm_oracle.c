@@ -857,21 +857,19 @@ OR_API double or_kn_cdf(double eta, double k)
     return 0.5 * (1.0 - ie * ie) + le + ie - 1.0 + (k1 * k1 * (1.0 - ie) - 2.0 * k1 * le + eta - 1.0) / (k * k);
 }
 
-/* Compton sampling by inverting the Klein-Nishina CDF (bisection in FP64).
- * One Philox block: word 0 -> eta, word 1 -> azimuth. */
-static void kn_sample(stream_t *st, double k, double *eta_out, double *phi_out)
+/* Compton sampling by inverting the Klein-Nishina CDF (bisection in FP64):
+ * Philox word w_eta -> eta, word w_phi -> azimuth. */
+static void kn_sample(uint32_t w_eta, uint32_t w_phi, double k, double *eta_out, double *phi_out)
 {
-    uint32_t q[4];
-    draw(st, q);
     double emax = 1.0 + 2.0 * k;
-    double target = u01(q[0]) * or_kn_cdf(emax, k);
+    double target = u01(w_eta) * or_kn_cdf(emax, k);
     double lo = 1.0, hi = emax;
     for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
         double mid = 0.5 * (lo + hi);
         if (or_kn_cdf(mid, k) < target) lo = mid; else hi = mid;
     }
     *eta_out = 0.5 * (lo + hi);
-    *phi_out = 2.0 * PI_D * u01(q[1]);
+    *phi_out = 2.0 * PI_D * u01(w_phi);
 }
 
 /* One Compton event at photon energy E travelling along (u, v, w): the
@@ -880,11 +878,11 @@ static void kn_sample(stream_t *st, double k, double *eta_out, double *phi_out)
  * inverse Klein-Nishina CDF; the recoil electron (kinetic energy E - E1) moves
  * along the momentum the photon gave up, E * u_old - E1 * u_new (photon
  * momenta E / c and E1 / c, so the electron's direction is their difference). */
-static void compton_event(stream_t *st, double E, double u, double v, double w, double *E1,
+static void compton_event(uint32_t w_eta, uint32_t w_phi, double E, double u, double v, double w, double *E1,
                           double d1[3], double de[3])
 {
     double k = E / ME, eta, phi;
-    kn_sample(st, k, &eta, &phi);
+    kn_sample(w_eta, w_phi, k, &eta, &phi);
     double cost = 1.0 - (eta - 1.0) / k;
     double e1 = E / eta;
     double un = u, vn = v, wn = w;
@@ -929,6 +927,9 @@ static void photon_track(tctx *T, part_t *p)
         if (vox < 0) { T->esc += p->E; return; }
         if (p->E < E_CUT_G) { deposit(T, vox, p->E, p); return; }
         if (++steps > T->O->max_steps) { T->n_cap++; deposit(T, vox, p->E, p); return; }
+        /* one Philox block per flight: word 0 -> flight length, word 1 ->
+         * the collision (virtual, or which interaction), words 2-3 -> a
+         * Compton event's eta and azimuth */
         uint32_t r[4];
         draw(&p->rng, r);
         double mumax = majorant(T, p->E);
@@ -943,12 +944,15 @@ static void photon_track(tctx *T, part_t *p)
         double muP = mu_comp(p->E, m, 1, T->O) * rho;
         double muQ = mu_comp(p->E, m, 2, T->O) * rho;
         double mut = muC + muP + muQ;
-        if (u01(r[1]) * mumax > mut) continue;                /* virtual collision */
+        /* t is uniform on [0, mumax): above mut the collision is virtual;
+         * below it t is uniform on [0, mut) and picks the interaction with
+         * probabilities muC, muP, muQ over mut */
+        double t = u01(r[1]) * mumax;
+        if (t > mut) continue;                                /* virtual collision */
         T->n_real++;
-        double t = u01(r[2]) * mut;
         if (t <= muC) {
             double E1, d1[3], de[3];
-            compton_event(&p->rng, p->E, p->u, p->v, p->w, &E1, d1, de);
+            compton_event(r[2], r[3], p->E, p->u, p->v, p->w, &E1, d1, de);
             spawn_electron(T, p, p->E - E1, de[0], de[1], de[2], child_id(&p->rng, 0), vox);
             p->E = E1; p->u = d1[0]; p->v = d1[1]; p->w = d1[2];
         } else if (t <= muC + muP) {
@@ -1174,15 +1178,17 @@ OR_API void or_first_collision(const or_phantom *Ph, const or_opts *O, double E,
     }
 }
 
-/* Pin helper: n Compton events at energy E through the same inverse-CDF sampler;
- * out [n][2] = (E'/E, cos theta). */
+/* Pin helper: n Compton events at energy E through the same inverse-CDF sampler
+ * (words 2-3 of a fresh block, as in a flight); out [n][2] = (E'/E, cos theta). */
 OR_API void or_kn_samples(double E, uint64_t seed, int64_t n, double *out)
 {
     for (int64_t i = 0; i < n; ++i) {
         stream_t st;
         stream_init(&st, seed, (uint64_t)i, 1u);
+        uint32_t r[4];
+        draw(&st, r);
         double k = E / ME, eta, phi;
-        kn_sample(&st, k, &eta, &phi);
+        kn_sample(r[2], r[3], k, &eta, &phi);
         out[2 * i] = 1.0 / eta;
         out[2 * i + 1] = 1.0 - (eta - 1.0) / k;
     }
@@ -1213,7 +1219,8 @@ OR_API void or_electron_path(const or_phantom *Ph, const or_opts *O, double E, u
 }
 
 /* Pin helper: n Compton events of photons of energy E along d0 through the
- * transport's own event code (history i, primary transport stream); out
+ * transport's own event code (history i, primary transport stream; eta and
+ * azimuth from words 2-3 of the stream's first block, as in a flight); out
  * [n][8] = (E1, photon direction[3], electron kinetic energy, electron
  * direction[3]). */
 OR_API void or_compton_events(double E, const double d0[3], uint64_t seed, int64_t n, double *out)
@@ -1221,8 +1228,10 @@ OR_API void or_compton_events(double E, const double d0[3], uint64_t seed, int64
     for (int64_t i = 0; i < n; ++i) {
         stream_t st;
         stream_init(&st, seed, (uint64_t)i, 1u);
+        uint32_t r[4];
+        draw(&st, r);
         double E1, d1[3], de[3];
-        compton_event(&st, E, d0[0], d0[1], d0[2], &E1, d1, de);
+        compton_event(r[2], r[3], E, d0[0], d0[1], d0[2], &E1, d1, de);
         double *o = out + 8 * i;
         o[0] = E1; o[1] = d1[0]; o[2] = d1[1]; o[3] = d1[2];
         o[4] = E - E1; o[5] = de[0]; o[6] = de[1]; o[7] = de[2];

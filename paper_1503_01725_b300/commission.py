@@ -97,8 +97,12 @@ def curve(case: Case, rows: np.ndarray, name: str):
     return pos.astype(np.float32), rows[r].astype(np.float32)
 
 
-def compare_field(case: Case, field_cm: float, calc: np.ndarray, meas: np.ndarray) -> dict:
-    """Sec. 3.2 metrics of one field (fractions of the measured maximum; cm)."""
+def compare_field(case: Case, field_cm: float, calc: np.ndarray, meas: np.ndarray, calc_sig=None,
+                  meas_sig=None) -> dict:
+    """Sec. 3.2 metrics of one field (fractions of the measured maximum; cm).
+    With the batch sigmas of both doses, the depth dose also gets its noise
+    floor: the RMS difference that two exact models would show through the
+    statistical noise of the two Monte Carlo curves alone."""
     pos, c = curve(case, calc, "pdd")
     _, m = curve(case, meas, "pdd")
     dmax = float(m.max())
@@ -107,6 +111,11 @@ def compare_field(case: Case, field_cm: float, calc: np.ndarray, meas: np.ndarra
     after = lsm.lsm_curve_compare(pos, c, m, d_max, np.inf, dmax)
     out = {"pdd": {"buildup_dta_mean": bu["dta_mean"], "buildup_dta_max": bu["dta_max"],
                    "rms": after["rms"], "max": after["max"]}}
+    if calc_sig is not None and meas_sig is not None:
+        _, sc = curve(case, calc_sig, "pdd")
+        _, sm = curve(case, meas_sig, "pdd")
+        k = pos >= d_max
+        out["pdd"]["noise_rms"] = float(np.sqrt(np.mean(sc[k].astype(np.float64) ** 2 + sm[k] ** 2)) / dmax)
     for d in DEPTHS:
         w = 0.5 * field_cm * (W.SSD + d) / W.SAD
         for kind in ("inline", "crossline"):
@@ -147,8 +156,9 @@ def run(case: Case | None = None, *, n_large: float = 2e9, hist_lo: int = 20_000
     # 2. measurements of the synthetic linac
     x_true = truth_factors(m)
     m_true = lsm.lsm_model_commission(mh, x_true)
-    meas = {f: field_rows(ph, case, m_true, f, field_histories(f, n_large), seed + 100 + k)[0]
-            for k, f in enumerate(FIELDS)}
+    meas_rs = {f: field_rows(ph, case, m_true, f, field_histories(f, n_large), seed + 100 + k)
+               for k, f in enumerate(FIELDS)}
+    meas = {f: v[0] for f, v in meas_rs.items()}
     # 3. Eq. 8 on the two commissioning fields (rows beam-major, as A)
     b = np.concatenate([meas[f] for f in COMMISSION_FIELDS])
     scale = 1.0 / np.abs(b).max()
@@ -158,12 +168,14 @@ def run(case: Case | None = None, *, n_large: float = 2e9, hist_lo: int = 20_000
     t_fit = time.perf_counter() - t1
     m_com = lsm.lsm_model_commission(mh, x)
     t2 = time.perf_counter()
-    calc = {f: field_rows(ph, case, m_com, f, field_histories(f, n_large), seed + 200 + k)[0]
-            for k, f in enumerate(FIELDS)}
+    calc_rs = {f: field_rows(ph, case, m_com, f, field_histories(f, n_large), seed + 200 + k)
+               for k, f in enumerate(FIELDS)}
     torch.cuda.synchronize()
     t_val = time.perf_counter() - t2
-    ref = {f: field_rows(ph, case, mh, f, field_histories(f, n_large), seed + 300 + k)[0]
-           for k, f in enumerate(FIELDS)}
+    ref_rs = {f: field_rows(ph, case, mh, f, field_histories(f, n_large), seed + 300 + k)
+              for k, f in enumerate(FIELDS)}
+    calc = {f: v[0] for f, v in calc_rs.items()}
+    ref = {f: v[0] for f, v in ref_rs.items()}
     # 4. comparison
     # output factor: axis dose over 9-11 cm depth relative to the 10x10 field's
     r10 = case.curves["pdd"][1][np.abs(case.curves["pdd"][0] - 10.0) <= 1.0]
@@ -174,8 +186,9 @@ def run(case: Case | None = None, *, n_large: float = 2e9, hist_lo: int = 20_000
     of_meas, of_com, of_ref = of(meas), of(calc), of(ref)
     fields = {}
     for f in FIELDS:
-        fields[f"{f:g}x{f:g}"] = {"commissioned": compare_field(case, f, calc[f], meas[f]),
-                                  "reference": compare_field(case, f, ref[f], meas[f])}
+        fields[f"{f:g}x{f:g}"] = {
+            "commissioned": compare_field(case, f, calc[f], meas[f], calc_rs[f][1], meas_rs[f][1]),
+            "reference": compare_field(case, f, ref[f], meas[f], ref_rs[f][1], meas_rs[f][1])}
     return {
         "x": x, "x_true": x_true, "nnls": rep, "model_handle": m_com,
         "model": m.with_weights(lsm.lsm_model_weights(m_com)),
@@ -217,6 +230,8 @@ def summary(rep: dict) -> dict:
                       "inline10_inner_max_pct": rng("inline@10", "inner_max", which),
                       "inline10_penumbra_dta_mean_cm": rng("inline@10", "penumbra_dta_mean", which),
                       "inline10_outer_rms_pct": rng("inline@10", "outer_rms", which)}
+        if all("noise_rms" in rep["fields"][f][which]["pdd"] for f in rep["fields"]):
+            out[which]["pdd_noise_floor_pct"] = rng("pdd", "noise_rms", which)
     return out
 
 

@@ -89,9 +89,8 @@ struct Stream {
 };
 
 // --------------------------------------------------------- particle queue ---
-// SoA queue of particles waiting for transport, phantom-local coordinates
-// (x - x0, y - y0, z - z0). pb = psr | beam << 16.
-// A particle queue: three 16-byte words per particle, (x, y, z, E),
+// Queue of particles waiting for transport, phantom-local coordinates
+// (x - x0, y - y0, z - z0): three 16-byte words per particle, (x, y, z, E),
 // (u, v, w, stream id bits), (history lo, history hi, PSR | beam << 16 |
 // slot << 20, unused), so that a particle moves as one 48-byte record.
 struct Queue {

@@ -365,8 +365,10 @@ __device__ __forceinline__ void spawn_electron(const TP &T, Acc &A, const Queue 
     store_part(eq, slot, p.x, p.y, p.z, u, v, w, Te, p.rng.glo, p.rng.ghi, sid, p.pb);
 }
 
-// One Woodcock flight (and the interaction if the collision is real).
-// Returns false when the photon's history ends.
+// One Woodcock flight (and the interaction if the collision is real), on one
+// Philox block: word 0 -> flight length, word 1 -> the collision (virtual, or
+// which interaction), words 2-3 -> a Compton event's eta and azimuth; a pair
+// event draws one more block. Returns false when the photon's history ends.
 template <int MODE>
 __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t, Acc &A, Part &p,
                             const Queue &eq, const Queue *pq, Pend &pe, bool &pend)
@@ -384,28 +386,29 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
     A.flights++;
     vox = voxel(T, p.x, p.y, p.z);
-    const float rm = vox >= 0 ? __ldg(T.rhomat + vox) : 0.0f;
-    // the block of the next draw (next flight or the Compton block) does not
+    if (vox < 0) { A.esc += p.E; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
+    const float rm = __ldg(T.rhomat + vox);
+    // the block of the next draw (next flight, or a pair event's) does not
     // depend on the density: compute it while the load is in flight
     p.rng.prefetch();
-    if (vox < 0) { A.esc += p.E; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
     const int m = rm < 0.0f;
     const float rho = fabsf(rm);
     const float4 c = lerp4(xs + m * kGrid, ti, tf);
     const float muC = c.x * rho, muP = c.y * rho, muQ = c.z * rho;
     const float mut = muC + muP + muQ;
-    if (u01(r.y) * mm > mut) return true;                       // virtual collision
+    // t is uniform on [0, mm): above mut the collision is virtual, below it t
+    // is uniform on [0, mut) and picks the interaction
+    const float t = u01(r.y) * mm;
+    if (t > mut) return true;                                   // virtual collision
     A.real++;
-    const float t = u01(r.z) * mut;
     if (t <= muC) {
-        // Compton: one block, word 0 -> E'/E by the inverse Klein-Nishina CDF, word 1 -> azimuth
-        const uint4 q = p.rng.next();
+        // Compton: word 2 -> E'/E by the inverse Klein-Nishina CDF, word 3 -> azimuth
         const float k = p.E * (1.0f / kMe);
-        const float vkn = kn_inverse(mumax_t + kGrid, p.E, u01(q.x));
+        const float vkn = kn_inverse(mumax_t + kGrid, p.E, u01(r.z));
         const float eta = 1.0f + 2.0f * k * vkn;
         const float cost = 1.0f - 2.0f * vkn;
         const float E1 = __fdividef(p.E, eta);
-        const float uphi = u01(q.y);
+        const float uphi = u01(r.w);
         float u = p.u, v = p.v, w = p.w;
         rotate(u, v, w, cost, uphi);
         float ex = p.E * p.u - E1 * u, ey = p.E * p.v - E1 * v, ez = p.E * p.w - E1 * w;
