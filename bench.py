@@ -544,15 +544,17 @@ def multibeam_block(lsm, W, opts, n_hist: int = 10_000_000, n_batches: int = 16,
         for r in range(3):
             step(100 + r)
         lsm.lsm_timing_read(reset=True)
-        ms = []
+        evs, plans = [], []
+        torch.cuda.synchronize()
         for r in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
             a.record(stream)
-            psl = step(200 + r)
+            plans.append(step(200 + r))
             b.record(stream)
-            torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        psl = plans[-1]
         tm = lsm.lsm_timing_read(reset=True)
         led, st = lsm.lsm_tally_ledger(tally)
         d, sg = lsm.lsm_dose(tally, ph, psl.denom / n_plan)
@@ -587,16 +589,20 @@ def _timed_steps(lsm, wl, opts, n_plan: int, reps: int, seed0: int, model_h=None
         step(seed0 + r)
     torch.cuda.synchronize()
     lsm.lsm_timing_read(reset=True)
-    ms = []
+    # steps queued back to back, each timed by its own events (L2 flush between
+    # them, outside the events), as in the headline loop
+    evs, plans = [], []
+    torch.cuda.synchronize()
     for r in range(reps):
         flush.fill_(r & 0xFF)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
         a.record(stream)
-        psl = step(seed0 + 10 + r)
+        plans.append(step(seed0 + 10 + r))
         b.record(stream)
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    psl = plans[-1]
     tm = lsm.lsm_timing_read(reset=True)
     led, st = lsm.lsm_tally_ledger(tally)
     d, sg = lsm.lsm_dose(tally, ph, psl.denom / n_plan)
@@ -981,22 +987,26 @@ def main():
     lsm.lsm_timing_read(reset=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = lsm.lsm_launch_count()
-    ms_steps = []
-    u_vals = []
-    if True:
-        torch.cuda.synchronize()
-        tw0 = time.time()
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)                      # L2 flush outside the timed events
-            ev[i][0].record(stream)
-            res = step(i)
-            ev[i][1].record(stream)
-            _, d, s = res          # the previous step's plan is released after the end event
-            torch.cuda.synchronize()
-            ms_steps.append(ev[i][0].elapsed_time(ev[i][1]))
-            u_vals.append(u_mean_rel(d.cpu().numpy(), s.cpu().numpy()))
-        clk.window(tw0, time.time())
-        clk.stop()
+    # The steps are queued back to back, as a stream of dose calculations
+    # runs: the host does not wait for one step before queueing the next, so
+    # its calls overlap the previous step's device work instead of delaying
+    # the step's first kernels. Each step's device time is taken by its own
+    # pair of events; the L2 flush between steps lies outside them. Plans and
+    # doses are kept until the last step has run.
+    keep = []
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)                      # L2 flush outside the timed events
+        ev[i][0].record(stream)
+        keep.append(step(i))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk.window(tw0, time.time())
+    clk.stop()
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    u_vals = [u_mean_rel(d.cpu().numpy(), s.cpu().numpy()) for _, d, s in keep]
+    del keep
     print("per-step ms: " + " ".join(f"{v:.3f}" for v in ms_steps), file=sys.stderr)
     launches = lsm.lsm_launch_count() - launches0
     timers = lsm.lsm_timing_read(reset=True)

@@ -200,8 +200,25 @@ __device__ __forceinline__ float kn_inverse(const float *__restrict__ kn, float 
     return lo + f * (hi - lo);
 }
 
+// Compensated FP32 sum (Kahan): the running error of each addition is kept
+// in c and subtracted from the next term, so that a thread's sum of a few
+// hundred energies stays within a few FP32 roundings of the exact sum. It
+// replaces FP64 accumulation in the particle loops, where every FP64
+// conversion and add occupies the B300's narrow FP64 pipe for a warp.
+struct KSum {
+    float s, c;
+};
+__device__ __forceinline__ void kadd(KSum &k, float x)
+{
+    const float y = x - k.c;
+    const float t = k.s + y;
+    k.c = (t - k.s) - y;
+    k.s = t;
+}
+__device__ __forceinline__ double kval(const KSum &k) { return (double)k.s - (double)k.c; }
+
 struct Acc {
-    double esc, dep;
+    KSum esc, dep;     // escaped energy; deposits of ended particles
     float dep32;       // deposits of the current particle, folded into dep when it ends
     unsigned long long flights, real, esteps, cap;
 };
@@ -374,7 +391,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
                             const Queue &eq, const Queue *pq, Pend &pe, bool &pend)
 {
     int vox = voxel(T, p.x, p.y, p.z);
-    if (vox < 0) { A.esc += p.E; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
+    if (vox < 0) { kadd(A.esc, p.E); hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
     if (p.E < kCutG) { deposit<MODE, true>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
     if (++p.steps > T.max_steps) { A.cap++; deposit<MODE, true>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
     const uint4 r = p.rng.next();
@@ -386,7 +403,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
     A.flights++;
     vox = voxel(T, p.x, p.y, p.z);
-    if (vox < 0) { A.esc += p.E; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
+    if (vox < 0) { kadd(A.esc, p.E); hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
     const float rm = __ldg(T.rhomat + vox);
     // the block of the next draw (next flight, or a pair event's) does not
     // depend on the density: compute it while the load is in flight
@@ -485,7 +502,7 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p, co
 {
     // (reusing the previous step's end voxel here measured 1.6x slower)
     const int vox = voxel(T, p.x, p.y, p.z);
-    if (vox < 0) { eflush<MODE>(T, A, p); A.esc += p.E; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
+    if (vox < 0) { eflush<MODE>(T, A, p); kadd(A.esc, p.E); hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
     if (p.E < kCutE) { edep<MODE>(T, A, p, vox, p.E); eflush<MODE>(T, A, p); return false; }
     if (++p.steps > T.max_steps) {
         A.cap++;
@@ -511,7 +528,7 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p, co
     const float hs = 0.5f * ds;
     const int vm = voxel(T, p.x + hs * p.u, p.y + hs * p.v, p.z + hs * p.w);
     if (vm >= 0) edep<MODE>(T, A, p, vm, dE);
-    else { A.esc += dE; hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, dE); }
+    else { kadd(A.esc, dE); hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, dE); }
     A.esteps++;
     const float E0 = p.E;
     p.x += ds * p.u; p.y += ds * p.v; p.z += ds * p.w;
@@ -557,7 +574,7 @@ __device__ bool electron_step(const TP &T, const float4 *xs, Acc &A, Part &p, co
 
 __device__ void flush_acc(const TP &T, const Acc &A)
 {
-    const double esc = warp_sum(A.esc), dep = warp_sum(A.dep + (double)A.dep32);
+    const double esc = warp_sum(kval(A.esc)), dep = warp_sum(kval(A.dep) + (double)A.dep32);
     const unsigned long long fl = warp_sum_u64(A.flights), re = warp_sum_u64(A.real),
                              es = warp_sum_u64(A.esteps), cp = warp_sum_u64(A.cap);
     if (lane_id() == 0) {
@@ -593,7 +610,7 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
     const unsigned lane = lane_id();
     unsigned lt;
     lanemask_lt(lt);
-    Acc A = {0.0, 0.0, 0.0f, 0ull, 0ull, 0ull, 0ull};
+    Acc A = {{0.0f, 0.0f}, {0.0f, 0.0f}, 0.0f, 0ull, 0ull, 0ull, 0ull};
     Part p;
     bool alive = false;
     // Each warp reserves kGrab consecutive queue slots per atomic and hands
@@ -663,7 +680,7 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
                 bool used = false;
                 alive = electron_step<MODE>(T, xs, A, p, blk, used);
                 if (alive) alive = electron_step<MODE>(T, xs, A, p, blk, used);
-                if (!alive) { A.dep += A.dep32; A.dep32 = 0.0f; }
+                if (!alive) { kadd(A.dep, A.dep32); A.dep32 = 0.0f; }
             }
         } else {
             bool pend = false;
@@ -671,7 +688,7 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
             const uint32_t pb_keep = p.pb;
             if (alive) {
                 alive = photon_step<MODE>(T, xs, mm, A, p, eq, has_pq ? &pq : nullptr, pe, pend);
-                if (!alive) { A.dep += A.dep32; A.dep32 = 0.0f; }
+                if (!alive) { kadd(A.dep, A.dep32); A.dep32 = 0.0f; }
             }
             // warp-wide push of the electrons created in this step
             const unsigned pm = __ballot_sync(0xffffffffu, pend);
@@ -693,7 +710,7 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
                     } else {
                         atomicAdd(&T.stats->c[9], 1ull);
                         deposit<MODE, true>(T, A, pe.vox, pe.E, pb_keep, p.rng.glo, p.rng.ghi);
-                        A.dep += A.dep32;
+                        kadd(A.dep, A.dep32);
                         A.dep32 = 0.0f;
                     }
                 }
@@ -781,8 +798,10 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
     lanemask_lt(lt);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // source, rejected and missed energy per thread in FP64: the source
+    // energy is the same sum, to FP64 rounding, however the run is split
     double src = 0.0, rej = 0.0, esc = 0.0;
-    Acc A = {0.0, 0.0, 0.0f, 0ull, 0ull, 0ull, 0ull};
+    Acc A = {{0.0f, 0.0f}, {0.0f, 0.0f}, 0.0f, 0ull, 0ull, 0ull, 0ull};
     unsigned long long nph = 0, nel = 0, nrej = 0, nmiss = 0;
     for (int64_t base = warp * 32; base < S.n; base += nwarps * 32) {
         const int64_t i = base + lane;
@@ -843,13 +862,13 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
             }
         }
     }
-    src = warp_sum(src); rej = warp_sum(rej); esc = warp_sum(esc);
-    const double dep = warp_sum(A.dep + (double)A.dep32);
+    const double src_d = warp_sum(src), rej_d = warp_sum(rej), esc_d = warp_sum(esc);
+    const double dep = warp_sum(kval(A.dep) + (double)A.dep32);
     nph = warp_sum_u64(nph); nel = warp_sum_u64(nel); nrej = warp_sum_u64(nrej); nmiss = warp_sum_u64(nmiss);
     if (lane == 0) {
-        atomicAdd(&T.stats->ledger[0], src);
-        if (rej != 0.0) atomicAdd(&T.stats->ledger[1], rej);
-        if (esc != 0.0) atomicAdd(&T.stats->ledger[2], esc);
+        atomicAdd(&T.stats->ledger[0], src_d);
+        if (rej_d != 0.0) atomicAdd(&T.stats->ledger[1], rej_d);
+        if (esc_d != 0.0) atomicAdd(&T.stats->ledger[2], esc_d);
         if (dep != 0.0) atomicAdd(&T.stats->ledger[3], dep);
         if (nph) atomicAdd(&T.stats->c[1], nph);
         if (nel) atomicAdd(&T.stats->c[2], nel);
@@ -896,7 +915,7 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double esc = 0.0;
-    Acc A = {0.0, 0.0, 0.0f, 0ull, 0ull, 0ull, 0ull};
+    Acc A = {{0.0f, 0.0f}, {0.0f, 0.0f}, 0.0f, 0ull, 0ull, 0ull, 0ull};
     unsigned long long nph = 0, nel = 0, nmiss = 0;
     for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
         const int64_t i = base + lane;
@@ -937,7 +956,7 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
         }
     }
     esc = warp_sum(esc);
-    const double dep = warp_sum(A.dep + (double)A.dep32);
+    const double dep = warp_sum(kval(A.dep) + (double)A.dep32);
     nph = warp_sum_u64(nph); nel = warp_sum_u64(nel); nmiss = warp_sum_u64(nmiss);
     if (lane == 0) {
         if (esc != 0.0) atomicAdd(&T.stats->ledger[2], esc);
@@ -974,8 +993,10 @@ __global__ void __launch_bounds__(256) k_pslfile_enqueue(const PslRec *__restric
     lanemask_lt(lt);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // source, rejected and missed energy per thread in FP64: the source
+    // energy is the same sum, to FP64 rounding, however the run is split
     double src = 0.0, rej = 0.0, esc = 0.0;
-    Acc A = {0.0, 0.0, 0.0f, 0ull, 0ull, 0ull, 0ull};
+    Acc A = {{0.0f, 0.0f}, {0.0f, 0.0f}, 0.0f, 0ull, 0ull, 0ull, 0ull};
     unsigned long long nph = 0, nel = 0, nrej = 0, nmiss = 0;
     for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
         const int64_t i = base + lane;
@@ -1030,13 +1051,13 @@ __global__ void __launch_bounds__(256) k_pslfile_enqueue(const PslRec *__restric
             }
         }
     }
-    src = warp_sum(src); rej = warp_sum(rej); esc = warp_sum(esc);
-    const double dep = warp_sum(A.dep + (double)A.dep32);
+    const double src_d = warp_sum(src), rej_d = warp_sum(rej), esc_d = warp_sum(esc);
+    const double dep = warp_sum(kval(A.dep) + (double)A.dep32);
     nph = warp_sum_u64(nph); nel = warp_sum_u64(nel); nrej = warp_sum_u64(nrej); nmiss = warp_sum_u64(nmiss);
     if (lane == 0) {
-        atomicAdd(&T.stats->ledger[0], src);
-        if (rej != 0.0) atomicAdd(&T.stats->ledger[1], rej);
-        if (esc != 0.0) atomicAdd(&T.stats->ledger[2], esc);
+        atomicAdd(&T.stats->ledger[0], src_d);
+        if (rej_d != 0.0) atomicAdd(&T.stats->ledger[1], rej_d);
+        if (esc_d != 0.0) atomicAdd(&T.stats->ledger[2], esc_d);
         if (dep != 0.0) atomicAdd(&T.stats->ledger[3], dep);
         if (nph) atomicAdd(&T.stats->c[1], nph);
         if (nel) atomicAdd(&T.stats->c[2], nel);
