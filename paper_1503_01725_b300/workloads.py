@@ -397,16 +397,23 @@ def workload_denoise(case: int, n_hist: int = 1_000_000) -> Workload:
     """Denoiser pair `case`: a 128^3 phantom at 0.25 cm (a quarter of the cases
     plain water, the rest water with seeded slabs and spheres), one square field
     of 4-20 cm, the three-sub-source model with rings to 3.2 cm. The pair is
-    this workload run with n_hist = 1e6 (input) and 1e8 (target)."""
-    rng = np.random.default_rng(5000 + case)
-    field_cm = float(rng.uniform(4.0, 20.0))
+    this workload run with n_hist = 1e6 (input) and 1e8 (target).
+    Training cases (DENOISE_TRAIN) draw the field log-uniformly, i.e. as many
+    4-5 cm fields as 16-20 cm ones: a small field's dose region is a small part
+    of its volume and of the training loss, and with uniform fields the
+    smallest ones were the held-out failures. Held-out cases (DENOISE_TEST)
+    draw it uniformly."""
+    train = case in DENOISE_TRAIN
+    rng = np.random.default_rng((25000 if train else 5000) + case)
+    u = float(rng.uniform(0.0, 1.0)) if train else 0.0
+    field_cm = 4.0 * 5.0 ** u if train else float(rng.uniform(4.0, 20.0))
     if rng.random() < 0.25:
         ph = water_phantom(128, 128, 128, 0.25)
     else:
-        ph = heterogeneous_phantom(128, 128, 128, 0.25, seed=7000 + case, n_slabs=int(rng.integers(0, 5)),
-                                   n_spheres=int(rng.integers(2, 13)))
+        ph = heterogeneous_phantom(128, 128, 128, 0.25, seed=(27000 if train else 7000) + case,
+                                   n_slabs=int(rng.integers(0, 5)), n_spheres=int(rng.integers(2, 13)))
     return Workload(f"denoise-{case}", psr_model(10, 10, 0.32, seed=3), beams(square_field(field_cm)), ph,
-                    n_hist, 1, 9000 + case, extra={"field_cm": field_cm})
+                    n_hist, 1, (29000 if train else 9000) + case, extra={"field_cm": field_cm})
 
 
 def pslfile_records(seed: int, n_xy: int = 20, dr: float = 0.25, n_e: int = 10, mean_per_cell: float = 40.0,
