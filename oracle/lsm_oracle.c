@@ -315,6 +315,28 @@ static void ent_alloc(or_plan *P, int64_t n)
     P->ent_scale = (double *)calloc(m, 8);
 }
 
+/* The plan's sums over the PSLs of a block (step 4's raw total, Eq. 3's
+ * partial denominators, a basis run's denominator) in one fixed order, so
+ * that any implementation reproduces them bit for bit: 32 interleaved
+ * partial sums, partial l adding x[l], x[l + 32], x[l + 64], ... in index
+ * order from 0.0, then combined by halving, partial l += partial l + h for
+ * h = 16, 8, 4, 2, 1; the result is partial 0. With a mask, excluded
+ * elements contribute +0.0 (which leaves a sum of non-negative terms
+ * unchanged). The paper fixes no order; a sequential sum of 400 FP64 terms
+ * is a chain of 400 dependent adds, this one a chain of 18. */
+OR_API double or_sum32(const double *x, const uint8_t *mask, int64_t n)
+{
+    double t[32];
+    for (int l = 0; l < 32; ++l) {
+        double a = 0.0;
+        for (int64_t j = l; j < n; j += 32) a += (mask && !mask[j]) ? 0.0 : x[j];
+        t[l] = a;
+    }
+    for (int h = 16; h >= 1; h >>= 1)
+        for (int l = 0; l < h; ++l) t[l] = t[l] + t[l + h];
+    return t[0];
+}
+
 /*
  * Build the PSL representation and the sampling plan.
  *   per_psr_n == NULL: whole-source plan, n_hist histories shared by Eq. 3 over
@@ -344,7 +366,6 @@ OR_API void *or_plan_build(const or_model *M, const or_beams *B, int64_t n_hist,
     double p = M->dr;
 
     /* Sec. 2.1.1 steps 1-3 per PSL centre; step 4 per (sub-source, energy) block */
-    double *rawi = (double *)calloc(npsl, 8);   /* interpolation density / (2 pi r) without W */
     for (int s = 0; s < 3; ++s)
         for (int e = 0; e < ne; ++e) {
             const double *W = &M->w[((size_t)s * ne + e) * nr];
@@ -364,18 +385,17 @@ OR_API void *or_plan_build(const or_model *M, const or_beams *B, int64_t n_hist,
                     }
                     double raw = dens / (2.0 * PI_D * r);           /* step 3 */
                     out[iy * nxy + ix] = raw;
-                    sraw += raw;
                     if (s == 0 && e == 0) {
                         P->tag_r0[iy * nxy + ix] = r0;
                         P->tag_l0[iy * nxy + ix] = in ? l0 : 0.0;
                     }
                 }
+            sraw = or_sum32(out, NULL, (int64_t)npsl);
             double sR = 0.0;
             for (int R = 0; R < nr; ++R) sR += W[R];
             double scale = sraw > 0.0 ? sR / sraw : 0.0;           /* step 4 */
             for (size_t j = 0; j < npsl; ++j) out[j] = out[j] * scale;
         }
-    free(rawi);
 
     /* sampling areas and PSL inclusion (positive-area overlap) */
     for (int b = 0; b < nb; ++b) {
@@ -402,10 +422,7 @@ OR_API void *or_plan_build(const or_model *M, const or_beams *B, int64_t n_hist,
                 for (int e = 0; e < ne; ++e) {
                     const uint8_t *inc = &P->incl[((size_t)(b * 2 + (s ? 1 : 0))) * npsl];
                     const double *W = &P->wpsl[((size_t)s * ne + e) * npsl];
-                    double part = 0.0;
-                    for (size_t j = 0; j < npsl; ++j)
-                        if (inc[j]) part += W[j];
-                    D += part;
+                    D += or_sum32(W, inc, (int64_t)npsl);
                 }
         P->denom = D;
         size_t ncnt = (size_t)nb * 3 * ne * npsl;
@@ -455,6 +472,7 @@ OR_API void *or_plan_build(const or_model *M, const or_beams *B, int64_t n_hist,
         double *q = (double *)calloc(npsl, 8);
         int64_t *c1 = (int64_t *)calloc(npsl, 8);
         double *wk = (double *)calloc(npsl, 8);
+        double *rawk = (double *)calloc(npsl, 8);
         int64_t total = 0;
         for (int k = 0; k < npsr; ++k) {
             int s = k / (ne * nr), e = (k / nr) % ne, R = k % nr;
@@ -474,17 +492,16 @@ OR_API void *or_plan_build(const or_model *M, const or_beams *B, int64_t n_hist,
                         if (r0 == R) dk = l0 * (W[R] / M->dr);
                         else if (r0 + 1 == R && l0 < 1.0) dk = (1.0 - l0) * (W[R] / M->dr);
                     }
-                    sraw += dens / (2.0 * PI_D * r);
+                    rawk[iy * nxy + ix] = dens / (2.0 * PI_D * r);
                     wk[iy * nxy + ix] = dk / (2.0 * PI_D * r);
                 }
+            sraw = or_sum32(rawk, NULL, (int64_t)npsl);
             for (int RR = 0; RR < nr; ++RR) sR += W[RR];
             double scale = sraw > 0.0 ? sR / sraw : 0.0;
             for (size_t j = 0; j < npsl; ++j) wk[j] = wk[j] * scale;
             for (int b = 0; b < nb; ++b) {
                 const uint8_t *inc = &P->incl[((size_t)(b * 2 + (s ? 1 : 0))) * npsl];
-                double D = 0.0;
-                for (size_t j = 0; j < npsl; ++j)
-                    if (inc[j]) D += wk[j];
+                const double D = or_sum32(wk, inc, (int64_t)npsl);
                 dkb[(size_t)k * nb + b] = D;
                 for (size_t j = 0; j < npsl; ++j)
                     q[j] = (inc[j] && D > 0.0) ? ((double)per_psr_n[k] * wk[j]) / D : 0.0;
@@ -513,7 +530,7 @@ OR_API void *or_plan_build(const or_model *M, const or_beams *B, int64_t n_hist,
         P->n_ent = kk;
         P->n_hist = acc;
         P->count = cnt_all;   /* [npsr][n_beams][n_xy][n_xy] */
-        free(dkb); free(q); free(c1); free(wk);
+        free(dkb); free(q); free(c1); free(wk); free(rawk);
     }
     return P;
 }

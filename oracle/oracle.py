@@ -105,6 +105,8 @@ def load(path: str):
     L.or_first_collision.argtypes = [C.POINTER(_Phantom), C.POINTER(_Opts), C.c_double,
                                      C.c_uint64, C.c_int64, _dp]
     L.or_kn_samples.argtypes = [C.c_double, C.c_uint64, C.c_int64, _dp]
+    L.or_sum32.restype = C.c_double
+    L.or_sum32.argtypes = [_dp, C.c_void_p, C.c_int64]
     L.or_electron_path.argtypes = [C.POINTER(_Phantom), C.POINTER(_Opts), C.c_double,
                                    C.c_uint64, _dp]
     L.or_compton_events.argtypes = [C.c_double, _dp, C.c_uint64, C.c_int64, _dp]
@@ -306,6 +308,13 @@ def first_collision(phantom, E: float, seed: int, n: int, **opts) -> np.ndarray:
     d = np.zeros(n)
     lib().or_first_collision(C.byref(ps), C.byref(os_), E, seed, n, _ptr(d))
     return d
+
+
+def sum32(x, mask=None) -> float:
+    """The plan's fixed-order sum over a block's PSLs (or_sum32)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    return float(lib().or_sum32(_ptr(x), None if m is None else m.ctypes.data, len(x)))
 
 
 def kn_samples(E: float, seed: int, n: int) -> np.ndarray:

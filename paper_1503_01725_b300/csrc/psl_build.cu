@@ -5,9 +5,10 @@
 //
 // Everything here is FP64 and this translation unit is compiled with
 // -fmad=false: each per-PSL value is the correctly rounded result of one fixed
-// sequence of IEEE operations, and every sum runs sequentially in loop order,
-// so the integer counts that Eq. 3 produces do not depend on thread
-// scheduling. The integerisation is largest-remainder (Hamilton) with ties to
+// sequence of IEEE operations, and every sum runs in one fixed order (sums
+// over a block's PSLs in the 32-way order of warp_sum32, the others
+// sequentially in loop order), so the integer counts that Eq. 3 produces do
+// not depend on thread scheduling. The integerisation is largest-remainder (Hamilton) with ties to
 // the lower loop index; integer sums use 64-bit atomics (exact, any order).
 #include <math.h>
 #include <stdlib.h>
@@ -92,6 +93,25 @@ __device__ __forceinline__ void incl_cell(const Geom &G, int n_r, double p, int6
     incl[i] = (uint8_t)(xh > a[0] && xl < a[1] && yh > a[2] && yl < a[3]);
 }
 
+// The plan's sums over the PSLs of a block (step 4's raw total, Eq. 3's
+// partial denominators, a basis run's denominator) in one fixed order, the
+// oracle's or_sum32: lane l of one warp adds x[l], x[l + 32], ... in index
+// order from 0.0, then an xor butterfly over the lanes (offsets 16, 8, 4, 2,
+// 1; both lanes of a pair form the same IEEE sum, so lane 0 ends with the
+// halving order). Excluded elements (mask 0) contribute +0.0. All 32 lanes
+// call it; lane 0's result is the sum in that order (the other lanes hold
+// the same terms added in other orders). A sequential FP64 sum of a block's
+// 400 PSLs was a chain of 400 dependent adds on the B300's narrow FP64
+// pipe: the plan build 0.109 -> 0.080 ms.
+__device__ __forceinline__ double warp_sum32(const double *x, const uint8_t *mask, int n)
+{
+    const int lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (int j = lane; j < n; j += 32) a += (mask && !mask[j]) ? 0.0 : x[j];
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
 // Steps 1-4 per (sub-source, energy bin) block: one CTA per block.
 __device__ __forceinline__ void psl_weights_block(int blk, const double *__restrict__ w, int n_e, int n_r, double dr,
                                                   double *__restrict__ wpsl, double *__restrict__ block_scale,
@@ -121,12 +141,14 @@ __device__ __forceinline__ void psl_weights_block(int blk, const double *__restr
     }
     __syncthreads();
     __shared__ double s_scale;
-    if (threadIdx.x == 0) {                                              // step 4
-        double sraw = 0.0, sR = 0.0;
-        for (int j = 0; j < npsl; ++j) sraw += sraw_v[j];
-        for (int R = 0; R < n_r; ++R) sR += W[R];
-        s_scale = sraw > 0.0 ? sR / sraw : 0.0;
-        block_scale[blk] = s_scale;
+    if (threadIdx.x < 32) {                                              // step 4
+        const double sraw = warp_sum32(sraw_v, nullptr, npsl);
+        if (threadIdx.x == 0) {
+            double sR = 0.0;
+            for (int R = 0; R < n_r; ++R) sR += W[R];
+            s_scale = sraw > 0.0 ? sR / sraw : 0.0;
+            block_scale[blk] = s_scale;
+        }
     }
     __syncthreads();
     const double sc = s_scale;
@@ -184,8 +206,8 @@ __global__ void k_setup(SetupArgs A)
 
 // ------------------------------------------------ whole-source plan (Eq. 3) --
 
-// partial sum of included weights per (beam, sub-source, energy), sequential
-// in PSL order; one CTA per block stages the values through shared memory
+// partial sum of included weights per (beam, sub-source, energy) in the
+// warp_sum32 order; one CTA per block stages the values through shared memory
 __global__ void k_eq3_parts(const double *__restrict__ wpsl, const uint8_t *__restrict__ incl,
                             int n_beams, int n_e, int npsl, double *__restrict__ parts)
 {
@@ -194,13 +216,11 @@ __global__ void k_eq3_parts(const double *__restrict__ wpsl, const uint8_t *__re
     const int b = i / (3 * n_e), s = (i / n_e) % 3, e = i % n_e;
     const uint8_t *inc = incl + (size_t)(b * 2 + (s ? 1 : 0)) * npsl;
     const double *W = wpsl + ((size_t)s * n_e + e) * npsl;
-    // excluded PSLs contribute +0.0, which leaves a sum of non-negative terms unchanged
-    for (int j = threadIdx.x; j < npsl; j += blockDim.x) sv[j] = inc[j] ? W[j] : 0.0;
+    for (int j = threadIdx.x; j < npsl; j += blockDim.x) sv[j] = W[j];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double part = 0.0;
-        for (int j = 0; j < npsl; ++j) part += sv[j];
-        parts[i] = part;
+    if (threadIdx.x < 32) {
+        const double part = warp_sum32(sv, inc, npsl);
+        if (threadIdx.x == 0) parts[i] = part;
     }
 }
 
@@ -403,12 +423,12 @@ __global__ void k_psr_counts(const double *__restrict__ w, const double *__restr
         q[j] = (dk / (2.0 * kPiD * r)) * scale;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double D = 0.0;
-        for (int j = 0; j < npsl; ++j)
-            if (inc[j]) D += q[j];
-        s_D = D;
-        dkb[kb] = D;
+    if (threadIdx.x < 32) {
+        const double D = warp_sum32(q, inc, npsl);
+        if (threadIdx.x == 0) {
+            s_D = D;
+            dkb[kb] = D;
+        }
     }
     __syncthreads();
     const double D = s_D;

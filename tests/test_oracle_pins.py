@@ -724,3 +724,22 @@ def test_noiseless_recovery():
     xt[[3, 17]] = 0.0
     x, _ = N.lawson_hanson(A, A @ xt)
     np.testing.assert_allclose(x, xt, atol=1e-8)
+
+
+@pytest.mark.parametrize("n", [1, 7, 31, 32, 33, 400, 1600, 5000])
+def test_plan_block_sum_is_a_sum(n):
+    """The plan's fixed-order block sum (or_sum32) against the correctly
+    rounded sum (math.fsum): within the worst-case bound of a sum whose
+    longest chain of additions is n/32 + 5 deep; exact on integer-valued
+    terms (every partial sum is representable); masked terms count as zero."""
+    import math
+    rng = np.random.default_rng(n)
+    x = rng.random(n) * np.exp(rng.normal(0.0, 3.0, n))
+    got, want = O.sum32(x), math.fsum(x)
+    depth = -(-n // 32) + 5
+    assert abs(got - want) <= depth * 2.0 ** -53 * math.fsum(np.abs(x)) + 1e-300
+    xi = rng.integers(0, 1 << 40, n).astype(np.float64)
+    assert O.sum32(xi) == math.fsum(xi)
+    mask = rng.random(n) < 0.5
+    assert O.sum32(xi, mask) == math.fsum(xi[mask])
+    assert O.sum32(x, np.zeros(n, dtype=bool)) == 0.0
