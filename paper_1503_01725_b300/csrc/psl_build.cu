@@ -121,6 +121,11 @@ __device__ __forceinline__ void psl_weights_block(int blk, const double *__restr
     const double *W = w + (size_t)blk * n_r;
     double *out = wpsl + (size_t)blk * npsl;
     extern __shared__ double sraw_v[];
+    // the ring densities W_R / dr, one division per ring instead of two per
+    // PSL (the same correctly rounded quotients)
+    __shared__ double s_wd[32];
+    if ((int)threadIdx.x < n_r) s_wd[threadIdx.x] = W[threadIdx.x] / dr;
+    __syncthreads();
     for (int j = threadIdx.x; j < npsl; j += blockDim.x) {
         const int iy = j / nxy, ix = j % nxy;
         const double r = psl_radius(ix, iy, n_r, dr);                    // step 1
@@ -129,8 +134,8 @@ __device__ __forceinline__ void psl_weights_block(int blk, const double *__restr
         ring_interp(r, n_r, dr, &r0, &l0, &in);
         double dens = 0.0;                                               // step 2
         if (in) {
-            dens = l0 * (W[r0] / dr);
-            if (l0 < 1.0) dens += (1.0 - l0) * (W[r0 + 1] / dr);
+            dens = l0 * s_wd[r0];
+            if (l0 < 1.0) dens += (1.0 - l0) * s_wd[r0 + 1];
         }
         out[j] = dens / (2.0 * kPiD * r);                               // step 3
         sraw_v[j] = out[j];

@@ -806,17 +806,25 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
     double src = 0.0, rej = 0.0, esc = 0.0;
     Acc A = {{0.0f, 0.0f}, {0.0f, 0.0f}, 0.0f, 0ull, 0ull, 0ull, 0ull};
     unsigned long long nph = 0, nel = 0, nrej = 0, nmiss = 0;
-    for (int64_t base = warp * 32; base < S.n; base += nwarps * 32) {
+    // batch slot and plan position of this lane's history, (h0 + i) / plan and
+    // its remainder, advanced by the loop's stride without a 64-bit division
+    // per history
+    const int64_t stride = nwarps * 32;
+    const int64_t q_st = stride / S.plan, r_st = stride - q_st * S.plan;
+    int64_t slot_l = (S.h0 + warp * 32 + lane) / S.plan;
+    int64_t hpos_l = S.h0 + warp * 32 + lane - slot_l * S.plan;
+    for (int64_t base = warp * 32; base < S.n; base += stride) {
         const int64_t i = base + lane;
         const bool valid = i < S.n;
         SrcParticle o;
         o.stype = 0;
-        uint32_t slot = 0;
         bool in = false;
         float lx = 0.0f, ly = 0.0f, lz = 0.0f;
-        const int64_t hh = S.h0 + i;
-        slot = valid ? (uint32_t)(hh / S.plan) : 0u;
-        const int64_t hpos = hh - (int64_t)slot * S.plan;
+        const uint32_t slot = valid ? (uint32_t)slot_l : 0u;
+        const int64_t hpos = hpos_l;
+        hpos_l += r_st;
+        slot_l += q_st;
+        if (hpos_l >= S.plan) { hpos_l -= S.plan; ++slot_l; }
         const int64_t ek = find_entry_warp(S.sp.start, n_ent, hpos, valid);
         if (valid) {
             sample_history(S.sp, k0, k1, S.g0 + (uint64_t)i, hpos, S.z_rel, o, ek);
