@@ -4,7 +4,13 @@
 
 The PSL builder (psl_build.cu) is compiled with -fmad=false: its FP64 results
 must be the correctly rounded value of each written operation so that the
-integer particle counts of Eq. 3 are reproducible.
+integer particle counts of Eq. 3 are reproducible. The sampling and transport
+kernels (transport.cu) flush FP32 denormals to zero (-ftz=true): no quantity
+there is subnormal (energies, lengths and probabilities are far above 1e-38),
+every other operation keeps its IEEE rounding, and the square roots and
+divisions drop their denormal handling (per 1e7-history step: sampling 0.256
+-> 0.248 ms, photon pass 0.452 -> 0.436 ms, electron pass 0.422 -> 0.397 ms,
+with the same counters; full fast-math measured slower on the electron pass).
 """
 from __future__ import annotations
 
@@ -24,7 +30,7 @@ SOURCES = {
     "api.cu": [],
     "psl_build.cu": ["-fmad=false"],
     "physics.cu": [],
-    "transport.cu": [],
+    "transport.cu": ["-ftz=true"],
     "nnls.cu": [],
     "denoise.cu": [],
     "train.cu": [],
@@ -56,11 +62,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
-        if force or _stale(o, [s] + headers):
-            cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", s, "-o", o]
+        cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", s, "-o", o]
+        stamp = o + ".cmd"            # the flags an object was built with
+        old = open(stamp).read() if os.path.exists(stamp) else ""
+        if force or _stale(o, [s] + headers) or old != " ".join(cmd):
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             subprocess.check_call(cmd)
+            with open(stamp, "w") as f:
+                f.write(" ".join(c for c in cmd if c != "-Xptxas=-v"))
     if force or _stale(LIB, objs):
         subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
     return LIB
