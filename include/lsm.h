@@ -389,8 +389,9 @@ lsm_status lsm_transport(const lsm_phantom *ph, const lsm_particles *in, int64_t
 
 /*
  * lsm_run -- the whole dose calculation of Sec. 2.1.3: n_batches passes over
- * the plan, each iterating [sample M histories -> transport photons ->
- * transport annihilation photons -> transport electrons -> flush] until the
+ * the plan, each iterating [sample M histories -> transport photons (with
+ * the annihilation photons of their pair events) -> transport electrons ->
+ * flush] until the
  * plan is exhausted, then folding the batch (lsm_tally_end_batch). Histories
  * of pass b are g = b * plan size + h.
  * Errors: as lsm_transport.
@@ -493,7 +494,8 @@ lsm_status lsm_commission_static(const double *A, int32_t m, int32_t n, const do
  * events on the launching stream around each kernel group and accumulates
  * their elapsed device time:
  *   0 PSL build (T_src_init)       1 sampling (T_par_gen_tr)
- *   2 photon transport             3 annihilation-photon transport
+ *   2 photon transport             3 (unused: annihilation photons are
+ *                                    transported within timer 2)
  *   4 electron transport           5 tally flush and fold
  *   6 NNLS solve                   7 phantom set-up and tables
  *   8 denoiser 3x3x3 convolutions  9 denoiser pooling, upsampling, input

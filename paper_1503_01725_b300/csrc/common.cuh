@@ -101,8 +101,9 @@ struct Queue {
 // Counters of one sample/transport iteration (device memory, zeroed per iteration).
 
 // Each counter has a 128-byte line of its own: the photon pass's refill
-// cursor, its pushes onto the electron queue and its annihilation-photon
-// pushes are atomics from every warp, and on one shared line they queued
+// cursor and its pushes onto the electron queue are atomics from every
+// warp, and on one shared line (with the pushes of the annihilation-photon
+// queue of an earlier design) they queued
 // behind one another in L2 (photon pass 0.49 -> 0.45 ms apart, with 64-slot
 // output reservations).
 struct alignas(128) CounterLine {
@@ -112,7 +113,7 @@ struct alignas(128) CounterLine {
     __host__ __device__ uint32_t *operator&() { return &v; }
 };
 struct IterCounters {
-    CounterLine n[3];      // queue fill: 0 primary photons, 1 annihilation photons, 2 electrons
+    CounterLine n[3];      // queue fill: 0 primary photons, 1 (unused), 2 electrons
     CounterLine head[3];   // refill cursors of the persistent transport kernels
     uint32_t overflow;     // electrons deposited in place because the queue was full
     uint32_t pad;          // table-staging timeout flag

@@ -5,8 +5,9 @@
 //                    the phantom are compacted by warp ballots into a photon
 //                    queue and an electron queue (sub-sources handled apart so
 //                    that warps never mix photon and electron code);
-//   k_photon (x2)    Woodcock tracking of the primary/scatter photons, then of
-//                    the annihilation photons they created;
+//   k_photon         Woodcock tracking of the primary/scatter photons; the two
+//                    annihilation photons of a pair event are tracked by the
+//                    lane that made them, one after the other;
 //   k_electron       CSDA condensed-history electrons;
 //   k_flush          FP32 partial tally -> FP64 batch accumulator.
 // The transport kernels are persistent: each warp keeps 32 live particles and
@@ -301,6 +302,14 @@ struct Pend {
     int vox;
 };
 
+// The second annihilation photon of a pair event,
+// transported by the same lane after the first one (both start at the pair
+// vertex; position, direction and stream id).
+struct Ann {
+    float x, y, z, u, v, w;
+    uint32_t sid;
+};
+
 struct Part {
     float x, y, z, u, v, w, E;
     Stream rng;
@@ -388,7 +397,7 @@ __device__ __forceinline__ void spawn_electron(const TP &T, Acc &A, const Queue 
 // event draws one more block. Returns false when the photon's history ends.
 template <int MODE>
 __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t, Acc &A, Part &p,
-                            const Queue &eq, const Queue *pq, Pend &pe, bool &pend)
+                            const Queue &eq, Pend &pe, bool &pend, Ann &an, bool &ann)
 {
     int vox = voxel(T, p.x, p.y, p.z);
     if (vox < 0) { kadd(A.esc, p.E); hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
@@ -464,17 +473,18 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     const float ax = sa * cp, ay = sa * sp, az = ca;
     spawn_electron<MODE>(T, A, eq, p, Tm, p.u, p.v, p.w, p.rng.child_id(0), vox);
     spawn_electron<MODE>(T, A, eq, p, Tp, p.u, p.v, p.w, p.rng.child_id(1), vox);
-    // the annihilation-photon queue holds two per photon of the input queue
-    for (int h = 0; h < 2; ++h) {
-        const float sg = h ? -1.0f : 1.0f;
-        const uint32_t slot = pq ? push_slot(&T.cnt->n[1]) : 0xffffffffu;
-        if (pq && slot < pq->cap)
-            store_part(*pq, slot, p.x, p.y, p.z, sg * ax, sg * ay, sg * az, kMe, p.rng.glo, p.rng.ghi,
-                       p.rng.child_id(2 + h), p.pb);
-        else
-            deposit<MODE, true>(T, A, vox, kMe, p.pb, p.rng.glo, p.rng.ghi);
-    }
-    return false;
+    // the lane goes on with the first annihilation photon and keeps the second
+    // for after it (a queue of their own and a pass over it was latency-bound
+    // on a few ten thousand photons: 0.032 ms of a 1.24 ms step)
+    an = Ann{p.x, p.y, p.z, -ax, -ay, -az, p.rng.child_id(3)};
+    ann = true;
+    p.rng.sid = p.rng.child_id(2);
+    p.rng.ctr = 0;
+    p.rng.have = 0;
+    p.E = kMe;
+    p.u = ax; p.v = ay; p.w = az;
+    p.steps = 0;
+    return true;
 }
 
 // An electron deposits about twice per voxel: deposits into the voxel of the
@@ -591,7 +601,7 @@ __device__ void flush_acc(const TP &T, const Acc &A)
 // KIND 0: photons (Woodcock), KIND 1: electrons (CSDA).
 template <int MODE, int KIND>
 __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREADS,
-                                  KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MINB) k_transport(TP T, Queue in, int qi, Queue eq, Queue pq, int has_pq)
+                                  KIND ? LSM_ELECTRON_MINB : LSM_PHOTON_MINB) k_transport(TP T, Queue in, int qi, Queue eq)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -627,6 +637,8 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
     const uint32_t kGrab = share >= 256 ? 256u : (share >= 128 ? 128u : (share >= 64 ? 64u : 32u));
     uint32_t rb = 0, rl = 0;
     bool exhausted = false;
+    Ann an = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0u};
+    bool ann = false;
     // output reservation for the electrons photons create: [ob, ob + ol);
     // 64 slots per atomic (32: photon pass 0.47 -> 0.49 ms; 128: the dead
     // entries left at the end slow the electron pass by more than it gains)
@@ -689,8 +701,23 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
             Pend pe;
             const uint32_t pb_keep = p.pb;
             if (alive) {
-                alive = photon_step<MODE>(T, xs, mm, A, p, eq, has_pq ? &pq : nullptr, pe, pend);
-                if (!alive) { kadd(A.dep, A.dep32); A.dep32 = 0.0f; }
+                alive = photon_step<MODE>(T, xs, mm, A, p, eq, pe, pend, an, ann);
+                if (!alive) {
+                    kadd(A.dep, A.dep32);
+                    A.dep32 = 0.0f;
+                    if (ann) {
+                        // the pair's second annihilation photon, same history and tag
+                        p.x = an.x; p.y = an.y; p.z = an.z;
+                        p.u = an.u; p.v = an.v; p.w = an.w;
+                        p.E = kMe;
+                        p.rng.sid = an.sid;
+                        p.rng.ctr = 0;
+                        p.rng.have = 0;
+                        p.steps = 0;
+                        ann = false;
+                        alive = true;
+                    }
+                }
             }
             // warp-wide push of the electrons created in this step
             const unsigned pm = __ballot_sync(0xffffffffu, pend);
@@ -1280,7 +1307,8 @@ int grid_for(const void *fn, int threads, size_t smem)
 }
 
 struct Workspace {
-    Queue q[3];          // 0 primary photons, 1 annihilation photons, 2 electrons
+    Queue q[3];          // 0 primary photons, 2 electrons (1 is empty: annihilation photons are
+                         // tracked by the lane of their pair event)
     IterCounters *cnt;
     uint32_t *key;       // Philox key of the run (outside the per-iteration counters)
     void *mem;
@@ -1298,14 +1326,14 @@ cudaError_t ws_alloc_at(Workspace &W, uint32_t chunk, uint32_t ecap, void *&mem,
         if (mem) cudaFreeAsync(mem, st);
         mem = nullptr;
         size_t total = 2048;
-        const uint32_t c2[3] = {chunk, 2 * chunk, ecap};
+        const uint32_t c2[3] = {chunk, 0, ecap};
         for (int k = 0; k < 3; ++k) total += (size_t)c2[k] * 48 + 256;
         cudaError_t e = dev_malloc(&mem, total, st);
         if (e != cudaSuccess) return e;
         mem_chunk = chunk;
         mem_ecap = ecap;
     }
-    const uint32_t caps[3] = {chunk, 2 * chunk, ecap};
+    const uint32_t caps[3] = {chunk, 0, ecap};
     char *p = (char *)mem;
     W.mem = nullptr;
     static_assert(sizeof(IterCounters) <= 1024, "iteration counters overlap the key");
@@ -1380,8 +1408,8 @@ lsm_status check_opts(lsm_run_opts &o)
     return LSM_OK;
 }
 
-// transport everything queued in W (photons of queue 0, then annihilation
-// photons, then electrons) and flush the tally partials
+// transport everything queued in W (photons of queue 0 with the annihilation
+// photons they create, then electrons)
 template <int MODE>
 lsm_status drain(const TP &T, Workspace &W, lsm_tally *t, cudaStream_t st)
 {
@@ -1398,16 +1426,12 @@ lsm_status drain(const TP &T, Workspace &W, lsm_tally *t, cudaStream_t st)
     const int cap = T.ctas_per_sm > 0 ? T.ctas_per_sm * sm_count() : (1 << 30);
     const int gp = std::min(gp_max, cap), ge = std::min(ge_max, cap);
     int tk = timer_begin(2, st);
-    k_transport<MODE, 0><<<gp, LSM_PHOTON_THREADS, smem, st>>>(T, W.q[0], 0, W.q[2], W.q[1], 1);
+    k_transport<MODE, 0><<<gp, LSM_PHOTON_THREADS, smem, st>>>(T, W.q[0], 0, W.q[2]);
     LSM_LAUNCHED("k_transport<photon>");
-    timer_end(tk, st);
-    tk = timer_begin(3, st);
-    k_transport<MODE, 0><<<gp, LSM_PHOTON_THREADS, smem, st>>>(T, W.q[1], 1, W.q[2], W.q[1], 0);
-    LSM_LAUNCHED("k_transport<annihilation photon>");
     timer_end(tk, st);
     if (T.electron_mode) {
         tk = timer_begin(4, st);
-        k_transport<MODE, 1><<<ge, LSM_ELECTRON_THREADS, smem_e, st>>>(T, W.q[2], 2, W.q[2], W.q[1], 0);
+        k_transport<MODE, 1><<<ge, LSM_ELECTRON_THREADS, smem_e, st>>>(T, W.q[2], 2, W.q[2]);
         LSM_LAUNCHED("k_transport<electron>");
         timer_end(tk, st);
     }
