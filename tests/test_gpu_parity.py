@@ -42,10 +42,15 @@ def _models():
         (m2, W.beams(W.square_field(10.0)), 1_000_003),
         (m3, W.beams(W.square_field(4.0, cx=1.5, cy=-2.0), W.square_field(20.0),
                      np.array([-7.0, 2.0, -1.0, 9.0])), 777_777),
+        # 3.1e6 cells in four beams: the largest-remainder selection over a
+        # million included cells, 1136 of their remainders within 2^-11 of
+        # the threshold
+        (W.psr_model(64, 32, 0.1, seed=7),
+         W.beams(*[W.square_field(40.0, cx=0.3 * k, cy=-0.2 * k) for k in range(4)]), 10_000_019),
     ]
 
 
-@pytest.mark.parametrize("case", range(3))
+@pytest.mark.parametrize("case", range(4))
 def test_psl_build_bit_exact(L, case):
     m, b, n = _models()[case]
     g = L.lsm_build_psl(m, b, n)
