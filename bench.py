@@ -5,8 +5,9 @@
 
 One step is one pass of the whole hot path over one workload: PSR -> PSL
 conversion with sampling areas and Eq. 3 counts (lsm_build_psl), then n_batches
-passes of [sample M histories -> transport photons -> annihilation photons ->
-electrons -> tally flush] (lsm_run), then dose and batch uncertainty
+passes of [sample M histories -> transport photons (and the annihilation
+photons of their pair events) -> electrons -> tally flush] (lsm_run), then
+dose and batch uncertainty
 (lsm_dose). The workload is all three sub-sources, a 10x10 cm2 field, water
 64^3 at 0.25 cm, 1e7 histories, CSDA electrons (synthetic inputs from
 paper_1503_01725_b300.workloads). Prints one JSON line.

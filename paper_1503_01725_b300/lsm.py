@@ -774,6 +774,8 @@ def lsm_commission_static(A, b, x, method: int = 0, max_iter: int = 0, delta: fl
             "kkt": rep.kkt, "status": rc}
 
 
+# library timer indices (include/lsm.h); index 3 stays 0: annihilation photons
+# are transported, and timed, within the photon pass
 TIMER_NAMES = ("psl_build", "sample", "photon", "annihilation_photon", "electron", "tally", "nnls",
                "phantom", "conv3d", "denoise_other")
 
