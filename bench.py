@@ -904,11 +904,18 @@ def main():
                            "mat": torch.from_numpy(wl.phantom.mat).pin_memory()})
     out_d = torch.empty(wl.phantom.nvox, dtype=torch.float64).pin_memory()
     out_s = torch.empty(wl.phantom.nvox, dtype=torch.float64).pin_memory()
+    # the plan build is queued first; the phantom upload (whose validation
+    # waits on the host) and the tally go on a side stream meanwhile, and the
+    # run waits for both (1.434 -> 1.417 ms per one-at-a-time step, six A/B pairs)
+    side_of = {}
+
     def e2e_enqueue(i, stream):
-        phh = lsm.lsm_phantom_create(host_ph, stream=stream)          # host rho/mat -> device
-        phh.desc = wl.phantom
+        side = side_of.setdefault(stream, torch.cuda.Stream())
         psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True, stream=stream)   # host model -> handle -> device
-        tt = lsm.lsm_tally_create(phh, stream=stream)
+        phh = lsm.lsm_phantom_create(host_ph, stream=side)            # host rho/mat -> device
+        phh.desc = wl.phantom
+        tt = lsm.lsm_tally_create(phh, stream=side)
+        stream.wait_stream(side)
         lsm.lsm_run(psl, phh, tt, 5000 + i, e2e_opts, stream=stream)
         return phh, psl, tt, stream
 
@@ -957,7 +964,7 @@ def main():
     # leave nothing of the end-to-end steps behind: their handles freed, and
     # the memory pool (grown by two concurrent workspaces) trimmed back, so
     # that the device-timed steps start from the state they run in
-    del host_ph, outs, streams
+    del host_ph, outs, streams, side_of
     import gc
     gc.collect()
     torch.cuda.synchronize()
