@@ -402,10 +402,16 @@ template <int MODE>
 __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t, Acc &A, Part &p,
                             const Queue &eq, Pend &pe, bool &pend, Ann &an, bool &ann)
 {
-    int vox = voxel(T, p.x, p.y, p.z);
-    if (vox < 0) { kadd(A.esc, p.E); hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
-    if (p.E < kCutG) { deposit<MODE, true>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
-    if (++p.steps > T.max_steps) { A.cap++; deposit<MODE, true>(T, A, vox, p.E, p.pb, p.rng.glo, p.rng.ghi); return false; }
+    // A photon starts a flight inside the phantom with E at or above the
+    // cutoff: queued photons are checked where a lane loads them, a flight
+    // that leaves the phantom ends the photon, and a Compton event that takes
+    // E below the cutoff deposits it at once. So the top of a flight needs no
+    // voxel lookup (one per flight fewer: photon pass 0.441 -> 0.426 ms).
+    if (++p.steps > T.max_steps) {
+        A.cap++;
+        deposit<MODE, true>(T, A, voxel(T, p.x, p.y, p.z), p.E, p.pb, p.rng.glo, p.rng.ghi);
+        return false;
+    }
     const uint4 r = p.rng.next();
     int ti;
     float tf;
@@ -414,7 +420,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
     const float s = __fdividef(-__logf(u01(r.x)), mm);
     p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
     A.flights++;
-    vox = voxel(T, p.x, p.y, p.z);
+    const int vox = voxel(T, p.x, p.y, p.z);
     if (vox < 0) { kadd(A.esc, p.E); hl_add<MODE>(T, p.rng.glo, p.rng.ghi, 1, p.E); return false; }
     const float rm = __ldg(T.rhomat + vox);
     // the block of the next draw (next flight, or a pair event's) does not
@@ -451,6 +457,7 @@ __device__ bool photon_step(const TP &T, const float4 *xs, const float *mumax_t,
         } else {
             deposit<MODE, true>(T, A, vox, Te, p.pb, p.rng.glo, p.rng.ghi);
         }
+        if (E1 < kCutG) { deposit<MODE, true>(T, A, vox, E1, p.pb, p.rng.glo, p.rng.ghi); return false; }
         p.E = E1; p.u = u; p.v = v; p.w = w;
         return true;
     }
@@ -675,7 +682,18 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
             if (!alive) {
                 const uint32_t r = (uint32_t)__popc(need & lt);
                 const uint32_t i = r < rl ? rb + r : (grabbed ? nb + (r - rl) : 0xffffffffu);
-                if (i < n_in) { load_part(in, i, k0, k1, p); alive = true; }
+                if (i < n_in) {
+                    load_part(in, i, k0, k1, p);
+                    alive = true;
+                    // queued photons lie inside the phantom; one below the
+                    // photon cutoff (a caller's particle) deposits where it is
+                    if (KIND == 0 && p.E < kCutG) {
+                        deposit<MODE, true>(T, A, voxel(T, p.x, p.y, p.z), p.E, p.pb, p.rng.glo, p.rng.ghi);
+                        kadd(A.dep, A.dep32);
+                        A.dep32 = 0.0f;
+                        alive = false;
+                    }
+                }
             }
             if (grabbed) {
                 const uint32_t from_new = k - rl;
@@ -685,6 +703,17 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
                 rb += k;
                 rl = rl > k ? rl - k : 0;
             }
+        }
+        if (KIND == 0 && rl > 0 && rb < n_in) {
+            // the records the next refills take (the next 32 slots of the
+            // reservation, already in L2): one L1 prefetch per 128-byte line,
+            // so that a refilled lane's first flight does not wait on L2
+            // (photon pass 0.426 -> 0.421 ms; on the electron pass it cost
+            // 0.39 -> 0.405 ms, so electrons do without)
+            const uint32_t nrec = min(min(rl, 32u), n_in - rb);
+            const size_t line = (((size_t)rb * 48) >> 7) + lane;
+            if (line <= ((((size_t)rb + nrec) * 48 - 1) >> 7))
+                asm volatile("prefetch.global.L1 [%0];" ::"l"((const char *)in.rec + (line << 7)));
         }
         if (!__any_sync(0xffffffffu, alive)) break;
         if constexpr (KIND == 1) {
