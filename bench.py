@@ -50,16 +50,18 @@ FALLBACK_HBM_GBS = 6400.0
 #     tables (entries and prefix, a few hundred KB) are read once per launch and
 #     stay in cache for the lookups of every history;
 #   photon transport: per Woodcock flight one density load (4 B), per photon the
-#     queue read (48 B), per real interaction one tally update (8 B) or queue write (48 B);
+#     queue read (48 B), per electron it queues (the run's `secondaries`) the
+#     queue write (48 B), per other real interaction one tally update (8 B);
 #   electron transport: per CSDA step one density load (4 B) + one tally update
-#     (4 B read + 4 B write), per electron the queue read (48 B).
+#     (4 B read + 4 B write), per electron the queue read (48 B): source
+#     electrons and the secondaries.
 # DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # on a reduced case of this workload with the benchmark's 16 tally slices (4e6
 # histories in one iteration: 226.6 MB over 3,101,770 photons and the
-# annihilation photons they create; 112.3 MB over 9,896,378 electron steps;
+# annihilation photons they create; 112.2 MB over 9,896,378 electron steps;
 # ncu replays start from flushed caches).
 # Valid for the kernels as profiled; set to None when they change.
-TRAFFIC_PER_UNIT = {"photon": ("photons", 73.0), "electron": ("esteps", 11.34)}
+TRAFFIC_PER_UNIT = {"photon": ("photons", 73.0), "electron": ("esteps", 11.33)}
 B_SAMPLE_PER_ENTERING = 48.0
 B_FLIGHT = 4.0
 B_QUEUE = 48.0
@@ -1056,8 +1058,9 @@ def main():
     per_step = {k: v[0] / n_st for k, v in timers.items()}
     units = {
         "sample": (st["photons"] + st["electrons"]) * B_SAMPLE_PER_ENTERING,
-        "photon": st["flights"] * B_FLIGHT + st["photons"] * B_QUEUE + st["real"] * B_DEPOSIT,
-        "electron": st["esteps"] * B_ESTEP + st["electrons"] * B_QUEUE,
+        "photon": st["flights"] * B_FLIGHT + st["photons"] * B_QUEUE + st["secondaries"] * B_QUEUE
+        + max(st["real"] - st["secondaries"], 0) * B_DEPOSIT,
+        "electron": st["esteps"] * B_ESTEP + (st["electrons"] + st["secondaries"]) * B_QUEUE,
     }
     dom = max(("sample", "photon", "electron"), key=lambda k: per_step[k])
     achieved = units[dom] / (per_step[dom] / 1e3) / 1e9
@@ -1148,8 +1151,8 @@ def main():
         "s_to_1pct": t1, "u_mean_rel_D50": u,
         "kernels_ms_per_step": {k: round(v, 4) for k, v in per_step.items() if v > 0},
         "work_per_step": {"photons": st["photons"], "electrons": st["electrons"], "flights": st["flights"],
-                          "real": st["real"], "esteps": st["esteps"], "rejected": st["rejected"],
-                          "queue_overflows": st["overflows"]},
+                          "real": st["real"], "secondaries": st["secondaries"], "esteps": st["esteps"],
+                          "rejected": st["rejected"], "queue_overflows": st["overflows"]},
         "roofline": roofline,
         "l2_atomics": l2_atomics,
         "batched": batched,

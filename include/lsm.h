@@ -290,7 +290,7 @@ lsm_status lsm_tally_read(lsm_tally *t, double *s1, double *s2, lsm_mem mem, int
  * batch are cleared. Stream-ordered (host arrays are read before it returns).
  * Errors: LSM_ERR_ARG for a NULL tally or S1/S2, or n_batches < 0. */
 lsm_status lsm_tally_load(lsm_tally *t, const double *s1, const double *s2, int32_t n_batches,
-                          const double ledger[4], const int64_t stats[10], lsm_mem mem, lsm_stream stream);
+                          const double ledger[4], const int64_t stats[11], lsm_mem mem, lsm_stream stream);
 /*
  * lsm_tally_history_ledger -- a test mode: attach (ledger != NULL) or detach
  * (NULL) a per-history energy ledger to a dose (mode 0) tally. While attached,
@@ -310,8 +310,10 @@ lsm_status lsm_tally_history_ledger(lsm_tally *t, double *ledger, int64_t n_hist
 /* ledger (MeV): source, rejected, escaped (incl. missed), deposited.
  * stats: histories, accepted photons, accepted electrons, rejected, missed,
  * Woodcock flights, real photon interactions, electron steps, step-cap hits,
- * queue overflows. Synchronises. */
-lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], lsm_stream stream);
+ * queue overflows, secondary electrons (those photon interactions put on the
+ * electron queue: Compton, photoelectric and pair electrons at or above the
+ * electron cutoff, electron_mode 1). Synchronises. */
+lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[11], lsm_stream stream);
 
 /*
  * Transport options (the stated simplification of the paper's engine; the

@@ -789,7 +789,7 @@ typedef struct {
     double rho_max[2];
     double *acc;             /* batch accumulator */
     double dep, esc;         /* per-history ledger */
-    int64_t n_flight, n_real, n_esteps, n_cap;
+    int64_t n_flight, n_real, n_esteps, n_cap, n_sec;
     part_t *stack; int sp, cap;
     int64_t overflow;
 } tctx;
@@ -862,6 +862,7 @@ static void spawn_electron(tctx *T, const part_t *par, double Ee, double u, doub
     part_t c = *par;
     c.type = 1; c.E = Ee; c.u = u; c.v = v; c.w = w;
     c.rng.sid = sid; c.rng.ctr = 0; c.have = 0;
+    if (T->sp < T->cap) T->n_sec++;     /* a secondary electron handed to electron transport */
     push(T, &c);
 }
 
@@ -1038,9 +1039,10 @@ static void electron_track(tctx *T, part_t *p)
  * a run of B batches equals runs over disjoint batch ranges, summed).
  * s1/s2: per tally cell, the sum over batches of the batch total and of its
  * square (energy in MeV). ledger[4]: source, rejected, escaped (incl. missing
- * the phantom), deposited energy. stats[8]: histories, accepted photons,
+ * the phantom), deposited energy. stats[9]: histories, accepted photons,
  * accepted electrons, rejected, missed, Woodcock flights, real interactions,
- * electron steps. cons[2]: max per-history |balance| / E_source, step-cap hits.
+ * electron steps, secondary electrons (those photon interactions hand to
+ * electron transport). cons[2]: max per-history |balance| / E_source, step-cap hits.
  * per_hist (may be NULL): [n_batches*n_hist] energy deposited per history.
  */
 /*
@@ -1153,7 +1155,7 @@ OR_API int or_run(const void *h, const or_phantom *Ph, const or_opts *O, uint64_
             T.acc[c] = 0.0;
         }
     }
-    stats[5] = T.n_flight; stats[6] = T.n_real; stats[7] = T.n_esteps;
+    stats[5] = T.n_flight; stats[6] = T.n_real; stats[7] = T.n_esteps; stats[8] = T.n_sec;
     cons[1] = (double)T.n_cap + (double)T.overflow * 1e6;
     free(T.acc); free(T.stack);
     return 0;

@@ -280,7 +280,7 @@ def run(plan: Plan, phantom, seed: int, *, n_batches: int = 1, electron_mode: in
     s1 = np.zeros(ncell)
     s2 = np.zeros(ncell)
     ledger = np.zeros(4)
-    stats = np.zeros(8, dtype=np.int64)
+    stats = np.zeros(9, dtype=np.int64)
     cons = np.zeros(2)
     ph = np.zeros(plan.n_hist * n_batches) if per_history else None
     rc = lib().or_run(plan.h, C.byref(ps), C.byref(os_), seed, _ptr(s1), _ptr(s2), _ptr(ledger),
@@ -294,7 +294,7 @@ def run(plan: Plan, phantom, seed: int, *, n_batches: int = 1, electron_mode: in
         s1 = s1.reshape(plan.beams.n_beams * n_rows, n_psr)
         s2 = s2.reshape(plan.beams.n_beams * n_rows, n_psr)
     keys = ["histories", "photons", "electrons", "rejected", "missed", "flights", "real",
-            "esteps"]
+            "esteps", "secondaries"]
     return {"s1": s1, "s2": s2, "n_batches": n_batches,
             "ledger": dict(zip(["source", "rejected", "escaped", "deposited"], ledger)),
             "stats": dict(zip(keys, (int(v) for v in stats))),

@@ -469,7 +469,7 @@ lsm_status lsm_tally_read(lsm_tally *t, double *s1, double *s2, lsm_mem mem, int
 }
 
 lsm_status lsm_tally_load(lsm_tally *t, const double *s1, const double *s2, int32_t n_batches,
-                          const double ledger[4], const int64_t stats[10], lsm_mem mem, lsm_stream stream)
+                          const double ledger[4], const int64_t stats[11], lsm_mem mem, lsm_stream stream)
 {
     if (!t || !s1 || !s2) return set_arg_error("lsm_tally_load: NULL argument");
     if (n_batches < 0) return set_arg_error("lsm_tally_load: n_batches < 0");
@@ -482,7 +482,7 @@ lsm_status lsm_tally_load(lsm_tally *t, const double *s1, const double *s2, int3
     RunStats h;
     memset(&h, 0, sizeof(h));
     if (ledger) for (int i = 0; i < 4; ++i) h.ledger[i] = ledger[i];
-    if (stats) for (int i = 0; i < 10; ++i) h.c[i] = (unsigned long long)stats[i];
+    if (stats) for (int i = 0; i < 11; ++i) h.c[i] = (unsigned long long)stats[i];
     LSM_CUDA(cudaMemcpyAsync(t->d_stats, &h, sizeof(h), cudaMemcpyHostToDevice, st));
     // the host arrays (and the statistics staged above) are read before returning
     LSM_CUDA(cudaStreamSynchronize(st));
@@ -508,14 +508,14 @@ lsm_status lsm_tally_history_ledger(lsm_tally *t, double *ledger, int64_t n_hist
     return LSM_OK;
 }
 
-lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[10], lsm_stream stream)
+lsm_status lsm_tally_ledger(lsm_tally *t, double ledger[4], int64_t stats[11], lsm_stream stream)
 {
     if (!t) return set_arg_error("lsm_tally_ledger: NULL tally");
     RunStats h;
     LSM_CUDA(cudaMemcpyAsync(&h, t->d_stats, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
     LSM_CUDA(cudaStreamSynchronize(S(stream)));
     if (ledger) for (int i = 0; i < 4; ++i) ledger[i] = h.ledger[i];
-    if (stats) for (int i = 0; i < 10; ++i) stats[i] = (int64_t)h.c[i];
+    if (stats) for (int i = 0; i < 11; ++i) stats[i] = (int64_t)h.c[i];
     return LSM_OK;
 }
 

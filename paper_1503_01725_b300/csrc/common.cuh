@@ -117,12 +117,17 @@ struct IterCounters {
     CounterLine head[3];   // refill cursors of the persistent transport kernels
     uint32_t overflow;     // electrons deposited in place because the queue was full
     uint32_t pad;          // table-staging timeout flag
+    uint32_t src_e;        // electron-queue slots the source (sampler or a particle list) filled
+    uint32_t dead;         // electron-queue slots photon warps reserved and left empty
 };
 
 // Run-long statistics and the FP64 energy ledger.
 struct RunStats {
     double ledger[4];     // source, rejected, escaped, deposited (MeV)
-    unsigned long long c[10];
+    // histories, accepted photons, accepted electrons, rejected, missed,
+    // Woodcock flights, real photon interactions, electron steps, step-cap
+    // hits, queue overflows, electrons queued by photon transport
+    unsigned long long c[11];
 };
 
 // ---------------------------------------------------- interaction tables ---

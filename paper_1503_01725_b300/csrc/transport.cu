@@ -618,6 +618,12 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
     const uint32_t n_q = *(volatile uint32_t *)&T.cnt->n[qi];
     const uint32_t n_in = n_q < in.cap ? n_q : in.cap;     // pushes beyond capacity were not stored
     const uint32_t k0 = T.key[0], k1 = T.key[1];
+    if (KIND == 1 && blockIdx.x == 0 && threadIdx.x == 0) {
+        // the photon pass is complete: the electron queue holds the source's
+        // electrons, the secondaries of photon interactions and dead slots
+        const uint32_t other = T.cnt->src_e + T.cnt->dead;
+        if (n_in > other) atomicAdd(&T.stats->c[10], (unsigned long long)(n_in - other));
+    }
     // blocks whose first slot lies past the queue end have nothing to refill
     // from once the earlier blocks start: leave before staging the tables
     if ((uint64_t)blockIdx.x * blockDim.x >= n_in) return;
@@ -792,6 +798,7 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
         for (uint32_t j = lane; j < ol; j += 32)
             if (ob + j < eq.cap)
                 store_part(eq, ob + j, -1.0f, -1.0f, -1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0u, 0u, 2u, 0u);
+        if (lane == 0 && ob < eq.cap) atomicAdd(&T.cnt->dead, min(ol, eq.cap - ob));
     }
     flush_acc(T, A);
     if (!staged) drain_stage(&mbar);
@@ -910,7 +917,10 @@ __global__ void __launch_bounds__(256) k_sample_queue(SQ S, TP T, Queue pq, Queu
         uint32_t bp = 0, be = 0;
         if (lane == 0) {
             if (mp) bp = atomicAdd(&T.cnt->n[0], (uint32_t)__popc(mp));
-            if (me) be = atomicAdd(&T.cnt->n[2], (uint32_t)__popc(me));
+            if (me) {
+                be = atomicAdd(&T.cnt->n[2], (uint32_t)__popc(me));
+                atomicAdd(&T.cnt->src_e, (uint32_t)__popc(me));
+            }
         }
         bp = __shfl_sync(0xffffffffu, bp, 0);
         be = __shfl_sync(0xffffffffu, be, 0);
@@ -1004,7 +1014,10 @@ __global__ void k_enqueue(lsm_particles P, int64_t n, float x0, float y0, float 
         uint32_t bp = 0, be = 0;
         if (lane == 0) {
             if (mp) bp = atomicAdd(&T.cnt->n[0], (uint32_t)__popc(mp));
-            if (me) be = atomicAdd(&T.cnt->n[2], (uint32_t)__popc(me));
+            if (me) {
+                be = atomicAdd(&T.cnt->n[2], (uint32_t)__popc(me));
+                atomicAdd(&T.cnt->src_e, (uint32_t)__popc(me));
+            }
         }
         bp = __shfl_sync(0xffffffffu, bp, 0);
         be = __shfl_sync(0xffffffffu, be, 0);
@@ -1100,7 +1113,10 @@ __global__ void __launch_bounds__(256) k_pslfile_enqueue(const PslRec *__restric
         uint32_t bp = 0, be = 0;
         if (lane == 0) {
             if (mp) bp = atomicAdd(&T.cnt->n[0], (uint32_t)__popc(mp));
-            if (me) be = atomicAdd(&T.cnt->n[2], (uint32_t)__popc(me));
+            if (me) {
+                be = atomicAdd(&T.cnt->n[2], (uint32_t)__popc(me));
+                atomicAdd(&T.cnt->src_e, (uint32_t)__popc(me));
+            }
         }
         bp = __shfl_sync(0xffffffffu, bp, 0);
         be = __shfl_sync(0xffffffffu, be, 0);

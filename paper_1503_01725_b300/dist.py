@@ -21,7 +21,7 @@ from __future__ import annotations
 
 LEDGER_KEYS = ("source", "rejected", "escaped", "deposited")
 STAT_KEYS = ("histories", "photons", "electrons", "rejected", "missed", "flights", "real", "esteps",
-             "cap_hits", "overflows")
+             "cap_hits", "overflows", "secondaries")
 
 
 def batch_shard(n_batches: int, rank: int, world: int) -> tuple[int, int]:
@@ -54,7 +54,7 @@ def reduce_sums(s1, s2, n_batches: int, ledger: dict, stats: dict, group=None, d
     t1 = torch.as_tensor(s1, dtype=torch.float64, device=device).contiguous()
     t2 = torch.as_tensor(s2, dtype=torch.float64, device=device).contiguous()
     led = torch.tensor([float(ledger[k]) for k in LEDGER_KEYS], dtype=torch.float64, device=device)
-    cnt = torch.tensor([int(n_batches)] + [int(stats[k]) for k in STAT_KEYS], dtype=torch.int64, device=device)
+    cnt = torch.tensor([int(n_batches)] + [int(stats.get(k, 0)) for k in STAT_KEYS], dtype=torch.int64, device=device)
     allreduce_sum([t1, t2, led, cnt], group)
     c = cnt.cpu().tolist()
     return (t1, t2, c[0], dict(zip(LEDGER_KEYS, led.cpu().tolist())), dict(zip(STAT_KEYS, c[1:])))

@@ -516,6 +516,11 @@ def lsm_tally_read(t: Tally, stream=None, out=None):
     return s1, s2, nb.value
 
 
+# run statistics in the order lsm_tally_ledger returns them
+STAT_KEYS = ("histories", "photons", "electrons", "rejected", "missed", "flights", "real", "esteps",
+             "cap_hits", "overflows", "secondaries")
+
+
 def lsm_tally_load(t: Tally, s1, s2, n_batches: int, ledger=None, stats=None, stream=None):
     """Restore a checkpoint (S1, S2, folded batches, optional ledger and
     statistics dicts as lsm_tally_ledger returns them). S1, S2: host arrays or
@@ -533,9 +538,7 @@ def lsm_tally_load(t: Tally, s1, s2, n_batches: int, ledger=None, stats=None, st
     if ledger is not None:
         led = np.array([ledger[k] for k in ("source", "rejected", "escaped", "deposited")], dtype=np.float64)
     if stats is not None:
-        keys = ["histories", "photons", "electrons", "rejected", "missed", "flights", "real", "esteps",
-                "cap_hits", "overflows"]
-        st = np.array([stats[k] for k in keys], dtype=np.int64)
+        st = np.array([stats.get(k, 0) for k in STAT_KEYS], dtype=np.int64)
     p1 = a1.data_ptr() if dev else a1.ctypes.data
     p2 = a2.data_ptr() if dev else a2.ctypes.data
     _check(_lib.lsm_tally_load(t.ptr, p1, p2, int(n_batches),
@@ -546,12 +549,10 @@ def lsm_tally_load(t: Tally, s1, s2, n_batches: int, ledger=None, stats=None, st
 
 def lsm_tally_ledger(t: Tally, stream=None):
     led = np.zeros(4)
-    st = np.zeros(10, dtype=np.int64)
+    st = np.zeros(len(STAT_KEYS), dtype=np.int64)
     _check(_lib.lsm_tally_ledger(t.ptr, led.ctypes.data_as(_dp), st.ctypes.data_as(C.POINTER(C.c_int64)),
                                  _stream(stream)), "lsm_tally_ledger")
-    keys = ["histories", "photons", "electrons", "rejected", "missed", "flights", "real", "esteps",
-            "cap_hits", "overflows"]
-    return dict(zip(["source", "rejected", "escaped", "deposited"], led)), dict(zip(keys, (int(v) for v in st)))
+    return dict(zip(["source", "rejected", "escaped", "deposited"], led)), dict(zip(STAT_KEYS, (int(v) for v in st)))
 
 
 @dataclass

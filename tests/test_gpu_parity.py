@@ -268,7 +268,7 @@ def test_dose_parity_three_sources_csda(L):
     assert st["overflows"] == 0 and st["cap_hits"] == 0
     assert led["source"] == pytest.approx(led["rejected"] + led["escaped"] + led["deposited"], rel=1e-6)
     # algorithmic work within statistics of the oracle's counts
-    for k in ("flights", "real", "esteps"):
+    for k in ("flights", "real", "esteps", "secondaries"):
         assert st[k] == pytest.approx(r["stats"][k], rel=0.01), k
     assert st["electrons"] == r["stats"]["electrons"]
 

@@ -638,6 +638,19 @@ def test_energy_conservation_per_history(small_dose):
     assert r["cap_hits"] == 0
 
 
+def test_secondary_electron_count(small_dose):
+    """Electrons handed from photon interactions to CSDA transport (Sec. 2.3
+    cutoff 200 keV): none when electrons deposit where they are created; with
+    transport, at most two per real interaction (a pair event makes two) and
+    every one of them takes at least one CSDA step."""
+    wl, ph, p, r = small_dose
+    st = r["stats"]
+    assert 0 < st["secondaries"] <= 2 * st["real"]
+    assert st["esteps"] >= st["secondaries"]
+    r0 = O.run(p, ph, 5, n_batches=2, electron_mode=0)
+    assert r0["stats"]["secondaries"] == 0 and r0["stats"]["esteps"] == 0
+
+
 def test_dose_mirror_symmetry_of_centred_field(small_dose):
     wl, ph, p, r = small_dose
     d, sd = O.dose_and_sigma(r["s1"], r["s2"], r["n_batches"])
