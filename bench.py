@@ -390,7 +390,8 @@ def commissioning_block(lsm, W, reps: int = 3, n_batches: int = 16):
     scale = 1.0 / np.abs(bvec).max()
     out = {}
     f_opt = None
-    for method, name, it, delta in ((0, "active_set", 0, 1e-12), (1, "projected_gradient", 20000, 1e-12)):
+    for method, name, it, delta in ((0, "active_set", 0, 1e-12), (1, "projected_gradient", 20000, 1e-12),
+                                    (2, "projected_gradient_bb", 20000, 1e-12)):
         lsm.lsm_commission(Ag * scale, bvec * scale, method=method, max_iter=it, delta=delta)      # warm-up
         t0 = time.perf_counter()
         x, rep = lsm.lsm_commission(Ag * scale, bvec * scale, method=method, max_iter=it, delta=delta)
@@ -403,7 +404,8 @@ def commissioning_block(lsm, W, reps: int = 3, n_batches: int = 16):
         if method == 0:
             f_opt = rep["objective"]
         else:
-            # the paper's iteration (Sec. 2.2.4) with a bounded budget: its objective
+            # the paper's iteration (Sec. 2.2.4), and the same projection with
+            # Barzilai-Borwein steps, with a bounded budget: the objective
             # against the active-set minimum of the same problem
             out[name]["objective_gap_rel"] = (rep["objective"] - f_opt) / f_opt
     return {"workload": wl.name, "histories": hist, "A_shape": list(Ag.shape),

@@ -436,12 +436,15 @@ lsm_status lsm_basis_matrix_units(const lsm_tally *t, const lsm_psl *psl, const 
 /*
  * lsm_commission -- Eq. 8: x = argmin_{x >= 0} ||A x - b||^2 in FP64 on the
  * GPU. A: double [m][n] row-major, b: double [m], both in `mem`; x: host
- * double [n] (also the starting point of the projected-gradient method when
+ * double [n] (also the starting point of the projected-gradient methods when
  * opts->use_x0 != 0). method 0: active set (Lawson & Hanson) with the
  * passive-set least squares solved by Cholesky of the normal equations;
  * method 1: gradient projection with Armijo's rule (Sec. 2.2.4), stopped when
- * the relative change of F falls below delta. Synchronises.
- * Errors: LSM_ERR_ARG for m < 1, 1 > n > 1024 or NULL pointers;
+ * the relative change of F falls below delta; method 2: gradient projection
+ * with Barzilai-Borwein step lengths (alpha = d'd / (2 d'Gd) from the last
+ * move d, G = A'A) and the exact minimiser of F along each projected step,
+ * same stop (armijo_sigma and armijo_beta unused). Synchronises.
+ * Errors: LSM_ERR_ARG for m < 1, 1 > n > 1024, a method other than 0-2 or NULL pointers;
  * LSM_ERR_NOT_CONVERGED when max_iter was reached (x holds the last iterate).
  */
 typedef struct {

@@ -6,6 +6,9 @@ with one column of A per photon PSR and per effective electron unit.
 * ``gradient_projection`` follows Sec. 2.2.4: x^{k+1} = P(x^k - s_k grad F(x^k)),
   P(y) = max(0, y), s_k from Armijo's rule along the projection arc, stopped
   when the relative change of F between two iterations falls below delta.
+* ``gradient_projection_bb`` is the spectral projected gradient of Birgin,
+  Martinez & Raydan (2000): Barzilai & Borwein's (1988) step length and a
+  nonmonotone line search along the projected step.
 * ``lawson_hanson`` is the active-set method of Lawson & Hanson (1974), with the
   passive-set least-squares solved through the normal equations.
 * ``brute_force`` enumerates every support (tiny problems only).
@@ -61,6 +64,56 @@ def gradient_projection(A, b, x0=None, *, delta=1e-12, max_iter=200000, sigma=1e
         change = abs(F - Fn)
         x, Fprev, F = xn, F, Fn
         if change <= delta * max(Fprev, 1e-300):
+            return x, it, True
+    return x, max_iter, False
+
+
+def gradient_projection_bb(A, b, x0=None, *, delta=1e-12, max_iter=200000, memory=10, gamma=1e-4):
+    """Spectral projected gradient (Birgin, Martinez & Raydan 2000): the step
+    length before projection is Barzilai and Borwein's s's / s'y (s = x_k -
+    x_{k-1}, y = grad_k - grad_{k-1}; the first is s_bar = 1 / lambda_max(A^T A)).
+    Along d = P(x - alpha grad) - x the full step t = 1 is taken when F(x + t d)
+    <= max(last `memory` values of F) + gamma t grad'd (a nonmonotone test);
+    otherwise t becomes the minimiser of the quadratic through F(x), its slope
+    and F(x + t d), kept within [0.1 t, 0.9 t] (t / 2 outside). Stop when
+    P(x - alpha grad) = x or |F_k - F_{k+1}| <= delta * F_k.
+    Returns (x, iterations, converged)."""
+    m, n = A.shape
+    x = np.ones(n) if x0 is None else np.array(x0, dtype=np.float64)
+    x = np.maximum(x, 0.0)
+    G = A.T @ A
+    c = A.T @ b
+    v = np.ones(n) / np.sqrt(n)
+    for _ in range(100):
+        w = G @ v
+        v = w / np.linalg.norm(w)
+    s_bar = 1.0 / float(v @ G @ v)
+    alpha = s_bar
+    F = objective(A, b, x)
+    recent = [F]
+    grad = 2.0 * (G @ x - c)
+    for it in range(1, max_iter + 1):
+        d = np.maximum(x - alpha * grad, 0.0) - x
+        slope = float(grad @ d)
+        if not np.any(d) or slope >= 0.0:
+            return x, it, True
+        F_ref = max(recent)
+        t = 1.0
+        while True:
+            F_new = objective(A, b, x + t * d)
+            if F_new <= F_ref + gamma * t * slope or t < 1e-30:
+                break
+            t_q = -0.5 * t * t * slope / (F_new - F - t * slope)
+            t = t_q if 0.1 * t <= t_q <= 0.9 * t else 0.5 * t
+        x_new = x + t * d
+        grad_new = 2.0 * (G @ x_new - c)
+        s, y = x_new - x, grad_new - grad
+        sy = float(s @ y)
+        alpha = min(max(float(s @ s) / sy, 1e-12 * s_bar), 1e12 * s_bar) if sy > 0.0 else 1e12 * s_bar
+        change = abs(F - F_new)
+        x, grad, F_prev, F = x_new, grad_new, F, F_new
+        recent = (recent + [F])[-memory:]
+        if change <= delta * max(F_prev, 1e-300):
             return x, it, True
     return x, max_iter, False
 

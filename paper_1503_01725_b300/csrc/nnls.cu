@@ -77,6 +77,22 @@ __device__ double block_sum(double v, double *red)
     return red[32];
 }
 
+// Three block-wide sums in one pass (red: at least 97 doubles).
+__device__ void block_sum3(double &a, double &b, double &c, double *red)
+{
+    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) { red[w] = a; red[32 + w] = b; red[64 + w] = c; }
+    __syncthreads();
+    if (w == 0) {
+        const double ta = warp_sum(red[l]), tb = warp_sum(red[32 + l]), tc = warp_sum(red[64 + l]);
+        if (l == 0) { red[96] = ta; red[97] = tb; red[98] = tc; }
+    }
+    __syncthreads();
+    a = red[96]; b = red[97]; c = red[98];
+}
+
 // argmax of v over j with mask(j) true; returns index (-1 if none) and value
 __device__ int block_argmax(double v, int j, double *redv, int *redi, double *best)
 {
@@ -363,15 +379,30 @@ __global__ void __launch_bounds__(kT) k_lawson_hanson(const double *__restrict__
     }
 }
 
-// Gradient projection with Armijo's rule along the projection arc.
+constexpr int kSpgMemory = 10;        // nonmonotone line search: F compared with the max of the last 10
+constexpr double kSpgGamma = 1e-4;    // sufficient-decrease constant of that test
+
+// Gradient projection. bb = 0: Armijo's rule along the projection arc
+// (Sec. 2.2.4), every trial step starting from s_bar = 1 / lambda_max(G).
+// bb = 1: the spectral projected gradient of Birgin, Martinez & Raydan
+// (2000): the step length before projection is Barzilai and Borwein's
+// alpha = s's / s'y for the last move s and gradient change y, which on
+// F = x'Gx - 2c'x + const is d'd / (2 d'Gd) whatever the fraction t of d
+// taken; along d = P(x - alpha g) - x the full step is kept when F(x + t d)
+// <= max(last kSpgMemory values of F) + gamma t g'd, else t becomes the
+// minimiser of the quadratic through F(x), its slope and F(x + t d) (kept
+// within [0.1 t, 0.9 t], t / 2 outside). F is quadratic along d, F(x + t d) =
+// F + t g'd + t^2 d'Gd, so a trial costs no product with G. Both stop when
+// the relative change of F falls below delta.
 __global__ void __launch_bounds__(kT) k_projected_gradient(const double *__restrict__ G,
                                                            const double *__restrict__ cg, int n, double F0,
                                                            double delta, int max_iter, double sigma,
-                                                           double beta, double *__restrict__ xio, NnlsOut *out)
+                                                           double beta, int bb, double *__restrict__ xio,
+                                                           NnlsOut *out)
 {
     extern __shared__ double sm[];
     double *x = sm, *gx = sm + n, *g = sm + 2 * n, *d = sm + 3 * n, *gd = sm + 4 * n, *v = sm + 5 * n;
-    __shared__ double red[33];
+    __shared__ double red[99];
     for (int j = threadIdx.x; j < n; j += kT) { x[j] = fmax(xio[j], 0.0); v[j] = rsqrt((double)n); }
     __syncthreads();
     // s_bar = 1 / lambda_max(G) by power iteration
@@ -406,7 +437,47 @@ __global__ void __launch_bounds__(kT) k_projected_gradient(const double *__restr
     __syncthreads();
     double F = F0;
     int it = 0, conv = 0;
-    while (it < max_iter) {
+    double alpha = s_bar;
+    // the last kSpgMemory values of F (every thread holds the same copy);
+    // entries not yet written hold F0
+    double hist[kSpgMemory];
+    for (int k = 0; k < kSpgMemory; ++k) hist[k] = F0;
+    while (bb && it < max_iter) {
+        ++it;
+        for (int j = threadIdx.x; j < n; j += kT) {
+            g[j] = 2.0 * (gx[j] - cg[j]);
+            d[j] = fmax(x[j] - alpha * g[j], 0.0) - x[j];
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += kT) {
+            double q = 0.0;
+            const double *gr = G + (size_t)j * n;
+            for (int l = 0; l < n; ++l) q += gr[l] * d[l];
+            gd[j] = q;
+        }
+        __syncthreads();
+        double gdot = 0.0, dgd = 0.0, dd = 0.0;
+        for (int j = threadIdx.x; j < n; j += kT) { gdot += g[j] * d[j]; dgd += d[j] * gd[j]; dd += d[j] * d[j]; }
+        block_sum3(gdot, dgd, dd, red);
+        if (dd == 0.0 || gdot >= 0.0) { conv = 1; break; }       // P(x - alpha g) = x: x is stationary
+        double Fref = F;
+        for (int k = 0; k < kSpgMemory; ++k) Fref = fmax(Fref, hist[k]);
+        double t = 1.0, dF = gdot + dgd;
+        for (int trial = 0; trial < 200; ++trial) {
+            dF = t * gdot + t * t * dgd;                          // F(x + t d) - F(x)
+            if (F + dF <= Fref + kSpgGamma * t * gdot || t < 1e-30) break;
+            const double tq = -0.5 * t * t * gdot / (dF - t * gdot);
+            t = (tq >= 0.1 * t && tq <= 0.9 * t) ? tq : 0.5 * t;
+        }
+        for (int j = threadIdx.x; j < n; j += kT) { x[j] += t * d[j]; gx[j] += t * gd[j]; }
+        __syncthreads();
+        const double Fprev = F;
+        F = F + dF;
+        hist[it % kSpgMemory] = F;
+        alpha = dgd > 0.0 ? fmin(fmax(dd / (2.0 * dgd), 1e-12 * s_bar), 1e12 * s_bar) : 1e12 * s_bar;
+        if (fabs(dF) <= delta * fmax(Fprev, 1e-300)) { conv = 1; break; }
+    }
+    while (!bb && it < max_iter) {
         ++it;
         for (int j = threadIdx.x; j < n; j += kT) g[j] = 2.0 * (gx[j] - cg[j]);
         __syncthreads();
@@ -423,8 +494,8 @@ __global__ void __launch_bounds__(kT) k_projected_gradient(const double *__restr
             __syncthreads();
             double gdot = 0.0, dgd = 0.0;
             for (int j = threadIdx.x; j < n; j += kT) { gdot += g[j] * d[j]; dgd += d[j] * gd[j]; }
-            gdot = block_sum(gdot, red);
-            dgd = block_sum(dgd, red);
+            double unused = 0.0;
+            block_sum3(gdot, dgd, unused, red);
             dF = gdot + dgd;                      // F(x + d) - F(x)
             if (dF <= sigma * gdot || s < 1e-30) break;
             s *= beta;
@@ -510,7 +581,7 @@ lsm_status commission(const double *A, int32_t m, int32_t n, const double *b, ls
     if (!A || !b || !x || m < 1 || n < 1 || n > 1024) return set_arg_error("lsm_commission: need m >= 1, 1 <= n <= 1024");
     lsm_nnls_opts o = {0, 0, 1e-12, 1e-4, 0.5, 0};
     if (opts) o = *opts;
-    if (o.method != 0 && o.method != 1) return set_arg_error("lsm_commission: method must be 0 or 1");
+    if (o.method < 0 || o.method > 2) return set_arg_error("lsm_commission: method must be 0, 1 or 2");
     if (o.max_iter <= 0) o.max_iter = o.method == 0 ? 3 * n : 200000;
     if (!(o.delta > 0)) o.delta = 1e-12;
     if (!(o.armijo_sigma > 0 && o.armijo_sigma < 1)) o.armijo_sigma = 1e-4;
@@ -561,7 +632,7 @@ lsm_status commission(const double *A, int32_t m, int32_t n, const double *b, ls
             const size_t smem = (size_t)n * 8 * 6;
             cudaFuncSetAttribute(k_projected_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_projected_gradient<<<1, kT, smem, st>>>(G, c, n, f0.objective, o.delta, o.max_iter, o.armijo_sigma,
-                                                      o.armijo_beta, dx, dout);
+                                                      o.armijo_beta, o.method == 2, dx, dout);
             count_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) break;
         }
@@ -676,7 +747,7 @@ extern "C" lsm_status lsm_commission_static(const double *A, int32_t m, int32_t 
     if (lsm_status pc = check_device_pointer(x, "x")) return pc;
     lsm_nnls_opts o = {0, 0, 1e-12, 1e-4, 0.5, 0};
     if (opts) o = *opts;
-    if (o.method != 0 && o.method != 1) return set_arg_error("lsm_commission_static: method must be 0 or 1");
+    if (o.method < 0 || o.method > 2) return set_arg_error("lsm_commission_static: method must be 0, 1 or 2");
     if (o.max_iter <= 0) o.max_iter = o.method == 0 ? 3 * n : 200000;
     if (!(o.delta > 0)) o.delta = 1e-12;
     if (!(o.armijo_sigma > 0 && o.armijo_sigma < 1)) o.armijo_sigma = 1e-4;
@@ -709,7 +780,7 @@ extern "C" lsm_status lsm_commission_static(const double *A, int32_t m, int32_t 
         const size_t smem = (size_t)n * 8 * 6;
         LSM_CUDA(cudaFuncSetAttribute(k_projected_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_projected_gradient<<<1, kT, smem, st>>>(G, c, n, f0.objective, o.delta, o.max_iter, o.armijo_sigma,
-                                                  o.armijo_beta, x, dout);
+                                                  o.armijo_beta, o.method == 2, x, dout);
         LSM_LAUNCHED("k_projected_gradient");
     }
     NnlsOut keep, fin;

@@ -730,6 +730,25 @@ def test_gradient_projection_reaches_kkt_point():
     np.testing.assert_allclose(x, xs, atol=1e-5)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_spectral_projected_gradient_reaches_the_nnls_minimiser(seed):
+    """The Barzilai-Borwein projection (Birgin, Martinez & Raydan 2000) on
+    problems of rising condition number: its limit is the NNLS minimiser
+    (scipy's active-set solution), and it needs fewer iterations than the
+    Armijo projection of Sec. 2.2.4 (which at condition 1e5 does not converge
+    in 200,000)."""
+    cond = (20, 1e3, 1e5)[seed]
+    A, b = _rand_problem(80, 20, 40 + seed, cond=cond)
+    x, it, ok = N.gradient_projection_bb(A, b, delta=1e-15, max_iter=200000)
+    xs, _ = optimize.nnls(A, b)
+    assert ok
+    assert N.objective(A, b, x) == pytest.approx(N.objective(A, b, xs), rel=1e-8)
+    assert N.kkt_residual(A, b, x) < 1e-4 * np.linalg.norm(A.T @ b)
+    if seed < 2:
+        _, it_gp, _ = N.gradient_projection(A, b, delta=1e-15, max_iter=200000)
+        assert it < it_gp
+
+
 def test_noiseless_recovery():
     rng = np.random.default_rng(3)
     A = np.abs(rng.standard_normal((200, 30)))
