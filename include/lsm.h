@@ -241,6 +241,19 @@ typedef struct {
 } lsm_phantom_desc;
 
 lsm_status lsm_phantom_create(const lsm_phantom_desc *desc, lsm_phantom **out, lsm_stream stream);
+/* The same phantom without waiting on the host for the input check: the
+ * copies and set-up kernels are only queued on `stream`, so host code goes on
+ * at once (the end-to-end path of a dose calculation). The check's verdict
+ * stays on the device: runs on an invalid phantom transport nothing, and
+ * lsm_dose into host memory and lsm_phantom_check report LSM_ERR_ARG for it.
+ * rho/mat in pageable host memory are read before the call returns; in pinned
+ * host or device memory they must stay unchanged until `stream` has passed the
+ * call. Errors at the call: as lsm_phantom_create except the value check. */
+lsm_status lsm_phantom_create_async(const lsm_phantom_desc *desc, lsm_phantom **out, lsm_stream stream);
+/* The verdict of the phantom's input check (densities in [1e-4, 25], materials
+ * in {0, 1}): LSM_OK or LSM_ERR_ARG. Synchronises `stream`, which must be
+ * ordered after the creation. */
+lsm_status lsm_phantom_check(const lsm_phantom *ph, lsm_stream stream);
 /* Releases the phantom; its device memory returns to the device's memory
  * pool in the order of the legacy default stream (no device-wide wait). Work
  * using it on non-blocking streams must have completed. */

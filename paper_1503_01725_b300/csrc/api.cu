@@ -25,7 +25,7 @@ lsm_status build_psl(const lsm_model *, const lsm_beams *, int64_t, const int64_
                      bool);
 lsm_status free_psl(lsm_psl *);
 lsm_status resolve_psl(lsm_psl *);
-lsm_status create_phantom(const lsm_phantom_desc *, lsm_phantom **, cudaStream_t);
+lsm_status create_phantom(const lsm_phantom_desc *, lsm_phantom **, cudaStream_t, bool);
 void free_phantom(lsm_phantom *);
 lsm_status sample_public(const lsm_psl *, uint64_t, uint64_t, int64_t, double, const lsm_particles *, cudaStream_t);
 lsm_status transport_particles(const lsm_phantom *, const lsm_particles *, int64_t, uint64_t, lsm_tally *,
@@ -331,9 +331,27 @@ lsm_status lsm_sample(const lsm_psl *psl, uint64_t seed, uint64_t hist_begin, in
 lsm_status lsm_phantom_create(const lsm_phantom_desc *desc, lsm_phantom **out, lsm_stream stream)
 {
     const int tk = timer_begin(7, S(stream));
-    lsm_status rc = create_phantom(desc, out, S(stream));
+    lsm_status rc = create_phantom(desc, out, S(stream), false);
     timer_end(tk, S(stream));
     return rc;
+}
+
+lsm_status lsm_phantom_create_async(const lsm_phantom_desc *desc, lsm_phantom **out, lsm_stream stream)
+{
+    const int tk = timer_begin(7, S(stream));
+    lsm_status rc = create_phantom(desc, out, S(stream), true);
+    timer_end(tk, S(stream));
+    return rc;
+}
+
+lsm_status lsm_phantom_check(const lsm_phantom *ph, lsm_stream stream)
+{
+    if (!ph) return set_arg_error("lsm_phantom_check: NULL phantom");
+    unsigned bad = 0;
+    LSM_CUDA(cudaMemcpyAsync(&bad, ph->d_flags + 2, 4, cudaMemcpyDeviceToHost, S(stream)));
+    LSM_CUDA(cudaStreamSynchronize(S(stream)));
+    if (bad) return set_arg_error("lsm_phantom_check: densities must be in [1e-4, 25] and materials in {0, 1}");
+    return LSM_OK;
 }
 
 void lsm_phantom_destroy(lsm_phantom *ph) { free_phantom(ph); }

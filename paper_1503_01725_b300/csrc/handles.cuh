@@ -108,6 +108,8 @@ struct lsm_phantom {
     double *d_inv_mass;   // 1 / (rho V) per voxel (g^-1): the dose is the deposit times it
     float4 *d_xs;         // [2][kGrid]
     float *d_mumax;       // [kGrid] majorant at factor 1
+    unsigned *d_flags;    // [0..1] largest density per material (float bits), [2] nonzero: invalid input
+    int validated;        // 1: the input was checked on the host at creation (0: lsm_phantom_create_async)
     double rho_max[2];
 };
 

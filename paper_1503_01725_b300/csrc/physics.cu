@@ -164,6 +164,7 @@ void free_phantom(lsm_phantom *P)
     dev_free(P->d_inv_mass);
     dev_free(P->d_xs);
     dev_free(P->d_mumax);
+    dev_free(P->d_flags);
     free(P);
 }
 
@@ -209,7 +210,7 @@ cudaError_t shared_tables(cudaStream_t st, SharedTables **out)
 }
 }  // namespace
 
-lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStream_t st)
+lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStream_t st, bool deferred)
 {
     if (!D || !out || !D->rho || !D->mat) return set_arg_error("lsm_phantom_create: NULL argument");
     *out = nullptr;
@@ -234,7 +235,7 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     do {                                                                                \
         e = (call);                                                                     \
         if (e != cudaSuccess) {                                                         \
-            cudaStreamSynchronize(st); dev_free(d_bits); free_phantom(P);              \
+            cudaStreamSynchronize(st); free_phantom(P);                                 \
             return set_cuda_error(e, #call);                                            \
         }                                                                               \
     } while (0)
@@ -249,7 +250,8 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     CK(dev_malloc((void **)&P->d_xs, 2 * kGrid * sizeof(float4), st));
     // majorant followed by the inverse-KN table: staged into shared memory by one copy
     CK(dev_malloc((void **)&P->d_mumax, kGrid * 4 + kKnE * kKnU * 4, st));
-    CK(dev_malloc((void **)&d_bits, 16, st));
+    CK(dev_malloc((void **)&P->d_flags, 16, st));
+    d_bits = P->d_flags;
     CK(cudaMemcpyAsync(P->d_rho, D->rho, n * 4, kind, st));
     CK(cudaMemcpyAsync(P->d_mat, D->mat, n, kind, st));
     CK(cudaMemsetAsync(d_bits, 0, 16, st));
@@ -264,10 +266,17 @@ lsm_status create_phantom(const lsm_phantom_desc *D, lsm_phantom **out, cudaStre
     k_majorant<<<(kGrid + 127) / 128, 128, 0, st>>>(d_mutot, d_bits, P->d_mumax);
     CKL("k_majorant");
     CK(cudaMemcpyAsync(P->d_mumax + kGrid, tab->kn, kKnE * kKnU * 4, cudaMemcpyDeviceToDevice, st));
+    if (deferred) {
+        // the check's verdict stays on the device: the transport kernels skip
+        // an invalid phantom, and lsm_dose to host memory or
+        // lsm_phantom_check report it
+        P->validated = 0;
+        *out = P;
+        return LSM_OK;
+    }
     CK(cudaMemcpyAsync(bits, d_bits, 12, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    dev_free(d_bits);
-    d_bits = nullptr;
+    P->validated = 1;
     if (bits[2]) {
         free_phantom(P);
         return set_arg_error("lsm_phantom_create: densities must be in [1e-4, 25] and materials in {0, 1}");

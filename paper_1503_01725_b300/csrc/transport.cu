@@ -55,6 +55,7 @@ struct TP {
     int electron_mode, max_steps;
     float f_e, s_geo;
     const uint32_t *key;       // Philox key (seed) in device memory, so one captured graph serves every seed
+    const unsigned *ph_bad;    // nonzero: the phantom's input failed its check (transport does nothing)
     RunStats *stats;
     IterCounters *cnt;
     int ctas_per_sm;           // transport grid: CTAs per SM (0: as many as fit)
@@ -625,8 +626,10 @@ __global__ void __launch_bounds__(KIND ? LSM_ELECTRON_THREADS : LSM_PHOTON_THREA
         if (n_in > other) atomicAdd(&T.stats->c[10], (unsigned long long)(n_in - other));
     }
     // blocks whose first slot lies past the queue end have nothing to refill
-    // from once the earlier blocks start: leave before staging the tables
-    if ((uint64_t)blockIdx.x * blockDim.x >= n_in) return;
+    // from once the earlier blocks start: leave before staging the tables; a
+    // phantom whose input failed its check (a creation that left the check to
+    // the device) is not transported through
+    if ((uint64_t)blockIdx.x * blockDim.x >= n_in || *(volatile const unsigned *)T.ph_bad) return;
     float4 *s_xs = reinterpret_cast<float4 *>(smem);
     float *s_mm = reinterpret_cast<float *>(smem + 2 * kGrid * 16);
     const bool staged = stage_tables<KIND == 0>(s_xs, T.xs, T.mumax, &mbar, &T.cnt->pad, T.stage_polls);
@@ -1432,6 +1435,7 @@ TP make_tp(const lsm_phantom *ph, const lsm_tally *t, const lsm_run_opts &o, con
     const double sg = o.s_geo > 0 ? o.s_geo : 0.5 * fmin(ph->dx, fmin(ph->dy, ph->dz));
     T.s_geo = (float)sg;
     T.key = key;
+    T.ph_bad = ph->d_flags + 2;
     T.ctas_per_sm = o.ctas_per_sm;
     T.stage_polls = g_stage_polls;
     T.stats = t->d_stats;
@@ -1910,6 +1914,7 @@ lsm_status dose_impl(const lsm_tally *t, const lsm_phantom *ph, double scale, do
     const int64_t n = t->nvox;
     double *dd = dose, *ds = sigma;
     void *tmp = nullptr;
+    unsigned bad = 0;
     if (mem == LSM_MEM_HOST) {
         LSM_CUDA(dev_malloc(&tmp, (size_t)n * 16, st));
         dd = (double *)tmp;
@@ -1924,10 +1929,14 @@ lsm_status dose_impl(const lsm_tally *t, const lsm_phantom *ph, double scale, do
     if (e == cudaSuccess && mem == LSM_MEM_HOST) {
         e = cudaMemcpyAsync(dose, dd, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && sigma) e = cudaMemcpyAsync(sigma, ds, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
+        // a phantom created without the host check: its verdict comes back too
+        if (e == cudaSuccess && !ph->validated)
+            e = cudaMemcpyAsync(&bad, ph->d_flags + 2, 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     if (tmp) cudaFreeAsync(tmp, st);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_dose");
+    if (bad) return set_arg_error("lsm_dose: the phantom's densities must be in [1e-4, 25] and materials in {0, 1}");
     return LSM_OK;
 }
 

@@ -108,6 +108,8 @@ _EXPORTS = {
     "lsm_sample": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64, C.c_double,
                              C.POINTER(lsm_particles), C.c_void_p]),
     "lsm_phantom_create": (C.c_int, [C.POINTER(lsm_phantom_desc), C.POINTER(C.c_void_p), C.c_void_p]),
+    "lsm_phantom_create_async": (C.c_int, [C.POINTER(lsm_phantom_desc), C.POINTER(C.c_void_p), C.c_void_p]),
+    "lsm_phantom_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lsm_phantom_destroy": (None, [C.c_void_p]),
     "lsm_phantom_tables": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), _dp]),
     "lsm_tally_create": (C.c_int, [C.c_void_p, C.POINTER(lsm_tally_desc), C.POINTER(C.c_void_p),
@@ -419,7 +421,11 @@ def lsm_sample(psl: PSL, seed: int, hist_begin: int, n: int, z_surface: float = 
     return out
 
 
-def lsm_phantom_create(ph, stream=None) -> PhantomHandle:
+def lsm_phantom_create(ph, stream=None, async_: bool = False) -> PhantomHandle:
+    """Phantom on the device. async_: only queue the copies and set-up kernels
+    (lsm_phantom_create_async); the input check's verdict is reported by
+    lsm_dose into host memory or lsm_phantom_check. The handle keeps `ph` (and
+    so its arrays) alive."""
     L = load_library()
     import torch
     rho = ph.rho if isinstance(ph.rho, torch.Tensor) else np.ascontiguousarray(ph.rho, dtype=np.float32)
@@ -431,10 +437,17 @@ def lsm_phantom_create(ph, stream=None) -> PhantomHandle:
                          z0=ph.z0, rho=ptr(rho), mat=ptr(mat),
                          mem=LSM_MEM_DEVICE if dev else LSM_MEM_HOST)
     out = C.c_void_p()
-    _check(L.lsm_phantom_create(C.byref(d), C.byref(out), _stream(stream)), "lsm_phantom_create")
+    fn = L.lsm_phantom_create_async if async_ else L.lsm_phantom_create
+    _check(fn(C.byref(d), C.byref(out), _stream(stream)), "lsm_phantom_create")
     h = PhantomHandle(out)
     h.desc = ph
+    h.arrays = (rho, mat)
     return h
+
+
+def lsm_phantom_check(ph: PhantomHandle, stream=None):
+    """Raise LSMError (LSM_ERR_ARG) when the phantom's input failed its check."""
+    _check(_lib.lsm_phantom_check(ph.ptr, _stream(stream)), "lsm_phantom_check")
 
 
 def lsm_phantom_tables(ph: PhantomHandle):

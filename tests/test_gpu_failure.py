@@ -145,3 +145,41 @@ def test_conv_wait_timeout_is_reported_and_recovers(L):
         L.lsm_timing_enable(False)
     again = L.lsm_unet_forward(u, dose, rho)
     assert np.array_equal(again, ref)
+
+
+def test_async_phantom_equals_checked_one_and_reports_bad_input_later(L):
+    """lsm_phantom_create_async leaves the input check to the device: a valid
+    phantom gives the dose of the checked creation (same seed and histories);
+    an invalid one (a density above 25 g/cm^3) is created, transports nothing,
+    and lsm_dose into host memory and lsm_phantom_check report LSM_ERR_ARG."""
+    wl = _case(20_000)
+    g = L.lsm_build_psl(wl.model, wl.beams, wl.n_hist)
+    scale = g.denom / wl.n_hist
+    doses = []
+    for async_ in (False, True):
+        ph = L.lsm_phantom_create(wl.phantom, async_=async_)
+        t = L.lsm_tally_create(ph)
+        assert L.lsm_run(g, ph, t, wl.seed, L.RunOpts(electron_mode=1, n_batches=4)) == L.LSM_OK
+        doses.append(L.lsm_dose(t, ph, scale)[0])
+        L.lsm_phantom_check(ph)
+    np.testing.assert_allclose(doses[1], doses[0], rtol=1e-5, atol=1e-9 * doses[0].max())
+    bad = W.Phantom(**{**wl.phantom.__dict__, "rho": wl.phantom.rho.copy()})
+    bad.rho.flat[bad.rho.size // 2] = 30.0
+    with pytest.raises(L.LSMError):
+        L.lsm_phantom_create(bad)
+    ph = L.lsm_phantom_create(bad, async_=True)
+    t = L.lsm_tally_create(ph)
+    rc = L.lsm_run(g, ph, t, wl.seed, L.RunOpts(electron_mode=1, n_batches=2, no_sync=True, max_steps=50))
+    assert rc == L.LSM_OK
+    with pytest.raises(L.LSMError) as e:
+        L.lsm_dose(t, ph, scale)
+    assert e.value.status == L.LSM_ERR_ARG
+    with pytest.raises(L.LSMError):
+        L.lsm_phantom_check(ph)
+    s1, _, _ = L.lsm_tally_read(t)
+    assert not np.any(s1)
+    # the library stays usable
+    ph2 = L.lsm_phantom_create(wl.phantom, async_=True)
+    t2 = L.lsm_tally_create(ph2)
+    assert L.lsm_run(g, ph2, t2, wl.seed, L.RunOpts(electron_mode=1, n_batches=2)) == L.LSM_OK
+    L.lsm_phantom_check(ph2)
