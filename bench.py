@@ -707,6 +707,37 @@ def precision_vs_oracle(keep, n_o: int = 6_000_000, plan_o: int = 375_000):
             "oracle_max_history_imbalance": float(r["max_balance"])}
 
 
+def headline_vs_oracle(keep, seed: int = 23):
+    """CPU-baseline leg of the headline workload: the FP64 oracle runs the
+    same plan (the step's 16 batches of its batch-size plan, one seed of its
+    own) on the host's cores, and its dose per history is compared voxel by
+    voxel with the GPU's FP32 step: fraction of |z| < 3 over voxels above 10 %
+    of the maximum (chosen on another GPU step), and the mean dose ratio with
+    its statistical sigma."""
+    from oracle import oracle as O
+    from oracle import pool
+    nz, ny, nx = keep["shape"]
+    box = ((0, nz), (0, ny), (0, nx))
+    nb = keep["n_batches"]
+    r = pool.run_batches("workload_full_10x10", keep["n_hist"], keep["n_plan"], nb, seed=seed, box=box)
+    dg, sg = O.dose_and_sigma(keep["s1"], keep["s2"], nb)
+    dg, sg = dg.reshape(nz, ny, nx) / keep["n_hist"], sg.reshape(nz, ny, nx) / keep["n_hist"]
+    n_o = keep["n_plan"] * nb
+    do, so = O.dose_and_sigma(r["s1"], r["s2"], nb)
+    do, so = do / n_o, so / n_o
+    ref = keep["select"].reshape(nz, ny, nx)
+    sel = ref > 0.1 * ref.max()
+    z = (dg - do)[sel] / np.sqrt(sg[sel] ** 2 + so[sel] ** 2 + 1e-300)
+    ratio = float(dg[sel].sum() / do[sel].sum())
+    sig_ratio = float(np.sqrt((sg[sel] ** 2).sum()) / dg[sel].sum() + np.sqrt((so[sel] ** 2).sum()) / do[sel].sum())
+    return {"kind": "oracle", "value": n_o / r["run_s"], "unit": "histories/s", "cores": r["processes"],
+            "sample": f"{n_o} histories of the headline workload as {nb} batches of {keep['n_plan']} over "
+                      f"{r['processes']} processes, {r['wall_s']:.1f} s with set-up",
+            "voxels_compared": int(sel.sum()), "z_pass_frac": float(np.mean(np.abs(z) < 3)),
+            "mean_dose_ratio_gpu_over_oracle": ratio, "mean_dose_ratio_sigma": sig_ratio,
+            "oracle_max_history_imbalance": float(r["max_balance"])}
+
+
 def _fs_type(path: str) -> str:
     """File-system type of the mount holding `path` (from /proc/mounts)."""
     best, kind = "", "unknown"
@@ -1094,6 +1125,18 @@ def main():
             l2_atomics[f"{k}_steps_per_s"] = r
             l2_atomics[f"{k}_frac"] = r / peak_at if peak_at > 0 else None
 
+    # two more (untimed) steps of the headline workload for its comparison with
+    # the FP64 oracle in the CPU leg: the first chooses the voxels, the second
+    # is compared (no selection bias)
+    keep_h = None
+    if not args.no_cpu_baseline and world == 1:
+        step(7001)
+        sel_h, _, _ = lsm.lsm_tally_read(tally)
+        step(7002)
+        s1_h, s2_h, nb_h = lsm.lsm_tally_read(tally)
+        keep_h = {"s1": s1_h, "s2": s2_h, "n_batches": nb_h, "n_hist": args.n_hist, "select": sel_h,
+                  "n_plan": n_plan, "shape": wl.phantom.rho.shape}
+
     # the other blocks run after the timed steps: run before them, the PSL-file
     # block (file writes and reads of 0.5 GB, a memory pool grown to 5.6 GB)
     # was measured to slow the plan build's kernel launches in later steps
@@ -1134,6 +1177,9 @@ def main():
                          f"(disjoint seeds), {el:.1f} s",
                "one_core": {"value": rate1, "cores": 1,
                             "sample": f"{n_done1} histories as 1e5-history plans, {el1:.1f} s"}}
+        if keep_h is not None:
+            # the headline dose's error against the FP64 oracle, same workload and size
+            cpu["headline_vs_oracle"] = headline_vs_oracle(keep_h)
         if keep is not None:
             # the precision case's error against the FP64 oracle (FP32 transport, FP32 partials)
             cpu["precision_case"] = precision_vs_oracle(keep)
