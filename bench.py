@@ -57,11 +57,11 @@ FALLBACK_HBM_GBS = 6400.0
 #     electrons and the secondaries.
 # DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # on a reduced case of this workload with the benchmark's 16 tally slices (4e6
-# histories in one iteration: 226.6 MB over 3,101,770 photons and the
+# histories in one iteration: 227.0 MB over 3,101,770 photons and the
 # annihilation photons they create; 112.2 MB over 9,896,378 electron steps;
 # ncu replays start from flushed caches).
 # Valid for the kernels as profiled; set to None when they change.
-TRAFFIC_PER_UNIT = {"photon": ("photons", 73.0), "electron": ("esteps", 11.33)}
+TRAFFIC_PER_UNIT = {"photon": ("photons", 73.2), "electron": ("esteps", 11.34)}
 B_SAMPLE_PER_ENTERING = 48.0
 B_FLIGHT = 4.0
 B_QUEUE = 48.0
