@@ -939,18 +939,14 @@ def main():
                            "mat": torch.from_numpy(wl.phantom.mat).pin_memory()})
     out_d = torch.empty(wl.phantom.nvox, dtype=torch.float64).pin_memory()
     out_s = torch.empty(wl.phantom.nvox, dtype=torch.float64).pin_memory()
-    # the plan build is queued first; the phantom upload (its input check left
-    # to the device, reported by lsm_dose) and the tally go on a side stream
-    # meanwhile, and the run waits for both
-    side_of = {}
-
+    # every call only queues its work on the step's stream (the phantom's
+    # input check is left to the device and reported by lsm_dose); the host
+    # waits once, for the dose
     def e2e_enqueue(i, stream):
-        side = side_of.setdefault(stream, torch.cuda.Stream())
-        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True, stream=stream)   # host model -> handle -> device
-        phh = lsm.lsm_phantom_create(host_ph, stream=side, async_=True)   # host rho/mat -> device
+        phh = lsm.lsm_phantom_create(host_ph, stream=stream, async_=True)   # host rho/mat -> device
         phh.desc = wl.phantom
-        tt = lsm.lsm_tally_create(phh, stream=side)
-        stream.wait_stream(side)
+        psl = lsm.lsm_build_psl(wl.model, wl.beams, n_plan, async_=True, stream=stream)   # host model -> handle -> device
+        tt = lsm.lsm_tally_create(phh, stream=stream)
         lsm.lsm_run(psl, phh, tt, 5000 + i, e2e_opts, stream=stream)
         return phh, psl, tt, stream
 
@@ -999,7 +995,7 @@ def main():
     # leave nothing of the end-to-end steps behind: their handles freed, and
     # the memory pool (grown by two concurrent workspaces) trimmed back, so
     # that the device-timed steps start from the state they run in
-    del host_ph, outs, streams, side_of
+    del host_ph, outs, streams
     import gc
     gc.collect()
     torch.cuda.synchronize()
