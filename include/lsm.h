@@ -245,7 +245,8 @@ lsm_status lsm_phantom_create(const lsm_phantom_desc *desc, lsm_phantom **out, l
  * copies and set-up kernels are only queued on `stream`, so host code goes on
  * at once (the end-to-end path of a dose calculation). The check's verdict
  * stays on the device: runs on an invalid phantom transport nothing, and
- * lsm_dose into host memory and lsm_phantom_check report LSM_ERR_ARG for it.
+ * lsm_dose and lsm_basis_matrix(_units) into host memory and
+ * lsm_phantom_check report LSM_ERR_ARG for it.
  * rho/mat in pageable host memory are read before the call returns; in pinned
  * host or device memory they must stay unchanged until `stream` has passed the
  * call. Errors at the call: as lsm_phantom_create except the value check. */

@@ -1978,12 +1978,17 @@ lsm_status basis_impl(const lsm_tally *t, const lsm_psl *P, const lsm_phantom *p
         count_launch();
         e = cudaGetLastError();
     }
+    unsigned bad = 0;
     if (e == cudaSuccess && mem == LSM_MEM_HOST) {
         e = cudaMemcpyAsync(A, dA, (size_t)ncell * 8, cudaMemcpyDeviceToHost, st);
+        // a phantom created without the host check: its verdict comes back too
+        if (e == cudaSuccess && !ph->validated)
+            e = cudaMemcpyAsync(&bad, ph->d_flags + 2, 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     cudaFreeAsync(tmp, st);
     if (e != cudaSuccess) return set_cuda_error(e, "lsm_basis_matrix");
+    if (bad) return set_arg_error("lsm_basis_matrix: the phantom's densities must be in [1e-4, 25] and materials in {0, 1}");
     return LSM_OK;
 }
 
