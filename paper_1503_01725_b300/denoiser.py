@@ -166,7 +166,7 @@ def load(path: str = WEIGHTS):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--cases", type=int, default=W.DENOISE_CASES)
-    ap.add_argument("--epochs", type=int, default=120)
+    ap.add_argument("--epochs", type=int, default=240)
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--n-lo", type=int, default=1_000_000)
     ap.add_argument("--n-hi", type=int, default=100_000_000)
