@@ -130,3 +130,19 @@ def test_library_has_no_unresolved_own_symbols(lib):
     out = subprocess.check_output(["nm", "-D", "--undefined-only", LIB], text=True)
     own = [ln for ln in out.splitlines() if "_ZN3lsm" in ln or " lsm_" in ln]
     assert not own, own
+
+
+def test_run_statistics_layout_agrees_across_header_binding_and_reduction():
+    """lsm_tally_ledger and lsm_tally_load exchange one int64 array of run
+    statistics: the header's length, the binding's keys and the multi-GPU
+    reduction's keys must agree, and the header must list them in that order."""
+    from paper_1503_01725_b300 import dist, lsm
+    txt = open(HDR).read()
+    sizes = set(re.findall(r"int64_t stats\[(\d+)\]", txt))
+    assert sizes == {str(len(lsm.STAT_KEYS))}
+    assert tuple(dist.STAT_KEYS) == tuple(lsm.STAT_KEYS)
+    doc = re.search(r"stats: histories, accepted photons.*?Synchronises", txt, re.S).group(0)
+    order = ["histories", "accepted photons", "accepted electrons", "rejected", "missed", "Woodcock flights",
+             "real photon interactions", "electron steps", "step-cap hits", "queue overflows", "secondary electrons"]
+    pos = [doc.find(w) for w in order]
+    assert all(p >= 0 for p in pos) and pos == sorted(pos) and len(order) == len(lsm.STAT_KEYS)
